@@ -1,0 +1,330 @@
+"""Pins of the FP64 CPU oracle against results fixed by the mathematics and the textbooks,
+independent of the oracle's own code: exact Riemann solutions (Toro), the Sedov-Taylor
+similarity radius, discrete conservation, axis-permutation symmetry, second-order convergence,
+HLLC special cases, a brute-force first step, the CFL formula, and the two derivative modes
+(dual-number tangent vs central differences; reverse tape vs tangent by the dot-product test)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import riemann_exact, sedov
+from conftest import golden_rows
+
+G = 2
+
+
+# ----------------------------------------------------------------------------- helpers
+def edge_ghosts(U):
+    """Zero-gradient ghosts on every side."""
+    return np.pad(U, ((0, 0), (G, G), (G, G), (G, G)), mode="edge")
+
+
+def run_edge(U, dx, t_end, cfg):
+    """Advance with zero-gradient boundaries to t_end, dt from the CFL condition."""
+    t = 0.0
+    while t < t_end - 1e-15:
+        Ug = edge_ghosts(U)
+        dt = min(oracle.cfl_patch(Ug, dx, cfg), t_end - t)
+        U = oracle.step_patch(Ug, dx, dt, cfg)
+        t += dt
+    return U
+
+
+def phys_flux_x(rho, u, v, w, p, gamma):
+    E = p / (gamma - 1) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.array([rho * u, rho * u * u + p, rho * u * v, rho * u * w, u * (E + p)])
+
+
+# ----------------------------------------------------------------------------- exact solvers
+def test_exact_riemann_matches_toro_table():
+    for row in golden_rows("toro_riemann_star.txt"):
+        _, rl, ul, pl, rr, ur, pr, ps, us, rls, rrs = row
+        p, u = riemann_exact.star_state((rl, ul, pl), (rr, ur, pr), 1.4)
+        s = riemann_exact.sample((rl, ul, pl), (rr, ur, pr), 1.4, np.array([u - 1e-9, u + 1e-9]))
+        assert p == pytest.approx(ps, rel=1e-5, abs=6e-6)
+        assert u == pytest.approx(us, rel=1e-5, abs=6e-6)
+        assert s[0, 0] == pytest.approx(rls, rel=1.5e-4)
+        assert s[0, 1] == pytest.approx(rrs, rel=1.5e-4)
+
+
+def test_sedov_constant_matches_tables():
+    for g, x in golden_rows("sedov_xi0.txt"):
+        assert sedov.xi0(g) == pytest.approx(x, abs=1.5e-3)
+
+
+# ----------------------------------------------------------------------------- HLLC special cases
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hllc_consistency_equal_states(d):
+    cfg = oracle.config()
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        q = np.array([rng.uniform(0.1, 3), *rng.normal(0, 1, 3), rng.uniform(0.1, 3)])
+        F = oracle.hllc(q, q, d, cfg)
+        # physical flux written independently, rotated so that direction d is normal
+        perm = [0, 1 + d] + [1 + m for m in range(3) if m != d] + [4]
+        qr = q[perm]
+        Fr = phys_flux_x(*qr, cfg.gamma)
+        Fexp = np.empty(5)
+        Fexp[perm] = Fr
+        np.testing.assert_allclose(F, Fexp, rtol=1e-13, atol=1e-13 * np.abs(Fexp).max())
+
+
+def test_hllc_stationary_contact_has_no_mass_flux():
+    cfg = oracle.config()
+    for d in range(3):
+        qL = np.array([1.0, 0, 0, 0, 0.7])
+        qR = np.array([0.2, 0, 0, 0, 0.7])
+        F = oracle.hllc(qL, qR, d, cfg)
+        expect = np.zeros(5)
+        expect[1 + d] = 0.7
+        np.testing.assert_allclose(F, expect, atol=1e-15)
+
+
+def test_hllc_supersonic_is_upwind():
+    cfg = oracle.config()
+    qL = np.array([1.0, 5.0, 0.3, -0.2, 0.5])
+    qR = np.array([0.5, 4.0, 0.1, 0.2, 0.4])
+    F = oracle.hllc(qL, qR, 0, cfg)
+    np.testing.assert_array_equal(F, phys_flux_x(*qL, cfg.gamma))
+    qL2, qR2 = qR.copy(), qL.copy()
+    qL2[1], qR2[1] = -4.0, -5.0
+    F2 = oracle.hllc(qL2, qR2, 0, cfg)
+    np.testing.assert_allclose(F2, phys_flux_x(*qR2, cfg.gamma), rtol=1e-15)
+
+
+# ----------------------------------------------------------------------------- brute-force first step
+def test_first_step_of_single_jump_is_godunov_hllc():
+    """A single jump has zero limited slopes everywhere (minmod(0, jump) = 0), so the first step
+    only changes the two cells beside the jump, by the HLLC flux of the two states."""
+    cfg = oracle.config()
+    n = 8
+    left, right = (1.0, 0.3, 1.0), (0.4, -0.1, 0.3)
+    U = workloads.riemann_1d(n, left, right, axis=0, ntrans=3).numpy()
+    dx, dt = 1.0 / n, 0.01
+    V = oracle.step_patch(edge_ghosts(U), dx, dt, cfg)
+    qL = np.array([left[0], left[1], 0, 0, left[2]])
+    qR = np.array([right[0], right[1], 0, 0, right[2]])
+    Fm = oracle.hllc(qL, qR, 0, cfg)
+    FL, FR = phys_flux_x(*qL, cfg.gamma), phys_flux_x(*qR, cfg.gamma)
+    i = n // 2
+    for j in range(3):
+        for k in range(3):
+            np.testing.assert_allclose(V[:, k, j, i - 1], U[:, k, j, i - 1] - dt / dx * (Fm - FL), rtol=1e-14,
+                                       atol=1e-15)
+            np.testing.assert_allclose(V[:, k, j, i], U[:, k, j, i] - dt / dx * (FR - Fm), rtol=1e-14, atol=1e-15)
+    others = [c for c in range(n) if c not in (i - 1, i)]
+    np.testing.assert_array_equal(V[:, :, :, others], U[:, :, :, others])
+
+
+def test_uniform_state_is_a_fixed_point():
+    cfg = oracle.config()
+    U = workloads.cons_from_prim(*[__import__("torch").full((5, 6, 7), x, dtype=__import__("torch").float64)
+                                   for x in (1.3, 0.2, -0.4, 0.1, 0.9)]).numpy()
+    V = oracle.step_periodic(U, 0.1, 0.01, cfg)
+    np.testing.assert_array_equal(U, V)
+
+
+# ----------------------------------------------------------------------------- shock tubes vs exact
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_sod_converges_to_exact_solution(gamma):
+    cfg = oracle.config(gamma=gamma)
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = []
+    for n in (64, 128, 256):
+        U = workloads.riemann_1d(n, left, right, axis=0, ntrans=4, gamma=gamma).numpy()
+        U = run_edge(U, 1.0 / n, 0.2, cfg)
+        xc = (np.arange(n) + 0.5) / n
+        ex = riemann_exact.sample(left, right, gamma, (xc - 0.5) / 0.2)
+        rho = U[0, 1, 1, :]
+        errs.append(np.abs(rho - ex[0]).mean())
+        if n == 256:
+            # star-region plateau between contact and shock, away from both
+            ps, us = riemann_exact.star_state(left, right, gamma)
+            xi = (xc - 0.5) / 0.2
+            shock = ex[0] < 0.126  # first cell at right state
+            xs = xi[np.argmax(shock)]
+            plateau = (xi > us + 0.15) & (xi < xs - 0.15)
+            assert plateau.sum() > 5
+            prim = oracle.recover(U[:, 1:2, 1:2, :], cfg)[:, 0, 0, :]
+            np.testing.assert_allclose(prim[4][plateau], ps, rtol=1e-2)
+            np.testing.assert_allclose(prim[1][plateau], us, rtol=1e-2)
+            np.testing.assert_allclose(prim[0][plateau], ex[0][plateau], rtol=1e-2)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.006
+    assert errs[0] / errs[2] > 2.5  # at least ~first order at discontinuities
+
+
+# ----------------------------------------------------------------------------- conservation
+def test_periodic_conservation_to_roundoff():
+    cfg = oracle.config()
+    U0 = workloads.white_velocity_state(16, seed=1).numpy()
+    U, _ = oracle.run_periodic(U0, 1.0 / 16, 10, cfg)
+    for f in range(5):
+        scale = np.abs(U0[f]).sum()
+        assert abs(U[f].sum() - U0[f].sum()) <= 1e-13 * scale
+
+
+# ----------------------------------------------------------------------------- symmetry
+def test_one_dimensional_problem_is_bitwise_axis_symmetric():
+    cfg = oracle.config()
+    n = 24
+    res = []
+    for axis in range(3):
+        U = workloads.riemann_1d(n, (1.0, 0.2, 1.0), (0.3, -0.4, 0.2), axis=axis, ntrans=3).numpy()
+        U, _ = oracle.run_periodic(U, 1.0 / n, 6, cfg)
+        # bring the tube axis to x and the normal momentum to slot 1
+        order = {0: (0, 1, 2), 1: (0, 2, 1), 2: (2, 1, 0)}[axis]
+        A = np.transpose(U, (0,) + tuple(1 + o for o in order))
+        mom = [1, 2, 3]
+        mom[0], mom[axis] = mom[axis], mom[0]
+        res.append(A[[0] + mom + [4]])
+    np.testing.assert_array_equal(res[0], res[1])
+    np.testing.assert_array_equal(res[0], res[2])
+
+
+def test_three_dimensional_axis_permutation():
+    cfg = oracle.config()
+    U = workloads.white_velocity_state((10, 12, 14), seed=7).numpy()
+    dx = 1.0 / 14
+    dt = 0.5 * oracle.cfl_periodic(U, dx, cfg)
+    V = oracle.step_periodic(U, dx, dt, cfg)
+    # swap x <-> y: bitwise (sums are commutative pairwise)
+    Us = np.transpose(U, (0, 1, 3, 2))[[0, 2, 1, 3, 4]]
+    Vs = oracle.step_periodic(Us, dx, dt, cfg)
+    np.testing.assert_array_equal(np.transpose(Vs, (0, 1, 3, 2))[[0, 2, 1, 3, 4]], V)
+    # swap x <-> z: the x, y, z summation order changes, so agree to round-off
+    Uz = np.transpose(U, (0, 3, 2, 1))[[0, 3, 2, 1, 4]]
+    Vz = oracle.step_periodic(Uz, dx, dt, cfg)
+    back = np.transpose(Vz, (0, 3, 2, 1))[[0, 3, 2, 1, 4]]
+    for f in range(5):
+        assert np.abs(back[f] - V[f]).max() <= 1e-14 * np.abs(V[f]).max()
+
+
+# ----------------------------------------------------------------------------- convergence order
+@pytest.mark.parametrize("limiter,min_order", [("mc", 1.8), ("none", 1.8), ("minmod", 1.5)])
+def test_sound_wave_second_order(limiter, min_order):
+    cfg = oracle.config(limiter=limiter)
+    errs = []
+    ns = (16, 32, 64)
+    for n in ns:
+        # amplitude 1e-5 keeps the nonlinear steepening (~amp^2) far below the truncation error
+        U0, period = workloads.sound_wave((4, n, n), amp=1e-5, kvec=(1, 1, 0))
+        U0 = U0.numpy()
+        U = U0.copy()
+        dx = 1.0 / n
+        t = 0.0
+        while t < period - 1e-14:
+            dt = min(oracle.cfl_periodic(U, dx, cfg), period - t)
+            U = oracle.step_periodic(U, dx, dt, cfg)
+            t += dt
+        errs.append(np.abs(U[0] - U0[0]).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(ns) - 1)]
+    assert orders[-1] >= min_order, (errs, orders)
+
+
+# ----------------------------------------------------------------------------- Sedov-Taylor
+def test_sedov_taylor_radius():
+    cfg = oracle.config()
+    n = 32
+    U = workloads.sedov_blast(n, p_amb=1e-5).numpy()
+    dx = 1.0 / n
+    t_end = 0.05
+    t = 0.0
+    while t < t_end - 1e-15:
+        dt = min(oracle.cfl_periodic(U, dx, cfg), t_end - t)
+        U = oracle.step_periodic(U, dx, dt, cfg)
+        t += dt
+    c = (np.arange(n) + 0.5) / n
+    x0 = (n // 2 + 0.5) / n
+    r = np.sqrt((c[None, None, :] - x0) ** 2 + (c[None, :, None] - x0) ** 2 + (c[:, None, None] - x0) ** 2)
+    bins = np.floor(r / dx).astype(int)
+    prof = np.bincount(bins.ravel(), weights=U[0].ravel()) / np.bincount(bins.ravel())
+    r_peak = (np.argmax(prof[: n // 2]) + 0.5) * dx
+    R = sedov.shock_radius(t_end, E=1.0, rho0=1.0, gamma=cfg.gamma)
+    assert abs(r_peak - R) <= 2 * dx, (r_peak, R)
+    # total energy is conserved exactly up to round-off on the periodic box
+    assert U[4].sum() * dx ** 3 == pytest.approx(1.0 + 1e-5 / (cfg.gamma - 1), rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- CFL
+def test_cfl_bruteforce():
+    cfg = oracle.config()
+    U = workloads.white_velocity_state(4, seed=9).numpy()
+    dx = 0.25
+    rho = U[0]
+    u, v, w = U[1] / rho, U[2] / rho, U[3] / rho
+    p = (cfg.gamma - 1) * (U[4] - 0.5 * rho * (u * u + v * v + w * w))
+    c = np.sqrt(cfg.gamma * p / rho)
+    best = min(dx / (abs(u.flat[i]) + abs(v.flat[i]) + abs(w.flat[i]) + 3 * c.flat[i]) for i in range(u.size))
+    assert oracle.cfl_periodic(U, dx, cfg) == pytest.approx(cfg.cfl * best, rel=1e-14)
+
+
+# ----------------------------------------------------------------------------- derivatives
+@pytest.mark.parametrize("limiter", ["none", "minmod"])
+def test_tangent_matches_central_differences(limiter):
+    """Smooth 3D sound wave (phase offset: no exact ties at the extrema, so no slope sits on a
+    limiter kink); central differences with eps = 1e-6 relative agree to O(eps^2)."""
+    cfg = oracle.config(limiter=limiter)
+    U, _ = workloads.sound_wave((8, 8, 8), amp=1e-3, kvec=(1, 1, 1), phase=0.3)
+    U = U.numpy()
+    dx = 1.0 / 8
+    dt = 0.5 * oracle.cfl_periodic(U, dx, cfg)
+    rng = np.random.default_rng(4)
+    for _ in range(4):
+        v = rng.standard_normal(U.shape) * np.abs(U).max(axis=(1, 2, 3), keepdims=True)
+        _, Jv = oracle.step_periodic_tangent(U, v, dx, dt, cfg)
+        eps = 1e-6
+        fd = (oracle.step_periodic(U + eps * v, dx, dt, cfg) - oracle.step_periodic(U - eps * v, dx, dt, cfg)) / (2 * eps)
+        assert np.abs(fd - Jv).max() <= 1e-8 * np.abs(Jv).max()
+
+
+@pytest.mark.parametrize("limiter", ["minmod", "mc", "none"])
+def test_adjoint_dot_product(limiter):
+    cfg = oracle.config(limiter=limiter)
+    U = workloads.white_velocity_state((7, 9, 10), seed=11).numpy()
+    dx = 0.1
+    dt = 0.7 * oracle.cfl_periodic(U, dx, cfg)
+    rng = np.random.default_rng(12)
+    v = rng.standard_normal(U.shape)
+    w = rng.standard_normal(U.shape)
+    _, Jv = oracle.step_periodic_tangent(U, v, dx, dt, cfg)
+    JTw = oracle.step_periodic_adjoint(U, w, dx, dt, cfg, block=4)
+    a, b = np.vdot(w, Jv), np.vdot(JTw, v)
+    assert abs(a - b) <= 1e-12 * max(abs(a), np.abs(w * Jv).sum())
+
+
+def test_adjoint_block_split_is_exact():
+    cfg = oracle.config()
+    U = workloads.white_velocity_state((6, 6, 8), seed=13).numpy()
+    w = np.random.default_rng(14).standard_normal(U.shape)
+    a = oracle.step_periodic_adjoint(U, w, 0.1, 0.01, cfg, block=3)
+    b = oracle.step_periodic_adjoint(U, w, 0.1, 0.01, cfg, block=64)
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-13 * np.abs(b).max())
+
+
+def test_prim_to_cons_adjoint_is_transpose_of_jacobian():
+    cfg = oracle.config()
+    rng = np.random.default_rng(15)
+    q = np.stack([rng.uniform(0.5, 2, 6), *rng.normal(0, 1, (3, 6)), rng.uniform(0.5, 2, 6)])
+    lam = rng.standard_normal(q.shape)
+    g = oracle.prim_to_cons_adjoint(q, lam, cfg)
+    # Jacobian by central differences (the map is a polynomial of degree 3: FD is exact-ish)
+    h = 1e-6
+    for var in range(5):
+        dq = np.zeros_like(q)
+        dq[var] = h
+        J = (oracle.prim_to_cons(q + dq, cfg) - oracle.prim_to_cons(q - dq, cfg)) / (2 * h)
+        np.testing.assert_allclose((J * lam).sum(axis=0), g[var], rtol=1e-8, atol=1e-9)
+
+
+def test_op_counts_match_stage_formulas():
+    cfg = oracle.config()
+    U = workloads.white_velocity_state(8, seed=1).numpy()
+    c = oracle.count_ops(U, 1 / 8, 1e-3, cfg)
+    assert c["recover"] == 12  # |m|^2 (5), /2, /rho, E-kin, *(gamma-1), three m/rho
+    assert c["slopes"] == 30  # two differences per variable and direction (minmod selects)
+    assert c["update"] == 35  # five (3 differences + 2 sums + scale + subtract)
+    assert 90 <= c["face"] <= 130
