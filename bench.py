@@ -1,0 +1,559 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 hydro path: one MUSCL-Hancock/HLLC step of a 512^3 periodic grid.
+
+Workload (the single-uniform-grid configuration): 512^3 periodic box, Gaussian random k^-4
+velocities at rms Mach 5, lognormal density (sigma 1), cold gas P/rho = 1e-4 plus a Sedov cell
+(E = 1 in one cell); MinMod PLM + HLLC, CFL 0.8, gamma 5/3; each step's dt is the CFL dt of its
+input, fused into the previous step's epilogue (device-resident, no host sync per step).  The
+state (5.4 GB in FP64) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line: value = interior cells x steps / time (Mcell-updates/s, whole job), the
+roofline of the step kernel (algorithmic bytes or flops per launch / CUDA-event duration), the
+clocks seen during the timed region, an end-to-end number through the C ABI with host buffers,
+the CPU oracle as a reported baseline, and the other forms (FP32, mixed-precision batched AMR
+patches and oct groups, adjoint/forward ratio, 1024^3 graph-captured run) beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--precision fp64|fp32]
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas: the path
+does not shard); value sums all ranks' cells over the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+# Algorithmic arithmetic per interior cell of one step (binary +, -, *, / and sqrt, each 1),
+# counted stage by stage on a 64^3 sample of each workload (tests/test_bench_constants.py
+# recomputes them): recovery 12 + slopes + predictor 56 + 3 x face (states + HLLC) + update 35.
+ALG_FLOPS_PER_CELL = {"turb_minmod": 375.0, "turb_mc": 402.0, "mach10_mc": 387.0}
+BYTES_PER_CELL = {"fp64": 80.0, "fp32": 40.0, "mixed": 80.0}  # 5 fields read + 5 written
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# Arithmetic peaks from unit counts and the maximum SM clock (2070 MHz), 152 SMs:
+# FP32 128 FMA lanes/SM/clk -> 80.5 TFLOP/s; FP64 2 DFMA/SM/clk -> 1.26 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=512)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    p.add_argument("--forms", default="all", help="comma list of extra forms, 'all' or 'none'")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1412_0934_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") != kernel_source_hash():
+            return None, "stale"
+        return float(kv["dram_bytes_per_launch_full"]), path
+    except Exception:
+        return None, "absent"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.lines = []
+        self.proc = None
+        sel = []
+        try:
+            uuid = str(torch.cuda.get_device_properties(device).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        self.cmd = ["nvidia-smi"] + sel + ["--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------- workloads
+def turbulent(n, precision, device, seed=2, mach=5.0, sigma=1.0, p_over_rho=1e-4, sedov=True):
+    import workloads
+    U = workloads.turbulent_state(n, seed=seed, mach=mach, sigma_rho=sigma, p_over_rho=p_over_rho, sedov=sedov,
+                                  device=device)
+    if precision == "fp32":
+        U = U.float()
+    return U.contiguous()
+
+
+def time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream, per_launch=True):
+    """warmup + steps ping-pong steps with device-resident dt; returns (ms total, per-launch ms list,
+    final state tensor, launches in the timed region)."""
+    pa, pb = hy.patch(a, 0, dx), hy.patch(b, 0, dx)
+    hy.hydro_cfl_dt(ctx, pa, dts[0:1])
+    cur = 0
+    for i in range(warmup):
+        src, dst = (pa, pb) if cur == 0 else (pb, pa)
+        hy.hydro_step(ctx, src, dst, dts[i:i + 1], dts[i + 1:i + 2])
+        cur ^= 1
+    torch.cuda.synchronize()
+    launches0 = hy.hydro_launch_count(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(steps):
+        k = warmup + i
+        src, dst = (pa, pb) if cur == 0 else (pb, pa)
+        if per_launch:
+            ev[i][0].record(stream)
+        hy.hydro_step(ctx, src, dst, dts[k:k + 1], dts[k + 1:k + 2])
+        if per_launch:
+            ev[i][1].record(stream)
+        cur ^= 1
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = hy.hydro_launch_count(ctx) - launches0
+    per = [s.elapsed_time(e) for s, e in ev] if per_launch else []
+    return t0.elapsed_time(t1), per, (a if cur == 0 else b), launches
+
+
+def roofline(precision, cells, per_ms, flops_per_cell, hbm_gbs, peak_src, traffic):
+    """Roofline object of the step kernel: the binding roof is the one with the larger fraction."""
+    avg_s = statistics.mean(per_ms) / 1e3
+    bytes_launch = cells * BYTES_PER_CELL[precision]
+    flops_launch = cells * flops_per_cell
+    gbs = bytes_launch / avg_s / 1e9
+    tfl = flops_launch / avg_s / 1e12
+    fpeak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    hbm_frac = gbs / hbm_gbs
+    alu_frac = tfl / fpeak
+    common = {"hbm_frac": round(hbm_frac, 4), "alu_frac": round(alu_frac, 4),
+              "alu_peak_tflops": round(fpeak, 2), "alu_peak_source": "unit counts x 2070 MHz",
+              "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": peak_src, "avg_launch_ms": round(avg_s * 1e3, 4),
+              "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch}
+    if alu_frac >= hbm_frac:
+        r = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(fpeak, 2), "unit": "TFLOP/s",
+             "frac": round(alu_frac, 4)}
+    else:
+        r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s", "frac": round(hbm_frac, 4)}
+    r["traffic"] = traffic
+    r.update(common)
+    return r
+
+
+# ----------------------------------------------------------------------------- forms
+def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, sigma=1.0, p_over_rho=1e-4,
+                 sedov=True, seed=2, graph=False):
+    stream = torch.cuda.current_stream()
+    ctx = hy.hydro_init(precision=precision, limiter=limiter)
+    a = turbulent(n, precision, "cuda", seed=seed, mach=mach, sigma=sigma, p_over_rho=p_over_rho, sedov=sedov)
+    b = torch.empty_like(a)
+    dx = 1.0 / n
+    cells = n ** 3
+    if graph:
+        hist = torch.empty(steps + 1, dtype=torch.float64, device="cuda")
+        pa, pb = hy.patch(a, 0, dx), hy.patch(b, 0, dx)
+        hy.hydro_run(ctx, pa, pb, steps, hist, use_graph=True)  # capture + first replay (warm-up)
+        torch.cuda.synchronize()
+        a.copy_(turbulent(n, precision, "cuda", seed=seed, mach=mach, sigma=sigma, p_over_rho=p_over_rho,
+                          sedov=sedov))
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        hy.hydro_run(ctx, pa, pb, steps, hist, use_graph=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        rc, bits = hy.hydro_get_error(ctx)
+        out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
+               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "graph": True, "error_bits": bits}
+    else:
+        dts = torch.empty(warmup + steps + 1, dtype=torch.float64, device="cuda")
+        ms, per, _, launches = time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream)
+        rc, bits = hy.hydro_get_error(ctx)
+        hbm, src = peaks()
+        out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
+               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "error_bits": bits,
+               "roofline": roofline(precision, cells, per, ALG_FLOPS_PER_CELL[flops_key], hbm, src, None)}
+    del a, b
+    hy.hydro_finalize(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
+def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
+    """4096 AMR patches (edges {8..48}, cubes and 2:1 boxes, levels 0-5, own dx and CFL dt) in one
+    persistent launch per step, plus 262144 oct groups; mixed precision."""
+    import workloads
+    stream = torch.cuda.current_stream()
+    ctx = hy.hydro_init(precision="mixed")
+    parent = turbulent(256, "mixed", "cuda", seed=3, sedov=False)
+    descs = workloads.patch_set(npatch, seed=3)
+    origins = workloads.patch_origins(descs, parent.shape[1:], seed=3)
+    ins, outs, keep = [], [], []
+    interior = 0
+    ghosted = 0
+    for d, o in zip(descs, origins):
+        Ug = workloads.ghosted_from_periodic(parent, o, (d["nx"], d["ny"], d["nz"])).contiguous()
+        Vg = torch.empty_like(Ug)
+        keep += [Ug, Vg]
+        ins.append(hy.patch(Ug, 2, d["dx"], d["level"]))
+        outs.append(hy.patch(Vg, 2, d["dx"], d["level"]))
+        interior += d["nx"] * d["ny"] * d["nz"]
+        ghosted += Ug[0].numel()
+    n = len(ins)
+    dt = torch.empty(n, dtype=torch.float64, device="cuda")
+    dn = torch.empty(n, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(ctx, ins, dt)
+    for _ in range(warmup):
+        hy.hydro_step(ctx, ins, outs, dt, dn)
+    torch.cuda.synchronize()
+    l0 = hy.hydro_launch_count(ctx)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        hy.hydro_step(ctx, ins, outs, dt, dn)  # same input each step: the per-patch dt stays valid
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    launches = (hy.hydro_launch_count(ctx) - l0) / steps
+    # oct groups
+    og = workloads.oct_origins(ngroups, parent.shape[1:], seed=3)
+    g = workloads.gather_octs(parent, og).contiguous()
+    go = torch.empty((5, ngroups, 2, 2, 2), dtype=torch.float64, device="cuda")
+    dto = torch.tensor([0.5 * dt.min().item()], dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        hy.hydro_step_octs(ctx, g, go, 1.0 / 256, dto)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        hy.hydro_step_octs(ctx, g, go, 1.0 / 256, dto)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_o = t0.elapsed_time(t1) / steps
+    rc, bits = hy.hydro_get_error(ctx)
+    hbm, src = peaks()
+    bytes_p = (ghosted * 5 * 8 + interior * 5 * 8)
+    bytes_o = ngroups * (216 + 8) * 5 * 8
+    out = {"patches": n, "interior_cells": interior, "ghosted_cells": ghosted, "ms_per_step": ms,
+           "mcell_updates_per_s": interior / (ms / 1e3) / 1e6, "launches_per_step": launches,
+           "hbm_frac": bytes_p / (ms / 1e3) / 1e9 / hbm,
+           "octs": {"groups": ngroups, "ms_per_step": ms_o, "mcell_updates_per_s": ngroups * 8 / (ms_o / 1e3) / 1e6,
+                    "hbm_frac": bytes_o / (ms_o / 1e3) / 1e9 / hbm},
+           "error_bits": bits}
+    del keep, parent, g, go
+    hy.hydro_finalize(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
+def form_adjoint(hy, precision, n=64, nsteps=40):
+    """Adjoint/forward time ratio on the 64^3 periodic grid (one step each, and the 40-step
+    checkpointed gradient against the 40-step forward)."""
+    from paper_1412_0934_gb300 import autograd as hag
+    import workloads
+    stream = torch.cuda.current_stream()
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    ctx = hy.hydro_init(precision=precision)
+    U = workloads.turbulent_state(n, seed=4, mach=2.0, sedov=False, device="cuda").to(dtype).contiguous()
+    V = torch.empty_like(U)
+    L = torch.randn(U.shape, dtype=dtype, device="cuda")
+    M = torch.empty_like(U)
+    dx = 1.0 / n
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(ctx, hy.patch(U, 0, dx), dt)
+    pU, pV, pL, pM = (hy.patch(t, 0, dx) for t in (U, V, L, M))
+    reps = 50
+    for _ in range(5):
+        hy.hydro_step(ctx, pU, pV, dt)
+        hy.hydro_adjoint_step(ctx, pU, dt, pL, pM)
+    torch.cuda.synchronize()
+    t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t0.record(stream)
+    for _ in range(reps):
+        hy.hydro_step(ctx, pU, pV, dt)
+    t1.record(stream)
+    for _ in range(reps):
+        hy.hydro_adjoint_step(ctx, pU, dt, pL, pM)
+    t2.record(stream)
+    torch.cuda.synchronize()
+    f_ms, a_ms = t0.elapsed_time(t1) / reps, t1.elapsed_time(t2) / reps
+    # 40-step run: forward only vs forward + checkpointed gradient
+    W = workloads.turbulent_state(n, seed=4, mach=2.0, sedov=False, device="cuda")
+    rho0 = (W[0]).to(dtype).requires_grad_(True)
+    vel0 = (W[1:4] / W[0]).to(dtype).requires_grad_(True)
+    p0 = ((2.0 / 3.0) * (W[4] - 0.5 * (W[1] ** 2 + W[2] ** 2 + W[3] ** 2) / W[0])).to(dtype)
+    target = torch.ones_like(rho0)
+    sim = hag.Simulation(ctx, (n, n, n), dx, nsteps=nsteps, checkpoint_every=8)
+    with torch.no_grad():
+        sim.forward_only(rho0, vel0, p0)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    with torch.no_grad():
+        sim.forward_only(rho0, vel0, p0)
+    t1.record(stream)
+    loss = ((sim(rho0, vel0, p0) - target) ** 2).sum()
+    loss.backward()
+    t2.record(stream)
+    torch.cuda.synchronize()
+    fwd40, grad40 = t0.elapsed_time(t1), t1.elapsed_time(t2)
+    rc, bits = hy.hydro_get_error(ctx)
+    hy.hydro_finalize(ctx)
+    return {"n": n, "forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_over_forward": a_ms / f_ms,
+            "steps40_forward_ms": fwd40, "steps40_forward_plus_gradient_ms": grad40,
+            "gradient_over_forward_40": grad40 / fwd40, "error_bits": bits}
+
+
+def cpu_baseline(n, seconds, steps_cap=1000):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload (an n^3 box of
+    the same distributions), timed on this host's cores."""
+    import numpy as np
+    import oracle
+    import workloads
+    U = workloads.turbulent_state(n, seed=2, mach=5.0, sedov=True).numpy()
+    dx = 1.0 / n
+    cfg = oracle.config()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < steps_cap and (time.perf_counter() - t0) < seconds:
+        dt = oracle.cfl_periodic(U, dx, cfg)
+        U = oracle.step_periodic(U, dx, dt, cfg)
+        steps += 1
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n ** 3 * steps / el / 1e6, "unit": "Mcell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": "%d^3 box of the same workload (lognormal rho, k^-4 Mach-5 velocities, P/rho=1e-4, Sedov "
+                      "cell), %d FP64 steps incl. CFL dt, %.1f s" % (n, steps, el)}
+
+
+# ----------------------------------------------------------------------------- arms
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401  (the reference arm is the CPU oracle)
+    n = 96
+    for _ in range(args.warmup):
+        cpu_baseline(n, 0.0, steps_cap=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_baseline(n, 0.0, steps_cap=1)
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n ** 3 * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": "Mcell-updates/s per hydro step (1 GB300)", "value": value,
+            "unit": "Mcell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "FP64 CPU oracle; each step one %d^3 sample of the 512^3 periodic Mach-5 k^-4 "
+                                   "turbulence box (lognormal rho sigma 1, P/rho 1e-4, Sedov cell), MinMod, CFL 0.8"
+                                   % n},
+            "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d^3 per step (new state each step, CFL dt included)" % n},
+            "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1412_0934_gb300 as hy
+
+    precision = args.precision
+    n = args.n
+    dx = 1.0 / n
+    cells = n ** 3
+    stream = torch.cuda.current_stream()
+    ctx = hy.hydro_init(precision=precision, limiter="minmod")
+    a = turbulent(n, precision, "cuda")
+    b = torch.empty_like(a)
+    dts = torch.empty(args.warmup + args.steps + 1, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        ms, per, final, launches = time_steps(hy, ctx, a, b, dx, dts, args.steps, args.warmup, stream)
+    barrier()
+    rc, bits = hy.hydro_get_error(ctx)
+    if rc != hy.HYDRO_OK:
+        print("device error bits %#x" % bits, file=sys.stderr)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = t.item()
+    value = world * cells * args.steps / (t_max / 1e3) / 1e6
+    hbm, src = peaks()
+    traffic, tsrc = profile_traffic("step_uniform_512_%s.txt" % precision)
+    roof = roofline(precision, cells, per, ALG_FLOPS_PER_CELL["turb_minmod"], hbm, src, traffic)
+    roof["traffic_source"] = tsrc
+
+    # end to end through the C ABI with host buffers: H2D of the state, one step, D2H of the result
+    e2e_steps = 3
+    host_in = a.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    d1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        a.copy_(host_in, non_blocking=True)
+        hy.hydro_cfl_dt(ctx, hy.patch(a, 0, dx), d1)
+        hy.hydro_step(ctx, hy.patch(a, 0, dx), hy.patch(b, 0, dx), d1)
+        host_out.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    barrier()
+    esz = a.element_size()
+    e2e = {"value": world * cells / e2e_s / 1e6, "unit": "Mcell-updates/s",
+           "h2d_bytes_per_step": 5 * cells * esz, "d2h_bytes_per_step": 5 * cells * esz,
+           "note": "pinned host state -> device, CFL dt + step, result -> host, every step"}
+    del host_in, host_out, a, b, final
+    hy.hydro_finalize(ctx)
+    torch.cuda.empty_cache()
+
+    line = {"metric": "Mcell-updates/s per hydro step (1 GB300)", "value": round(value, 2),
+            "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64-state/f32"}[precision],
+            "data": "synthetic",
+            "config": {"workload": "%d^3 periodic uniform grid, Gaussian k^-4 velocities at rms Mach 5, lognormal rho "
+                                   "(sigma 1), P/rho = 1e-4, Sedov cell E=1; MinMod PLM + HLLC, CFL 0.8, gamma 5/3; "
+                                   "%s; dt from the fused CFL of each step" % (n, precision.upper()),
+                       "cells": cells, "state_bytes": 5 * cells * esz,
+                       "l2": "inputs larger than L2 (state %.1f GB vs 129 MB L2); no flush" % (5 * cells * esz / 1e9),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "device_error_bits": bits}
+
+    forms = [] if args.forms == "none" else (
+        ["fp32", "batched", "adjoint", "graph1024"] if args.forms == "all" else args.forms.split(","))
+    if rank == 0:
+        extra = {}
+        for f in forms:
+            try:
+                if f == "fp32":
+                    extra["fp32_512"] = form_uniform(hy, n, "fp32", "minmod", args.steps, args.warmup, "turb_minmod")
+                elif f == "fp64_256":
+                    extra["fp64_256"] = form_uniform(hy, 256, "fp64", "minmod", args.steps, args.warmup,
+                                                     "turb_minmod")
+                elif f == "batched":
+                    extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2)
+                elif f == "adjoint":
+                    extra["adjoint_fp64"] = form_adjoint(hy, "fp64")
+                    extra["adjoint_fp32"] = form_adjoint(hy, "fp32")
+                elif f == "graph1024":
+                    extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
+                                                               sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,
+                                                               graph=True)
+            except Exception as e:  # a failing extra form is reported, not fatal
+                extra[f] = {"error": repr(e)[:300]}
+        line["forms"] = extra
+        line["cpu_baseline"] = cpu_baseline(128, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) hydro library: one second-order unsplit
+ * MUSCL-Hancock step (PLM primitive reconstruction, Hancock half-step predictor, HLLC fluxes,
+ * conservative update) of the 3D ideal-gas Euler equations on AMR grid patches, the per-patch
+ * CFL time step, Ramses-style oct groups, and the adjoint of the step.
+ *
+ * What the calls compute follows the paper's description of the hydro path: the baryonic
+ * component is an ideal fluid governed by the Euler equations, solved with PLM among other
+ * methods (Sec. 2); "all fluxes necessary to update the patch's cells are computed on the GPU"
+ * and the adaptive time step (Sec. 4, Enzo); hydro solved on chunks of patches that carry their
+ * boundary cells (Sec. 3, Ramses GPU procedure); the N_v x 6^3 gathered cell buffer (Sec. 3).
+ * The paper prints no equations; the scheme is the textbook one, with these readings: primitive
+ * reconstruction; MinMod / MC / unlimited slopes; unsplit primitive Hancock predictor summed over
+ * x, y, z; Davis wave speeds and Batten et al. star states in HLLC; dt = cfl * dx /
+ * max(|u|+|v|+|w|+3c); density and pressure floors after recovery and on face states.
+ *
+ * Conventions
+ *   - Every field pointer is DEVICE memory owned by the caller; the library never frees it.
+ *     Fields are structure-of-arrays: five separate arrays (rho, m_x, m_y, m_z, E), x fastest.
+ *     Element type: double for HYDRO_FP64 and HYDRO_MIXED, float for HYDRO_FP32.
+ *   - The library owns only what a hydro_ctx holds: the device error word, uploaded patch
+ *     descriptors, the tile work-list and its counter, captured CUDA graphs, autotune results.
+ *   - Every call is asynchronous on the context's stream, except hydro_get_error (and
+ *     hydro_autotune), which synchronise it.  After a first call with a given patch set, calls
+ *     with the same set allocate nothing and can be captured in a CUDA graph.
+ *   - Argument errors are detected on the host and return HYDRO_ERR_ARG before anything is
+ *     launched.  Physical errors found on the device set bits of the error word
+ *     (HYDRO_EBIT_*), read back by hydro_get_error.  CUDA errors return HYDRO_ERR_CUDA.
+ *   - Ghost cells: a patch with ng == 2 carries two ghost layers filled by the caller (the paper's
+ *     chunks carry their boundary cells, Sec. 3).  ng == 0 means a periodic box: the library wraps
+ *     indices itself.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYDRO_OK = 0,
+  HYDRO_ERR_ARG = -1,        /* bad argument; nothing launched */
+  HYDRO_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  HYDRO_ERR_UNPHYSICAL = -3, /* hydro_get_error: the error word is non-zero */
+  HYDRO_ERR_TIMEOUT = -4,    /* a bounded device wait ran out */
+  HYDRO_ERR_NOMEM = -5,      /* device allocation of library-owned scratch failed */
+  HYDRO_ERR_STATE = -6       /* call not valid in the context's current state */
+} hydro_status;
+
+typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2 } hydro_precision;
+/* HYDRO_FP64 : double state, double arithmetic throughout.
+ * HYDRO_FP32 : float state; float reconstruction, predictor, HLLC and update; the pressure
+ *              recovery p = (gamma-1)(E - |m|^2/(2 rho)) is evaluated with error-free float
+ *              transformations to double-float accuracy (at least as accurate as evaluating it in
+ *              double and rounding to float).
+ * HYDRO_MIXED: double state; the same recovery evaluated in double; float reconstruction,
+ *              predictor, HLLC and flux divergence; the update U + dU accumulated in double. */
+
+typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2 } hydro_limiter;
+
+/* Bits of the device error word. */
+#define HYDRO_EBIT_NONFINITE 0x01u /* a recovered density or pressure was not finite */
+#define HYDRO_EBIT_RHO_FLOOR 0x02u /* recovered density below rho_floor (floored) */
+#define HYDRO_EBIT_P_FLOOR 0x04u   /* E below the kinetic energy: negative pressure (floored) */
+#define HYDRO_EBIT_BAD_DT 0x08u    /* a step was given dt <= 0 or non-finite (no update done) */
+#define HYDRO_EBIT_BAD_TILE 0x10u  /* a work-list record pointed outside its patch */
+#define HYDRO_EBIT_TIMEOUT 0x20u   /* a bounded device wait gave up */
+
+typedef struct {
+  double gamma;      /* ratio of specific heats, > 1 */
+  double cfl;        /* Courant number C of the dt formula, in (0, 1] */
+  double rho_floor;  /* density floor, >= 0 */
+  double p_floor;    /* pressure floor, >= 0 */
+  int limiter;       /* hydro_limiter */
+  int precision;     /* hydro_precision */
+  void* cuda_stream; /* cudaStream_t all calls are enqueued on; NULL = legacy default stream */
+} hydro_config;
+
+typedef struct {
+  void* U[5];        /* device pointers to rho, m_x, m_y, m_z, E (see the element type above) */
+  int nx, ny, nz;    /* interior cells, each >= 1 */
+  int ng;            /* ghost layers: 2 (caller-filled) or 0 (periodic box, wrapped by the library) */
+  long long sy, sz;  /* element strides of y and z in the stored (ghosted) array; x stride is 1.
+                        Require sy >= nx + 2 ng and sz >= sy * (ny + 2 ng). */
+  double dx;         /* cell size, > 0 */
+  int level;         /* refinement level (informational; dx carries the geometry) */
+} hydro_patch;
+
+typedef struct hydro_ctx hydro_ctx;
+
+/* Create a context on the current CUDA device.  Validates cfg (gamma > 1, 0 < cfl <= 1,
+ * floors >= 0, enums in range) and allocates the device error word.  *ctx is set to NULL on
+ * failure.  Returns HYDRO_OK, HYDRO_ERR_ARG, HYDRO_ERR_NOMEM or HYDRO_ERR_CUDA. */
+int hydro_init(hydro_ctx** ctx, const hydro_config* cfg);
+
+/* Synchronise the context's stream and free everything the context owns. NULL is a no-op. */
+int hydro_finalize(hydro_ctx* ctx);
+
+/* Per-patch CFL time step (adaptive time step, Sec. 2 and Sec. 4):
+ *   dt_dev[p] = cfl * dx_p / max over the interior cells of patch p of (|u|+|v|+|w| + 3 c),
+ *   c = sqrt(gamma p / rho), from the recovered (floored) primitive state.
+ * p: host array of npatch descriptors (npatch >= 1).  dt_dev: device array of npatch doubles,
+ * overwritten.  In HYDRO_FP32 and HYDRO_MIXED the per-cell speeds are float; the dt formula is
+ * evaluated in double.  The result is bit-identical to the dt_next output of hydro_step on the
+ * same state. */
+int hydro_cfl_dt(hydro_ctx* ctx, const hydro_patch* p, int npatch, double* dt_dev);
+
+/* One MUSCL-Hancock/HLLC step of every patch (recovery, PLM slopes, Hancock predictor, HLLC
+ * fluxes on every face, conservative update; Sec. 2 and Sec. 4):
+ *   out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] and cell size in[p].dx.
+ * in, out: host arrays of npatch descriptors with equal nx, ny, nz and dx per patch; out[p] may
+ * have ng 0 or 2 (only its interior is written) and must not overlap in[p] (use two buffers).
+ * dt_dev: device array of npatch doubles.  dt_next_dev: NULL, or a device array of npatch
+ * doubles that receives the CFL dt of U^{n+1} (same formula as hydro_cfl_dt), fused into the
+ * step.  A single periodic box (npatch == 1, ng == 0) runs the uniform-grid kernel; any other
+ * set runs one persistent launch over a device-built tile work-list.  The descriptors are
+ * uploaded and the work-list rebuilt only when the patch set differs from the previous call's. */
+int hydro_step(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
+               double* dt_next_dev);
+
+/* One step of Ramses-style oct groups (Sec. 3: the N_v x 6 x 6 x 6 gathered buffer): each
+ * group is the 2x2x2 oct plus two ghost layers, gathered by the caller.
+ *   gathered[f]: device array [ngroups][6][6][6] (z, y, x) of field f;
+ *   out[f]:      device array [ngroups][2][2][2] receiving U^{n+1} of the oct's 8 cells.
+ * All groups share dx and the time step dt_dev[0].  ngroups >= 1. */
+int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5], long long ngroups, double dx,
+                    const double* dt_dev);
+
+/* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
+ * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64 or
+ * HYDRO_FP32.  U_n: the state the forward step started from; dt_dev[p] its time step; lam_np1,
+ * lam_n: adjoint fields with the same layout and element type as U_n (must not overlap).  The
+ * derivative of each limiter / HLLC branch / floor is that of the branch the forward values
+ * select.  Deterministic: every face's contribution is gathered, never atomically scattered. */
+int hydro_adjoint_step(hydro_ctx* ctx, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
+                       const hydro_patch* lam_n, int npatch);
+
+/* Primitive -> conservative map of the initial state and its adjoint (used to turn gradients with
+ * respect to U^0 into gradients with respect to the initial density and velocity):
+ *   U = (rho, rho u, rho v, rho w, p/(gamma-1) + rho |u|^2 / 2).
+ * W holds (rho, u, v, w, p) in the layout of a patch; lamW receives (dU/dW)^T lamU. */
+int hydro_prim_to_cons(hydro_ctx* ctx, const hydro_patch* W, const hydro_patch* U, int npatch);
+int hydro_prim_to_cons_adjoint(hydro_ctx* ctx, const hydro_patch* W, const hydro_patch* lamU,
+                               const hydro_patch* lamW, int npatch);
+
+/* Multi-step run of one periodic box with the time step kept on the device (no host
+ * synchronisation per step): dt_hist_dev[0] = CFL dt of the state in a; step n advances by
+ * dt_hist_dev[n] and writes dt_hist_dev[n+1] = CFL dt of its result; states ping-pong between
+ * a (even n) and b (odd n), so the result is in a if nsteps is even, else in b.
+ * dt_hist_dev: device array of nsteps + 1 doubles.  With use_graph != 0 the nsteps launches are
+ * captured once into a CUDA graph (cached in the context for the same a, b, nsteps, dt_hist_dev)
+ * and replayed. */
+int hydro_run(hydro_ctx* ctx, const hydro_patch* a, const hydro_patch* b, int nsteps, double* dt_hist_dev,
+              int use_graph);
+
+/* Autotuner: times the candidate tile shapes and z-chunk depths of hydro_step on this patch set
+ * (in, out, dt_dev as for hydro_step; contents of out are overwritten) and keeps the fastest in
+ * the context for later hydro_step calls.  If cache_path is not NULL the choice is read from /
+ * appended to that text file, keyed by GPU name, SM count, precision and patch-set signature.
+ * Synchronises the stream. */
+int hydro_autotune(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
+                   const char* cache_path);
+
+/* Current tile configuration: *tile_id (index into the compiled tile shapes) and *zchunk. */
+int hydro_get_tuning(hydro_ctx* ctx, int* tile_id, int* zchunk);
+int hydro_set_tuning(hydro_ctx* ctx, int tile_id, int zchunk);
+
+/* Synchronise the context's stream and return the device error word in *error_bits (may be
+ * NULL).  Returns HYDRO_ERR_UNPHYSICAL if any bit is set, HYDRO_OK otherwise, HYDRO_ERR_CUDA on
+ * a CUDA error.  hydro_clear_error zeroes the word (asynchronously). */
+int hydro_get_error(hydro_ctx* ctx, unsigned* error_bits);
+int hydro_clear_error(hydro_ctx* ctx);
+
+/* Number of kernels this context has launched so far (graph replays count their kernels). */
+int hydro_launch_count(hydro_ctx* ctx, long long* count);
+
+/* Static description of a status code. */
+const char* hydro_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

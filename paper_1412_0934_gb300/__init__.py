@@ -1,0 +1,289 @@
+"""Python binding of libhydro.so, the sm_103a CUDA library declared in include/hydro.h.
+
+Argument marshalling only: every step of the hydro path runs in the library's kernels.  The
+functions carry the C ABI's names (hydro_init, hydro_step, hydro_cfl_dt, hydro_step_octs,
+hydro_adjoint_step, hydro_run, ...) and take torch CUDA tensors, which own all field memory.
+There is no CPU fallback: if the library is not built, or no GPU is present, calls raise.
+
+A patch is built from a tensor of shape (5, nz + 2 ng, ny + 2 ng, nx + 2 ng) (fields rho, m_x,
+m_y, m_z, E; x fastest) with ``patch(U, ng, dx)``; float64 for FP64/MIXED, float32 for FP32.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhydro.so")
+
+HYDRO_OK = 0
+HYDRO_ERR_ARG = -1
+HYDRO_ERR_CUDA = -2
+HYDRO_ERR_UNPHYSICAL = -3
+HYDRO_ERR_TIMEOUT = -4
+HYDRO_ERR_NOMEM = -5
+HYDRO_ERR_STATE = -6
+
+HYDRO_FP64, HYDRO_FP32, HYDRO_MIXED = 0, 1, 2
+HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT = 0, 1, 2
+PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED}
+LIMITERS = {"minmod": HYDRO_MINMOD, "mc": HYDRO_MC, "none": HYDRO_NOLIMIT}
+
+EBIT_NONFINITE = 0x01
+EBIT_RHO_FLOOR = 0x02
+EBIT_P_FLOOR = 0x04
+EBIT_BAD_DT = 0x08
+EBIT_BAD_TILE = 0x10
+EBIT_TIMEOUT = 0x20
+
+# C symbols that include/hydro.h declares (checked by the tests).
+EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_octs", "hydro_adjoint_step",
+           "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
+           "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string")
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, status_string(status), status))
+
+
+class hydro_config(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("rho_floor", ctypes.c_double),
+                ("p_floor", ctypes.c_double), ("limiter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class hydro_patch(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p * 5), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("ng", ctypes.c_int), ("sy", ctypes.c_longlong), ("sz", ctypes.c_longlong), ("dx", ctypes.c_double),
+                ("level", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhydro.so is not built; run paper_1412_0934_gb300.build.build() "
+                               "(or __graft_entry__.build()) first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        PP = ctypes.POINTER(hydro_patch)
+        L.hydro_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(hydro_config)]
+        L.hydro_finalize.argtypes = [vp]
+        L.hydro_cfl_dt.argtypes = [vp, PP, i, vp]
+        L.hydro_step.argtypes = [vp, PP, PP, i, vp, vp]
+        L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
+        L.hydro_adjoint_step.argtypes = [vp, PP, vp, PP, PP, i]
+        L.hydro_prim_to_cons.argtypes = [vp, PP, PP, i]
+        L.hydro_prim_to_cons_adjoint.argtypes = [vp, PP, PP, PP, i]
+        L.hydro_run.argtypes = [vp, PP, PP, i, vp, i]
+        L.hydro_autotune.argtypes = [vp, PP, PP, i, vp, ctypes.c_char_p]
+        L.hydro_get_tuning.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.hydro_set_tuning.argtypes = [vp, i, i]
+        L.hydro_get_error.argtypes = [vp, ctypes.POINTER(ctypes.c_uint)]
+        L.hydro_clear_error.argtypes = [vp]
+        L.hydro_launch_count.argtypes = [vp, ctypes.POINTER(ll)]
+        L.hydro_status_string.argtypes = [i]
+        L.hydro_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(status):
+    return lib().hydro_status_string(int(status)).decode()
+
+
+def hydro_status_string(status):
+    return status_string(status)
+
+
+def _check(rc, what):
+    if rc != HYDRO_OK:
+        raise HydroError(rc, what)
+
+
+class Patch:
+    """A hydro_patch plus the tensors it points into (kept alive while the patch is)."""
+
+    def __init__(self, fields, ng, dx, level=0):
+        if isinstance(fields, torch.Tensor):
+            if fields.dim() != 4 or fields.shape[0] != 5:
+                raise ValueError("expected a (5, nz, ny, nx) tensor")
+            fs = [fields[v] for v in range(5)]
+        else:
+            fs = list(fields)
+            if len(fs) != 5:
+                raise ValueError("expected five field tensors")
+        for f in fs:
+            if not f.is_cuda:
+                raise ValueError("patch fields must be CUDA tensors")
+            if f.dim() != 3 or f.stride(2) != 1:
+                raise ValueError("each field must be 3D with unit x stride")
+            if f.shape != fs[0].shape or f.stride() != fs[0].stride() or f.dtype != fs[0].dtype:
+                raise ValueError("fields must share shape, strides and dtype")
+        Z, Y, X = fs[0].shape
+        self.tensors = fs
+        self.dtype = fs[0].dtype
+        self.c = hydro_patch()
+        for v in range(5):
+            self.c.U[v] = fs[v].data_ptr()
+        self.c.nx, self.c.ny, self.c.nz = X - 2 * ng, Y - 2 * ng, Z - 2 * ng
+        self.c.ng = ng
+        self.c.sy = fs[0].stride(1)
+        self.c.sz = fs[0].stride(0)
+        self.c.dx = float(dx)
+        self.c.level = int(level)
+
+
+def patch(fields, ng, dx, level=0):
+    return Patch(fields, ng, dx, level)
+
+
+def _parray(patches):
+    patches = [patches] if isinstance(patches, Patch) else list(patches)
+    arr = (hydro_patch * len(patches))(*[p.c for p in patches])
+    return arr, len(patches)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+class Context:
+    """An open hydro_ctx (create with hydro_init, release with hydro_finalize)."""
+
+    def __init__(self, handle, cfg):
+        self.handle = handle
+        self.cfg = cfg
+
+    @property
+    def precision(self):
+        return self.cfg.precision
+
+    @property
+    def dtype(self):
+        return torch.float32 if self.cfg.precision == HYDRO_FP32 else torch.float64
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().hydro_finalize(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def hydro_init(gamma=5.0 / 3.0, cfl=0.8, rho_floor=1e-10, p_floor=1e-14, limiter="minmod", precision="fp64",
+               stream=None):
+    """Open a context on the current device; all calls go to `stream` (default: torch's current stream)."""
+    cfg = hydro_config()
+    cfg.gamma, cfg.cfl, cfg.rho_floor, cfg.p_floor = gamma, cfl, rho_floor, p_floor
+    cfg.limiter = LIMITERS[limiter] if isinstance(limiter, str) else int(limiter)
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    cfg.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    h = ctypes.c_void_p()
+    _check(lib().hydro_init(ctypes.byref(h), ctypes.byref(cfg)), "hydro_init")
+    return Context(h, cfg)
+
+
+def hydro_finalize(ctx):
+    if ctx.handle:
+        _check(lib().hydro_finalize(ctx.handle), "hydro_finalize")
+        ctx.handle = None
+
+
+def hydro_cfl_dt(ctx, patches, dt_out):
+    arr, n = _parray(patches)
+    _check(lib().hydro_cfl_dt(ctx.handle, arr, n, _ptr(dt_out)), "hydro_cfl_dt")
+
+
+def hydro_step(ctx, inp, out, dt, dt_next=None):
+    a, n = _parray(inp)
+    b, m = _parray(out)
+    if n != m:
+        raise ValueError("in and out patch counts differ")
+    _check(lib().hydro_step(ctx.handle, a, b, n, _ptr(dt), _ptr(dt_next)), "hydro_step")
+
+
+def hydro_step_octs(ctx, gathered, out, dx, dt):
+    """gathered: (5, G, 6, 6, 6) tensor (or 5 tensors); out: (5, G, 2, 2, 2)."""
+    g = (ctypes.c_void_p * 5)(*[_ptr(gathered[v]) for v in range(5)])
+    o = (ctypes.c_void_p * 5)(*[_ptr(out[v]) for v in range(5)])
+    for v in range(5):
+        if not gathered[v].is_contiguous() or not out[v].is_contiguous():
+            raise ValueError("oct arrays must be contiguous per field")
+    G = gathered[0].shape[0]
+    _check(lib().hydro_step_octs(ctx.handle, g, o, G, float(dx), _ptr(dt)), "hydro_step_octs")
+
+
+def hydro_adjoint_step(ctx, U_n, dt, lam_np1, lam_n):
+    a, n = _parray(U_n)
+    b, _ = _parray(lam_np1)
+    c, _ = _parray(lam_n)
+    _check(lib().hydro_adjoint_step(ctx.handle, a, _ptr(dt), b, c, n), "hydro_adjoint_step")
+
+
+def hydro_prim_to_cons(ctx, W, U):
+    a, n = _parray(W)
+    b, _ = _parray(U)
+    _check(lib().hydro_prim_to_cons(ctx.handle, a, b, n), "hydro_prim_to_cons")
+
+
+def hydro_prim_to_cons_adjoint(ctx, W, lamU, lamW):
+    a, n = _parray(W)
+    b, _ = _parray(lamU)
+    c, _ = _parray(lamW)
+    _check(lib().hydro_prim_to_cons_adjoint(ctx.handle, a, b, c, n), "hydro_prim_to_cons_adjoint")
+
+
+def hydro_run(ctx, a, b, nsteps, dt_hist, use_graph=True):
+    pa, _ = _parray(a)
+    pb, _ = _parray(b)
+    _check(lib().hydro_run(ctx.handle, pa, pb, int(nsteps), _ptr(dt_hist), 1 if use_graph else 0), "hydro_run")
+
+
+def hydro_autotune(ctx, inp, out, dt, cache_path=None):
+    a, n = _parray(inp)
+    b, _ = _parray(out)
+    cp = cache_path.encode() if cache_path else None
+    _check(lib().hydro_autotune(ctx.handle, a, b, n, _ptr(dt), cp), "hydro_autotune")
+
+
+def hydro_get_tuning(ctx):
+    t, z = ctypes.c_int(), ctypes.c_int()
+    _check(lib().hydro_get_tuning(ctx.handle, ctypes.byref(t), ctypes.byref(z)), "hydro_get_tuning")
+    return t.value, z.value
+
+
+def hydro_set_tuning(ctx, tile_id, zchunk):
+    _check(lib().hydro_set_tuning(ctx.handle, int(tile_id), int(zchunk)), "hydro_set_tuning")
+
+
+def hydro_get_error(ctx):
+    """(status, bits): synchronises the context's stream."""
+    bits = ctypes.c_uint()
+    rc = lib().hydro_get_error(ctx.handle, ctypes.byref(bits))
+    if rc not in (HYDRO_OK, HYDRO_ERR_UNPHYSICAL):
+        raise HydroError(rc, "hydro_get_error")
+    return rc, bits.value
+
+
+def hydro_clear_error(ctx):
+    _check(lib().hydro_clear_error(ctx.handle), "hydro_clear_error")
+
+
+def hydro_launch_count(ctx):
+    n = ctypes.c_longlong()
+    _check(lib().hydro_launch_count(ctx.handle, ctypes.byref(n)), "hydro_launch_count")
+    return n.value

@@ -1,0 +1,561 @@
+// C ABI of the hydro library (include/hydro.h): argument validation, the context and its
+// library-owned scratch, patch-set caching and work-list rebuilds, launch selection, the
+// CUDA-graph multi-step runner and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hydro.h"
+#include "hydro_device.cuh"
+#include "internal.h"
+
+using hydro::HostPatchIO;
+using hydro::HostTileRec;
+
+struct hydro_ctx {
+  hydro_config cfg;
+  hydro::Params prm;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;  // private stream used to capture graphs
+  const hydro::KernelOps* ops = nullptr;
+  int device = 0, sm_count = 0;
+  unsigned* d_err = nullptr;
+  // batched step: cached patch set, device descriptors and work-list
+  std::vector<hydro_patch> key_in, key_out;
+  HostPatchIO* h_patches = nullptr;  // pinned staging
+  HostPatchIO* d_patches = nullptr;
+  size_t patches_cap = 0;
+  int* d_counts = nullptr;
+  size_t counts_cap = 0;
+  HostTileRec* d_tiles = nullptr;
+  size_t tiles_cap = 0;
+  int ntiles = 0;
+  int* d_counter = nullptr;
+  int wl_tile = -1, wl_zchunk = -1;
+  // CFL of many patches: cached descriptors
+  std::vector<hydro_patch> cfl_key;
+  HostPatchIO* h_cfl = nullptr;
+  HostPatchIO* d_cfl = nullptr;
+  size_t cfl_cap = 0;
+  // tuning
+  int tile_id = 0, zchunk = 32;
+  // graph cache of hydro_run
+  cudaGraphExec_t graph = nullptr;
+  const void* g_a = nullptr;
+  const void* g_b = nullptr;
+  int g_n = -1;
+  double* g_dt = nullptr;
+  int g_tile = -1, g_zc = -1;
+  // adjoint scratch
+  void* d_adj = nullptr;
+  size_t adj_cap = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_CUDA; }
+
+int elem_size(const hydro_ctx* c) { return c->cfg.precision == HYDRO_FP32 ? 4 : 8; }
+
+bool valid_patch(const hydro_ctx* c, const hydro_patch& p) {
+  if (p.nx < 1 || p.ny < 1 || p.nz < 1) return false;
+  if (p.ng != 0 && p.ng != 2) return false;
+  if (!finite_pos(p.dx)) return false;
+  const long long gx = p.nx + 2LL * p.ng, gy = p.ny + 2LL * p.ng;
+  if (p.sy < gx || p.sz < p.sy * gy) return false;
+  const int es = elem_size(c);
+  for (int v = 0; v < 5; ++v) {
+    if (!p.U[v]) return false;
+    if (reinterpret_cast<uintptr_t>(p.U[v]) % es) return false;
+  }
+  return true;
+}
+
+// Byte extent of a field of patch p.
+size_t field_bytes(const hydro_ctx* c, const hydro_patch& p) {
+  return (size_t)(p.nz + 2 * p.ng) * (size_t)p.sz * elem_size(c);
+}
+
+bool overlaps(const hydro_ctx* c, const hydro_patch& a, const hydro_patch& b) {
+  const size_t na = field_bytes(c, a), nb = field_bytes(c, b);
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      const char* x = static_cast<const char*>(a.U[i]);
+      const char* y = static_cast<const char*>(b.U[j]);
+      if (x < y + nb && y < x + na) return true;
+    }
+  return false;
+}
+
+bool same_shape(const hydro_patch& a, const hydro_patch& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.dx == b.dx;
+}
+
+HostPatchIO make_io(const hydro_patch& in, const hydro_patch& out) {
+  HostPatchIO h;
+  for (int v = 0; v < 5; ++v) {
+    h.in[v] = in.U[v];
+    h.out[v] = out.U[v];
+  }
+  h.nx = in.nx; h.ny = in.ny; h.nz = in.nz;
+  h.gin = in.ng; h.gout = out.ng;
+  h.isy = in.sy; h.isz = in.sz; h.osy = out.sy; h.osz = out.sz;
+  h.dx = in.dx;
+  return h;
+}
+
+bool same_patch(const hydro_patch& a, const hydro_patch& b) { return std::memcmp(&a, &b, sizeof(hydro_patch)) == 0; }
+
+bool same_set(const std::vector<hydro_patch>& key, const hydro_patch* p, int n) {
+  if ((int)key.size() != n) return false;
+  for (int i = 0; i < n; ++i)
+    if (!same_patch(key[i], p[i])) return false;
+  return true;
+}
+
+template <class T>
+int ensure_device(T** d, size_t* cap, size_t n) {
+  if (*cap >= n) return HYDRO_OK;
+  if (*d) cudaFree(*d);
+  *d = nullptr;
+  *cap = 0;
+  if (cudaMalloc(reinterpret_cast<void**>(d), n * sizeof(T)) != cudaSuccess) return HYDRO_ERR_NOMEM;
+  *cap = n;
+  return HYDRO_OK;
+}
+
+// Upload the descriptors of (in, out) and build the tile work-list for the current tuning,
+// unless the cached set and tuning are unchanged.
+int prepare_batch(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int n) {
+  const bool set_same = same_set(c->key_in, in, n) && same_set(c->key_out, out, n);
+  const int tx = hydro::kTileX[c->tile_id], ty = hydro::kTileY[c->tile_id];
+  if (set_same && c->wl_tile == c->tile_id && c->wl_zchunk == c->zchunk) return HYDRO_OK;
+  if (!set_same) {
+    size_t old = c->patches_cap;
+    int rc = ensure_device(&c->d_patches, &c->patches_cap, (size_t)n);
+    if (rc) return rc;
+    if (c->patches_cap != old || !c->h_patches) {
+      if (c->h_patches) cudaFreeHost(c->h_patches);
+      if (cudaMallocHost(&c->h_patches, c->patches_cap * sizeof(HostPatchIO)) != cudaSuccess) return HYDRO_ERR_NOMEM;
+    }
+    // the staging buffer may still be read by an earlier copy on the stream
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    for (int i = 0; i < n; ++i) c->h_patches[i] = make_io(in[i], out[i]);
+    if (cudaMemcpyAsync(c->d_patches, c->h_patches, n * sizeof(HostPatchIO), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return HYDRO_ERR_CUDA;
+    c->key_in.assign(in, in + n);
+    c->key_out.assign(out, out + n);
+  }
+  // tile count on the host sizes the buffer; the device builds the list itself
+  size_t total = 0;
+  for (int i = 0; i < n; ++i)
+    total += (size_t)((in[i].nx + tx - 1) / tx) * ((in[i].ny + ty - 1) / ty) * ((in[i].nz + c->zchunk - 1) / c->zchunk);
+  if (total > 0x7fffffff) return HYDRO_ERR_ARG;
+  int rc = ensure_device(&c->d_counts, &c->counts_cap, (size_t)n + 1);
+  if (rc) return rc;
+  rc = ensure_device(&c->d_tiles, &c->tiles_cap, total);
+  if (rc) return rc;
+  if (hydro::build_worklist(c->d_patches, n, tx, ty, c->zchunk, c->d_counts, c->d_tiles, c->stream) != cudaSuccess)
+    return HYDRO_ERR_CUDA;
+  c->launches += 3;
+  c->ntiles = (int)total;
+  c->wl_tile = c->tile_id;
+  c->wl_zchunk = c->zchunk;
+  return HYDRO_OK;
+}
+
+int reset_slots(hydro_ctx* c, double* p, int n, cudaStream_t s) {
+  // 0xFF.. is above the bits of every positive double: the neutral element of the min.
+  return cuda_status(cudaMemsetAsync(p, 0xFF, (size_t)n * sizeof(double), s));
+}
+
+int step_one_uniform(hydro_ctx* c, const hydro_patch& in, const hydro_patch& out, const double* dt, double* dt_next,
+                     cudaStream_t s) {
+  if (dt_next) {
+    int rc = reset_slots(c, dt_next, 1, s);
+    if (rc) return rc;
+  }
+  int zc = std::min(c->zchunk, in.nz);
+  cudaError_t e = c->ops->step_uniform(c->tile_id, make_io(in, out), c->prm, dt, dt_next, zc, c->d_err, s);
+  c->launches += 1;
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hydro_status_string(int status) {
+  switch (status) {
+    case HYDRO_OK: return "ok";
+    case HYDRO_ERR_ARG: return "invalid argument";
+    case HYDRO_ERR_CUDA: return "CUDA error";
+    case HYDRO_ERR_UNPHYSICAL: return "unphysical state flagged on the device";
+    case HYDRO_ERR_TIMEOUT: return "bounded device wait timed out";
+    case HYDRO_ERR_NOMEM: return "device allocation failed";
+    case HYDRO_ERR_STATE: return "invalid context state";
+  }
+  return "unknown status";
+}
+
+int hydro_init(hydro_ctx** ctx, const hydro_config* cfg) {
+  if (!ctx) return HYDRO_ERR_ARG;
+  *ctx = nullptr;
+  if (!cfg) return HYDRO_ERR_ARG;
+  if (!(cfg->gamma > 1.0 && std::isfinite(cfg->gamma))) return HYDRO_ERR_ARG;
+  if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return HYDRO_ERR_ARG;
+  if (!(cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0)) return HYDRO_ERR_ARG;
+  if (cfg->limiter < HYDRO_MINMOD || cfg->limiter > HYDRO_NOLIMIT) return HYDRO_ERR_ARG;
+  if (cfg->precision < HYDRO_FP64 || cfg->precision > HYDRO_MIXED) return HYDRO_ERR_ARG;
+  hydro_ctx* c = new hydro_ctx();
+  c->cfg = *cfg;
+  c->prm = hydro::Params{cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter};
+  c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  c->ops = cfg->precision == HYDRO_FP64 ? &hydro::ops_f64()
+                                        : (cfg->precision == HYDRO_FP32 ? &hydro::ops_f32() : &hydro::ops_mixed());
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return HYDRO_ERR_CUDA;
+  }
+  if (cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&c->d_counter, sizeof(int)) != cudaSuccess) {
+    hydro_finalize(c);
+    return HYDRO_ERR_NOMEM;
+  }
+  if (cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    hydro_finalize(c);
+    return HYDRO_ERR_CUDA;
+  }
+  // FP64 favours the square tile (fewest recomputed halo cells per update); others the wide one.
+  c->tile_id = 0;
+  c->zchunk = 32;
+  *ctx = c;
+  return HYDRO_OK;
+}
+
+int hydro_finalize(hydro_ctx* c) {
+  if (!c) return HYDRO_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->capture) cudaStreamDestroy(c->capture);
+  cudaFree(c->d_err);
+  cudaFree(c->d_counter);
+  cudaFree(c->d_patches);
+  cudaFree(c->d_counts);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_cfl);
+  cudaFree(c->d_adj);
+  if (c->h_patches) cudaFreeHost(c->h_patches);
+  if (c->h_cfl) cudaFreeHost(c->h_cfl);
+  delete c;
+  return HYDRO_OK;
+}
+
+int hydro_cfl_dt(hydro_ctx* c, const hydro_patch* p, int npatch, double* dt_dev) {
+  if (!c || !p || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i)
+    if (!valid_patch(c, p[i])) return HYDRO_ERR_ARG;
+  int rc = reset_slots(c, dt_dev, npatch, c->stream);
+  if (rc) return rc;
+  if (npatch == 1) {
+    c->launches += 1;
+    return cuda_status(c->ops->cfl(nullptr, make_io(p[0], p[0]), 1, c->prm, dt_dev, c->d_err, c->stream));
+  }
+  if (!same_set(c->cfl_key, p, npatch)) {
+    size_t old = c->cfl_cap;
+    rc = ensure_device(&c->d_cfl, &c->cfl_cap, (size_t)npatch);
+    if (rc) return rc;
+    if (c->cfl_cap != old || !c->h_cfl) {
+      if (c->h_cfl) cudaFreeHost(c->h_cfl);
+      if (cudaMallocHost(&c->h_cfl, c->cfl_cap * sizeof(HostPatchIO)) != cudaSuccess) return HYDRO_ERR_NOMEM;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    for (int i = 0; i < npatch; ++i) c->h_cfl[i] = make_io(p[i], p[i]);
+    if (cudaMemcpyAsync(c->d_cfl, c->h_cfl, npatch * sizeof(HostPatchIO), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      return HYDRO_ERR_CUDA;
+    c->cfl_key.assign(p, p + npatch);
+  }
+  HostPatchIO big = make_io(p[0], p[0]);
+  c->launches += 1;
+  return cuda_status(c->ops->cfl(c->d_cfl, big, npatch, c->prm, dt_dev, c->d_err, c->stream));
+}
+
+int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
+               double* dt_next_dev) {
+  if (!c || !in || !out || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i) {
+    if (!valid_patch(c, in[i]) || !valid_patch(c, out[i])) return HYDRO_ERR_ARG;
+    if (!same_shape(in[i], out[i])) return HYDRO_ERR_ARG;
+    if (overlaps(c, in[i], out[i])) return HYDRO_ERR_ARG;
+  }
+  if (npatch == 1 && in[0].ng == 0) return step_one_uniform(c, in[0], out[0], dt_dev, dt_next_dev, c->stream);
+  int rc = prepare_batch(c, in, out, npatch);
+  if (rc) return rc;
+  if (cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (dt_next_dev) {
+    rc = reset_slots(c, dt_next_dev, npatch, c->stream);
+    if (rc) return rc;
+  }
+  const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id);
+  int grid = std::max(1, std::min(c->ntiles, c->sm_count * per_sm));
+  c->launches += 1;
+  return cuda_status(c->ops->step_batched(c->tile_id, c->d_patches, c->d_tiles, c->ntiles, c->d_counter, c->prm,
+                                          dt_dev, dt_next_dev, c->zchunk, c->d_err, grid, c->stream));
+}
+
+int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], long long ngroups, double dx,
+                    const double* dt_dev) {
+  if (!c || !gathered || !out || ngroups < 1 || !finite_pos(dx) || !dt_dev) return HYDRO_ERR_ARG;
+  const int es = elem_size(c);
+  for (int v = 0; v < 5; ++v) {
+    if (!gathered[v] || !out[v]) return HYDRO_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(gathered[v]) % es || reinterpret_cast<uintptr_t>(out[v]) % es) return HYDRO_ERR_ARG;
+  }
+  c->launches += 1;
+  return cuda_status(c->ops->octs(gathered, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
+}
+
+int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
+                       const hydro_patch* lam_n, int npatch) {
+  if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1) return HYDRO_ERR_ARG;
+  if (c->cfg.precision == HYDRO_MIXED) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_patch &U = U_n[i], &L = lam_np1[i], &O = lam_n[i];
+    if (!valid_patch(c, U) || !valid_patch(c, L) || !valid_patch(c, O)) return HYDRO_ERR_ARG;
+    if (U.ng != 0 || L.ng != 0 || O.ng != 0) return HYDRO_ERR_ARG;
+    if (!same_shape(U, L) || !same_shape(U, O)) return HYDRO_ERR_ARG;
+    if (overlaps(c, L, O) || overlaps(c, U, O)) return HYDRO_ERR_ARG;
+  }
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_patch &U = U_n[i], &L = lam_np1[i], &O = lam_n[i];
+    const size_t need = c->ops->adjoint_scratch_bytes(U.nx, U.ny, U.nz);
+    if (need > c->adj_cap) {
+      cudaFree(c->d_adj);
+      c->d_adj = nullptr;
+      c->adj_cap = 0;
+      if (cudaMalloc(&c->d_adj, need) != cudaSuccess) return HYDRO_ERR_NOMEM;
+      c->adj_cap = need;
+    }
+    void* outp[5];
+    for (int v = 0; v < 5; ++v) outp[v] = O.U[v];
+    HostPatchIO lam = make_io(L, O);
+    c->launches += 2;
+    cudaError_t e = c->ops->adjoint(make_io(U, O), lam, outp, c->prm, dt_dev + i, c->d_adj, c->adj_cap, c->d_err,
+                                    c->stream);
+    if (e == cudaErrorNotSupported) return HYDRO_ERR_STATE;
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_prim_to_cons(hydro_ctx* c, const hydro_patch* W, const hydro_patch* U, int npatch) {
+  if (!c || !W || !U || npatch < 1) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i) {
+    if (!valid_patch(c, W[i]) || !valid_patch(c, U[i]) || !same_shape(W[i], U[i]) || overlaps(c, W[i], U[i]))
+      return HYDRO_ERR_ARG;
+  }
+  for (int i = 0; i < npatch; ++i) {
+    void* o[5];
+    for (int v = 0; v < 5; ++v) o[v] = U[i].U[v];
+    c->launches += 1;
+    cudaError_t e = c->ops->p2c(make_io(W[i], U[i]), o, c->prm, c->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_prim_to_cons_adjoint(hydro_ctx* c, const hydro_patch* W, const hydro_patch* lamU, const hydro_patch* lamW,
+                               int npatch) {
+  if (!c || !W || !lamU || !lamW || npatch < 1) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i) {
+    if (!valid_patch(c, W[i]) || !valid_patch(c, lamU[i]) || !valid_patch(c, lamW[i])) return HYDRO_ERR_ARG;
+    if (!same_shape(W[i], lamU[i]) || !same_shape(W[i], lamW[i])) return HYDRO_ERR_ARG;
+    if (overlaps(c, W[i], lamW[i]) || overlaps(c, lamU[i], lamW[i])) return HYDRO_ERR_ARG;
+  }
+  for (int i = 0; i < npatch; ++i) {
+    void* o[5];
+    for (int v = 0; v < 5; ++v) o[v] = lamW[i].U[v];
+    c->launches += 1;
+    cudaError_t e = c->ops->p2c_adjoint(make_io(W[i], lamW[i]), make_io(lamU[i], lamU[i]), o, c->prm, c->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+  }
+  return HYDRO_OK;
+}
+
+int hydro_run(hydro_ctx* c, const hydro_patch* a, const hydro_patch* b, int nsteps, double* dt_hist_dev,
+              int use_graph) {
+  if (!c || !a || !b || nsteps < 1 || !dt_hist_dev) return HYDRO_ERR_ARG;
+  if (!valid_patch(c, *a) || !valid_patch(c, *b) || a->ng != 0 || b->ng != 0) return HYDRO_ERR_ARG;
+  if (!same_shape(*a, *b) || overlaps(c, *a, *b)) return HYDRO_ERR_ARG;
+  auto enqueue = [&](cudaStream_t s) -> int {
+    int rc = reset_slots(c, dt_hist_dev, 1, s);
+    if (rc) return rc;
+    cudaError_t e = c->ops->cfl(nullptr, make_io(*a, *a), 1, c->prm, dt_hist_dev, c->d_err, s);
+    c->launches += 1;
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    for (int n = 0; n < nsteps; ++n) {
+      const hydro_patch& src = (n % 2 == 0) ? *a : *b;
+      const hydro_patch& dst = (n % 2 == 0) ? *b : *a;
+      rc = step_one_uniform(c, src, dst, dt_hist_dev + n, dt_hist_dev + n + 1, s);
+      if (rc) return rc;
+    }
+    return HYDRO_OK;
+  };
+  if (!use_graph) return enqueue(c->stream);
+  const bool hit = c->graph && c->g_a == a->U[0] && c->g_b == b->U[0] && c->g_n == nsteps && c->g_dt == dt_hist_dev &&
+                   c->g_tile == c->tile_id && c->g_zc == c->zchunk;
+  if (!hit) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    const long long before = c->launches;
+    if (cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HYDRO_ERR_CUDA;
+    int rc = enqueue(c->capture);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->capture, &g);
+    c->launches = before;  // capture launches nothing
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return HYDRO_ERR_CUDA;
+    }
+    c->g_a = a->U[0];
+    c->g_b = b->U[0];
+    c->g_n = nsteps;
+    c->g_dt = dt_hist_dev;
+    c->g_tile = c->tile_id;
+    c->g_zc = c->zchunk;
+  }
+  c->launches += nsteps + 1;
+  return cuda_status(cudaGraphLaunch(c->graph, c->stream));
+}
+
+int hydro_get_tuning(hydro_ctx* c, int* tile_id, int* zchunk) {
+  if (!c) return HYDRO_ERR_ARG;
+  if (tile_id) *tile_id = c->tile_id;
+  if (zchunk) *zchunk = c->zchunk;
+  return HYDRO_OK;
+}
+
+int hydro_set_tuning(hydro_ctx* c, int tile_id, int zchunk) {
+  if (!c || tile_id < 0 || tile_id >= hydro::kNumTiles || zchunk < 1 || zchunk > 4096) return HYDRO_ERR_ARG;
+  c->tile_id = tile_id;
+  c->zchunk = zchunk;
+  return HYDRO_OK;
+}
+
+int hydro_autotune(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
+                   const char* cache_path) {
+  if (!c || !in || !out || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  // signature of the patch set: count, precision and total cells
+  long long cells = 0;
+  for (int i = 0; i < npatch; ++i) cells += (long long)in[i].nx * in[i].ny * in[i].nz;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return HYDRO_ERR_CUDA;
+  char key[512];
+  std::snprintf(key, sizeof(key), "%s|sm%d|p%d|l%d|n%d|c%lld|g%d", prop.name, c->sm_count, c->cfg.precision,
+                c->cfg.limiter, npatch, cells, in[0].ng);
+  for (char* k = key; *k; ++k)
+    if (*k == ' ') *k = '_';
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char k2[512];
+      int t, z;
+      while (std::fscanf(f, "%511s %d %d", k2, &t, &z) == 3) {
+        if (std::strcmp(k2, key) == 0 && t >= 0 && t < hydro::kNumTiles && z >= 1) {
+          c->tile_id = t;
+          c->zchunk = z;
+          std::fclose(f);
+          return HYDRO_OK;
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  int maxnz = 1;
+  for (int i = 0; i < npatch; ++i) maxnz = std::max(maxnz, in[i].nz);
+  const int zcs[] = {8, 16, 32, 64, 128};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bt = c->tile_id, bz = c->zchunk;
+  for (int t = 0; t < hydro::kNumTiles; ++t) {
+    for (int zc : zcs) {
+      if (zc > std::max(8, maxnz)) continue;
+      c->tile_id = t;
+      c->zchunk = zc;
+      int rc = hydro_step(c, in, out, npatch, dt_dev, nullptr);  // warm-up (and work-list build)
+      if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3; ++r) hydro_step(c, in, out, npatch, dt_dev, nullptr);
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return HYDRO_ERR_CUDA;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bt = t;
+        bz = zc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tile_id = bt;
+  c->zchunk = bz;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s %d %d\n", key, bt, bz);
+      std::fclose(f);
+    }
+  }
+  return HYDRO_OK;
+}
+
+int hydro_get_error(hydro_ctx* c, unsigned* error_bits) {
+  if (!c) return HYDRO_ERR_ARG;
+  unsigned bits = 0;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (cudaMemcpy(&bits, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (error_bits) *error_bits = bits;
+  return bits ? HYDRO_ERR_UNPHYSICAL : HYDRO_OK;
+}
+
+int hydro_clear_error(hydro_ctx* c) {
+  if (!c) return HYDRO_ERR_ARG;
+  return cuda_status(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+}
+
+int hydro_launch_count(hydro_ctx* c, long long* count) {
+  if (!c || !count) return HYDRO_ERR_ARG;
+  *count = c->launches;
+  return HYDRO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+// Device-side arithmetic of one MUSCL-Hancock/HLLC step of the 3D ideal-gas Euler equations
+// (the hydro path of the paper, Sec. 2 and Sec. 4; textbook scheme, see include/hydro.h):
+// primitive recovery, limited PLM slopes, the unsplit primitive Hancock predictor, floored face
+// states, HLLC fluxes and the per-cell CFL speed.  Three precision policies:
+//   PolF64   double state, double arithmetic;
+//   PolF32   float state, float arithmetic, pressure recovery by error-free transformations;
+//   PolMixed double state, double pressure recovery and update accumulation, float bulk.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hydro.h"
+
+namespace hydro {
+
+constexpr int NG = 2;  // ghost layers of the stencil
+
+struct Params {
+  double gamma, cfl, rho_floor, p_floor;
+  int limiter;
+};
+
+// ------------------------------------------------------------------ small helpers
+template <class R>
+__device__ __forceinline__ R rabs(R x) {
+  return x < R(0) ? -x : x;
+}
+__device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+
+// Order-preserving 64-bit key of a non-negative double (IEEE bits compare as unsigned ints).
+__device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// ------------------------------------------------------------------ slope limiter
+// MinMod: 0 if a*b <= 0, else the argument of smaller magnitude (tie -> a).
+// MC: 0 if a*b <= 0, else the smallest magnitude of 2a, 2b, (a+b)/2 (ties -> earlier).
+// None: the centred difference (a+b)/2.
+template <class R>
+__device__ __forceinline__ R limited(R a, R b, int lim) {
+  if (lim == HYDRO_NOLIMIT) return R(0.5) * (a + b);
+  if (a * b <= R(0)) return R(0);
+  if (lim == HYDRO_MINMOD) return (rabs(a) <= rabs(b)) ? a : b;
+  R ta = R(2) * a, tb = R(2) * b, m = R(0.5) * (a + b);
+  R best = ta;
+  if (rabs(tb) < rabs(best)) best = tb;
+  if (rabs(m) < rabs(best)) best = m;
+  return best;
+}
+
+// ------------------------------------------------------------------ Hancock predictor
+// qh = q - hdt * (A_x dqx + A_y dqy + A_z dqz), A_d the primitive Jacobian of direction d.
+template <class R>
+__device__ __forceinline__ void hancock(const R q[5], const R dqx[5], const R dqy[5], const R dqz[5], R gamma, R hdt,
+                                        R qh[5]) {
+  const R ir = rcp_(q[0]);
+  const R gp = gamma * q[4];
+  // x: normal u
+  R tx0 = q[1] * dqx[0] + q[0] * dqx[1];
+  R tx1 = q[1] * dqx[1] + dqx[4] * ir;
+  R tx2 = q[1] * dqx[2];
+  R tx3 = q[1] * dqx[3];
+  R tx4 = gp * dqx[1] + q[1] * dqx[4];
+  // y: normal v
+  R ty0 = q[2] * dqy[0] + q[0] * dqy[2];
+  R ty1 = q[2] * dqy[1];
+  R ty2 = q[2] * dqy[2] + dqy[4] * ir;
+  R ty3 = q[2] * dqy[3];
+  R ty4 = gp * dqy[2] + q[2] * dqy[4];
+  // z: normal w
+  R tz0 = q[3] * dqz[0] + q[0] * dqz[3];
+  R tz1 = q[3] * dqz[1];
+  R tz2 = q[3] * dqz[2];
+  R tz3 = q[3] * dqz[3] + dqz[4] * ir;
+  R tz4 = gp * dqz[3] + q[3] * dqz[4];
+  qh[0] = q[0] - hdt * ((tx0 + ty0) + tz0);
+  qh[1] = q[1] - hdt * ((tx1 + ty1) + tz1);
+  qh[2] = q[2] - hdt * ((tx2 + ty2) + tz2);
+  qh[3] = q[3] - hdt * ((tx3 + ty3) + tz3);
+  qh[4] = q[4] - hdt * ((tx4 + ty4) + tz4);
+}
+
+template <class R>
+__device__ __forceinline__ void floor_state(R q[5], R rho_floor, R p_floor) {
+  q[0] = q[0] < rho_floor ? rho_floor : q[0];
+  q[4] = q[4] < p_floor ? p_floor : q[4];
+}
+
+// ------------------------------------------------------------------ HLLC
+// Flux through a face between floored states, in face-normal components: q = (rho, u_n, u_t1,
+// u_t2, p); ke = u^2 + v^2 + w^2 summed in x, y, z order.  F = F_L if 0 <= S_L; F_R if S_R <= 0;
+// else F_K + S_K (U*_K - U_K) with K = L if S* >= 0 else R (Davis speeds, Batten et al. star
+// state).  Only the upwind side's physical flux is formed; branches are selected, not multiplied.
+template <class R>
+__device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R keR, R gamma, R inv_gm1, R F[5]) {
+  const R irL = rcp_(qL[0]), irR = rcp_(qR[0]);
+  const R cL = rsqrt_(gamma * qL[4] * irL);
+  const R cR = rsqrt_(gamma * qR[4] * irR);
+  const R uL = qL[1], uR = qR[1];
+  const R aL = uL - cL, bL = uR - cR;
+  const R SL = aL <= bL ? aL : bL;
+  const R aR = uL + cL, bR = uR + cR;
+  const R SR = aR >= bR ? aR : bR;
+  const R mL = qL[0] * (SL - uL);
+  const R mR = qR[0] * (SR - uR);
+  const R Ss = (qR[4] - qL[4] + uL * mL - uR * mR) / (mL - mR);
+  const bool star = (SL < R(0)) && (SR > R(0));
+  const bool left = (SL >= R(0)) || (SR > R(0) && Ss >= R(0));
+  const R rK = left ? qL[0] : qR[0];
+  const R uK = left ? uL : uR;
+  const R t1 = left ? qL[2] : qR[2];
+  const R t2 = left ? qL[3] : qR[3];
+  const R pK = left ? qL[4] : qR[4];
+  const R keK = left ? keL : keR;
+  const R irK = left ? irL : irR;
+  const R SK = left ? SL : SR;
+  const R mK = left ? mL : mR;
+  const R EK = pK * inv_gm1 + R(0.5) * rK * keK;
+  const R mn = rK * uK;
+  R FK[5], UK[5];
+  FK[0] = mn;
+  FK[1] = mn * uK + pK;
+  FK[2] = mn * t1;
+  FK[3] = mn * t2;
+  FK[4] = uK * (EK + pK);
+  UK[0] = rK;
+  UK[1] = mn;
+  UK[2] = rK * t1;
+  UK[3] = rK * t2;
+  UK[4] = EK;
+  const R fac = mK / (SK - Ss);
+  R Us[5];
+  Us[0] = fac;
+  Us[1] = fac * Ss;
+  Us[2] = fac * t1;
+  Us[3] = fac * t2;
+  Us[4] = fac * (EK * irK + (Ss - uK) * (Ss + pK / mK));
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = star ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
+}
+
+template <class R>
+__device__ __forceinline__ R kinetic_sum(const R q[5]) {
+  return (q[1] * q[1] + q[2] * q[2]) + q[3] * q[3];
+}
+
+// Face of compile-time normal D (0 x, 1 y, 2 z); q, F in (rho, u, v, w, p) / (rho, m_x, m_y, m_z, E).
+template <int D, class R>
+__device__ __forceinline__ void hllc(const R qL[5], const R qR[5], R gamma, R inv_gm1, R F[5]) {
+  constexpr int N = 1 + D;
+  constexpr int T1 = (D == 0) ? 2 : 1;
+  constexpr int T2 = (D == 2) ? 2 : 3;
+  const R a[5] = {qL[0], qL[N], qL[T1], qL[T2], qL[4]};
+  const R b[5] = {qR[0], qR[N], qR[T1], qR[T2], qR[4]};
+  R Fr[5];
+  hllc_core(a, b, kinetic_sum(qL), kinetic_sum(qR), gamma, inv_gm1, Fr);
+  F[0] = Fr[0];
+  F[N] = Fr[1];
+  F[T1] = Fr[2];
+  F[T2] = Fr[3];
+  F[4] = Fr[4];
+}
+
+// Same flux for a runtime normal d (selects instead of register indexing).
+template <class R>
+__device__ __forceinline__ void hllc_dyn(int d, const R qL[5], const R qR[5], R gamma, R inv_gm1, R F[5]) {
+  const R a[5] = {qL[0], d == 0 ? qL[1] : (d == 1 ? qL[2] : qL[3]), d == 0 ? qL[2] : qL[1],
+                  d == 2 ? qL[2] : qL[3], qL[4]};
+  const R b[5] = {qR[0], d == 0 ? qR[1] : (d == 1 ? qR[2] : qR[3]), d == 0 ? qR[2] : qR[1],
+                  d == 2 ? qR[2] : qR[3], qR[4]};
+  R Fr[5];
+  hllc_core(a, b, kinetic_sum(qL), kinetic_sum(qR), gamma, inv_gm1, Fr);
+  F[0] = Fr[0];
+  F[1] = d == 0 ? Fr[1] : Fr[2];
+  F[2] = d == 1 ? Fr[1] : (d == 0 ? Fr[2] : Fr[3]);
+  F[3] = d == 2 ? Fr[1] : Fr[3];
+  F[4] = Fr[4];
+}
+
+// ------------------------------------------------------------------ error-free transformations
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  float bb = s - a;
+  return (a - (s - bb)) + (b - bb);
+}
+
+// ------------------------------------------------------------------ precision policies
+// recover(): U (storage) -> q (arithmetic), floors applied, flags set on floors / non-finite.
+// speed():   |u| + |v| + |w| + 3c of a stored state (CFL), in the arithmetic type.
+// update():  U_old - dtdx * div in the policy's accumulation precision.
+
+struct PolF64 {
+  using S = double;
+  using R = double;
+  static __device__ __forceinline__ void recover(const double U[5], const Params& P, double q[5], unsigned& flags) {
+    double rho = U[0];
+    if (rho < P.rho_floor) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = P.rho_floor; }
+    const double ir = 1.0 / rho;
+    const double kin = 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir;
+    const double eint = U[4] - kin;
+    if (eint < 0.0) flags |= HYDRO_EBIT_P_FLOOR;
+    double p = (P.gamma - 1.0) * eint;
+    if (!(isfinite(p) && isfinite(rho))) flags |= HYDRO_EBIT_NONFINITE;
+    q[0] = rho;
+    q[1] = U[1] * ir;
+    q[2] = U[2] * ir;
+    q[3] = U[3] * ir;
+    q[4] = p < P.p_floor ? P.p_floor : p;
+  }
+  static __device__ __forceinline__ double update(double Uold, double dtdx, double div) { return Uold - dtdx * div; }
+};
+
+struct PolF32 {
+  using S = float;
+  using R = float;
+  // p = (gamma-1)(E - K/(2 rho)), K = |m|^2, with K formed exactly as a float pair (two-product
+  // and two-sum), K/rho as a float pair (exact FMA residual), and E - K/(2 rho) by two-sum: the
+  // cancellation between E and the kinetic energy loses nothing beyond the final rounding.
+  static __device__ __forceinline__ void recover(const float U[5], const Params& P, float q[5], unsigned& flags) {
+    float rho = U[0];
+    const float rf = (float)P.rho_floor;
+    if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
+    const float ir = __frcp_rn(rho);
+    const float mx = U[1], my = U[2], mz = U[3];
+    const float a1 = mx * mx, e1 = fmaf(mx, mx, -a1);
+    const float a2 = my * my, e2 = fmaf(my, my, -a2);
+    const float a3 = mz * mz, e3 = fmaf(mz, mz, -a3);
+    const float s1 = a1 + a2;
+    const float t1 = two_sum_err(a1, a2, s1);
+    const float Kh = s1 + a3;
+    const float t2 = two_sum_err(s1, a3, Kh);
+    const float Kl = ((e1 + e2) + e3) + (t1 + t2);
+    // kinetic energy (K/rho)/2 = (kh + kl)/2
+    const float kh = Kh * ir;
+    const float r = fmaf(-kh, rho, Kh);
+    const float kl = (r + Kl) * ir;
+    const float hk = 0.5f * kh;
+    const float d = U[4] - hk;
+    const float de = two_sum_err(U[4], -hk, d);
+    const float eint = d + (de - 0.5f * kl);
+    if (eint < 0.f) flags |= HYDRO_EBIT_P_FLOOR;
+    float p = (float)(P.gamma - 1.0) * eint;
+    if (!(isfinite(p) && isfinite(rho))) flags |= HYDRO_EBIT_NONFINITE;
+    const float pf = (float)P.p_floor;
+    q[0] = rho;
+    q[1] = mx * ir;
+    q[2] = my * ir;
+    q[3] = mz * ir;
+    q[4] = p < pf ? pf : p;
+  }
+  static __device__ __forceinline__ float update(float Uold, float dtdx, float div) { return Uold - dtdx * div; }
+};
+
+struct PolMixed {
+  using S = double;
+  using R = float;
+  // Recovery in double: the kinetic energy with a float reciprocal refined by one Newton step in
+  // double (relative error ~2^-46), the subtraction E - kin in double, then rounded to float.
+  static __device__ __forceinline__ void recover(const double U[5], const Params& P, float q[5], unsigned& flags) {
+    double rho = U[0];
+    if (rho < P.rho_floor) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = P.rho_floor; }
+    const double ir0 = (double)__frcp_rn((float)rho);
+    const double ir = fma(ir0, fma(-rho, ir0, 1.0), ir0);
+    const double K = fma(U[3], U[3], fma(U[2], U[2], U[1] * U[1]));
+    const double eint = fma(-0.5 * K, ir, U[4]);
+    if (eint < 0.0) flags |= HYDRO_EBIT_P_FLOOR;
+    float p = (float)((P.gamma - 1.0) * eint);
+    const float rhof = (float)rho;
+    if (!(isfinite(p) && isfinite(rhof))) flags |= HYDRO_EBIT_NONFINITE;
+    const float irf = (float)ir;
+    const float pf = (float)P.p_floor;
+    q[0] = rhof;
+    q[1] = (float)U[1] * irf;
+    q[2] = (float)U[2] * irf;
+    q[3] = (float)U[3] * irf;
+    q[4] = p < pf ? pf : p;
+  }
+  // dU = dtdx * div in float, accumulated into the double state.
+  static __device__ __forceinline__ double update(double Uold, float dtdx, float div) {
+    return Uold - (double)(dtdx * div);
+  }
+};
+
+// CFL speed of a recovered state.
+template <class R>
+__device__ __forceinline__ R cfl_speed(const R q[5], R gamma) {
+  const R c = rsqrt_(gamma * q[4] * rcp_(q[0]));
+  return ((rabs(q[1]) + rabs(q[2])) + rabs(q[3])) + R(3) * c;
+}
+
+}  // namespace hydro

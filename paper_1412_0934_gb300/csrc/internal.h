@@ -1,0 +1,66 @@
+// Host-side interface between the C ABI (hydro_api.cu) and the per-precision kernel files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hydro.h"
+
+namespace hydro {
+
+struct Params;
+
+// Layout-compatible host image of PatchIO<S> (pointers are untyped here).
+struct HostPatchIO {
+  const void* in[5];
+  void* out[5];
+  int nx, ny, nz;
+  int gin, gout;
+  long long isy, isz, osy, osz;
+  double dx;
+};
+
+struct HostTileRec {
+  int patch, x0, y0, z0;
+};
+
+// Compiled tile shapes of the step kernels (TX x TY columns per block).
+constexpr int kNumTiles = 3;
+constexpr int kTileX[kNumTiles] = {16, 32, 8};
+constexpr int kTileY[kNumTiles] = {16, 8, 8};
+
+struct KernelOps {
+  // Uniform periodic grid (npatch == 1, gin == 0).
+  cudaError_t (*step_uniform)(int tile, const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next,
+                              int zchunk, unsigned* err, cudaStream_t s);
+  // Persistent batched step over a device work-list.
+  cudaError_t (*step_batched)(int tile, const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles,
+                              int* d_counter, const Params& prm, const double* dt, double* dt_next, int zchunk,
+                              unsigned* err, int grid, cudaStream_t s);
+  // Occupancy (blocks per SM) of the batched kernel for a tile shape.
+  int (*batched_blocks_per_sm)(int tile);
+  // CFL dt per patch: d_patches (device) or a single patch by value when d_patches == nullptr.
+  cudaError_t (*cfl)(const HostPatchIO* d_patches, const HostPatchIO& single, int npatch, const Params& prm,
+                     double* dt_out, unsigned* err, cudaStream_t s);
+  // Oct groups (6^3 gathered -> 2^3).
+  cudaError_t (*octs)(void* const gathered[5], void* const out[5], long long ngroups, double dx, const Params& prm,
+                      const double* dt, unsigned* err, cudaStream_t s);
+  // Adjoint of one periodic step.
+  cudaError_t (*adjoint)(const HostPatchIO& U, const HostPatchIO& lam, void* const lam_out[5], const Params& prm,
+                         const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s);
+  size_t (*adjoint_scratch_bytes)(int nx, int ny, int nz);
+  // Primitive -> conservative map and its adjoint, elementwise over a patch (interior).
+  cudaError_t (*p2c)(const HostPatchIO& W, void* const U[5], const Params& prm, cudaStream_t s);
+  cudaError_t (*p2c_adjoint)(const HostPatchIO& W, const HostPatchIO& lamU, void* const lamW[5], const Params& prm,
+                             cudaStream_t s);
+  int elem_size;  // bytes per stored element
+  int launches_per_step;
+};
+
+const KernelOps& ops_f64();
+const KernelOps& ops_f32();
+const KernelOps& ops_mixed();
+
+// Work-list construction (precision-independent; descriptors read through HostPatchIO).
+cudaError_t build_worklist(const HostPatchIO* d_patches, int npatch, int tx, int ty, int zchunk, int* d_counts,
+                           HostTileRec* d_tiles, cudaStream_t s);
+
+}  // namespace hydro

@@ -1,0 +1,400 @@
+// Kernels and launchers of one precision policy POL (included once per policy by kernels_*.cu):
+// the step kernels of step_tile.cuh for every compiled tile shape, the standalone CFL dt
+// reduction, the oct-group step, the primitive->conservative map and its adjoint, and the
+// adjoint step (adjoint.cuh).
+#pragma once
+#include "adjoint.cuh"
+#include "internal.h"
+#include "step_tile.cuh"
+
+namespace hydro {
+
+// ------------------------------------------------------------------ step launchers
+template <class Pol, int TX, int TY>
+cudaError_t launch_uniform_t(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
+                             unsigned* err, cudaStream_t s) {
+  const size_t smem = sizeof(TileShared<Pol, TX, TY>);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
+  k_step_uniform<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
+  return cudaGetLastError();
+}
+
+template <class Pol, int TX, int TY>
+cudaError_t launch_batched_t(const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles, int* d_counter,
+                             const Params& prm, const double* dt, double* dt_next, int zchunk, unsigned* err, int grid,
+                             cudaStream_t s) {
+  const size_t smem = sizeof(TileShared<Pol, TX, TY>);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_batched<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_step_batched<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(
+      reinterpret_cast<const PatchIO<typename Pol::S>*>(d_patches), reinterpret_cast<const TileRec*>(d_tiles), ntiles,
+      d_counter, prm, dt, dt_next, zchunk, err);
+  return cudaGetLastError();
+}
+
+template <class Pol, int TX, int TY>
+int blocks_per_sm_t() {
+  const size_t smem = sizeof(TileShared<Pol, TX, TY>);
+  cudaFuncSetAttribute(k_step_batched<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<Pol, TX, TY>, TX * TY, smem) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+template <class Pol>
+cudaError_t launch_uniform(int tile, const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next,
+                           int zchunk, unsigned* err, cudaStream_t s) {
+  switch (tile) {
+    case 0: return launch_uniform_t<Pol, kTileX[0], kTileY[0]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 1: return launch_uniform_t<Pol, kTileX[1], kTileY[1]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 2: return launch_uniform_t<Pol, kTileX[2], kTileY[2]>(P, prm, dt, dt_next, zchunk, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class Pol>
+cudaError_t launch_batched(int tile, const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles,
+                           int* d_counter, const Params& prm, const double* dt, double* dt_next, int zchunk,
+                           unsigned* err, int grid, cudaStream_t s) {
+  switch (tile) {
+    case 0: return launch_batched_t<Pol, kTileX[0], kTileY[0]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 1: return launch_batched_t<Pol, kTileX[1], kTileY[1]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 2: return launch_batched_t<Pol, kTileX[2], kTileY[2]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class Pol>
+int batched_blocks_per_sm(int tile) {
+  switch (tile) {
+    case 0: return blocks_per_sm_t<Pol, kTileX[0], kTileY[0]>();
+    case 1: return blocks_per_sm_t<Pol, kTileX[1], kTileY[1]>();
+    case 2: return blocks_per_sm_t<Pol, kTileX[2], kTileY[2]>();
+  }
+  return 1;
+}
+
+// ------------------------------------------------------------------ CFL dt (standalone)
+// blockIdx.y walks the patches, blockIdx.x the interior cells of one patch.  The per-block
+// largest speed is reduced by warp shuffles and shared memory and folded into the patch's dt
+// slot exactly as the step's fused epilogue does, so both give the same bits.
+template <class Pol>
+__global__ void __launch_bounds__(256) k_cfl(const PatchIO<typename Pol::S>* patches, PatchIO<typename Pol::S> single,
+                                             int npatch, Params prm, double* dt_out, unsigned* err) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  __shared__ R red[8];
+  unsigned flags = 0;
+  for (int pi = blockIdx.y; pi < npatch; pi += gridDim.y) {
+    const PatchIO<S> P = patches ? patches[pi] : single;
+    const long long nxy = (long long)P.nx * P.ny, n = nxy * P.nz;
+    R smax = 0;
+    for (long long c = (long long)blockIdx.x * 256 + threadIdx.x; c < n; c += (long long)gridDim.x * 256) {
+      const int k = (int)(c / nxy);
+      const long long r = c - (long long)k * nxy;
+      const int j = (int)(r / P.nx);
+      const int i = (int)(r - (long long)j * P.nx);
+      const long long a = (long long)(k + P.gin) * P.isz + (long long)(j + P.gin) * P.isy + (i + P.gin);
+      S U[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = __ldg(P.in[v] + a);
+      R q[5];
+      Pol::recover(U, prm, q, flags);
+      const R sp = cfl_speed(q, (R)prm.gamma);
+      smax = sp > smax ? sp : smax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      R w = __shfl_xor_sync(0xffffffffu, smax, o);
+      smax = w > smax ? w : smax;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; ++w) smax = red[w] > smax ? red[w] : smax;
+      publish_dt(prm.cfl, P.dx, (double)smax, dt_out + pi);
+    }
+  }
+  flush_flags(flags, err);
+}
+
+template <class Pol>
+cudaError_t launch_cfl(const HostPatchIO* d_patches, const HostPatchIO& single, int npatch, const Params& prm,
+                       double* dt_out, unsigned* err, cudaStream_t s) {
+  long long maxcells = (long long)single.nx * single.ny * single.nz;
+  int gx;
+  if (d_patches) {
+    gx = 64;  // patches up to a few 10^5 cells
+  } else {
+    long long b = (maxcells + 256 * 4 - 1) / (256 * 4);
+    gx = (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+  }
+  dim3 grid(gx, npatch < 65535 ? npatch : 65535);
+  k_cfl<Pol><<<grid, 256, 0, s>>>(reinterpret_cast<const PatchIO<typename Pol::S>*>(d_patches), to_dev<Pol>(single),
+                                  npatch, prm, dt_out, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ oct groups
+// One warp per group.  The 80 cells of the 6^3 stencil that the step reads are recovered into
+// shared memory; the 32 cells next to the oct's faces (the oct and the 24 outside neighbours
+// across its faces) are predicted; the 36 faces of the oct get HLLC fluxes; 8 lanes update the
+// oct.  Local coordinates run from -2 to 3 (stored at +2).
+__device__ __forceinline__ bool oct_needed(int x, int y, int z) {
+  const int ox = (x < 0 || x > 1), oy = (y < 0 || y > 1), oz = (z < 0 || z > 1);
+  const int nout = ox + oy + oz;
+  const bool far = (x == -2 || x == 3 || y == -2 || y == 3 || z == -2 || z == 3);
+  return nout <= 1 || (nout == 2 && !far);
+}
+// Coordinates of predicted cell e (0..31): 0..7 the oct, 8..31 the face neighbours.
+__device__ __forceinline__ void oct_ecell(int e, int& x, int& y, int& z) {
+  if (e < 8) { x = e & 1; y = (e >> 1) & 1; z = (e >> 2) & 1; return; }
+  const int r = e - 8, f = r >> 2, a = r & 1, b = (r >> 1) & 1;
+  const int out = (f & 1) ? 2 : -1;
+  const int d = f >> 1;
+  x = d == 0 ? out : a;
+  y = d == 1 ? out : (d == 0 ? a : b);
+  z = d == 2 ? out : b;
+}
+__device__ __forceinline__ int oct_eindex(int x, int y, int z) {
+  const bool ix = (x == 0 || x == 1), iy = (y == 0 || y == 1), iz = (z == 0 || z == 1);
+  if (ix && iy && iz) return x + 2 * y + 4 * z;
+  int d, c, a, b;
+  if (!ix) { d = 0; c = x; a = y; b = z; }
+  else if (!iy) { d = 1; c = y; a = x; b = z; }
+  else { d = 2; c = z; a = x; b = y; }
+  const int f = 2 * d + (c == 2 ? 1 : 0);
+  return 8 + 4 * f + a + 2 * b;
+}
+
+constexpr int kOctWarps = 4;
+
+template <class Pol>
+struct OctSmem {
+  using R = typename Pol::R;
+  R q[kOctWarps][5][216];
+  R qh[kOctWarps][5][32];
+  R sl[kOctWarps][3][5][32];
+  R f[kOctWarps][5][36];
+  short need[80];
+};
+
+template <class Pol>
+__global__ void __launch_bounds__(32 * kOctWarps) k_octs(const typename Pol::S* __restrict__ g0,
+                                                         const typename Pol::S* __restrict__ g1,
+                                                         const typename Pol::S* __restrict__ g2,
+                                                         const typename Pol::S* __restrict__ g3,
+                                                         const typename Pol::S* __restrict__ g4,
+                                                         typename Pol::S* o0, typename Pol::S* o1, typename Pol::S* o2,
+                                                         typename Pol::S* o3, typename Pol::S* o4, long long ngroups,
+                                                         double dx, Params prm, const double* dt_dev, unsigned* err) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<OctSmem<Pol>*>(smem_raw);
+  const S* gin[5] = {g0, g1, g2, g3, g4};
+  S* gout[5] = {o0, o1, o2, o3, o4};
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int c = 0; c < 216; ++c) {
+      const int x = c % 6 - 2, y = (c / 6) % 6 - 2, z = c / 36 - 2;
+      if (oct_needed(x, y, z)) sm.need[n++] = (short)c;
+    }
+  }
+  __syncthreads();
+  const double dt = dt_dev[0];
+  if (!(dt > 0.0 && dt <= 1e300)) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(err, HYDRO_EBIT_BAD_DT);
+    return;
+  }
+  const R hdt = (R)(0.5 * dt / dx);
+  const R dtdx = (R)(dt / dx);
+  const R gamma = (R)prm.gamma, igm1 = (R)(1.0 / (prm.gamma - 1.0));
+  const R rf = (R)prm.rho_floor, pf = (R)prm.p_floor;
+  unsigned flags = 0;
+  for (long long g = (long long)blockIdx.x * kOctWarps + w; g < ngroups; g += (long long)gridDim.x * kOctWarps) {
+    const long long base = g * 216;
+    for (int t = lane; t < 80; t += 32) {
+      const int c = sm.need[t];
+      S U[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = __ldg(gin[v] + base + c);
+      R q[5];
+      Pol::recover(U, prm, q, flags);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.q[w][v][c] = q[v];
+    }
+    __syncwarp();
+    {
+      int x, y, z;
+      oct_ecell(lane, x, y, z);
+      const int c = (z + 2) * 36 + (y + 2) * 6 + (x + 2);
+      R q0[5], dqx[5], dqy[5], dqz[5], qh[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R* Q = sm.q[w][v];
+        const R cc = Q[c];
+        q0[v] = cc;
+        dqx[v] = limited(cc - Q[c - 1], Q[c + 1] - cc, prm.limiter);
+        dqy[v] = limited(cc - Q[c - 6], Q[c + 6] - cc, prm.limiter);
+        dqz[v] = limited(cc - Q[c - 36], Q[c + 36] - cc, prm.limiter);
+      }
+      hancock(q0, dqx, dqy, dqz, gamma, hdt, qh);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        sm.qh[w][v][lane] = qh[v];
+        sm.sl[w][0][v][lane] = dqx[v];
+        sm.sl[w][1][v][lane] = dqy[v];
+        sm.sl[w][2][v][lane] = dqz[v];
+      }
+    }
+    __syncwarp();
+    for (int fi = lane; fi < 36; fi += 32) {
+      const int d = fi / 12, m = fi % 12, s = m >> 2, a = m & 1, b = (m >> 1) & 1;
+      // face between cells at coordinate s-1 and s along d; (a, b) the transverse coordinates
+      int lx, ly, lz;
+      if (d == 0) { lx = s - 1; ly = a; lz = b; }
+      else if (d == 1) { lx = a; ly = s - 1; lz = b; }
+      else { lx = a; ly = b; lz = s - 1; }
+      const int eL = oct_eindex(lx, ly, lz);
+      const int eR = oct_eindex(lx + (d == 0), ly + (d == 1), lz + (d == 2));
+      R qL[5], qR[5], F[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qL[v] = sm.qh[w][v][eL] + R(0.5) * sm.sl[w][d][v][eL];
+        qR[v] = sm.qh[w][v][eR] - R(0.5) * sm.sl[w][d][v][eR];
+      }
+      floor_state(qL, rf, pf);
+      floor_state(qR, rf, pf);
+      hllc_dyn(d, qL, qR, gamma, igm1, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.f[w][v][fi] = F[v];
+    }
+    __syncwarp();
+    if (lane < 8) {
+      const int x = lane & 1, y = (lane >> 1) & 1, z = (lane >> 2) & 1;
+      const int c = (z + 2) * 36 + (y + 2) * 6 + (x + 2);
+      const int fxm = 0 * 12 + (x * 4 + y + 2 * z), fxp = fxm + 4;
+      const int fym = 1 * 12 + (y * 4 + x + 2 * z), fyp = fym + 4;
+      const int fzm = 2 * 12 + (z * 4 + x + 2 * y), fzp = fzm + 4;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R* F = sm.f[w][v];
+        const R div = ((F[fxp] - F[fxm]) + (F[fyp] - F[fym])) + (F[fzp] - F[fzm]);
+        gout[v][g * 8 + lane] = Pol::update(__ldg(gin[v] + base + c), dtdx, div);
+      }
+    }
+    __syncwarp();
+  }
+  flush_flags(flags, err);
+}
+
+template <class Pol>
+cudaError_t launch_octs(void* const gathered[5], void* const out[5], long long ngroups, double dx, const Params& prm,
+                        const double* dt, unsigned* err, cudaStream_t s) {
+  using S = typename Pol::S;
+  const size_t smem = sizeof(OctSmem<Pol>);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_octs<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  long long blocks = (ngroups + kOctWarps - 1) / kOctWarps;
+  const long long cap = 152LL * 64;
+  if (blocks > cap) blocks = cap;
+  k_octs<Pol><<<(unsigned)blocks, 32 * kOctWarps, smem, s>>>(
+      (const S*)gathered[0], (const S*)gathered[1], (const S*)gathered[2], (const S*)gathered[3],
+      (const S*)gathered[4], (S*)out[0], (S*)out[1], (S*)out[2], (S*)out[3], (S*)out[4], ngroups, dx, prm, dt, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ primitive <-> conservative
+template <class S>
+__device__ __forceinline__ long long cell_offset(const PatchIO<S>& P, long long c, bool out_side) {
+  const long long nxy = (long long)P.nx * P.ny;
+  const int k = (int)(c / nxy);
+  const long long r = c - (long long)k * nxy;
+  const int j = (int)(r / P.nx);
+  const int i = (int)(r - (long long)j * P.nx);
+  const int g = out_side ? P.gout : P.gin;
+  const long long sy = out_side ? P.osy : P.isy, sz = out_side ? P.osz : P.isz;
+  return (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g);
+}
+
+// U = (rho, rho u, rho v, rho w, p/(gamma-1) + rho |u|^2 / 2), in the storage type.
+template <class S>
+__global__ void k_p2c(PatchIO<S> P, double gamma) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  const S igm1 = (S)(1.0 / (gamma - 1.0));
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const long long a = cell_offset(P, c, false), b = cell_offset(P, c, true);
+    const S r = P.in[0][a], u = P.in[1][a], v = P.in[2][a], w = P.in[3][a], p = P.in[4][a];
+    P.out[0][b] = r;
+    P.out[1][b] = r * u;
+    P.out[2][b] = r * v;
+    P.out[3][b] = r * w;
+    P.out[4][b] = p * igm1 + S(0.5) * r * ((u * u + v * v) + w * w);
+  }
+}
+
+// lamW = (dU/dW)^T lamU.  W and lamU share one layout (P.in / L.in); lamW uses P.out's layout.
+template <class S>
+__global__ void k_p2c_adjoint(PatchIO<S> P, PatchIO<S> L, double gamma) {
+  const long long n = (long long)P.nx * P.ny * P.nz;
+  const S igm1 = (S)(1.0 / (gamma - 1.0));
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const long long a = cell_offset(P, c, false), la = cell_offset(L, c, false), b = cell_offset(P, c, true);
+    const S r = P.in[0][a], u = P.in[1][a], v = P.in[2][a], w = P.in[3][a];
+    const S l0 = L.in[0][la], l1 = L.in[1][la], l2 = L.in[2][la], l3 = L.in[3][la], l4 = L.in[4][la];
+    P.out[0][b] = l0 + u * l1 + v * l2 + w * l3 + S(0.5) * ((u * u + v * v) + w * w) * l4;
+    P.out[1][b] = r * l1 + r * u * l4;
+    P.out[2][b] = r * l2 + r * v * l4;
+    P.out[3][b] = r * l3 + r * w * l4;
+    P.out[4][b] = igm1 * l4;
+  }
+}
+
+template <class Pol>
+cudaError_t launch_p2c(const HostPatchIO& W, void* const U[5], const Params& prm, cudaStream_t s) {
+  HostPatchIO h = W;
+  for (int v = 0; v < 5; ++v) h.out[v] = U[v];
+  k_p2c<typename Pol::S><<<152 * 8, 256, 0, s>>>(to_dev<Pol>(h), prm.gamma);
+  return cudaGetLastError();
+}
+
+template <class Pol>
+cudaError_t launch_p2c_adjoint(const HostPatchIO& W, const HostPatchIO& lamU, void* const lamW[5], const Params& prm,
+                               cudaStream_t s) {
+  HostPatchIO h = W;
+  for (int v = 0; v < 5; ++v) h.out[v] = lamW[v];
+  k_p2c_adjoint<typename Pol::S><<<152 * 8, 256, 0, s>>>(to_dev<Pol>(h), to_dev<Pol>(lamU), prm.gamma);
+  return cudaGetLastError();
+}
+
+template <class Pol>
+const KernelOps& make_ops() {
+  static const KernelOps ops = {
+      &launch_uniform<Pol>,      &launch_batched<Pol>,      &batched_blocks_per_sm<Pol>,
+      &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_adjoint<Pol>,
+      &adjoint_scratch_bytes<Pol>, &launch_p2c<Pol>,        &launch_p2c_adjoint<Pol>,
+      (int)sizeof(typename Pol::S), 1};
+  return ops;
+}
+
+}  // namespace hydro

@@ -1,0 +1,329 @@
+// One MUSCL-Hancock/HLLC step of a TX x TY column tile of a patch, marching in z through
+// shared memory (the GPU solves hydro on chunks of patches carrying their boundary cells,
+// Sec. 3; every flux that updates a patch's cells is computed on the GPU, Sec. 4).
+//
+// Per plane p of the march (p = z0-1 .. z1), with a 3-plane ring of primitive planes:
+//   A  load U of plane p+1 over the tile plus 2 halo cells per side, recover q -> ring
+//   B  slopes (x, y, z) and Hancock predictor of plane p over the tile plus a 1-cell ring;
+//      each interior column also forms its z face states and the HLLC flux of face p-1/2
+//   C  HLLC fluxes of the x and y faces of plane p (each face once)
+//   D  each interior column updates plane p-1:  U - dt/dx ((dFx + dFy) + dFz), writes it, and
+//      folds the CFL speed of the new state into a running maximum
+// Global memory is read once per cell per plane (halo re-reads come from L2) and written once.
+#pragma once
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+// Device view of one (input, output) patch pair.
+template <class S>
+struct PatchIO {
+  const S* in[5];
+  S* out[5];
+  int nx, ny, nz;
+  int gin, gout;  // ghost layers of in / out; gin == 0 means a periodic box
+  long long isy, isz, osy, osz;
+  double dx;
+};
+
+// One tile of the work-list: columns [x0, x0+TX) x [y0, y0+TY), planes [z0, min(z0+zchunk, nz)).
+struct TileRec {
+  int patch, x0, y0, z0;
+};
+
+template <class Pol, int TX, int TY>
+struct TileShared {
+  using R = typename Pol::R;
+  R q[3][5][TY + 4][TX + 4];  // primitive planes p-1, p, p+1 (ring)
+  R qh[5][TY + 2][TX + 2];    // predicted state of plane p (tile + 1 ring)
+  R sx[5][TY + 2][TX + 2];    // x slopes of plane p
+  R sy[5][TY + 2][TX + 2];    // y slopes of plane p
+  R fx[5][TY][TX + 1];        // x-face fluxes of plane p, index i+1 for face i+1/2
+  R fy[5][TY + 1][TX];        // y-face fluxes of plane p, index j+1 for face j+1/2
+  long long yoff[TY + 4];     // y offset (y index * stride) of the halo rows
+  int xoff[TX + 4];           // x index of the halo columns
+  R red[TX * TY / 32];
+  int tile;
+};
+
+__device__ __forceinline__ int wrapi(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+__device__ __forceinline__ int ring_slot(int p) { return (p + 3) % 3; }
+
+template <class Pol, int TX, int TY>
+__device__ __forceinline__ void predict_cell(TileShared<Pol, TX, TY>& sm, int i, int j, int sm1, int s0, int sp1,
+                                             const Params& prm, typename Pol::R hdt, typename Pol::R qh[5],
+                                             typename Pol::R dqz[5]) {
+  using R = typename Pol::R;
+  const int ci = i + 2, cj = j + 2;
+  R q0[5], dqx[5], dqy[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const R c = sm.q[s0][v][cj][ci];
+    q0[v] = c;
+    dqx[v] = limited(c - sm.q[s0][v][cj][ci - 1], sm.q[s0][v][cj][ci + 1] - c, prm.limiter);
+    dqy[v] = limited(c - sm.q[s0][v][cj - 1][ci], sm.q[s0][v][cj + 1][ci] - c, prm.limiter);
+    dqz[v] = limited(c - sm.q[sm1][v][cj][ci], sm.q[sp1][v][cj][ci] - c, prm.limiter);
+  }
+  hancock(q0, dqx, dqy, dqz, (R)prm.gamma, hdt, qh);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    sm.qh[v][j + 1][i + 1] = qh[v];
+    sm.sx[v][j + 1][i + 1] = dqx[v];
+    sm.sy[v][j + 1][i + 1] = dqy[v];
+  }
+}
+
+// Flux of the x face between tile cells (i, j) and (i+1, j) (D = 0) or the y face between
+// (i, j) and (i, j+1) (D = 1), from the predicted states and slopes of plane p.
+template <int D, class Pol, int TX, int TY>
+__device__ __forceinline__ void face_flux(TileShared<Pol, TX, TY>& sm, int i, int j, const Params& prm,
+                                          typename Pol::R F[5]) {
+  using R = typename Pol::R;
+  const int li = i + 1, lj = j + 1;
+  const int ri = li + (D == 0), rj = lj + (D == 1);
+  R qL[5], qR[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const R sL = (D == 0) ? sm.sx[v][lj][li] : sm.sy[v][lj][li];
+    const R sR = (D == 0) ? sm.sx[v][rj][ri] : sm.sy[v][rj][ri];
+    qL[v] = sm.qh[v][lj][li] + R(0.5) * sL;
+    qR[v] = sm.qh[v][rj][ri] - R(0.5) * sR;
+  }
+  floor_state(qL, (R)prm.rho_floor, (R)prm.p_floor);
+  floor_state(qR, (R)prm.rho_floor, (R)prm.p_floor);
+  hllc<D>(qL, qR, (R)prm.gamma, (R)(1.0 / (prm.gamma - 1.0)), F);
+}
+
+// Advances the tile; returns (through smax) the largest CFL speed of the updated cells.
+template <class Pol, int TX, int TY>
+__device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Pol::S>& P, int x0, int y0, int z0,
+                          int z1, const Params& prm, double dt, bool want_cfl, unsigned& flags,
+                          typename Pol::R& smax) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  constexpr int NT = TX * TY;
+  constexpr int QW = TX + 4, QH = TY + 4, QN = QW * QH;
+  const int tid = threadIdx.x;
+  const int ti = tid % TX, tj = tid / TX;
+  const bool periodic = (P.gin == 0);
+
+  for (int c = tid; c < QW; c += NT) {
+    int x = x0 - 2 + c;
+    sm.xoff[c] = periodic ? wrapi(x, P.nx) : min(max(x, -2), P.nx + 1) + 2;
+  }
+  for (int c = tid; c < QH; c += NT) {
+    int y = y0 - 2 + c;
+    y = periodic ? wrapi(y, P.ny) : min(max(y, -2), P.ny + 1) + 2;
+    sm.yoff[c] = (long long)y * P.isy;
+  }
+  __syncthreads();
+
+  auto load_plane = [&](int z) {
+    const int slot = ring_slot(z);
+    const int zi = periodic ? wrapi(z, P.nz) : z + 2;
+    const long long zo = (long long)zi * P.isz;
+    for (int c = tid; c < QN; c += NT) {
+      const int cy = c / QW, cx = c - cy * QW;
+      const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
+      S U[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = __ldg(P.in[v] + a);
+      R q[5];
+      Pol::recover(U, prm, q, flags);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.q[slot][v][cy][cx] = q[v];
+    }
+  };
+
+  const R hdt = (R)(0.5 * dt / P.dx);
+  const auto dtdx = (decltype(Pol::update(S(0), R(0), R(0))))0 + (R)(dt / P.dx);
+  const int gx = x0 + ti, gy = y0 + tj;
+  const bool own = (gx < P.nx) && (gy < P.ny);
+  const R gamma = (R)prm.gamma;
+
+  R LzPrev[5], FzPrev[5], dFprev[5], Fz[5], dF[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { LzPrev[v] = FzPrev[v] = dFprev[v] = Fz[v] = dF[v] = R(0); }
+
+  load_plane(z0 - 2);
+  load_plane(z0 - 1);
+  for (int p = z0 - 1; p <= z1; ++p) {
+    // ---- A
+    load_plane(p + 1);
+    __syncthreads();
+    // ---- B
+    const int sm1 = ring_slot(p - 1), s0 = ring_slot(p), sp1 = ring_slot(p + 1);
+    {
+      R qh[5], dqz[5];
+      predict_cell(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
+      R Lz[5], Rz[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        Lz[v] = qh[v] + R(0.5) * dqz[v];
+        Rz[v] = qh[v] - R(0.5) * dqz[v];
+      }
+      floor_state(Lz, (R)prm.rho_floor, (R)prm.p_floor);
+      floor_state(Rz, (R)prm.rho_floor, (R)prm.p_floor);
+      if (p >= z0) hllc<2>(LzPrev, Rz, gamma, (R)(1.0 / (prm.gamma - 1.0)), Fz);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) LzPrev[v] = Lz[v];
+    }
+    if (p >= z0 && p < z1 && tid < 2 * (TX + TY)) {
+      int ri, rj;
+      const int r = tid;
+      if (r < TX) { ri = r; rj = -1; }
+      else if (r < 2 * TX) { ri = r - TX; rj = TY; }
+      else if (r < 2 * TX + TY) { ri = -1; rj = r - 2 * TX; }
+      else { ri = TX; rj = r - 2 * TX - TY; }
+      R qh[5], dqz[5];
+      predict_cell(sm, ri, rj, sm1, s0, sp1, prm, hdt, qh, dqz);
+    }
+    __syncthreads();
+    // ---- C
+    if (p >= z0 && p < z1) {
+      R F[5];
+      face_flux<0>(sm, ti, tj, prm, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.fx[v][tj][ti + 1] = F[v];
+      face_flux<1>(sm, ti, tj, prm, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.fy[v][tj + 1][ti] = F[v];
+      if (tid < TY) {
+        face_flux<0>(sm, -1, tid, prm, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sm.fx[v][tid][0] = F[v];
+      } else if (tid >= 32 && tid < 32 + TX) {
+        face_flux<1>(sm, tid - 32, -1, prm, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sm.fy[v][0][tid - 32] = F[v];
+      }
+    }
+    __syncthreads();
+    // ---- D
+    if (p >= z0 && p < z1) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        dF[v] = (sm.fx[v][tj][ti + 1] - sm.fx[v][tj][ti]) + (sm.fy[v][tj + 1][ti] - sm.fy[v][tj][ti]);
+    }
+    if (p >= z0 + 1 && own) {
+      const int k = p - 1;
+      const long long ai = (long long)(k + P.gin) * P.isz + (long long)(gy + P.gin) * P.isy + (gx + P.gin);
+      const long long ao = (long long)(k + P.gout) * P.osz + (long long)(gy + P.gout) * P.osy + (gx + P.gout);
+      S Un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R div = dFprev[v] + (Fz[v] - FzPrev[v]);
+        Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, div);
+        P.out[v][ao] = Un[v];
+      }
+      if (want_cfl) {
+        R qn[5];
+        Pol::recover(Un, prm, qn, flags);
+        const R s = cfl_speed(qn, gamma);
+        smax = s > smax ? s : smax;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      FzPrev[v] = Fz[v];
+      dFprev[v] = dF[v];
+    }
+  }
+}
+
+// Block-wide maximum of v (all threads call); the result is valid in thread 0.
+template <class Pol, int TX, int TY>
+__device__ __forceinline__ typename Pol::R block_max(TileShared<Pol, TX, TY>& sm, typename Pol::R v) {
+  using R = typename Pol::R;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    R w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm.red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < TX * TY / 32; ++w) v = sm.red[w] > v ? sm.red[w] : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void flush_flags(unsigned flags, unsigned* err) {
+  const unsigned f = __reduce_or_sync(0xffffffffu, flags);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(err, f);
+}
+
+// dt of a tile from its largest speed; folded into the patch's slot by an order-preserving min.
+__device__ __forceinline__ void publish_dt(double cfl, double dx, double smax, double* slot) {
+  if (smax > 0.0) {
+    const double dt = cfl * (dx / smax);
+    atomicMin(reinterpret_cast<unsigned long long*>(slot), dkey(dt));
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+// Uniform grid: one tile per block, tiles from the block index.
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
+                                                         double* dt_next, int zchunk, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<TileShared<Pol, TX, TY>*>(smem_raw);
+  const double dt = dt_dev[0];
+  if (!(dt > 0.0 && dt <= 1e300)) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicOr(err, HYDRO_EBIT_BAD_DT);
+    return;
+  }
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, P.nz);
+  unsigned flags = 0;
+  typename Pol::R smax = 0;
+  step_tile(sm, P, x0, y0, z0, z1, prm, dt, dt_next != nullptr, flags, smax);
+  if (dt_next) {
+    const auto m = block_max(sm, smax);
+    if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next);
+  }
+  flush_flags(flags, err);
+}
+
+// Batched patches: a persistent grid pulls tiles from the work-list through an atomic counter.
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_step_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles,
+                                                         int ntiles, int* counter, Params prm, const double* dt_dev,
+                                                         double* dt_next, int zchunk, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<TileShared<Pol, TX, TY>*>(smem_raw);
+  unsigned flags = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) sm.tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = sm.tile;
+    if (t >= ntiles) break;
+    const TileRec r = tiles[t];
+    const PatchIO<typename Pol::S> P = patches[r.patch];
+    if (r.x0 < 0 || r.y0 < 0 || r.z0 < 0 || r.x0 >= P.nx || r.y0 >= P.ny || r.z0 >= P.nz) {
+      flags |= HYDRO_EBIT_BAD_TILE;
+      continue;
+    }
+    const double dt = dt_dev[r.patch];
+    if (!(dt > 0.0 && dt <= 1e300)) {
+      flags |= HYDRO_EBIT_BAD_DT;
+      continue;
+    }
+    const int z1 = min(r.z0 + zchunk, P.nz);
+    typename Pol::R smax = 0;
+    step_tile(sm, P, r.x0, r.y0, r.z0, z1, prm, dt, dt_next != nullptr, flags, smax);
+    if (dt_next) {
+      const auto m = block_max(sm, smax);
+      if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next + r.patch);
+    }
+  }
+  flush_flags(flags, err);
+}
+
+}  // namespace hydro

@@ -1,0 +1,244 @@
+"""GPU parity of the forward step (uniform periodic grid, ghosted patches, batched patches, oct
+groups, CFL dt) against the FP64 oracle, element by element on seeded inputs, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from hydro_testlib import cfl, check_clean, ctx, dev, dts, normwise, step_periodic
+
+import paper_1412_0934_gb300 as hy
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12  # FP64: relative (normwise per field) per step
+TOL32 = 1e-5  # FP32 / MIXED after one step
+
+
+def ocfg(limiter="minmod"):
+    return oracle.config(limiter=limiter)
+
+
+def _inputs(limiter, shape):
+    """TVD limiters: k^-4 turbulence with a Sedov cell, and white-noise velocities.  Unlimited
+    slopes: smooth data only (k^-4 turbulence without the blast, a 3D sound wave).  Unlimited
+    slopes across the blast or on white noise are ill-conditioned -- the oracle itself moves by
+    ~1e-12 under a 1-ulp input perturbation there (test_oracle_conditioning.py)."""
+    if limiter == "none":
+        wave, _ = workloads.sound_wave(shape, amp=0.1, kvec=(1, 1, 1), phase=0.3)
+        return [workloads.turbulent_state(shape, seed=2, mach=5.0, sedov=False).numpy(), wave.numpy()]
+    return [workloads.turbulent_state(shape, seed=2, mach=5.0, sedov=True).numpy(),
+            workloads.white_velocity_state(shape, seed=1).numpy()]
+
+
+@pytest.mark.parametrize("limiter", ["minmod", "mc", "none"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (9, 13, 20), (5, 3, 37)])
+def test_fp64_one_step_matches_oracle(limiter, shape):
+    dx = 1.0 / shape[2]
+    c = ctx("fp64", limiter)
+    for U in _inputs(limiter, shape):
+        dt = oracle.cfl_periodic(U, dx, ocfg(limiter))
+        o = oracle.step_periodic(U, dx, dt, ocfg(limiter))
+        for tile in range(3):
+            hy.hydro_set_tuning(c, tile, 8)
+            g, _ = step_periodic(c, U, dx, dt)
+            assert normwise(g, o).max() <= TOL64, (tile, normwise(g, o))
+    check_clean(c)
+
+
+def test_fp64_cfl_matches_oracle_and_fused_is_bitwise():
+    U = workloads.white_velocity_state((20, 24, 28), seed=3).numpy()
+    dx = 1.0 / 28
+    c = ctx("fp64")
+    d_gpu = cfl(c, U, dx)
+    assert d_gpu == pytest.approx(oracle.cfl_periodic(U, dx, ocfg()), rel=1e-14)
+    # the fused epilogue of a step on U0 gives the dt of U1; the standalone kernel on U1 the same bits
+    U1, dnext = step_periodic(c, U, dx, 0.5 * d_gpu, dt_next=True)
+    assert dnext == cfl(c, U1, dx)
+    check_clean(c)
+
+
+def test_fp64_ten_steps_config1():
+    """32^3, lognormal density (sigma 0.5), white velocities (0.3 c_s), P = 1, MinMod, CFL 0.8:
+    ten steps with each side taking its own CFL dt."""
+    U0 = workloads.white_velocity_state(32, seed=1).numpy()
+    dx = 1.0 / 32
+    c = ctx("fp64")
+    a = dev(U0)
+    b = torch.empty_like(a)
+    hist = torch.empty(11, dtype=torch.float64, device="cuda")
+    hy.hydro_run(c, hy.patch(a, 0, dx), hy.patch(b, 0, dx), 10, hist, use_graph=False)
+    torch.cuda.synchronize()
+    g = a.cpu().numpy()  # 10 steps: result back in a
+    o, odts = oracle.run_periodic(U0, dx, 10, ocfg())
+    np.testing.assert_allclose(hist.cpu().numpy()[:10], odts, rtol=1e-12)
+    assert normwise(g, o).max() <= 10 * TOL64
+    check_clean(c)
+
+
+def test_graph_run_matches_eager_run_bitwise():
+    U0 = workloads.turbulent_state(24, seed=2, mach=5.0, sedov=True).numpy()
+    dx = 1.0 / 24
+    res = []
+    for graph in (False, True, True):
+        c = ctx("fp64")
+        a = dev(U0)
+        b = torch.empty_like(a)
+        hist = torch.empty(8, dtype=torch.float64, device="cuda")
+        hy.hydro_run(c, hy.patch(a, 0, dx), hy.patch(b, 0, dx), 7, hist, use_graph=graph)
+        torch.cuda.synchronize()
+        res.append((b.cpu().numpy(), hist.cpu().numpy()))
+        check_clean(c)
+    for r in res[1:]:
+        np.testing.assert_array_equal(r[0], res[0][0])
+        np.testing.assert_array_equal(r[1], res[0][1])
+
+
+def test_ghosted_patch_equals_periodic_box():
+    U = workloads.white_velocity_state((12, 16, 20), seed=4).numpy()
+    dx = 1.0 / 20
+    dt = 0.5 * oracle.cfl_periodic(U, dx, ocfg())
+    Ug = oracle.fill_ghosts_periodic(U)
+    c = ctx("fp64")
+    a = dev(Ug)
+    out = torch.zeros_like(a)
+    hy.hydro_step(c, hy.patch(a, 2, dx), hy.patch(out, 2, dx), dts(dt))
+    torch.cuda.synchronize()
+    g = out[:, 2:-2, 2:-2, 2:-2].cpu().numpy()
+    assert normwise(g, oracle.step_patch(Ug, dx, dt, ocfg())).max() <= TOL64
+    # ghost layers of the output are untouched
+    assert float(out[:, :2].abs().max()) == 0.0
+    check_clean(c)
+
+
+def _patch_batch(npatch, seed, precision, dtype, edges=(4, 8, 12, 16, 24), max_level=3):
+    parent = workloads.turbulent_state(32, seed=seed, mach=5.0, sedov=False)
+    descs = workloads.patch_set(npatch, seed=seed, edges=edges, max_level=max_level)
+    origins = workloads.patch_origins(descs, parent.shape[1:], seed=seed)
+    ins, outs, host = [], [], []
+    for d, o in zip(descs, origins):
+        Ug = workloads.ghosted_from_periodic(parent, o, (d["nx"], d["ny"], d["nz"])).numpy()
+        host.append((Ug, d))
+        t = dev(Ug, dtype)
+        ins.append(hy.patch(t, 2, d["dx"], d["level"]))
+        outs.append(hy.patch(torch.zeros_like(t), 2, d["dx"], d["level"]))
+    return host, ins, outs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+def test_batched_patches_match_oracle(precision):
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    host, ins, outs = _patch_batch(24, 5, precision, dtype)
+    c = ctx(precision)
+    dt_list = [0.7 * oracle.cfl_patch(Ug, d["dx"], ocfg()) for Ug, d in host]
+    dt = dts(*dt_list)
+    dn = torch.empty(len(host), dtype=torch.float64, device="cuda")
+    for tile in (0, 2):
+        hy.hydro_set_tuning(c, tile, 8)
+        hy.hydro_step(c, ins, outs, dt, dn)
+        torch.cuda.synchronize()
+        tol = TOL64 if precision == "fp64" else TOL32
+        for (Ug, d), po, dtp in zip(host, outs, dt_list):
+            out = torch.stack(po.tensors).double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
+            o = oracle.step_patch(Ug, d["dx"], dtp, ocfg())
+            assert normwise(out, o).max() <= tol, (precision, tile, d, normwise(out, o))
+    # per-patch dt of U^{n+1}: fused and standalone agree bitwise
+    dn2 = torch.empty_like(dn)
+    hy.hydro_cfl_dt(c, outs, dn2)
+    torch.cuda.synchronize()
+    assert torch.equal(dn, dn2)
+    check_clean(c)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("limiter", ["minmod", "mc"])
+def test_reduced_precision_one_step(precision, limiter):
+    """FP32 state rounded from the FP64 initial state, one step, vs the FP64 oracle."""
+    U = workloads.turbulent_state(32, seed=2, mach=5.0, sedov=True).numpy()
+    dx = 1.0 / 32
+    dt = oracle.cfl_periodic(U, dx, ocfg(limiter))
+    c = ctx(precision, limiter)
+    Uin = U.astype(np.float32).astype(np.float64) if precision == "fp32" else U
+    g, _ = step_periodic(c, Uin, dx, dt)
+    o = oracle.step_periodic(U, dx, dt, ocfg(limiter))
+    assert normwise(g, o).max() <= TOL32, normwise(g, o)
+    check_clean(c)
+
+
+def test_fp32_conservation_100_steps():
+    U0 = workloads.turbulent_state(32, seed=2, mach=5.0, sedov=False).numpy()
+    dx = 1.0 / 32
+    c = ctx("fp32")
+    a = dev(U0, torch.float32)
+    b = torch.empty_like(a)
+    tot0 = a.double().sum(dim=(1, 2, 3))
+    scale = a.double().abs().sum(dim=(1, 2, 3))
+    hist = torch.empty(101, dtype=torch.float64, device="cuda")
+    hy.hydro_run(c, hy.patch(a, 0, dx), hy.patch(b, 0, dx), 100, hist)
+    torch.cuda.synchronize()
+    tot = a.double().sum(dim=(1, 2, 3))
+    rel = ((tot - tot0).abs() / scale).max().item()
+    assert rel <= 1e-6, rel
+    check_clean(c)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+def test_octs_match_oracle_and_uniform_grid(precision):
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    parent = workloads.white_velocity_state(16, seed=6)
+    dx = 1.0 / 16
+    U = parent.numpy()
+    dt = 0.6 * oracle.cfl_periodic(U, dx, ocfg())
+    origins = workloads.oct_origins(37, parent.shape[1:], seed=6)
+    gathered = workloads.gather_octs(parent, origins)  # (5, G, 6, 6, 6)
+    c = ctx(precision)
+    gd = gathered.to(device="cuda", dtype=dtype).contiguous()
+    od = torch.zeros((5, gd.shape[1], 2, 2, 2), dtype=dtype, device="cuda")
+    hy.hydro_step_octs(c, gd, od, dx, dts(dt))
+    torch.cuda.synchronize()
+    full = oracle.step_periodic(U, dx, dt, ocfg())
+    tol = 1e-13 if precision == "fp64" else TOL32
+    g = od.double().cpu().numpy()
+    for k, (ox, oy, oz) in enumerate(origins):
+        o = full[:, oz:oz + 2, oy:oy + 2, ox:ox + 2]
+        err = np.abs(g[:, k] - o).max(axis=(1, 2, 3)) / np.abs(full).max(axis=(1, 2, 3))
+        assert err.max() <= tol, (k, err)
+    check_clean(c)
+
+
+def test_error_word_flags_and_argument_errors():
+    U = workloads.white_velocity_state(8, seed=1).numpy()
+    c = ctx("fp64")
+    a = dev(U)
+    b = torch.empty_like(a)
+    # dt <= 0: flagged on the device, nothing written
+    hy.hydro_step(c, hy.patch(a, 0, 0.1), hy.patch(b, 0, 0.1), dts(0.0))
+    rc, bits = hy.hydro_get_error(c)
+    assert rc == hy.HYDRO_ERR_UNPHYSICAL and bits & hy.EBIT_BAD_DT
+    hy.hydro_clear_error(c)
+    check_clean(c)
+    # a non-finite cell is flagged
+    a[0, 3, 3, 3] = float("nan")
+    hy.hydro_step(c, hy.patch(a, 0, 0.1), hy.patch(b, 0, 0.1), dts(1e-3))
+    rc, bits = hy.hydro_get_error(c)
+    assert bits & hy.EBIT_NONFINITE
+    hy.hydro_clear_error(c)
+    # negative internal energy is flagged (and floored)
+    a = dev(U)
+    a[4, 2, 2, 2] = 0.0
+    hy.hydro_step(c, hy.patch(a, 0, 0.1), hy.patch(b, 0, 0.1), dts(1e-3))
+    rc, bits = hy.hydro_get_error(c)
+    assert bits & hy.EBIT_P_FLOOR
+    hy.hydro_clear_error(c)
+    # host-side argument errors: aliasing, bad ghost width, wrong strides
+    with pytest.raises(hy.HydroError) as e:
+        hy.hydro_step(c, hy.patch(a, 0, 0.1), hy.patch(a, 0, 0.1), dts(1e-3))
+    assert e.value.status == hy.HYDRO_ERR_ARG
+    with pytest.raises(hy.HydroError):
+        hy.hydro_step(c, hy.patch(a, 1, 0.1), hy.patch(b, 1, 0.1), dts(1e-3))
+    with pytest.raises(hy.HydroError):
+        hy.hydro_step(c, hy.patch(a, 0, -0.1), hy.patch(b, 0, -0.1), dts(1e-3))
+    with pytest.raises(hy.HydroError):  # FP32 context given FP64 data of odd alignment is fine; a bad dx is not
+        hy.hydro_cfl_dt(c, hy.patch(a, 0, 0.0), dts(0.0))
+    check_clean(c)
