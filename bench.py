@@ -172,6 +172,15 @@ def turbulent(n, precision, device, seed=2, mach=5.0, sigma=1.0, p_over_rho=1e-4
     return U.contiguous()
 
 
+def tune(hy, ctx, a, b, dx, dts):
+    """Autotune tile shape and z-chunk on this machine (writes b), then restore dts[0]."""
+    pa, pb = hy.patch(a, 0, dx), hy.patch(b, 0, dx)
+    hy.hydro_cfl_dt(ctx, pa, dts[0:1])
+    hy.hydro_autotune(ctx, pa, pb, dts[0:1])
+    t, z = hy.hydro_get_tuning(ctx)
+    return {"tile": "%dx%d" % ({0: (16, 16), 1: (32, 8), 2: (8, 8), 3: (32, 16)}[t]), "zchunk": z}
+
+
 def time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream, per_launch=True):
     """warmup + steps ping-pong steps with device-resident dt; returns (ms total, per-launch ms list,
     final state tensor, launches in the timed region)."""
@@ -256,11 +265,12 @@ def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, 
                "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "graph": True, "error_bits": bits}
     else:
         dts = torch.empty(warmup + steps + 1, dtype=torch.float64, device="cuda")
+        tuning = tune(hy, ctx, a, b, dx, dts)
         ms, per, _, launches = time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream)
         rc, bits = hy.hydro_get_error(ctx)
         hbm, src = peaks()
         out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
-               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "error_bits": bits,
+               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "error_bits": bits, "tuning": tuning,
                "roofline": roofline(precision, cells, per, ALG_FLOPS_PER_CELL[flops_key], hbm, src, None)}
     del a, b
     hy.hydro_finalize(ctx)
@@ -469,6 +479,7 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    tuning = tune(hy, ctx, a, b, dx, dts)
     barrier()
     with ClockSampler(local) as clk:
         ms, per, final, launches = time_steps(hy, ctx, a, b, dx, dts, args.steps, args.warmup, stream)
@@ -520,7 +531,7 @@ def main():
                                    "%s; dt from the fused CFL of each step" % (n, precision.upper()),
                        "cells": cells, "state_bytes": 5 * cells * esz,
                        "l2": "inputs larger than L2 (state %.1f GB vs 129 MB L2); no flush" % (5 * cells * esz / 1e9),
-                       "parallelism": "replicas x%d" % world},
+                       "parallelism": "replicas x%d" % world, "tuning": tuning},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "device_error_bits": bits}
 
@@ -547,7 +558,8 @@ def main():
             except Exception as e:  # a failing extra form is reported, not fatal
                 extra[f] = {"error": repr(e)[:300]}
         line["forms"] = extra
-        line["cpu_baseline"] = cpu_baseline(128, args.cpu_seconds)
+        if args.cpu_seconds > 0:
+            line["cpu_baseline"] = cpu_baseline(128, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -6,8 +6,8 @@
  *
  * What the calls compute follows the paper's description of the hydro path: the baryonic
  * component is an ideal fluid governed by the Euler equations, solved with PLM among other
- * methods (Sec. 2); "all fluxes necessary to update the patch's cells are computed on the GPU"
- * and the adaptive time step (Sec. 4, Enzo); hydro solved on chunks of patches that carry their
+ * methods (Sec. 2); the GPU computes every flux that updates a patch's cells, with an adaptive
+ * time step (Sec. 4, Enzo); hydro solved on chunks of patches that carry their
  * boundary cells (Sec. 3, Ramses GPU procedure); the N_v x 6^3 gathered cell buffer (Sec. 3).
  * The paper prints no equations; the scheme is the textbook one, with these readings: primitive
  * reconstruction; MinMod / MC / unlimited slopes; unsplit primitive Hancock predictor summed over

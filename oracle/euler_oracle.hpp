@@ -4,7 +4,7 @@
 // What it computes: the Euler equations of an ideal fluid on the mesh (paper Sec. 2, where the
 // baryonic component is an ideal fluid and the Euler equations are solved with PLM among other
 // methods, the PLM reference being Colella & Glaz 1985); the fluxes that update a patch's cells
-// (Sec. 4, Enzo: all fluxes needed to update the patch's cells are computed on the GPU); and the
+// (Sec. 4, Enzo: the GPU computes every flux that updates a patch's cells); and the
 // adaptive time step (Sec. 2 and Sec. 4).  The paper prints no equations, so each step below is
 // the textbook method (Toro, "Riemann Solvers and Numerical Methods for Fluid Dynamics":
 // MUSCL-Hancock in primitive variables, HLLC of Toro, Spruce & Speares with the star states of

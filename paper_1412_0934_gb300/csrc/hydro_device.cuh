@@ -25,10 +25,22 @@ template <class R>
 __device__ __forceinline__ R rabs(R x) {
   return x < R(0) ? -x : x;
 }
-__device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+// Float policies use the SFU approximations (relative error a few ulp of float); double uses
+// correctly rounded IEEE operations.
+__device__ __forceinline__ float rcp_(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
 __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
 
 // Order-preserving 64-bit key of a non-negative double (IEEE bits compare as unsigned ints).
 __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned long long)__double_as_longlong(x); }
@@ -104,7 +116,7 @@ __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R
   const R SR = aR >= bR ? aR : bR;
   const R mL = qL[0] * (SL - uL);
   const R mR = qR[0] * (SR - uR);
-  const R Ss = (qR[4] - qL[4] + uL * mL - uR * mR) / (mL - mR);
+  const R Ss = div_(qR[4] - qL[4] + uL * mL - uR * mR, mL - mR);
   const bool star = (SL < R(0)) && (SR > R(0));
   const bool left = (SL >= R(0)) || (SR > R(0) && Ss >= R(0));
   const R rK = left ? qL[0] : qR[0];
@@ -117,27 +129,22 @@ __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R
   const R SK = left ? SL : SR;
   const R mK = left ? mL : mR;
   const R EK = pK * inv_gm1 + R(0.5) * rK * keK;
-  const R mn = rK * uK;
-  R FK[5], UK[5];
-  FK[0] = mn;
-  FK[1] = mn * uK + pK;
-  FK[2] = mn * t1;
-  FK[3] = mn * t2;
-  FK[4] = uK * (EK + pK);
-  UK[0] = rK;
-  UK[1] = mn;
-  UK[2] = rK * t1;
-  UK[3] = rK * t2;
-  UK[4] = EK;
-  const R fac = mK / (SK - Ss);
-  R Us[5];
-  Us[0] = fac;
-  Us[1] = fac * Ss;
-  Us[2] = fac * t1;
-  Us[3] = fac * t2;
-  Us[4] = fac * (EK * irK + (Ss - uK) * (Ss + pK / mK));
-#pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = star ? FK[v] + SK * (Us[v] - UK[v]) : FK[v];
+  // Star state of side K: density r* = m_K/(S_K - S*), velocity S*, pressure p* = p_K + m_K (S* - u_K),
+  // energy E* = r* (E_K/rho_K + (S* - u_K)(S* + p_K/m_K)).  F*_K = F_K + S_K (U*_K - U_K) equals the
+  // physical flux of that state, so one flux formula serves every branch.
+  const R rs = div_(mK, SK - Ss);
+  const R ps = pK + mK * (Ss - uK);
+  const R Es = rs * (EK * irK + (Ss - uK) * (Ss + div_(pK, mK)));
+  const R re = star ? rs : rK;
+  const R ue = star ? Ss : uK;
+  const R pe = star ? ps : pK;
+  const R Ee = star ? Es : EK;
+  const R mn = re * ue;
+  F[0] = mn;
+  F[1] = mn * ue + pe;
+  F[2] = mn * t1;
+  F[3] = mn * t2;
+  F[4] = ue * (Ee + pe);
 }
 
 template <class R>
@@ -208,6 +215,7 @@ struct PolF64 {
     q[4] = p < P.p_floor ? P.p_floor : p;
   }
   static __device__ __forceinline__ double update(double Uold, double dtdx, double div) { return Uold - dtdx * div; }
+  static __device__ __forceinline__ double speed(const double U[5], const Params& P, unsigned& flags);
 };
 
 struct PolF32 {
@@ -249,6 +257,21 @@ struct PolF32 {
     q[4] = p < pf ? pf : p;
   }
   static __device__ __forceinline__ float update(float Uold, float dtdx, float div) { return Uold - dtdx * div; }
+  // CFL speed of a stored state: plain float recovery (the dt only needs float accuracy).
+  static __device__ __forceinline__ float speed(const float U[5], const Params& P, unsigned& flags) {
+    float rho = U[0];
+    const float rf = (float)P.rho_floor;
+    if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
+    const float ir = rcp_(rho);
+    const float u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const float eint = U[4] - 0.5f * rho * ((u * u + v * v) + w * w);
+    float p = (float)(P.gamma - 1.0) * eint;
+    if (!(isfinite(p) && isfinite(rho))) flags |= HYDRO_EBIT_NONFINITE;
+    const float pf = (float)P.p_floor;
+    p = p < pf ? pf : p;
+    const float c = rsqrt_((float)P.gamma * p * ir);
+    return ((fabsf(u) + fabsf(v)) + fabsf(w)) + 3.0f * c;
+  }
 };
 
 struct PolMixed {
@@ -279,6 +302,7 @@ struct PolMixed {
   static __device__ __forceinline__ double update(double Uold, float dtdx, float div) {
     return Uold - (double)(dtdx * div);
   }
+  static __device__ __forceinline__ float speed(const double U[5], const Params& P, unsigned& flags);
 };
 
 // CFL speed of a recovered state.
@@ -286,6 +310,19 @@ template <class R>
 __device__ __forceinline__ R cfl_speed(const R q[5], R gamma) {
   const R c = rsqrt_(gamma * q[4] * rcp_(q[0]));
   return ((rabs(q[1]) + rabs(q[2])) + rabs(q[3])) + R(3) * c;
+}
+
+// CFL speed of a stored state (the step's epilogue and the standalone dt kernel share it, so
+// both produce the same bits): FP64 and mixed through their recovery, FP32 through a plain one.
+__device__ __forceinline__ double PolF64::speed(const double U[5], const Params& P, unsigned& flags) {
+  double q[5];
+  recover(U, P, q, flags);
+  return cfl_speed(q, P.gamma);
+}
+__device__ __forceinline__ float PolMixed::speed(const double U[5], const Params& P, unsigned& flags) {
+  float q[5];
+  recover(U, P, q, flags);
+  return cfl_speed(q, (float)P.gamma);
 }
 
 }  // namespace hydro

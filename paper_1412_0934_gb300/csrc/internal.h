@@ -23,9 +23,9 @@ struct HostTileRec {
 };
 
 // Compiled tile shapes of the step kernels (TX x TY columns per block).
-constexpr int kNumTiles = 3;
-constexpr int kTileX[kNumTiles] = {16, 32, 8};
-constexpr int kTileY[kNumTiles] = {16, 8, 8};
+constexpr int kNumTiles = 4;
+constexpr int kTileX[kNumTiles] = {16, 32, 8, 32};
+constexpr int kTileY[kNumTiles] = {16, 8, 8, 16};
 
 struct KernelOps {
   // Uniform periodic grid (npatch == 1, gin == 0).

@@ -61,6 +61,7 @@ cudaError_t launch_uniform(int tile, const HostPatchIO& P, const Params& prm, co
     case 0: return launch_uniform_t<Pol, kTileX[0], kTileY[0]>(P, prm, dt, dt_next, zchunk, err, s);
     case 1: return launch_uniform_t<Pol, kTileX[1], kTileY[1]>(P, prm, dt, dt_next, zchunk, err, s);
     case 2: return launch_uniform_t<Pol, kTileX[2], kTileY[2]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 3: return launch_uniform_t<Pol, kTileX[3], kTileY[3]>(P, prm, dt, dt_next, zchunk, err, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -73,6 +74,7 @@ cudaError_t launch_batched(int tile, const HostPatchIO* d_patches, const HostTil
     case 0: return launch_batched_t<Pol, kTileX[0], kTileY[0]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
     case 1: return launch_batched_t<Pol, kTileX[1], kTileY[1]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
     case 2: return launch_batched_t<Pol, kTileX[2], kTileY[2]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 3: return launch_batched_t<Pol, kTileX[3], kTileY[3]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -83,6 +85,7 @@ int batched_blocks_per_sm(int tile) {
     case 0: return blocks_per_sm_t<Pol, kTileX[0], kTileY[0]>();
     case 1: return blocks_per_sm_t<Pol, kTileX[1], kTileY[1]>();
     case 2: return blocks_per_sm_t<Pol, kTileX[2], kTileY[2]>();
+    case 3: return blocks_per_sm_t<Pol, kTileX[3], kTileY[3]>();
   }
   return 1;
 }
@@ -111,9 +114,7 @@ __global__ void __launch_bounds__(256) k_cfl(const PatchIO<typename Pol::S>* pat
       S U[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) U[v] = __ldg(P.in[v] + a);
-      R q[5];
-      Pol::recover(U, prm, q, flags);
-      const R sp = cfl_speed(q, (R)prm.gamma);
+      const R sp = Pol::speed(U, prm, flags);
       smax = sp > smax ? sp : smax;
     }
 #pragma unroll

@@ -139,7 +139,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
   };
 
   const R hdt = (R)(0.5 * dt / P.dx);
-  const auto dtdx = (decltype(Pol::update(S(0), R(0), R(0))))0 + (R)(dt / P.dx);
+  const R dtdx = (R)(dt / P.dx);
   const int gx = x0 + ti, gy = y0 + tj;
   const bool own = (gx < P.nx) && (gy < P.ny);
   const R gamma = (R)prm.gamma;
@@ -220,9 +220,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
         P.out[v][ao] = Un[v];
       }
       if (want_cfl) {
-        R qn[5];
-        Pol::recover(Un, prm, qn, flags);
-        const R s = cfl_speed(qn, gamma);
+        const R s = Pol::speed(Un, prm, flags);
         smax = s > smax ? s : smax;
       }
     }

@@ -1,0 +1,32 @@
+"""The algorithmic flop counts per cell that bench.py divides by for its roofline, recomputed with
+the oracle's op-counting scalar type on a 64^3 sample of each benchmark workload."""
+import importlib.util
+import os
+
+import pytest
+
+import oracle
+import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def bench_module():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+@pytest.mark.parametrize("key,limiter,kw", [
+    ("turb_minmod", "minmod", dict(seed=2, mach=5.0, sigma_rho=1.0, p_over_rho=1e-4, sedov=True)),
+    ("turb_mc", "mc", dict(seed=2, mach=5.0, sigma_rho=1.0, p_over_rho=1e-4, sedov=True)),
+    ("mach10_mc", "mc", dict(seed=5, mach=10.0, sigma_rho=1.5, p_over_rho=1e-5, sedov=False)),
+])
+def test_flop_constants(key, limiter, kw):
+    b = bench_module()
+    U = workloads.turbulent_state(64, **kw).numpy()
+    cfg = oracle.config(limiter=limiter)
+    dt = oracle.cfl_periodic(U, 1 / 64, cfg)
+    c = oracle.count_ops(U, 1 / 64, dt, cfg)
+    assert c["per_cell"] == pytest.approx(b.ALG_FLOPS_PER_CELL[key], rel=0.01)

@@ -60,9 +60,11 @@ def powerlaw_velocity(shape, slope_power, gen, device):
     return out
 
 
-def white_velocity_state(n=32, seed=1, sigma_rho=0.5, p0=1.0, vel_frac=0.3, gamma=GAMMA, device="cpu"):
+def white_velocity_state(n=32, seed=1, sigma_rho=0.5, p0=1.0, vel_frac=0.3, gamma=GAMMA, p_jitter=0.0,
+                         device="cpu"):
     """Lognormal density (mean 1), white Gaussian velocities with sigma = vel_frac * c_s,
-    c_s = sqrt(gamma p0 / <rho>), mean removed, uniform pressure p0.  (The 32^3 FP64 case.)"""
+    c_s = sqrt(gamma p0 / <rho>), mean removed, uniform pressure p0 (the 32^3 FP64 case), or with
+    p_jitter > 0 a pressure p0 * exp(p_jitter g - p_jitter^2/2) per cell."""
     shape = (n, n, n) if isinstance(n, int) else tuple(n)
     gen = _gen(seed, device)
     rho = lognormal_density(shape, sigma_rho, gen, device)
@@ -72,6 +74,8 @@ def white_velocity_state(n=32, seed=1, sigma_rho=0.5, p0=1.0, vel_frac=0.3, gamm
         c = torch.randn(shape, generator=gen, device=device, dtype=torch.float64) * (vel_frac * cs)
         v.append(c - c.mean())
     p = torch.full(shape, p0, dtype=torch.float64, device=device)
+    if p_jitter > 0:
+        p = p * lognormal_density(shape, p_jitter, gen, device)
     return cons_from_prim(rho, v[0], v[1], v[2], p, gamma)
 
 
