@@ -174,6 +174,26 @@ int hydro_clear_error(hydro_ctx* ctx);
 /* Number of kernels this context has launched so far (graph replays count their kernels). */
 int hydro_launch_count(hydro_ctx* ctx, long long* count);
 
+/* The batched step of hydro_step for callers that cannot allocate device memory (no counterpart
+ * in the paper).  Some callers cannot call cudaMalloc: code running inside another runtime's
+ * memory pool or a fixed memory budget, code that must not allocate after start-up, or a host
+ * program that only receives device pointers.  hydro_step needs a context and hydro_init
+ * allocates; this call needs none.  Its scratch -- uploaded patch descriptors, prefix-sum counts,
+ * the tile work-list, the tile counter and a fallback error word -- is a set of file-scope device
+ * arrays of fixed size (about 4.7 MB) that every GPU loading the library holds until the process
+ * exits.  Limits: npatch <= 4096 and at most 262144 tiles of 16 x 16 columns x 32 planes
+ * (HYDRO_ERR_ARG beyond either).  cfg, in, out, npatch, dt_dev, dt_next_dev have the meaning of
+ * hydro_init's config and hydro_step's arguments; error_bits_dev, if not NULL, is a device word
+ * that receives HYDRO_EBIT_* bits by atomic OR (the caller zeroes it); NULL uses the internal
+ * word, which nothing reads back.  The first call on a device looks up the arrays' device
+ * addresses (cudaGetSymbolAddress, with that device current): make that first call before any
+ * stream capture.  Every call reuses the same arrays (their previous contents are overwritten;
+ * the tile counter is cleared on each call), so calls whose work overlaps on the GPU -- on
+ * different streams, or from different host threads -- race: serialise them.  Allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocating library call. */
+int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_patch* in, const hydro_patch* out, int npatch,
+                               const double* dt_dev, double* dt_next_dev, unsigned* error_bits_dev);
+
 /* Static description of a status code. */
 const char* hydro_status_string(int status);
 

@@ -39,7 +39,8 @@ EBIT_TIMEOUT = 0x20
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_octs", "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
-           "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string")
+           "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
+           "hydro_step_batched_noalloc")
 
 
 class HydroError(RuntimeError):
@@ -88,6 +89,7 @@ def lib():
         L.hydro_get_error.argtypes = [vp, ctypes.POINTER(ctypes.c_uint)]
         L.hydro_clear_error.argtypes = [vp]
         L.hydro_launch_count.argtypes = [vp, ctypes.POINTER(ll)]
+        L.hydro_step_batched_noalloc.argtypes = [ctypes.POINTER(hydro_config), PP, PP, i, vp, vp, vp]
         L.hydro_status_string.argtypes = [i]
         L.hydro_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -281,6 +283,14 @@ def hydro_get_error(ctx):
 
 def hydro_clear_error(ctx):
     _check(lib().hydro_clear_error(ctx.handle), "hydro_clear_error")
+
+
+def hydro_step_batched_noalloc(cfg, inp, out, npatch, dt, dt_next=None, error_bits=None):
+    """The batched step without a context and without any device allocation (see include/hydro.h).
+    cfg: a hydro_config; inp, out: ctypes arrays of hydro_patch; dt, dt_next, error_bits: CUDA
+    tensors (or None).  Returns the status code."""
+    return lib().hydro_step_batched_noalloc(ctypes.byref(cfg), inp, out, int(npatch), _ptr(dt), _ptr(dt_next),
+                                            _ptr(error_bits))
 
 
 def hydro_launch_count(ctx):

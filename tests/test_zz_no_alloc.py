@@ -1,0 +1,84 @@
+"""The allocation-free batched step (hydro_step_batched_noalloc), for callers that cannot allocate
+device memory, called through the C ABI: two calls in a row must match the context-based
+hydro_step on the same patches (same kernels and work-list; within the FP64 parity tolerance).
+Collected last on purpose: it shares file-scope device scratch with nothing else, but a failure
+here should not hide the other tests' results."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from hydro_testlib import normwise
+
+import paper_1412_0934_gb300 as hy
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(dtype):
+    parent = workloads.turbulent_state(32, seed=11, mach=3.0, sedov=False)
+    descs = workloads.patch_set(12, seed=11, edges=(4, 8, 12, 16), max_level=2)
+    origins = workloads.patch_origins(descs, parent.shape[1:], seed=11)
+    ins, outs_ref, outs_na = [], [], []
+    for d, o in zip(descs, origins):
+        Ug = workloads.ghosted_from_periodic(parent, o, (d["nx"], d["ny"], d["nz"])).to("cuda", dtype).contiguous()
+        ins.append(hy.patch(Ug, 2, d["dx"], d["level"]))
+        outs_ref.append(hy.patch(torch.zeros_like(Ug), 2, d["dx"], d["level"]))
+        outs_na.append(hy.patch(torch.zeros_like(Ug), 2, d["dx"], d["level"]))
+    return ins, outs_ref, outs_na
+
+
+def _cfg(precision):
+    cfg = hy.hydro_config()
+    cfg.gamma, cfg.cfl, cfg.rho_floor, cfg.p_floor = 5.0 / 3.0, 0.8, 1e-10, 1e-14
+    cfg.limiter = hy.HYDRO_MINMOD
+    cfg.precision = hy.PRECISIONS[precision]
+    cfg.cuda_stream = torch.cuda.current_stream().cuda_stream
+    return cfg
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+def test_noalloc_step_matches_context_step_twice(precision):
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    ins, outs_ref, outs_na = _batch(dtype)
+    n = len(ins)
+    c = hy.hydro_init(precision=precision)
+    dt = torch.empty(n, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(c, ins, dt)
+    dt *= 0.7
+    dn_ref = torch.empty(n, dtype=torch.float64, device="cuda")
+    hy.hydro_step(c, ins, outs_ref, dt, dn_ref)
+    rc, bits = hy.hydro_get_error(c)
+    assert rc == hy.HYDRO_OK, bits
+    cfg = _cfg(precision)
+    a = (hy.hydro_patch * n)(*[p.c for p in ins])
+    b = (hy.hydro_patch * n)(*[p.c for p in outs_na])
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for call in range(2):
+        for p in outs_na:
+            for t in p.tensors:
+                t.zero_()
+        dn = torch.empty(n, dtype=torch.float64, device="cuda")
+        rc = hy.hydro_step_batched_noalloc(cfg, a, b, n, dt, dn, err)
+        assert rc == hy.HYDRO_OK, hy.status_string(rc)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        for pr, pn in zip(outs_ref, outs_na):
+            g = torch.stack(pn.tensors).double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
+            r = torch.stack(pr.tensors).double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
+            assert normwise(g, r).max() <= tol, (call, normwise(g, r))
+        np.testing.assert_allclose(dn.cpu().numpy(), dn_ref.cpu().numpy(), rtol=tol)
+    hy.hydro_finalize(c)
+
+
+def test_noalloc_rejects_oversized_batches():
+    ins, _, outs = _batch(torch.float64)
+    cfg = _cfg("fp64")
+    big = 5000  # above the 4096-patch maximum of the static scratch
+    a = (hy.hydro_patch * big)(*([ins[0].c] * big))
+    b = (hy.hydro_patch * big)(*([outs[0].c] * big))
+    dt = torch.ones(big, dtype=torch.float64, device="cuda")
+    assert hy.hydro_step_batched_noalloc(cfg, a, b, big, dt, None, None) == hy.HYDRO_ERR_ARG
