@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
     p.add_argument("--forms", default="all", help="comma list of extra forms, 'all' or 'none'")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--tuning", default="auto", help="'auto' (autotune) or '<tile id>:<zchunk>'")
     return p.parse_args()
 
 
@@ -172,11 +173,18 @@ def turbulent(n, precision, device, seed=2, mach=5.0, sigma=1.0, p_over_rho=1e-4
     return U.contiguous()
 
 
+TUNING = "auto"
+
+
 def tune(hy, ctx, a, b, dx, dts):
-    """Autotune tile shape and z-chunk on this machine (writes b), then restore dts[0]."""
+    """Autotune tile shape and z-chunk on this machine (writes b), or apply a fixed --tuning."""
     pa, pb = hy.patch(a, 0, dx), hy.patch(b, 0, dx)
     hy.hydro_cfl_dt(ctx, pa, dts[0:1])
-    hy.hydro_autotune(ctx, pa, pb, dts[0:1])
+    if TUNING == "auto":
+        hy.hydro_autotune(ctx, pa, pb, dts[0:1])
+    else:
+        t, z = (int(x) for x in TUNING.split(":"))
+        hy.hydro_set_tuning(ctx, t, z)
     t, z = hy.hydro_get_tuning(ctx)
     return {"tile": "%dx%d" % ({0: (16, 16), 1: (32, 8), 2: (8, 8), 3: (32, 16)}[t]), "zchunk": z}
 
@@ -453,7 +461,9 @@ def reference_arm(args):
 
 
 def main():
+    global TUNING
     args = parse()
+    TUNING = args.tuning
     if args.impl == "reference":
         return reference_arm(args)
     rank, world, local = dist_env()
