@@ -37,7 +37,13 @@ import torch  # noqa: E402
 # counted stage by stage on a 64^3 sample of each workload (tests/test_bench_constants.py
 # recomputes them): recovery 12 + slopes + predictor 56 + 3 x face (states + HLLC) + update 35.
 ALG_FLOPS_PER_CELL = {"turb_minmod": 375.0, "turb_mc": 402.0, "mach10_mc": 387.0}
-BYTES_PER_CELL = {"fp64": 80.0, "fp32": 40.0, "mixed": 80.0}  # 5 fields read + 5 written
+# The same step in double-float arithmetic (the df64 precision): each operation of the scheme
+# becomes FP32 operations of the double-word algorithms -- add/sub 20 (two TwoSums, two
+# Fast2Sums), mul 9 (TwoProd by FMA, two cross FMAs, Fast2Sum), div 35, sqrt 12 -- applied to the
+# oracle's count by kind on the same sample (+- 178.3, * 167.5, / 22.9, sqrt 6.0 per cell).
+DF_COST = {"addsub": 20, "mul": 9, "div": 35, "sqrt": 12}
+ALG_DF_FLOPS_PER_CELL = {"turb_minmod": 5940.0}
+BYTES_PER_CELL = {"fp64": 80.0, "fp32": 40.0, "mixed": 80.0, "df64": 80.0}  # 5 fields read + 5 written
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -54,7 +60,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=512)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed", "df64"])
     p.add_argument("--forms", default="all", help="comma list of extra forms, 'all' or 'none'")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--tuning", default="auto", help="'auto' (autotune) or '<tile id>:<zchunk>'")
@@ -222,9 +228,13 @@ def time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream, per_launch=True):
 
 
 def roofline(precision, cells, per_ms, flops_per_cell, hbm_gbs, peak_src, traffic):
-    """Roofline object of the step kernel: the binding roof is the one with the larger fraction."""
+    """Roofline object of the step kernel: the binding roof is the one with the larger fraction.
+    For df64 the arithmetic is FP32 operations of the double-float algorithms (ALG_DF_FLOPS_PER_CELL)
+    against the FP32 peak."""
     avg_s = statistics.mean(per_ms) / 1e3
     bytes_launch = cells * BYTES_PER_CELL[precision]
+    if precision == "df64":
+        flops_per_cell = ALG_DF_FLOPS_PER_CELL["turb_minmod"]
     flops_launch = cells * flops_per_cell
     gbs = bytes_launch / avg_s / 1e9
     tfl = flops_launch / avg_s / 1e12
@@ -534,7 +544,9 @@ def main():
     line = {"metric": "Mcell-updates/s per hydro step (1 GB300)", "value": round(value, 2),
             "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64-state/f32"}[precision],
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64-state/f32",
+                      "df64": "f64 state, double-float (f32 pair) arithmetic"}[precision],
             "data": "synthetic",
             "config": {"workload": "%d^3 periodic uniform grid, Gaussian k^-4 velocities at rms Mach 5, lognormal rho "
                                    "(sigma 1), P/rho = 1e-4, Sedov cell E=1; MinMod PLM + HLLC, CFL 0.8, gamma 5/3; "
@@ -556,6 +568,8 @@ def main():
                 elif f == "fp64_256":
                     extra["fp64_256"] = form_uniform(hy, 256, "fp64", "minmod", args.steps, args.warmup,
                                                      "turb_minmod")
+                elif f in ("fp64", "df64"):
+                    extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod")
                 elif f == "batched":
                     extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2)
                 elif f == "adjoint":

@@ -17,7 +17,7 @@
  * Conventions
  *   - Every field pointer is DEVICE memory owned by the caller; the library never frees it.
  *     Fields are structure-of-arrays: five separate arrays (rho, m_x, m_y, m_z, E), x fastest.
- *     Element type: double for HYDRO_FP64 and HYDRO_MIXED, float for HYDRO_FP32.
+ *     Element type: double for HYDRO_FP64, HYDRO_MIXED and HYDRO_FP64_DF, float for HYDRO_FP32.
  *   - The library owns only what a hydro_ctx holds: the device error word, uploaded patch
  *     descriptors, the tile work-list and its counter, captured CUDA graphs, autotune results.
  *   - Every call is asynchronous on the context's stream, except hydro_get_error (and
@@ -47,14 +47,18 @@ typedef enum {
   HYDRO_ERR_STATE = -6       /* call not valid in the context's current state */
 } hydro_status;
 
-typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2 } hydro_precision;
+typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2, HYDRO_FP64_DF = 3 } hydro_precision;
 /* HYDRO_FP64 : double state, double arithmetic throughout.
  * HYDRO_FP32 : float state; float reconstruction, predictor, HLLC and update; the pressure
  *              recovery p = (gamma-1)(E - |m|^2/(2 rho)) is evaluated with error-free float
  *              transformations to double-float accuracy (at least as accurate as evaluating it in
  *              double and rounding to float).
  * HYDRO_MIXED: double state; the same recovery evaluated in double; float reconstruction,
- *              predictor, HLLC and flux divergence; the update U + dU accumulated in double. */
+ *              predictor, HLLC and flux divergence; the update U + dU accumulated in double.
+ * HYDRO_FP64_DF: double state; every step of the scheme in double-float arithmetic (pairs of
+ *              floats, about 48 significant bits, on the FP32 pipes), the update U + dU accumulated
+ *              in double.  Same results as HYDRO_FP64 to about 1e-13 relative, several times faster
+ *              on parts whose FP64 rate is a small fraction of their FP32 rate. */
 
 typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2 } hydro_limiter;
 
@@ -129,7 +133,8 @@ int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5],
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
  * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64 or
  * HYDRO_FP32.  U_n: the state the forward step started from; dt_dev[p] its time step; lam_np1,
- * lam_n: adjoint fields with the same layout and element type as U_n (must not overlap).  The
+ * lam_n: adjoint fields with the same layout and element type as U_n (must not overlap).
+ * Other precisions return HYDRO_ERR_ARG.  The
  * derivative of each limiter / HLLC branch / floor is that of the branch the forward values
  * select.  Deterministic: every face's contribution is gathered, never atomically scattered. */
 int hydro_adjoint_step(hydro_ctx* ctx, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

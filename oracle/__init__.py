@@ -188,10 +188,13 @@ def count_ops(U, dx, dt, cfg=None):
     cfg = cfg or config()
     U, pu = _c(U)
     _, nz, ny, nx = U.shape
-    out = np.zeros(5)
+    out = np.zeros(25)
     _check(lib().oracle_count_ops(ctypes.byref(cfg), pu, nx, ny, nz, dx, dt, out.ctypes.data))
     d = dict(recover=out[0], slopes=out[1], predict=out[2], face=out[3], update=out[4])
     d["per_cell"] = out[0] + out[1] + out[2] + 3 * out[3] + out[4]
+    mult = [1, 1, 1, 3, 1]
+    kinds = ("addsub", "mul", "div", "sqrt")
+    d["by_kind"] = {k: float(sum(mult[s] * out[5 + 4 * s + i] for s in range(5))) for i, k in enumerate(kinds)}
     return d
 
 

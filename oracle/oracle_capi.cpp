@@ -226,7 +226,8 @@ int oracle_prim_to_cons_adjoint(const oracle_config* cfg, const double* q, const
 
 // Operation counts of one periodic step, per unit of each stage: out[0] recovery per cell,
 // out[1] slopes per cell (3 directions), out[2] predictor per cell, out[3] face states + HLLC
-// per face, out[4] update per cell.  Counts binary +, -, *, / and sqrt.
+// per face, out[4] update per cell (binary +, -, *, / and sqrt); out[5..24] the same by kind.
+// out must hold 25 doubles.
 int oracle_count_ops(const oracle_config* cfg, const double* U, int nx, int ny, int nz, double dx, double dt,
                      double* out) {
   if (!cfg || !U || !out || bad_dims(nx, ny, nz)) return -1;
@@ -234,22 +235,25 @@ int oracle_count_ops(const oracle_config* cfg, const double* U, int nx, int ny, 
   Fields<Counted> A, Ug, q, qh, slope[3], flux[3], B;
   load(A, U, nx, ny, nz);
   fill_periodic(A, Ug);
+  // out[0..4]: all operations per unit of each stage; out[5 + 4*s + k]: operations of kind k
+  // (+-, *, /, sqrt) per unit of stage s.
   uint64_t& cnt = op_counter();
-  cnt = 0;
-  size_t n0 = stage_recover(c, Ug, q);
-  out[0] = (double)cnt / (double)n0;
-  cnt = 0;
-  size_t n1 = stage_slopes(c, q, slope);
-  out[1] = (double)cnt / (double)n1;
-  cnt = 0;
-  size_t n2 = stage_predict(c, q, slope, qh, dx, dt);
-  out[2] = (double)cnt / (double)n2;
-  cnt = 0;
-  size_t n3 = stage_fluxes(c, qh, slope, flux);
-  out[3] = (double)cnt / (double)n3;
-  cnt = 0;
-  size_t n4 = stage_update(Ug, flux, B, dx, dt);
-  out[4] = (double)cnt / (double)n4;
+  uint64_t* kinds = op_kinds();
+  auto reset = [&]() { cnt = 0; for (int k = 0; k < 4; ++k) kinds[k] = 0; };
+  auto record = [&](int s, size_t units) {
+    out[s] = (double)cnt / (double)units;
+    for (int k = 0; k < 4; ++k) out[5 + 4 * s + k] = (double)kinds[k] / (double)units;
+  };
+  reset();
+  record(0, stage_recover(c, Ug, q));
+  reset();
+  record(1, stage_slopes(c, q, slope));
+  reset();
+  record(2, stage_predict(c, q, slope, qh, dx, dt));
+  reset();
+  record(3, stage_fluxes(c, qh, slope, flux));
+  reset();
+  record(4, stage_update(Ug, flux, B, dx, dt));
   return 0;
 }
 

@@ -103,17 +103,22 @@ inline uint64_t& op_counter() {
   static thread_local uint64_t c = 0;
   return c;
 }
+// The same operations by kind: [0] + and -, [1] *, [2] /, [3] sqrt.
+inline uint64_t* op_kinds() {
+  static thread_local uint64_t k[4] = {0, 0, 0, 0};
+  return k;
+}
 struct Counted {
   double v;
   Counted() : v(0) {}
   Counted(double x) : v(x) {}
 };
 inline double value(const Counted& a) { return a.v; }
-inline Counted operator+(const Counted& a, const Counted& b) { ++op_counter(); return Counted(a.v + b.v); }
-inline Counted operator-(const Counted& a, const Counted& b) { ++op_counter(); return Counted(a.v - b.v); }
+inline Counted operator+(const Counted& a, const Counted& b) { ++op_counter(); ++op_kinds()[0]; return Counted(a.v + b.v); }
+inline Counted operator-(const Counted& a, const Counted& b) { ++op_counter(); ++op_kinds()[0]; return Counted(a.v - b.v); }
 inline Counted operator-(const Counted& a) { return Counted(-a.v); }  // sign flip: free
-inline Counted operator*(const Counted& a, const Counted& b) { ++op_counter(); return Counted(a.v * b.v); }
-inline Counted operator/(const Counted& a, const Counted& b) { ++op_counter(); return Counted(a.v / b.v); }
-inline Counted sqrt(const Counted& a) { ++op_counter(); return Counted(std::sqrt(a.v)); }
+inline Counted operator*(const Counted& a, const Counted& b) { ++op_counter(); ++op_kinds()[1]; return Counted(a.v * b.v); }
+inline Counted operator/(const Counted& a, const Counted& b) { ++op_counter(); ++op_kinds()[2]; return Counted(a.v / b.v); }
+inline Counted sqrt(const Counted& a) { ++op_counter(); ++op_kinds()[3]; return Counted(std::sqrt(a.v)); }
 
 }  // namespace oracle

@@ -24,9 +24,9 @@ HYDRO_ERR_TIMEOUT = -4
 HYDRO_ERR_NOMEM = -5
 HYDRO_ERR_STATE = -6
 
-HYDRO_FP64, HYDRO_FP32, HYDRO_MIXED = 0, 1, 2
+HYDRO_FP64, HYDRO_FP32, HYDRO_MIXED, HYDRO_FP64_DF = 0, 1, 2, 3
 HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT = 0, 1, 2
-PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED}
+PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED, "df64": HYDRO_FP64_DF}
 LIMITERS = {"minmod": HYDRO_MINMOD, "mc": HYDRO_MC, "none": HYDRO_NOLIMIT}
 
 EBIT_NONFINITE = 0x01

@@ -13,17 +13,17 @@ namespace hydro {
 template <class R>
 __device__ __forceinline__ R limited_code(R a, R b, int lim, unsigned& code) {
   if (lim == HYDRO_NOLIMIT) { code = 3; return R(0.5) * (a + b); }
-  if (a * b <= R(0)) { code = 0; return R(0); }
+  if (prod_nonpos(a, b)) { code = 0; return R(0); }
   if (lim == HYDRO_MINMOD) {
-    if (rabs(a) <= rabs(b)) { code = 1; return a; }
+    if (abs_le(a, b)) { code = 1; return a; }
     code = 2;
     return b;
   }
   R ta = R(2) * a, tb = R(2) * b, m = R(0.5) * (a + b);
   R best = ta;
   code = 1;
-  if (rabs(tb) < rabs(best)) { best = tb; code = 2; }
-  if (rabs(m) < rabs(best)) { best = m; code = 3; }
+  if (abs_lt(tb, best)) { best = tb; code = 2; }
+  if (abs_lt(m, best)) { best = m; code = 3; }
   return best;
 }
 
@@ -57,8 +57,9 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   const R num = qR[4] - qL[4] + uL * mL - uR * mR;
   const R den = mL - mR;
   const R Ss = num / den;
-  const bool star = (SL < R(0)) && (SR > R(0));
-  const bool left = (SL >= R(0)) || (SR > R(0) && Ss >= R(0));
+  const bool SLneg = cmp_neg(SL), SRpos = cmp_pos(SR);
+  const bool star = SLneg && SRpos;
+  const bool left = !SLneg || (SRpos && !cmp_neg(Ss));
   const R rK = left ? qL[0] : qR[0];
   const R uK = left ? uL : uR;
   const R t1 = left ? qL[2] : qR[2];
@@ -233,8 +234,8 @@ __device__ __forceinline__ void hancock_adj(const R q[5], const R dq[3][5], R ga
 // Reverse of floor_state: zero the adjoint of a floored density / pressure (pre: unfloored).
 template <class R>
 __device__ __forceinline__ void floor_mask(const R pre[5], R lq[5], R rho_floor, R p_floor) {
-  if (pre[0] < rho_floor) lq[0] = R(0);
-  if (pre[4] < p_floor) lq[4] = R(0);
+  if (cmp_lt_floor(pre[0], rho_floor)) lq[0] = R(0);
+  if (cmp_lt_floor(pre[4], p_floor)) lq[4] = R(0);
 }
 
 // ------------------------------------------------------------------ recovery reverse

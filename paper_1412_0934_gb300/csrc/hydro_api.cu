@@ -58,6 +58,18 @@ struct hydro_ctx {
   long long launches = 0;
 };
 
+namespace hydro {
+const KernelOps* ops_for(int precision) {
+  switch (precision) {
+    case HYDRO_FP64: return &ops_f64();
+    case HYDRO_FP32: return &ops_f32();
+    case HYDRO_MIXED: return &ops_mixed();
+    case HYDRO_FP64_DF: return &ops_df();
+  }
+  return nullptr;
+}
+}  // namespace hydro
+
 namespace {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
@@ -216,13 +228,12 @@ int hydro_init(hydro_ctx** ctx, const hydro_config* cfg) {
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return HYDRO_ERR_ARG;
   if (!(cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0)) return HYDRO_ERR_ARG;
   if (cfg->limiter < HYDRO_MINMOD || cfg->limiter > HYDRO_NOLIMIT) return HYDRO_ERR_ARG;
-  if (cfg->precision < HYDRO_FP64 || cfg->precision > HYDRO_MIXED) return HYDRO_ERR_ARG;
+  if (!hydro::ops_for(cfg->precision)) return HYDRO_ERR_ARG;
   hydro_ctx* c = new hydro_ctx();
   c->cfg = *cfg;
   c->prm = hydro::Params{cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter};
   c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
-  c->ops = cfg->precision == HYDRO_FP64 ? &hydro::ops_f64()
-                                        : (cfg->precision == HYDRO_FP32 ? &hydro::ops_f32() : &hydro::ops_mixed());
+  c->ops = hydro::ops_for(cfg->precision);
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     delete c;
@@ -330,7 +341,7 @@ int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], l
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
                        const hydro_patch* lam_n, int npatch) {
   if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1) return HYDRO_ERR_ARG;
-  if (c->cfg.precision == HYDRO_MIXED) return HYDRO_ERR_ARG;
+  if (c->cfg.precision != HYDRO_FP64 && c->cfg.precision != HYDRO_FP32) return HYDRO_ERR_ARG;
   for (int i = 0; i < npatch; ++i) {
     const hydro_patch &U = U_n[i], &L = lam_np1[i], &O = lam_n[i];
     if (!valid_patch(c, U) || !valid_patch(c, L) || !valid_patch(c, O)) return HYDRO_ERR_ARG;

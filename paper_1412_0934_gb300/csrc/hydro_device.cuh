@@ -4,11 +4,14 @@
 // states, HLLC fluxes and the per-cell CFL speed.  Three precision policies:
 //   PolF64   double state, double arithmetic;
 //   PolF32   float state, float arithmetic, pressure recovery by error-free transformations;
-//   PolMixed double state, double pressure recovery and update accumulation, float bulk.
+//   PolMixed double state, double pressure recovery and update accumulation, float bulk;
+//   PolDF    double state, double-float arithmetic (about 48 bits, on the FP32 pipes), double
+//            update accumulation.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "hydro.h"
 
 namespace hydro {
@@ -42,8 +45,45 @@ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 
+__device__ __forceinline__ float shfl_xor_(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor_(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ bool isfinite_(float x) { return isfinite(x); }
+__device__ __forceinline__ bool isfinite_(double x) { return isfinite(x); }
+
 // Order-preserving 64-bit key of a non-negative double (IEEE bits compare as unsigned ints).
 __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// ------------------------------------------------------------------ comparisons
+// For doubles the tests below run on the integer pipe over the IEEE bit patterns (GB300's FP64
+// pipe is 1/73 of its FP32 rate, and comparisons would occupy it); they give the same result as
+// the floating-point comparison for every non-NaN operand.  Floats use plain comparisons.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool cmp_lt_floor(double x, double f) {  // x < f for f > 0
+  const long long X = dbits(x);
+  return X < 0 ? (X & 0x7fffffffffffffffLL) != 0 || dbits(f) > 0 : X < dbits(f);
+}
+__device__ __forceinline__ bool cmp_lt_floor(float x, float f) { return x < f; }
+__device__ __forceinline__ bool cmp_neg(double x) {  // x < 0
+  const long long X = dbits(x);
+  return X < 0 && (X & 0x7fffffffffffffffLL) != 0;
+}
+__device__ __forceinline__ bool cmp_neg(float x) { return x < 0.f; }
+__device__ __forceinline__ bool cmp_pos(double x) { return dbits(x) > 0; }  // x > 0
+__device__ __forceinline__ bool cmp_pos(float x) { return x > 0.f; }
+// |a| <= |b|
+__device__ __forceinline__ bool abs_le(double a, double b) {
+  return (unsigned long long)(dbits(a) & 0x7fffffffffffffffLL) <= (unsigned long long)(dbits(b) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool abs_le(float a, float b) { return fabsf(a) <= fabsf(b); }
+__device__ __forceinline__ bool abs_lt(double a, double b) { return !abs_le(b, a); }
+__device__ __forceinline__ bool abs_lt(float a, float b) { return fabsf(a) < fabsf(b); }
+// a * b <= 0: opposite signs or a zero factor.  (Differs from the rounded product only when
+// |a b| underflows below 1e-308, where either limiter result is below 1e-154.)
+__device__ __forceinline__ bool prod_nonpos(double a, double b) {
+  const long long A = dbits(a), B = dbits(b);
+  return ((A ^ B) < 0) || (A & 0x7fffffffffffffffLL) == 0 || (B & 0x7fffffffffffffffLL) == 0;
+}
+__device__ __forceinline__ bool prod_nonpos(float a, float b) { return a * b <= 0.f; }
 
 // ------------------------------------------------------------------ slope limiter
 // MinMod: 0 if a*b <= 0, else the argument of smaller magnitude (tie -> a).
@@ -52,12 +92,12 @@ __device__ __forceinline__ unsigned long long dkey(double x) { return (unsigned 
 template <class R>
 __device__ __forceinline__ R limited(R a, R b, int lim) {
   if (lim == HYDRO_NOLIMIT) return R(0.5) * (a + b);
-  if (a * b <= R(0)) return R(0);
-  if (lim == HYDRO_MINMOD) return (rabs(a) <= rabs(b)) ? a : b;
+  if (prod_nonpos(a, b)) return R(0);
+  if (lim == HYDRO_MINMOD) return abs_le(a, b) ? a : b;
   R ta = R(2) * a, tb = R(2) * b, m = R(0.5) * (a + b);
   R best = ta;
-  if (rabs(tb) < rabs(best)) best = tb;
-  if (rabs(m) < rabs(best)) best = m;
+  if (abs_lt(tb, best)) best = tb;
+  if (abs_lt(m, best)) best = m;
   return best;
 }
 
@@ -95,8 +135,8 @@ __device__ __forceinline__ void hancock(const R q[5], const R dqx[5], const R dq
 
 template <class R>
 __device__ __forceinline__ void floor_state(R q[5], R rho_floor, R p_floor) {
-  q[0] = q[0] < rho_floor ? rho_floor : q[0];
-  q[4] = q[4] < p_floor ? p_floor : q[4];
+  q[0] = cmp_lt_floor(q[0], rho_floor) ? rho_floor : q[0];
+  q[4] = cmp_lt_floor(q[4], p_floor) ? p_floor : q[4];
 }
 
 // ------------------------------------------------------------------ HLLC
@@ -117,8 +157,9 @@ __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R
   const R mL = qL[0] * (SL - uL);
   const R mR = qR[0] * (SR - uR);
   const R Ss = div_(qR[4] - qL[4] + uL * mL - uR * mR, mL - mR);
-  const bool star = (SL < R(0)) && (SR > R(0));
-  const bool left = (SL >= R(0)) || (SR > R(0) && Ss >= R(0));
+  const bool SLneg = cmp_neg(SL), SRpos = cmp_pos(SR);
+  const bool star = SLneg && SRpos;
+  const bool left = !SLneg || (SRpos && !cmp_neg(Ss));
   const R rK = left ? qL[0] : qR[0];
   const R uK = left ? uL : uR;
   const R t1 = left ? qL[2] : qR[2];
@@ -305,6 +346,36 @@ struct PolMixed {
   static __device__ __forceinline__ float speed(const double U[5], const Params& P, unsigned& flags);
 };
 
+struct PolDF {
+  using S = double;
+  using R = df;
+  // The same recovery as PolF64, in double-float from the double state.
+  static __device__ __forceinline__ void recover(const double U[5], const Params& P, df q[5], unsigned& flags) {
+    df rho(U[0]);
+    const df rf(P.rho_floor);
+    if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
+    const df ir = rcp_(rho);
+    const df mx(U[1]), my(U[2]), mz(U[3]);
+    const df kin = df(0.5f) * ((mx * mx + my * my) + mz * mz) * ir;
+    const df eint = df(U[4]) - kin;
+    if (cmp_neg(eint)) flags |= HYDRO_EBIT_P_FLOOR;
+    df p = df(P.gamma - 1.0) * eint;
+    if (!(isfinite(p.h) && isfinite(rho.h))) flags |= HYDRO_EBIT_NONFINITE;
+    const df pf(P.p_floor);
+    q[0] = rho;
+    q[1] = mx * ir;
+    q[2] = my * ir;
+    q[3] = mz * ir;
+    q[4] = p < pf ? pf : p;
+  }
+  // U_old - dtdx * div with the double-float increment added to the double state in double.
+  static __device__ __forceinline__ double update(double Uold, const df& dtdx, const df& div) {
+    const df d = dtdx * div;
+    return (Uold - (double)d.h) - (double)d.l;
+  }
+  static __device__ __forceinline__ df speed(const double U[5], const Params& P, unsigned& flags);
+};
+
 // CFL speed of a recovered state.
 template <class R>
 __device__ __forceinline__ R cfl_speed(const R q[5], R gamma) {
@@ -323,6 +394,11 @@ __device__ __forceinline__ float PolMixed::speed(const double U[5], const Params
   float q[5];
   recover(U, P, q, flags);
   return cfl_speed(q, (float)P.gamma);
+}
+__device__ __forceinline__ df PolDF::speed(const double U[5], const Params& P, unsigned& flags) {
+  df q[5];
+  recover(U, P, q, flags);
+  return cfl_speed(q, df(P.gamma));
 }
 
 }  // namespace hydro

@@ -58,6 +58,9 @@ struct KernelOps {
 const KernelOps& ops_f64();
 const KernelOps& ops_f32();
 const KernelOps& ops_mixed();
+const KernelOps& ops_df();
+// Kernel set of a hydro_precision value (nullptr if out of range).
+const KernelOps* ops_for(int precision);
 
 // Work-list construction (precision-independent; descriptors read through HostPatchIO).
 cudaError_t build_worklist(const HostPatchIO* d_patches, int npatch, int tx, int ty, int zchunk, int* d_counts,

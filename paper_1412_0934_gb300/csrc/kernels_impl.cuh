@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_cfl(const PatchIO<typename Pol::S>* pat
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      R w = __shfl_xor_sync(0xffffffffu, smax, o);
+      R w = shfl_xor_(smax, o);
       smax = w > smax ? w : smax;
     }
     __syncthreads();

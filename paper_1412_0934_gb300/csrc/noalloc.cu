@@ -91,7 +91,7 @@ extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_p
   if (npatch > kMaxPatches) return HYDRO_ERR_ARG;
   if (!(cfg->gamma > 1.0 && std::isfinite(cfg->gamma)) || !(cfg->cfl > 0.0 && cfg->cfl <= 1.0) ||
       !(cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0) || cfg->limiter < HYDRO_MINMOD || cfg->limiter > HYDRO_NOLIMIT ||
-      cfg->precision < HYDRO_FP64 || cfg->precision > HYDRO_MIXED)
+      !hydro::ops_for(cfg->precision))
     return HYDRO_ERR_ARG;
   const int es = cfg->precision == HYDRO_FP32 ? 4 : 8;
   const int tile = 0;
@@ -112,9 +112,7 @@ extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_p
   int rc = setup_device(dev, &s);
   if (rc) return rc;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HYDRO_ERR_CUDA;
-  const hydro::KernelOps& ops = cfg->precision == HYDRO_FP64
-                                    ? hydro::ops_f64()
-                                    : (cfg->precision == HYDRO_FP32 ? hydro::ops_f32() : hydro::ops_mixed());
+  const hydro::KernelOps& ops = *hydro::ops_for(cfg->precision);
   const hydro::Params prm{cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter};
   cudaStream_t st = static_cast<cudaStream_t>(cfg->cuda_stream);
   unsigned* err = error_bits_dev ? error_bits_dev : s->error;

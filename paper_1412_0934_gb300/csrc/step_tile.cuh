@@ -31,17 +31,70 @@ struct TileRec {
   int patch, x0, y0, z0;
 };
 
+// Five values per cell of an H x W plane, packed for wide shared-memory accesses:
+// float: (v0..v3) as one float4 + v4; double: (v0,v1), (v2,v3) as double2 + v4.
+template <class R, int H, int W>
+struct Plane5;
+template <int H, int W>
+struct Plane5<float, H, W> {
+  float4 a[H][W];
+  float b[H][W];
+  __device__ __forceinline__ void st(int j, int i, const float v[5]) {
+    a[j][i] = make_float4(v[0], v[1], v[2], v[3]);
+    b[j][i] = v[4];
+  }
+  __device__ __forceinline__ void ld(int j, int i, float v[5]) const {
+    const float4 t = a[j][i];
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    v[4] = b[j][i];
+  }
+};
+template <int H, int W>
+struct Plane5<double, H, W> {
+  double2 a[H][W];
+  double2 b[H][W];
+  double c[H][W];
+  __device__ __forceinline__ void st(int j, int i, const double v[5]) {
+    a[j][i] = make_double2(v[0], v[1]);
+    b[j][i] = make_double2(v[2], v[3]);
+    c[j][i] = v[4];
+  }
+  __device__ __forceinline__ void ld(int j, int i, double v[5]) const {
+    const double2 t = a[j][i], u = b[j][i];
+    v[0] = t.x; v[1] = t.y; v[2] = u.x; v[3] = u.y;
+    v[4] = c[j][i];
+  }
+};
+
+template <int H, int W>
+struct Plane5<df, H, W> {
+  float4 a[H][W];  // (h0, l0, h1, l1)
+  float4 b[H][W];  // (h2, l2, h3, l3)
+  float2 c[H][W];  // (h4, l4)
+  __device__ __forceinline__ void st(int j, int i, const df v[5]) {
+    a[j][i] = make_float4(v[0].h, v[0].l, v[1].h, v[1].l);
+    b[j][i] = make_float4(v[2].h, v[2].l, v[3].h, v[3].l);
+    c[j][i] = make_float2(v[4].h, v[4].l);
+  }
+  __device__ __forceinline__ void ld(int j, int i, df v[5]) const {
+    const float4 t = a[j][i], u = b[j][i];
+    const float2 w = c[j][i];
+    v[0] = df(t.x, t.y); v[1] = df(t.z, t.w); v[2] = df(u.x, u.y); v[3] = df(u.z, u.w);
+    v[4] = df(w.x, w.y);
+  }
+};
+
 template <class Pol, int TX, int TY>
 struct TileShared {
   using R = typename Pol::R;
-  R q[3][5][TY + 4][TX + 4];  // primitive planes p-1, p, p+1 (ring)
-  R qh[5][TY + 2][TX + 2];    // predicted state of plane p (tile + 1 ring)
-  R sx[5][TY + 2][TX + 2];    // x slopes of plane p
-  R sy[5][TY + 2][TX + 2];    // y slopes of plane p
-  R fx[5][TY][TX + 1];        // x-face fluxes of plane p, index i+1 for face i+1/2
-  R fy[5][TY + 1][TX];        // y-face fluxes of plane p, index j+1 for face j+1/2
-  long long yoff[TY + 4];     // y offset (y index * stride) of the halo rows
-  int xoff[TX + 4];           // x index of the halo columns
+  Plane5<R, TY + 4, TX + 4> q[3];  // primitive planes p-1, p, p+1 (ring)
+  Plane5<R, TY + 2, TX + 2> qh;    // predicted state of plane p (tile + 1 ring)
+  Plane5<R, TY + 2, TX + 2> sx;    // x slopes of plane p
+  Plane5<R, TY + 2, TX + 2> sy;    // y slopes of plane p
+  Plane5<R, TY, TX + 1> fx;        // x-face fluxes of plane p, index i+1 for face i+1/2
+  Plane5<R, TY + 1, TX> fy;        // y-face fluxes of plane p, index j+1 for face j+1/2
+  long long yoff[TY + 4];          // y offset (y index * stride) of the halo rows
+  int xoff[TX + 4];                // x index of the halo columns
   R red[TX * TY / 32];
   int tile;
 };
@@ -58,22 +111,24 @@ __device__ __forceinline__ void predict_cell(TileShared<Pol, TX, TY>& sm, int i,
                                              typename Pol::R dqz[5]) {
   using R = typename Pol::R;
   const int ci = i + 2, cj = j + 2;
-  R q0[5], dqx[5], dqy[5];
+  R c[5], xm[5], xp[5], ym[5], yp[5], zm[5], zp[5], dqx[5], dqy[5];
+  sm.q[s0].ld(cj, ci, c);
+  sm.q[s0].ld(cj, ci - 1, xm);
+  sm.q[s0].ld(cj, ci + 1, xp);
+  sm.q[s0].ld(cj - 1, ci, ym);
+  sm.q[s0].ld(cj + 1, ci, yp);
+  sm.q[sm1].ld(cj, ci, zm);
+  sm.q[sp1].ld(cj, ci, zp);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const R c = sm.q[s0][v][cj][ci];
-    q0[v] = c;
-    dqx[v] = limited(c - sm.q[s0][v][cj][ci - 1], sm.q[s0][v][cj][ci + 1] - c, prm.limiter);
-    dqy[v] = limited(c - sm.q[s0][v][cj - 1][ci], sm.q[s0][v][cj + 1][ci] - c, prm.limiter);
-    dqz[v] = limited(c - sm.q[sm1][v][cj][ci], sm.q[sp1][v][cj][ci] - c, prm.limiter);
+    dqx[v] = limited(c[v] - xm[v], xp[v] - c[v], prm.limiter);
+    dqy[v] = limited(c[v] - ym[v], yp[v] - c[v], prm.limiter);
+    dqz[v] = limited(c[v] - zm[v], zp[v] - c[v], prm.limiter);
   }
-  hancock(q0, dqx, dqy, dqz, (R)prm.gamma, hdt, qh);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    sm.qh[v][j + 1][i + 1] = qh[v];
-    sm.sx[v][j + 1][i + 1] = dqx[v];
-    sm.sy[v][j + 1][i + 1] = dqy[v];
-  }
+  hancock(c, dqx, dqy, dqz, (R)prm.gamma, hdt, qh);
+  sm.qh.st(j + 1, i + 1, qh);
+  sm.sx.st(j + 1, i + 1, dqx);
+  sm.sy.st(j + 1, i + 1, dqy);
 }
 
 // Flux of the x face between tile cells (i, j) and (i+1, j) (D = 0) or the y face between
@@ -84,13 +139,20 @@ __device__ __forceinline__ void face_flux(TileShared<Pol, TX, TY>& sm, int i, in
   using R = typename Pol::R;
   const int li = i + 1, lj = j + 1;
   const int ri = li + (D == 0), rj = lj + (D == 1);
-  R qL[5], qR[5];
+  R qL[5], qR[5], sL[5], sR[5];
+  sm.qh.ld(lj, li, qL);
+  sm.qh.ld(rj, ri, qR);
+  if (D == 0) {
+    sm.sx.ld(lj, li, sL);
+    sm.sx.ld(rj, ri, sR);
+  } else {
+    sm.sy.ld(lj, li, sL);
+    sm.sy.ld(rj, ri, sR);
+  }
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const R sL = (D == 0) ? sm.sx[v][lj][li] : sm.sy[v][lj][li];
-    const R sR = (D == 0) ? sm.sx[v][rj][ri] : sm.sy[v][rj][ri];
-    qL[v] = sm.qh[v][lj][li] + R(0.5) * sL;
-    qR[v] = sm.qh[v][rj][ri] - R(0.5) * sR;
+    qL[v] = qL[v] + R(0.5) * sL[v];
+    qR[v] = qR[v] - R(0.5) * sR[v];
   }
   floor_state(qL, (R)prm.rho_floor, (R)prm.p_floor);
   floor_state(qR, (R)prm.rho_floor, (R)prm.p_floor);
@@ -133,8 +195,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
       for (int v = 0; v < 5; ++v) U[v] = __ldg(P.in[v] + a);
       R q[5];
       Pol::recover(U, prm, q, flags);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sm.q[slot][v][cy][cx] = q[v];
+      sm.q[slot].st(cy, cx, q);
     }
   };
 
@@ -186,27 +247,27 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     if (p >= z0 && p < z1) {
       R F[5];
       face_flux<0>(sm, ti, tj, prm, F);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sm.fx[v][tj][ti + 1] = F[v];
+      sm.fx.st(tj, ti + 1, F);
       face_flux<1>(sm, ti, tj, prm, F);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sm.fy[v][tj + 1][ti] = F[v];
+      sm.fy.st(tj + 1, ti, F);
       if (tid < TY) {
         face_flux<0>(sm, -1, tid, prm, F);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sm.fx[v][tid][0] = F[v];
+        sm.fx.st(tid, 0, F);
       } else if (tid >= 32 && tid < 32 + TX) {
         face_flux<1>(sm, tid - 32, -1, prm, F);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sm.fy[v][0][tid - 32] = F[v];
+        sm.fy.st(0, tid - 32, F);
       }
     }
     __syncthreads();
     // ---- D
     if (p >= z0 && p < z1) {
+      R xp[5], xm[5], yp[5], ym[5];
+      sm.fx.ld(tj, ti + 1, xp);
+      sm.fx.ld(tj, ti, xm);
+      sm.fy.ld(tj + 1, ti, yp);
+      sm.fy.ld(tj, ti, ym);
 #pragma unroll
-      for (int v = 0; v < 5; ++v)
-        dF[v] = (sm.fx[v][tj][ti + 1] - sm.fx[v][tj][ti]) + (sm.fy[v][tj + 1][ti] - sm.fy[v][tj][ti]);
+      for (int v = 0; v < 5; ++v) dF[v] = (xp[v] - xm[v]) + (yp[v] - ym[v]);
     }
     if (p >= z0 + 1 && own) {
       const int k = p - 1;
@@ -238,7 +299,7 @@ __device__ __forceinline__ typename Pol::R block_max(TileShared<Pol, TX, TY>& sm
   using R = typename Pol::R;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    R w = __shfl_xor_sync(0xffffffffu, v, o);
+    R w = shfl_xor_(v, o);
     v = w > v ? w : v;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -265,9 +326,17 @@ __device__ __forceinline__ void publish_dt(double cfl, double dx, double smax, d
 }
 
 // ------------------------------------------------------------------ kernels
+// Resident blocks per SM the register allocation must allow: 2 x 256 threads for FP64 (its
+// shared memory allows 2), 3 x 256 for the float policies.
+template <class Pol, int NT>
+constexpr int min_blocks() {
+  constexpr int b = (sizeof(typename Pol::R) >= 8 ? 2 : 3) * 256 / NT;
+  return b < 1 ? 1 : b;
+}
+
 // Uniform grid: one tile per block, tiles from the block index.
 template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
+__global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY>())) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
                                                          double* dt_next, int zchunk, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<TileShared<Pol, TX, TY>*>(smem_raw);
@@ -290,7 +359,7 @@ __global__ void __launch_bounds__(TX* TY) k_step_uniform(PatchIO<typename Pol::S
 
 // Batched patches: a persistent grid pulls tiles from the work-list through an atomic counter.
 template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_step_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles,
+__global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY>())) k_step_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles,
                                                          int ntiles, int* counter, Params prm, const double* dt_dev,
                                                          double* dt_next, int zchunk, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

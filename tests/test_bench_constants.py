@@ -30,3 +30,12 @@ def test_flop_constants(key, limiter, kw):
     dt = oracle.cfl_periodic(U, 1 / 64, cfg)
     c = oracle.count_ops(U, 1 / 64, dt, cfg)
     assert c["per_cell"] == pytest.approx(b.ALG_FLOPS_PER_CELL[key], rel=0.01)
+
+
+def test_double_float_flop_constant():
+    b = bench_module()
+    U = workloads.turbulent_state(64, seed=2, mach=5.0, sigma_rho=1.0, p_over_rho=1e-4, sedov=True).numpy()
+    cfg = oracle.config()
+    c = oracle.count_ops(U, 1 / 64, oracle.cfl_periodic(U, 1 / 64, cfg), cfg)
+    df = sum(b.DF_COST[k] * v for k, v in c["by_kind"].items())
+    assert df == pytest.approx(b.ALG_DF_FLOPS_PER_CELL["turb_minmod"], rel=0.01)

@@ -32,11 +32,15 @@ def _inputs(limiter, shape):
             workloads.white_velocity_state(shape, seed=1).numpy()]
 
 
+F64 = ["fp64", "df64"]  # native double, and double-float arithmetic on a double state
+
+
+@pytest.mark.parametrize("precision", F64)
 @pytest.mark.parametrize("limiter", ["minmod", "mc", "none"])
 @pytest.mark.parametrize("shape", [(32, 32, 32), (9, 13, 20), (5, 3, 37)])
-def test_fp64_one_step_matches_oracle(limiter, shape):
+def test_fp64_one_step_matches_oracle(precision, limiter, shape):
     dx = 1.0 / shape[2]
-    c = ctx("fp64", limiter)
+    c = ctx(precision, limiter)
     for U in _inputs(limiter, shape):
         dt = oracle.cfl_periodic(U, dx, ocfg(limiter))
         o = oracle.step_periodic(U, dx, dt, ocfg(limiter))
@@ -47,24 +51,26 @@ def test_fp64_one_step_matches_oracle(limiter, shape):
     check_clean(c)
 
 
-def test_fp64_cfl_matches_oracle_and_fused_is_bitwise():
+@pytest.mark.parametrize("precision", F64)
+def test_fp64_cfl_matches_oracle_and_fused_is_bitwise(precision):
     U = workloads.white_velocity_state((20, 24, 28), seed=3).numpy()
     dx = 1.0 / 28
-    c = ctx("fp64")
+    c = ctx(precision)
     d_gpu = cfl(c, U, dx)
-    assert d_gpu == pytest.approx(oracle.cfl_periodic(U, dx, ocfg()), rel=1e-14)
+    assert d_gpu == pytest.approx(oracle.cfl_periodic(U, dx, ocfg()), rel=1e-14 if precision == "fp64" else 1e-12)
     # the fused epilogue of a step on U0 gives the dt of U1; the standalone kernel on U1 the same bits
     U1, dnext = step_periodic(c, U, dx, 0.5 * d_gpu, dt_next=True)
     assert dnext == cfl(c, U1, dx)
     check_clean(c)
 
 
-def test_fp64_ten_steps_config1():
+@pytest.mark.parametrize("precision", F64)
+def test_fp64_ten_steps_config1(precision):
     """32^3, lognormal density (sigma 0.5), white velocities (0.3 c_s), P = 1, MinMod, CFL 0.8:
     ten steps with each side taking its own CFL dt."""
     U0 = workloads.white_velocity_state(32, seed=1).numpy()
     dx = 1.0 / 32
-    c = ctx("fp64")
+    c = ctx(precision)
     a = dev(U0)
     b = torch.empty_like(a)
     hist = torch.empty(11, dtype=torch.float64, device="cuda")
@@ -95,12 +101,13 @@ def test_graph_run_matches_eager_run_bitwise():
         np.testing.assert_array_equal(r[1], res[0][1])
 
 
-def test_ghosted_patch_equals_periodic_box():
+@pytest.mark.parametrize("precision", F64)
+def test_ghosted_patch_equals_periodic_box(precision):
     U = workloads.white_velocity_state((12, 16, 20), seed=4).numpy()
     dx = 1.0 / 20
     dt = 0.5 * oracle.cfl_periodic(U, dx, ocfg())
     Ug = oracle.fill_ghosts_periodic(U)
-    c = ctx("fp64")
+    c = ctx(precision)
     a = dev(Ug)
     out = torch.zeros_like(a)
     hy.hydro_step(c, hy.patch(a, 2, dx), hy.patch(out, 2, dx), dts(dt))
@@ -126,7 +133,7 @@ def _patch_batch(npatch, seed, precision, dtype, edges=(4, 8, 12, 16, 24), max_l
     return host, ins, outs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "fp32"])
 def test_batched_patches_match_oracle(precision):
     dtype = torch.float32 if precision == "fp32" else torch.float64
     host, ins, outs = _patch_batch(24, 5, precision, dtype)
@@ -138,7 +145,7 @@ def test_batched_patches_match_oracle(precision):
         hy.hydro_set_tuning(c, tile, 8)
         hy.hydro_step(c, ins, outs, dt, dn)
         torch.cuda.synchronize()
-        tol = TOL64 if precision == "fp64" else TOL32
+        tol = TOL64 if precision in F64 else TOL32
         for (Ug, d), po, dtp in zip(host, outs, dt_list):
             out = torch.stack(po.tensors).double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
             o = oracle.step_patch(Ug, d["dx"], dtp, ocfg())
@@ -183,7 +190,7 @@ def test_fp32_conservation_100_steps():
     check_clean(c)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "fp32"])
 def test_octs_match_oracle_and_uniform_grid(precision):
     dtype = torch.float32 if precision == "fp32" else torch.float64
     parent = workloads.white_velocity_state(16, seed=6)
@@ -198,7 +205,7 @@ def test_octs_match_oracle_and_uniform_grid(precision):
     hy.hydro_step_octs(c, gd, od, dx, dts(dt))
     torch.cuda.synchronize()
     full = oracle.step_periodic(U, dx, dt, ocfg())
-    tol = 1e-13 if precision == "fp64" else TOL32
+    tol = {"fp64": 1e-13, "df64": TOL64}.get(precision, TOL32)
     g = od.double().cpu().numpy()
     for k, (ox, oy, oz) in enumerate(origins):
         o = full[:, oz:oz + 2, oy:oy + 2, ox:ox + 2]
