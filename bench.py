@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--forms", default="all", help="comma list of extra forms, 'all' or 'none'")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--tuning", default="auto", help="'auto' (autotune) or '<tile id>:<zchunk>'")
+    p.add_argument("--npatch", type=int, default=4096, help="patches of the batched form")
+    p.add_argument("--ngroups", type=int, default=262144, help="oct groups of the batched form")
+    p.add_argument("--adj-n", type=int, default=64, help="grid edge of the adjoint form")
     return p.parse_args()
 
 
@@ -192,7 +195,7 @@ def tune(hy, ctx, a, b, dx, dts):
         t, z = (int(x) for x in TUNING.split(":"))
         hy.hydro_set_tuning(ctx, t, z)
     t, z = hy.hydro_get_tuning(ctx)
-    return {"tile": "%dx%d" % ({0: (16, 16), 1: (32, 8), 2: (8, 8), 3: (32, 16)}[t]), "zchunk": z}
+    return {"tile": {0: "16x16", 1: "32x8", 2: "8x8", 3: "32x16", 4: "16x16/1 block per SM"}[t], "zchunk": z}
 
 
 def time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream, per_launch=True):
@@ -267,6 +270,7 @@ def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, 
     if graph:
         hist = torch.empty(steps + 1, dtype=torch.float64, device="cuda")
         pa, pb = hy.patch(a, 0, dx), hy.patch(b, 0, dx)
+        tuning = tune(hy, ctx, a, b, dx, hist)
         hy.hydro_run(ctx, pa, pb, steps, hist, use_graph=True)  # capture + first replay (warm-up)
         torch.cuda.synchronize()
         a.copy_(turbulent(n, precision, "cuda", seed=seed, mach=mach, sigma=sigma, p_over_rho=p_over_rho,
@@ -280,7 +284,8 @@ def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, 
         ms = t0.elapsed_time(t1)
         rc, bits = hy.hydro_get_error(ctx)
         out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
-               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "graph": True, "error_bits": bits}
+               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "graph": True, "error_bits": bits,
+               "tuning": tuning}
     else:
         dts = torch.empty(warmup + steps + 1, dtype=torch.float64, device="cuda")
         tuning = tune(hy, ctx, a, b, dx, dts)
@@ -378,6 +383,7 @@ def form_adjoint(hy, precision, n=64, nsteps=40):
     dt = torch.empty(1, dtype=torch.float64, device="cuda")
     hy.hydro_cfl_dt(ctx, hy.patch(U, 0, dx), dt)
     pU, pV, pL, pM = (hy.patch(t, 0, dx) for t in (U, V, L, M))
+    hy.hydro_autotune(ctx, pU, pV, dt)  # the forward at its best tile shape for this grid
     reps = 50
     for _ in range(5):
         hy.hydro_step(ctx, pU, pV, dt)
@@ -413,8 +419,9 @@ def form_adjoint(hy, precision, n=64, nsteps=40):
     torch.cuda.synchronize()
     fwd40, grad40 = t0.elapsed_time(t1), t1.elapsed_time(t2)
     rc, bits = hy.hydro_get_error(ctx)
+    t, z = hy.hydro_get_tuning(ctx)
     hy.hydro_finalize(ctx)
-    return {"n": n, "forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_over_forward": a_ms / f_ms,
+    return {"n": n, "forward_tuning": [t, z], "forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_over_forward": a_ms / f_ms,
             "steps40_forward_ms": fwd40, "steps40_forward_plus_gradient_ms": grad40,
             "gradient_over_forward_40": grad40 / fwd40, "error_bits": bits}
 
@@ -571,10 +578,11 @@ def main():
                 elif f in ("fp64", "df64"):
                     extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod")
                 elif f == "batched":
-                    extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2)
+                    extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch,
+                                                          ngroups=args.ngroups)
                 elif f == "adjoint":
-                    extra["adjoint_fp64"] = form_adjoint(hy, "fp64")
-                    extra["adjoint_fp32"] = form_adjoint(hy, "fp32")
+                    extra["adjoint_fp64"] = form_adjoint(hy, "fp64", n=args.adj_n)
+                    extra["adjoint_fp32"] = form_adjoint(hy, "fp32", n=args.adj_n)
                 elif f == "graph1024":
                     extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                                sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,

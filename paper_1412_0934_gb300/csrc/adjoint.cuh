@@ -69,7 +69,7 @@ __device__ __forceinline__ void adj_predict(AdjShared<typename Pol::R, TX, TY>& 
     dqz[v] = limited_code(c - sm.q[sq0][v][cj][ci], sm.q[sq2][v][cj][ci] - c, prm.limiter, cz);
     code |= (cx << (2 * v)) | (cy << (2 * (5 + v))) | (cz << (2 * (10 + v)));
   }
-  hancock(q0, dqx, dqy, dqz, (R)prm.gamma, hdt, qh);
+  hancock(q0, dqx, dqy, dqz, kc<R>(prm, K_GAMMA), hdt, qh);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     sm.qh[sp][v][j + 1][i + 1] = qh[v];
@@ -100,10 +100,10 @@ __device__ __forceinline__ void adj_face_xy(AdjShared<typename Pol::R, TX, TY>& 
     lL[v] = R(0);
     lR[v] = R(0);
   }
-  const R rf = (R)prm.rho_floor, pf = (R)prm.p_floor;
+  const R rf = kc<R>(prm, K_RHOF), pf = kc<R>(prm, K_PF);
   floor_state(qL, rf, pf);
   floor_state(qR, rf, pf);
-  hllc_adj<D>(qL, qR, (R)prm.gamma, (R)(1.0 / (prm.gamma - 1.0)), lF, lL, lR);
+  hllc_adj<D>(qL, qR, kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), lF, lL, lR);
   floor_mask(pL, lL, rf, pf);
   floor_mask(pR, lR, rf, pf);
 }
@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, P.nz);
   const R hdt = (R)(0.5 * dt / P.dx), dtdx = (R)(dt / P.dx);
-  const R gamma = (R)prm.gamma, igm1 = (R)(1.0 / (prm.gamma - 1.0));
-  const R rf = (R)prm.rho_floor, pf = (R)prm.p_floor;
+  const R gamma = kc<R>(prm, K_GAMMA), igm1 = kc<R>(prm, K_IGM1);
+  const R rf = kc<R>(prm, K_RHOF), pf = kc<R>(prm, K_PF);
   unsigned flags = 0;
   for (int c = tid; c < QW; c += NT) sm.xoff[c] = wrapi(x0 - 2 + c, P.nx);
   for (int c = tid; c < QH; c += NT) sm.yoff[c] = (long long)wrapi(y0 - 2 + c, P.ny) * P.isy;

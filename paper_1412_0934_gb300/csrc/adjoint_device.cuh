@@ -247,7 +247,7 @@ __device__ __forceinline__ void recover_adj(const R U[5], const Params& P, const
   const R ir = rcp_(rho);
   const R K = (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
   const R kin = R(0.5) * K * ir;
-  const R gm1 = (R)(P.gamma - 1.0);
+  const R gm1 = kc<R>(P, K_GM1);
   const R praw = gm1 * (U[4] - kin);
   const R lpr = (praw < (R)P.p_floor) ? R(0) : lq[4];
   lU[4] = gm1 * lpr;

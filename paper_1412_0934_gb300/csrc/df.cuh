@@ -52,6 +52,15 @@ __device__ __forceinline__ df operator*(const df& x, const df& y) {
   return fast_two_sum(c.h, c.l + t);
 }
 
+// Exact scaling by a power of two, and double-word x float (TwoProd + one FMA + Fast2Sum).
+__device__ __forceinline__ df half_(const df& x) { return df(0.5f * x.h, 0.5f * x.l); }
+__device__ __forceinline__ df twice_(const df& x) { return df(2.f * x.h, 2.f * x.l); }
+__device__ __forceinline__ df mulf_(const df& x, float f) {
+  const df c = two_prod(x.h, f);
+  return fast_two_sum(c.h, fmaf(x.l, f, c.l));
+}
+__device__ __forceinline__ df rabs(const df& x) { return x.h < 0.f ? -x : x; }
+
 // Reciprocal: r0 from the SFU, then r = r0 + r0 (1 - y r0) with the residual formed exactly.
 __device__ __forceinline__ df rcp_(const df& y) {
   float r0;

@@ -231,7 +231,7 @@ int hydro_init(hydro_ctx** ctx, const hydro_config* cfg) {
   if (!hydro::ops_for(cfg->precision)) return HYDRO_ERR_ARG;
   hydro_ctx* c = new hydro_ctx();
   c->cfg = *cfg;
-  c->prm = hydro::Params{cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter};
+  c->prm = hydro::make_params(cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter);
   c->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   c->ops = hydro::ops_for(cfg->precision);
   if (cudaGetDevice(&c->device) != cudaSuccess ||

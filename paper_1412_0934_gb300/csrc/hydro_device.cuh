@@ -21,7 +21,27 @@ constexpr int NG = 2;  // ghost layers of the stencil
 struct Params {
   double gamma, cfl, rho_floor, p_floor;
   int limiter;
+  // Derived constants, precomputed on the host so kernels never convert or divide them:
+  // index 0 gamma, 1 1/(gamma-1), 2 gamma-1, 3 rho_floor, 4 p_floor; as doubles, as floats,
+  // and as (hi, lo) float pairs.
+  double kd[5];
+  float kf[5];
+  float kh[5], kl[5];
 };
+
+enum { K_GAMMA = 0, K_IGM1 = 1, K_GM1 = 2, K_RHOF = 3, K_PF = 4 };
+
+inline Params make_params(double gamma, double cfl, double rho_floor, double p_floor, int limiter) {
+  Params p{gamma, cfl, rho_floor, p_floor, limiter, {}, {}, {}, {}};
+  const double k[5] = {gamma, 1.0 / (gamma - 1.0), gamma - 1.0, rho_floor, p_floor};
+  for (int i = 0; i < 5; ++i) {
+    p.kd[i] = k[i];
+    p.kf[i] = (float)k[i];
+    p.kh[i] = (float)k[i];
+    p.kl[i] = (float)(k[i] - (double)p.kh[i]);
+  }
+  return p;
+}
 
 // ------------------------------------------------------------------ small helpers
 template <class R>
@@ -44,6 +64,34 @@ __device__ __forceinline__ float div_(float a, float b) { return a * rcp_(b); }
 __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+
+// Constant i of the parameters in arithmetic type R.
+template <class R>
+struct KC;
+template <>
+struct KC<float> {
+  static __device__ __forceinline__ float get(const Params& P, int i) { return P.kf[i]; }
+};
+template <>
+struct KC<double> {
+  static __device__ __forceinline__ double get(const Params& P, int i) { return P.kd[i]; }
+};
+template <>
+struct KC<df> {
+  static __device__ __forceinline__ df get(const Params& P, int i) { return df(P.kh[i], P.kl[i]); }
+};
+template <class R>
+__device__ __forceinline__ R kc(const Params& P, int i) {
+  return KC<R>::get(P, i);
+}
+
+// 0.5 x, 2 x and x f for a float constant f (exact scalings; df overloads in df.cuh).
+__device__ __forceinline__ float half_(float x) { return 0.5f * x; }
+__device__ __forceinline__ double half_(double x) { return 0.5 * x; }
+__device__ __forceinline__ float twice_(float x) { return 2.f * x; }
+__device__ __forceinline__ double twice_(double x) { return 2.0 * x; }
+__device__ __forceinline__ float mulf_(float x, float f) { return x * f; }
+__device__ __forceinline__ double mulf_(double x, float f) { return x * (double)f; }
 
 __device__ __forceinline__ float shfl_xor_(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double shfl_xor_(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
@@ -91,10 +139,10 @@ __device__ __forceinline__ bool prod_nonpos(float a, float b) { return a * b <= 
 // None: the centred difference (a+b)/2.
 template <class R>
 __device__ __forceinline__ R limited(R a, R b, int lim) {
-  if (lim == HYDRO_NOLIMIT) return R(0.5) * (a + b);
+  if (lim == HYDRO_NOLIMIT) return half_(a + b);
   if (prod_nonpos(a, b)) return R(0);
   if (lim == HYDRO_MINMOD) return abs_le(a, b) ? a : b;
-  R ta = R(2) * a, tb = R(2) * b, m = R(0.5) * (a + b);
+  R ta = twice_(a), tb = twice_(b), m = half_(a + b);
   R best = ta;
   if (abs_lt(tb, best)) best = tb;
   if (abs_lt(m, best)) best = m;
@@ -169,7 +217,7 @@ __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R
   const R irK = left ? irL : irR;
   const R SK = left ? SL : SR;
   const R mK = left ? mL : mR;
-  const R EK = pK * inv_gm1 + R(0.5) * rK * keK;
+  const R EK = pK * inv_gm1 + half_(rK * keK);
   // Star state of side K: density r* = m_K/(S_K - S*), velocity S*, pressure p* = p_K + m_K (S* - u_K),
   // energy E* = r* (E_K/rho_K + (S* - u_K)(S* + p_K/m_K)).  F*_K = F_K + S_K (U*_K - U_K) equals the
   // physical flux of that state, so one flux formula serves every branch.
@@ -247,7 +295,7 @@ struct PolF64 {
     const double kin = 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir;
     const double eint = U[4] - kin;
     if (eint < 0.0) flags |= HYDRO_EBIT_P_FLOOR;
-    double p = (P.gamma - 1.0) * eint;
+    double p = P.kd[K_GM1] * eint;
     if (!(isfinite(p) && isfinite(rho))) flags |= HYDRO_EBIT_NONFINITE;
     q[0] = rho;
     q[1] = U[1] * ir;
@@ -267,7 +315,7 @@ struct PolF32 {
   // cancellation between E and the kinetic energy loses nothing beyond the final rounding.
   static __device__ __forceinline__ void recover(const float U[5], const Params& P, float q[5], unsigned& flags) {
     float rho = U[0];
-    const float rf = (float)P.rho_floor;
+    const float rf = P.kf[K_RHOF];
     if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
     const float ir = __frcp_rn(rho);
     const float mx = U[1], my = U[2], mz = U[3];
@@ -288,9 +336,9 @@ struct PolF32 {
     const float de = two_sum_err(U[4], -hk, d);
     const float eint = d + (de - 0.5f * kl);
     if (eint < 0.f) flags |= HYDRO_EBIT_P_FLOOR;
-    float p = (float)(P.gamma - 1.0) * eint;
+    float p = P.kf[K_GM1] * eint;
     if (!(isfinite(p) && isfinite(rho))) flags |= HYDRO_EBIT_NONFINITE;
-    const float pf = (float)P.p_floor;
+    const float pf = P.kf[K_PF];
     q[0] = rho;
     q[1] = mx * ir;
     q[2] = my * ir;
@@ -301,16 +349,16 @@ struct PolF32 {
   // CFL speed of a stored state: plain float recovery (the dt only needs float accuracy).
   static __device__ __forceinline__ float speed(const float U[5], const Params& P, unsigned& flags) {
     float rho = U[0];
-    const float rf = (float)P.rho_floor;
+    const float rf = P.kf[K_RHOF];
     if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
     const float ir = rcp_(rho);
     const float u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
     const float eint = U[4] - 0.5f * rho * ((u * u + v * v) + w * w);
-    float p = (float)(P.gamma - 1.0) * eint;
+    float p = P.kf[K_GM1] * eint;
     if (!(isfinite(p) && isfinite(rho))) flags |= HYDRO_EBIT_NONFINITE;
-    const float pf = (float)P.p_floor;
+    const float pf = P.kf[K_PF];
     p = p < pf ? pf : p;
-    const float c = rsqrt_((float)P.gamma * p * ir);
+    const float c = rsqrt_(P.kf[K_GAMMA] * p * ir);
     return ((fabsf(u) + fabsf(v)) + fabsf(w)) + 3.0f * c;
   }
 };
@@ -328,11 +376,11 @@ struct PolMixed {
     const double K = fma(U[3], U[3], fma(U[2], U[2], U[1] * U[1]));
     const double eint = fma(-0.5 * K, ir, U[4]);
     if (eint < 0.0) flags |= HYDRO_EBIT_P_FLOOR;
-    float p = (float)((P.gamma - 1.0) * eint);
+    float p = (float)(P.kd[K_GM1] * eint);
     const float rhof = (float)rho;
     if (!(isfinite(p) && isfinite(rhof))) flags |= HYDRO_EBIT_NONFINITE;
     const float irf = (float)ir;
-    const float pf = (float)P.p_floor;
+    const float pf = P.kf[K_PF];
     q[0] = rhof;
     q[1] = (float)U[1] * irf;
     q[2] = (float)U[2] * irf;
@@ -352,16 +400,16 @@ struct PolDF {
   // The same recovery as PolF64, in double-float from the double state.
   static __device__ __forceinline__ void recover(const double U[5], const Params& P, df q[5], unsigned& flags) {
     df rho(U[0]);
-    const df rf(P.rho_floor);
+    const df rf = kc<df>(P, K_RHOF);
     if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
     const df ir = rcp_(rho);
     const df mx(U[1]), my(U[2]), mz(U[3]);
-    const df kin = df(0.5f) * ((mx * mx + my * my) + mz * mz) * ir;
+    const df kin = half_(((mx * mx + my * my) + mz * mz) * ir);
     const df eint = df(U[4]) - kin;
     if (cmp_neg(eint)) flags |= HYDRO_EBIT_P_FLOOR;
-    df p = df(P.gamma - 1.0) * eint;
+    df p = kc<df>(P, K_GM1) * eint;
     if (!(isfinite(p.h) && isfinite(rho.h))) flags |= HYDRO_EBIT_NONFINITE;
-    const df pf(P.p_floor);
+    const df pf = kc<df>(P, K_PF);
     q[0] = rho;
     q[1] = mx * ir;
     q[2] = my * ir;
@@ -380,7 +428,7 @@ struct PolDF {
 template <class R>
 __device__ __forceinline__ R cfl_speed(const R q[5], R gamma) {
   const R c = rsqrt_(gamma * q[4] * rcp_(q[0]));
-  return ((rabs(q[1]) + rabs(q[2])) + rabs(q[3])) + R(3) * c;
+  return ((rabs(q[1]) + rabs(q[2])) + rabs(q[3])) + mulf_(c, 3.f);
 }
 
 // CFL speed of a stored state (the step's epilogue and the standalone dt kernel share it, so
@@ -388,17 +436,17 @@ __device__ __forceinline__ R cfl_speed(const R q[5], R gamma) {
 __device__ __forceinline__ double PolF64::speed(const double U[5], const Params& P, unsigned& flags) {
   double q[5];
   recover(U, P, q, flags);
-  return cfl_speed(q, P.gamma);
+  return cfl_speed(q, P.kd[K_GAMMA]);
 }
 __device__ __forceinline__ float PolMixed::speed(const double U[5], const Params& P, unsigned& flags) {
   float q[5];
   recover(U, P, q, flags);
-  return cfl_speed(q, (float)P.gamma);
+  return cfl_speed(q, P.kf[K_GAMMA]);
 }
 __device__ __forceinline__ df PolDF::speed(const double U[5], const Params& P, unsigned& flags) {
   df q[5];
   recover(U, P, q, flags);
-  return cfl_speed(q, df(P.gamma));
+  return cfl_speed(q, kc<df>(P, K_GAMMA));
 }
 
 }  // namespace hydro

@@ -22,10 +22,13 @@ struct HostTileRec {
   int patch, x0, y0, z0;
 };
 
-// Compiled tile shapes of the step kernels (TX x TY columns per block).
-constexpr int kNumTiles = 4;
-constexpr int kTileX[kNumTiles] = {16, 32, 8, 32};
-constexpr int kTileY[kNumTiles] = {16, 8, 8, 16};
+// Compiled tile shapes of the step kernels (TX x TY columns per block) and the resident blocks
+// per SM their register allocation targets (0: the policy default, 2 x 256 threads for 8-byte
+// arithmetic, 3 x 256 for float; 1: a whole SM's registers for one block, no spills).
+constexpr int kNumTiles = 5;
+constexpr int kTileX[kNumTiles] = {16, 32, 8, 32, 16};
+constexpr int kTileY[kNumTiles] = {16, 8, 8, 16, 16};
+constexpr int kTileMinBlocks[kNumTiles] = {0, 0, 0, 0, 1};
 
 struct KernelOps {
   // Uniform periodic grid (npatch == 1, gin == 0).

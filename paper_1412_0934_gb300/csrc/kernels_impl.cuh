@@ -10,46 +10,46 @@
 namespace hydro {
 
 // ------------------------------------------------------------------ step launchers
-template <class Pol, int TX, int TY>
+template <class Pol, int TX, int TY, int MINB>
 cudaError_t launch_uniform_t(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
                              unsigned* err, cudaStream_t s) {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
-  k_step_uniform<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
+  k_step_uniform<Pol, TX, TY, MINB><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
   return cudaGetLastError();
 }
 
-template <class Pol, int TX, int TY>
+template <class Pol, int TX, int TY, int MINB>
 cudaError_t launch_batched_t(const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles, int* d_counter,
                              const Params& prm, const double* dt, double* dt_next, int zchunk, unsigned* err, int grid,
                              cudaStream_t s) {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_batched<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_step_batched<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(
+  k_step_batched<Pol, TX, TY, MINB><<<grid, TX * TY, smem, s>>>(
       reinterpret_cast<const PatchIO<typename Pol::S>*>(d_patches), reinterpret_cast<const TileRec*>(d_tiles), ntiles,
       d_counter, prm, dt, dt_next, zchunk, err);
   return cudaGetLastError();
 }
 
-template <class Pol, int TX, int TY>
+template <class Pol, int TX, int TY, int MINB>
 int blocks_per_sm_t() {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
-  cudaFuncSetAttribute(k_step_batched<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<Pol, TX, TY>, TX * TY, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<Pol, TX, TY, MINB>, TX * TY, smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
@@ -58,10 +58,11 @@ template <class Pol>
 cudaError_t launch_uniform(int tile, const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next,
                            int zchunk, unsigned* err, cudaStream_t s) {
   switch (tile) {
-    case 0: return launch_uniform_t<Pol, kTileX[0], kTileY[0]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 1: return launch_uniform_t<Pol, kTileX[1], kTileY[1]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 2: return launch_uniform_t<Pol, kTileX[2], kTileY[2]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 3: return launch_uniform_t<Pol, kTileX[3], kTileY[3]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 0: return launch_uniform_t<Pol, kTileX[0], kTileY[0], kTileMinBlocks[0]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 1: return launch_uniform_t<Pol, kTileX[1], kTileY[1], kTileMinBlocks[1]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 2: return launch_uniform_t<Pol, kTileX[2], kTileY[2], kTileMinBlocks[2]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 3: return launch_uniform_t<Pol, kTileX[3], kTileY[3], kTileMinBlocks[3]>(P, prm, dt, dt_next, zchunk, err, s);
+    case 4: return launch_uniform_t<Pol, kTileX[4], kTileY[4], kTileMinBlocks[4]>(P, prm, dt, dt_next, zchunk, err, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -71,10 +72,11 @@ cudaError_t launch_batched(int tile, const HostPatchIO* d_patches, const HostTil
                            int* d_counter, const Params& prm, const double* dt, double* dt_next, int zchunk,
                            unsigned* err, int grid, cudaStream_t s) {
   switch (tile) {
-    case 0: return launch_batched_t<Pol, kTileX[0], kTileY[0]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 1: return launch_batched_t<Pol, kTileX[1], kTileY[1]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 2: return launch_batched_t<Pol, kTileX[2], kTileY[2]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 3: return launch_batched_t<Pol, kTileX[3], kTileY[3]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 0: return launch_batched_t<Pol, kTileX[0], kTileY[0], kTileMinBlocks[0]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 1: return launch_batched_t<Pol, kTileX[1], kTileY[1], kTileMinBlocks[1]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 2: return launch_batched_t<Pol, kTileX[2], kTileY[2], kTileMinBlocks[2]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 3: return launch_batched_t<Pol, kTileX[3], kTileY[3], kTileMinBlocks[3]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
+    case 4: return launch_batched_t<Pol, kTileX[4], kTileY[4], kTileMinBlocks[4]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -82,10 +84,11 @@ cudaError_t launch_batched(int tile, const HostPatchIO* d_patches, const HostTil
 template <class Pol>
 int batched_blocks_per_sm(int tile) {
   switch (tile) {
-    case 0: return blocks_per_sm_t<Pol, kTileX[0], kTileY[0]>();
-    case 1: return blocks_per_sm_t<Pol, kTileX[1], kTileY[1]>();
-    case 2: return blocks_per_sm_t<Pol, kTileX[2], kTileY[2]>();
-    case 3: return blocks_per_sm_t<Pol, kTileX[3], kTileY[3]>();
+    case 0: return blocks_per_sm_t<Pol, kTileX[0], kTileY[0], kTileMinBlocks[0]>();
+    case 1: return blocks_per_sm_t<Pol, kTileX[1], kTileY[1], kTileMinBlocks[1]>();
+    case 2: return blocks_per_sm_t<Pol, kTileX[2], kTileY[2], kTileMinBlocks[2]>();
+    case 3: return blocks_per_sm_t<Pol, kTileX[3], kTileY[3], kTileMinBlocks[3]>();
+    case 4: return blocks_per_sm_t<Pol, kTileX[4], kTileY[4], kTileMinBlocks[4]>();
   }
   return 1;
 }
@@ -225,8 +228,8 @@ __global__ void __launch_bounds__(32 * kOctWarps) k_octs(const typename Pol::S* 
   }
   const R hdt = (R)(0.5 * dt / dx);
   const R dtdx = (R)(dt / dx);
-  const R gamma = (R)prm.gamma, igm1 = (R)(1.0 / (prm.gamma - 1.0));
-  const R rf = (R)prm.rho_floor, pf = (R)prm.p_floor;
+  const R gamma = kc<R>(prm, K_GAMMA), igm1 = kc<R>(prm, K_IGM1);
+  const R rf = kc<R>(prm, K_RHOF), pf = kc<R>(prm, K_PF);
   unsigned flags = 0;
   for (long long g = (long long)blockIdx.x * kOctWarps + w; g < ngroups; g += (long long)gridDim.x * kOctWarps) {
     const long long base = g * 216;
@@ -277,8 +280,8 @@ __global__ void __launch_bounds__(32 * kOctWarps) k_octs(const typename Pol::S* 
       R qL[5], qR[5], F[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        qL[v] = sm.qh[w][v][eL] + R(0.5) * sm.sl[w][d][v][eL];
-        qR[v] = sm.qh[w][v][eR] - R(0.5) * sm.sl[w][d][v][eR];
+        qL[v] = sm.qh[w][v][eL] + half_(sm.sl[w][d][v][eL]);
+        qR[v] = sm.qh[w][v][eR] - half_(sm.sl[w][d][v][eR]);
       }
       floor_state(qL, rf, pf);
       floor_state(qR, rf, pf);

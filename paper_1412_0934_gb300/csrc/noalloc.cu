@@ -113,7 +113,7 @@ extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_p
   if (rc) return rc;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HYDRO_ERR_CUDA;
   const hydro::KernelOps& ops = *hydro::ops_for(cfg->precision);
-  const hydro::Params prm{cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter};
+  const hydro::Params prm = hydro::make_params(cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter);
   cudaStream_t st = static_cast<cudaStream_t>(cfg->cuda_stream);
   unsigned* err = error_bits_dev ? error_bits_dev : s->error;
   {

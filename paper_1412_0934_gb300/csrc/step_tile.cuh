@@ -11,6 +11,8 @@
 //      folds the CFL speed of the new state into a running maximum
 // Global memory is read once per cell per plane (halo re-reads come from L2) and written once.
 #pragma once
+#include <type_traits>
+
 #include "hydro_device.cuh"
 
 namespace hydro {
@@ -125,7 +127,7 @@ __device__ __forceinline__ void predict_cell(TileShared<Pol, TX, TY>& sm, int i,
     dqy[v] = limited(c[v] - ym[v], yp[v] - c[v], prm.limiter);
     dqz[v] = limited(c[v] - zm[v], zp[v] - c[v], prm.limiter);
   }
-  hancock(c, dqx, dqy, dqz, (R)prm.gamma, hdt, qh);
+  hancock(c, dqx, dqy, dqz, kc<R>(prm, K_GAMMA), hdt, qh);
   sm.qh.st(j + 1, i + 1, qh);
   sm.sx.st(j + 1, i + 1, dqx);
   sm.sy.st(j + 1, i + 1, dqy);
@@ -151,12 +153,35 @@ __device__ __forceinline__ void face_flux(TileShared<Pol, TX, TY>& sm, int i, in
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    qL[v] = qL[v] + R(0.5) * sL[v];
-    qR[v] = qR[v] - R(0.5) * sR[v];
+    qL[v] = qL[v] + half_(sL[v]);
+    qR[v] = qR[v] - half_(sR[v]);
   }
-  floor_state(qL, (R)prm.rho_floor, (R)prm.p_floor);
-  floor_state(qR, (R)prm.rho_floor, (R)prm.p_floor);
-  hllc<D>(qL, qR, (R)prm.gamma, (R)(1.0 / (prm.gamma - 1.0)), F);
+  floor_state(qL, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+  floor_state(qR, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+  hllc<D>(qL, qR, kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), F);
+}
+
+// The same for a runtime direction d (one inlined copy serves both x and y faces).
+template <class Pol, int TX, int TY>
+__device__ __forceinline__ void face_flux_dyn(TileShared<Pol, TX, TY>& sm, int d, int i, int j, const Params& prm,
+                                              typename Pol::R F[5]) {
+  using R = typename Pol::R;
+  const int li = i + 1, lj = j + 1;
+  const int ri = li + (d == 0), rj = lj + (d == 1);
+  R qL[5], qR[5], sL[5], sR[5];
+  sm.qh.ld(lj, li, qL);
+  sm.qh.ld(rj, ri, qR);
+  const auto& sl = d == 0 ? sm.sx : sm.sy;
+  sl.ld(lj, li, sL);
+  sl.ld(rj, ri, sR);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = qL[v] + half_(sL[v]);
+    qR[v] = qR[v] - half_(sR[v]);
+  }
+  floor_state(qL, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+  floor_state(qR, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+  hllc_dyn(d, qL, qR, kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), F);
 }
 
 // Advances the tile; returns (through smax) the largest CFL speed of the updated cells.
@@ -183,10 +208,13 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
   }
   __syncthreads();
 
+  auto plane_offset = [&](int z) {
+    const int zi = periodic ? wrapi(z, P.nz) : z + 2;
+    return (long long)zi * P.isz;
+  };
   auto load_plane = [&](int z) {
     const int slot = ring_slot(z);
-    const int zi = periodic ? wrapi(z, P.nz) : z + 2;
-    const long long zo = (long long)zi * P.isz;
+    const long long zo = plane_offset(z);
     for (int c = tid; c < QN; c += NT) {
       const int cy = c / QW, cx = c - cy * QW;
       const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
@@ -198,68 +226,142 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
       sm.q[slot].st(cy, cx, q);
     }
   };
+  // Float state: the next plane's loads are issued into registers one iteration early, so their
+  // latency overlaps the predictor, flux and update phases of the current plane.
+  constexpr bool kPrefetch = false;
+  constexpr bool kCompact = std::is_same<R, df>::value;  // double-float arithmetic
+  constexpr int NPF = kPrefetch ? (QN + NT - 1) / NT : 1;
+  S pre[NPF][5];
+  auto prefetch = [&](int z) {
+    const long long zo = plane_offset(z);
+#pragma unroll
+    for (int k = 0; k < NPF; ++k) {
+      const int c = tid + k * NT;
+      if (c < QN) {
+        const int cy = c / QW, cx = c - cy * QW;
+        const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) pre[k][v] = __ldg(P.in[v] + a);
+      }
+    }
+  };
+  auto commit = [&](int z) {
+    const int slot = ring_slot(z);
+#pragma unroll
+    for (int k = 0; k < NPF; ++k) {
+      const int c = tid + k * NT;
+      if (c < QN) {
+        const int cy = c / QW, cx = c - cy * QW;
+        R q[5];
+        Pol::recover(pre[k], prm, q, flags);
+        sm.q[slot].st(cy, cx, q);
+      }
+    }
+  };
 
   const R hdt = (R)(0.5 * dt / P.dx);
   const R dtdx = (R)(dt / P.dx);
   const int gx = x0 + ti, gy = y0 + tj;
   const bool own = (gx < P.nx) && (gy < P.ny);
-  const R gamma = (R)prm.gamma;
+  const R gamma = kc<R>(prm, K_GAMMA);
 
-  R LzPrev[5], FzPrev[5], dFprev[5], Fz[5], dF[5];
+  // Carried across planes: the lower z state of the next face, and for the plane awaiting its
+  // update, acc = (x and y flux differences) - (flux through its lower z face).
+  R LzPrev[5], acc[5], Fz[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { LzPrev[v] = FzPrev[v] = dFprev[v] = Fz[v] = dF[v] = R(0); }
+  for (int v = 0; v < 5; ++v) { LzPrev[v] = acc[v] = Fz[v] = R(0); }
 
   load_plane(z0 - 2);
   load_plane(z0 - 1);
+  if constexpr (kPrefetch) prefetch(z0);
   for (int p = z0 - 1; p <= z1; ++p) {
     // ---- A
-    load_plane(p + 1);
+    if constexpr (kPrefetch) {
+      commit(p + 1);
+      if (p + 2 <= z1 + 1) prefetch(p + 2);
+    } else {
+      load_plane(p + 1);
+    }
     __syncthreads();
-    // ---- B
+    // ---- B: the interior cell of this thread (with its z faces), then the ring cells
     const int sm1 = ring_slot(p - 1), s0 = ring_slot(p), sp1 = ring_slot(p + 1);
-    {
-      R qh[5], dqz[5];
-      predict_cell(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
+    const bool xy = p >= z0 && p < z1;
+    auto z_faces = [&](const R qh[5], const R dqz[5]) {
       R Lz[5], Rz[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        Lz[v] = qh[v] + R(0.5) * dqz[v];
-        Rz[v] = qh[v] - R(0.5) * dqz[v];
+        Lz[v] = qh[v] + half_(dqz[v]);
+        Rz[v] = qh[v] - half_(dqz[v]);
       }
-      floor_state(Lz, (R)prm.rho_floor, (R)prm.p_floor);
-      floor_state(Rz, (R)prm.rho_floor, (R)prm.p_floor);
-      if (p >= z0) hllc<2>(LzPrev, Rz, gamma, (R)(1.0 / (prm.gamma - 1.0)), Fz);
+      floor_state(Lz, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+      floor_state(Rz, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+      if (p >= z0) hllc<2>(LzPrev, Rz, gamma, kc<R>(prm, K_IGM1), Fz);
 #pragma unroll
       for (int v = 0; v < 5; ++v) LzPrev[v] = Lz[v];
-    }
-    if (p >= z0 && p < z1 && tid < 2 * (TX + TY)) {
-      int ri, rj;
-      const int r = tid;
-      if (r < TX) { ri = r; rj = -1; }
-      else if (r < 2 * TX) { ri = r - TX; rj = TY; }
-      else if (r < 2 * TX + TY) { ri = -1; rj = r - 2 * TX; }
-      else { ri = TX; rj = r - 2 * TX - TY; }
-      R qh[5], dqz[5];
-      predict_cell(sm, ri, rj, sm1, s0, sp1, prm, hdt, qh, dqz);
-    }
-    __syncthreads();
-    // ---- C
-    if (p >= z0 && p < z1) {
-      R F[5];
-      face_flux<0>(sm, ti, tj, prm, F);
-      sm.fx.st(tj, ti + 1, F);
-      face_flux<1>(sm, ti, tj, prm, F);
-      sm.fy.st(tj + 1, ti, F);
-      if (tid < TY) {
-        face_flux<0>(sm, -1, tid, prm, F);
-        sm.fx.st(tid, 0, F);
-      } else if (tid >= 32 && tid < 32 + TX) {
-        face_flux<1>(sm, tid - 32, -1, prm, F);
-        sm.fy.st(0, tid - 32, F);
+    };
+    auto ring_cell = [&](int r, int& ci, int& cj) {
+      if (r < TX) { ci = r; cj = -1; }
+      else if (r < 2 * TX) { ci = r - TX; cj = TY; }
+      else if (r < 2 * TX + TY) { ci = -1; cj = r - 2 * TX; }
+      else { ci = TX; cj = r - 2 * TX - TY; }
+    };
+    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+    if constexpr (kCompact) {
+      // One call site each for the predictor and the x/y face flux: double-float code is large
+      // enough that several inlined copies overflow the instruction cache.
+      for (int c = tid; c < (xy ? NT + 2 * (TX + TY) : NT); c += NT) {
+        int ci = ti, cj = tj;
+        if (c >= NT) ring_cell(c - NT, ci, cj);
+        R qh[5], dqz[5];
+        predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
+        if (c < NT) z_faces(qh, dqz);
       }
+      __syncthreads();
+      if (xy) {
+        for (int f = tid; f < NXF + NYF; f += NT) {
+          int d, i, j;
+          if (f < NXF) { d = 0; i = f % (TX + 1) - 1; j = f / (TX + 1); }
+          else { d = 1; i = (f - NXF) % TX; j = (f - NXF) / TX - 1; }
+          R F[5];
+          face_flux_dyn(sm, d, i, j, prm, F);
+          if (d == 0) sm.fx.st(j, i + 1, F);
+          else sm.fy.st(j + 1, i, F);
+        }
+      }
+      __syncthreads();
+    } else {
+      {
+        R qh[5], dqz[5];
+        predict_cell(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
+        z_faces(qh, dqz);
+      }
+      if (xy && tid < 2 * (TX + TY)) {
+        int ci, cj;
+        ring_cell(tid, ci, cj);
+        R qh[5], dqz[5];
+        predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
+      }
+      __syncthreads();
+      // ---- C: the x face on this column's right and the y face above it; the first warps also
+      // take the faces on the tile's left and bottom edges
+      if (xy) {
+        R F[5];
+        face_flux<0>(sm, ti, tj, prm, F);
+        sm.fx.st(tj, ti + 1, F);
+        face_flux<1>(sm, ti, tj, prm, F);
+        sm.fy.st(tj + 1, ti, F);
+        if (tid < TY) {
+          face_flux<0>(sm, -1, tid, prm, F);
+          sm.fx.st(tid, 0, F);
+        } else if (tid >= 32 && tid < 32 + TX) {
+          face_flux<1>(sm, tid - 32, -1, prm, F);
+          sm.fy.st(0, tid - 32, F);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // ---- D
+    R dF[5];
     if (p >= z0 && p < z1) {
       R xp[5], xm[5], yp[5], ym[5];
       sm.fx.ld(tj, ti + 1, xp);
@@ -276,7 +378,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
       S Un[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const R div = dFprev[v] + (Fz[v] - FzPrev[v]);
+        const R div = acc[v] + Fz[v];
         Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, div);
         P.out[v][ao] = Un[v];
       }
@@ -285,10 +387,9 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
         smax = s > smax ? s : smax;
       }
     }
+    if (p >= z0 && p < z1) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      FzPrev[v] = Fz[v];
-      dFprev[v] = dF[v];
+      for (int v = 0; v < 5; ++v) acc[v] = dF[v] - Fz[v];
     }
   }
 }
@@ -328,15 +429,15 @@ __device__ __forceinline__ void publish_dt(double cfl, double dx, double smax, d
 // ------------------------------------------------------------------ kernels
 // Resident blocks per SM the register allocation must allow: 2 x 256 threads for FP64 (its
 // shared memory allows 2), 3 x 256 for the float policies.
-template <class Pol, int NT>
+template <class Pol, int NT, int MINB>
 constexpr int min_blocks() {
   constexpr int b = (sizeof(typename Pol::R) >= 8 ? 2 : 3) * 256 / NT;
-  return b < 1 ? 1 : b;
+  return MINB > 0 ? MINB : (b < 1 ? 1 : b);
 }
 
 // Uniform grid: one tile per block, tiles from the block index.
-template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY>())) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
+template <class Pol, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
                                                          double* dt_next, int zchunk, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<TileShared<Pol, TX, TY>*>(smem_raw);
@@ -358,8 +459,8 @@ __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY>())) k_step_u
 }
 
 // Batched patches: a persistent grid pulls tiles from the work-list through an atomic counter.
-template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY>())) k_step_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles,
+template <class Pol, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_step_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles,
                                                          int ntiles, int* counter, Params prm, const double* dt_dev,
                                                          double* dt_next, int zchunk, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
