@@ -131,10 +131,11 @@ int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5],
                     const double* dt_dev);
 
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
- * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64 or
- * HYDRO_FP32.  U_n: the state the forward step started from; dt_dev[p] its time step; lam_np1,
- * lam_n: adjoint fields with the same layout and element type as U_n (must not overlap).
- * Other precisions return HYDRO_ERR_ARG.  The
+ * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64,
+ * HYDRO_FP64_DF (the same reverse sweep in double-float arithmetic) or HYDRO_FP32.  U_n: the
+ * state the forward step started from; dt_dev[p] its time step; lam_np1, lam_n: adjoint fields
+ * with the same layout and element type as U_n (must not overlap).  HYDRO_MIXED returns
+ * HYDRO_ERR_ARG.  The
  * derivative of each limiter / HLLC branch / floor is that of the branch the forward values
  * select.  Deterministic: every face's contribution is gathered, never atomically scattered. */
 int hydro_adjoint_step(hydro_ctx* ctx, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

@@ -92,8 +92,8 @@ __device__ __forceinline__ void adj_face_xy(AdjShared<typename Pol::R, TX, TY>& 
   for (int v = 0; v < 5; ++v) {
     const R sL = (D == 0) ? sm.sx[sp][v][lj][li] : sm.sy[sp][v][lj][li];
     const R sR = (D == 0) ? sm.sx[sp][v][rj][ri] : sm.sy[sp][v][rj][ri];
-    pL[v] = sm.qh[sp][v][lj][li] + R(0.5) * sL;
-    pR[v] = sm.qh[sp][v][rj][ri] - R(0.5) * sR;
+    pL[v] = sm.qh[sp][v][lj][li] + half_(sL);
+    pR[v] = sm.qh[sp][v][rj][ri] - half_(sR);
     qL[v] = pL[v];
     qR[v] = pR[v];
     lF[v] = dtdx * (sm.lam[sp][v][rj][ri] - sm.lam[sp][v][lj][li]);
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
       R pL[5], pR[5], qL[5], qR[5], lF[5], lL[5], lRn[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        pL[v] = sm.qh[pk][v][tj + 1][ti + 1] + R(0.5) * sm.sz[pk][v][tj][ti];
-        pR[v] = sm.qh[pk1][v][tj + 1][ti + 1] - R(0.5) * sm.sz[pk1][v][tj][ti];
+        pL[v] = sm.qh[pk][v][tj + 1][ti + 1] + half_(sm.sz[pk][v][tj][ti]);
+        pR[v] = sm.qh[pk1][v][tj + 1][ti + 1] - half_(sm.sz[pk1][v][tj][ti]);
         qL[v] = pL[v];
         qR[v] = pR[v];
         lF[v] = dtdx * (sm.lam[pk1][v][tj + 1][ti + 1] - sm.lam[pk][v][tj + 1][ti + 1]);
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
           const R xl = sm.axL[v][tj][ti + 1], xr = sm.axR[v][tj][ti];
           const R yl = sm.ayL[v][tj + 1][ti], yr = sm.ayR[v][tj][ti];
           lqh[v] = ((xl + xr) + (yl + yr)) + (lLz[v] + lRz[v]);
-          ldq[0][v] = R(0.5) * (xl - xr);
-          ldq[1][v] = R(0.5) * (yl - yr);
-          ldq[2][v] = R(0.5) * (lLz[v] - lRz[v]);
+          ldq[0][v] = half_(xl - xr);
+          ldq[1][v] = half_(yl - yr);
+          ldq[2][v] = half_(lLz[v] - lRz[v]);
           q0[v] = sm.q[ring_slot(k)][v][tj + 2][ti + 2];
           dq[0][v] = sm.sx[pk][v][tj + 1][ti + 1];
           dq[1][v] = sm.sy[pk][v][tj + 1][ti + 1];
@@ -304,19 +304,19 @@ __global__ void __launch_bounds__(256) k_adj_cells(PatchIO<typename Pol::S> P, P
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const int sh = 2 * (5 * d + v);
-        R a0, b0, am, bm, ap, bp;
-        code_weights<R>((cc >> sh) & 3u, prm.limiter, a0, b0);
-        code_weights<R>((cm >> sh) & 3u, prm.limiter, am, bm);
-        code_weights<R>((cp >> sh) & 3u, prm.limiter, ap, bp);
+        float a0, b0, am, bm, ap, bp;
+        code_weights((cc >> sh) & 3u, prm.limiter, a0, b0);
+        code_weights((cm >> sh) & 3u, prm.limiter, am, bm);
+        code_weights((cp >> sh) & 3u, prm.limiter, ap, bp);
         const R* ld = scr.ld + (long long)(5 * d + v) * N;
-        lq[v] += ((a0 - b0) * ld[c] + bm * ld[nb[d][0]]) - ap * ld[nb[d][1]];
+        lq[v] += (mulf_(ld[c], a0 - b0) + mulf_(ld[nb[d][0]], bm)) - mulf_(ld[nb[d][1]], ap);
       }
     }
     const long long a = (long long)k * P.isz + (long long)j * P.isy + i;
     const long long la = (long long)k * L.isz + (long long)j * L.isy + i;
     R U[5], lU[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) U[v] = (R)P.in[v][a];
+    for (int v = 0; v < 5; ++v) U[v] = R(P.in[v][a]);
     recover_adj(U, prm, lq, lU);
     const long long o = (long long)(k + out_g) * osz + (long long)(j + out_g) * osy + (i + out_g);
 #pragma unroll
@@ -354,8 +354,8 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
                            const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s) {
   using R = typename Pol::R;
   using S = typename Pol::S;
-  if constexpr (std::is_same<Pol, PolMixed>::value || std::is_same<Pol, PolDF>::value) {
-    return cudaErrorNotSupported;  // the adjoint runs in FP64 or FP32 only
+  if constexpr (std::is_same<Pol, PolMixed>::value) {
+    return cudaErrorNotSupported;  // the adjoint runs in FP64, double-float FP64 or FP32
   } else {
   constexpr int TX = AdjTile<Pol>::TX, TY = AdjTile<Pol>::TY;
   if (scratch_bytes < adjoint_scratch_bytes<Pol>(U.nx, U.ny, U.nz)) return cudaErrorInvalidValue;
@@ -372,7 +372,23 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int zc = U.nz < 16 ? U.nz : 16;
+  // z chunk: FP32 and double-float take the longest of 16, 8, 4, 2 planes whose grid still fills
+  // every SM's resident blocks (a small grid leaves SMs idle and their FP32 pipes waiting on
+  // dependent chains).  FP64 keeps 16: it is bound by the FP64 pipe, which a few warps per SM
+  // already keep busy, and a shorter march repeats halo planes on it.
+  static int resident = 0;
+  if (!resident) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adj_faces<Pol, TX, TY>, TX * TY, smem);
+    if (e != cudaSuccess) return e;
+    if (resident < 1) resident = 1;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorUnknown;
+  const long long cols = (long long)((U.nx + TX - 1) / TX) * ((U.ny + TY - 1) / TY);
+  int zc = 16;
+  while (!std::is_same<R, double>::value && zc > 2 && cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms) zc /= 2;
+  if (zc > U.nz) zc = U.nz;
   dim3 grid((U.nx + TX - 1) / TX, (U.ny + TY - 1) / TY, (U.nz + zc - 1) / zc);
   k_adj_faces<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, dt, zc, scr,
                                                         err);

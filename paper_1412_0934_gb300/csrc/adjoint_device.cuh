@@ -3,23 +3,29 @@
 // 2-bit code), and the primitive recovery.  Each function recomputes the forward values it needs
 // and returns adjoints with respect to its inputs.
 #pragma once
+#include "df.cuh"
 #include "hydro_device.cuh"
 
 namespace hydro {
+
+// Compound assignment and division of double-float values, used by the reverse sweeps below.
+__device__ __forceinline__ df& operator+=(df& a, const df& b) { return a = a + b; }
+__device__ __forceinline__ df& operator-=(df& a, const df& b) { return a = a - b; }
+__device__ __forceinline__ df operator/(const df& a, const df& b) { return div_(a, b); }
 
 // ------------------------------------------------------------------ limiter with branch code
 // Code: 0 zero slope, 1 the first argument (a, or 2a for MC), 2 the second (b, or 2b for MC),
 // 3 the centred (a+b)/2.  Same comparisons as limited().
 template <class R>
 __device__ __forceinline__ R limited_code(R a, R b, int lim, unsigned& code) {
-  if (lim == HYDRO_NOLIMIT) { code = 3; return R(0.5) * (a + b); }
+  if (lim == HYDRO_NOLIMIT) { code = 3; return half_(a + b); }
   if (prod_nonpos(a, b)) { code = 0; return R(0); }
   if (lim == HYDRO_MINMOD) {
     if (abs_le(a, b)) { code = 1; return a; }
     code = 2;
     return b;
   }
-  R ta = R(2) * a, tb = R(2) * b, m = R(0.5) * (a + b);
+  R ta = twice_(a), tb = twice_(b), m = half_(a + b);
   R best = ta;
   code = 1;
   if (abs_lt(tb, best)) { best = tb; code = 2; }
@@ -27,12 +33,12 @@ __device__ __forceinline__ R limited_code(R a, R b, int lim, unsigned& code) {
   return best;
 }
 
-// Partial derivatives (alpha, beta) of the limited slope with respect to (a, b) for a code.
-template <class R>
-__device__ __forceinline__ void code_weights(unsigned code, int lim, R& alpha, R& beta) {
-  const R w = (lim == HYDRO_MC) ? R(2) : R(1);
-  alpha = code == 1 ? w : (code == 3 ? R(0.5) : R(0));
-  beta = code == 2 ? w : (code == 3 ? R(0.5) : R(0));
+// Partial derivatives (alpha, beta) of the limited slope with respect to (a, b) for a code
+// (0, 1/2, 1 or 2: exact in any arithmetic type).
+__device__ __forceinline__ void code_weights(unsigned code, int lim, float& alpha, float& beta) {
+  const float w = (lim == HYDRO_MC) ? 2.f : 1.f;
+  alpha = code == 1 ? w : (code == 3 ? 0.5f : 0.f);
+  beta = code == 2 ? w : (code == 3 ? 0.5f : 0.f);
 }
 
 // ------------------------------------------------------------------ HLLC reverse
@@ -56,7 +62,7 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   const R mR = qR[0] * (SR - uR);
   const R num = qR[4] - qL[4] + uL * mL - uR * mR;
   const R den = mL - mR;
-  const R Ss = num / den;
+  const R Ss = div_(num, den);
   const bool SLneg = cmp_neg(SL), SRpos = cmp_pos(SR);
   const bool star = SLneg && SRpos;
   const bool left = !SLneg || (SRpos && !cmp_neg(Ss));
@@ -69,11 +75,11 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   const R irK = left ? irL : irR;
   const R SK = left ? SL : SR;
   const R mK = left ? mL : mR;
-  const R EK = pK * inv_gm1 + R(0.5) * rK * keK;
+  const R EK = pK * inv_gm1 + half_(rK * keK);
   const R mn = rK * uK;
   const R Dd = SK - Ss;
-  const R fac = mK / Dd;
-  const R w = pK / mK;
+  const R fac = div_(mK, Dd);
+  const R w = div_(pK, mK);
   const R Y = Ss - uK, Z = Ss + w;
   const R X = EK * irK + Y * Z;
   // ---- reverse
@@ -97,11 +103,12 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
     lirK += EK * lX;
     lSs += (Z + Y) * lX;
     luK -= Z * lX;
-    const R lw = Y * lX;
-    lpK += lw / mK;
-    lmK -= lw * w / mK;
-    lmK += lfac / Dd;
-    const R lD = -lfac * fac / Dd;
+    const R lwm = div_(Y * lX, mK);  // adjoint of w = p_K / m_K, over m_K
+    lpK += lwm;
+    lmK -= lwm * w;
+    const R lfd = div_(lfac, Dd);  // adjoint of fac = m_K / D, over D
+    lmK += lfd;
+    const R lD = -(lfd * fac);
     lSK += lD;
     lSs -= lD;
     lrK += lUK[0] + t1 * lUK[2] + t2 * lUK[3];
@@ -120,8 +127,8 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   lrK += uK * lmn;
   luK += rK * lmn;
   lpK += inv_gm1 * lEK;
-  lrK += R(0.5) * keK * lEK;
-  lkeK += R(0.5) * rK * lEK;
+  lrK += half_(keK * lEK);
+  lkeK += half_(rK * lEK);
   // scatter the upwind side's adjoints
   R lrL = 0, luL = 0, lpL = 0, lirL = 0, lSL = 0, lmL = 0;
   R lrR = 0, luR = 0, lpR = 0, lirR = 0, lSR = 0, lmR = 0;
@@ -133,8 +140,8 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
     lSR += lSK; lmR += lmK;
   }
   // S* = num / den
-  const R lnum = lSs / den;
-  const R lden = -lSs * Ss / den;
+  const R lnum = div_(lSs, den);
+  const R lden = -(lnum * Ss);
   lpR += lnum;
   lpL -= lnum;
   luL += mL * lnum;
@@ -153,7 +160,7 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   if (selL) { luL += lSL; lcL -= lSL; } else { luR += lSL; lcR -= lSL; }
   if (selR) { luL += lSR; lcL += lSR; } else { luR += lSR; lcR += lSR; }
   // c = sqrt(gamma p ir), ir = 1/rho
-  const R lxL = lcL / (R(2) * cL), lxR = lcR / (R(2) * cR);
+  const R lxL = div_(half_(lcL), cL), lxR = div_(half_(lcR), cR);
   lpL += gamma * irL * lxL;
   lirL += gamma * qL[4] * lxL;
   lpR += gamma * irR * lxR;
@@ -193,8 +200,8 @@ __device__ __forceinline__ void hllc_adj(const R qL[5], const R qR[5], R gamma, 
   lqR[4] += lb[4];
 #pragma unroll
   for (int m = 1; m <= 3; ++m) {
-    lqL[m] += R(2) * qL[m] * lkeL;
-    lqR[m] += R(2) * qR[m] * lkeR;
+    lqL[m] += twice_(qL[m] * lkeL);
+    lqR[m] += twice_(qR[m] * lkeR);
   }
 }
 
@@ -242,17 +249,18 @@ __device__ __forceinline__ void floor_mask(const R pre[5], R lq[5], R rho_floor,
 // q = recover(U) with floors; given lq returns lU (same arithmetic type throughout).
 template <class R>
 __device__ __forceinline__ void recover_adj(const R U[5], const Params& P, const R lq[5], R lU[5]) {
-  const bool rho_free = !(U[0] < (R)P.rho_floor);
-  const R rho = rho_free ? U[0] : (R)P.rho_floor;
+  const R rf = kc<R>(P, K_RHOF);
+  const bool rho_free = !(U[0] < rf);
+  const R rho = rho_free ? U[0] : rf;
   const R ir = rcp_(rho);
   const R K = (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
-  const R kin = R(0.5) * K * ir;
+  const R kin = half_(K * ir);
   const R gm1 = kc<R>(P, K_GM1);
   const R praw = gm1 * (U[4] - kin);
-  const R lpr = (praw < (R)P.p_floor) ? R(0) : lq[4];
+  const R lpr = (praw < kc<R>(P, K_PF)) ? R(0) : lq[4];
   lU[4] = gm1 * lpr;
   const R lkin = -gm1 * lpr;
-  R lir = lkin * R(0.5) * K;
+  R lir = half_(lkin * K);
 #pragma unroll
   for (int m = 1; m <= 3; ++m) {
     lU[m] = lq[m] * ir + lkin * U[m] * ir;

@@ -341,7 +341,7 @@ int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], l
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
                        const hydro_patch* lam_n, int npatch) {
   if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1) return HYDRO_ERR_ARG;
-  if (c->cfg.precision != HYDRO_FP64 && c->cfg.precision != HYDRO_FP32) return HYDRO_ERR_ARG;
+  if (c->cfg.precision == HYDRO_MIXED) return HYDRO_ERR_ARG;
   for (int i = 0; i < npatch; ++i) {
     const hydro_patch &U = U_n[i], &L = lam_np1[i], &O = lam_n[i];
     if (!valid_patch(c, U) || !valid_patch(c, L) || !valid_patch(c, O)) return HYDRO_ERR_ARG;
@@ -502,7 +502,8 @@ int hydro_autotune(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, 
   }
   int maxnz = 1;
   for (int i = 0; i < npatch; ++i) maxnz = std::max(maxnz, in[i].nz);
-  const int zcs[] = {8, 16, 32, 64, 128};
+  // short z chunks only pay on small grids, where the longer ones leave SMs without a block
+  const int zcs[] = {2, 4, 8, 16, 32, 64, 128};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -511,6 +512,7 @@ int hydro_autotune(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, 
   for (int t = 0; t < hydro::kNumTiles; ++t) {
     for (int zc : zcs) {
       if (zc > std::max(8, maxnz)) continue;
+      if (zc < 8 && cells > (1LL << 22)) continue;
       c->tile_id = t;
       c->zchunk = zc;
       int rc = hydro_step(c, in, out, npatch, dt_dev, nullptr);  // warm-up (and work-list build)

@@ -38,10 +38,15 @@ def inputs(limiter, shape):
             workloads.white_velocity_state(shape, seed=1, p_jitter=0.2).numpy()]
 
 
+# FP64 adjoints: native double, and the same reverse sweep in double-float arithmetic.
+F64 = ["fp64", "df64"]
+
+
+@pytest.mark.parametrize("precision", F64)
 @pytest.mark.parametrize("limiter", ["minmod", "mc", "none"])
 @pytest.mark.parametrize("shape", [(12, 10, 9), (18, 20, 17)])
-def test_fp64_adjoint_matches_oracle_tape(limiter, shape):
-    c = ctx("fp64", limiter)
+def test_fp64_adjoint_matches_oracle_tape(limiter, shape, precision):
+    c = ctx(precision, limiter)
     dx = 1.0 / shape[2]
     cfg = oracle.config(limiter=limiter)
     for U in inputs(limiter, shape):
@@ -69,11 +74,12 @@ def test_fp32_adjoint_matches_oracle_tape(limiter):
     check_clean(c)
 
 
+@pytest.mark.parametrize("precision", F64)
 @pytest.mark.parametrize("limiter", ["none", "minmod"])
-def test_adjoint_dot_product_against_gpu_central_differences(limiter):
+def test_adjoint_dot_product_against_gpu_central_differences(limiter, precision):
     """<w, (S(U+eps v) - S(U-eps v)) / 2 eps> = <J^T w, v> on a smooth field, all on the GPU."""
     shape = (16, 16, 16)
-    c = ctx("fp64", limiter)
+    c = ctx(precision, limiter)
     dx = 1.0 / 16
     U, _ = workloads.sound_wave(shape, amp=1e-3, kvec=(1, 1, 1), phase=0.3)
     U = U.numpy()
@@ -104,8 +110,9 @@ def _loss_setup(n, amp=1e-3):
     return q, target
 
 
-@pytest.mark.parametrize("limiter,eps,tol", [("none", 1e-6, 1e-6), ("minmod", 1e-8, 1e-5)])
-def test_checkpointed_gradient_64cube_40steps_vs_central_differences(limiter, eps, tol):
+@pytest.mark.parametrize("precision,limiter,eps,tol", [("fp64", "none", 1e-6, 1e-6), ("fp64", "minmod", 1e-8, 1e-5),
+                                                       ("df64", "minmod", 1e-8, 1e-5)])
+def test_checkpointed_gradient_64cube_40steps_vs_central_differences(precision, limiter, eps, tol):
     """Loss sum (rho_40 - rho_target)^2 on the 64^3 periodic grid, 40 steps, checkpoint every 8;
     gradient w.r.t. rho0 and v0 against central differences over 64 random directions,
     replaying the recorded dt sequence.  The unlimited scheme is smooth: eps = 1e-6.  MinMod has
@@ -114,7 +121,7 @@ def test_checkpointed_gradient_64cube_40steps_vs_central_differences(limiter, ep
     detects; directions that cross a kink are counted (they must be a minority) and the rest must
     agree."""
     n, nsteps = 64, 40
-    c = ctx("fp64", limiter)
+    c = ctx(precision, limiter)
     q, target = _loss_setup(n)
     rho0 = torch.tensor(q[0], device="cuda", requires_grad=True)
     vel0 = torch.tensor(q[1:4], device="cuda", requires_grad=True)
@@ -150,11 +157,12 @@ def test_checkpointed_gradient_64cube_40steps_vs_central_differences(limiter, ep
     check_clean(c)
 
 
-def test_checkpointed_gradient_matches_oracle_chain():
+@pytest.mark.parametrize("precision", F64)
+def test_checkpointed_gradient_matches_oracle_chain(precision):
     """Small case (12^3, 5 steps, checkpoint every 2): the autograd gradient equals the oracle's
     forward run + chained one-step adjoints + prim->cons adjoint."""
     n, nsteps = 12, 5
-    c = ctx("fp64", "minmod")
+    c = ctx(precision, "minmod")
     q, target = _loss_setup(n, amp=0.05)
     dx = 1.0 / n
     rho0 = torch.tensor(q[0], device="cuda", requires_grad=True)
