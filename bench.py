@@ -83,6 +83,7 @@ def parse():
     p.add_argument("--npatch", type=int, default=4096, help="patches of the batched form")
     p.add_argument("--ngroups", type=int, default=262144, help="oct groups of the batched form")
     p.add_argument("--adj-n", type=int, default=64, help="grid edge of the adjoint form")
+    p.add_argument("--adj-precisions", default="df64,fp64,fp32", help="precisions of the adjoint form")
     return p.parse_args()
 
 
@@ -613,7 +614,7 @@ def main():
                     extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch,
                                                           ngroups=args.ngroups)
                 elif f == "adjoint":
-                    for prec in ("df64", "fp64", "fp32"):
+                    for prec in args.adj_precisions.split(","):
                         extra["adjoint_" + prec] = form_adjoint(hy, prec, n=args.adj_n)
                 elif f == "graph1024":
                     extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
