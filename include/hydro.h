@@ -81,7 +81,8 @@ typedef struct {
 } hydro_config;
 
 typedef struct {
-  void* U[5];        /* device pointers to rho, m_x, m_y, m_z, E (see the element type above) */
+  void* U[5];        /* device pointers to rho, m_x, m_y, m_z, E (see the element type above);
+                        host pointers for hydro_step_host only */
   int nx, ny, nz;    /* interior cells, each >= 1 */
   int ng;            /* ghost layers: 2 (caller-filled) or 0 (periodic box, wrapped by the library) */
   long long sy, sz;  /* element strides of y and z in the stored (ghosted) array; x stride is 1.
@@ -158,6 +159,21 @@ int hydro_prim_to_cons_adjoint(hydro_ctx* ctx, const hydro_patch* W, const hydro
  * and replayed. */
 int hydro_run(hydro_ctx* ctx, const hydro_patch* a, const hydro_patch* b, int nsteps, double* dt_hist_dev,
               int use_graph);
+
+/* One step of a periodic box whose state lives in HOST memory (the paper's GPU ports copy each
+ * patch chunk to the GPU and back every step, and those copies cost a quarter of the GPU hydro time
+ * and more, Sec. 3 and Table 1).  in->U / out->U are host pointers (page-locked memory lets the
+ * copies run asynchronously; pageable memory works but serialises them), ng == 0, the same sy, sz
+ * for in and out, and each field spans nz * sz elements.  The library stages the box in device
+ * memory it owns (10 fields of nz * sz elements, kept for later calls) and pipelines the step over
+ * z slabs: host->device copies on one stream, the step kernel on the context stream over each slab
+ * whose halo planes have arrived, device->host copies of finished slabs on a third stream, so the
+ * two transfers and the compute overlap.  dt_dev / dt_next_dev are DEVICE pointers as in
+ * hydro_step (dt_next_dev, if not NULL, receives the CFL dt of the result).  The call returns once
+ * the work is enqueued; out is complete when the context stream has been synchronised.  Device
+ * pointers in in/out give HYDRO_ERR_ARG. */
+int hydro_step_host(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, const double* dt_dev,
+                    double* dt_next_dev);
 
 /* Autotuner: times the candidate tile shapes and z-chunk depths of hydro_step on this patch set
  * (in, out, dt_dev as for hydro_step; contents of out are overwritten) and keeps the fastest in

@@ -37,7 +37,8 @@ EBIT_BAD_TILE = 0x10
 EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
-EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_octs", "hydro_adjoint_step",
+EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
+           "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
            "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
            "hydro_step_batched_noalloc")
@@ -78,6 +79,7 @@ def lib():
         L.hydro_finalize.argtypes = [vp]
         L.hydro_cfl_dt.argtypes = [vp, PP, i, vp]
         L.hydro_step.argtypes = [vp, PP, PP, i, vp, vp]
+        L.hydro_step_host.argtypes = [vp, PP, PP, vp, vp]
         L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
         L.hydro_adjoint_step.argtypes = [vp, PP, vp, PP, PP, i]
         L.hydro_prim_to_cons.argtypes = [vp, PP, PP, i]
@@ -112,7 +114,7 @@ def _check(rc, what):
 class Patch:
     """A hydro_patch plus the tensors it points into (kept alive while the patch is)."""
 
-    def __init__(self, fields, ng, dx, level=0):
+    def __init__(self, fields, ng, dx, level=0, host=False):
         if isinstance(fields, torch.Tensor):
             if fields.dim() != 4 or fields.shape[0] != 5:
                 raise ValueError("expected a (5, nz, ny, nx) tensor")
@@ -122,8 +124,8 @@ class Patch:
             if len(fs) != 5:
                 raise ValueError("expected five field tensors")
         for f in fs:
-            if not f.is_cuda:
-                raise ValueError("patch fields must be CUDA tensors")
+            if f.is_cuda == host:
+                raise ValueError("patch fields must be %s tensors" % ("host (CPU)" if host else "CUDA"))
             if f.dim() != 3 or f.stride(2) != 1:
                 raise ValueError("each field must be 3D with unit x stride")
             if f.shape != fs[0].shape or f.stride() != fs[0].stride() or f.dtype != fs[0].dtype:
@@ -144,6 +146,11 @@ class Patch:
 
 def patch(fields, ng, dx, level=0):
     return Patch(fields, ng, dx, level)
+
+
+def host_patch(fields, dx):
+    """A periodic box (ng = 0) in host memory, for hydro_step_host (page-locked tensors overlap)."""
+    return Patch(fields, 0, dx, host=True)
 
 
 def _parray(patches):
@@ -216,6 +223,12 @@ def hydro_step(ctx, inp, out, dt, dt_next=None):
     if n != m:
         raise ValueError("in and out patch counts differ")
     _check(lib().hydro_step(ctx.handle, a, b, n, _ptr(dt), _ptr(dt_next)), "hydro_step")
+
+
+def hydro_step_host(ctx, inp, out, dt, dt_next=None):
+    """One step of a host-resident periodic box (host_patch in / out; dt, dt_next CUDA tensors)."""
+    _check(lib().hydro_step_host(ctx.handle, ctypes.byref(inp.c), ctypes.byref(out.c), _ptr(dt), _ptr(dt_next)),
+           "hydro_step_host")
 
 
 def hydro_step_octs(ctx, gathered, out, dx, dt):

@@ -55,6 +55,20 @@ struct hydro_ctx {
   // adjoint scratch
   void* d_adj = nullptr;
   size_t adj_cap = 0;
+  // host-buffer step: device staging of one box (in and out), its descriptor and slab tile list,
+  // per-slab tile counters, the two copy streams and the events that chain the pipeline
+  char* d_stage = nullptr;
+  size_t stage_cap = 0;
+  HostPatchIO* d_stage_io = nullptr;
+  HostTileRec* d_stage_tiles = nullptr;
+  size_t stage_tiles_cap = 0;
+  int* d_stage_counters = nullptr;
+  size_t stage_counters_cap = 0;
+  long long stage_key[7] = {-1, -1, -1, -1, -1, -1, -1};  // nx ny nz sy sz tile zc of the uploaded list
+  double stage_dx = 0.0;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  std::vector<cudaEvent_t> ev_copied, ev_stepped;
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   long long launches = 0;
 };
 
@@ -267,6 +281,18 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_tiles);
   cudaFree(c->d_cfl);
   cudaFree(c->d_adj);
+  if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
+  if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
+  cudaFree(c->d_stage);
+  cudaFree(c->d_stage_io);
+  cudaFree(c->d_stage_tiles);
+  cudaFree(c->d_stage_counters);
+  for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
+  if (c->ev_begin) cudaEventDestroy(c->ev_begin);
+  if (c->ev_end) cudaEventDestroy(c->ev_end);
+  if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+  if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
   if (c->h_patches) cudaFreeHost(c->h_patches);
   if (c->h_cfl) cudaFreeHost(c->h_cfl);
   delete c;
@@ -324,6 +350,146 @@ int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int 
   c->launches += 1;
   return cuda_status(c->ops->step_batched(c->tile_id, c->d_patches, c->d_tiles, c->ntiles, c->d_counter, c->prm,
                                           dt_dev, dt_next_dev, c->zchunk, c->d_err, grid, c->stream));
+}
+
+// Host-buffer step of one periodic box: the state crosses the host link in z slabs on two copy
+// streams while the step kernel runs on the slabs that have arrived (copies of a quarter of the
+// GPU hydro time and more are the paper's data-movement cost, Sec. 3 and Table 1; here they
+// overlap the compute instead of preceding and following it).
+//   H2D:  planes nz-2, nz-1 (slab 0's lower halo), then slabs 0 .. S-1
+//   step: slab k once slab k+1 has arrived (slab S-1 wraps onto slab 0, already there)
+//   D2H:  slab k once its step has run
+int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, const double* dt_dev,
+                    double* dt_next_dev) {
+  if (!c || !in || !out || !dt_dev) return HYDRO_ERR_ARG;
+  const hydro_patch &I = *in, &O = *out;
+  if (!valid_patch(c, I) || !valid_patch(c, O) || !same_shape(I, O) || overlaps(c, I, O)) return HYDRO_ERR_ARG;
+  if (I.ng != 0 || O.ng != 0 || I.sy != O.sy || I.sz != O.sz) return HYDRO_ERR_ARG;
+  for (int v = 0; v < 5; ++v) {
+    for (const void* ptr : {static_cast<const void*>(I.U[v]), static_cast<const void*>(O.U[v])}) {
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) return HYDRO_ERR_CUDA;
+      if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return HYDRO_ERR_ARG;
+    }
+  }
+  const int es = elem_size(c);
+  const size_t plane = (size_t)I.sz * es;
+  const size_t fb = (size_t)I.nz * plane;
+  // slabs: the z chunk shortened until the box has >= 16 slabs (or 2-plane chunks)
+  int zc = c->zchunk;
+  while (zc > 2 && I.nz / zc < 16) zc /= 2;
+  zc = std::max(1, std::min(zc, I.nz));
+  const int S = (I.nz + zc - 1) / zc;
+  const int tx = hydro::kTileX[c->tile_id], ty = hydro::kTileY[c->tile_id];
+  const int ntx = (I.nx + tx - 1) / tx, nty = (I.ny + ty - 1) / ty, tps = ntx * nty;
+  // staging, descriptors, tile list, counters, streams, events
+  int rc = HYDRO_OK;
+  if (c->stage_cap < 10 * fb) {
+    if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
+    if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_cap = 0;
+    if (cudaMalloc(&c->d_stage, 10 * fb) != cudaSuccess) return HYDRO_ERR_NOMEM;
+    c->stage_cap = 10 * fb;
+    c->stage_key[0] = -1;
+  }
+  if (!c->d_stage_io && cudaMalloc(&c->d_stage_io, sizeof(HostPatchIO)) != cudaSuccess) return HYDRO_ERR_NOMEM;
+  rc = ensure_device(&c->d_stage_tiles, &c->stage_tiles_cap, (size_t)S * tps);
+  if (rc) return rc;
+  rc = ensure_device(&c->d_stage_counters, &c->stage_counters_cap, (size_t)S);
+  if (rc) return rc;
+  if (!c->s_h2d && cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (!c->s_d2h && cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (!c->ev_begin && (cudaEventCreateWithFlags(&c->ev_begin, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) != cudaSuccess))
+    return HYDRO_ERR_CUDA;
+  while ((int)c->ev_copied.size() < S) {
+    cudaEvent_t a, b;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return HYDRO_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return HYDRO_ERR_CUDA;
+    }
+    c->ev_copied.push_back(a);
+    c->ev_stepped.push_back(b);
+  }
+  char* din[5];
+  char* dout[5];
+  for (int v = 0; v < 5; ++v) {
+    din[v] = c->d_stage + v * fb;
+    dout[v] = c->d_stage + (5 + v) * fb;
+  }
+  const long long key[7] = {I.nx, I.ny, I.nz, I.sy, I.sz, c->tile_id, zc};
+  if (std::memcmp(key, c->stage_key, sizeof(key)) != 0 || c->stage_dx != I.dx) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    HostPatchIO h;
+    for (int v = 0; v < 5; ++v) {
+      h.in[v] = din[v];
+      h.out[v] = dout[v];
+    }
+    h.nx = I.nx; h.ny = I.ny; h.nz = I.nz; h.gin = 0; h.gout = 0;
+    h.isy = h.osy = I.sy; h.isz = h.osz = I.sz; h.dx = I.dx;
+    std::vector<HostTileRec> t((size_t)S * tps);
+    for (int k = 0; k < S; ++k)
+      for (int j = 0; j < nty; ++j)
+        for (int i = 0; i < ntx; ++i) t[(size_t)k * tps + j * ntx + i] = HostTileRec{0, i * tx, j * ty, k * zc};
+    if (cudaMemcpy(c->d_stage_io, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_stage_tiles, t.data(), t.size() * sizeof(HostTileRec), cudaMemcpyHostToDevice) != cudaSuccess)
+      return HYDRO_ERR_CUDA;
+    std::memcpy(c->stage_key, key, sizeof(key));
+    c->stage_dx = I.dx;
+  }
+  // planes [za, zb) of the five fields, one copy per field (a z range of a field is contiguous)
+  auto upload = [&](int za, int zb) -> bool {
+    for (int v = 0; v < 5 && zb > za; ++v)
+      if (cudaMemcpyAsync(din[v] + za * plane, static_cast<const char*>(I.U[v]) + za * plane, (zb - za) * plane,
+                          cudaMemcpyHostToDevice, c->s_h2d) != cudaSuccess)
+        return false;
+    return true;
+  };
+  auto download = [&](int za, int zb) -> bool {
+    for (int v = 0; v < 5 && zb > za; ++v)
+      if (cudaMemcpyAsync(static_cast<char*>(O.U[v]) + za * plane, dout[v] + za * plane, (zb - za) * plane,
+                          cudaMemcpyDeviceToHost, c->s_d2h) != cudaSuccess)
+        return false;
+    return true;
+  };
+  // the staging buffers may still be read or written by the previous call's work
+  if (cudaEventRecord(c->ev_begin, c->stream) != cudaSuccess || cudaStreamWaitEvent(c->s_h2d, c->ev_begin) != cudaSuccess ||
+      cudaStreamWaitEvent(c->s_d2h, c->ev_begin) != cudaSuccess)
+    return HYDRO_ERR_CUDA;
+  const int tail = S > 1 ? std::max(0, I.nz - 2) : I.nz;
+  if (!upload(tail, I.nz)) return HYDRO_ERR_CUDA;
+  for (int k = 0; k < S; ++k) {
+    const int za = k * zc, zb = std::min(I.nz, za + zc);
+    if (!upload(za, std::min(zb, tail))) return HYDRO_ERR_CUDA;
+    if (cudaEventRecord(c->ev_copied[k], c->s_h2d) != cudaSuccess) return HYDRO_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(c->d_stage_counters, 0, (size_t)S * sizeof(int), c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (dt_next_dev) {
+    rc = reset_slots(c, dt_next_dev, 1, c->stream);
+    if (rc) return rc;
+  }
+  const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id);
+  const int grid = std::max(1, std::min(tps, c->sm_count * per_sm));
+  for (int k = 0; k < S; ++k) {
+    const int za = k * zc, zb = std::min(I.nz, za + zc);
+    if (cudaStreamWaitEvent(c->stream, c->ev_copied[std::min(k + 1, S - 1)]) != cudaSuccess) return HYDRO_ERR_CUDA;
+    c->launches += 1;
+    if (c->ops->step_batched(c->tile_id, c->d_stage_io, c->d_stage_tiles + (size_t)k * tps, tps,
+                             c->d_stage_counters + k, c->prm, dt_dev, dt_next_dev, zc, c->d_err, grid,
+                             c->stream) != cudaSuccess)
+      return HYDRO_ERR_CUDA;
+    if (cudaEventRecord(c->ev_stepped[k], c->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->s_d2h, c->ev_stepped[k]) != cudaSuccess)
+      return HYDRO_ERR_CUDA;
+    if (!download(za, zb)) return HYDRO_ERR_CUDA;
+  }
+  if (cudaEventRecord(c->ev_end, c->s_d2h) != cudaSuccess || cudaStreamWaitEvent(c->stream, c->ev_end) != cudaSuccess)
+    return HYDRO_ERR_CUDA;
+  return HYDRO_OK;
 }
 
 int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], long long ngroups, double dx,
