@@ -62,7 +62,8 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   const R mR = qR[0] * (SR - uR);
   const R num = qR[4] - qL[4] + uL * mL - uR * mR;
   const R den = mL - mR;
-  const R Ss = div_(num, den);
+  const R iden = rcp_(den);  // S* = num / den; its sign (the only branch it decides) is exact
+  const R Ss = num * iden;
   const bool SLneg = cmp_neg(SL), SRpos = cmp_pos(SR);
   const bool star = SLneg && SRpos;
   const bool left = !SLneg || (SRpos && !cmp_neg(Ss));
@@ -77,14 +78,16 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   const R mK = left ? mL : mR;
   const R EK = pK * inv_gm1 + half_(rK * keK);
   const R mn = rK * uK;
-  const R Dd = SK - Ss;
-  const R fac = div_(mK, Dd);
-  const R w = div_(pK, mK);
-  const R Y = Ss - uK, Z = Ss + w;
-  const R X = EK * irK + Y * Z;
   // ---- reverse
   R lrK = 0, luK = 0, lt1 = 0, lt2 = 0, lpK = 0, lkeK = 0, lirK = 0, lSK = 0, lmK = 0, lSs = 0, lEK = 0, lmn = 0;
   if (star) {
+    // star state of side K: fac = m_K / D (its density), D = S_K - S*, w = p_K / m_K
+    const R Dd = SK - Ss;
+    const R imK = rcp_(mK), iDd = rcp_(Dd);
+    const R fac = mK * iDd;
+    const R w = pK * imK;
+    const R Y = Ss - uK, Z = Ss + w;
+    const R X = EK * irK + Y * Z;
     const R UK[5] = {rK, mn, rK * t1, rK * t2, EK};
     const R Us[5] = {fac, fac * Ss, fac * t1, fac * t2, fac * X};
     R lUs[5], lUK[5];
@@ -103,10 +106,10 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
     lirK += EK * lX;
     lSs += (Z + Y) * lX;
     luK -= Z * lX;
-    const R lwm = div_(Y * lX, mK);  // adjoint of w = p_K / m_K, over m_K
+    const R lwm = (Y * lX) * imK;  // adjoint of w = p_K / m_K, over m_K
     lpK += lwm;
     lmK -= lwm * w;
-    const R lfd = div_(lfac, Dd);  // adjoint of fac = m_K / D, over D
+    const R lfd = lfac * iDd;  // adjoint of fac = m_K / D, over D
     lmK += lfd;
     const R lD = -(lfd * fac);
     lSK += lD;
@@ -140,7 +143,7 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
     lSR += lSK; lmR += lmK;
   }
   // S* = num / den
-  const R lnum = div_(lSs, den);
+  const R lnum = lSs * iden;
   const R lden = -(lnum * Ss);
   lpR += lnum;
   lpL -= lnum;
@@ -160,7 +163,8 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   if (selL) { luL += lSL; lcL -= lSL; } else { luR += lSL; lcR -= lSL; }
   if (selR) { luL += lSR; lcL += lSR; } else { luR += lSR; lcR += lSR; }
   // c = sqrt(gamma p ir), ir = 1/rho
-  const R lxL = div_(half_(lcL), cL), lxR = div_(half_(lcR), cR);
+  const R icc = rcp_(cL * cR);  // 1/c_L = c_R icc, 1/c_R = c_L icc
+  const R lxL = half_(lcL) * (cR * icc), lxR = half_(lcR) * (cL * icc);
   lpL += gamma * irL * lxL;
   lirL += gamma * qL[4] * lxL;
   lpR += gamma * irR * lxR;
