@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
   flush_flags(flags, err);
 }
 
-// Per cell: lam_n = lam_np1 + recover^T(lq_pred + slope gathers).
+// Per cell: lam_n = lam_np1 + recover^T(lq_pred + slope gathers).  One thread per cell of a
+// 32 x 8 x 1 block over (x, y, z): indices from the grid, periodic neighbours by one compare each.
 template <class Pol>
 __global__ void __launch_bounds__(256) k_adj_cells(PatchIO<typename Pol::S> P, PatchIO<typename Pol::S> L,
                                                    Params prm, AdjScratch<typename Pol::R> scr,
@@ -284,44 +285,41 @@ __global__ void __launch_bounds__(256) k_adj_cells(PatchIO<typename Pol::S> P, P
                                                    long long osy, long long osz) {
   using S = typename Pol::S;
   using R = typename Pol::R;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (i >= P.nx || j >= P.ny) return;
   S* outp[5] = {o0, o1, o2, o3, o4};
-  const long long nxy = (long long)P.nx * P.ny, N = nxy * P.nz;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(c / nxy);
-    const long long r = c - (long long)k * nxy;
-    const int j = (int)(r / P.nx), i = (int)(r - (long long)j * P.nx);
-    const long long nb[3][2] = {
-        {((long long)k * P.ny + j) * P.nx + wrapi(i - 1, P.nx), ((long long)k * P.ny + j) * P.nx + wrapi(i + 1, P.nx)},
-        {((long long)k * P.ny + wrapi(j - 1, P.ny)) * P.nx + i, ((long long)k * P.ny + wrapi(j + 1, P.ny)) * P.nx + i},
-        {((long long)wrapi(k - 1, P.nz) * P.ny + j) * P.nx + i, ((long long)wrapi(k + 1, P.nz) * P.ny + j) * P.nx + i}};
-    const unsigned cc = scr.code[c];
-    R lq[5];
+  const long long nx = P.nx, nxy = nx * P.ny, N = nxy * P.nz;
+  const long long c = k * nxy + j * nx + i;
+  const long long nb[3][2] = {{c + (i == 0 ? nx - 1 : -1), c + (i == P.nx - 1 ? 1 - nx : 1)},
+                              {c + (j == 0 ? nxy - nx : -nx), c + (j == P.ny - 1 ? nx - nxy : nx)},
+                              {c + (k == 0 ? N - nxy : -nxy), c + (k == P.nz - 1 ? nxy - N : nxy)}};
+  const unsigned cc = scr.code[c];
+  R lq[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) lq[v] = scr.lq[v * N + c];
+  for (int v = 0; v < 5; ++v) lq[v] = scr.lq[v * N + c];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const unsigned cm = scr.code[nb[d][0]], cp = scr.code[nb[d][1]];
+  for (int d = 0; d < 3; ++d) {
+    const unsigned cm = scr.code[nb[d][0]], cp = scr.code[nb[d][1]];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const int sh = 2 * (5 * d + v);
-        float a0, b0, am, bm, ap, bp;
-        code_weights((cc >> sh) & 3u, prm.limiter, a0, b0);
-        code_weights((cm >> sh) & 3u, prm.limiter, am, bm);
-        code_weights((cp >> sh) & 3u, prm.limiter, ap, bp);
-        const R* ld = scr.ld + (long long)(5 * d + v) * N;
-        lq[v] += (mulf_(ld[c], a0 - b0) + mulf_(ld[nb[d][0]], bm)) - mulf_(ld[nb[d][1]], ap);
-      }
+    for (int v = 0; v < 5; ++v) {
+      const int sh = 2 * (5 * d + v);
+      float a0, b0, am, bm, ap, bp;
+      code_weights((cc >> sh) & 3u, prm.limiter, a0, b0);
+      code_weights((cm >> sh) & 3u, prm.limiter, am, bm);
+      code_weights((cp >> sh) & 3u, prm.limiter, ap, bp);
+      const R* ld = scr.ld + (long long)(5 * d + v) * N;
+      lq[v] += (mulf_(ld[c], a0 - b0) + mulf_(ld[nb[d][0]], bm)) - mulf_(ld[nb[d][1]], ap);
     }
-    const long long a = (long long)k * P.isz + (long long)j * P.isy + i;
-    const long long la = (long long)k * L.isz + (long long)j * L.isy + i;
-    R U[5], lU[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) U[v] = R(P.in[v][a]);
-    recover_adj(U, prm, lq, lU);
-    const long long o = (long long)(k + out_g) * osz + (long long)(j + out_g) * osy + (i + out_g);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) outp[v][o] = (S)((R)L.in[v][la] + lU[v]);
   }
+  const long long a = (long long)k * P.isz + (long long)j * P.isy + i;
+  const long long la = (long long)k * L.isz + (long long)j * L.isy + i;
+  R U[5], lU[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) U[v] = R(P.in[v][a]);
+  recover_adj(U, prm, lq, lU);
+  const long long o = (long long)(k + out_g) * osz + (long long)(j + out_g) * osy + (i + out_g);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) outp[v][o] = (S)(R(L.in[v][la]) + lU[v]);
 }
 
 template <class Pol>
@@ -394,9 +392,8 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
                                                         err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  long long blocks = ((long long)N + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_adj_cells<Pol><<<(unsigned)blocks, 256, 0, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, scr,
+  const dim3 cgrid((U.nx + 31) / 32, (U.ny + 7) / 8, U.nz);
+  k_adj_cells<Pol><<<cgrid, dim3(32, 8), 0, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, scr,
                                                     (S*)lam_out[0], (S*)lam_out[1], (S*)lam_out[2], (S*)lam_out[3],
                                                     (S*)lam_out[4], lam.gout, lam.osy, lam.osz);
   return cudaGetLastError();
