@@ -133,7 +133,8 @@ int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5],
 
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
  * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64,
- * HYDRO_FP64_DF (the same reverse sweep in double-float arithmetic) or HYDRO_FP32.  U_n: the
+ * HYDRO_FP64_DF (which runs the FP64 reverse sweep: faster on GB300 than a double-float one) or
+ * HYDRO_FP32.  U_n: the
  * state the forward step started from; dt_dev[p] its time step; lam_np1, lam_n: adjoint fields
  * with the same layout and element type as U_n (must not overlap).  HYDRO_MIXED returns
  * HYDRO_ERR_ARG.  The

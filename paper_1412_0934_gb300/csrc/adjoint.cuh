@@ -336,10 +336,6 @@ template <>
 struct AdjTile<PolMixed> {
   static constexpr int TX = 16, TY = 8;
 };
-template <>
-struct AdjTile<PolDF> {
-  static constexpr int TX = 8, TY = 8;
-};
 
 template <class Pol>
 size_t adjoint_scratch_bytes(int nx, int ny, int nz) {
@@ -352,8 +348,8 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
                            const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s) {
   using R = typename Pol::R;
   using S = typename Pol::S;
-  if constexpr (std::is_same<Pol, PolMixed>::value) {
-    return cudaErrorNotSupported;  // the adjoint runs in FP64, double-float FP64 or FP32
+  if constexpr (std::is_same<Pol, PolMixed>::value || std::is_same<Pol, PolDF>::value) {
+    return cudaErrorNotSupported;  // the adjoint kernels are FP64 and FP32 (double-float uses FP64's)
   } else {
   constexpr int TX = AdjTile<Pol>::TX, TY = AdjTile<Pol>::TY;
   if (scratch_bytes < adjoint_scratch_bytes<Pol>(U.nx, U.ny, U.nz)) return cudaErrorInvalidValue;

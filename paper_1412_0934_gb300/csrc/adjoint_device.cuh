@@ -3,15 +3,9 @@
 // 2-bit code), and the primitive recovery.  Each function recomputes the forward values it needs
 // and returns adjoints with respect to its inputs.
 #pragma once
-#include "df.cuh"
 #include "hydro_device.cuh"
 
 namespace hydro {
-
-// Compound assignment and division of double-float values, used by the reverse sweeps below.
-__device__ __forceinline__ df& operator+=(df& a, const df& b) { return a = a + b; }
-__device__ __forceinline__ df& operator-=(df& a, const df& b) { return a = a - b; }
-__device__ __forceinline__ df operator/(const df& a, const df& b) { return div_(a, b); }
 
 // ------------------------------------------------------------------ limiter with branch code
 // Code: 0 zero slope, 1 the first argument (a, or 2a for MC), 2 the second (b, or 2b for MC),

@@ -508,6 +508,10 @@ int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_de
                        const hydro_patch* lam_n, int npatch) {
   if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1) return HYDRO_ERR_ARG;
   if (c->cfg.precision == HYDRO_MIXED) return HYDRO_ERR_ARG;
+  // The double-float context runs the FP64 reverse sweep: on GB300 it is faster than the same
+  // sweep in double-float arithmetic, whose register footprint (~240 per thread) leaves too few
+  // warps per SM to cover the FP32 pipes' dependent chains; both keep the FP64 accuracy.
+  const hydro::KernelOps* aops = c->cfg.precision == HYDRO_FP64_DF ? hydro::ops_for(HYDRO_FP64) : c->ops;
   for (int i = 0; i < npatch; ++i) {
     const hydro_patch &U = U_n[i], &L = lam_np1[i], &O = lam_n[i];
     if (!valid_patch(c, U) || !valid_patch(c, L) || !valid_patch(c, O)) return HYDRO_ERR_ARG;
@@ -517,7 +521,7 @@ int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_de
   }
   for (int i = 0; i < npatch; ++i) {
     const hydro_patch &U = U_n[i], &L = lam_np1[i], &O = lam_n[i];
-    const size_t need = c->ops->adjoint_scratch_bytes(U.nx, U.ny, U.nz);
+    const size_t need = aops->adjoint_scratch_bytes(U.nx, U.ny, U.nz);
     if (need > c->adj_cap) {
       cudaFree(c->d_adj);
       c->d_adj = nullptr;
@@ -529,8 +533,8 @@ int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_de
     for (int v = 0; v < 5; ++v) outp[v] = O.U[v];
     HostPatchIO lam = make_io(L, O);
     c->launches += 2;
-    cudaError_t e = c->ops->adjoint(make_io(U, O), lam, outp, c->prm, dt_dev + i, c->d_adj, c->adj_cap, c->d_err,
-                                    c->stream);
+    cudaError_t e = aops->adjoint(make_io(U, O), lam, outp, c->prm, dt_dev + i, c->d_adj, c->adj_cap, c->d_err,
+                                  c->stream);
     if (e == cudaErrorNotSupported) return HYDRO_ERR_STATE;
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
   }

@@ -1,0 +1,175 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times, on sampled
+outputs the oracle computes one by one: each sampled cell from its own 5^3 periodic neighbourhood
+(the step's stencil radius is 2), each sampled patch or oct group whole.
+  - 512^3 Mach-5 turbulence + Sedov cell, MinMod (the headline workload): the CFL dt of the whole
+    box (oracle over every cell), one step in double-float, FP64 and FP32 with the bench's tile
+    (16x16, z chunk 128), and the fused dt of the result (oracle over every cell again);
+  - 1024^3 Mach-10 MC FP32 (the first step of the graph-captured run): the step on samples, the dt
+    at the cell the GPU's dt comes from and a lower bound at every sampled cell;
+  - the 4096-patch mixed-precision set in one persistent launch, per-patch dt, and 262144 oct groups."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from hydro_testlib import ctx
+
+import paper_1412_0934_gb300 as hy
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "df64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+DT_TOL = {"fp64": 1e-13, "df64": 1e-12, "fp32": 1e-6, "mixed": 1e-6}
+
+
+def sample_cells(shape, count, seed):
+    """Random cells plus the box's corners and cells on both sides of tile and z-chunk seams."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    cells = [tuple(int(rng.integers(0, m)) for m in shape) for _ in range(count)]
+    for z in (0, 1, 127, 128, nz - 1):
+        for y in (0, 15, 16, ny - 1):
+            for x in (0, 15, 16, nx - 1):
+                cells.append((z % nz, y % ny, x % nx))
+    return np.array(cells)
+
+
+def neighbourhoods(U, cells):
+    """(S, 5, 5, 5, 5) periodic 5^3 neighbourhoods of the cells (z, y, x), gathered on U's device."""
+    _, NZ, NY, NX = U.shape
+    c = torch.as_tensor(cells, device=U.device, dtype=torch.long)
+    r = torch.arange(-2, 3, device=U.device)
+    iz = (c[:, 0, None] + r) % NZ
+    iy = (c[:, 1, None] + r) % NY
+    ix = (c[:, 2, None] + r) % NX
+    flat = (iz[:, :, None, None] * NY + iy[:, None, :, None]) * NX + ix[:, None, None, :]
+    return U.reshape(5, -1)[:, flat].permute(1, 0, 2, 3, 4).double().cpu().numpy()
+
+
+def oracle_cells(nbs, dx, dt, cfg):
+    return np.stack([oracle.step_patch(nb, dx, dt, cfg)[:, 0, 0, 0] for nb in nbs])
+
+
+def fieldwise(got, want):
+    scale = np.maximum(np.abs(want).max(axis=0), 1e-300)
+    return (np.abs(got - want) / scale).max(axis=0)
+
+
+@pytest.mark.parametrize("precision", ["df64", "fp64", "fp32"])
+def test_512_headline_step_sampled(precision):
+    n = 512
+    dx = 1.0 / n
+    cfg = oracle.config()
+    c = ctx(precision)
+    hy.hydro_set_tuning(c, 0, 128)
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    U = workloads.turbulent_state(n, seed=2, mach=5.0, sedov=True, device="cuda").to(dtype).contiguous()
+    d = torch.empty(2, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(c, hy.patch(U, 0, dx), d[0:1])
+    Uh = U.double().cpu().numpy()
+    assert d[0].item() == pytest.approx(oracle.cfl_periodic(Uh, dx, cfg), rel=DT_TOL[precision])
+    del Uh
+    out = torch.empty_like(U)
+    hy.hydro_step(c, hy.patch(U, 0, dx), hy.patch(out, 0, dx), d[0:1], d[1:2])
+    torch.cuda.synchronize()
+    cells = sample_cells((n, n, n), 3000, seed=11)
+    want = oracle_cells(neighbourhoods(U, cells), dx, d[0].item(), cfg)
+    ci = torch.as_tensor(cells, device="cuda")
+    got = out[:, ci[:, 0], ci[:, 1], ci[:, 2]].double().cpu().numpy().T
+    err = fieldwise(got, want)
+    assert err.max() <= TOL[precision], err
+    Oh = out.double().cpu().numpy()
+    assert d[1].item() == pytest.approx(oracle.cfl_periodic(Oh, dx, cfg), rel=DT_TOL[precision])
+    rc, bits = hy.hydro_get_error(c)
+    assert rc == hy.HYDRO_OK, bits
+
+
+def test_1024_mach10_mc_fp32_step_sampled():
+    n = 1024
+    dx = 1.0 / n
+    cfg = oracle.config(limiter="mc")
+    c = ctx("fp32", "mc")
+    hy.hydro_set_tuning(c, 0, 128)
+    U = workloads.turbulent_state(n, seed=5, mach=10.0, sigma_rho=1.5, p_over_rho=1e-5, sedov=False,
+                                  device="cuda").float().contiguous()
+    d = torch.empty(1, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(c, hy.patch(U, 0, dx), d)
+    dt = d.item()
+    # the cell the dt comes from (largest |u|+|v|+|w|+3c, located here with torch) and samples
+    W = U.double()
+    rho = W[0]
+    ke = (W[1] ** 2 + W[2] ** 2 + W[3] ** 2) / rho
+    p = ((5.0 / 3.0 - 1.0) * (W[4] - 0.5 * ke)).clamp_min(1e-14)
+    s = (W[1].abs() + W[2].abs() + W[3].abs()) / rho + 3.0 * torch.sqrt((5.0 / 3.0) * p / rho)
+    top = np.array(np.unravel_index(int(torch.argmax(s).item()), (n, n, n)))
+    del W, rho, ke, p, s
+    cells = np.concatenate([top[None], sample_cells((n, n, n), 2000, seed=12)])
+    nbs = neighbourhoods(U, cells)
+    dts_o = np.array([oracle.cfl_patch(nb, dx, cfg) for nb in nbs])  # a 1-cell interior: the cell's dt
+    assert dt == pytest.approx(dts_o[0], rel=DT_TOL["fp32"])
+    assert (dts_o >= dt * (1 - DT_TOL["fp32"])).all()
+    out = torch.empty_like(U)
+    hy.hydro_step(c, hy.patch(U, 0, dx), hy.patch(out, 0, dx), d)
+    torch.cuda.synchronize()
+    want = oracle_cells(nbs, dx, dt, cfg)
+    ci = torch.as_tensor(cells, device="cuda")
+    got = out[:, ci[:, 0], ci[:, 1], ci[:, 2]].double().cpu().numpy().T
+    err = fieldwise(got, want)
+    assert err.max() <= TOL["fp32"], err
+
+
+def test_4096_patches_and_262144_octs_mixed_sampled():
+    cfg = oracle.config()
+    c = ctx("mixed")
+    parent = workloads.turbulent_state(256, seed=3, sedov=False, device="cuda")
+    descs = workloads.patch_set(4096, seed=3)
+    origins = workloads.patch_origins(descs, parent.shape[1:], seed=3)
+    ins, outs, keep = [], [], []
+    for dsc, o in zip(descs, origins):
+        Ug = workloads.ghosted_from_periodic(parent, o, (dsc["nx"], dsc["ny"], dsc["nz"])).contiguous()
+        Vg = torch.empty_like(Ug)
+        keep.append((Ug, Vg))
+        ins.append(hy.patch(Ug, 2, dsc["dx"], dsc["level"]))
+        outs.append(hy.patch(Vg, 2, dsc["dx"], dsc["level"]))
+    dt = torch.empty(len(ins), dtype=torch.float64, device="cuda")
+    dn = torch.empty_like(dt)
+    hy.hydro_cfl_dt(c, ins, dt)
+    hy.hydro_step(c, ins, outs, dt, dn)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(13)
+    big = sorted(range(len(descs)), key=lambda i: -descs[i]["nx"] * descs[i]["ny"] * descs[i]["nz"])[:4]
+    picks = sorted(set(big) | set(int(i) for i in rng.choice(len(descs), 20, replace=False)))
+    dth, dnh = dt.cpu().numpy(), dn.cpu().numpy()
+    for i in picks:
+        Ug, Vg = keep[i]
+        Uh = Ug.cpu().numpy()
+        dx = descs[i]["dx"]
+        assert dth[i] == pytest.approx(oracle.cfl_patch(Uh, dx, cfg), rel=DT_TOL["mixed"])
+        want = oracle.step_patch(Uh, dx, dth[i], cfg)
+        got = Vg[:, 2:-2, 2:-2, 2:-2].cpu().numpy()
+        err = fieldwise(got.reshape(5, -1).T, want.reshape(5, -1).T)
+        assert err.max() <= TOL["mixed"], (i, err)
+        # fused dt of the result: the oracle's CFL of the updated interior (ghosts: any values
+        # give the same dt, the CFL reads the interior only)
+        Vh = Vg.cpu().numpy()
+        Vh[:, 2:-2, 2:-2, 2:-2] = got
+        assert dnh[i] == pytest.approx(oracle.cfl_patch(Vh, dx, cfg), rel=DT_TOL["mixed"])
+    del keep, ins, outs
+    # oct groups
+    G = 262144
+    og = workloads.oct_origins(G, parent.shape[1:], seed=3)
+    g = workloads.gather_octs(parent, og).contiguous()
+    go = torch.empty((5, G, 2, 2, 2), dtype=torch.float64, device="cuda")
+    dto = torch.tensor([0.5 * dth.min()], dtype=torch.float64, device="cuda")
+    dxo = 1.0 / 256
+    hy.hydro_step_octs(c, g, go, dxo, dto)
+    torch.cuda.synchronize()
+    sel = rng.choice(G, 1500, replace=False)
+    gh = g[:, torch.as_tensor(sel, device="cuda")].permute(1, 0, 2, 3, 4).cpu().numpy()
+    want = np.stack([oracle.step_patch(b, dxo, dto.item(), cfg) for b in gh])  # (S, 5, 2, 2, 2)
+    got = go[:, torch.as_tensor(sel, device="cuda")].permute(1, 0, 2, 3, 4).cpu().numpy()
+    err = fieldwise(got.transpose(0, 2, 3, 4, 1).reshape(-1, 5), want.transpose(0, 2, 3, 4, 1).reshape(-1, 5))
+    assert err.max() <= TOL["mixed"], err
+    rc, bits = hy.hydro_get_error(c)
+    assert rc == hy.HYDRO_OK, bits
