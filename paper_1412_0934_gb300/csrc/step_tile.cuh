@@ -2,13 +2,15 @@
 // shared memory (the GPU solves hydro on chunks of patches carrying their boundary cells,
 // Sec. 3; every flux that updates a patch's cells is computed on the GPU, Sec. 4).
 //
-// Per plane p of the march (p = z0-1 .. z1), with a 3-plane ring of primitive planes:
-//   A  load U of plane p+1 over the tile plus 2 halo cells per side, recover q -> ring
-//   B  slopes (x, y, z) and Hancock predictor of plane p over the tile plus a 1-cell ring;
-//      each interior column also forms its z face states and the HLLC flux of face p-1/2
-//   C  HLLC fluxes of the x and y faces of plane p (each face once)
-//   D  each interior column updates plane p-1:  U - dt/dx ((dFx + dFy) + dFz), writes it, and
-//      folds the CFL speed of the new state into a running maximum
+// Per plane p of the march (p = z0-1 .. z1), with a 3-plane ring of primitive planes, two phases
+// separated by block barriers:
+//   1  slopes (x, y, z) and Hancock predictor of plane p over the tile (plus a 1-cell ring when
+//      plane p's x/y faces are needed); each interior column forms its z face states and the HLLC
+//      flux of face p-1/2, then updates plane p-1:  U - dt/dx ((dFx + dFy) + dFz) from the x/y
+//      fluxes of plane p-1 in shared memory, writes it, and folds the CFL speed of the new state
+//      into a running maximum
+//   2  HLLC fluxes of the x and y faces of plane p (each face once), and the load of U of plane
+//      p+2 over the tile plus 2 halo cells per side, recovered to q into the ring
 // Global memory is read once per cell per plane (halo re-reads come from L2) and written once.
 #pragma once
 #include <type_traits>
@@ -212,10 +214,13 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     const int zi = periodic ? wrapi(z, P.nz) : z + 2;
     return (long long)zi * P.isz;
   };
+  // Plane loads: cell c of the (TX+4) x (TY+4) halo plane goes to thread NT-1-c (mod NT), so the
+  // threads that load a second cell are the last ones, not the warps that also take the tile's edge
+  // faces.
   auto load_plane = [&](int z) {
     const int slot = ring_slot(z);
     const long long zo = plane_offset(z);
-    for (int c = tid; c < QN; c += NT) {
+    for (int c = NT - 1 - tid; c < QN; c += NT) {
       const int cy = c / QW, cx = c - cy * QW;
       const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
       S U[5];
@@ -226,38 +231,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
       sm.q[slot].st(cy, cx, q);
     }
   };
-  // Float state: the next plane's loads are issued into registers one iteration early, so their
-  // latency overlaps the predictor, flux and update phases of the current plane.
-  constexpr bool kPrefetch = false;
   constexpr bool kCompact = std::is_same<R, df>::value;  // double-float arithmetic
-  constexpr int NPF = kPrefetch ? (QN + NT - 1) / NT : 1;
-  S pre[NPF][5];
-  auto prefetch = [&](int z) {
-    const long long zo = plane_offset(z);
-#pragma unroll
-    for (int k = 0; k < NPF; ++k) {
-      const int c = tid + k * NT;
-      if (c < QN) {
-        const int cy = c / QW, cx = c - cy * QW;
-        const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) pre[k][v] = __ldg(P.in[v] + a);
-      }
-    }
-  };
-  auto commit = [&](int z) {
-    const int slot = ring_slot(z);
-#pragma unroll
-    for (int k = 0; k < NPF; ++k) {
-      const int c = tid + k * NT;
-      if (c < QN) {
-        const int cy = c / QW, cx = c - cy * QW;
-        R q[5];
-        Pol::recover(pre[k], prm, q, flags);
-        sm.q[slot].st(cy, cx, q);
-      }
-    }
-  };
 
   const R hdt = (R)(0.5 * dt / P.dx);
   const R dtdx = (R)(dt / P.dx);
@@ -265,59 +239,111 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
   const bool own = (gx < P.nx) && (gy < P.ny);
   const R gamma = kc<R>(prm, K_GAMMA);
 
-  // Carried across planes: the lower z state of the next face, and for the plane awaiting its
-  // update, acc = (x and y flux differences) - (flux through its lower z face).
-  R LzPrev[5], acc[5], Fz[5];
+  // Carried across planes: the lower z state of the next face, and the flux through the lower z
+  // face of the plane awaiting its update.
+  R LzPrev[5], FzPrev[5], Fz[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { LzPrev[v] = acc[v] = Fz[v] = R(0); }
+  for (int v = 0; v < 5; ++v) { LzPrev[v] = FzPrev[v] = Fz[v] = R(0); }
+
+  auto z_faces = [&](int p, const R qh[5], const R dqz[5]) {
+    R Lz[5], Rz[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      Lz[v] = qh[v] + half_(dqz[v]);
+      Rz[v] = qh[v] - half_(dqz[v]);
+    }
+    floor_state(Lz, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+    floor_state(Rz, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+    if (p >= z0) hllc<2>(LzPrev, Rz, gamma, kc<R>(prm, K_IGM1), Fz);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) LzPrev[v] = Lz[v];
+  };
+  // Update of plane k = p-1 by this column: the x and y flux differences of plane k (written to
+  // shared memory by the previous plane's phase 2) and its two z fluxes.
+  auto update = [&](int k) {
+    R xp[5], xm[5], yp[5], ym[5], dF[5];
+    sm.fx.ld(tj, ti + 1, xp);
+    sm.fx.ld(tj, ti, xm);
+    sm.fy.ld(tj + 1, ti, yp);
+    sm.fy.ld(tj, ti, ym);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dF[v] = (xp[v] - xm[v]) + (yp[v] - ym[v]);
+    if (own) {
+      const long long ai = (long long)(k + P.gin) * P.isz + (long long)(gy + P.gin) * P.isy + (gx + P.gin);
+      const long long ao = (long long)(k + P.gout) * P.osz + (long long)(gy + P.gout) * P.osy + (gx + P.gout);
+      S Un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R div = (dF[v] - FzPrev[v]) + Fz[v];
+        Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, div);
+        P.out[v][ao] = Un[v];
+      }
+      if (want_cfl) {
+        const R sp = Pol::speed(Un, prm, flags);
+        smax = sp > smax ? sp : smax;
+      }
+    }
+  };
+  auto ring_cell = [&](int r, int& ci, int& cj) {
+    if (r < TX) { ci = r; cj = -1; }
+    else if (r < 2 * TX) { ci = r - TX; cj = TY; }
+    else if (r < 2 * TX + TY) { ci = -1; cj = r - 2 * TX; }
+    else { ci = TX; cj = r - 2 * TX - TY; }
+  };
+  constexpr int NR = 2 * (TX + TY);  // ring cells
+  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
 
   load_plane(z0 - 2);
   load_plane(z0 - 1);
-  if constexpr (kPrefetch) prefetch(z0);
+  load_plane(z0);
+  __syncthreads();
+  // Per plane p, two phases separated by barriers:
+  //   1  predict plane p (tile; its ring when its x/y faces are needed), the z face p-1/2 of each
+  //      column, and the update of plane p-1 (x/y flux differences from shared memory)
+  //   2  the x/y faces of plane p, and the load + recovery of plane p+2 into the ring slot that
+  //      plane p-1 held
   for (int p = z0 - 1; p <= z1; ++p) {
-    // ---- A
-    if constexpr (kPrefetch) {
-      commit(p + 1);
-      if (p + 2 <= z1 + 1) prefetch(p + 2);
-    } else {
-      load_plane(p + 1);
-    }
-    __syncthreads();
-    // ---- B: the interior cell of this thread (with its z faces), then the ring cells
     const int sm1 = ring_slot(p - 1), s0 = ring_slot(p), sp1 = ring_slot(p + 1);
     const bool xy = p >= z0 && p < z1;
-    auto z_faces = [&](const R qh[5], const R dqz[5]) {
-      R Lz[5], Rz[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Lz[v] = qh[v] + half_(dqz[v]);
-        Rz[v] = qh[v] - half_(dqz[v]);
-      }
-      floor_state(Lz, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
-      floor_state(Rz, kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
-      if (p >= z0) hllc<2>(LzPrev, Rz, gamma, kc<R>(prm, K_IGM1), Fz);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) LzPrev[v] = Lz[v];
-    };
-    auto ring_cell = [&](int r, int& ci, int& cj) {
-      if (r < TX) { ci = r; cj = -1; }
-      else if (r < 2 * TX) { ci = r - TX; cj = TY; }
-      else if (r < 2 * TX + TY) { ci = -1; cj = r - 2 * TX; }
-      else { ci = TX; cj = r - 2 * TX - TY; }
-    };
-    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+    const bool upd = p >= z0 + 1;
+    // ---- phase 1
     if constexpr (kCompact) {
       // One call site each for the predictor and the x/y face flux: double-float code is large
-      // enough that several inlined copies overflow the instruction cache.
-      for (int c = tid; c < (xy ? NT + 2 * (TX + TY) : NT); c += NT) {
+      // enough that several inlined copies overflow the instruction cache.  The ring cells go
+      // to the last threads.
+      for (int it = 0; it < 2; ++it) {
         int ci = ti, cj = tj;
-        if (c >= NT) ring_cell(c - NT, ci, cj);
+        if (it == 1) {
+          if (!xy || tid < NT - NR) break;
+          ring_cell(tid - (NT - NR), ci, cj);
+        }
         R qh[5], dqz[5];
         predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
-        if (c < NT) z_faces(qh, dqz);
+        if (it == 0) {
+          z_faces(p, qh, dqz);
+          if (upd) update(p - 1);
+        }
       }
-      __syncthreads();
-      if (xy) {
+    } else {
+      {
+        R qh[5], dqz[5];
+        predict_cell(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
+        z_faces(p, qh, dqz);
+      }
+      if (upd) update(p - 1);
+      if (xy && tid >= NT - NR) {
+        int ci, cj;
+        ring_cell(tid - (NT - NR), ci, cj);
+        R qh[5], dqz[5];
+        predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) FzPrev[v] = Fz[v];
+    __syncthreads();
+    // ---- phase 2
+    if (xy) {
+      if constexpr (kCompact) {
         for (int f = tid; f < NXF + NYF; f += NT) {
           int d, i, j;
           if (f < NXF) { d = 0; i = f % (TX + 1) - 1; j = f / (TX + 1); }
@@ -327,24 +353,9 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
           if (d == 0) sm.fx.st(j, i + 1, F);
           else sm.fy.st(j + 1, i, F);
         }
-      }
-      __syncthreads();
-    } else {
-      {
-        R qh[5], dqz[5];
-        predict_cell(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
-        z_faces(qh, dqz);
-      }
-      if (xy && tid < 2 * (TX + TY)) {
-        int ci, cj;
-        ring_cell(tid, ci, cj);
-        R qh[5], dqz[5];
-        predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
-      }
-      __syncthreads();
-      // ---- C: the x face on this column's right and the y face above it; the first warps also
-      // take the faces on the tile's left and bottom edges
-      if (xy) {
+      } else {
+        // the x face on this column's right and the y face above it; the first warps also take
+        // the faces on the tile's left and bottom edges
         R F[5];
         face_flux<0>(sm, ti, tj, prm, F);
         sm.fx.st(tj, ti + 1, F);
@@ -358,39 +369,9 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
           sm.fy.st(0, tid - 32, F);
         }
       }
-      __syncthreads();
     }
-    // ---- D
-    R dF[5];
-    if (p >= z0 && p < z1) {
-      R xp[5], xm[5], yp[5], ym[5];
-      sm.fx.ld(tj, ti + 1, xp);
-      sm.fx.ld(tj, ti, xm);
-      sm.fy.ld(tj + 1, ti, yp);
-      sm.fy.ld(tj, ti, ym);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) dF[v] = (xp[v] - xm[v]) + (yp[v] - ym[v]);
-    }
-    if (p >= z0 + 1 && own) {
-      const int k = p - 1;
-      const long long ai = (long long)(k + P.gin) * P.isz + (long long)(gy + P.gin) * P.isy + (gx + P.gin);
-      const long long ao = (long long)(k + P.gout) * P.osz + (long long)(gy + P.gout) * P.osy + (gx + P.gout);
-      S Un[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const R div = acc[v] + Fz[v];
-        Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, div);
-        P.out[v][ao] = Un[v];
-      }
-      if (want_cfl) {
-        const R s = Pol::speed(Un, prm, flags);
-        smax = s > smax ? s : smax;
-      }
-    }
-    if (p >= z0 && p < z1) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] = dF[v] - Fz[v];
-    }
+    if (p + 2 <= z1 + 1) load_plane(p + 2);
+    __syncthreads();
   }
 }
 
