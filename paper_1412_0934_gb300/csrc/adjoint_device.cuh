@@ -41,8 +41,9 @@ __device__ __forceinline__ void code_weights(unsigned code, int lim, float& alph
 template <class R>
 __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R keL, R keR, R gamma, R inv_gm1,
                                               const R lamF[5], R lqL[5], R lqR[5], R& lkeL, R& lkeR) {
-  // ---- forward recomputation
-  const R irL = rcp_(qL[0]), irR = rcp_(qR[0]);
+  // ---- forward recomputation (the values that select branches exactly as hllc_core forms them)
+  R irL, irR;
+  rcp2(qL[0], qR[0], irL, irR);
   const R cL = rsqrt_(gamma * qL[4] * irL);
   const R cR = rsqrt_(gamma * qR[4] * irR);
   const R uL = qL[1], uR = qR[1];
@@ -77,7 +78,8 @@ __device__ __forceinline__ void hllc_core_adj(const R qL[5], const R qR[5], R ke
   if (star) {
     // star state of side K: fac = m_K / D (its density), D = S_K - S*, w = p_K / m_K
     const R Dd = SK - Ss;
-    const R imK = rcp_(mK), iDd = rcp_(Dd);
+    R iDd, imK;
+    rcp2(Dd, mK, iDd, imK);
     const R fac = mK * iDd;
     const R w = pK * imK;
     const R Y = Ss - uK, Z = Ss + w;

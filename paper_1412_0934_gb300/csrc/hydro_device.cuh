@@ -192,9 +192,29 @@ __device__ __forceinline__ void floor_state(R q[5], R rho_floor, R p_floor) {
 // u_t2, p); ke = u^2 + v^2 + w^2 summed in x, y, z order.  F = F_L if 0 <= S_L; F_R if S_R <= 0;
 // else F_K + S_K (U*_K - U_K) with K = L if S* >= 0 else R (Davis speeds, Batten et al. star
 // state).  Only the upwind side's physical flux is formed; branches are selected, not multiplied.
+// 1/a and 1/b.  In double, where a division is a long sequence on the FP64 pipe, both come from
+// one division, 1/a = b/(ab), 1/b = a/(ab) (the operands here are positive densities, or a mass
+// flux and a speed difference, whose products stay far inside the exponent range).  A float
+// reciprocal is one SFU instruction, and a double-float one costs about what the two extra
+// double-float products would: two reciprocals.
+__device__ __forceinline__ void rcp2(float a, float b, float& ra, float& rb) {
+  ra = rcp_(a);
+  rb = rcp_(b);
+}
+__device__ __forceinline__ void rcp2(double a, double b, double& ra, double& rb) {
+  const double i = 1.0 / (a * b);
+  ra = b * i;
+  rb = a * i;
+}
+__device__ __forceinline__ void rcp2(const df& a, const df& b, df& ra, df& rb) {
+  ra = rcp_(a);
+  rb = rcp_(b);
+}
+
 template <class R>
 __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R keR, R gamma, R inv_gm1, R F[5]) {
-  const R irL = rcp_(qL[0]), irR = rcp_(qR[0]);
+  R irL, irR;
+  rcp2(qL[0], qR[0], irL, irR);
   const R cL = rsqrt_(gamma * qL[4] * irL);
   const R cR = rsqrt_(gamma * qR[4] * irR);
   const R uL = qL[1], uR = qR[1];
@@ -221,9 +241,11 @@ __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R
   // Star state of side K: density r* = m_K/(S_K - S*), velocity S*, pressure p* = p_K + m_K (S* - u_K),
   // energy E* = r* (E_K/rho_K + (S* - u_K)(S* + p_K/m_K)).  F*_K = F_K + S_K (U*_K - U_K) equals the
   // physical flux of that state, so one flux formula serves every branch.
-  const R rs = div_(mK, SK - Ss);
+  R iD, imK;
+  rcp2(SK - Ss, mK, iD, imK);
+  const R rs = mK * iD;
   const R ps = pK + mK * (Ss - uK);
-  const R Es = rs * (EK * irK + (Ss - uK) * (Ss + div_(pK, mK)));
+  const R Es = rs * (EK * irK + (Ss - uK) * (Ss + pK * imK));
   const R re = star ? rs : rK;
   const R ue = star ? Ss : uK;
   const R pe = star ? ps : pK;

@@ -231,6 +231,38 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
       sm.q[slot].st(cy, cx, q);
     }
   };
+  // Float arithmetic: phase 2 issues the next plane's loads into registers before its face fluxes
+  // and recovers them after, so the load latency overlaps the fluxes (8-byte arithmetic has no
+  // registers to spare for it).
+  constexpr bool kPrefetch = std::is_same<R, float>::value;
+  constexpr int NPF = kPrefetch ? (QN + NT - 1) / NT : 1;
+  S pre[NPF][5];
+  auto fetch_plane = [&](int z) {
+    const long long zo = plane_offset(z);
+#pragma unroll
+    for (int k = 0; k < NPF; ++k) {
+      const int c = NT - 1 - tid + k * NT;
+      if (c < QN) {
+        const int cy = c / QW, cx = c - cy * QW;
+        const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) pre[k][v] = __ldg(P.in[v] + a);
+      }
+    }
+  };
+  auto commit_plane = [&](int z) {
+    const int slot = ring_slot(z);
+#pragma unroll
+    for (int k = 0; k < NPF; ++k) {
+      const int c = NT - 1 - tid + k * NT;
+      if (c < QN) {
+        const int cy = c / QW, cx = c - cy * QW;
+        R q[5];
+        Pol::recover(pre[k], prm, q, flags);
+        sm.q[slot].st(cy, cx, q);
+      }
+    }
+  };
   constexpr bool kCompact = std::is_same<R, df>::value;  // double-float arithmetic
 
   const R hdt = (R)(0.5 * dt / P.dx);
@@ -342,6 +374,8 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     for (int v = 0; v < 5; ++v) FzPrev[v] = Fz[v];
     __syncthreads();
     // ---- phase 2
+    const bool ld2 = p + 2 <= z1 + 1;
+    if (kPrefetch && ld2) fetch_plane(p + 2);
     if (xy) {
       if constexpr (kCompact) {
         for (int f = tid; f < NXF + NYF; f += NT) {
@@ -370,7 +404,10 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
         }
       }
     }
-    if (p + 2 <= z1 + 1) load_plane(p + 2);
+    if (ld2) {
+      if constexpr (kPrefetch) commit_plane(p + 2);
+      else load_plane(p + 2);
+    }
     __syncthreads();
   }
 }
