@@ -53,8 +53,10 @@ typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2, HYDRO_FP64_DF = 
  *              recovery p = (gamma-1)(E - |m|^2/(2 rho)) is evaluated with error-free float
  *              transformations to double-float accuracy (at least as accurate as evaluating it in
  *              double and rounding to float).
- * HYDRO_MIXED: double state; the same recovery evaluated in double; float reconstruction,
- *              predictor, HLLC and flux divergence; the update U + dU accumulated in double.
+ * HYDRO_MIXED: double state; the pressure recovery to double-float accuracy from the double
+ *              state split exactly into float pairs (error-free float transformations, no FP64
+ *              arithmetic); float reconstruction, predictor, HLLC and flux divergence; the update
+ *              U + dU accumulated in double.
  * HYDRO_FP64_DF: double state; every step of the scheme in double-float arithmetic (pairs of
  *              floats, about 48 significant bits, on the FP32 pipes), the update U + dU accumulated
  *              in double.  Same results as HYDRO_FP64 to about 1e-13 relative, several times faster

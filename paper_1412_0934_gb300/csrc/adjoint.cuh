@@ -366,10 +366,10 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // z chunk: FP32 and double-float take the longest of 16, 8, 4, 2 planes whose grid still fills
-  // every SM's resident blocks (a small grid leaves SMs idle and their FP32 pipes waiting on
-  // dependent chains).  FP64 keeps 16: it is bound by the FP64 pipe, which a few warps per SM
-  // already keep busy, and a shorter march repeats halo planes on it.
+  // z chunk: FP32 takes the longest of 16, 8, 4, 2 planes whose grid still fills half of the SMs'
+  // resident blocks (a small grid leaves SMs idle, a short march repeats halo planes; half is the
+  // measured balance).  FP64 keeps 16: it is bound by the FP64 pipe, which a few warps per SM
+  // already keep busy.
   static int resident = 0;
   if (!resident) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adj_faces<Pol, TX, TY>, TX * TY, smem);
@@ -381,7 +381,8 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
     return cudaErrorUnknown;
   const long long cols = (long long)((U.nx + TX - 1) / TX) * ((U.ny + TY - 1) / TY);
   int zc = 16;
-  while (!std::is_same<R, double>::value && zc > 2 && cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms) zc /= 2;
+  while (!std::is_same<R, double>::value && zc > 2 && 2 * cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms)
+    zc /= 2;
   if (zc > U.nz) zc = U.nz;
   dim3 grid((U.nx + TX - 1) / TX, (U.ny + TY - 1) / TY, (U.nz + zc - 1) / zc);
   k_adj_faces<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, dt, zc, scr,

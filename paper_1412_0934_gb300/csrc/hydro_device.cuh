@@ -302,6 +302,42 @@ __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
   return (a - (s - bb)) + (b - bb);
 }
 
+// Conversions for the mixed policy without conversion instructions, which share GB300's narrow
+// FP64 pipe with the double arithmetic.
+// Exact float of an integer 0 <= n < 2^23: the bits of 2^23 + n read as a float, minus 2^23.
+__device__ __forceinline__ float small_uint_to_float(unsigned n) {
+  return __uint_as_float(0x4B000000u | n) - 8388608.f;
+}
+// Double -> float pair (hi, lo), hi + lo = x to 2^-47 relative, by rearranging IEEE-754 bit fields
+// on the integer pipe and exact float arithmetic: hi is x cut to its leading 24 significant bits,
+// lo the remaining 29-bit integer rounded once to a float (its top 23 bits times 64 plus its low 6
+// bits, one FMA) and scaled by the power of two 2^(E-52), then one Fast2Sum.  Zero and |x|
+// outside [2^-74, 2^99) take the conversion instructions instead.
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
+  const unsigned ex = (xh >> 20) & 0x7FFu;
+  if (ex - 949u >= 173u) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+    return;
+  }
+  const unsigned sign = xh & 0x80000000u;
+  const float ht = __uint_as_float(sign | ((ex - 896u) << 23) | ((xh & 0xFFFFFu) << 3) | (xl >> 29));
+  const unsigned r = xl & 0x1FFFFFFFu;
+  const float rf = fmaf(small_uint_to_float(r >> 6), 64.f, small_uint_to_float(r & 63u));
+  const float lt = __uint_as_float(__float_as_uint(rf * __uint_as_float((ex - 948u) << 23)) | sign);
+  hi = ht + lt;
+  lo = lt - (hi - ht);
+}
+// Exact float -> double: sign kept, exponent rebiased by 1023 - 127, the 23 fraction bits placed
+// at the top of the 52.  Zero maps to zero; subnormal, infinite and NaN floats take the cvt.
+__device__ __forceinline__ double float_to_double(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (b & 0x7FFFFFFFu) == 0u ? __hiloint2double((int)(b & 0x80000000u), 0) : (double)f;
+  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
+}
+
 // ------------------------------------------------------------------ precision policies
 // recover(): U (storage) -> q (arithmetic), floors applied, flags set on floors / non-finite.
 // speed():   |u| + |v| + |w| + 3c of a stored state (CFL), in the arithmetic type.
@@ -388,30 +424,54 @@ struct PolF32 {
 struct PolMixed {
   using S = double;
   using R = float;
-  // Recovery in double: the kinetic energy with a float reciprocal refined by one Newton step in
-  // double (relative error ~2^-46), the subtraction E - kin in double, then rounded to float.
+  // Recovery from the double state split into float pairs (split_double): |m|^2 as a float pair
+  // (exact squares of the high parts, their exact sum errors, the cross terms 2 m_hi m_lo; the
+  // m_lo^2 terms are below 2^-47 |m|^2), |m|^2/rho as a float pair (quotient of the high parts
+  // plus the FMA residual and the rho_lo term over rho), and E - |m|^2/(2 rho) by a two-sum with
+  // E's low part: the internal energy to float accuracy unless the kinetic energy exceeds it by
+  // ~2^20, with no FP64 instruction.
   static __device__ __forceinline__ void recover(const double U[5], const Params& P, float q[5], unsigned& flags) {
-    double rho = U[0];
-    if (rho < P.rho_floor) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = P.rho_floor; }
-    const double ir0 = (double)__frcp_rn((float)rho);
-    const double ir = fma(ir0, fma(-rho, ir0, 1.0), ir0);
-    const double K = fma(U[3], U[3], fma(U[2], U[2], U[1] * U[1]));
-    const double eint = fma(-0.5 * K, ir, U[4]);
-    if (eint < 0.0) flags |= HYDRO_EBIT_P_FLOOR;
-    float p = (float)(P.kd[K_GM1] * eint);
-    const float rhof = (float)rho;
-    if (!(isfinite(p) && isfinite(rhof))) flags |= HYDRO_EBIT_NONFINITE;
-    const float irf = (float)ir;
+    float rh, rl;
+    if (cmp_lt_floor(U[0], P.kd[K_RHOF])) {
+      flags |= HYDRO_EBIT_RHO_FLOOR;
+      rh = P.kh[K_RHOF];
+      rl = P.kl[K_RHOF];
+    } else {
+      split_double(U[0], rh, rl);
+    }
+    float xh, xl, yh, yl, zh, zl, eh, el;
+    split_double(U[1], xh, xl);
+    split_double(U[2], yh, yl);
+    split_double(U[3], zh, zl);
+    split_double(U[4], eh, el);
+    const float ir = __frcp_rn(rh);
+    const float a1 = xh * xh, e1 = fmaf(xh, xh, -a1);
+    const float a2 = yh * yh, e2 = fmaf(yh, yh, -a2);
+    const float a3 = zh * zh, e3 = fmaf(zh, zh, -a3);
+    const float s1 = a1 + a2;
+    const float t1 = two_sum_err(a1, a2, s1);
+    const float Kh = s1 + a3;
+    const float t2 = two_sum_err(s1, a3, Kh);
+    const float Kl = (((e1 + e2) + e3) + (t1 + t2)) + 2.f * ((xh * xl + yh * yl) + zh * zl);
+    const float kh = Kh * ir;
+    const float kl = ((fmaf(-kh, rh, Kh) + Kl) - kh * rl) * ir;
+    const float hk = 0.5f * kh;
+    const float d = eh - hk;
+    const float de = two_sum_err(eh, -hk, d);
+    const float eint = d + ((de + el) - 0.5f * kl);
+    if (eint < 0.f) flags |= HYDRO_EBIT_P_FLOOR;
+    float p = P.kf[K_GM1] * eint;
+    if (!(isfinite(p) && isfinite(rh))) flags |= HYDRO_EBIT_NONFINITE;
     const float pf = P.kf[K_PF];
-    q[0] = rhof;
-    q[1] = (float)U[1] * irf;
-    q[2] = (float)U[2] * irf;
-    q[3] = (float)U[3] * irf;
+    q[0] = rh;
+    q[1] = xh * ir;
+    q[2] = yh * ir;
+    q[3] = zh * ir;
     q[4] = p < pf ? pf : p;
   }
-  // dU = dtdx * div in float, accumulated into the double state.
+  // dU = dtdx * div in float, accumulated into the double state (one FP64 add per field).
   static __device__ __forceinline__ double update(double Uold, float dtdx, float div) {
-    return Uold - (double)(dtdx * div);
+    return Uold - float_to_double(dtdx * div);
   }
   static __device__ __forceinline__ float speed(const double U[5], const Params& P, unsigned& flags);
 };
