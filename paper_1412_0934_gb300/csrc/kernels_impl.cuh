@@ -231,18 +231,37 @@ __global__ void __launch_bounds__(32 * kOctWarps) k_octs(const typename Pol::S* 
   const R gamma = kc<R>(prm, K_GAMMA), igm1 = kc<R>(prm, K_IGM1);
   const R rf = kc<R>(prm, K_RHOF), pf = kc<R>(prm, K_PF);
   unsigned flags = 0;
-  for (long long g = (long long)blockIdx.x * kOctWarps + w; g < ngroups; g += (long long)gridDim.x * kOctWarps) {
+  // The needed cells of the next group are loaded into registers while this group is computed.
+  const long long gstride = (long long)gridDim.x * kOctWarps;
+  S pre[3][5];
+  auto fetch = [&](long long g) {
     const long long base = g * 216;
-    for (int t = lane; t < 80; t += 32) {
-      const int c = sm.need[t];
-      S U[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) U[v] = __ldg(gin[v] + base + c);
-      R q[5];
-      Pol::recover(U, prm, q, flags);
+    for (int t = 0; t < 3; ++t) {
+      const int k = lane + 32 * t;
+      if (k < 80) {
+        const int c = sm.need[k];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sm.q[w][v][c] = q[v];
+        for (int v = 0; v < 5; ++v) pre[t][v] = __ldg(gin[v] + base + c);
+      }
     }
+  };
+  long long g = (long long)blockIdx.x * kOctWarps + w;
+  if (g < ngroups) fetch(g);
+  for (; g < ngroups; g += gstride) {
+    const long long base = g * 216;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int k = lane + 32 * t;
+      if (k < 80) {
+        R q[5];
+        Pol::recover(pre[t], prm, q, flags);
+        const int c = sm.need[k];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sm.q[w][v][c] = q[v];
+      }
+    }
+    if (g + gstride < ngroups) fetch(g + gstride);
     __syncwarp();
     {
       int x, y, z;
