@@ -197,9 +197,9 @@ struct OctSmem {
   short need[80];
 };
 
-template <class Pol>
 // Six resident blocks (24 warps) per SM: measured fastest against the register budget of the
 // prefetched next group.
+template <class Pol>
 __global__ void __launch_bounds__(32 * kOctWarps, 6) k_octs(const typename Pol::S* __restrict__ g0,
                                                          const typename Pol::S* __restrict__ g1,
                                                          const typename Pol::S* __restrict__ g2,
