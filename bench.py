@@ -207,6 +207,9 @@ def turbulent(n, precision, device, seed=2, mach=5.0, sigma=1.0, p_over_rho=1e-4
 TUNING = "auto"
 
 
+TILE_NAMES = {0: "16x16", 1: "32x8", 2: "8x8", 3: "32x16", 4: "16x16/1 block per SM"}
+
+
 def tune(hy, ctx, a, b, dx, dts):
     """Autotune tile shape and z-chunk on this machine (writes b), or apply a fixed --tuning."""
     pa, pb = hy.patch(a, 0, dx), hy.patch(b, 0, dx)
@@ -217,7 +220,7 @@ def tune(hy, ctx, a, b, dx, dts):
         t, z = (int(x) for x in TUNING.split(":"))
         hy.hydro_set_tuning(ctx, t, z)
     t, z = hy.hydro_get_tuning(ctx)
-    return {"tile": {0: "16x16", 1: "32x8", 2: "8x8", 3: "32x16", 4: "16x16/1 block per SM"}[t], "zchunk": z}
+    return {"tile": TILE_NAMES[t], "zchunk": z}
 
 
 def time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream, per_launch=True):
@@ -347,6 +350,9 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     dt = torch.empty(n, dtype=torch.float64, device="cuda")
     dn = torch.empty(n, dtype=torch.float64, device="cuda")
     hy.hydro_cfl_dt(ctx, ins, dt)
+    if TUNING == "auto":
+        hy.hydro_autotune(ctx, ins, outs, dt)  # tile shape and z chunk for this patch set
+    tt, tz = hy.hydro_get_tuning(ctx)
     for _ in range(warmup):
         hy.hydro_step(ctx, ins, outs, dt, dn)
     torch.cuda.synchronize()
@@ -379,6 +385,7 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     bytes_o = ngroups * (216 + 8) * 5 * 8
     out = {"patches": n, "interior_cells": interior, "ghosted_cells": ghosted, "ms_per_step": ms,
            "mcell_updates_per_s": interior / (ms / 1e3) / 1e6, "launches_per_step": launches,
+           "tuning": {"tile": TILE_NAMES[tt], "zchunk": tz},
            "hbm_frac": bytes_p / (ms / 1e3) / 1e9 / hbm,
            "octs": {"groups": ngroups, "ms_per_step": ms_o, "mcell_updates_per_s": ngroups * 8 / (ms_o / 1e3) / 1e6,
                     "hbm_frac": bytes_o / (ms_o / 1e3) / 1e9 / hbm},
