@@ -133,6 +133,19 @@ int hydro_step(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, in
 int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5], long long ngroups, double dx,
                     const double* dt_dev);
 
+/* Oct groups read in place from a periodic level grid instead of a gathered buffer (the paper's
+ * Ramses GPU procedure gathers each oct's neighbourhood into an N_v x 6^3 buffer first, Sec. 3;
+ * here each group's 6^3 stencil is read from the level with periodic wrap as it is needed).
+ *   level:       a periodic box (ng == 0, each of nx, ny, nz >= 4) of the level's cells; dx is
+ *                the level's cell size;
+ *   origins_dev: device array [ngroups][3] of int (x, y, z): the oct's lowest cell, in [0, n)
+ *                per axis (an origin outside the grid sets HYDRO_EBIT_BAD_TILE and that group's
+ *                output is left unwritten);
+ *   out[f]:      device array [ngroups][2][2][2] (z, y, x) receiving U^{n+1} of the oct's cells.
+ * Same arithmetic, so the same bits, as hydro_step_octs on the gathered stencils. */
+int hydro_step_octs_level(hydro_ctx* ctx, const hydro_patch* level, const int* origins_dev, long long ngroups,
+                          void* const out[5], const double* dt_dev);
+
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
  * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64,
  * HYDRO_FP64_DF (which runs the FP64 reverse sweep: faster on GB300 than a double-float one) or

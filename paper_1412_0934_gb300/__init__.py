@@ -38,6 +38,7 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
+           "hydro_step_octs_level",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
            "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
@@ -81,6 +82,7 @@ def lib():
         L.hydro_step.argtypes = [vp, PP, PP, i, vp, vp]
         L.hydro_step_host.argtypes = [vp, PP, PP, vp, vp]
         L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
+        L.hydro_step_octs_level.argtypes = [vp, PP, vp, ll, vp * 5, vp]
         L.hydro_adjoint_step.argtypes = [vp, PP, vp, PP, PP, i]
         L.hydro_prim_to_cons.argtypes = [vp, PP, PP, i]
         L.hydro_prim_to_cons_adjoint.argtypes = [vp, PP, PP, PP, i]
@@ -229,6 +231,19 @@ def hydro_step_host(ctx, inp, out, dt, dt_next=None):
     """One step of a host-resident periodic box (host_patch in / out; dt, dt_next CUDA tensors)."""
     _check(lib().hydro_step_host(ctx.handle, ctypes.byref(inp.c), ctypes.byref(out.c), _ptr(dt), _ptr(dt_next)),
            "hydro_step_host")
+
+
+def hydro_step_octs_level(ctx, level, origins, out, dt):
+    """level: periodic Patch of the level grid; origins: (G, 3) int32 CUDA tensor (x, y, z);
+    out: (5, G, 2, 2, 2)."""
+    if origins.dtype != torch.int32 or not origins.is_contiguous() or origins.dim() != 2 or origins.shape[1] != 3:
+        raise ValueError("origins must be a contiguous (G, 3) int32 tensor")
+    o = (ctypes.c_void_p * 5)(*[_ptr(out[v]) for v in range(5)])
+    for v in range(5):
+        if not out[v].is_contiguous():
+            raise ValueError("oct arrays must be contiguous per field")
+    _check(lib().hydro_step_octs_level(ctx.handle, ctypes.byref(level.c), _ptr(origins), origins.shape[0], o, _ptr(dt)),
+           "hydro_step_octs_level")
 
 
 def hydro_step_octs(ctx, gathered, out, dx, dt):

@@ -504,6 +504,19 @@ int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], l
   return cuda_status(c->ops->octs(gathered, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
 }
 
+int hydro_step_octs_level(hydro_ctx* c, const hydro_patch* level, const int* origins_dev, long long ngroups,
+                          void* const out[5], const double* dt_dev) {
+  if (!c || !level || !origins_dev || !out || ngroups < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  const hydro_patch& L = *level;
+  if (!valid_patch(c, L) || L.ng != 0 || L.nx < 4 || L.ny < 4 || L.nz < 4) return HYDRO_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(origins_dev) % sizeof(int)) return HYDRO_ERR_ARG;
+  const int es = elem_size(c);
+  for (int v = 0; v < 5; ++v)
+    if (!out[v] || reinterpret_cast<uintptr_t>(out[v]) % es) return HYDRO_ERR_ARG;
+  c->launches += 1;
+  return cuda_status(c->ops->octs_level(make_io(L, L), origins_dev, out, ngroups, c->prm, dt_dev, c->d_err, c->stream));
+}
+
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
                        const hydro_patch* lam_n, int npatch) {
   if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1) return HYDRO_ERR_ARG;

@@ -46,6 +46,9 @@ struct KernelOps {
   // Oct groups (6^3 gathered -> 2^3).
   cudaError_t (*octs)(void* const gathered[5], void* const out[5], long long ngroups, double dx, const Params& prm,
                       const double* dt, unsigned* err, cudaStream_t s);
+  // Oct groups read in place from a periodic level grid at the given origins (-> 2^3 each).
+  cudaError_t (*octs_level)(const HostPatchIO& level, const int* origins, void* const out[5], long long ngroups,
+                            const Params& prm, const double* dt, unsigned* err, cudaStream_t s);
   // Adjoint of one periodic step.
   cudaError_t (*adjoint)(const HostPatchIO& U, const HostPatchIO& lam, void* const lam_out[5], const Params& prm,
                          const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s);

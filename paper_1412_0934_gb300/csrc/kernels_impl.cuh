@@ -197,22 +197,58 @@ struct OctSmem {
   short need[80];
 };
 
-// Six resident blocks (24 warps) per SM: measured fastest against the register budget of the
-// prefetched next group.
+// Where a group's 6^3 stencil comes from.  OctGathered: the caller's gathered buffer, group g's
+// cell c (z, y, x from -2) at g*216 + c.  OctLevel: a periodic level grid and the groups' origins
+// (the oct's lowest cell, x, y, z), wrapped on the fly -- no gathered copy of the stencils.
+template <class S>
+struct OctGathered {
+  const S* f[5];
+  __device__ __forceinline__ bool begin(long long, unsigned&) const { return true; }
+  __device__ __forceinline__ long long cell(long long g, int c) const { return g * 216 + c; }
+};
+template <class S>
+struct OctLevel {
+  const S* f[5];
+  int nx, ny, nz;
+  long long sy, sz;
+  const int* origins;  // [ngroups][3]
+  int ox, oy, oz;      // origin of the current group
+  // Loads group g's origin; an origin outside the grid flags HYDRO_EBIT_BAD_TILE and the group
+  // is skipped (nothing is read or written for it).
+  __device__ __forceinline__ bool begin(long long g, unsigned& flags) {
+    ox = __ldg(origins + 3 * g);
+    oy = __ldg(origins + 3 * g + 1);
+    oz = __ldg(origins + 3 * g + 2);
+    if (ox < 0 || oy < 0 || oz < 0 || ox >= nx || oy >= ny || oz >= nz) {
+      flags |= HYDRO_EBIT_BAD_TILE;
+      return false;
+    }
+    return true;
+  }
+  __device__ __forceinline__ long long cell(long long, int c) const {
+    int x = ox + c % 6 - 2, y = oy + (c / 6) % 6 - 2, z = oz + c / 36 - 2;
+    x += x < 0 ? nx : (x >= nx ? -nx : 0);
+    y += y < 0 ? ny : (y >= ny ? -ny : 0);
+    z += z < 0 ? nz : (z >= nz ? -nz : 0);
+    return z * sz + y * sy + x;
+  }
+};
+
+// Resident blocks per SM: six (24 warps) for float arithmetic, measured fastest against the
+// register budget of the prefetched next group; four for 8-byte arithmetic, whose larger
+// registers would otherwise spill.
 template <class Pol>
-__global__ void __launch_bounds__(32 * kOctWarps, 6) k_octs(const typename Pol::S* __restrict__ g0,
-                                                         const typename Pol::S* __restrict__ g1,
-                                                         const typename Pol::S* __restrict__ g2,
-                                                         const typename Pol::S* __restrict__ g3,
-                                                         const typename Pol::S* __restrict__ g4,
-                                                         typename Pol::S* o0, typename Pol::S* o1, typename Pol::S* o2,
-                                                         typename Pol::S* o3, typename Pol::S* o4, long long ngroups,
-                                                         double dx, Params prm, const double* dt_dev, unsigned* err) {
+constexpr int oct_min_blocks() { return sizeof(typename Pol::R) >= 8 ? 4 : 6; }
+
+template <class Pol, class Src>
+__global__ void __launch_bounds__(32 * kOctWarps, oct_min_blocks<Pol>()) k_octs(Src src, typename Pol::S* o0, typename Pol::S* o1,
+                                                         typename Pol::S* o2, typename Pol::S* o3,
+                                                         typename Pol::S* o4, long long ngroups, double dx, Params prm,
+                                                         const double* dt_dev, unsigned* err) {
   using S = typename Pol::S;
   using R = typename Pol::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& sm = *reinterpret_cast<OctSmem<Pol>*>(smem_raw);
-  const S* gin[5] = {g0, g1, g2, g3, g4};
   S* gout[5] = {o0, o1, o2, o3, o4};
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
@@ -236,22 +272,30 @@ __global__ void __launch_bounds__(32 * kOctWarps, 6) k_octs(const typename Pol::
   // The needed cells of the next group are loaded into registers while this group is computed.
   const long long gstride = (long long)gridDim.x * kOctWarps;
   S pre[3][5];
+  Src nxt = src;  // source state of the prefetched group
+  bool nxt_ok = false;
   auto fetch = [&](long long g) {
-    const long long base = g * 216;
+    nxt_ok = nxt.begin(g, flags);
+    if (!nxt_ok) return;
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       const int k = lane + 32 * t;
       if (k < 80) {
-        const int c = sm.need[k];
+        const long long a = nxt.cell(g, sm.need[k]);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) pre[t][v] = __ldg(gin[v] + base + c);
+        for (int v = 0; v < 5; ++v) pre[t][v] = __ldg(nxt.f[v] + a);
       }
     }
   };
   long long g = (long long)blockIdx.x * kOctWarps + w;
   if (g < ngroups) fetch(g);
   for (; g < ngroups; g += gstride) {
-    const long long base = g * 216;
+    const Src cur = nxt;
+    const bool ok = nxt_ok;
+    if (!ok) {  // (warp-uniform: one warp per group)
+      if (g + gstride < ngroups) fetch(g + gstride);
+      continue;
+    }
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       const int k = lane + 32 * t;
@@ -321,7 +365,7 @@ __global__ void __launch_bounds__(32 * kOctWarps, 6) k_octs(const typename Pol::
       for (int v = 0; v < 5; ++v) {
         const R* F = sm.f[w][v];
         const R div = ((F[fxp] - F[fxm]) + (F[fyp] - F[fym])) + (F[fzp] - F[fzm]);
-        gout[v][g * 8 + lane] = Pol::update(__ldg(gin[v] + base + c), dtdx, div);
+        gout[v][g * 8 + lane] = Pol::update(__ldg(cur.f[v] + cur.cell(g, c)), dtdx, div);
       }
     }
     __syncwarp();
@@ -329,24 +373,45 @@ __global__ void __launch_bounds__(32 * kOctWarps, 6) k_octs(const typename Pol::
   flush_flags(flags, err);
 }
 
-template <class Pol>
-cudaError_t launch_octs(void* const gathered[5], void* const out[5], long long ngroups, double dx, const Params& prm,
-                        const double* dt, unsigned* err, cudaStream_t s) {
+template <class Pol, class Src>
+cudaError_t launch_octs_src(const Src& src, void* const out[5], long long ngroups, double dx, const Params& prm,
+                            const double* dt, unsigned* err, cudaStream_t s) {
   using S = typename Pol::S;
   const size_t smem = sizeof(OctSmem<Pol>);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_octs<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_octs<Pol, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   long long blocks = (ngroups + kOctWarps - 1) / kOctWarps;
   const long long cap = 152LL * 64;
   if (blocks > cap) blocks = cap;
-  k_octs<Pol><<<(unsigned)blocks, 32 * kOctWarps, smem, s>>>(
-      (const S*)gathered[0], (const S*)gathered[1], (const S*)gathered[2], (const S*)gathered[3],
-      (const S*)gathered[4], (S*)out[0], (S*)out[1], (S*)out[2], (S*)out[3], (S*)out[4], ngroups, dx, prm, dt, err);
+  k_octs<Pol, Src><<<(unsigned)blocks, 32 * kOctWarps, smem, s>>>(src, (S*)out[0], (S*)out[1], (S*)out[2], (S*)out[3],
+                                                                   (S*)out[4], ngroups, dx, prm, dt, err);
   return cudaGetLastError();
+}
+
+template <class Pol>
+cudaError_t launch_octs(void* const gathered[5], void* const out[5], long long ngroups, double dx, const Params& prm,
+                        const double* dt, unsigned* err, cudaStream_t s) {
+  using S = typename Pol::S;
+  OctGathered<S> src;
+  for (int v = 0; v < 5; ++v) src.f[v] = static_cast<const S*>(gathered[v]);
+  return launch_octs_src<Pol>(src, out, ngroups, dx, prm, dt, err, s);
+}
+
+template <class Pol>
+cudaError_t launch_octs_level(const HostPatchIO& level, const int* origins, void* const out[5], long long ngroups,
+                              const Params& prm, const double* dt, unsigned* err, cudaStream_t s) {
+  using S = typename Pol::S;
+  OctLevel<S> src;
+  for (int v = 0; v < 5; ++v) src.f[v] = static_cast<const S*>(level.in[v]);
+  src.nx = level.nx; src.ny = level.ny; src.nz = level.nz;
+  src.sy = level.isy; src.sz = level.isz;
+  src.origins = origins;
+  src.ox = src.oy = src.oz = 0;
+  return launch_octs_src<Pol>(src, out, ngroups, level.dx, prm, dt, err, s);
 }
 
 // ------------------------------------------------------------------ primitive <-> conservative
@@ -416,7 +481,7 @@ template <class Pol>
 const KernelOps& make_ops() {
   static const KernelOps ops = {
       &launch_uniform<Pol>,      &launch_batched<Pol>,      &batched_blocks_per_sm<Pol>,
-      &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_adjoint<Pol>,
+      &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_octs_level<Pol>,   &launch_adjoint<Pol>,
       &adjoint_scratch_bytes<Pol>, &launch_p2c<Pol>,        &launch_p2c_adjoint<Pol>,
       (int)sizeof(typename Pol::S), 1};
   return ops;

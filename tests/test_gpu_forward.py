@@ -214,6 +214,42 @@ def test_octs_match_oracle_and_uniform_grid(precision):
     check_clean(c)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "fp32"])
+def test_octs_from_level_grid_equal_gathered_octs(precision):
+    """hydro_step_octs_level (stencils read in place from the periodic level, wrapped) gives the
+    bits of hydro_step_octs on the gathered stencils; origins on the grid's edges included; an
+    origin outside the grid flags HYDRO_EBIT_BAD_TILE and leaves its group unwritten."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    shape = (12, 10, 14)
+    parent = workloads.turbulent_state(shape, seed=7, mach=2.0, sedov=False)
+    dx = 1.0 / 14
+    dt = 0.6 * oracle.cfl_periodic(parent.numpy(), dx, ocfg())
+    rng = np.random.default_rng(8)
+    origins = np.stack([rng.integers(0, 14, 61), rng.integers(0, 10, 61), rng.integers(0, 12, 61)], axis=1)
+    origins[:4] = [[0, 0, 0], [13, 9, 11], [12, 8, 10], [1, 9, 0]]
+    c = ctx(precision)
+    gd = workloads.gather_octs(parent, origins).to(device="cuda", dtype=dtype).contiguous()
+    og = torch.zeros((5, len(origins), 2, 2, 2), dtype=dtype, device="cuda")
+    hy.hydro_step_octs(c, gd, og, dx, dts(dt))
+    level = parent.to(device="cuda", dtype=dtype).contiguous()
+    ol = torch.zeros_like(og)
+    od = torch.as_tensor(origins, dtype=torch.int32, device="cuda").contiguous()
+    hy.hydro_step_octs_level(c, hy.patch(level, 0, dx), od, ol, dts(dt))
+    torch.cuda.synchronize()
+    assert torch.equal(ol, og)
+    check_clean(c)
+    bad = od.clone()
+    bad[5] = torch.tensor([14, 0, 0], dtype=torch.int32)
+    ob = torch.full_like(og, 7.0)
+    hy.hydro_step_octs_level(c, hy.patch(level, 0, dx), bad, ob, dts(dt))
+    torch.cuda.synchronize()
+    rc, bits = hy.hydro_get_error(c)
+    assert bits & hy.EBIT_BAD_TILE
+    assert torch.equal(ob[:, 5], torch.full_like(ob[:, 5], 7.0))
+    keep = [k for k in range(len(origins)) if k != 5]
+    assert torch.equal(ob[:, keep], og[:, keep])
+
+
 def test_error_word_flags_and_argument_errors():
     U = workloads.white_velocity_state(8, seed=1).numpy()
     c = ctx("fp64")
