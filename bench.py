@@ -590,7 +590,7 @@ def main():
     # end to end through the C ABI with the state in (page-locked) host memory: hydro_step_host
     # copies the state in, steps it and copies the result out every step, pipelined over z slabs;
     # host buffers ping-pong, each step's dt is the fused CFL dt of the previous step's result.
-    e2e_steps = 4
+    e2e_steps = 6
     esz = a.element_size()
     hbuf = [a.cpu().pin_memory(), torch.empty(a.shape, dtype=a.dtype).pin_memory()]
     hd = torch.empty(e2e_steps + 2, dtype=torch.float64, device="cuda")
