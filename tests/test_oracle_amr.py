@@ -1,0 +1,70 @@
+"""Pins of the coarse-to-fine ghost fill oracle (oracle/amr.py) by what the prolongation must
+satisfy: the eight children of a coarse cell average to it; a field linear across a cell's
+neighbours is reproduced exactly at the fine centres; no fine value leaves the range of its parent
+and the parent's face neighbours (MinMod slopes); a constant field stays constant; the ghost fill
+of a patch agrees with the whole-level prolongation, including ghosts that wrap around the
+periodic level."""
+import numpy as np
+import pytest
+
+from oracle import amr
+
+
+def _field(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((5,) + shape) + np.array([3.0, 0.0, 0.0, 0.0, 5.0])[:, None, None, None]
+
+
+def test_children_average_to_parent():
+    Uc = _field((6, 5, 7), 1)
+    Uf = amr.prolong_box(Uc)
+    avg = Uf.reshape(5, 6, 2, 5, 2, 7, 2).mean(axis=(2, 4, 6))
+    assert np.abs(avg - Uc).max() <= 1e-15 * np.abs(Uc).max() * 8
+
+
+def test_linear_field_reproduced_at_fine_centres():
+    NZ, NY, NX = 6, 7, 8
+    k, j, i = np.meshgrid(np.arange(NZ), np.arange(NY), np.arange(NX), indexing="ij")
+    coef = np.array([[1.0, 0.5, -0.25, 2.0], [0.0, -1.0, 0.3, 0.1], [2.0, 0.2, 0.2, -0.7],
+                     [-1.0, 0.0, 1.5, 0.4], [4.0, 0.9, -0.6, 0.05]])
+    Uc = np.stack([c[0] + c[1] * i + c[2] * j + c[3] * k for c in coef])
+    # fine cells whose parent and the parent's neighbours do not wrap
+    f = np.array([[x, y, z] for z in range(2, 2 * NZ - 2) for y in range(2, 2 * NY - 2) for x in range(2, 2 * NX - 2)])
+    got = amr.prolong_cells(Uc, f)
+    pos = f / 2.0 - 0.25  # fine centres in coarse index units
+    want = np.stack([c[0] + c[1] * pos[:, 0] + c[2] * pos[:, 1] + c[3] * pos[:, 2] for c in coef])
+    assert np.abs(got - want).max() <= 1e-13
+
+
+def test_no_new_extrema_and_constant_field():
+    Uc = _field((5, 6, 4), 2)
+    NZ, NY, NX = Uc.shape[1:]
+    f = np.array([[x, y, z] for z in range(2 * NZ) for y in range(2 * NY) for x in range(2 * NX)])
+    got = amr.prolong_cells(Uc, f)
+    C = f // 2
+    lo = np.full(got.shape, np.inf)
+    hi = np.full(got.shape, -np.inf)
+    for e in ([0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]):
+        c = np.mod(C + np.array(e), [NX, NY, NZ])
+        v = Uc[:, c[:, 2], c[:, 1], c[:, 0]]
+        lo, hi = np.minimum(lo, v), np.maximum(hi, v)
+    assert (got >= lo - 1e-14).all() and (got <= hi + 1e-14).all()
+    const = np.ones((5, 3, 3, 3)) * np.array([1.5, -2.0, 0.0, 0.25, 7.0])[:, None, None, None]
+    assert np.array_equal(amr.prolong_box(const), np.ones((5, 6, 6, 6)) * const[:, :1, :1, :1])
+
+
+@pytest.mark.parametrize("origin", [(0, 0, 0), (5, 3, 1), (10, 12, 8)])
+def test_patch_ghosts_agree_with_level_prolongation(origin):
+    Uc = _field((6, 7, 6), 3)
+    Uf = amr.prolong_box(Uc)  # fine level (12, 14, 12)
+    nx, ny, nz = 4, 6, 4
+    Ug = amr.fill_ghosts(Uc, np.zeros((5, nz + 4, ny + 4, nx + 4)), origin)
+    ox, oy, oz = origin
+    ix = np.mod(np.arange(ox - 2, ox + nx + 2), 12)
+    iy = np.mod(np.arange(oy - 2, oy + ny + 2), 14)
+    iz = np.mod(np.arange(oz - 2, oz + nz + 2), 12)
+    ref = Uf[:, iz][:, :, iy][:, :, :, ix]
+    interior = np.zeros(Ug.shape[1:], dtype=bool)
+    interior[2:-2, 2:-2, 2:-2] = True
+    assert np.array_equal(Ug[:, interior], np.zeros((5, interior.sum())))
+    assert np.abs(Ug[:, ~interior] - ref[:, ~interior]).max() <= 1e-15 * np.abs(ref).max()
