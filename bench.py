@@ -398,6 +398,22 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     t1.record(stream)
     torch.cuda.synchronize()
     ms_l = t0.elapsed_time(t1) / steps
+    # coarse-to-fine ghost fill of the same patch set from a 128^3 coarse level (fine dx = 1/256)
+    coarse = turbulent(128, "mixed", "cuda", seed=3, sedov=False)
+    rng = np.random.default_rng(14)
+    gorig = [(int(rng.integers(0, 256)), int(rng.integers(0, 256)), int(rng.integers(0, 256))) for _ in descs]
+    gfine = [hy.patch(keep[2 * i], 2, 1.0 / 256) for i in range(n)]
+    gcoarse = hy.patch(coarse, 0, 1.0 / 128)
+    for _ in range(warmup):
+        hy.hydro_fill_ghosts(ctx, gcoarse, gfine, gorig)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        hy.hydro_fill_ghosts(ctx, gcoarse, gfine, gorig)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_g = t0.elapsed_time(t1) / steps
+    nghost = ghosted - interior
     rc, bits = hy.hydro_get_error(ctx)
     hbm, src = peaks()
     bytes_p = (ghosted * 5 * 8 + interior * 5 * 8)
@@ -413,8 +429,12 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
                           "hbm_frac": ngroups * (80 + 8) * 5 * 8 / (ms_l / 1e3) / 1e9 / hbm,
                           "note": "stencils read in place from the 256^3 level (80 needed cells per group, "
                                   "8 written), groups in Morton order; no gathered copy"},
+           "ghost_fill": {"ghost_cells": nghost, "ms": ms_g, "mcells_per_s": nghost / (ms_g / 1e3) / 1e6,
+                          "hbm_frac": (nghost + 128 ** 3) * 5 * 8 / (ms_g / 1e3) / 1e9 / hbm,
+                          "note": "2 ghost layers of the 4096 patches prolonged from a 128^3 coarse level "
+                                  "(writes + one read of the coarse level)"},
            "error_bits": bits}
-    del keep, parent, g, go, od
+    del keep, parent, g, go, od, coarse
     hy.hydro_finalize(ctx)
     torch.cuda.empty_cache()
     return out

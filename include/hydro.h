@@ -133,6 +133,23 @@ int hydro_step(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, in
 int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5], long long ngroups, double dx,
                     const double* dt_dev);
 
+/* Fill the two ghost layers of fine patches from the next-coarser level (refinement ratio 2), the
+ * boundary-cell interpolation of the paper's Ramses chunk builder (Sec. 3): conservative
+ * piecewise-linear prolongation of each conserved variable with MinMod-limited slopes,
+ *     U_f = U_C + s_x D_x + s_y D_y + s_z D_z,  s_d = +-1/4,  D_d = minmod(U_C - U_{C-e_d}, U_{C+e_d} - U_C),
+ * for a fine cell with fine-level index f in coarse cell C = floor(f/2) (upper half when f is odd),
+ * the coarse level periodic.  The eight children of a coarse cell average to it.
+ *   coarse:       the coarse level as a periodic box (ng == 0);
+ *   fine:         npatch patches with ng == 2 and dx == coarse->dx / 2; only their ghost cells are
+ *                 written, the interiors are left untouched; they must not overlap the coarse
+ *                 level or one another;
+ *   fine_origins: host array [npatch][3] of int (x, y, z): the fine-level index of each patch's
+ *                 first interior cell (any integers: fine indices wrap with the level's period).
+ * Arithmetic in the storage type.  A call with a patch set different from the previous call's
+ * uploads its descriptors and synchronises the stream first. */
+int hydro_fill_ghosts(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
+                      int npatch);
+
 /* Oct groups read in place from a periodic level grid instead of a gathered buffer (the paper's
  * Ramses GPU procedure gathers each oct's neighbourhood into an N_v x 6^3 buffer first, Sec. 3;
  * here each group's 6^3 stencil is read from the level with periodic wrap as it is needed).

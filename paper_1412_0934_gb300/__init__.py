@@ -38,7 +38,7 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level",
+           "hydro_step_octs_level", "hydro_fill_ghosts",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
            "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
@@ -83,6 +83,7 @@ def lib():
         L.hydro_step_host.argtypes = [vp, PP, PP, vp, vp]
         L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
         L.hydro_step_octs_level.argtypes = [vp, PP, vp, ll, vp * 5, vp]
+        L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
         L.hydro_adjoint_step.argtypes = [vp, PP, vp, PP, PP, i]
         L.hydro_prim_to_cons.argtypes = [vp, PP, PP, i]
         L.hydro_prim_to_cons_adjoint.argtypes = [vp, PP, PP, PP, i]
@@ -231,6 +232,16 @@ def hydro_step_host(ctx, inp, out, dt, dt_next=None):
     """One step of a host-resident periodic box (host_patch in / out; dt, dt_next CUDA tensors)."""
     _check(lib().hydro_step_host(ctx.handle, ctypes.byref(inp.c), ctypes.byref(out.c), _ptr(dt), _ptr(dt_next)),
            "hydro_step_host")
+
+
+def hydro_fill_ghosts(ctx, coarse, fine, origins):
+    """Fill the ghost layers of the fine patches (list of Patch, ng = 2) from the periodic coarse
+    Patch; origins: (x, y, z) fine-level index of each patch's first interior cell."""
+    f, n = _parray(fine)
+    o = (ctypes.c_int * (3 * n))(*[int(v) for xyz in origins for v in xyz])
+    if len(o) != 3 * n:
+        raise ValueError("one (x, y, z) origin per patch")
+    _check(lib().hydro_fill_ghosts(ctx.handle, ctypes.byref(coarse.c), f, o, n), "hydro_fill_ghosts")
 
 
 def hydro_step_octs_level(ctx, level, origins, out, dt):

@@ -69,6 +69,13 @@ struct hydro_ctx {
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
   std::vector<cudaEvent_t> ev_copied, ev_stepped;
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+  // coarse-to-fine ghost fill: uploaded patch descriptors and ghost-cell offsets of the last set
+  std::vector<hydro::HostGhostPatch> ghost_key;
+  hydro::HostGhostPatch* d_ghost = nullptr;
+  size_t ghost_cap = 0;
+  int2* d_ghost_blocks = nullptr;
+  size_t ghost_blocks_cap = 0;
+  int ghost_nblocks = 0;
   long long launches = 0;
 };
 
@@ -287,6 +294,8 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_stage_io);
   cudaFree(c->d_stage_tiles);
   cudaFree(c->d_stage_counters);
+  cudaFree(c->d_ghost);
+  cudaFree(c->d_ghost_blocks);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
@@ -502,6 +511,48 @@ int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], l
   }
   c->launches += 1;
   return cuda_status(c->ops->octs(gathered, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
+}
+
+int hydro_fill_ghosts(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
+                      int npatch) {
+  if (!c || !coarse || !fine || !fine_origins || npatch < 1) return HYDRO_ERR_ARG;
+  const hydro_patch& C = *coarse;
+  if (!valid_patch(c, C) || C.ng != 0) return HYDRO_ERR_ARG;
+  std::vector<hydro::HostGhostPatch> set((size_t)npatch);
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_patch& F = fine[i];
+    if (!valid_patch(c, F) || F.ng != 2 || F.dx != 0.5 * C.dx || overlaps(c, C, F)) return HYDRO_ERR_ARG;
+    hydro::HostGhostPatch& g = set[i];
+    for (int v = 0; v < 5; ++v) g.U[v] = F.U[v];
+    g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
+    g.ox = fine_origins[3 * i]; g.oy = fine_origins[3 * i + 1]; g.oz = fine_origins[3 * i + 2];
+    g.sy = F.sy; g.sz = F.sz;
+    const long long cells = (long long)(F.nx + 4) * (F.ny + 4) * (F.nz + 4) - (long long)F.nx * F.ny * F.nz;
+    if (cells > 0x7fffffff) return HYDRO_ERR_ARG;
+    g.nghost = (int)cells;
+  }
+  const bool same = c->ghost_key.size() == set.size() &&
+                    std::memcmp(c->ghost_key.data(), set.data(), set.size() * sizeof(set[0])) == 0;
+  if (!same) {
+    std::vector<int2> blocks;
+    for (int i = 0; i < npatch; ++i)
+      for (int first = 0; first < set[i].nghost; first += 256) blocks.push_back(make_int2(i, first));
+    if (blocks.size() > 0x7fffffff) return HYDRO_ERR_ARG;
+    int rc = ensure_device(&c->d_ghost, &c->ghost_cap, (size_t)npatch);
+    if (rc) return rc;
+    rc = ensure_device(&c->d_ghost_blocks, &c->ghost_blocks_cap, blocks.size());
+    if (rc) return rc;
+    // the descriptors may still be read by an earlier fill on the stream
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    if (cudaMemcpy(c->d_ghost, set.data(), set.size() * sizeof(set[0]), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_ghost_blocks, blocks.data(), blocks.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return HYDRO_ERR_CUDA;
+    c->ghost_key.swap(set);
+    c->ghost_nblocks = (int)blocks.size();
+  }
+  c->launches += 1;
+  return cuda_status(hydro::launch_fill_ghosts(elem_size(c), c->d_ghost, c->d_ghost_blocks, c->ghost_nblocks,
+                                               make_io(C, C), c->stream));
 }
 
 int hydro_step_octs_level(hydro_ctx* c, const hydro_patch* level, const int* origins_dev, long long ngroups,

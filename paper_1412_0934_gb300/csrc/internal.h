@@ -68,6 +68,21 @@ const KernelOps& ops_df();
 // Kernel set of a hydro_precision value (nullptr if out of range).
 const KernelOps* ops_for(int precision);
 
+// A fine patch whose ghost layers the coarse-to-fine fill writes: its fields, interior size,
+// strides and the fine-level index of its first interior cell.
+struct HostGhostPatch {
+  void* U[5];
+  int nx, ny, nz;
+  int ox, oy, oz;
+  int nghost;  // ghost cells: (nx+4)(ny+4)(nz+4) - nx ny nz
+  long long sy, sz;
+};
+
+// Coarse-to-fine ghost fill (ghosts.cu): block b fills ghost cells d_blocks[b].y .. +255 of patch
+// d_blocks[b].x.
+cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
+                               const HostPatchIO& coarse, cudaStream_t s);
+
 // Work-list construction (precision-independent; descriptors read through HostPatchIO).
 cudaError_t build_worklist(const HostPatchIO* d_patches, int npatch, int tx, int ty, int zchunk, int* d_counts,
                            HostTileRec* d_tiles, cudaStream_t s);

@@ -1,0 +1,80 @@
+"""GPU coarse-to-fine ghost fill (hydro_fill_ghosts) against the oracle (oracle/amr.py): every
+ghost cell of patches of mixed sizes whose ghosts wrap around the periodic coarse level and whose
+origins lie outside [0, period); bitwise for double storage (the arithmetic is exact up to the same
+roundings in the same order), float storage against the oracle on the float coarse level; the
+interiors are left untouched; argument errors; the 4096-patch set on a 128^3 coarse level, sampled."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from hydro_testlib import check_clean, ctx
+from oracle import amr
+
+import paper_1412_0934_gb300 as hy
+
+pytestmark = pytest.mark.gpu
+
+
+def _patches(rng, n, period, sizes=(1, 2, 3, 5, 8)):
+    dims = [tuple(int(rng.choice(sizes)) for _ in range(3)) for _ in range(n)]
+    origins = [tuple(int(rng.integers(-6, p + 6)) for p in period) for _ in range(n)]
+    return dims, origins
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64", "fp32"])
+def test_ghost_fill_matches_oracle(precision):
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    c = ctx(precision)
+    coarse = workloads.turbulent_state((6, 5, 7), seed=9, mach=3.0, sedov=False).to(dtype).contiguous()
+    Uc = coarse.double().numpy()
+    dxc = 1.0 / 7
+    rng = np.random.default_rng(10)
+    dims, origins = _patches(rng, 40, (14, 10, 12))
+    tens = [torch.full((5, nz + 4, ny + 4, nx + 4), 7.0, dtype=dtype, device="cuda") for nx, ny, nz in dims]
+    hy.hydro_fill_ghosts(c, hy.patch(coarse.cuda(), 0, dxc), [hy.patch(t, 2, dxc / 2) for t in tens], origins)
+    torch.cuda.synchronize()
+    for t, (nx, ny, nz), o in zip(tens, dims, origins):
+        got = t.double().cpu().numpy()
+        want = amr.fill_ghosts(Uc, np.full(got.shape, 7.0), o)
+        if dtype == torch.float64:
+            assert np.array_equal(got, want), o
+        else:
+            err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(Uc).max(axis=(1, 2, 3))
+            assert err.max() <= 1e-6, (o, err)
+        assert (got[:, 2:-2, 2:-2, 2:-2] == 7.0).all()
+    check_clean(c)
+
+
+def test_ghost_fill_argument_errors():
+    c = ctx("fp64")
+    coarse = torch.zeros((5, 4, 4, 4), dtype=torch.float64, device="cuda")
+    fine = torch.zeros((5, 6, 6, 6), dtype=torch.float64, device="cuda")
+    o = (ctypes.c_int * 3)(0, 0, 0)
+    good = hy.patch(fine, 2, 0.125)
+    for cp, fp in ((hy.patch(coarse, 0, 0.25), hy.patch(fine, 2, 0.1)),  # dx not half the coarse dx
+                   (hy.Patch(coarse, 0, 0.25), hy.patch(fine, 0, 0.125)),  # fine without ghosts
+                   (hy.patch(fine, 2, 0.25), good)):  # coarse with ghosts
+        rc = hy.lib().hydro_fill_ghosts(c.handle, ctypes.byref(cp.c), ctypes.byref(fp.c), o, 1)
+        assert rc == hy.HYDRO_ERR_ARG
+
+
+def test_ghost_fill_4096_patches_on_128cube_sampled():
+    c = ctx("mixed")
+    coarse = workloads.turbulent_state(128, seed=3, sedov=False, device="cuda")
+    dxc = 1.0 / 128
+    descs = workloads.patch_set(4096, seed=3)
+    rng = np.random.default_rng(14)
+    origins = [(int(rng.integers(0, 256)), int(rng.integers(0, 256)), int(rng.integers(0, 256))) for _ in descs]
+    tens = [torch.full((5, d["nz"] + 4, d["ny"] + 4, d["nx"] + 4), 7.0, dtype=torch.float64, device="cuda")
+            for d in descs]
+    hy.hydro_fill_ghosts(c, hy.patch(coarse, 0, dxc), [hy.patch(t, 2, dxc / 2) for t in tens], origins)
+    torch.cuda.synchronize()
+    Uc = coarse.cpu().numpy()
+    for i in list(rng.choice(len(descs), 24, replace=False)) + [0, len(descs) - 1]:
+        got = tens[i].cpu().numpy()
+        want = amr.fill_ghosts(Uc, np.full(got.shape, 7.0), origins[i])
+        assert np.array_equal(got, want), i
+    check_clean(c)
