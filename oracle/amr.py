@@ -68,3 +68,28 @@ def prolong_box(Uc):
     k, j, i = np.meshgrid(np.arange(2 * NZ), np.arange(2 * NY), np.arange(2 * NX), indexing="ij")
     f = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
     return prolong_cells(Uc, f).reshape(5, 2 * NZ, 2 * NY, 2 * NX)
+
+
+def exchange_ghosts(patches, origins, period):
+    """Ghost cells of each ghosted patch covered by the interior of a patch of the same level (another
+    one, or the patch itself across the period) take that interior's values (the level periodic
+    with `period` (x, y, z) fine cells); other ghosts are left as they are.  patches: list of (5, nz+4, ny+4, nx+4) arrays; origins: their
+    first interior cells (x, y, z).  Returns new arrays.  Patch interiors must not overlap."""
+    P = np.asarray(period, dtype=np.int64)
+    out = [np.array(p, dtype=np.float64) for p in patches]
+    dims = [np.array([p.shape[3] - 4, p.shape[2] - 4, p.shape[1] - 4]) for p in patches]
+    for a, (Ua, oa) in enumerate(zip(out, origins)):
+        _, GZ, GY, GX = Ua.shape
+        k, j, i = np.meshgrid(np.arange(GZ), np.arange(GY), np.arange(GX), indexing="ij")
+        ghost = (i < 2) | (i >= GX - 2) | (j < 2) | (j >= GY - 2) | (k < 2) | (k >= GZ - 2)
+        f = np.stack([i[ghost], j[ghost], k[ghost]], axis=1) - 2 + np.asarray(oa)[None, :]
+        f = np.mod(f, P)
+        vals = Ua[:, ghost]
+        for b, (Ub, ob) in enumerate(zip(patches, origins)):  # b == a: the patch's own periodic image
+            rel = np.mod(f - np.asarray(ob)[None, :], P)  # position inside b's interior, if any
+            inside = np.all(rel < dims[b][None, :], axis=1)
+            if inside.any():
+                r = rel[inside]
+                vals[:, inside] = np.asarray(Ub)[:, r[:, 2] + 2, r[:, 1] + 2, r[:, 0] + 2]
+        Ua[:, ghost] = vals
+    return out

@@ -68,3 +68,39 @@ def test_patch_ghosts_agree_with_level_prolongation(origin):
     interior[2:-2, 2:-2, 2:-2] = True
     assert np.array_equal(Ug[:, interior], np.zeros((5, interior.sum())))
     assert np.abs(Ug[:, ~interior] - ref[:, ~interior]).max() <= 1e-15 * np.abs(ref).max()
+
+
+def test_sibling_exchange_reassembles_a_partitioned_level():
+    """A periodic fine level cut into patches that tile it exactly: after the exchange every
+    patch's ghosts equal the level's own cells around it (cut independently, with wrap)."""
+    rng = np.random.default_rng(5)
+    NZ, NY, NX = 8, 6, 10
+    level = rng.standard_normal((5, NZ, NY, NX))
+    cuts = [(x0, y0, z0, nx, ny, nz) for z0, nz in ((0, 3), (3, 5)) for y0, ny in ((0, 6),)
+            for x0, nx in ((0, 4), (4, 2), (6, 4))]
+    patches, origins = [], []
+    for x0, y0, z0, nx, ny, nz in cuts:
+        Ug = np.zeros((5, nz + 4, ny + 4, nx + 4))
+        Ug[:, 2:-2, 2:-2, 2:-2] = level[:, z0:z0 + nz, y0:y0 + ny, x0:x0 + nx]
+        patches.append(Ug)
+        origins.append((x0, y0, z0))
+    done = amr.exchange_ghosts(patches, origins, (NX, NY, NZ))
+    for Ug, (x0, y0, z0, nx, ny, nz) in zip(done, cuts):
+        ix = np.mod(np.arange(x0 - 2, x0 + nx + 2), NX)
+        iy = np.mod(np.arange(y0 - 2, y0 + ny + 2), NY)
+        iz = np.mod(np.arange(z0 - 2, z0 + nz + 2), NZ)
+        assert np.array_equal(Ug, level[:, iz][:, :, iy][:, :, :, ix])
+
+
+def test_sibling_exchange_leaves_uncovered_ghosts():
+    """Two patches apart on a large level: nothing covers their ghosts, which keep their values;
+    touching along x, each patch's x ghosts on that side take the other's first two columns."""
+    a = np.full((5, 7, 7, 7), 1.0)
+    b = np.full((5, 7, 7, 7), 2.0)
+    a[:, 2:-2, 2:-2, 2:-2] = 10.0
+    b[:, 2:-2, 2:-2, 2:-2] = 20.0
+    far = amr.exchange_ghosts([a, b], [(0, 0, 0), (20, 20, 20)], (40, 40, 40))
+    assert np.array_equal(far[0], a) and np.array_equal(far[1], b)
+    near = amr.exchange_ghosts([a, b], [(0, 0, 0), (3, 0, 0)], (40, 40, 40))
+    assert (near[0][:, 2:-2, 2:-2, 5:7] == 20.0).all() and (near[0][:, 2:-2, 2:-2, :2] == 1.0).all()
+    assert (near[1][:, 2:-2, 2:-2, 0:2] == 10.0).all() and (near[1][:, 0:2] == 2.0).all()
