@@ -150,6 +150,18 @@ int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5],
 int hydro_fill_ghosts(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
                       int npatch);
 
+/* Same-level ghost exchange: every ghost cell of a patch that lies in the interior of a patch of the
+ * same level (another one, or the patch itself across the period) takes that interior cell's
+ * values; other ghost cells are left as they are (fill them from the coarser level first with
+ * hydro_fill_ghosts).  The level is periodic with period[3] = (x, y, z) fine cells.
+ *   fine:    npatch patches, ng == 2, interiors no larger than the period and not overlapping one
+ *            another (modulo the period); they must not share memory;
+ *   origins: host array [npatch][3] of int: each patch's first interior cell (wrapped by the period).
+ * Deterministic (each ghost cell has at most one source).  A call with a patch set different from
+ * the previous call's builds its copy list on the host (a spatial hash of the interiors) and
+ * synchronises the stream first. */
+int hydro_exchange_ghosts(hydro_ctx* ctx, const hydro_patch* fine, const int* origins, int npatch, const int period[3]);
+
 /* Oct groups read in place from a periodic level grid instead of a gathered buffer (the paper's
  * Ramses GPU procedure gathers each oct's neighbourhood into an N_v x 6^3 buffer first, Sec. 3;
  * here each group's 6^3 stencil is read from the level with periodic wrap as it is needed).

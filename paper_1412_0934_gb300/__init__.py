@@ -38,7 +38,7 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level", "hydro_fill_ghosts",
+           "hydro_step_octs_level", "hydro_fill_ghosts", "hydro_exchange_ghosts",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
            "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
@@ -84,6 +84,7 @@ def lib():
         L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
         L.hydro_step_octs_level.argtypes = [vp, PP, vp, ll, vp * 5, vp]
         L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
+        L.hydro_exchange_ghosts.argtypes = [vp, PP, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ctypes.c_int)]
         L.hydro_adjoint_step.argtypes = [vp, PP, vp, PP, PP, i]
         L.hydro_prim_to_cons.argtypes = [vp, PP, PP, i]
         L.hydro_prim_to_cons_adjoint.argtypes = [vp, PP, PP, PP, i]
@@ -242,6 +243,17 @@ def hydro_fill_ghosts(ctx, coarse, fine, origins):
     if len(o) != 3 * n:
         raise ValueError("one (x, y, z) origin per patch")
     _check(lib().hydro_fill_ghosts(ctx.handle, ctypes.byref(coarse.c), f, o, n), "hydro_fill_ghosts")
+
+
+def hydro_exchange_ghosts(ctx, fine, origins, period):
+    """Ghosts of the patches (list of Patch, ng = 2) covered by a same-level interior take its
+    values; origins: first interior cell (x, y, z) per patch; period: (x, y, z) of the level."""
+    f, n = _parray(fine)
+    o = (ctypes.c_int * (3 * n))(*[int(v) for xyz in origins for v in xyz])
+    if len(o) != 3 * n:
+        raise ValueError("one (x, y, z) origin per patch")
+    per = (ctypes.c_int * 3)(*[int(v) for v in period])
+    _check(lib().hydro_exchange_ghosts(ctx.handle, f, o, n, per), "hydro_exchange_ghosts")
 
 
 def hydro_step_octs_level(ctx, level, origins, out, dt):

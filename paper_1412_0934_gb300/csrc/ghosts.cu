@@ -1,4 +1,5 @@
-// Coarse-to-fine ghost fill of AMR patches, refinement ratio 2 (the paper's Ramses GPU procedure
+// Ghost cells of AMR patches.
+// Coarse-to-fine ghost fill, refinement ratio 2 (the paper's Ramses GPU procedure
 // builds chunks of patches whose boundary cells are interpolated from the coarser level, Sec. 3):
 // conservative piecewise-linear prolongation of each conserved variable, MinMod-limited slopes.
 // A fine cell with fine-level index f lies in coarse cell floor(f/2) (wrapped on the periodic
@@ -89,6 +90,32 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(const HostGhostPatch* patch
       static_cast<S*>(P.U[v])[out] = u;
     }
   }
+}
+
+// Same-level exchange: one block per copy task (a box of a source patch's interior into a box of a
+// destination patch's ghost shell), threads over the box's cells, five fields each.
+template <class S>
+__global__ void __launch_bounds__(256) k_copy_boxes(const HostGhostPatch* patches, const HostCopyTask* tasks) {
+  const HostCopyTask t = tasks[blockIdx.x];
+  const HostGhostPatch& D = patches[t.dst];
+  const HostGhostPatch& Sp = patches[t.src];
+  const int nxy = t.n[0] * t.n[1], total = nxy * t.n[2];
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    const int z = c / nxy, r = c - z * nxy, y = r / t.n[0], x = r - y * t.n[0];
+    const long long d = (long long)(t.dlo[2] + z) * D.sz + (long long)(t.dlo[1] + y) * D.sy + (t.dlo[0] + x);
+    const long long s = (long long)(t.slo[2] + z) * Sp.sz + (long long)(t.slo[1] + y) * Sp.sy + (t.slo[0] + x);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) static_cast<S*>(D.U[v])[d] = static_cast<const S*>(Sp.U[v])[s];
+  }
+}
+
+cudaError_t launch_copy_boxes(int elem_size, const HostGhostPatch* d_patches, const HostCopyTask* d_tasks, int ntasks,
+                              cudaStream_t s) {
+  if (elem_size == 4)
+    k_copy_boxes<float><<<ntasks, 256, 0, s>>>(d_patches, d_tasks);
+  else
+    k_copy_boxes<double><<<ntasks, 256, 0, s>>>(d_patches, d_tasks);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,

@@ -76,6 +76,14 @@ struct hydro_ctx {
   int2* d_ghost_blocks = nullptr;
   size_t ghost_blocks_cap = 0;
   int ghost_nblocks = 0;
+  // same-level ghost exchange: uploaded patch descriptors and copy tasks of the last set
+  std::vector<hydro::HostGhostPatch> xchg_key;
+  int xchg_period[3] = {0, 0, 0};
+  hydro::HostGhostPatch* d_xchg = nullptr;
+  size_t xchg_cap = 0;
+  hydro::HostCopyTask* d_tasks = nullptr;
+  size_t tasks_cap = 0;
+  int ntasks = 0;
   long long launches = 0;
 };
 
@@ -296,6 +304,8 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_stage_counters);
   cudaFree(c->d_ghost);
   cudaFree(c->d_ghost_blocks);
+  cudaFree(c->d_xchg);
+  cudaFree(c->d_tasks);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
@@ -553,6 +563,120 @@ int hydro_fill_ghosts(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch
   c->launches += 1;
   return cuda_status(hydro::launch_fill_ghosts(elem_size(c), c->d_ghost, c->d_ghost_blocks, c->ghost_nblocks,
                                                make_io(C, C), c->stream));
+}
+
+// Copy tasks of the same-level exchange: for each destination patch, every periodic image of every
+// patch interior (its own included) that meets its ghosted box.  Candidate sources come from a
+// coarse spatial hash of the interiors (64-cell bins over the period).
+static std::vector<hydro::HostCopyTask> exchange_tasks(const std::vector<hydro::HostGhostPatch>& P, const int per[3]) {
+  const int n = (int)P.size();
+  const int B = 64;
+  int nb[3];
+  for (int d = 0; d < 3; ++d) nb[d] = std::max(1, (per[d] + B - 1) / B);
+  auto org = [&](int p, int d) { const int o[3] = {P[p].ox, P[p].oy, P[p].oz}; return ((o[d] % per[d]) + per[d]) % per[d]; };
+  auto dim = [&](int p, int d) { return d == 0 ? P[p].nx : (d == 1 ? P[p].ny : P[p].nz); };
+  std::vector<std::vector<int>> bins((size_t)nb[0] * nb[1] * nb[2]);
+  // bins met by the positions [lo, hi) of axis d, each position wrapped into [0, period) first
+  auto bins_of = [&](int lo, int hi, int d) {
+    std::vector<int> out;
+    for (int x = lo; x < hi; ++x) {
+      const int b = (((x % per[d]) + per[d]) % per[d]) / B;
+      if (out.empty() || out.back() != b)
+        if (std::find(out.begin(), out.end(), b) == out.end()) out.push_back(b);
+    }
+    return out;
+  };
+  for (int p = 0; p < n; ++p) {
+    const std::vector<int> bx = bins_of(org(p, 0), org(p, 0) + dim(p, 0), 0);
+    const std::vector<int> by = bins_of(org(p, 1), org(p, 1) + dim(p, 1), 1);
+    const std::vector<int> bz = bins_of(org(p, 2), org(p, 2) + dim(p, 2), 2);
+    for (int z : bz)
+      for (int y : by)
+        for (int x : bx) bins[((size_t)z * nb[1] + y) * nb[0] + x].push_back(p);
+  }
+  std::vector<hydro::HostCopyTask> tasks;
+  std::vector<int> seen(n, -1);
+  for (int a = 0; a < n; ++a) {
+    int glo[3], ghi[3];
+    for (int d = 0; d < 3; ++d) {
+      glo[d] = org(a, d) - 2;
+      ghi[d] = org(a, d) + dim(a, d) + 2;
+    }
+    const std::vector<int> bx = bins_of(glo[0], ghi[0], 0), by = bins_of(glo[1], ghi[1], 1), bz = bins_of(glo[2], ghi[2], 2);
+    std::vector<int> cand;
+    for (int z : bz)
+      for (int y : by)
+        for (int x : bx)
+          for (int q : bins[((size_t)z * nb[1] + y) * nb[0] + x])
+            if (seen[q] != a) { seen[q] = a; cand.push_back(q); }
+    for (int b : cand) {
+      for (int kz = -2; kz <= 2; ++kz)
+        for (int ky = -2; ky <= 2; ++ky)
+          for (int kx = -2; kx <= 2; ++kx) {
+            const int k[3] = {kx, ky, kz};
+            int lo[3], hi[3];
+            bool empty = false, own = (b == a);
+            for (int d = 0; d < 3; ++d) {
+              const int s = org(b, d) + k[d] * per[d];
+              lo[d] = std::max(glo[d], s);
+              hi[d] = std::min(ghi[d], s + dim(b, d));
+              if (lo[d] >= hi[d]) empty = true;
+              if (k[d] != 0) own = false;
+            }
+            if (empty || own) continue;
+            hydro::HostCopyTask t;
+            t.dst = a;
+            t.src = b;
+            for (int d = 0; d < 3; ++d) {
+              t.dlo[d] = lo[d] - glo[d];
+              t.slo[d] = lo[d] - (org(b, d) + k[d] * per[d]) + 2;
+              t.n[d] = hi[d] - lo[d];
+            }
+            tasks.push_back(t);
+          }
+    }
+  }
+  return tasks;
+}
+
+int hydro_exchange_ghosts(hydro_ctx* c, const hydro_patch* fine, const int* origins, int npatch, const int period[3]) {
+  if (!c || !fine || !origins || !period || npatch < 1) return HYDRO_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (period[d] < 1) return HYDRO_ERR_ARG;
+  std::vector<hydro::HostGhostPatch> set((size_t)npatch);
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_patch& F = fine[i];
+    if (!valid_patch(c, F) || F.ng != 2 || F.nx > period[0] || F.ny > period[1] || F.nz > period[2])
+      return HYDRO_ERR_ARG;
+    hydro::HostGhostPatch& g = set[i];
+    for (int v = 0; v < 5; ++v) g.U[v] = F.U[v];
+    g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
+    g.ox = origins[3 * i]; g.oy = origins[3 * i + 1]; g.oz = origins[3 * i + 2];
+    g.nghost = 0;
+    g.sy = F.sy; g.sz = F.sz;
+  }
+  const bool same = c->xchg_key.size() == set.size() &&
+                    std::memcmp(c->xchg_key.data(), set.data(), set.size() * sizeof(set[0])) == 0 &&
+                    std::memcmp(c->xchg_period, period, sizeof(c->xchg_period)) == 0;
+  if (!same) {
+    const std::vector<hydro::HostCopyTask> tasks = exchange_tasks(set, period);
+    if (tasks.size() > 0x7fffffff) return HYDRO_ERR_ARG;
+    int rc = ensure_device(&c->d_xchg, &c->xchg_cap, (size_t)npatch);
+    if (rc) return rc;
+    rc = ensure_device(&c->d_tasks, &c->tasks_cap, std::max<size_t>(1, tasks.size()));
+    if (rc) return rc;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    if (cudaMemcpy(c->d_xchg, set.data(), set.size() * sizeof(set[0]), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!tasks.empty() && cudaMemcpy(c->d_tasks, tasks.data(), tasks.size() * sizeof(tasks[0]),
+                                      cudaMemcpyHostToDevice) != cudaSuccess))
+      return HYDRO_ERR_CUDA;
+    c->xchg_key.swap(set);
+    std::memcpy(c->xchg_period, period, sizeof(c->xchg_period));
+    c->ntasks = (int)tasks.size();
+  }
+  if (c->ntasks == 0) return HYDRO_OK;
+  c->launches += 1;
+  return cuda_status(hydro::launch_copy_boxes(elem_size(c), c->d_xchg, c->d_tasks, c->ntasks, c->stream));
 }
 
 int hydro_step_octs_level(hydro_ctx* c, const hydro_patch* level, const int* origins_dev, long long ngroups,

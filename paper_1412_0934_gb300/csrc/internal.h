@@ -78,6 +78,15 @@ struct HostGhostPatch {
   long long sy, sz;
 };
 
+// A box copied from patch src's interior (local ghosted coordinates slo) into patch dst's ghost
+// shell (dlo), n cells per axis (x, y, z).
+struct HostCopyTask {
+  int dst, src;
+  int dlo[3], slo[3], n[3];
+};
+cudaError_t launch_copy_boxes(int elem_size, const HostGhostPatch* d_patches, const HostCopyTask* d_tasks, int ntasks,
+                              cudaStream_t s);
+
 // Coarse-to-fine ghost fill (ghosts.cu): block b fills ghost cells d_blocks[b].y .. +255 of patch
 // d_blocks[b].x.
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,

@@ -78,3 +78,70 @@ def test_ghost_fill_4096_patches_on_128cube_sampled():
         want = amr.fill_ghosts(Uc, np.full(got.shape, 7.0), origins[i])
         assert np.array_equal(got, want), i
     check_clean(c)
+
+
+def _partition(rng, period, pieces):
+    """Blocks tiling the periodic level: cut positions per axis (x, y, z) -> list of (origin, dims)."""
+    cuts = []
+    for P, k in zip(period, pieces):
+        c = np.sort(rng.choice(np.arange(1, P), k - 1, replace=False)) if k > 1 else np.array([], dtype=int)
+        edges = np.concatenate([[0], c, [P]])
+        cuts.append(list(zip(edges[:-1], np.diff(edges))))
+    return [((int(x0), int(y0), int(z0)), (int(nx), int(ny), int(nz)))
+            for z0, nz in cuts[2] for y0, ny in cuts[1] for x0, nx in cuts[0]]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_exchange_then_fill_matches_oracle(precision):
+    """Coarse fill, then the same-level exchange, on blocks tiling a periodic fine level with a
+    third of them removed (their neighbours' ghosts stay prolonged), origins shifted by whole
+    periods, and one axis of a single block (the block's own periodic image)."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    c = ctx(precision)
+    rng = np.random.default_rng(21)
+    coarse = workloads.turbulent_state((5, 4, 6), seed=12, mach=3.0, sedov=False).to(dtype).contiguous()
+    Uc = coarse.double().numpy()
+    period = (12, 8, 10)  # fine level (x, y, z) = 2 x coarse
+    blocks = _partition(rng, period, (3, 1, 3))
+    keep = [b for b in blocks if rng.random() > 0.33]
+    origins = [(o[0] + int(rng.integers(-1, 2)) * period[0], o[1] + int(rng.integers(-1, 2)) * period[1],
+                o[2] + int(rng.integers(-1, 2)) * period[2]) for o, _ in keep]
+    fine = workloads.turbulent_state((10, 8, 12), seed=13, mach=3.0, sedov=False).to(dtype)
+    tens, host = [], []
+    for (o, (nx, ny, nz)), oo in zip(keep, origins):
+        t = torch.zeros((5, nz + 4, ny + 4, nx + 4), dtype=dtype)
+        t[:, 2:-2, 2:-2, 2:-2] = fine[:, o[2]:o[2] + nz, o[1]:o[1] + ny, o[0]:o[0] + nx]
+        host.append(t.double().numpy())
+        tens.append(t.cuda())
+    dxc = 1.0 / 6
+    pf = [hy.patch(t, 2, dxc / 2) for t in tens]
+    hy.hydro_fill_ghosts(c, hy.patch(coarse.cuda(), 0, dxc), pf, origins)
+    hy.hydro_exchange_ghosts(c, pf, origins, period)
+    torch.cuda.synchronize()
+    want = [amr.fill_ghosts(Uc, h, o) for h, o in zip(host, origins)]
+    want = amr.exchange_ghosts(want, origins, period)
+    for t, w in zip(tens, want):
+        got = t.double().cpu().numpy()
+        if dtype == torch.float64:
+            assert np.array_equal(got, w)
+        else:
+            assert np.abs(got - w).max() <= 1e-6 * np.abs(w).max()
+    check_clean(c)
+
+
+def test_exchange_reassembles_a_tiled_level_bitwise():
+    c = ctx("fp64")
+    rng = np.random.default_rng(22)
+    period = (40, 24, 32)
+    level = workloads.turbulent_state((32, 24, 40), seed=14, mach=2.0, sedov=False)
+    blocks = _partition(rng, period, (4, 2, 3))
+    tens = []
+    for o, (nx, ny, nz) in blocks:
+        t = torch.full((5, nz + 4, ny + 4, nx + 4), -1.0, dtype=torch.float64)
+        t[:, 2:-2, 2:-2, 2:-2] = level[:, o[2]:o[2] + nz, o[1]:o[1] + ny, o[0]:o[0] + nx]
+        tens.append(t.cuda())
+    hy.hydro_exchange_ghosts(c, [hy.patch(t, 2, 1.0 / 40) for t in tens], [o for o, _ in blocks], period)
+    torch.cuda.synchronize()
+    for t, (o, (nx, ny, nz)) in zip(tens, blocks):
+        want = workloads.ghosted_from_periodic(level, o, (nx, ny, nz))
+        assert torch.equal(t.cpu(), want)
