@@ -440,6 +440,77 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     return out
 
 
+def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
+    """One AMR level step: a 256^3 fine level tiled by 16^3 patches of random edges (cuts at random
+    positions per axis), ghosts prolonged from the 128^3 coarse level, then exchanged between
+    siblings, then the batched mixed-precision step of all patches; mixed precision."""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+    ctx = hy.hydro_init(precision="mixed")
+    coarse = turbulent(n // 2, "mixed", "cuda", seed=seed, sedov=False)
+    fine = turbulent(n, "mixed", "cuda", seed=seed + 1, sedov=False)
+    rng = np.random.default_rng(seed)
+    axes = []
+    for _ in range(3):
+        c = np.sort(rng.choice(np.arange(1, n), pieces - 1, replace=False))
+        e = np.concatenate([[0], c, [n]])
+        axes.append(list(zip(e[:-1].tolist(), np.diff(e).tolist())))
+    ins, outs, keep, origins = [], [], [], []
+    interior = 0
+    for z0, nz in axes[2]:
+        for y0, ny in axes[1]:
+            for x0, nx in axes[0]:
+                Ug = torch.zeros((5, nz + 4, ny + 4, nx + 4), dtype=torch.float64, device="cuda")
+                Ug[:, 2:-2, 2:-2, 2:-2] = fine[:, z0:z0 + nz, y0:y0 + ny, x0:x0 + nx]
+                Vg = torch.empty_like(Ug)
+                keep += [Ug, Vg]
+                ins.append(hy.patch(Ug, 2, 1.0 / n))
+                outs.append(hy.patch(Vg, 2, 1.0 / n))
+                origins.append((x0, y0, z0))
+                interior += nx * ny * nz
+    del fine
+    cp = hy.patch(coarse, 0, 2.0 / n)
+    per = (n, n, n)
+    dt = torch.empty(len(ins), dtype=torch.float64, device="cuda")
+    hy.hydro_fill_ghosts(ctx, cp, ins, origins)
+    hy.hydro_exchange_ghosts(ctx, ins, origins, per)
+    hy.hydro_cfl_dt(ctx, ins, dt)
+    if TUNING == "auto":
+        hy.hydro_autotune(ctx, ins, outs, dt)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def one():
+        ev[0].record(stream)
+        hy.hydro_fill_ghosts(ctx, cp, ins, origins)
+        ev[1].record(stream)
+        hy.hydro_exchange_ghosts(ctx, ins, origins, per)
+        ev[2].record(stream)
+        hy.hydro_step(ctx, ins, outs, dt)
+        ev[3].record(stream)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    parts = np.zeros(3)
+    for _ in range(steps):
+        one()
+        torch.cuda.synchronize()
+        parts += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    parts /= steps
+    ghosts = sum(t[0].numel() for t in keep[0::2]) - interior
+    rc, bits = hy.hydro_get_error(ctx)
+    t, z = hy.hydro_get_tuning(ctx)
+    out = {"patches": len(ins), "interior_cells": interior, "ghost_cells": ghosts,
+           "ms_fill_from_coarse": parts[0], "ms_exchange": parts[1], "ms_step": parts[2],
+           "mcell_updates_per_s": interior / (parts.sum() / 1e3) / 1e6,
+           "step_only_mcell_updates_per_s": interior / (parts[2] / 1e3) / 1e6,
+           "tuning": {"tile": TILE_NAMES[t], "zchunk": z}, "error_bits": bits}
+    del keep, coarse
+    hy.hydro_finalize(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
 def form_adjoint(hy, precision, n=64, nsteps=40):
     """Adjoint/forward time ratio on the 64^3 periodic grid (one step each, and the 40-step
     checkpointed gradient against the 40-step forward)."""
@@ -651,7 +722,7 @@ def main():
             "clocks": clk.summary(), "device_error_bits": bits}
 
     forms = [] if args.forms == "none" else (
-        ["fp64", "fp32", "batched", "adjoint", "graph1024"] if args.forms == "all" else args.forms.split(","))
+        ["fp64", "fp32", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all" else args.forms.split(","))
     forms = [f for f in forms if f != precision]
     if rank == 0:
         extra = {}
@@ -670,6 +741,8 @@ def main():
                 elif f == "adjoint":
                     for prec in args.adj_precisions.split(","):
                         extra["adjoint_" + prec] = form_adjoint(hy, prec, n=args.adj_n)
+                elif f == "amr":
+                    extra["amr_level_mixed"] = form_amr_level(hy, max(3, args.steps // 2), 2)
                 elif f == "graph1024":
                     extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                                sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,

@@ -55,7 +55,7 @@ template <class S>
 __global__ void __launch_bounds__(256) k_fill_ghosts(const HostGhostPatch* patches, const int2* blocks,
                                                      HostPatchIO coarse) {
   const int2 b = blocks[blockIdx.x];  // (patch, first ghost cell of this block)
-  const HostGhostPatch& P = patches[b.x];
+  const HostGhostPatch P = patches[b.x];  // by value: the stores below cannot alias it
   const int g = b.y + threadIdx.x;
   if (g < P.nghost) {
     int i, j, k;
@@ -97,8 +97,7 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(const HostGhostPatch* patch
 template <class S>
 __global__ void __launch_bounds__(256) k_copy_boxes(const HostGhostPatch* patches, const HostCopyTask* tasks) {
   const HostCopyTask t = tasks[blockIdx.x];
-  const HostGhostPatch& D = patches[t.dst];
-  const HostGhostPatch& Sp = patches[t.src];
+  const HostGhostPatch D = patches[t.dst], Sp = patches[t.src];  // by value: the stores cannot alias them
   const int nxy = t.n[0] * t.n[1], total = nxy * t.n[2];
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     const int z = c / nxy, r = c - z * nxy, y = r / t.n[0], x = r - y * t.n[0];
