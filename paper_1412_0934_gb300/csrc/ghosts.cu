@@ -21,73 +21,76 @@ __device__ __forceinline__ S minmod_s(S a, S b) {
   return abs_le(a, b) ? a : b;
 }
 
-// Ghost cell g (0 .. ghosts-1) of a ghosted box GX x GY x GZ (interior nx x ny x nz at offset 2):
-// the 4 full z planes below/above, then the 4 full y rows per interior plane, then the 4 x cells
-// per interior row.
-__device__ __forceinline__ void ghost_cell(int g, int nx, int ny, int nz, int& i, int& j, int& k) {
-  const int GX = nx + 4, GY = ny + 4;
-  const int A = 4 * GX * GY, B = 4 * nz * GX;
-  if (g < A) {
-    const int zi = g / (GX * GY);
-    const int r = g - zi * GX * GY;
-    k = zi < 2 ? zi : nz + zi;
-    j = r / GX;
-    i = r - j * GX;
-  } else if (g < A + B) {
-    const int h = g - A;
-    const int zi = h / (4 * GX);
-    const int r = h - zi * 4 * GX;
-    const int yi = r / GX;
-    k = zi + 2;
-    j = yi < 2 ? yi : ny + yi;
-    i = r - yi * GX;
-  } else {
-    const int h = g - A - B;
-    const int row = h >> 2;
-    const int xi = h & 3;
-    k = row / ny + 2;
-    j = row - (k - 2) * ny + 2;
-    i = xi < 2 ? xi : nx + xi;
-  }
-}
-
+// One thread per coarse cell under a patch's ghost shell: it forms the cell's three limited
+// slopes once and its eight children as ((U_C +- D_x/4) +- D_y/4) +- D_z/4 -- the two x partial
+// sums, then four, then eight (the same operations in the same order as child by child, so the
+// same bits) -- and writes the children that are ghost cells of the patch.  Coarse cells whose
+// children are all interior return at once.  Each block takes up to 256 coarse cells of one patch
+// (a block table built on the host).
 template <class S>
 __global__ void __launch_bounds__(256) k_fill_ghosts(const HostGhostPatch* patches, const int2* blocks,
                                                      HostPatchIO coarse) {
-  const int2 b = blocks[blockIdx.x];  // (patch, first ghost cell of this block)
+  const int2 b = blocks[blockIdx.x];      // (patch, first coarse cell of this block)
   const HostGhostPatch P = patches[b.x];  // by value: the stores below cannot alias it
-  const int g = b.y + threadIdx.x;
-  if (g < P.nghost) {
-    int i, j, k;
-    ghost_cell(g, P.nx, P.ny, P.nz, i, j, k);
-    const int f[3] = {P.ox + i - 2, P.oy + j - 2, P.oz + k - 2};
-    const int n[3] = {coarse.nx, coarse.ny, coarse.nz};
-    int c[3];
-    S s[3];
+  const int t = b.y + threadIdx.x;
+  const int ncell = P.cm[0] * P.cm[1] * P.cm[2];
+  if (t >= ncell) return;
+  const int cz = t / (P.cm[0] * P.cm[1]), r = t - cz * P.cm[0] * P.cm[1], cy = r / P.cm[0], cx = r - cy * P.cm[0];
+  const int cc[3] = {P.clo[0] + cx, P.clo[1] + cy, P.clo[2] + cz};
+  const int n[3] = {P.nx, P.ny, P.nz}, o[3] = {P.ox, P.oy, P.oz};
+  // local ghosted index of child h (0, 1) along d, and whether it is in the box / in the interior
+  int l[3][2];
+  bool inb[3][2], inr[3][2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      int q = f[d] >> 1;  // floor(f / 2)
-      q %= n[d];
-      c[d] = q < 0 ? q + n[d] : q;
-      s[d] = (f[d] & 1) ? S(0.25) : S(-0.25);
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      l[d][h] = 2 * cc[d] + h - (o[d] - 2);
+      inb[d][h] = l[d][h] >= 0 && l[d][h] < n[d] + 4;
+      inr[d][h] = l[d][h] >= 2 && l[d][h] < n[d] + 2;
     }
-    const long long a0 = c[2] * coarse.isz + c[1] * coarse.isy + c[0];
-    const long long st[3] = {1, coarse.isy, coarse.isz};
-    long long am[3], ap[3];
+  bool any = false;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      am[d] = a0 + (c[d] == 0 ? (long long)(n[d] - 1) * st[d] : -st[d]);
-      ap[d] = a0 + (c[d] == n[d] - 1 ? -(long long)(n[d] - 1) * st[d] : st[d]);
-    }
-    const long long out = (long long)k * P.sz + (long long)j * P.sy + i;
+  for (int k = 0; k < 8; ++k) {
+    const int hx = k & 1, hy = (k >> 1) & 1, hz = k >> 2;
+    any |= inb[0][hx] && inb[1][hy] && inb[2][hz] && !(inr[0][hx] && inr[1][hy] && inr[2][hz]);
+  }
+  if (!any) return;
+  const int nc[3] = {coarse.nx, coarse.ny, coarse.nz};
+  int c[3];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const S* U = static_cast<const S*>(coarse.in[v]);
-      const S u0 = __ldg(U + a0);
-      S u = u0;
+  for (int d = 0; d < 3; ++d) {
+    const int q = cc[d] % nc[d];
+    c[d] = q < 0 ? q + nc[d] : q;
+  }
+  const long long a0 = c[2] * coarse.isz + c[1] * coarse.isy + c[0];
+  const long long st[3] = {1, coarse.isy, coarse.isz};
+  long long am[3], ap[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) u = u + s[d] * minmod_s(u0 - __ldg(U + am[d]), __ldg(U + ap[d]) - u0);
-      static_cast<S*>(P.U[v])[out] = u;
+  for (int d = 0; d < 3; ++d) {
+    am[d] = a0 + (c[d] == 0 ? (long long)(nc[d] - 1) * st[d] : -st[d]);
+    ap[d] = a0 + (c[d] == nc[d] - 1 ? -(long long)(nc[d] - 1) * st[d] : st[d]);
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const S* U = static_cast<const S*>(coarse.in[v]);
+    const S u0 = __ldg(U + a0);
+    S D[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) D[d] = minmod_s(u0 - __ldg(U + am[d]), __ldg(U + ap[d]) - u0);
+    S ax[2], ay[4], az[8];
+#pragma unroll
+    for (int hx = 0; hx < 2; ++hx) ax[hx] = u0 + (hx ? S(0.25) : S(-0.25)) * D[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ay[k] = ax[k & 1] + ((k >> 1) ? S(0.25) : S(-0.25)) * D[1];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) az[k] = ay[k & 3] + ((k >> 2) ? S(0.25) : S(-0.25)) * D[2];
+    S* out = static_cast<S*>(P.U[v]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int hx = k & 1, hy = (k >> 1) & 1, hz = k >> 2;
+      if (inb[0][hx] && inb[1][hy] && inb[2][hz] && !(inr[0][hx] && inr[1][hy] && inr[2][hz]))
+        out[(long long)l[2][hz] * P.sz + (long long)l[1][hy] * P.sy + l[0][hx]] = az[k];
     }
   }
 }

@@ -537,16 +537,24 @@ int hydro_fill_ghosts(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch
     g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
     g.ox = fine_origins[3 * i]; g.oy = fine_origins[3 * i + 1]; g.oz = fine_origins[3 * i + 2];
     g.sy = F.sy; g.sz = F.sz;
-    const long long cells = (long long)(F.nx + 4) * (F.ny + 4) * (F.nz + 4) - (long long)F.nx * F.ny * F.nz;
+    const int o[3] = {g.ox, g.oy, g.oz}, nn[3] = {F.nx, F.ny, F.nz};
+    long long cells = 1;
+    for (int d = 0; d < 3; ++d) {  // coarse cells floor((o-2)/2) .. floor((o+n+1)/2)
+      const long long lo = (long long)std::floor((o[d] - 2) / 2.0), hi = (long long)std::floor((o[d] + nn[d] + 1) / 2.0);
+      if (lo < -0x3fffffffLL || hi > 0x3fffffffLL) return HYDRO_ERR_ARG;
+      g.clo[d] = (int)lo;
+      g.cm[d] = (int)(hi - lo + 1);
+      cells *= g.cm[d];
+    }
     if (cells > 0x7fffffff) return HYDRO_ERR_ARG;
-    g.nghost = (int)cells;
   }
   const bool same = c->ghost_key.size() == set.size() &&
                     std::memcmp(c->ghost_key.data(), set.data(), set.size() * sizeof(set[0])) == 0;
   if (!same) {
     std::vector<int2> blocks;
     for (int i = 0; i < npatch; ++i)
-      for (int first = 0; first < set[i].nghost; first += 256) blocks.push_back(make_int2(i, first));
+      for (int first = 0; first < set[i].cm[0] * set[i].cm[1] * set[i].cm[2]; first += 256)
+        blocks.push_back(make_int2(i, first));
     if (blocks.size() > 0x7fffffff) return HYDRO_ERR_ARG;
     int rc = ensure_device(&c->d_ghost, &c->ghost_cap, (size_t)npatch);
     if (rc) return rc;
@@ -652,7 +660,7 @@ int hydro_exchange_ghosts(hydro_ctx* c, const hydro_patch* fine, const int* orig
     for (int v = 0; v < 5; ++v) g.U[v] = F.U[v];
     g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
     g.ox = origins[3 * i]; g.oy = origins[3 * i + 1]; g.oz = origins[3 * i + 2];
-    g.nghost = 0;
+    for (int d = 0; d < 3; ++d) g.clo[d] = g.cm[d] = 0;
     g.sy = F.sy; g.sz = F.sz;
   }
   const bool same = c->xchg_key.size() == set.size() &&

@@ -74,7 +74,7 @@ struct HostGhostPatch {
   void* U[5];
   int nx, ny, nz;
   int ox, oy, oz;
-  int nghost;  // ghost cells: (nx+4)(ny+4)(nz+4) - nx ny nz
+  int clo[3], cm[3];  // coarse cells under the ghosted box: lowest index and count per axis
   long long sy, sz;
 };
 
@@ -87,8 +87,8 @@ struct HostCopyTask {
 cudaError_t launch_copy_boxes(int elem_size, const HostGhostPatch* d_patches, const HostCopyTask* d_tasks, int ntasks,
                               cudaStream_t s);
 
-// Coarse-to-fine ghost fill (ghosts.cu): block b fills ghost cells d_blocks[b].y .. +255 of patch
-// d_blocks[b].x.
+// Coarse-to-fine ghost fill (ghosts.cu): block b takes coarse cells d_blocks[b].y .. +255 under
+// patch d_blocks[b].x.
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
                                const HostPatchIO& coarse, cudaStream_t s);
 
