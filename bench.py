@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--ngroups", type=int, default=262144, help="oct groups of the batched form")
     p.add_argument("--adj-n", type=int, default=64, help="grid edge of the adjoint form")
     p.add_argument("--adj-precisions", default="df64,fp64,fp32", help="precisions of the adjoint form")
+    p.add_argument("--forms-only", action="store_true",
+                   help="run only the extra forms and print their JSON (for profiling them alone)")
     return p.parse_args()
 
 
@@ -630,6 +632,38 @@ def reference_arm(args):
     return 0
 
 
+def run_forms(hy, args, n, precision):
+    """The extra forms beside the headline (each failure reported, not fatal)."""
+    forms = [] if args.forms == "none" else (
+        ["fp64", "fp32", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all" else args.forms.split(","))
+    forms = [f for f in forms if f != precision]
+    extra = {}
+    for f in forms:
+        try:
+            if f == "fp32":
+                extra["fp32_512"] = form_uniform(hy, n, "fp32", "minmod", args.steps, args.warmup, "turb_minmod")
+            elif f == "fp64_256":
+                extra["fp64_256"] = form_uniform(hy, 256, "fp64", "minmod", args.steps, args.warmup,
+                                                 "turb_minmod")
+            elif f in ("fp64", "df64"):
+                extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod")
+            elif f == "batched":
+                extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch,
+                                                      ngroups=args.ngroups)
+            elif f == "adjoint":
+                for prec in args.adj_precisions.split(","):
+                    extra["adjoint_" + prec] = form_adjoint(hy, prec, n=args.adj_n)
+            elif f == "amr":
+                extra["amr_level_mixed"] = form_amr_level(hy, max(3, args.steps // 2), 2)
+            elif f == "graph1024":
+                extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
+                                                           sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,
+                                                           graph=True)
+        except Exception as e:  # a failing extra form is reported, not fatal
+            extra[f] = {"error": repr(e)[:300]}
+    return extra
+
+
 def main():
     global TUNING
     args = parse()
@@ -645,6 +679,9 @@ def main():
 
     precision = args.precision
     n = args.n
+    if args.forms_only:
+        print(json.dumps(run_forms(hy, args, n, precision)), flush=True)
+        return 0
     dx = 1.0 / n
     cells = n ** 3
     stream = torch.cuda.current_stream()
@@ -721,34 +758,8 @@ def main():
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "device_error_bits": bits}
 
-    forms = [] if args.forms == "none" else (
-        ["fp64", "fp32", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all" else args.forms.split(","))
-    forms = [f for f in forms if f != precision]
     if rank == 0:
-        extra = {}
-        for f in forms:
-            try:
-                if f == "fp32":
-                    extra["fp32_512"] = form_uniform(hy, n, "fp32", "minmod", args.steps, args.warmup, "turb_minmod")
-                elif f == "fp64_256":
-                    extra["fp64_256"] = form_uniform(hy, 256, "fp64", "minmod", args.steps, args.warmup,
-                                                     "turb_minmod")
-                elif f in ("fp64", "df64"):
-                    extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod")
-                elif f == "batched":
-                    extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch,
-                                                          ngroups=args.ngroups)
-                elif f == "adjoint":
-                    for prec in args.adj_precisions.split(","):
-                        extra["adjoint_" + prec] = form_adjoint(hy, prec, n=args.adj_n)
-                elif f == "amr":
-                    extra["amr_level_mixed"] = form_amr_level(hy, max(3, args.steps // 2), 2)
-                elif f == "graph1024":
-                    extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
-                                                               sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,
-                                                               graph=True)
-            except Exception as e:  # a failing extra form is reported, not fatal
-                extra[f] = {"error": repr(e)[:300]}
+        extra = run_forms(hy, args, n, precision)
         line["forms"] = extra
         if args.cpu_seconds > 0:
             line["cpu_baseline"] = cpu_baseline(128, args.cpu_seconds)
