@@ -196,6 +196,20 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def job_time_ms(ms, world, device):
+    """The job's timed-region duration: the maximum over ranks of each rank's own (replicas)."""
+    if world == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(cells, steps, world, t_max_ms):
+    """Whole-job throughput in Mcell-updates/s: every rank's cells over the slowest rank's time."""
+    return world * cells * steps / (t_max_ms / 1e3) / 1e6
+
+
 # ----------------------------------------------------------------------------- workloads
 def turbulent(n, precision, device, seed=2, mach=5.0, sigma=1.0, p_over_rho=1e-4, sedov=True):
     import workloads
@@ -704,12 +718,8 @@ def main():
     rc, bits = hy.hydro_get_error(ctx)
     if rc != hy.HYDRO_OK:
         print("device error bits %#x" % bits, file=sys.stderr)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = t.item()
-    value = world * cells * args.steps / (t_max / 1e3) / 1e6
+    t_max = job_time_ms(ms, world, "cuda")
+    value = job_value(cells, args.steps, world, t_max)
     hbm, src = peaks()
     traffic, tsrc = profile_traffic("step_uniform_512_%s.txt" % precision)
     roof = roofline(precision, cells, per, ALG_FLOPS_PER_CELL["turb_minmod"], hbm, src, traffic)
