@@ -446,12 +446,11 @@ __device__ __forceinline__ void publish_dt(double cfl, double dx, double smax, d
 
 // ------------------------------------------------------------------ kernels
 // Resident blocks per SM the register allocation must allow: 2 x 256 threads for 8-byte
-// arithmetic (its shared memory allows 2), 3 x 256 for FP32, 4 x 256 for the mixed policy (which
-// gains more from the extra warps than it loses to the spills of a 64-register budget; FP32 does
-// not, measured).
+// arithmetic (its shared memory allows 2), 3 x 256 for float arithmetic (4 x 256, a 64-register
+// budget, spills more than the extra warps gain: measured -8% for FP32, 0..-2% for mixed).
 template <class Pol, int NT, int MINB>
 constexpr int min_blocks() {
-  constexpr int b = (sizeof(typename Pol::R) >= 8 ? 2 : std::is_same<Pol, PolMixed>::value ? 4 : 3) * 256 / NT;
+  constexpr int b = (sizeof(typename Pol::R) >= 8 ? 2 : 3) * 256 / NT;
   return MINB > 0 ? MINB : (b < 1 ? 1 : b);
 }
 
