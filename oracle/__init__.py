@@ -57,6 +57,7 @@ def lib():
         L.oracle_prim_to_cons.argtypes = [P, vp, vp, ctypes.c_long]
         L.oracle_prim_to_cons_adjoint.argtypes = [P, vp, vp, vp, ctypes.c_long]
         L.oracle_count_ops.argtypes = [P, vp, i, i, i, d, d, vp]
+        L.oracle_patch_boundary_fluxes.argtypes = [P, vp, i, i, i, d, d, vp]
         _lib = L
     return _lib
 
@@ -89,6 +90,19 @@ def step_patch(Ug, dx, dt, cfg=None):
     nx, ny, nz = NX - 2 * GHOST, NY - 2 * GHOST, NZ - 2 * GHOST
     out = np.empty((5, nz, ny, nx))
     _check(lib().oracle_step_patch(ctypes.byref(cfg), pu, out.ctypes.data, nx, ny, nz, dx, dt))
+    return out
+
+
+def patch_boundary_fluxes(Ug, dx, dt, cfg=None):
+    """Fluxes through the six boundary faces of the ghosted patch Ug's interior, as step_patch
+    applies them: (5, R) with R = 2 (ny nz + nx nz + nx ny), per field x-low [nz][ny], x-high,
+    y-low [nz][nx], y-high, z-low [ny][nx], z-high."""
+    cfg = cfg or config()
+    Ug, pu = _c(Ug)
+    _, NZ, NY, NX = Ug.shape
+    nx, ny, nz = NX - 2 * GHOST, NY - 2 * GHOST, NZ - 2 * GHOST
+    out = np.empty((5, 2 * (ny * nz + nx * nz + nx * ny)))
+    _check(lib().oracle_patch_boundary_fluxes(ctypes.byref(cfg), pu, nx, ny, nz, dx, dt, out.ctypes.data))
     return out
 
 

@@ -93,3 +93,73 @@ def exchange_ghosts(patches, origins, period):
                 vals[:, inside] = np.asarray(Ub)[:, r[:, 2] + 2, r[:, 1] + 2, r[:, 0] + 2]
         Ua[:, ghost] = vals
     return out
+
+
+# ------------------------------------------------------------------ flux registers and refluxing
+# A patch's boundary-face register, per field: x-low [nz][ny], x-high [nz][ny], y-low [nz][nx],
+# y-high [nz][nx], z-low [ny][nx], z-high [ny][nx] (the layout of oracle.patch_boundary_fluxes).
+# Registers hold time-integrated fluxes (sum over steps of dt * F).
+
+def _faces(R, n):
+    """Split a (5, R) register of a box with interior n = (nx, ny, nz) into the six face arrays."""
+    nx, ny, nz = n
+    sizes = [nz * ny, nz * ny, nz * nx, nz * nx, ny * nx, ny * nx]
+    shapes = [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+    out, a = [], 0
+    for s, sh in zip(sizes, shapes):
+        out.append(R[:, a:a + s].reshape((5,) + sh))
+        a += s
+    return out
+
+
+def reflux(Uc, origin_c, n_c, Rc, Rf, dxc):
+    """Coarse level Uc (5, NZ, NY, NX), periodic, after a coarse step whose fluxes through the
+    boundary faces of the coarse box B (origin_c, n_c (x, y, z)) integrate to the register Rc; the
+    fine patch covering B (refinement 2) integrated Rf through the same faces.  Each coarse cell
+    outside B across one of those faces is corrected from the coarse to the fine flux integral:
+        U_C += s / dxc * (Rc_face - (1/4) sum of the 4 fine faces' Rf),
+    s = +1 when the face is C's upper face (C below B), -1 when it is its lower face.  Cells
+    inside B are left to average_down.  Returns a new array."""
+    U = np.array(Uc, dtype=np.float64)
+    _, NZ, NY, NX = U.shape
+    ox, oy, oz = origin_c
+    nx, ny, nz = n_c
+    fc = _faces(np.asarray(Rc), (nx, ny, nz))
+    ff = _faces(np.asarray(Rf), (2 * nx, 2 * ny, 2 * nz))
+
+    def avg(F):  # (5, 2a, 2b) fine faces -> (5, a, b) coarse-face means
+        return 0.25 * (F[:, 0::2, 0::2] + F[:, 1::2, 0::2] + F[:, 0::2, 1::2] + F[:, 1::2, 1::2])
+
+    for side, s in ((0, 1.0), (1, -1.0)):
+        d = s / dxc * (fc[side] - avg(ff[side]))  # x faces [k][j]
+        x = (ox - 1) % NX if side == 0 else (ox + nx) % NX
+        for k in range(nz):
+            for j in range(ny):
+                U[:, (oz + k) % NZ, (oy + j) % NY, x] += d[:, k, j]
+        d = s / dxc * (fc[2 + side] - avg(ff[2 + side]))  # y faces [k][i]
+        y = (oy - 1) % NY if side == 0 else (oy + ny) % NY
+        for k in range(nz):
+            for i in range(nx):
+                U[:, (oz + k) % NZ, y, (ox + i) % NX] += d[:, k, i]
+        d = s / dxc * (fc[4 + side] - avg(ff[4 + side]))  # z faces [j][i]
+        z = (oz - 1) % NZ if side == 0 else (oz + nz) % NZ
+        for j in range(ny):
+            for i in range(nx):
+                U[:, z, (oy + j) % NY, (ox + i) % NX] += d[:, j, i]
+    return U
+
+
+def average_down(Uc, Uf, origin_c):
+    """Coarse cells of the box at origin_c (x, y, z) covered by the fine interior Uf (5, 2nz, 2ny,
+    2nx) replaced by the mean of their eight children.  Returns a new array."""
+    U = np.array(Uc, dtype=np.float64)
+    _, NZ, NY, NX = U.shape
+    _, FZ, FY, FX = Uf.shape
+    m = np.asarray(Uf, dtype=np.float64).reshape(5, FZ // 2, 2, FY // 2, 2, FX // 2, 2)
+    mean = 0.125 * m.sum(axis=(2, 4, 6))
+    ox, oy, oz = origin_c
+    iz = (oz + np.arange(FZ // 2)) % NZ
+    iy = (oy + np.arange(FY // 2)) % NY
+    ix = (ox + np.arange(FX // 2)) % NX
+    U[np.ix_(range(5), iz, iy, ix)] = mean
+    return U

@@ -88,6 +88,42 @@ int oracle_step_patch(const oracle_config* cfg, const double* Ug, double* out, i
   return 0;
 }
 
+// The fluxes through the six boundary faces of a ghosted patch's interior, the ones step_patch
+// applies there (for the flux registers of AMR refluxing).  out per field v, in this order:
+// x-low [nz][ny], x-high [nz][ny], y-low [nz][nx], y-high [nz][nx], z-low [ny][nx], z-high [ny][nx]
+// (faces i = 0 and i = nx of the interior, and so on).
+int oracle_patch_boundary_fluxes(const oracle_config* cfg, const double* Ug, int nx, int ny, int nz, double dx,
+                                 double dt, double* out) {
+  if (!cfg || !Ug || !out || bad_dims(nx, ny, nz)) return -1;
+  const Config c = to_cfg(cfg);
+  Fields<double> A, q, qh, slope[3], flux[3];
+  load(A, Ug, nx + 2 * G, ny + 2 * G, nz + 2 * G);
+  stage_recover(c, A, q);
+  stage_slopes(c, q, slope);
+  stage_predict(c, q, slope, qh, dx, dt);
+  stage_fluxes(c, qh, slope, flux);
+  const size_t R = 2 * ((size_t)ny * nz + (size_t)nx * nz + (size_t)nx * ny);
+  for (int v = 0; v < 5; ++v) {
+    double* o = out + v * R;
+    for (int side = 0; side < 2; ++side) {
+      const int i = side ? G + nx - 1 : G - 1;
+      for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j) *o++ = flux[0].f[v][A.at(i, G + j, G + k)];
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int j = side ? G + ny - 1 : G - 1;
+      for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < nx; ++i) *o++ = flux[1].f[v][A.at(G + i, j, G + k)];
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int k = side ? G + nz - 1 : G - 1;
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) *o++ = flux[2].f[v][A.at(G + i, G + j, k)];
+    }
+  }
+  return 0;
+}
+
 // CFL dt of a periodic box ([5][nz][ny][nx]) or of the interior of a ghosted patch.
 double oracle_cfl_periodic(const oracle_config* cfg, const double* U, int nx, int ny, int nz, double dx) {
   if (!cfg || !U || bad_dims(nx, ny, nz)) return -1.0;

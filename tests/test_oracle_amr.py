@@ -104,3 +104,47 @@ def test_sibling_exchange_leaves_uncovered_ghosts():
     near = amr.exchange_ghosts([a, b], [(0, 0, 0), (3, 0, 0)], (40, 40, 40))
     assert (near[0][:, 2:-2, 2:-2, 5:7] == 20.0).all() and (near[0][:, 2:-2, 2:-2, :2] == 1.0).all()
     assert (near[1][:, 2:-2, 2:-2, 0:2] == 10.0).all() and (near[1][:, 0:2] == 2.0).all()
+
+
+def _composite_step(reflux_on):
+    """Coarse 16^3 periodic level and one fine patch (refinement 2) over the coarse box
+    [4, 12)^3, stepped once on the coarse level and twice on the fine one (ghosts prolonged from
+    the coarse level at t and, linearly in time, at t + dt/2), then refluxed and averaged down."""
+    import oracle
+    import workloads
+    Uc = workloads.turbulent_state((16, 16, 16), seed=31, mach=2.0, sedov=False).numpy()
+    dxc = 1.0 / 16
+    cfg = oracle.config()
+    dtc = 0.5 * oracle.cfl_periodic(Uc, dxc, cfg)
+    oc, nc = (4, 4, 4), (8, 8, 8)
+    ofine = tuple(2 * o for o in oc)
+    Ucg = workloads.ghosted_from_periodic(torch_tensor(Uc), oc, nc).numpy()
+    Rc = dtc * oracle.patch_boundary_fluxes(Ucg, dxc, dtc, cfg)
+    Uc1 = oracle.step_periodic(Uc, dxc, dtc, cfg)
+    fine_level = amr.prolong_box(Uc)
+    Uf = fine_level[:, 8:24, 8:24, 8:24]
+    dxf, dtf = dxc / 2, dtc / 2
+    Rf = np.zeros_like(Rc, shape=(5, 2 * 3 * 16 * 16))
+    for sub, Ut in enumerate((Uc, 0.5 * (Uc + Uc1))):
+        Ug = np.zeros((5, 20, 20, 20))
+        Ug[:, 2:-2, 2:-2, 2:-2] = Uf
+        Ug = amr.fill_ghosts(Ut, Ug, ofine)
+        Rf = Rf + dtf * oracle.patch_boundary_fluxes(Ug, dxf, dtf, cfg)
+        Uf = oracle.step_patch(Ug, dxf, dtf, cfg)
+    U = amr.reflux(Uc1, oc, nc, Rc, Rf, dxc) if reflux_on else Uc1
+    return Uc, amr.average_down(U, Uf, oc)
+
+
+def torch_tensor(a):
+    import torch
+    return torch.as_tensor(a)
+
+
+def test_refluxed_composite_step_conserves_to_round_off():
+    U0, U1 = _composite_step(True)
+    scale = np.abs(U0).sum(axis=(1, 2, 3))
+    drift = np.abs(U1.sum(axis=(1, 2, 3)) - U0.sum(axis=(1, 2, 3))) / scale
+    assert drift.max() <= 1e-14, drift
+    _, U2 = _composite_step(False)  # without the correction the composite level leaks
+    leak = np.abs(U2.sum(axis=(1, 2, 3)) - U0.sum(axis=(1, 2, 3))) / scale
+    assert leak.max() > 1e-9, leak
