@@ -162,6 +162,37 @@ int hydro_fill_ghosts(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_pat
  * synchronises the stream first. */
 int hydro_exchange_ghosts(hydro_ctx* ctx, const hydro_patch* fine, const int* origins, int npatch, const int period[3]);
 
+/* Flux registers, refluxing and average-down: the coupling of two AMR levels (refinement ratio 2)
+ * that keeps the composite level conservative (Berger & Colella 1989; the paper's GPU ports compute
+ * every flux that updates a patch's cells, Sec. 4, and the coarse level's fluxes at a fine patch's
+ * boundary must then become the fine ones).  A register holds, per field, the time-integrated
+ * fluxes dt * F through the six boundary faces of a box of nx x ny x nz cells, in the storage type:
+ *     x-low [nz][ny], x-high [nz][ny], y-low [nz][nx], y-high [nz][nx], z-low [ny][nx], z-high [ny][nx]
+ * (5 x 2 (ny nz + nx nz + nx ny) elements; device memory owned by the caller).  The fluxes are the
+ * ones hydro_step applies there for the same state and dt: recovery, limited slopes and predictor
+ * of the two adjacent cells, floored face states, HLLC.
+ *   hydro_patch_fluxes: the boxes are the interiors of ghosted patches (ng == 2) with time steps
+ *       dt_dev[p]; registers[p] receives dt * F (accumulate == 0) or adds it (accumulate != 0: the
+ *       integral over a fine patch's substeps).
+ *   hydro_level_fluxes: the boxes (host arrays box_origins, box_dims [nbox][3] of int, x y z) of a
+ *       periodic level (ng == 0), all with time step dt_dev[0].
+ *   hydro_reflux: after the coarse step, each coarse cell outside box b across one of its faces gets
+ *       s/dx (Rc - mean of the four fine faces' Rf), s = +1 below the box, -1 above; Rc =
+ *       coarse_registers[b] (the box's coarse register), Rf = fine_registers[b] (the register of
+ *       the fine patch covering it, box sizes doubled).  Boxes must not overlap; the six face kinds
+ *       are applied in turn, so the result is deterministic.
+ *   hydro_average_down: the coarse cells under each fine patch's interior (fine origin and sizes
+ *       even) become the mean of their eight children.
+ * Each call uploads its descriptors and synchronises the stream first. */
+int hydro_patch_fluxes(hydro_ctx* ctx, const hydro_patch* patches, int npatch, const double* dt_dev,
+                       void* const* registers, int accumulate);
+int hydro_level_fluxes(hydro_ctx* ctx, const hydro_patch* level, const int* box_origins, const int* box_dims, int nbox,
+                       const double* dt_dev, void* const* registers, int accumulate);
+int hydro_reflux(hydro_ctx* ctx, const hydro_patch* coarse, const int* box_origins, const int* box_dims, int nbox,
+                 void* const* coarse_registers, void* const* fine_registers);
+int hydro_average_down(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
+                       int npatch);
+
 /* Oct groups read in place from a periodic level grid instead of a gathered buffer (the paper's
  * Ramses GPU procedure gathers each oct's neighbourhood into an N_v x 6^3 buffer first, Sec. 3;
  * here each group's 6^3 stencil is read from the level with periodic wrap as it is needed).

@@ -38,7 +38,8 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level", "hydro_fill_ghosts", "hydro_exchange_ghosts",
+           "hydro_step_octs_level", "hydro_fill_ghosts", "hydro_exchange_ghosts", "hydro_patch_fluxes",
+           "hydro_level_fluxes", "hydro_reflux", "hydro_average_down",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
            "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
@@ -85,6 +86,11 @@ def lib():
         L.hydro_step_octs_level.argtypes = [vp, PP, vp, ll, vp * 5, vp]
         L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
         L.hydro_exchange_ghosts.argtypes = [vp, PP, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ctypes.c_int)]
+        IP = ctypes.POINTER(ctypes.c_int)
+        L.hydro_patch_fluxes.argtypes = [vp, PP, i, vp, ctypes.POINTER(vp), i]
+        L.hydro_level_fluxes.argtypes = [vp, PP, IP, IP, i, vp, ctypes.POINTER(vp), i]
+        L.hydro_reflux.argtypes = [vp, PP, IP, IP, i, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.hydro_average_down.argtypes = [vp, PP, PP, IP, i]
         L.hydro_adjoint_step.argtypes = [vp, PP, vp, PP, PP, i]
         L.hydro_prim_to_cons.argtypes = [vp, PP, PP, i]
         L.hydro_prim_to_cons_adjoint.argtypes = [vp, PP, PP, PP, i]
@@ -254,6 +260,52 @@ def hydro_exchange_ghosts(ctx, fine, origins, period):
         raise ValueError("one (x, y, z) origin per patch")
     per = (ctypes.c_int * 3)(*[int(v) for v in period])
     _check(lib().hydro_exchange_ghosts(ctx.handle, f, o, n, per), "hydro_exchange_ghosts")
+
+
+def register_size(nx, ny, nz):
+    """Elements per field of a flux register of an nx x ny x nz box."""
+    return 2 * (ny * nz + nx * nz + nx * ny)
+
+
+def _ints(rows):
+    flat = [int(v) for r in rows for v in r]
+    return (ctypes.c_int * len(flat))(*flat)
+
+
+def _ptrs(tensors):
+    return (ctypes.c_void_p * len(tensors))(*[_ptr(t) for t in tensors])
+
+
+def hydro_patch_fluxes(ctx, patches, dt, registers, accumulate=False):
+    """registers[p]: CUDA tensor of 5 * register_size(...) elements of the storage type."""
+    a, n = _parray(patches)
+    if len(registers) != n:
+        raise ValueError("one register per patch")
+    _check(lib().hydro_patch_fluxes(ctx.handle, a, n, _ptr(dt), _ptrs(registers), int(bool(accumulate))),
+           "hydro_patch_fluxes")
+
+
+def hydro_level_fluxes(ctx, level, box_origins, box_dims, dt, registers, accumulate=False):
+    n = len(box_origins)
+    if len(box_dims) != n or len(registers) != n:
+        raise ValueError("one origin, size and register per box")
+    _check(lib().hydro_level_fluxes(ctx.handle, ctypes.byref(level.c), _ints(box_origins), _ints(box_dims), n,
+                                    _ptr(dt), _ptrs(registers), int(bool(accumulate))), "hydro_level_fluxes")
+
+
+def hydro_reflux(ctx, coarse, box_origins, box_dims, coarse_registers, fine_registers):
+    n = len(box_origins)
+    if len(box_dims) != n or len(coarse_registers) != n or len(fine_registers) != n:
+        raise ValueError("one origin, size and pair of registers per box")
+    _check(lib().hydro_reflux(ctx.handle, ctypes.byref(coarse.c), _ints(box_origins), _ints(box_dims), n,
+                              _ptrs(coarse_registers), _ptrs(fine_registers)), "hydro_reflux")
+
+
+def hydro_average_down(ctx, coarse, fine, origins):
+    f, n = _parray(fine)
+    if len(origins) != n:
+        raise ValueError("one origin per patch")
+    _check(lib().hydro_average_down(ctx.handle, ctypes.byref(coarse.c), f, _ints(origins), n), "hydro_average_down")
 
 
 def hydro_step_octs_level(ctx, level, origins, out, dt):

@@ -120,6 +120,114 @@ cudaError_t launch_copy_boxes(int elem_size, const HostGhostPatch* d_patches, co
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ refluxing and average-down
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// Faces of one kind (t = 2d + side: d the normal axis, side 0 the box's lower face) of every box:
+// the coarse cell outside the box across the face gets s/dx (Rc - mean of the 4 fine faces' Rf),
+// s = +1 on the lower side, -1 on the upper.  Boxes of a level do not overlap, so the cells one
+// launch writes are distinct; the six kinds run in turn, so the result is deterministic.  The
+// products and sums are kept unfused (explicitly rounded) in the order written.
+template <class S>
+__global__ void __launch_bounds__(256) k_reflux(const HostRefluxBox* boxes, const int2* blocks, int t, HostPatchIO coarse) {
+  const int2 b = blocks[blockIdx.x];
+  const HostRefluxBox B = boxes[b.x];
+  const int d = t >> 1, side = t & 1;
+  const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;  // the face's (col, row) axes: x faces [k][j], y [k][i], z [j][i]
+  const int ncol = B.n[a1], nrow = B.n[a2];
+  const int f = b.y * 256 + threadIdx.x;
+  if (f >= ncol * nrow) return;
+  const int row = f / ncol, col = f - row * ncol;
+  // register offsets: x-low, x-high [nz][ny]; y-low, y-high [nz][nx]; z-low, z-high [ny][nx]
+  const long long nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const long long base_c[3] = {0, 2 * ny * nz, 2 * ny * nz + 2 * nx * nz};
+  const long long size_c[3] = {ny * nz, nx * nz, nx * ny};
+  const long long RC = 2 * (ny * nz + nx * nz + nx * ny), RF = 4 * RC;
+  const long long fcol = 2 * ncol;
+  const long long base_f[3] = {0, 8 * ny * nz, 8 * ny * nz + 8 * nx * nz};
+  const long long size_f[3] = {4 * ny * nz, 4 * nx * nz, 4 * nx * ny};
+  const long long ic = base_c[d] + side * size_c[d] + (long long)row * ncol + col;
+  const long long if0 = base_f[d] + side * size_f[d] + (long long)(2 * row) * fcol + 2 * col;
+  int cell[3];
+  cell[a1] = B.o[a1] + col;
+  cell[a2] = B.o[a2] + row;
+  cell[d] = side ? B.o[d] + B.n[d] : B.o[d] - 1;
+  const int N[3] = {coarse.nx, coarse.ny, coarse.nz};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    cell[e] %= N[e];
+    cell[e] += cell[e] < 0 ? N[e] : 0;
+  }
+  const long long a = (long long)cell[2] * coarse.isz + (long long)cell[1] * coarse.isy + cell[0];
+  const S sdx = (S)((side ? -1.0 : 1.0) / B.dx);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const S* Rc = static_cast<const S*>(B.rc) + v * RC;
+    const S* Rf = static_cast<const S*>(B.rf) + v * RF;
+    const S p = Rf[if0], q = Rf[if0 + fcol], r = Rf[if0 + 1], u = Rf[if0 + fcol + 1];
+    const S avg = mul_rn(S(0.25), add_rn(add_rn(add_rn(p, q), r), u));
+    S* U = static_cast<S*>(coarse.out[v]);
+    U[a] = add_rn(U[a], mul_rn(sdx, add_rn(Rc[ic], -avg)));
+  }
+}
+
+// Coarse cells under a fine patch's interior (origin even, sizes even) <- mean of their children.
+template <class S>
+__global__ void __launch_bounds__(256) k_average_down(const HostGhostPatch* patches, const int2* blocks,
+                                                      HostPatchIO coarse) {
+  const int2 b = blocks[blockIdx.x];
+  const HostGhostPatch P = patches[b.x];
+  const int mx = P.nx / 2, my = P.ny / 2, mz = P.nz / 2;
+  const int c = b.y * 256 + threadIdx.x;
+  if (c >= mx * my * mz) return;
+  const int cz = c / (mx * my), r = c - cz * mx * my, cy = r / mx, cx = r - cy * mx;
+  int g[3] = {P.ox / 2 + cx, P.oy / 2 + cy, P.oz / 2 + cz};
+  const int N[3] = {coarse.nx, coarse.ny, coarse.nz};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    g[e] %= N[e];
+    g[e] += g[e] < 0 ? N[e] : 0;
+  }
+  const long long a = (long long)g[2] * coarse.isz + (long long)g[1] * coarse.isy + g[0];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const S* F = static_cast<const S*>(P.U[v]);
+    S sum = S(0);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int x = 2 * cx + (h & 1) + 2, y = 2 * cy + ((h >> 1) & 1) + 2, z = 2 * cz + (h >> 2) + 2;
+      sum = add_rn(sum, F[(long long)z * P.sz + (long long)y * P.sy + x]);
+    }
+    static_cast<S*>(coarse.out[v])[a] = mul_rn(S(0.125), sum);
+  }
+}
+
+cudaError_t launch_reflux(int elem_size, const HostRefluxBox* d_boxes, const int2* const d_blocks[6],
+                          const int nblocks[6], const HostPatchIO& coarse, cudaStream_t s) {
+  for (int t = 0; t < 6; ++t) {
+    if (nblocks[t] == 0) continue;
+    if (elem_size == 4)
+      k_reflux<float><<<nblocks[t], 256, 0, s>>>(d_boxes, d_blocks[t], t, coarse);
+    else
+      k_reflux<double><<<nblocks[t], 256, 0, s>>>(d_boxes, d_blocks[t], t, coarse);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_average_down(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
+                                const HostPatchIO& coarse, cudaStream_t s) {
+  if (elem_size == 4)
+    k_average_down<float><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse);
+  else
+    k_average_down<double><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
                                const HostPatchIO& coarse, cudaStream_t s) {
   if (elem_size == 4)

@@ -84,6 +84,9 @@ struct hydro_ctx {
   hydro::HostCopyTask* d_tasks = nullptr;
   size_t tasks_cap = 0;
   int ntasks = 0;
+  // flux registers, refluxing, average-down: descriptors and block tables of the last call
+  char* d_aux = nullptr;
+  size_t aux_cap = 0;
   long long launches = 0;
 };
 
@@ -232,6 +235,49 @@ int step_one_uniform(hydro_ctx* c, const hydro_patch& in, const hydro_patch& out
   return cuda_status(e);
 }
 
+// Uploads host bytes to the context's descriptor buffer (after the stream has drained: the previous
+// call's kernels may still read it); returns the device address or nullptr.
+char* upload_aux(hydro_ctx* c, const std::vector<char>& bytes) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return nullptr;
+  if (c->aux_cap < bytes.size()) {
+    cudaFree(c->d_aux);
+    c->d_aux = nullptr;
+    c->aux_cap = 0;
+    if (cudaMalloc(&c->d_aux, bytes.size()) != cudaSuccess) return nullptr;
+    c->aux_cap = bytes.size();
+  }
+  if (!bytes.empty() && cudaMemcpy(c->d_aux, bytes.data(), bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return nullptr;
+  return c->d_aux;
+}
+template <class T>
+size_t append(std::vector<char>& bytes, const T* p, size_t n) {
+  const size_t off = (bytes.size() + 255) / 256 * 256;
+  bytes.resize(off + n * sizeof(T));
+  if (n) std::memcpy(bytes.data() + off, p, n * sizeof(T));
+  return off;
+}
+
+int box_fluxes(hydro_ctx* c, const std::vector<hydro::HostBoxFluxes>& boxes, const double* dt_dev,
+                      int accumulate) {
+  std::vector<int2> blocks;
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const long long nx = boxes[b].n[0], ny = boxes[b].n[1], nz = boxes[b].n[2];
+    const long long faces = 2 * (ny * nz + nx * nz + nx * ny);
+    for (long long k = 0; k * 256 < faces; ++k) blocks.push_back(make_int2((int)b, (int)k));
+  }
+  if (blocks.size() > 0x7fffffff) return HYDRO_ERR_ARG;
+  std::vector<char> bytes;
+  const size_t ob = append(bytes, boxes.data(), boxes.size());
+  const size_t ok = append(bytes, blocks.data(), blocks.size());
+  char* d = upload_aux(c, bytes);
+  if (!d) return HYDRO_ERR_CUDA;
+  c->launches += 1;
+  return cuda_status(c->ops->box_fluxes(reinterpret_cast<const hydro::HostBoxFluxes*>(d + ob),
+                                        reinterpret_cast<const int2*>(d + ok), (int)blocks.size(), c->prm, dt_dev,
+                                        accumulate, c->stream));
+}
+
 }  // namespace
 
 extern "C" {
@@ -306,6 +352,7 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_ghost_blocks);
   cudaFree(c->d_xchg);
   cudaFree(c->d_tasks);
+  cudaFree(c->d_aux);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
@@ -645,6 +692,123 @@ static std::vector<hydro::HostCopyTask> exchange_tasks(const std::vector<hydro::
     }
   }
   return tasks;
+}
+
+int hydro_patch_fluxes(hydro_ctx* c, const hydro_patch* patches, int npatch, const double* dt_dev,
+                       void* const* registers, int accumulate) {
+  if (!c || !patches || npatch < 1 || !dt_dev || !registers) return HYDRO_ERR_ARG;
+  std::vector<hydro::HostBoxFluxes> boxes((size_t)npatch);
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_patch& P = patches[i];
+    if (!valid_patch(c, P) || P.ng != 2 || !registers[i]) return HYDRO_ERR_ARG;
+    hydro::HostBoxFluxes& b = boxes[i];
+    for (int v = 0; v < 5; ++v) b.U[v] = P.U[v];
+    b.reg = registers[i];
+    b.n[0] = P.nx; b.n[1] = P.ny; b.n[2] = P.nz;
+    for (int d = 0; d < 3; ++d) b.o[d] = b.N[d] = 0;
+    b.periodic = 0;
+    b.dt_index = i;
+    b.sy = P.sy; b.sz = P.sz;
+    b.dx = P.dx;
+  }
+  return box_fluxes(c, boxes, dt_dev, accumulate);
+}
+
+int hydro_level_fluxes(hydro_ctx* c, const hydro_patch* level, const int* box_origins, const int* box_dims, int nbox,
+                       const double* dt_dev, void* const* registers, int accumulate) {
+  if (!c || !level || !box_origins || !box_dims || nbox < 1 || !dt_dev || !registers) return HYDRO_ERR_ARG;
+  const hydro_patch& L = *level;
+  if (!valid_patch(c, L) || L.ng != 0) return HYDRO_ERR_ARG;
+  std::vector<hydro::HostBoxFluxes> boxes((size_t)nbox);
+  for (int i = 0; i < nbox; ++i) {
+    hydro::HostBoxFluxes& b = boxes[i];
+    for (int v = 0; v < 5; ++v) b.U[v] = L.U[v];
+    b.reg = registers[i];
+    for (int d = 0; d < 3; ++d) {
+      b.n[d] = box_dims[3 * i + d];
+      b.o[d] = box_origins[3 * i + d];
+    }
+    if (!b.reg || b.n[0] < 1 || b.n[1] < 1 || b.n[2] < 1) return HYDRO_ERR_ARG;
+    b.N[0] = L.nx; b.N[1] = L.ny; b.N[2] = L.nz;
+    b.periodic = 1;
+    b.dt_index = 0;
+    b.sy = L.sy; b.sz = L.sz;
+    b.dx = L.dx;
+  }
+  return box_fluxes(c, boxes, dt_dev, accumulate);
+}
+
+int hydro_reflux(hydro_ctx* c, const hydro_patch* coarse, const int* box_origins, const int* box_dims, int nbox,
+                 void* const* coarse_registers, void* const* fine_registers) {
+  if (!c || !coarse || !box_origins || !box_dims || nbox < 1 || !coarse_registers || !fine_registers)
+    return HYDRO_ERR_ARG;
+  const hydro_patch& C = *coarse;
+  if (!valid_patch(c, C) || C.ng != 0) return HYDRO_ERR_ARG;
+  std::vector<hydro::HostRefluxBox> boxes((size_t)nbox);
+  std::vector<int2> tables[6];
+  for (int i = 0; i < nbox; ++i) {
+    hydro::HostRefluxBox& b = boxes[i];
+    for (int d = 0; d < 3; ++d) {
+      b.o[d] = box_origins[3 * i + d];
+      b.n[d] = box_dims[3 * i + d];
+      if (b.n[d] < 1) return HYDRO_ERR_ARG;
+    }
+    b.rc = coarse_registers[i];
+    b.rf = fine_registers[i];
+    if (!b.rc || !b.rf) return HYDRO_ERR_ARG;
+    b.dx = C.dx;
+    const long long faces[3] = {(long long)b.n[1] * b.n[2], (long long)b.n[0] * b.n[2], (long long)b.n[0] * b.n[1]};
+    for (int t = 0; t < 6; ++t)
+      for (long long k = 0; k * 256 < faces[t >> 1]; ++k) tables[t].push_back(make_int2(i, (int)k));
+  }
+  std::vector<char> bytes;
+  const size_t ob = append(bytes, boxes.data(), boxes.size());
+  size_t ot[6];
+  int nb[6];
+  for (int t = 0; t < 6; ++t) {
+    if (tables[t].size() > 0x7fffffff) return HYDRO_ERR_ARG;
+    ot[t] = append(bytes, tables[t].data(), tables[t].size());
+    nb[t] = (int)tables[t].size();
+  }
+  char* d = upload_aux(c, bytes);
+  if (!d) return HYDRO_ERR_CUDA;
+  const int2* dt[6];
+  for (int t = 0; t < 6; ++t) dt[t] = reinterpret_cast<const int2*>(d + ot[t]);
+  c->launches += 6;
+  return cuda_status(hydro::launch_reflux(elem_size(c), reinterpret_cast<const hydro::HostRefluxBox*>(d + ob), dt, nb,
+                                          make_io(C, C), c->stream));
+}
+
+int hydro_average_down(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
+                       int npatch) {
+  if (!c || !coarse || !fine || !fine_origins || npatch < 1) return HYDRO_ERR_ARG;
+  const hydro_patch& C = *coarse;
+  if (!valid_patch(c, C) || C.ng != 0) return HYDRO_ERR_ARG;
+  std::vector<hydro::HostGhostPatch> set((size_t)npatch);
+  std::vector<int2> blocks;
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_patch& F = fine[i];
+    const int o[3] = {fine_origins[3 * i], fine_origins[3 * i + 1], fine_origins[3 * i + 2]};
+    if (!valid_patch(c, F) || F.ng != 2 || overlaps(c, C, F)) return HYDRO_ERR_ARG;
+    if ((F.nx | F.ny | F.nz | o[0] | o[1] | o[2]) & 1) return HYDRO_ERR_ARG;  // aligned with coarse cells
+    hydro::HostGhostPatch& g = set[i];
+    for (int v = 0; v < 5; ++v) g.U[v] = F.U[v];
+    g.nx = F.nx; g.ny = F.ny; g.nz = F.nz;
+    g.ox = o[0]; g.oy = o[1]; g.oz = o[2];
+    for (int d = 0; d < 3; ++d) g.clo[d] = g.cm[d] = 0;
+    g.sy = F.sy; g.sz = F.sz;
+    const long long cells = (long long)(F.nx / 2) * (F.ny / 2) * (F.nz / 2);
+    for (long long k = 0; k * 256 < cells; ++k) blocks.push_back(make_int2(i, (int)k));
+  }
+  std::vector<char> bytes;
+  const size_t op = append(bytes, set.data(), set.size());
+  const size_t obk = append(bytes, blocks.data(), blocks.size());
+  char* d = upload_aux(c, bytes);
+  if (!d) return HYDRO_ERR_CUDA;
+  c->launches += 1;
+  return cuda_status(hydro::launch_average_down(elem_size(c), reinterpret_cast<const hydro::HostGhostPatch*>(d + op),
+                                                reinterpret_cast<const int2*>(d + obk), (int)blocks.size(),
+                                                make_io(C, C), c->stream));
 }
 
 int hydro_exchange_ghosts(hydro_ctx* c, const hydro_patch* fine, const int* origins, int npatch, const int period[3]) {

@@ -30,6 +30,20 @@ constexpr int kTileX[kNumTiles] = {16, 32, 8, 32, 16};
 constexpr int kTileY[kNumTiles] = {16, 8, 8, 16, 16};
 constexpr int kTileMinBlocks[kNumTiles] = {0, 0, 0, 0, 1};
 
+// A box whose boundary-face fluxes go to a register: a ghosted patch's interior (periodic == 0:
+// cell (x, y, z) of the interior at (z+2) sz + (y+2) sy + x + 2) or the box at o of a periodic
+// level of N cells per axis (periodic == 1).
+struct HostBoxFluxes {
+  const void* U[5];
+  void* reg;         // 5 x 2 (ny nz + nx nz + nx ny) elements of the storage type
+  int n[3];          // box cells (x, y, z)
+  int o[3], N[3];    // periodic level: box origin and level size
+  int periodic;
+  int dt_index;      // dt_dev[dt_index] is this box's time step
+  long long sy, sz;
+  double dx;
+};
+
 struct KernelOps {
   // Uniform periodic grid (npatch == 1, gin == 0).
   cudaError_t (*step_uniform)(int tile, const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next,
@@ -57,6 +71,9 @@ struct KernelOps {
   cudaError_t (*p2c)(const HostPatchIO& W, void* const U[5], const Params& prm, cudaStream_t s);
   cudaError_t (*p2c_adjoint)(const HostPatchIO& W, const HostPatchIO& lamU, void* const lamW[5], const Params& prm,
                              cudaStream_t s);
+  // Boundary-face fluxes of boxes into registers (block b: faces 256 d_blocks[b].y ... of box d_blocks[b].x).
+  cudaError_t (*box_fluxes)(const HostBoxFluxes* d_boxes, const int2* d_blocks, int nblocks, const Params& prm,
+                            const double* dt, int accumulate, cudaStream_t s);
   int elem_size;  // bytes per stored element
   int launches_per_step;
 };
@@ -86,6 +103,19 @@ struct HostCopyTask {
 };
 cudaError_t launch_copy_boxes(int elem_size, const HostGhostPatch* d_patches, const HostCopyTask* d_tasks, int ntasks,
                               cudaStream_t s);
+
+// A coarse box covered by a fine patch, with its coarse and fine flux registers (the fine one for
+// the box refined by 2), for refluxing.
+struct HostRefluxBox {
+  int o[3], n[3];      // coarse box origin and cells (x, y, z)
+  const void* rc;      // 5 x 2 (ny nz + nx nz + nx ny)
+  const void* rf;      // 5 x 8 (ny nz + nx nz + nx ny)
+  double dx;           // coarse cell size
+};
+cudaError_t launch_reflux(int elem_size, const HostRefluxBox* d_boxes, const int2* const d_blocks[6],
+                          const int nblocks[6], const HostPatchIO& coarse, cudaStream_t s);
+cudaError_t launch_average_down(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
+                                const HostPatchIO& coarse, cudaStream_t s);
 
 // Coarse-to-fine ghost fill (ghosts.cu): block b takes coarse cells d_blocks[b].y .. +255 under
 // patch d_blocks[b].x.

@@ -477,13 +477,124 @@ cudaError_t launch_p2c_adjoint(const HostPatchIO& W, const HostPatchIO& lamU, vo
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ flux registers
+// Fluxes through the six boundary faces of boxes (AMR refluxing, Berger & Colella 1989: the
+// coarse level's fluxes at a fine patch's boundary are replaced by the fine ones): one thread per
+// face; both adjacent cells predicted from their own 3^3-minus-corners stencil exactly as the step
+// does (recovery, limited slopes, Hancock predictor), face states floored, HLLC.  A box is either
+// a ghosted patch's interior or a box of a periodic level.  The register (storage type, layout
+// x-low [nz][ny], x-high, y-low [nz][nx], y-high, z-low [ny][nx], z-high per field) receives
+// dt * F, added to its contents when accumulating (the time integral over a patch's substeps).
+template <class Pol>
+__device__ __forceinline__ void box_face(const HostBoxFluxes& B, long long f, int& d, int& i, int& j, int& k) {
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const long long X = (long long)ny * nz, Y = (long long)nx * nz;
+  if (f < 2 * X) {
+    d = 0;
+    const int side = (int)(f / X);
+    const long long r = f - side * X;
+    k = (int)(r / ny);
+    j = (int)(r - (long long)k * ny);
+    i = side ? nx - 1 : -1;
+  } else if (f < 2 * X + 2 * Y) {
+    d = 1;
+    const long long g = f - 2 * X;
+    const int side = (int)(g / Y);
+    const long long r = g - side * Y;
+    k = (int)(r / nx);
+    i = (int)(r - (long long)k * nx);
+    j = side ? ny - 1 : -1;
+  } else {
+    d = 2;
+    const long long g = f - 2 * X - 2 * Y;
+    const long long Z = (long long)nx * ny;
+    const int side = (int)(g / Z);
+    const long long r = g - side * Z;
+    j = (int)(r / nx);
+    i = (int)(r - (long long)j * nx);
+    k = side ? nz - 1 : -1;
+  }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256) k_box_fluxes(const HostBoxFluxes* boxes, const int2* blocks, Params prm,
+                                                    const double* dt_dev, int accumulate) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  const int2 b = blocks[blockIdx.x];
+  const HostBoxFluxes B = boxes[b.x];
+  const long long nface = 2LL * ((long long)B.n[1] * B.n[2] + (long long)B.n[0] * B.n[2] + (long long)B.n[0] * B.n[1]);
+  const long long f = (long long)b.y * 256 + threadIdx.x;
+  if (f >= nface) return;
+  int d, i, j, k;
+  box_face<Pol>(B, f, d, i, j, k);  // the face between cell (i, j, k) and its +d neighbour
+  const double dt = dt_dev[B.dt_index];
+  unsigned flags = 0;
+  // address of cell (x, y, z) in box coordinates (interior from 0; the stencil reaches -2 .. n+1)
+  auto addr = [&](int x, int y, int z) -> long long {
+    if (B.periodic) {
+      x += B.o[0]; y += B.o[1]; z += B.o[2];
+      x %= B.N[0]; y %= B.N[1]; z %= B.N[2];
+      x += x < 0 ? B.N[0] : 0; y += y < 0 ? B.N[1] : 0; z += z < 0 ? B.N[2] : 0;
+      return (long long)z * B.sz + (long long)y * B.sy + x;
+    }
+    return (long long)(z + 2) * B.sz + (long long)(y + 2) * B.sy + (x + 2);
+  };
+  auto q_at = [&](int x, int y, int z, R q[5]) {
+    const long long a = addr(x, y, z);
+    S U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(static_cast<const S*>(B.U[v]) + a);
+    Pol::recover(U, prm, q, flags);
+  };
+  const R hdt = (R)(0.5 * dt / B.dx);
+  R st[2][5];  // face states: left then right
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int x = i + (side && d == 0), y = j + (side && d == 1), z = k + (side && d == 2);
+    R c[5], m[5], p[5], dq[3][5], qh[5];
+    q_at(x, y, z, c);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      q_at(x - (e == 0), y - (e == 1), z - (e == 2), m);
+      q_at(x + (e == 0), y + (e == 1), z + (e == 2), p);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dq[e][v] = limited(c[v] - m[v], p[v] - c[v], prm.limiter);
+    }
+    hancock(c, dq[0], dq[1], dq[2], kc<R>(prm, K_GAMMA), hdt, qh);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const R sd = d == 0 ? dq[0][v] : (d == 1 ? dq[1][v] : dq[2][v]);
+      st[side][v] = side ? qh[v] - half_(sd) : qh[v] + half_(sd);
+    }
+  }
+  floor_state(st[0], kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+  floor_state(st[1], kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
+  R F[5];
+  hllc_dyn(d, st[0], st[1], kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), F);
+  const long long R5 = nface;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    S* reg = static_cast<S*>(B.reg) + v * R5 + f;
+    const S add = (S)(dt * (double)F[v]);
+    *reg = accumulate ? *reg + add : add;
+  }
+}
+
+template <class Pol>
+cudaError_t launch_box_fluxes(const HostBoxFluxes* d_boxes, const int2* d_blocks, int nblocks, const Params& prm,
+                              const double* dt, int accumulate, cudaStream_t s) {
+  k_box_fluxes<Pol><<<nblocks, 256, 0, s>>>(d_boxes, d_blocks, prm, dt, accumulate);
+  return cudaGetLastError();
+}
+
 template <class Pol>
 const KernelOps& make_ops() {
   static const KernelOps ops = {
       &launch_uniform<Pol>,      &launch_batched<Pol>,      &batched_blocks_per_sm<Pol>,
       &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_octs_level<Pol>,   &launch_adjoint<Pol>,
       &adjoint_scratch_bytes<Pol>, &launch_p2c<Pol>,        &launch_p2c_adjoint<Pol>,
-      (int)sizeof(typename Pol::S), 1};
+      &launch_box_fluxes<Pol>,   (int)sizeof(typename Pol::S), 1};
   return ops;
 }
 
