@@ -22,6 +22,7 @@ Under torchrun (N > 1) every rank runs the same workload on its own GPU (replica
 does not shard); value sums all ranks' cells over the slowest rank's time.
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -420,12 +421,20 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     gorig = [(int(rng.integers(0, 256)), int(rng.integers(0, 256)), int(rng.integers(0, 256))) for _ in descs]
     gfine = [hy.patch(keep[2 * i], 2, 1.0 / 256) for i in range(n)]
     gcoarse = hy.patch(coarse, 0, 1.0 / 128)
+    # arguments marshalled once: the 4096-patch ctypes array would cost the host more than the fill
+    gf_a, gn = hy._parray(gfine)
+    go_i, gc = hy._ints(gorig), ctypes.byref(gcoarse.c)
+
+    def fill():
+        if hy.lib().hydro_fill_ghosts(ctx.handle, gc, gf_a, go_i, gn) != hy.HYDRO_OK:
+            raise RuntimeError("hydro_fill_ghosts failed")
+
     for _ in range(warmup):
-        hy.hydro_fill_ghosts(ctx, gcoarse, gfine, gorig)
+        fill()
     torch.cuda.synchronize()
     t0.record(stream)
     for _ in range(steps):
-        hy.hydro_fill_ghosts(ctx, gcoarse, gfine, gorig)
+        fill()
     t1.record(stream)
     torch.cuda.synchronize()
     ms_g = t0.elapsed_time(t1) / steps
@@ -457,9 +466,12 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
 
 
 def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
-    """One AMR level step: a 256^3 fine level tiled by 16^3 patches of random edges (cuts at random
-    positions per axis), ghosts prolonged from the 128^3 coarse level, then exchanged between
-    siblings, then the batched mixed-precision step of all patches; mixed precision."""
+    """One two-level AMR cycle, mixed precision: a 256^3 fine level tiled by 16^3 patches of random
+    even edges (cuts at random even positions per axis) over a 128^3 coarse level.  Per cycle: the
+    coarse step with the flux registers of the coarse boxes under the patches; fine ghosts
+    prolonged from the coarse level and exchanged between siblings; the fine patches' registers
+    and their batched step; refluxing and average-down onto the coarse level (one fine substep per
+    coarse step here: the kernels' costs, not a time-refinement schedule)."""
     import numpy as np
     stream = torch.cuda.current_stream()
     ctx = hy.hydro_init(precision="mixed")
@@ -468,7 +480,7 @@ def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
     rng = np.random.default_rng(seed)
     axes = []
     for _ in range(3):
-        c = np.sort(rng.choice(np.arange(1, n), pieces - 1, replace=False))
+        c = 2 * np.sort(rng.choice(np.arange(1, n // 2), pieces - 1, replace=False))
         e = np.concatenate([[0], c, [n]])
         axes.append(list(zip(e[:-1].tolist(), np.diff(e).tolist())))
     ins, outs, keep, origins = [], [], [], []
@@ -486,42 +498,76 @@ def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
                 interior += nx * ny * nz
     del fine
     cp = hy.patch(coarse, 0, 2.0 / n)
+    coarse2 = torch.empty_like(coarse)
+    cp2 = hy.patch(coarse2, 0, 2.0 / n)
     per = (n, n, n)
+    boxes_o = [(o[0] // 2, o[1] // 2, o[2] // 2) for o in origins]
+    boxes_n = [(p.c.nx // 2, p.c.ny // 2, p.c.nz // 2) for p in ins]
+    rc_regs = [torch.zeros(5 * hy.register_size(*b), dtype=torch.float64, device="cuda") for b in boxes_n]
+    rf_regs = [torch.zeros(5 * hy.register_size(p.c.nx, p.c.ny, p.c.nz), dtype=torch.float64, device="cuda")
+               for p in ins]
     dt = torch.empty(len(ins), dtype=torch.float64, device="cuda")
+    dtc = torch.empty(1, dtype=torch.float64, device="cuda")
     hy.hydro_fill_ghosts(ctx, cp, ins, origins)
     hy.hydro_exchange_ghosts(ctx, ins, origins, per)
     hy.hydro_cfl_dt(ctx, ins, dt)
+    hy.hydro_cfl_dt(ctx, cp, dtc)
     if TUNING == "auto":
         hy.hydro_autotune(ctx, ins, outs, dt)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    names = ["coarse_registers", "coarse_step", "fill_from_coarse", "exchange", "fine_registers", "fine_step",
+             "reflux_and_average_down"]
+    # the C calls with their arguments marshalled once (the 4096-patch ctypes arrays would
+    # otherwise cost the host milliseconds per call, and the GPU would wait for them)
+    L, H = hy.lib(), ctx.handle
+    cpc, cp2c = ctypes.byref(cp.c), ctypes.byref(cp2.c)
+    ins_a, npat = hy._parray(ins)
+    outs_a, _ = hy._parray(outs)
+    org_i, bo_i, bn_i = hy._ints(origins), hy._ints(boxes_o), hy._ints(boxes_n)
+    rc_p, rf_p = hy._ptrs(rc_regs), hy._ptrs(rf_regs)
+    per_i = (ctypes.c_int * 3)(*per)
+    dt_p, dtc_p = dt.data_ptr(), dtc.data_ptr()
+
+    def chk(rc):
+        if rc != hy.HYDRO_OK:
+            raise RuntimeError("AMR cycle call failed: %d" % rc)
 
     def one():
         ev[0].record(stream)
-        hy.hydro_fill_ghosts(ctx, cp, ins, origins)
+        chk(L.hydro_level_fluxes(H, cpc, bo_i, bn_i, npat, dtc_p, rc_p, 0))
         ev[1].record(stream)
-        hy.hydro_exchange_ghosts(ctx, ins, origins, per)
+        chk(L.hydro_step(H, cpc, cp2c, 1, dtc_p, None))
         ev[2].record(stream)
-        hy.hydro_step(ctx, ins, outs, dt)
+        chk(L.hydro_fill_ghosts(H, cpc, ins_a, org_i, npat))
         ev[3].record(stream)
+        chk(L.hydro_exchange_ghosts(H, ins_a, org_i, npat, per_i))
+        ev[4].record(stream)
+        chk(L.hydro_patch_fluxes(H, ins_a, npat, dt_p, rf_p, 0))
+        ev[5].record(stream)
+        chk(L.hydro_step(H, ins_a, outs_a, npat, dt_p, None))
+        ev[6].record(stream)
+        chk(L.hydro_reflux(H, cp2c, bo_i, bn_i, npat, rc_p, rf_p))
+        chk(L.hydro_average_down(H, cp2c, outs_a, org_i, npat))
+        ev[7].record(stream)
 
     for _ in range(warmup):
         one()
     torch.cuda.synchronize()
-    parts = np.zeros(3)
+    parts = np.zeros(7)
     for _ in range(steps):
         one()
         torch.cuda.synchronize()
-        parts += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+        parts += [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
     parts /= steps
     ghosts = sum(t[0].numel() for t in keep[0::2]) - interior
     rc, bits = hy.hydro_get_error(ctx)
     t, z = hy.hydro_get_tuning(ctx)
-    out = {"patches": len(ins), "interior_cells": interior, "ghost_cells": ghosts,
-           "ms_fill_from_coarse": parts[0], "ms_exchange": parts[1], "ms_step": parts[2],
-           "mcell_updates_per_s": interior / (parts.sum() / 1e3) / 1e6,
-           "step_only_mcell_updates_per_s": interior / (parts[2] / 1e3) / 1e6,
+    out = {"patches": len(ins), "fine_interior_cells": interior, "coarse_cells": (n // 2) ** 3,
+           "ghost_cells": ghosts, "ms": {k: round(v, 4) for k, v in zip(names, parts)},
+           "mcell_updates_per_s": (interior + (n // 2) ** 3) / (parts.sum() / 1e3) / 1e6,
+           "fine_step_only_mcell_updates_per_s": interior / (parts[5] / 1e3) / 1e6,
            "tuning": {"tile": TILE_NAMES[t], "zchunk": z}, "error_bits": bits}
-    del keep, coarse
+    del keep, coarse, coarse2
     hy.hydro_finalize(ctx)
     torch.cuda.empty_cache()
     return out

@@ -174,8 +174,9 @@ int hydro_exchange_ghosts(hydro_ctx* ctx, const hydro_patch* fine, const int* or
  *   hydro_patch_fluxes: the boxes are the interiors of ghosted patches (ng == 2) with time steps
  *       dt_dev[p]; registers[p] receives dt * F (accumulate == 0) or adds it (accumulate != 0: the
  *       integral over a fine patch's substeps).
- *   hydro_level_fluxes: the boxes (host arrays box_origins, box_dims [nbox][3] of int, x y z) of a
- *       periodic level (ng == 0), all with time step dt_dev[0].
+ *   hydro_level_fluxes: the boxes (host arrays box_origins, box_dims [nbox][3] of int, x y z;
+ *       origins wrapped by the level's size, sizes no larger than it) of a periodic level (ng == 0),
+ *       all with time step dt_dev[0].
  *   hydro_reflux: after the coarse step, each coarse cell outside box b across one of its faces gets
  *       s/dx (Rc - mean of the four fine faces' Rf), s = +1 below the box, -1 above; Rc =
  *       coarse_registers[b] (the box's coarse register), Rf = fine_registers[b] (the register of
@@ -183,7 +184,8 @@ int hydro_exchange_ghosts(hydro_ctx* ctx, const hydro_patch* fine, const int* or
  *       are applied in turn, so the result is deterministic.
  *   hydro_average_down: the coarse cells under each fine patch's interior (fine origin and sizes
  *       even) become the mean of their eight children.
- * Each call uploads its descriptors and synchronises the stream first. */
+ * A call whose descriptors differ from the previous call of the same kind uploads them and
+ * synchronises the stream first. */
 int hydro_patch_fluxes(hydro_ctx* ctx, const hydro_patch* patches, int npatch, const double* dt_dev,
                        void* const* registers, int accumulate);
 int hydro_level_fluxes(hydro_ctx* ctx, const hydro_patch* level, const int* box_origins, const int* box_dims, int nbox,

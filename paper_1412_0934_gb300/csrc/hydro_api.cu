@@ -84,9 +84,12 @@ struct hydro_ctx {
   hydro::HostCopyTask* d_tasks = nullptr;
   size_t tasks_cap = 0;
   int ntasks = 0;
-  // flux registers, refluxing, average-down: descriptors and block tables of the last call
-  char* d_aux = nullptr;
-  size_t aux_cap = 0;
+  // flux registers (patch boxes, level boxes), refluxing, average-down: descriptors and block
+  // tables of the last call of each kind (reused without an upload when unchanged)
+  static constexpr int kAux = 4;
+  char* d_aux[kAux] = {nullptr, nullptr, nullptr, nullptr};
+  size_t aux_cap[kAux] = {0, 0, 0, 0};
+  std::vector<char> aux_last[kAux];
   long long launches = 0;
 };
 
@@ -235,20 +238,25 @@ int step_one_uniform(hydro_ctx* c, const hydro_patch& in, const hydro_patch& out
   return cuda_status(e);
 }
 
-// Uploads host bytes to the context's descriptor buffer (after the stream has drained: the previous
-// call's kernels may still read it); returns the device address or nullptr.
-char* upload_aux(hydro_ctx* c, const std::vector<char>& bytes) {
+// Device copy of host descriptor bytes for a call kind: the buffer of the last call of that kind
+// when the bytes are unchanged, else a fresh upload (after the stream has drained: earlier
+// kernels may still read the buffer).  Returns the device address or nullptr.
+char* upload_aux(hydro_ctx* c, int kind, const std::vector<char>& bytes) {
+  if (c->d_aux[kind] && bytes == c->aux_last[kind]) return c->d_aux[kind];
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return nullptr;
-  if (c->aux_cap < bytes.size()) {
-    cudaFree(c->d_aux);
-    c->d_aux = nullptr;
-    c->aux_cap = 0;
-    if (cudaMalloc(&c->d_aux, bytes.size()) != cudaSuccess) return nullptr;
-    c->aux_cap = bytes.size();
+  if (c->aux_cap[kind] < bytes.size() || !c->d_aux[kind]) {
+    cudaFree(c->d_aux[kind]);
+    c->d_aux[kind] = nullptr;
+    c->aux_cap[kind] = 0;
+    c->aux_last[kind].clear();
+    const size_t n = std::max<size_t>(bytes.size(), 256);
+    if (cudaMalloc(&c->d_aux[kind], n) != cudaSuccess) return nullptr;
+    c->aux_cap[kind] = n;
   }
-  if (!bytes.empty() && cudaMemcpy(c->d_aux, bytes.data(), bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (!bytes.empty() && cudaMemcpy(c->d_aux[kind], bytes.data(), bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return nullptr;
-  return c->d_aux;
+  c->aux_last[kind] = bytes;
+  return c->d_aux[kind];
 }
 template <class T>
 size_t append(std::vector<char>& bytes, const T* p, size_t n) {
@@ -258,8 +266,8 @@ size_t append(std::vector<char>& bytes, const T* p, size_t n) {
   return off;
 }
 
-int box_fluxes(hydro_ctx* c, const std::vector<hydro::HostBoxFluxes>& boxes, const double* dt_dev,
-                      int accumulate) {
+int box_fluxes(hydro_ctx* c, int kind, const std::vector<hydro::HostBoxFluxes>& boxes, const double* dt_dev,
+               int accumulate) {
   std::vector<int2> blocks;
   for (size_t b = 0; b < boxes.size(); ++b) {
     const long long nx = boxes[b].n[0], ny = boxes[b].n[1], nz = boxes[b].n[2];
@@ -270,7 +278,7 @@ int box_fluxes(hydro_ctx* c, const std::vector<hydro::HostBoxFluxes>& boxes, con
   std::vector<char> bytes;
   const size_t ob = append(bytes, boxes.data(), boxes.size());
   const size_t ok = append(bytes, blocks.data(), blocks.size());
-  char* d = upload_aux(c, bytes);
+  char* d = upload_aux(c, kind, bytes);
   if (!d) return HYDRO_ERR_CUDA;
   c->launches += 1;
   return cuda_status(c->ops->box_fluxes(reinterpret_cast<const hydro::HostBoxFluxes*>(d + ob),
@@ -352,7 +360,7 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_ghost_blocks);
   cudaFree(c->d_xchg);
   cudaFree(c->d_tasks);
-  cudaFree(c->d_aux);
+  for (int k = 0; k < hydro_ctx::kAux; ++k) cudaFree(c->d_aux[k]);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
@@ -711,7 +719,7 @@ int hydro_patch_fluxes(hydro_ctx* c, const hydro_patch* patches, int npatch, con
     b.sy = P.sy; b.sz = P.sz;
     b.dx = P.dx;
   }
-  return box_fluxes(c, boxes, dt_dev, accumulate);
+  return box_fluxes(c, 0, boxes, dt_dev, accumulate);
 }
 
 int hydro_level_fluxes(hydro_ctx* c, const hydro_patch* level, const int* box_origins, const int* box_dims, int nbox,
@@ -724,18 +732,19 @@ int hydro_level_fluxes(hydro_ctx* c, const hydro_patch* level, const int* box_or
     hydro::HostBoxFluxes& b = boxes[i];
     for (int v = 0; v < 5; ++v) b.U[v] = L.U[v];
     b.reg = registers[i];
+    b.N[0] = L.nx; b.N[1] = L.ny; b.N[2] = L.nz;
     for (int d = 0; d < 3; ++d) {
       b.n[d] = box_dims[3 * i + d];
-      b.o[d] = box_origins[3 * i + d];
+      b.o[d] = ((box_origins[3 * i + d] % b.N[d]) + b.N[d]) % b.N[d];  // wrapped into [0, N)
+      if (b.n[d] < 1 || b.n[d] > b.N[d]) return HYDRO_ERR_ARG;
     }
-    if (!b.reg || b.n[0] < 1 || b.n[1] < 1 || b.n[2] < 1) return HYDRO_ERR_ARG;
-    b.N[0] = L.nx; b.N[1] = L.ny; b.N[2] = L.nz;
+    if (!b.reg) return HYDRO_ERR_ARG;
     b.periodic = 1;
     b.dt_index = 0;
     b.sy = L.sy; b.sz = L.sz;
     b.dx = L.dx;
   }
-  return box_fluxes(c, boxes, dt_dev, accumulate);
+  return box_fluxes(c, 1, boxes, dt_dev, accumulate);
 }
 
 int hydro_reflux(hydro_ctx* c, const hydro_patch* coarse, const int* box_origins, const int* box_dims, int nbox,
@@ -770,7 +779,7 @@ int hydro_reflux(hydro_ctx* c, const hydro_patch* coarse, const int* box_origins
     ot[t] = append(bytes, tables[t].data(), tables[t].size());
     nb[t] = (int)tables[t].size();
   }
-  char* d = upload_aux(c, bytes);
+  char* d = upload_aux(c, 2, bytes);
   if (!d) return HYDRO_ERR_CUDA;
   const int2* dt[6];
   for (int t = 0; t < 6; ++t) dt[t] = reinterpret_cast<const int2*>(d + ot[t]);
@@ -803,7 +812,7 @@ int hydro_average_down(hydro_ctx* c, const hydro_patch* coarse, const hydro_patc
   std::vector<char> bytes;
   const size_t op = append(bytes, set.data(), set.size());
   const size_t obk = append(bytes, blocks.data(), blocks.size());
-  char* d = upload_aux(c, bytes);
+  char* d = upload_aux(c, 3, bytes);
   if (!d) return HYDRO_ERR_CUDA;
   c->launches += 1;
   return cuda_status(hydro::launch_average_down(elem_size(c), reinterpret_cast<const hydro::HostGhostPatch*>(d + op),

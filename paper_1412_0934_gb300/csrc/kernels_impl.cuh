@@ -532,10 +532,15 @@ __global__ void __launch_bounds__(256) k_box_fluxes(const HostBoxFluxes* boxes, 
   unsigned flags = 0;
   // address of cell (x, y, z) in box coordinates (interior from 0; the stencil reaches -2 .. n+1)
   auto addr = [&](int x, int y, int z) -> long long {
-    if (B.periodic) {
-      x += B.o[0]; y += B.o[1]; z += B.o[2];
-      x %= B.N[0]; y %= B.N[1]; z %= B.N[2];
-      x += x < 0 ? B.N[0] : 0; y += y < 0 ? B.N[1] : 0; z += z < 0 ? B.N[2] : 0;
+    if (B.periodic) {  // origin in [0, N), box no larger than N: o + x in [-2, 2N + 2)
+      auto wrap = [](int v, int n) {
+        v += v < 0 ? n : 0;
+        v -= v >= n ? n : 0;
+        return v >= n ? v - n : v;
+      };
+      x = wrap(x + B.o[0], B.N[0]);
+      y = wrap(y + B.o[1], B.N[1]);
+      z = wrap(z + B.o[2], B.N[2]);
       return (long long)z * B.sz + (long long)y * B.sy + x;
     }
     return (long long)(z + 2) * B.sz + (long long)(y + 2) * B.sy + (x + 2);
