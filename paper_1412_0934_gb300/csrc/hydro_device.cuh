@@ -302,8 +302,8 @@ __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
   return (a - (s - bb)) + (b - bb);
 }
 
-// Conversions for the mixed policy without conversion instructions, which share GB300's narrow
-// FP64 pipe with the double arithmetic.
+// Conversions for the mixed and double-float policies without conversion instructions, which
+// share GB300's narrow FP64 pipe with the double arithmetic.
 // Exact float of an integer 0 <= n < 2^23: the bits of 2^23 + n read as a float, minus 2^23.
 __device__ __forceinline__ float small_uint_to_float(unsigned n) {
   return __uint_as_float(0x4B000000u | n) - 8388608.f;
@@ -313,12 +313,19 @@ __device__ __forceinline__ float small_uint_to_float(unsigned n) {
 // lo the remaining 29-bit integer rounded once to a float (its top 23 bits times 64 plus its low 6
 // bits, one FMA) and scaled by the power of two 2^(E-52), then one Fast2Sum.  Zero and |x|
 // outside [2^-74, 2^99) take the conversion instructions instead.
+// The rare cases out of line, so that the common path carries no conversion instruction (an
+// inlined branch this short would be predicated, and its conversions issued for every value).
+static __device__ __noinline__ void split_double_cvt(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+static __device__ __noinline__ double float_to_double_cvt(float f) { return (double)f; }
+
 __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
-  const unsigned ex = (xh >> 20) & 0x7FFu;
-  if (ex - 949u >= 173u) {
-    hi = (float)x;
-    lo = (float)(x - (double)hi);
+  const unsigned ex = (xh >> 20) & 0x7FFu;  // biased exponent, E = ex - 1023
+  if (__builtin_expect(ex - 949u >= 173u, 0)) {
+    split_double_cvt(x, hi, lo);
     return;
   }
   const unsigned sign = xh & 0x80000000u;
@@ -334,7 +341,8 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
 __device__ __forceinline__ double float_to_double(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned e = (b >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (b & 0x7FFFFFFFu) == 0u ? __hiloint2double((int)(b & 0x80000000u), 0) : (double)f;
+  if (__builtin_expect(e == 0u || e == 0xFFu, 0))
+    return (b & 0x7FFFFFFFu) == 0u ? __hiloint2double((int)(b & 0x80000000u), 0) : float_to_double_cvt(f);
   return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
 }
 
@@ -479,15 +487,20 @@ struct PolMixed {
 struct PolDF {
   using S = double;
   using R = df;
-  // The same recovery as PolF64, in double-float from the double state.
+  // The same recovery as PolF64, in double-float from the double state (split into float pairs on
+  // the integer pipe, split_double).
   static __device__ __forceinline__ void recover(const double U[5], const Params& P, df q[5], unsigned& flags) {
-    df rho(U[0]);
+    df rho, mx, my, mz, E;
+    split_double(U[0], rho.h, rho.l);
+    split_double(U[1], mx.h, mx.l);
+    split_double(U[2], my.h, my.l);
+    split_double(U[3], mz.h, mz.l);
+    split_double(U[4], E.h, E.l);
     const df rf = kc<df>(P, K_RHOF);
     if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
     const df ir = rcp_(rho);
-    const df mx(U[1]), my(U[2]), mz(U[3]);
     const df kin = half_(((mx * mx + my * my) + mz * mz) * ir);
-    const df eint = df(U[4]) - kin;
+    const df eint = E - kin;
     if (cmp_neg(eint)) flags |= HYDRO_EBIT_P_FLOOR;
     df p = kc<df>(P, K_GM1) * eint;
     if (!(isfinite(p.h) && isfinite(rho.h))) flags |= HYDRO_EBIT_NONFINITE;
@@ -498,10 +511,11 @@ struct PolDF {
     q[3] = mz * ir;
     q[4] = p < pf ? pf : p;
   }
-  // U_old - dtdx * div with the double-float increment added to the double state in double.
+  // U_old - dtdx * div: the double-float increment made a double exactly (float_to_double) and
+  // subtracted from the double state in double.
   static __device__ __forceinline__ double update(double Uold, const df& dtdx, const df& div) {
     const df d = dtdx * div;
-    return (Uold - (double)d.h) - (double)d.l;
+    return Uold - (float_to_double(d.h) + float_to_double(d.l));
   }
   static __device__ __forceinline__ df speed(const double U[5], const Params& P, unsigned& flags);
 };
