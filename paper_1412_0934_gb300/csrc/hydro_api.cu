@@ -272,6 +272,7 @@ int box_fluxes(hydro_ctx* c, int kind, const std::vector<hydro::HostBoxFluxes>& 
   for (size_t b = 0; b < boxes.size(); ++b) {
     const long long nx = boxes[b].n[0], ny = boxes[b].n[1], nz = boxes[b].n[2];
     const long long faces = 2 * (ny * nz + nx * nz + nx * ny);
+    if (faces > 0x7fffffffLL) return HYDRO_ERR_ARG;
     for (long long k = 0; k * 256 < faces; ++k) blocks.push_back(make_int2((int)b, (int)k));
   }
   if (blocks.size() > 0x7fffffff) return HYDRO_ERR_ARG;

@@ -106,13 +106,16 @@ __global__ void __launch_bounds__(256) k_cfl(const PatchIO<typename Pol::S>* pat
   unsigned flags = 0;
   for (int pi = blockIdx.y; pi < npatch; pi += gridDim.y) {
     const PatchIO<S> P = patches ? patches[pi] : single;
-    const long long nxy = (long long)P.nx * P.ny, n = nxy * P.nz;
+    // cells by (row, x): rows = (z, y) pairs, one 32-bit division per row (64-bit integer division
+    // is a long sequence that runs partly on the FP64 pipe)
+    const int rows = P.ny * P.nz;
     R smax = 0;
-    for (long long c = (long long)blockIdx.x * 256 + threadIdx.x; c < n; c += (long long)gridDim.x * 256) {
-      const int k = (int)(c / nxy);
-      const long long r = c - (long long)k * nxy;
-      const int j = (int)(r / P.nx);
-      const int i = (int)(r - (long long)j * P.nx);
+    const int nxb = (P.nx + 31) / 32;  // 32-wide segments per row
+    for (long long s = (long long)blockIdx.x * 8 + (threadIdx.x >> 5); s < (long long)rows * nxb;
+         s += (long long)gridDim.x * 8) {
+      const int row = (int)(s / nxb), i = (int)(s - (long long)row * nxb) * 32 + (threadIdx.x & 31);
+      if (i >= P.nx) continue;
+      const int k = row / P.ny, j = row - k * P.ny;
       const long long a = (long long)(k + P.gin) * P.isz + (long long)(j + P.gin) * P.isy + (i + P.gin);
       S U[5];
 #pragma unroll
@@ -415,13 +418,26 @@ cudaError_t launch_octs_level(const HostPatchIO& level, const int* origins, void
 }
 
 // ------------------------------------------------------------------ primitive <-> conservative
+// Interior cell c -> (i, j, k), in 32-bit arithmetic when the patch has fewer than 2^31 cells (a
+// 64-bit integer division is a long sequence that runs partly on the FP64 pipe).
 template <class S>
-__device__ __forceinline__ long long cell_offset(const PatchIO<S>& P, long long c, bool out_side) {
+__device__ __forceinline__ void cell_ijk(const PatchIO<S>& P, long long c, int& i, int& j, int& k) {
   const long long nxy = (long long)P.nx * P.ny;
-  const int k = (int)(c / nxy);
-  const long long r = c - (long long)k * nxy;
-  const int j = (int)(r / P.nx);
-  const int i = (int)(r - (long long)j * P.nx);
+  if (nxy * P.nz <= 0x7fffffffLL) {
+    const int cc = (int)c, nxy32 = (int)nxy;
+    k = cc / nxy32;
+    const int r = cc - k * nxy32;
+    j = r / P.nx;
+    i = r - j * P.nx;
+  } else {
+    k = (int)(c / nxy);
+    const long long r = c - (long long)k * nxy;
+    j = (int)(r / P.nx);
+    i = (int)(r - (long long)j * P.nx);
+  }
+}
+template <class S>
+__device__ __forceinline__ long long cell_offset(const PatchIO<S>& P, int i, int j, int k, bool out_side) {
   const int g = out_side ? P.gout : P.gin;
   const long long sy = out_side ? P.osy : P.isy, sz = out_side ? P.osz : P.isz;
   return (long long)(k + g) * sz + (long long)(j + g) * sy + (i + g);
@@ -433,7 +449,9 @@ __global__ void k_p2c(PatchIO<S> P, double gamma) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   const S igm1 = (S)(1.0 / (gamma - 1.0));
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    const long long a = cell_offset(P, c, false), b = cell_offset(P, c, true);
+    int i, j, k;
+    cell_ijk(P, c, i, j, k);
+    const long long a = cell_offset(P, i, j, k, false), b = cell_offset(P, i, j, k, true);
     const S r = P.in[0][a], u = P.in[1][a], v = P.in[2][a], w = P.in[3][a], p = P.in[4][a];
     P.out[0][b] = r;
     P.out[1][b] = r * u;
@@ -449,7 +467,10 @@ __global__ void k_p2c_adjoint(PatchIO<S> P, PatchIO<S> L, double gamma) {
   const long long n = (long long)P.nx * P.ny * P.nz;
   const S igm1 = (S)(1.0 / (gamma - 1.0));
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-    const long long a = cell_offset(P, c, false), la = cell_offset(L, c, false), b = cell_offset(P, c, true);
+    int i, j, k;
+    cell_ijk(P, c, i, j, k);
+    const long long a = cell_offset(P, i, j, k, false), la = cell_offset(L, i, j, k, false),
+                    b = cell_offset(P, i, j, k, true);
     const S r = P.in[0][a], u = P.in[1][a], v = P.in[2][a], w = P.in[3][a];
     const S l0 = L.in[0][la], l1 = L.in[1][la], l2 = L.in[2][la], l3 = L.in[3][la], l4 = L.in[4][la];
     P.out[0][b] = l0 + u * l1 + v * l2 + w * l3 + S(0.5) * ((u * u + v * v) + w * w) * l4;
@@ -485,33 +506,27 @@ cudaError_t launch_p2c_adjoint(const HostPatchIO& W, const HostPatchIO& lamU, vo
 // a ghosted patch's interior or a box of a periodic level.  The register (storage type, layout
 // x-low [nz][ny], x-high, y-low [nz][nx], y-high, z-low [ny][nx], z-high per field) receives
 // dt * F, added to its contents when accumulating (the time integral over a patch's substeps).
-template <class Pol>
-__device__ __forceinline__ void box_face(const HostBoxFluxes& B, long long f, int& d, int& i, int& j, int& k) {
+// Face f of a box's register (32-bit arithmetic: a box has fewer than 2^31 boundary faces).
+__device__ __forceinline__ void box_face(const HostBoxFluxes& B, int f, int& d, int& i, int& j, int& k) {
   const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
-  const long long X = (long long)ny * nz, Y = (long long)nx * nz;
+  const int X = ny * nz, Y = nx * nz;
   if (f < 2 * X) {
     d = 0;
-    const int side = (int)(f / X);
-    const long long r = f - side * X;
-    k = (int)(r / ny);
-    j = (int)(r - (long long)k * ny);
+    const int side = f >= X, r = f - side * X;
+    k = r / ny;
+    j = r - k * ny;
     i = side ? nx - 1 : -1;
   } else if (f < 2 * X + 2 * Y) {
     d = 1;
-    const long long g = f - 2 * X;
-    const int side = (int)(g / Y);
-    const long long r = g - side * Y;
-    k = (int)(r / nx);
-    i = (int)(r - (long long)k * nx);
+    const int g = f - 2 * X, side = g >= Y, r = g - side * Y;
+    k = r / nx;
+    i = r - k * nx;
     j = side ? ny - 1 : -1;
   } else {
     d = 2;
-    const long long g = f - 2 * X - 2 * Y;
-    const long long Z = (long long)nx * ny;
-    const int side = (int)(g / Z);
-    const long long r = g - side * Z;
-    j = (int)(r / nx);
-    i = (int)(r - (long long)j * nx);
+    const int g = f - 2 * X - 2 * Y, Z = nx * ny, side = g >= Z, r = g - side * Z;
+    j = r / nx;
+    i = r - j * nx;
     k = side ? nz - 1 : -1;
   }
 }
@@ -523,11 +538,11 @@ __global__ void __launch_bounds__(256) k_box_fluxes(const HostBoxFluxes* boxes, 
   using R = typename Pol::R;
   const int2 b = blocks[blockIdx.x];
   const HostBoxFluxes B = boxes[b.x];
-  const long long nface = 2LL * ((long long)B.n[1] * B.n[2] + (long long)B.n[0] * B.n[2] + (long long)B.n[0] * B.n[1]);
-  const long long f = (long long)b.y * 256 + threadIdx.x;
+  const int nface = 2 * (B.n[1] * B.n[2] + B.n[0] * B.n[2] + B.n[0] * B.n[1]);
+  const int f = b.y * 256 + threadIdx.x;
   if (f >= nface) return;
   int d, i, j, k;
-  box_face<Pol>(B, f, d, i, j, k);  // the face between cell (i, j, k) and its +d neighbour
+  box_face(B, f, d, i, j, k);  // the face between cell (i, j, k) and its +d neighbour
   const double dt = dt_dev[B.dt_index];
   unsigned flags = 0;
   // address of cell (x, y, z) in box coordinates (interior from 0; the stencil reaches -2 .. n+1)
@@ -577,10 +592,9 @@ __global__ void __launch_bounds__(256) k_box_fluxes(const HostBoxFluxes* boxes, 
   floor_state(st[1], kc<R>(prm, K_RHOF), kc<R>(prm, K_PF));
   R F[5];
   hllc_dyn(d, st[0], st[1], kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), F);
-  const long long R5 = nface;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    S* reg = static_cast<S*>(B.reg) + v * R5 + f;
+    S* reg = static_cast<S*>(B.reg) + (long long)v * nface + f;
     const S add = (S)(dt * (double)F[v]);
     *reg = accumulate ? *reg + add : add;
   }
