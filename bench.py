@@ -774,9 +774,10 @@ def main():
     # end to end through the C ABI with the state in (page-locked) host memory: hydro_step_host
     # copies the state in, steps it and copies the result out every step, pipelined over z slabs;
     # host buffers ping-pong, each step's dt is the fused CFL dt of the previous step's result.
-    e2e_steps = 6
+    e2e_steps = 8
     esz = a.element_size()
-    hbuf = [a.cpu().pin_memory(), torch.empty(a.shape, dtype=a.dtype).pin_memory()]
+    hbuf = [torch.empty(a.shape, dtype=a.dtype, pin_memory=True) for _ in range(2)]  # page-locked, no staging copy
+    hbuf[0].copy_(a)
     hd = torch.empty(e2e_steps + 2, dtype=torch.float64, device="cuda")
     hy.hydro_cfl_dt(ctx, hy.patch(a, 0, dx), hd[0:1])
     hy.hydro_step_host(ctx, hy.host_patch(hbuf[0], dx), hy.host_patch(hbuf[1], dx), hd[0:1], hd[1:2])  # warm-up
