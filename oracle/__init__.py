@@ -53,6 +53,7 @@ def lib():
         L.oracle_step_periodic_adjoint.argtypes = [P, vp, vp, vp, i, i, i, d, d, i]
         L.oracle_step_patch_adjoint.argtypes = [P, vp, vp, vp, i, i, i, d, d]
         L.oracle_hllc.argtypes = [P, vp, vp, i, vp]
+        L.oracle_hllc_n.argtypes = [P, vp, vp, i, vp, ctypes.c_long]
         L.oracle_recover.argtypes = [P, vp, vp, ctypes.c_long]
         L.oracle_prim_to_cons.argtypes = [P, vp, vp, ctypes.c_long]
         L.oracle_prim_to_cons_adjoint.argtypes = [P, vp, vp, vp, ctypes.c_long]
@@ -163,6 +164,16 @@ def hllc(qL, qR, d, cfg=None):
     qR, pr = _c(qR)
     F = np.empty(5)
     _check(lib().oracle_hllc(ctypes.byref(cfg), pl, pr, d, F.ctypes.data))
+    return F
+
+
+def hllc_n(qL, qR, d, cfg=None):
+    """HLLC fluxes (5, ...) of the faces of normal d between primitive states qL, qR (5, ...)."""
+    cfg = cfg or config()
+    qL, pl = _c(qL)
+    qR, pr = _c(qR)
+    F = np.empty_like(qL)
+    _check(lib().oracle_hllc_n(ctypes.byref(cfg), pl, pr, d, F.ctypes.data, qL[0].size))
     return F
 
 

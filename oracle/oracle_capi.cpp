@@ -214,6 +214,22 @@ int oracle_hllc(const oracle_config* cfg, const double* qL, const double* qR, in
   return 0;
 }
 
+// HLLC fluxes of n faces of normal d: qL, qR and F are [5][n].
+int oracle_hllc_n(const oracle_config* cfg, const double* qL, const double* qR, int d, double* F, long n) {
+  if (!cfg || !qL || !qR || !F || d < 0 || d > 2 || n < 0) return -1;
+  const Config c = to_cfg(cfg);
+  for (long a = 0; a < n; ++a) {
+    double l[5], r[5], f[5];
+    for (int v = 0; v < 5; ++v) {
+      l[v] = qL[(size_t)v * n + a];
+      r[v] = qR[(size_t)v * n + a];
+    }
+    hllc_flux(c, l, r, d, f);
+    for (int v = 0; v < 5; ++v) F[(size_t)v * n + a] = f[v];
+  }
+  return 0;
+}
+
 // Recovery of n cells: U and q are [5][n].
 int oracle_recover(const oracle_config* cfg, const double* U, double* q, long n) {
   if (!cfg || !U || !q || n < 0) return -1;
