@@ -415,6 +415,38 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     t1.record(stream)
     torch.cuda.synchronize()
     ms_l = t0.elapsed_time(t1) / steps
+    # the level stored oct-major (128^3 octs) with its device-built Morton order and neighbour
+    # table (the device chunk builder); the same groups, then every oct of the level in Morton
+    # order, stepped through the table
+    no = 128 ** 3
+    V = parent.reshape(5, 128, 2, 128, 2, 128, 2).permute(0, 1, 3, 5, 2, 4, 6).reshape(5, no, 8).contiguous()
+    Vo = torch.empty_like(V)
+    idx = torch.arange(no, device="cuda", dtype=torch.int32)
+    pos = torch.stack([idx % 128, (idx // 128) % 128, idx // (128 * 128)], dim=1).contiguous()
+    order = torch.empty(no, dtype=torch.int32, device="cuda")
+    nbr = torch.empty((no, 27), dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        hy.hydro_octs_build(ctx, pos, (128, 128, 128), order, nbr)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        hy.hydro_octs_build(ctx, pos, (128, 128, 128), order, nbr)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = t0.elapsed_time(t1) / steps
+    ol = (od[:, 0] // 2 + 128 * (od[:, 1] // 2 + 128 * (od[:, 2] // 2))).to(torch.int32).contiguous()
+    timed = {}
+    for name, lst in (("groups", ol), ("level", order)):
+        for _ in range(warmup):
+            hy.hydro_step_octs_table(ctx, V, Vo, nbr, lst, 1.0 / 256, dto)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(steps):
+            hy.hydro_step_octs_table(ctx, V, Vo, nbr, lst, 1.0 / 256, dto)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        timed[name] = t0.elapsed_time(t1) / steps
+    ms_t, ms_tl = timed["groups"], timed["level"]
     # coarse-to-fine ghost fill of the same patch set from a 128^3 coarse level (fine dx = 1/256)
     coarse = turbulent(128, "mixed", "cuda", seed=3, sedov=False)
     rng = np.random.default_rng(14)
@@ -454,12 +486,25 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
                           "hbm_frac": ngroups * (80 + 8) * 5 * 8 / (ms_l / 1e3) / 1e9 / hbm,
                           "note": "stencils read in place from the 256^3 level (80 needed cells per group, "
                                   "8 written), groups in Morton order; no gathered copy"},
+           "octs_table": {"groups": ngroups, "ms_per_step": ms_t,
+                          "mcell_updates_per_s": ngroups * 8 / (ms_t / 1e3) / 1e6,
+                          "hbm_frac": ngroups * ((80 + 8) * 5 * 8 + 27 * 4) / (ms_t / 1e3) / 1e9 / hbm,
+                          "note": "the same groups read from the oct-major level through the device-built "
+                                  "neighbour table (80 needed cells + 27 table entries per group, 8 written)"},
+           "octs_table_level": {"octs": no, "ms_per_step": ms_tl,
+                                "mcell_updates_per_s": no * 8 / (ms_tl / 1e3) / 1e6,
+                                "hbm_frac": no * (8 * 5 * 8 * 2 + 27 * 4) / (ms_tl / 1e3) / 1e9 / hbm,
+                                "note": "every oct of the 256^3 level in Morton order through the table "
+                                        "(each cell read once from HBM and written once, plus the table)"},
+           "octs_build": {"octs": no, "ms": ms_b, "mocts_per_s": no / (ms_b / 1e3) / 1e6,
+                          "note": "Morton order and 27-entry neighbour table of the level's 128^3 octs "
+                                  "(bitmap over the key space, prefix sums, O(1) rank lookups)"},
            "ghost_fill": {"ghost_cells": nghost, "ms": ms_g, "mcells_per_s": nghost / (ms_g / 1e3) / 1e6,
                           "hbm_frac": (nghost + 128 ** 3) * 5 * 8 / (ms_g / 1e3) / 1e9 / hbm,
                           "note": "2 ghost layers of the 4096 patches prolonged from a 128^3 coarse level "
                                   "(writes + one read of the coarse level)"},
            "error_bits": bits}
-    del keep, parent, g, go, od, coarse
+    del keep, parent, g, go, od, coarse, V, Vo, pos, order, nbr, ol
     hy.hydro_finalize(ctx)
     torch.cuda.empty_cache()
     return out

@@ -208,6 +208,39 @@ int hydro_average_down(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_pa
 int hydro_step_octs_level(hydro_ctx* ctx, const hydro_patch* level, const int* origins_dev, long long ngroups,
                           void* const out[5], const double* dt_dev);
 
+/* The device chunk builder's bookkeeping for one level's octs (Sec. 3 and Fig. 1: the Ramses GPU
+ * procedure orders a level's cells along the space-filling curve and gathers each oct's
+ * neighbourhood for the hydro kernel).  An oct at oct coordinates (X, Y, Z) holds the level's cells
+ * 2X..2X+1, 2Y..2Y+1, 2Z..2Z+1; the level is periodic with dims[3] = (X, Y, Z) octs per axis.
+ *
+ * hydro_octs_build: the Morton order of the octs and their neighbour table.
+ *   pos_dev:   device array [noct][3] of int, oct coordinates (X, Y, Z), each in [0, dims);
+ *   dims:      host array of 3 ints, each in 1..1024; 1 <= noct <= 2^28;
+ *   order_dev: device array [noct] of int, receives the oct indices in increasing Morton key
+ *              (bits of X, Y, Z interleaved, x lowest);
+ *   nbr_dev:   NULL, or a device array [noct][27] of int that receives, in entry
+ *              ((dz+1)*3 + dy+1)*3 + dx+1 of oct o, the index of the oct at (X+dx, Y+dy, Z+dz)
+ *              wrapped on the level, or -1 where the level has no oct; entry 13 is o.
+ *   A position outside dims, or two octs at one position, sets HYDRO_EBIT_BAD_TILE; order and the
+ *   table are then not meaningful (order entries left without an oct are -1).  The scratch (a
+ *   bitmap over 8^b keys, 2^b >= max dims) is owned by the context and grows on demand.
+ *
+ * hydro_step_octs_table: one step of the octs list_dev[0 .. ngroups-1] of an oct-major level whose
+ * 6^3 stencils are read through the neighbour table (stencil cell (x, y, z), each 0..5, is cell
+ * (x%2, y%2, z%2) of the neighbour at offset (x/2 - 1, y/2 - 1, z/2 - 1)).
+ *   in[f], out[f]: device arrays [noct][2][2][2] (cell (i, j, k) of oct o at o*8 + (k*2 + j)*2 + i),
+ *              in and out not overlapping; the listed octs' cells in out receive U^{n+1}, the other
+ *              octs' cells are left as they are;
+ *   nbr_dev:   the table of hydro_octs_build (or the caller's, same layout);
+ *   list_dev:  device array [ngroups] of oct indices (e.g. order_dev, or a part of it).
+ *   A listed oct outside [0, noct), or one with a neighbour entry outside it (-1 included: every
+ *   listed oct needs its 26 neighbours), sets HYDRO_EBIT_BAD_TILE and is skipped.
+ *   All octs share dx and dt_dev[0].  Same arithmetic, so the same bits, as hydro_step_octs on the
+ *   gathered stencils. */
+int hydro_octs_build(hydro_ctx* ctx, const int* pos_dev, int noct, const int dims[3], int* order_dev, int* nbr_dev);
+int hydro_step_octs_table(hydro_ctx* ctx, void* const in[5], void* const out[5], int noct, const int* nbr_dev,
+                          const int* list_dev, long long ngroups, double dx, const double* dt_dev);
+
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
  * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64,
  * HYDRO_FP64_DF (which runs the FP64 reverse sweep: faster on GB300 than a double-float one) or

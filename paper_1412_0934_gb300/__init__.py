@@ -38,7 +38,7 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level", "hydro_fill_ghosts", "hydro_exchange_ghosts", "hydro_patch_fluxes",
+           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_fill_ghosts", "hydro_exchange_ghosts", "hydro_patch_fluxes",
            "hydro_level_fluxes", "hydro_reflux", "hydro_average_down",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
@@ -84,6 +84,8 @@ def lib():
         L.hydro_step_host.argtypes = [vp, PP, PP, vp, vp]
         L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
         L.hydro_step_octs_level.argtypes = [vp, PP, vp, ll, vp * 5, vp]
+        L.hydro_octs_build.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_int), vp, vp]
+        L.hydro_step_octs_table.argtypes = [vp, vp * 5, vp * 5, i, vp, vp, ll, d, vp]
         L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
         L.hydro_exchange_ghosts.argtypes = [vp, PP, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ctypes.c_int)]
         IP = ctypes.POINTER(ctypes.c_int)
@@ -319,6 +321,37 @@ def hydro_step_octs_level(ctx, level, origins, out, dt):
             raise ValueError("oct arrays must be contiguous per field")
     _check(lib().hydro_step_octs_level(ctx.handle, ctypes.byref(level.c), _ptr(origins), origins.shape[0], o, _ptr(dt)),
            "hydro_step_octs_level")
+
+
+def _int_tensor(t, what, cols=None):
+    if t.dtype != torch.int32 or not t.is_contiguous() or (cols and (t.dim() != 2 or t.shape[1] != cols)):
+        raise ValueError("%s must be a contiguous int32 tensor%s" % (what, " of shape (n, %d)" % cols if cols else ""))
+
+
+def hydro_octs_build(ctx, pos, dims, order, nbr=None):
+    """pos: (n, 3) int32 CUDA tensor of oct coordinates (X, Y, Z); dims: 3 ints (octs per axis);
+    order: (n,) int32 out, the Morton order; nbr: None or (n, 27) int32 out, the neighbour table."""
+    _int_tensor(pos, "pos", 3)
+    _int_tensor(order, "order")
+    if nbr is not None:
+        _int_tensor(nbr, "nbr", 27)
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+    _check(lib().hydro_octs_build(ctx.handle, _ptr(pos), pos.shape[0], d, _ptr(order),
+                                  _ptr(nbr) if nbr is not None else None), "hydro_octs_build")
+
+
+def hydro_step_octs_table(ctx, U, out, nbr, octs, dx, dt):
+    """U, out: (5, noct, 8) oct-major level (or 5 tensors of (noct, 8)); nbr: (noct, 27) int32;
+    octs: (G,) int32 list of the octs to step; their cells of out receive U^{n+1}."""
+    _int_tensor(nbr, "nbr", 27)
+    _int_tensor(octs, "octs")
+    i = (ctypes.c_void_p * 5)(*[_ptr(U[v]) for v in range(5)])
+    o = (ctypes.c_void_p * 5)(*[_ptr(out[v]) for v in range(5)])
+    for v in range(5):
+        if not U[v].is_contiguous() or not out[v].is_contiguous():
+            raise ValueError("oct arrays must be contiguous per field")
+    _check(lib().hydro_step_octs_table(ctx.handle, i, o, nbr.shape[0], _ptr(nbr), _ptr(octs), octs.shape[0],
+                                       float(dx), _ptr(dt)), "hydro_step_octs_table")
 
 
 def hydro_step_octs(ctx, gathered, out, dx, dt):

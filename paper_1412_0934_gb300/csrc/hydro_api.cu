@@ -90,6 +90,9 @@ struct hydro_ctx {
   char* d_aux[kAux] = {nullptr, nullptr, nullptr, nullptr};
   size_t aux_cap[kAux] = {0, 0, 0, 0};
   std::vector<char> aux_last[kAux];
+  // oct builder scratch: key bitmap, word prefix sums, block prefix sums
+  unsigned* d_octs_scratch = nullptr;
+  size_t octs_scratch_cap = 0;
   long long launches = 0;
 };
 
@@ -362,6 +365,7 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_xchg);
   cudaFree(c->d_tasks);
   for (int k = 0; k < hydro_ctx::kAux; ++k) cudaFree(c->d_aux[k]);
+  cudaFree(c->d_octs_scratch);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
@@ -872,6 +876,48 @@ int hydro_step_octs_level(hydro_ctx* c, const hydro_patch* level, const int* ori
     if (!out[v] || reinterpret_cast<uintptr_t>(out[v]) % es) return HYDRO_ERR_ARG;
   c->launches += 1;
   return cuda_status(c->ops->octs_level(make_io(L, L), origins_dev, out, ngroups, c->prm, dt_dev, c->d_err, c->stream));
+}
+
+int hydro_octs_build(hydro_ctx* c, const int* pos_dev, int noct, const int dims[3], int* order_dev, int* nbr_dev) {
+  if (!c || !pos_dev || !dims || !order_dev || noct < 1 || noct > (1 << 28)) return HYDRO_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(pos_dev) % sizeof(int) || reinterpret_cast<uintptr_t>(order_dev) % sizeof(int) ||
+      reinterpret_cast<uintptr_t>(nbr_dev) % sizeof(int))
+    return HYDRO_ERR_ARG;
+  int bits = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (dims[d] < 1 || dims[d] > 1024) return HYDRO_ERR_ARG;
+    while ((1 << bits) < dims[d]) ++bits;
+  }
+  const size_t nwords = std::max<size_t>(1, ((size_t)1 << (3 * bits)) >> 5);
+  const size_t nblocks = (nwords + 1023) / 1024;
+  int rc = ensure_device(&c->d_octs_scratch, &c->octs_scratch_cap, 2 * nwords + nblocks);
+  if (rc) return rc;
+  unsigned* bitmap = c->d_octs_scratch;
+  c->launches += nbr_dev ? 5 : 4;
+  return cuda_status(hydro::launch_octs_build(pos_dev, noct, dims, bitmap, bitmap + nwords, bitmap + 2 * nwords,
+                                              nwords, order_dev, nbr_dev, c->d_err, c->stream));
+}
+
+int hydro_step_octs_table(hydro_ctx* c, void* const in[5], void* const out[5], int noct, const int* nbr_dev,
+                          const int* list_dev, long long ngroups, double dx, const double* dt_dev) {
+  if (!c || !in || !out || noct < 1 || !nbr_dev || !list_dev || ngroups < 1 || !finite_pos(dx) || !dt_dev)
+    return HYDRO_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(nbr_dev) % sizeof(int) || reinterpret_cast<uintptr_t>(list_dev) % sizeof(int))
+    return HYDRO_ERR_ARG;
+  const int es = elem_size(c);
+  const uintptr_t bytes = (uintptr_t)noct * 8 * es;
+  for (int v = 0; v < 5; ++v) {
+    if (!in[v] || !out[v]) return HYDRO_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(in[v]) % es || reinterpret_cast<uintptr_t>(out[v]) % es) return HYDRO_ERR_ARG;
+  }
+  for (int v = 0; v < 5; ++v)  // out is written while in is read as neighbours: no overlap
+    for (int u = 0; u < 5; ++u) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(out[v]), b = reinterpret_cast<uintptr_t>(in[u]);
+      if (a < b + bytes && b < a + bytes) return HYDRO_ERR_ARG;
+    }
+  c->launches += 1;
+  return cuda_status(
+      c->ops->octs_table(in, nbr_dev, noct, list_dev, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

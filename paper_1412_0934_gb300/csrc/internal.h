@@ -63,6 +63,11 @@ struct KernelOps {
   // Oct groups read in place from a periodic level grid at the given origins (-> 2^3 each).
   cudaError_t (*octs_level)(const HostPatchIO& level, const int* origins, void* const out[5], long long ngroups,
                             const Params& prm, const double* dt, unsigned* err, cudaStream_t s);
+  // Oct groups of oct-major storage read through a neighbour table; group g steps oct list[g] and
+  // writes its 8 cells in place of that oct in out.
+  cudaError_t (*octs_table)(void* const in[5], const int* nbr, int noct, const int* list, void* const out[5],
+                            long long ngroups, double dx, const Params& prm, const double* dt, unsigned* err,
+                            cudaStream_t s);
   // Adjoint of one periodic step.
   cudaError_t (*adjoint)(const HostPatchIO& U, const HostPatchIO& lam, void* const lam_out[5], const Params& prm,
                          const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s);
@@ -121,6 +126,13 @@ cudaError_t launch_average_down(int elem_size, const HostGhostPatch* d_patches, 
 // patch d_blocks[b].x.
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
                                const HostPatchIO& coarse, cudaStream_t s);
+
+// Morton order and neighbour table of a level's octs (octs_build.cu).  Scratch: bitmap and
+// word_prefix of nwords words, block_prefix of (nwords + 1023) / 1024 words; nwords = max(1, 8^b / 32)
+// for keys below 8^b.
+cudaError_t launch_octs_build(const int* pos, int noct, const int dims[3], unsigned* bitmap, unsigned* word_prefix,
+                              unsigned* block_prefix, size_t nwords, int* order, int* nbr, unsigned* err,
+                              cudaStream_t s);
 
 // Work-list construction (precision-independent; descriptors read through HostPatchIO).
 cudaError_t build_worklist(const HostPatchIO* d_patches, int npatch, int tx, int ty, int zchunk, int* d_counts,

@@ -200,14 +200,18 @@ struct OctSmem {
   short need[80];
 };
 
-// Where a group's 6^3 stencil comes from.  OctGathered: the caller's gathered buffer, group g's
-// cell c (z, y, x from -2) at g*216 + c.  OctLevel: a periodic level grid and the groups' origins
-// (the oct's lowest cell, x, y, z), wrapped on the fly -- no gathered copy of the stencils.
+// Where a group's 6^3 stencil comes from and where its 8 cells go.  OctGathered: the caller's
+// gathered buffer, group g's cell c (z, y, x from -2) at g*216 + c.  OctLevel: a periodic level
+// grid and the groups' origins (the oct's lowest cell, x, y, z), wrapped on the fly -- no gathered
+// copy of the stencils.  Both write group g's cells at g*8 .. g*8+7.  OctTable: octs stored
+// oct-major (cell (i, j, k) of oct o at o*8 + (k*2 + j)*2 + i) with their neighbour table; group g
+// steps oct list[g] and writes it in place of that oct.
 template <class S>
 struct OctGathered {
   const S* f[5];
   __device__ __forceinline__ bool begin(long long, unsigned&) const { return true; }
   __device__ __forceinline__ long long cell(long long g, int c) const { return g * 216 + c; }
+  __device__ __forceinline__ long long out_cell(long long g, int e) const { return g * 8 + e; }
 };
 template <class S>
 struct OctLevel {
@@ -235,6 +239,35 @@ struct OctLevel {
     z += z < 0 ? nz : (z >= nz ? -nz : 0);
     return z * sz + y * sy + x;
   }
+  __device__ __forceinline__ long long out_cell(long long g, int e) const { return g * 8 + e; }
+};
+template <class S>
+struct OctTable {
+  const S* f[5];
+  const int* nbr;   // [noct][27]: oct at offset (dx, dy, dz) in entry ((dz+1)*3 + dy+1)*3 + dx+1
+  const int* list;  // [ngroups]: the octs to step
+  int noct;
+  int oct;          // the current group's oct
+  // Loads group g's oct and checks it and its 27 neighbour entries (one per lane, warp-wide):
+  // an index outside [0, noct) flags HYDRO_EBIT_BAD_TILE and the group is skipped.
+  __device__ __forceinline__ bool begin(long long g, unsigned& flags) {
+    oct = __ldg(list + g);
+    bool bad = (unsigned)oct >= (unsigned)noct;
+    const int lane = threadIdx.x & 31;
+    if (!bad && lane < 27) bad = (unsigned)__ldg(nbr + 27LL * oct + lane) >= (unsigned)noct;
+    if (__any_sync(0xffffffffu, bad)) {
+      flags |= HYDRO_EBIT_BAD_TILE;
+      return false;
+    }
+    return true;
+  }
+  // Stencil cell (x, y, z), each 0..5, is cell (x%2, y%2, z%2) of neighbour (x/2, y/2, z/2).
+  __device__ __forceinline__ long long cell(long long, int c) const {
+    const int x = c % 6, y = (c / 6) % 6, z = c / 36;
+    const int n = __ldg(nbr + 27LL * oct + ((z >> 1) * 3 + (y >> 1)) * 3 + (x >> 1));
+    return 8LL * n + ((z & 1) * 2 + (y & 1)) * 2 + (x & 1);
+  }
+  __device__ __forceinline__ long long out_cell(long long, int e) const { return 8LL * oct + e; }
 };
 
 // Resident blocks per SM: six (24 warps) for float arithmetic, measured fastest against the
@@ -368,7 +401,7 @@ __global__ void __launch_bounds__(32 * kOctWarps, oct_min_blocks<Pol>()) k_octs(
       for (int v = 0; v < 5; ++v) {
         const R* F = sm.f[w][v];
         const R div = ((F[fxp] - F[fxm]) + (F[fyp] - F[fym])) + (F[fzp] - F[fzm]);
-        gout[v][g * 8 + lane] = Pol::update(__ldg(cur.f[v] + cur.cell(g, c)), dtdx, div);
+        gout[v][cur.out_cell(g, lane)] = Pol::update(__ldg(cur.f[v] + cur.cell(g, c)), dtdx, div);
       }
     }
     __syncwarp();
@@ -415,6 +448,20 @@ cudaError_t launch_octs_level(const HostPatchIO& level, const int* origins, void
   src.origins = origins;
   src.ox = src.oy = src.oz = 0;
   return launch_octs_src<Pol>(src, out, ngroups, level.dx, prm, dt, err, s);
+}
+
+template <class Pol>
+cudaError_t launch_octs_table(void* const in[5], const int* nbr, int noct, const int* list, void* const out[5],
+                              long long ngroups, double dx, const Params& prm, const double* dt, unsigned* err,
+                              cudaStream_t s) {
+  using S = typename Pol::S;
+  OctTable<S> src;
+  for (int v = 0; v < 5; ++v) src.f[v] = static_cast<const S*>(in[v]);
+  src.nbr = nbr;
+  src.list = list;
+  src.noct = noct;
+  src.oct = 0;
+  return launch_octs_src<Pol>(src, out, ngroups, dx, prm, dt, err, s);
 }
 
 // ------------------------------------------------------------------ primitive <-> conservative
@@ -611,7 +658,8 @@ template <class Pol>
 const KernelOps& make_ops() {
   static const KernelOps ops = {
       &launch_uniform<Pol>,      &launch_batched<Pol>,      &batched_blocks_per_sm<Pol>,
-      &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_octs_level<Pol>,   &launch_adjoint<Pol>,
+      &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_octs_level<Pol>,   &launch_octs_table<Pol>,
+      &launch_adjoint<Pol>,
       &adjoint_scratch_bytes<Pol>, &launch_p2c<Pol>,        &launch_p2c_adjoint<Pol>,
       &launch_box_fluxes<Pol>,   (int)sizeof(typename Pol::S), 1};
   return ops;
