@@ -331,12 +331,17 @@ def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, 
     else:
         dts = torch.empty(warmup + steps + 1, dtype=torch.float64, device="cuda")
         tuning = tune(hy, ctx, a, b, dx, dts)
+        if limiter == "ppm":
+            tuning["tile"] = "16x16"  # the PPM kernel's one tile shape; only the z chunk is tuned
         ms, per, _, launches = time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream)
         rc, bits = hy.hydro_get_error(ctx)
         hbm, src = peaks()
         out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
-               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "error_bits": bits, "tuning": tuning,
-               "roofline": roofline(precision, cells, per, ALG_FLOPS_PER_CELL[flops_key], hbm, src, None)}
+               "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "error_bits": bits, "tuning": tuning}
+        if flops_key is None:  # operations not counted for this form: the HBM fraction only
+            out["hbm_frac"] = cells * BYTES_PER_CELL[precision] / (statistics.mean(per) / 1e3) / 1e9 / hbm
+        else:
+            out["roofline"] = roofline(precision, cells, per, ALG_FLOPS_PER_CELL[flops_key], hbm, src, None)
     del a, b
     hy.hydro_finalize(ctx)
     torch.cuda.empty_cache()
@@ -740,7 +745,8 @@ def reference_arm(args):
 def run_forms(hy, args, n, precision):
     """The extra forms beside the headline (each failure reported, not fatal)."""
     forms = [] if args.forms == "none" else (
-        ["fp64", "fp32", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all" else args.forms.split(","))
+        ["fp64", "fp32", "ppm", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all"
+        else args.forms.split(","))
     forms = [f for f in forms if f != precision]
     extra = {}
     for f in forms:
@@ -760,6 +766,9 @@ def run_forms(hy, args, n, precision):
                     extra["adjoint_" + prec] = form_adjoint(hy, prec, n=args.adj_n)
             elif f == "amr":
                 extra["amr_level_mixed"] = form_amr_level(hy, max(3, args.steps // 2), 2)
+            elif f == "ppm":
+                for prec in ("df64", "fp32"):
+                    extra["ppm_%d_%s" % (n, prec)] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None)
             elif f == "graph1024":
                 extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                            sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,

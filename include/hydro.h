@@ -62,7 +62,15 @@ typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2, HYDRO_FP64_DF = 
  *              in double.  Same results as HYDRO_FP64 to about 1e-13 relative, several times faster
  *              on parts whose FP64 rate is a small fraction of their FP32 rate. */
 
-typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2 } hydro_limiter;
+typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2, HYDRO_PPM = 3 } hydro_limiter;
+/* HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT: piecewise-linear (PLM) reconstruction with that slope.
+ * HYDRO_PPM:  piecewise-parabolic reconstruction (Colella & Woodward 1984; the paper lists PPM
+ *             among its hydro methods, Sec. 2): fourth-order interface values from MC-limited
+ *             slopes, the monotonicity constraints on each cell's edges, the Hancock predictor with
+ *             the parabola's centre slope and face states q_h + (edge - q).  Stencil radius 3, so
+ *             only single periodic boxes (ng == 0) step with it: hydro_step with npatch == 1, ng == 0,
+ *             and hydro_run.  The batched, host-buffer, oct, flux-register and adjoint calls return
+ *             HYDRO_ERR_ARG for a PPM context. */
 
 /* Bits of the device error word. */
 #define HYDRO_EBIT_NONFINITE 0x01u /* a recovered density or pressure was not finite */

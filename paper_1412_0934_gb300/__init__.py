@@ -25,9 +25,9 @@ HYDRO_ERR_NOMEM = -5
 HYDRO_ERR_STATE = -6
 
 HYDRO_FP64, HYDRO_FP32, HYDRO_MIXED, HYDRO_FP64_DF = 0, 1, 2, 3
-HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT = 0, 1, 2
+HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT, HYDRO_PPM = 0, 1, 2, 3
 PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED, "df64": HYDRO_FP64_DF}
-LIMITERS = {"minmod": HYDRO_MINMOD, "mc": HYDRO_MC, "none": HYDRO_NOLIMIT}
+LIMITERS = {"minmod": HYDRO_MINMOD, "mc": HYDRO_MC, "none": HYDRO_NOLIMIT, "ppm": HYDRO_PPM}
 
 EBIT_NONFINITE = 0x01
 EBIT_RHO_FLOOR = 0x02

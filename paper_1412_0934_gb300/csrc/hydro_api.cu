@@ -163,6 +163,10 @@ HostPatchIO make_io(const hydro_patch& in, const hydro_patch& out) {
   return h;
 }
 
+// PPM (stencil radius 3) steps only single periodic boxes; every call built on the radius-2 PLM
+// stencil (ghosted patches, octs, boundary fluxes, the adjoint) rejects a PPM context.
+bool ppm(const hydro_ctx* c) { return c->cfg.limiter == HYDRO_PPM; }
+
 bool same_patch(const hydro_patch& a, const hydro_patch& b) { return std::memcmp(&a, &b, sizeof(hydro_patch)) == 0; }
 
 bool same_set(const std::vector<hydro_patch>& key, const hydro_patch* p, int n) {
@@ -236,6 +240,15 @@ int step_one_uniform(hydro_ctx* c, const hydro_patch& in, const hydro_patch& out
     if (rc) return rc;
   }
   int zc = std::min(c->zchunk, in.nz);
+  if (c->cfg.limiter == HYDRO_PPM) {  // the PPM kernel, then the CFL of U^{n+1} as its own launch
+    cudaError_t e = c->ops->step_ppm(make_io(in, out), c->prm, dt, zc, c->d_err, s);
+    c->launches += 1;
+    if (e == cudaSuccess && dt_next) {
+      e = c->ops->cfl(nullptr, make_io(out, out), 1, c->prm, dt_next, c->d_err, s);
+      c->launches += 1;
+    }
+    return cuda_status(e);
+  }
   cudaError_t e = c->ops->step_uniform(c->tile_id, make_io(in, out), c->prm, dt, dt_next, zc, c->d_err, s);
   c->launches += 1;
   return cuda_status(e);
@@ -314,7 +327,7 @@ int hydro_init(hydro_ctx** ctx, const hydro_config* cfg) {
   if (!(cfg->gamma > 1.0 && std::isfinite(cfg->gamma))) return HYDRO_ERR_ARG;
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return HYDRO_ERR_ARG;
   if (!(cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0)) return HYDRO_ERR_ARG;
-  if (cfg->limiter < HYDRO_MINMOD || cfg->limiter > HYDRO_NOLIMIT) return HYDRO_ERR_ARG;
+  if (cfg->limiter < HYDRO_MINMOD || cfg->limiter > HYDRO_PPM) return HYDRO_ERR_ARG;
   if (!hydro::ops_for(cfg->precision)) return HYDRO_ERR_ARG;
   hydro_ctx* c = new hydro_ctx();
   c->cfg = *cfg;
@@ -417,6 +430,7 @@ int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int 
     if (overlaps(c, in[i], out[i])) return HYDRO_ERR_ARG;
   }
   if (npatch == 1 && in[0].ng == 0) return step_one_uniform(c, in[0], out[0], dt_dev, dt_next_dev, c->stream);
+  if (ppm(c)) return HYDRO_ERR_ARG;
   int rc = prepare_batch(c, in, out, npatch);
   if (rc) return rc;
   if (cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
@@ -440,7 +454,7 @@ int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int 
 //   D2H:  slab k once its step has run
 int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, const double* dt_dev,
                     double* dt_next_dev) {
-  if (!c || !in || !out || !dt_dev) return HYDRO_ERR_ARG;
+  if (!c || !in || !out || !dt_dev || ppm(c)) return HYDRO_ERR_ARG;
   const hydro_patch &I = *in, &O = *out;
   if (!valid_patch(c, I) || !valid_patch(c, O) || !same_shape(I, O) || overlaps(c, I, O)) return HYDRO_ERR_ARG;
   if (I.ng != 0 || O.ng != 0 || I.sy != O.sy || I.sz != O.sz) return HYDRO_ERR_ARG;
@@ -573,7 +587,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
 
 int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], long long ngroups, double dx,
                     const double* dt_dev) {
-  if (!c || !gathered || !out || ngroups < 1 || !finite_pos(dx) || !dt_dev) return HYDRO_ERR_ARG;
+  if (!c || !gathered || !out || ngroups < 1 || !finite_pos(dx) || !dt_dev || ppm(c)) return HYDRO_ERR_ARG;
   const int es = elem_size(c);
   for (int v = 0; v < 5; ++v) {
     if (!gathered[v] || !out[v]) return HYDRO_ERR_ARG;
@@ -709,7 +723,7 @@ static std::vector<hydro::HostCopyTask> exchange_tasks(const std::vector<hydro::
 
 int hydro_patch_fluxes(hydro_ctx* c, const hydro_patch* patches, int npatch, const double* dt_dev,
                        void* const* registers, int accumulate) {
-  if (!c || !patches || npatch < 1 || !dt_dev || !registers) return HYDRO_ERR_ARG;
+  if (!c || !patches || npatch < 1 || !dt_dev || !registers || ppm(c)) return HYDRO_ERR_ARG;
   std::vector<hydro::HostBoxFluxes> boxes((size_t)npatch);
   for (int i = 0; i < npatch; ++i) {
     const hydro_patch& P = patches[i];
@@ -729,7 +743,7 @@ int hydro_patch_fluxes(hydro_ctx* c, const hydro_patch* patches, int npatch, con
 
 int hydro_level_fluxes(hydro_ctx* c, const hydro_patch* level, const int* box_origins, const int* box_dims, int nbox,
                        const double* dt_dev, void* const* registers, int accumulate) {
-  if (!c || !level || !box_origins || !box_dims || nbox < 1 || !dt_dev || !registers) return HYDRO_ERR_ARG;
+  if (!c || !level || !box_origins || !box_dims || nbox < 1 || !dt_dev || !registers || ppm(c)) return HYDRO_ERR_ARG;
   const hydro_patch& L = *level;
   if (!valid_patch(c, L) || L.ng != 0) return HYDRO_ERR_ARG;
   std::vector<hydro::HostBoxFluxes> boxes((size_t)nbox);
@@ -867,7 +881,7 @@ int hydro_exchange_ghosts(hydro_ctx* c, const hydro_patch* fine, const int* orig
 
 int hydro_step_octs_level(hydro_ctx* c, const hydro_patch* level, const int* origins_dev, long long ngroups,
                           void* const out[5], const double* dt_dev) {
-  if (!c || !level || !origins_dev || !out || ngroups < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  if (!c || !level || !origins_dev || !out || ngroups < 1 || !dt_dev || ppm(c)) return HYDRO_ERR_ARG;
   const hydro_patch& L = *level;
   if (!valid_patch(c, L) || L.ng != 0 || L.nx < 4 || L.ny < 4 || L.nz < 4) return HYDRO_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(origins_dev) % sizeof(int)) return HYDRO_ERR_ARG;
@@ -900,7 +914,7 @@ int hydro_octs_build(hydro_ctx* c, const int* pos_dev, int noct, const int dims[
 
 int hydro_step_octs_table(hydro_ctx* c, void* const in[5], void* const out[5], int noct, const int* nbr_dev,
                           const int* list_dev, long long ngroups, double dx, const double* dt_dev) {
-  if (!c || !in || !out || noct < 1 || !nbr_dev || !list_dev || ngroups < 1 || !finite_pos(dx) || !dt_dev)
+  if (!c || !in || !out || noct < 1 || !nbr_dev || !list_dev || ngroups < 1 || !finite_pos(dx) || !dt_dev || ppm(c))
     return HYDRO_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(nbr_dev) % sizeof(int) || reinterpret_cast<uintptr_t>(list_dev) % sizeof(int))
     return HYDRO_ERR_ARG;
@@ -922,7 +936,7 @@ int hydro_step_octs_table(hydro_ctx* c, void* const in[5], void* const out[5], i
 
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
                        const hydro_patch* lam_n, int npatch) {
-  if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1) return HYDRO_ERR_ARG;
+  if (!c || !U_n || !dt_dev || !lam_np1 || !lam_n || npatch < 1 || ppm(c)) return HYDRO_ERR_ARG;
   if (c->cfg.precision == HYDRO_MIXED) return HYDRO_ERR_ARG;
   // The double-float context runs the FP64 reverse sweep: on GB300 it is faster than the same
   // sweep in double-float arithmetic, whose register footprint (~240 per thread) leaves too few
@@ -1095,7 +1109,7 @@ int hydro_autotune(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, 
   cudaEventCreate(&e1);
   float best = 1e30f;
   int bt = c->tile_id, bz = c->zchunk;
-  for (int t = 0; t < hydro::kNumTiles; ++t) {
+  for (int t = 0; t < (ppm(c) ? 1 : hydro::kNumTiles); ++t) {  // the PPM kernel has one tile shape
     for (int zc : zcs) {
       if (zc > std::max(8, maxnz)) continue;
       if (zc < 8 && cells > (1LL << 22)) continue;

@@ -22,19 +22,19 @@ struct Params {
   double gamma, cfl, rho_floor, p_floor;
   int limiter;
   // Derived constants, precomputed on the host so kernels never convert or divide them:
-  // index 0 gamma, 1 1/(gamma-1), 2 gamma-1, 3 rho_floor, 4 p_floor; as doubles, as floats,
-  // and as (hi, lo) float pairs.
-  double kd[5];
-  float kf[5];
-  float kh[5], kl[5];
+  // index 0 gamma, 1 1/(gamma-1), 2 gamma-1, 3 rho_floor, 4 p_floor, 5 1/6; as doubles, as
+  // floats, and as (hi, lo) float pairs.
+  double kd[6];
+  float kf[6];
+  float kh[6], kl[6];
 };
 
-enum { K_GAMMA = 0, K_IGM1 = 1, K_GM1 = 2, K_RHOF = 3, K_PF = 4 };
+enum { K_GAMMA = 0, K_IGM1 = 1, K_GM1 = 2, K_RHOF = 3, K_PF = 4, K_SIXTH = 5 };
 
 inline Params make_params(double gamma, double cfl, double rho_floor, double p_floor, int limiter) {
   Params p{gamma, cfl, rho_floor, p_floor, limiter, {}, {}, {}, {}};
-  const double k[5] = {gamma, 1.0 / (gamma - 1.0), gamma - 1.0, rho_floor, p_floor};
-  for (int i = 0; i < 5; ++i) {
+  const double k[6] = {gamma, 1.0 / (gamma - 1.0), gamma - 1.0, rho_floor, p_floor, 1.0 / 6.0};
+  for (int i = 0; i < 6; ++i) {
     p.kd[i] = k[i];
     p.kf[i] = (float)k[i];
     p.kh[i] = (float)k[i];

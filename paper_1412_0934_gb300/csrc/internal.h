@@ -79,6 +79,9 @@ struct KernelOps {
   // Boundary-face fluxes of boxes into registers (block b: faces 256 d_blocks[b].y ... of box d_blocks[b].x).
   cudaError_t (*box_fluxes)(const HostBoxFluxes* d_boxes, const int2* d_blocks, int nblocks, const Params& prm,
                             const double* dt, int accumulate, cudaStream_t s);
+  // The PPM step of a periodic box (P.gin == 0), z chunks of zchunk planes.
+  cudaError_t (*step_ppm)(const HostPatchIO& P, const Params& prm, const double* dt, int zchunk, unsigned* err,
+                          cudaStream_t s);
   int elem_size;  // bytes per stored element
   int launches_per_step;
 };

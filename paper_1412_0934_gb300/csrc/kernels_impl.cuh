@@ -1,10 +1,12 @@
 // Kernels and launchers of one precision policy POL (included once per policy by kernels_*.cu):
-// the step kernels of step_tile.cuh for every compiled tile shape, the standalone CFL dt
+// the step kernels of step_tile.cuh for every compiled tile shape, the PPM step of step_ppm.cuh,
+// the standalone CFL dt
 // reduction, the oct-group step, the primitive->conservative map and its adjoint, and the
 // adjoint step (adjoint.cuh).
 #pragma once
 #include "adjoint.cuh"
 #include "internal.h"
+#include "step_ppm.cuh"
 #include "step_tile.cuh"
 
 namespace hydro {
@@ -661,7 +663,7 @@ const KernelOps& make_ops() {
       &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_octs_level<Pol>,   &launch_octs_table<Pol>,
       &launch_adjoint<Pol>,
       &adjoint_scratch_bytes<Pol>, &launch_p2c<Pol>,        &launch_p2c_adjoint<Pol>,
-      &launch_box_fluxes<Pol>,   (int)sizeof(typename Pol::S), 1};
+      &launch_box_fluxes<Pol>,   &launch_ppm<Pol>,          (int)sizeof(typename Pol::S), 1};
   return ops;
 }
 

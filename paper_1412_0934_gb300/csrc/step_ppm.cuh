@@ -1,0 +1,272 @@
+// The step with piecewise-parabolic reconstruction (PPM; the paper lists it among its hydro
+// methods, Sec. 2) on a periodic box.  Per axis and primitive variable (Colella & Woodward 1984):
+//   dq_i    = MC-limited slope (the PLM MC limiter of q_i - q_{i-1} and q_{i+1} - q_i);
+//   q_{i+h} = q_i + (q_{i+1} - q_i)/2 - (dq_{i+1} - dq_i)/6      (h = 1/2);
+//   edges qL = q_{i-h}, qR = q_{i+h}, then: both set to q_i at a local extremum
+//   ((qR - q)(q - qL) <= 0); else with D = qR - qL, Q6 = 6 (q - (qL + qR)/2): qL = 3q - 2qR if
+//   D Q6 > D^2, qR = 3q - 2qL if -D^2 > D Q6.
+// The rest is the PLM step with the parabola's centre slope D in the Hancock predictor and face
+// states q_h + (qR - q), q_h + (qL - q) in place of q_h +- dq/2.  The stencil radius is 3.
+//
+// Kernel layout: one thread per column of a TX x TY tile marching up z (as the PLM kernel).
+// Shared memory holds a ring of five recovered planes (p-2 .. p+2) over the tile and three halo
+// cells each side, the x- and y-face states of plane p (the tile's cells and one ring cell beyond
+// each edge) and the x and y fluxes of plane p.  The z reconstruction of a column reads its own
+// five ring entries; the z-face state of the plane below, the z flux below and the x/y flux
+// difference of the plane below stay in registers until the plane is updated one plane later.
+#pragma once
+
+#include "adjoint.cuh"
+#include "hydro_device.cuh"
+#include "internal.h"
+#include "step_tile.cuh"
+
+namespace hydro {
+
+constexpr int kPpmHalo = 3;
+
+template <class R, int TX, int TY>
+struct PpmShared {
+  static constexpr int QX = TX + 2 * kPpmHalo, QY = TY + 2 * kPpmHalo;
+  R q[5][5][QY][QX];       // ring of recovered planes: [slot][var][y + 3][x + 3]
+  R wx[2][5][TY][TX + 2];  // x-face states at n+1/2: [0: low face, 1: high face][var][y][x + 1]
+  R wy[2][5][TY + 2][TX];  // y-face states: [low/high][var][y + 1][x]
+  R fx[5][TY][TX + 1];     // flux through the low x face of cell x, x = 0 .. TX
+  R fy[5][TY + 1][TX];     // flux through the low y face of cell y, y = 0 .. TY
+  int sx[QX], sy[QY];      // wrapped grid index of each tile column / row
+};
+
+__device__ __forceinline__ int wrap_index(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// Edges (qL, qR) of the middle one of five consecutive cell values a .. e.
+template <class R>
+__device__ __forceinline__ void ppm_edges(R a, R b, R c, R d, R e, R sixth, R& qL, R& qR) {
+  const R sb = limited(b - a, c - b, HYDRO_MC);
+  const R sc = limited(c - b, d - c, HYDRO_MC);
+  const R sd = limited(d - c, e - d, HYDRO_MC);
+  qL = (b + half_(c - b)) - (sc - sb) * sixth;
+  qR = (c + half_(d - c)) - (sd - sc) * sixth;
+  if (prod_nonpos(qR - c, c - qL)) {
+    qL = c;
+    qR = c;
+    return;
+  }
+  const R D = qR - qL;
+  const R Q6 = mulf_(c - half_(qL + qR), 6.f);
+  const R DQ = D * Q6, DD = D * D;
+  if (DQ > DD)
+    qL = mulf_(c, 3.f) - twice_(qR);
+  else if (-DD > DQ)
+    qR = mulf_(c, 3.f) - twice_(qL);
+}
+
+// Edge offsets (edge - q) of tile cell (i, j) of the middle plane along x, y and z, and the
+// Hancock-predicted state qh.  sl: ring slots of planes p-2 .. p+2.
+template <class R, int TX, int TY>
+__device__ __forceinline__ void ppm_cell(const PpmShared<R, TX, TY>& sm, const int sl[5], int i, int j, R gamma,
+                                         R hdt, R sixth, R lo[3][5], R hi[3][5], R qh[5]) {
+  const int X = i + kPpmHalo, Y = j + kPpmHalo;
+  R q[5], D[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const R c = sm.q[sl[2]][v][Y][X];
+    q[v] = c;
+    R l, r;
+    ppm_edges(sm.q[sl[2]][v][Y][X - 2], sm.q[sl[2]][v][Y][X - 1], c, sm.q[sl[2]][v][Y][X + 1],
+              sm.q[sl[2]][v][Y][X + 2], sixth, l, r);
+    D[0][v] = r - l;
+    lo[0][v] = l - c;
+    hi[0][v] = r - c;
+    ppm_edges(sm.q[sl[2]][v][Y - 2][X], sm.q[sl[2]][v][Y - 1][X], c, sm.q[sl[2]][v][Y + 1][X],
+              sm.q[sl[2]][v][Y + 2][X], sixth, l, r);
+    D[1][v] = r - l;
+    lo[1][v] = l - c;
+    hi[1][v] = r - c;
+    ppm_edges(sm.q[sl[0]][v][Y][X], sm.q[sl[1]][v][Y][X], c, sm.q[sl[3]][v][Y][X], sm.q[sl[4]][v][Y][X], sixth, l,
+              r);
+    D[2][v] = r - l;
+    lo[2][v] = l - c;
+    hi[2][v] = r - c;
+  }
+  hancock(q, D[0], D[1], D[2], gamma, hdt, qh);
+}
+
+// Resident blocks per SM: the 8-byte ring and face arrays take ~165 KB of shared memory.
+template <class Pol>
+constexpr int ppm_min_blocks() { return sizeof(typename Pol::R) >= 8 ? 1 : 2; }
+
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
+    k_step_ppm(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev, int zchunk, unsigned* err) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  using SM = PpmShared<R, TX, TY>;
+  constexpr int QX = SM::QX, QY = SM::QY, NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM& sm = *reinterpret_cast<SM*>(smem_raw);
+  const int tid = threadIdx.x;
+  const double dtv = dt_dev[0];
+  if (!(dtv > 0.0 && dtv <= 1e300)) {
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicOr(err, HYDRO_EBIT_BAD_DT);
+    return;
+  }
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, P.nz);
+  for (int k = tid; k < QX; k += NT) sm.sx[k] = wrap_index(x0 + k - kPpmHalo, P.nx);
+  for (int k = tid; k < QY; k += NT) sm.sy[k] = wrap_index(y0 + k - kPpmHalo, P.ny);
+  __syncthreads();
+  const R gamma = kc<R>(prm, K_GAMMA), igm1 = kc<R>(prm, K_IGM1), sixth = kc<R>(prm, K_SIXTH);
+  const R rf = kc<R>(prm, K_RHOF), pf = kc<R>(prm, K_PF);
+  const R hdt = (R)(0.5 * dtv / P.dx);
+  const R dtdx = (R)(dtv / P.dx);
+  unsigned flags = 0;
+
+  // plane z of the box, wrapped, recovered into ring slot s over the tile and its halo
+  auto load_plane = [&](int z, int s) {
+    const long long zo = (long long)wrap_index(z, P.nz) * P.isz;
+    for (int c = tid; c < QX * QY; c += NT) {
+      const int y = c / QX, x = c - y * QX;
+      const long long a = zo + (long long)sm.sy[y] * P.isy + sm.sx[x];
+      S U[5];
+      R q[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) U[v] = __ldg(P.in[v] + a);
+      Pol::recover(U, prm, q, flags);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm.q[s][v][y][x] = q[v];
+    }
+  };
+  // slot of plane z: (z - z0 + 3) mod 5
+  for (int k = 0; k < 5; ++k) load_plane(z0 - kPpmHalo + k, k);
+  __syncthreads();
+
+  const int i = tid % TX, j = tid / TX;
+  const bool own = x0 + i < P.nx && y0 + j < P.ny;
+  // ring cell of this thread: x-low (i = -1), x-high (i = TX), y-low (j = -1), y-high (j = TY)
+  int rk = -1, ri = 0, rj = 0;
+  if (tid < TY) { rk = 0; ri = -1; rj = tid; }
+  else if (tid < 2 * TY) { rk = 1; ri = TX; rj = tid - TY; }
+  else if (tid < 2 * TY + TX) { rk = 2; ri = tid - 2 * TY; rj = -1; }
+  else if (tid < 2 * TY + 2 * TX) { rk = 3; ri = tid - 2 * TY - TX; rj = TY; }
+
+  R zhi[5], fzb[5], dxy[5];  // z-high face state, z flux below, x/y flux difference: plane p-1
+#pragma unroll
+  for (int v = 0; v < 5; ++v) zhi[v] = fzb[v] = dxy[v] = R(0);
+  for (int p = z0 - 1; p <= z1; ++p) {
+    const int base = p - z0 + 1;
+    int sl[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sl[k] = (base + k) % 5;
+    const bool xy = p >= z0 && p < z1;  // plane p is updated: its x and y faces are needed
+    R zlo[5], znew[5];
+    {
+      R lo[3][5], hi[3][5], qh[5];
+      ppm_cell(sm, sl, i, j, gamma, hdt, sixth, lo, hi, qh);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        zlo[v] = qh[v] + lo[2][v];
+        znew[v] = qh[v] + hi[2][v];
+        if (xy) {
+          sm.wx[0][v][j][i + 1] = qh[v] + lo[0][v];
+          sm.wx[1][v][j][i + 1] = qh[v] + hi[0][v];
+          sm.wy[0][v][j + 1][i] = qh[v] + lo[1][v];
+          sm.wy[1][v][j + 1][i] = qh[v] + hi[1][v];
+        }
+      }
+    }
+    if (xy && rk >= 0) {
+      R lo[3][5], hi[3][5], qh[5];
+      ppm_cell(sm, sl, ri, rj, gamma, hdt, sixth, lo, hi, qh);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if (rk == 0) sm.wx[1][v][rj][0] = qh[v] + hi[0][v];
+        else if (rk == 1) sm.wx[0][v][rj][TX + 1] = qh[v] + lo[0][v];
+        else if (rk == 2) sm.wy[1][v][0][ri] = qh[v] + hi[1][v];
+        else sm.wy[0][v][TY + 1][ri] = qh[v] + lo[1][v];
+      }
+    }
+    // z face p - 1/2, then the update of plane p - 1 (its faces p - 3/2 and p - 1/2 are known)
+    if (p > z0 - 1) {
+      R ql[5], qr[5], F[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        ql[v] = zhi[v];
+        qr[v] = zlo[v];
+      }
+      floor_state(ql, rf, pf);
+      floor_state(qr, rf, pf);
+      hllc<2>(ql, qr, gamma, igm1, F);
+      if (p > z0 && own) {
+        const int z = p - 1;
+        const long long ai = (long long)z * P.isz + (long long)(y0 + j) * P.isy + (x0 + i);
+        const long long ao = (long long)(z + P.gout) * P.osz + (long long)(y0 + j + P.gout) * P.osy + (x0 + i + P.gout);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) P.out[v][ao] = Pol::update(__ldg(P.in[v] + ai), dtdx, dxy[v] + (F[v] - fzb[v]));
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) fzb[v] = F[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) zhi[v] = znew[v];
+    __syncthreads();  // face states written; ring slot of plane p-2 free
+    if (xy) {
+      for (int f = tid; f < (TX + 1) * TY; f += NT) {
+        const int fy = f / (TX + 1), fx = f - fy * (TX + 1);
+        R ql[5], qr[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ql[v] = sm.wx[1][v][fy][fx];
+          qr[v] = sm.wx[0][v][fy][fx + 1];
+        }
+        floor_state(ql, rf, pf);
+        floor_state(qr, rf, pf);
+        hllc<0>(ql, qr, gamma, igm1, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sm.fx[v][fy][fx] = F[v];
+      }
+      for (int f = tid; f < TX * (TY + 1); f += NT) {
+        const int fy = f / TX, fx = f - fy * TX;
+        R ql[5], qr[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ql[v] = sm.wy[1][v][fy][fx];
+          qr[v] = sm.wy[0][v][fy + 1][fx];
+        }
+        floor_state(ql, rf, pf);
+        floor_state(qr, rf, pf);
+        hllc<1>(ql, qr, gamma, igm1, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sm.fy[v][fy][fx] = F[v];
+      }
+    }
+    if (p < z1) load_plane(p + kPpmHalo, sl[0]);
+    __syncthreads();  // fluxes and plane p+3 in place
+    if (xy) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        dxy[v] = (sm.fx[v][j][i + 1] - sm.fx[v][j][i]) + (sm.fy[v][j + 1][i] - sm.fy[v][j][i]);
+    }
+  }
+  flush_flags(flags, err);
+}
+
+template <class Pol>
+cudaError_t launch_ppm(const HostPatchIO& P, const Params& prm, const double* dt, int zchunk, unsigned* err,
+                       cudaStream_t s) {
+  constexpr int TX = 16, TY = 16;
+  const size_t smem = sizeof(PpmShared<typename Pol::R, TX, TY>);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_ppm<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
+  k_step_ppm<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, zchunk, err);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro
