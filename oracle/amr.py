@@ -62,6 +62,20 @@ def fill_ghosts(Uc, Ug, origin):
     return Ug
 
 
+def coarse_at(Uc_old, Uc_new, theta):
+    """The coarse level at a fraction theta (0..1) of its step, linear in time between its states
+    before and after the step: (1 - theta) U_old + theta U_new, each product and the sum rounded
+    once.  A fine level subcycling inside one coarse step takes its ghosts from this state (the
+    paper's time refinement: a finer level advances by smaller steps between the coarse ones, Sec. 2)."""
+    w0 = 1.0 - float(theta)
+    return w0 * np.asarray(Uc_old, dtype=np.float64) + float(theta) * np.asarray(Uc_new, dtype=np.float64)
+
+
+def fill_ghosts_time(Uc_old, Uc_new, theta, Ug, origin):
+    """fill_ghosts from the coarse level interpolated in time to the fraction theta of its step."""
+    return fill_ghosts(coarse_at(Uc_old, Uc_new, theta), Ug, origin)
+
+
 def prolong_box(Uc):
     """The whole fine level (5, 2NZ, 2NY, 2NX) prolonged from the periodic coarse box."""
     _, NZ, NY, NX = Uc.shape

@@ -3,7 +3,7 @@ satisfy: the eight children of a coarse cell average to it; a field linear acros
 neighbours is reproduced exactly at the fine centres; no fine value leaves the range of its parent
 and the parent's face neighbours (MinMod slopes); a constant field stays constant; the ghost fill
 of a patch agrees with the whole-level prolongation, including ghosts that wrap around the
-periodic level."""
+periodic level; the fill from the coarse level interpolated in time between two of its states."""
 import numpy as np
 import pytest
 
@@ -68,6 +68,29 @@ def test_patch_ghosts_agree_with_level_prolongation(origin):
     interior[2:-2, 2:-2, 2:-2] = True
     assert np.array_equal(Ug[:, interior], np.zeros((5, interior.sum())))
     assert np.abs(Ug[:, ~interior] - ref[:, ~interior]).max() <= 1e-15 * np.abs(ref).max()
+
+
+def test_time_interpolated_ghosts():
+    """The coarse level between its states: the end points are the plain fills bit for bit; the
+    midpoint is symmetric in the two states; a change of the coarse state that is uniform in space
+    (so no slope changes) moves every ghost by theta times that change."""
+    Uo = _field((6, 7, 6), 5)
+    c = np.array([0.3, -0.2, 0.1, 0.05, 0.7])[:, None, None, None]
+    Un = Uo + c
+    Ug = np.zeros((5, 8, 10, 8))
+    origin = (3, 9, 11)
+    assert np.array_equal(amr.fill_ghosts_time(Uo, Un, 0.0, Ug, origin), amr.fill_ghosts(Uo, Ug, origin))
+    assert np.array_equal(amr.fill_ghosts_time(Uo, Un, 1.0, Ug, origin), amr.fill_ghosts(Un, Ug, origin))
+    Ur = _field((6, 7, 6), 6)
+    assert np.array_equal(amr.fill_ghosts_time(Uo, Ur, 0.5, Ug, origin), amr.fill_ghosts_time(Ur, Uo, 0.5, Ug, origin))
+    base = amr.fill_ghosts(Uo, Ug, origin)
+    ghost = np.ones(Ug.shape[1:], dtype=bool)
+    ghost[2:-2, 2:-2, 2:-2] = False
+    for theta in (0.25, 0.5, 0.8):
+        got = amr.fill_ghosts_time(Uo, Un, theta, Ug, origin)
+        want = base + theta * c
+        assert np.abs(got[:, ghost] - want[:, ghost]).max() <= 1e-14
+        assert np.array_equal(got[:, ~ghost], Ug[:, ~ghost])
 
 
 def test_sibling_exchange_reassembles_a_partitioned_level():
