@@ -158,6 +158,15 @@ int hydro_step_octs(hydro_ctx* ctx, void* const gathered[5], void* const out[5],
 int hydro_fill_ghosts(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
                       int npatch);
 
+/* The same ghost fill from the coarse level interpolated in time within its step, for a finer level
+ * that advances by smaller steps between the coarse ones (time refinement, Sec. 2): each coarse
+ * value used is (1 - theta) * coarse_old + theta * coarse_new, each product and the sum rounded once
+ * in the storage type, then prolonged as by hydro_fill_ghosts.  coarse_old, coarse_new: the coarse
+ * level before and after its step (ng == 0, same sizes and strides); 0 <= theta <= 1 (theta = 1
+ * gives hydro_fill_ghosts on coarse_new, theta = 0 on coarse_old, bit for bit). */
+int hydro_fill_ghosts_time(hydro_ctx* ctx, const hydro_patch* coarse_old, const hydro_patch* coarse_new, double theta,
+                           const hydro_patch* fine, const int* fine_origins, int npatch);
+
 /* Same-level ghost exchange: every ghost cell of a patch that lies in the interior of a patch of the
  * same level (another one, or the patch itself across the period) takes that interior cell's
  * values; other ghost cells are left as they are (fill them from the coarser level first with

@@ -38,7 +38,7 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_fill_ghosts", "hydro_exchange_ghosts", "hydro_patch_fluxes",
+           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_fill_ghosts", "hydro_fill_ghosts_time", "hydro_exchange_ghosts", "hydro_patch_fluxes",
            "hydro_level_fluxes", "hydro_reflux", "hydro_average_down",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
@@ -87,6 +87,7 @@ def lib():
         L.hydro_octs_build.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_int), vp, vp]
         L.hydro_step_octs_table.argtypes = [vp, vp * 5, vp * 5, i, vp, vp, ll, d, vp]
         L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
+        L.hydro_fill_ghosts_time.argtypes = [vp, PP, PP, d, PP, ctypes.POINTER(ctypes.c_int), i]
         L.hydro_exchange_ghosts.argtypes = [vp, PP, ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(ctypes.c_int)]
         IP = ctypes.POINTER(ctypes.c_int)
         L.hydro_patch_fluxes.argtypes = [vp, PP, i, vp, ctypes.POINTER(vp), i]
@@ -251,6 +252,17 @@ def hydro_fill_ghosts(ctx, coarse, fine, origins):
     if len(o) != 3 * n:
         raise ValueError("one (x, y, z) origin per patch")
     _check(lib().hydro_fill_ghosts(ctx.handle, ctypes.byref(coarse.c), f, o, n), "hydro_fill_ghosts")
+
+
+def hydro_fill_ghosts_time(ctx, coarse_old, coarse_new, theta, fine, origins):
+    """hydro_fill_ghosts from the coarse level at the fraction theta of its step:
+    (1 - theta) coarse_old + theta coarse_new, then prolonged."""
+    f, n = _parray(fine)
+    o = (ctypes.c_int * (3 * n))(*[int(v) for xyz in origins for v in xyz])
+    if len(o) != 3 * n:
+        raise ValueError("one (x, y, z) origin per patch")
+    _check(lib().hydro_fill_ghosts_time(ctx.handle, ctypes.byref(coarse_old.c), ctypes.byref(coarse_new.c),
+                                        float(theta), f, o, n), "hydro_fill_ghosts_time")
 
 
 def hydro_exchange_ghosts(ctx, fine, origins, period):

@@ -7,7 +7,9 @@
 //     U_f = U_C + s_x D_x + s_y D_y + s_z D_z,  s_d = +-1/4,  D_d = minmod(U_C - U_{C-e_d}, U_{C+e_d} - U_C).
 // One thread per ghost cell; each block takes up to 256 consecutive ghost cells of one patch (a
 // block table built on the host: patch and first ghost index per block); the arithmetic is in
-// the storage type.
+// the storage type.  The coarse level may be taken at a fraction theta of its step, linear in time
+// between its states before and after the step (a finer level subcycles inside the coarse step:
+// the paper's time refinement, Sec. 2).
 #include <cuda_runtime.h>
 
 #include "hydro_device.cuh"
@@ -27,9 +29,18 @@ __device__ __forceinline__ S minmod_s(S a, S b) {
 // same bits) -- and writes the children that are ghost cells of the patch.  Coarse cells whose
 // children are all interior return at once.  Each block takes up to 256 coarse cells of one patch
 // (a block table built on the host).
-template <class S>
+// Coarse value at element a: the state after the coarse step, or with Blend the state at a
+// fraction of the step, w0 U_old + w1 U_new with each product and the sum rounded once (no FMA).
+__device__ __forceinline__ double blend_rn(double w0, double a, double w1, double b) {
+  return __dadd_rn(__dmul_rn(w0, a), __dmul_rn(w1, b));
+}
+__device__ __forceinline__ float blend_rn(float w0, float a, float w1, float b) {
+  return __fadd_rn(__fmul_rn(w0, a), __fmul_rn(w1, b));
+}
+
+template <class S, bool Blend>
 __global__ void __launch_bounds__(256) k_fill_ghosts(const HostGhostPatch* patches, const int2* blocks,
-                                                     HostPatchIO coarse) {
+                                                     HostPatchIO coarse, HostPatchIO coarse_old, S w0, S w1) {
   const int2 b = blocks[blockIdx.x];      // (patch, first coarse cell of this block)
   const HostGhostPatch P = patches[b.x];  // by value: the stores below cannot alias it
   const int t = b.y + threadIdx.x;
@@ -74,10 +85,12 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(const HostGhostPatch* patch
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const S* U = static_cast<const S*>(coarse.in[v]);
-    const S u0 = __ldg(U + a0);
+    const S* Uo = static_cast<const S*>(coarse_old.in[v]);
+    auto at = [&](long long a) { return Blend ? blend_rn(w0, __ldg(Uo + a), w1, __ldg(U + a)) : __ldg(U + a); };
+    const S u0 = at(a0);
     S D[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) D[d] = minmod_s(u0 - __ldg(U + am[d]), __ldg(U + ap[d]) - u0);
+    for (int d = 0; d < 3; ++d) D[d] = minmod_s(u0 - at(am[d]), at(ap[d]) - u0);
     S ax[2], ay[4], az[8];
 #pragma unroll
     for (int hx = 0; hx < 2; ++hx) ax[hx] = u0 + (hx ? S(0.25) : S(-0.25)) * D[0];
@@ -229,11 +242,21 @@ cudaError_t launch_average_down(int elem_size, const HostGhostPatch* d_patches, 
 }
 
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
-                               const HostPatchIO& coarse, cudaStream_t s) {
-  if (elem_size == 4)
-    k_fill_ghosts<float><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse);
-  else
-    k_fill_ghosts<double><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse);
+                               const HostPatchIO& coarse, const HostPatchIO* coarse_old, double theta,
+                               cudaStream_t s) {
+  const double w0 = 1.0 - theta, w1 = theta;
+  const HostPatchIO& old = coarse_old ? *coarse_old : coarse;
+  if (elem_size == 4) {
+    if (coarse_old)
+      k_fill_ghosts<float, true><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse, old, (float)w0, (float)w1);
+    else
+      k_fill_ghosts<float, false><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse, old, 0.f, 1.f);
+  } else {
+    if (coarse_old)
+      k_fill_ghosts<double, true><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse, old, w0, w1);
+    else
+      k_fill_ghosts<double, false><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, coarse, old, 0.0, 1.0);
+  }
   return cudaGetLastError();
 }
 

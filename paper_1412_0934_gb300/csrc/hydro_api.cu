@@ -597,11 +597,18 @@ int hydro_step_octs(hydro_ctx* c, void* const gathered[5], void* const out[5], l
   return cuda_status(c->ops->octs(gathered, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
 }
 
-int hydro_fill_ghosts(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
-                      int npatch) {
+// The ghost fill from the coarse level after its step (coarse_old == nullptr), or at the fraction
+// theta of its step between coarse_old and coarse.
+static int fill_ghosts_impl(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch* coarse_old, double theta,
+                            const hydro_patch* fine, const int* fine_origins, int npatch) {
   if (!c || !coarse || !fine || !fine_origins || npatch < 1) return HYDRO_ERR_ARG;
   const hydro_patch& C = *coarse;
   if (!valid_patch(c, C) || C.ng != 0) return HYDRO_ERR_ARG;
+  if (coarse_old) {
+    const hydro_patch& O = *coarse_old;
+    if (!valid_patch(c, O) || O.ng != 0 || !same_shape(O, C) || O.sy != C.sy || O.sz != C.sz) return HYDRO_ERR_ARG;
+    if (!(theta >= 0.0 && theta <= 1.0)) return HYDRO_ERR_ARG;
+  }
   std::vector<hydro::HostGhostPatch> set((size_t)npatch);
   for (int i = 0; i < npatch; ++i) {
     const hydro_patch& F = fine[i];
@@ -643,8 +650,20 @@ int hydro_fill_ghosts(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch
     c->ghost_nblocks = (int)blocks.size();
   }
   c->launches += 1;
+  const HostPatchIO old = coarse_old ? make_io(*coarse_old, *coarse_old) : make_io(C, C);
   return cuda_status(hydro::launch_fill_ghosts(elem_size(c), c->d_ghost, c->d_ghost_blocks, c->ghost_nblocks,
-                                               make_io(C, C), c->stream));
+                                               make_io(C, C), coarse_old ? &old : nullptr, theta, c->stream));
+}
+
+int hydro_fill_ghosts(hydro_ctx* c, const hydro_patch* coarse, const hydro_patch* fine, const int* fine_origins,
+                      int npatch) {
+  return fill_ghosts_impl(c, coarse, nullptr, 1.0, fine, fine_origins, npatch);
+}
+
+int hydro_fill_ghosts_time(hydro_ctx* c, const hydro_patch* coarse_old, const hydro_patch* coarse_new, double theta,
+                           const hydro_patch* fine, const int* fine_origins, int npatch) {
+  if (!coarse_old) return HYDRO_ERR_ARG;
+  return fill_ghosts_impl(c, coarse_new, coarse_old, theta, fine, fine_origins, npatch);
 }
 
 // Copy tasks of the same-level exchange: for each destination patch, every periodic image of every

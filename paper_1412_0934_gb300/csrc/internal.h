@@ -126,9 +126,11 @@ cudaError_t launch_average_down(int elem_size, const HostGhostPatch* d_patches, 
                                 const HostPatchIO& coarse, cudaStream_t s);
 
 // Coarse-to-fine ghost fill (ghosts.cu): block b takes coarse cells d_blocks[b].y .. +255 under
-// patch d_blocks[b].x.
+// patch d_blocks[b].x.  coarse_old: nullptr, or the coarse state before its step (same layout), the
+// coarse values then being (1 - theta) old + theta coarse.
 cudaError_t launch_fill_ghosts(int elem_size, const HostGhostPatch* d_patches, const int2* d_blocks, int nblocks,
-                               const HostPatchIO& coarse, cudaStream_t s);
+                               const HostPatchIO& coarse, const HostPatchIO* coarse_old, double theta,
+                               cudaStream_t s);
 
 // Morton order and neighbour table of a level's octs (octs_build.cu).  Scratch: bitmap and
 // word_prefix of nwords words, block_prefix of (nwords + 1023) / 1024 words; nwords = max(1, 8^b / 32)

@@ -2,7 +2,8 @@
 ghost cell of patches of mixed sizes whose ghosts wrap around the periodic coarse level and whose
 origins lie outside [0, period); bitwise for double storage (the arithmetic is exact up to the same
 roundings in the same order), float storage against the oracle on the float coarse level; the
-interiors are left untouched; argument errors; the 4096-patch set on a 128^3 coarse level, sampled."""
+interiors are left untouched; the fill from the coarse level interpolated in time within its step;
+argument errors; the 4096-patch set on a 128^3 coarse level, sampled."""
 import ctypes
 
 import numpy as np
@@ -45,6 +46,43 @@ def test_ghost_fill_matches_oracle(precision):
             err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(Uc).max(axis=(1, 2, 3))
             assert err.max() <= 1e-6, (o, err)
         assert (got[:, 2:-2, 2:-2, 2:-2] == 7.0).all()
+    check_clean(c)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_time_interpolated_ghost_fill_matches_oracle(precision):
+    """hydro_fill_ghosts_time against the oracle's fill from the coarse level at a fraction of its
+    step (bitwise for double storage); theta = 1 and 0 give the plain fills of the two states."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    c = ctx(precision)
+    old = workloads.turbulent_state((6, 5, 7), seed=11, mach=3.0, sedov=False).to(dtype).contiguous()
+    new = workloads.turbulent_state((6, 5, 7), seed=12, mach=3.0, sedov=False).to(dtype).contiguous()
+    Uo, Un = old.double().numpy(), new.double().numpy()
+    dxc = 1.0 / 7
+    rng = np.random.default_rng(13)
+    dims, origins = _patches(rng, 25, (14, 10, 12))
+    co, cn = hy.patch(old.cuda(), 0, dxc), hy.patch(new.cuda(), 0, dxc)
+    for theta in (0.0, 0.375, 0.7, 1.0):
+        tens = [torch.full((5, nz + 4, ny + 4, nx + 4), 7.0, dtype=dtype, device="cuda") for nx, ny, nz in dims]
+        fine = [hy.patch(t, 2, dxc / 2) for t in tens]
+        hy.hydro_fill_ghosts_time(c, co, cn, theta, fine, origins)
+        torch.cuda.synchronize()
+        for t, o in zip(tens, origins):
+            got = t.double().cpu().numpy()
+            want = amr.fill_ghosts_time(Uo, Un, theta, np.full(got.shape, 7.0), o)
+            if dtype == torch.float64:
+                assert np.array_equal(got, want), (theta, o)
+            else:
+                err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(Un).max(axis=(1, 2, 3))
+                assert err.max() <= 1e-6, (theta, o, err)
+        if theta in (0.0, 1.0):
+            plain = [torch.full_like(t, 7.0) for t in tens]
+            hy.hydro_fill_ghosts(c, co if theta == 0.0 else cn, [hy.patch(t, 2, dxc / 2) for t in plain], origins)
+            torch.cuda.synchronize()
+            for t, p in zip(tens, plain):
+                assert torch.equal(t, p)
+    with pytest.raises(hy.HydroError):
+        hy.hydro_fill_ghosts_time(c, co, cn, 1.5, [hy.patch(tens[0], 2, dxc / 2)], origins[:1])
     check_clean(c)
 
 
