@@ -27,8 +27,8 @@
  *     launched.  Physical errors found on the device set bits of the error word
  *     (HYDRO_EBIT_*), read back by hydro_get_error.  CUDA errors return HYDRO_ERR_CUDA.
  *   - Ghost cells: a patch with ng == 2 carries two ghost layers filled by the caller (the paper's
- *     chunks carry their boundary cells, Sec. 3).  ng == 0 means a periodic box: the library wraps
- *     indices itself.
+ *     chunks carry their boundary cells, Sec. 3); three (ng == 3) for the PPM reconstruction.
+ *     ng == 0 means a periodic box: the library wraps indices itself.
  */
 #ifndef HYDRO_H
 #define HYDRO_H
@@ -67,10 +67,10 @@ typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2, HYDRO_PPM = 3 
  * HYDRO_PPM:  piecewise-parabolic reconstruction (Colella & Woodward 1984; the paper lists PPM
  *             among its hydro methods, Sec. 2): fourth-order interface values from MC-limited
  *             slopes, the monotonicity constraints on each cell's edges, the Hancock predictor with
- *             the parabola's centre slope and face states q_h + (edge - q).  Stencil radius 3, so
- *             only single periodic boxes (ng == 0) step with it: hydro_step with npatch == 1, ng == 0,
- *             and hydro_run.  The batched, host-buffer, oct, flux-register and adjoint calls return
- *             HYDRO_ERR_ARG for a PPM context. */
+ *             the parabola's centre slope and face states q_h + (edge - q).  Stencil radius 3:
+ *             hydro_step takes a periodic box (ng == 0) or patches carrying three ghost layers
+ *             (ng == 3; ng == 2 patches are refused), and hydro_run a periodic box.  The host-buffer,
+ *             oct, flux-register and adjoint calls return HYDRO_ERR_ARG for a PPM context. */
 
 /* Bits of the device error word. */
 #define HYDRO_EBIT_NONFINITE 0x01u /* a recovered density or pressure was not finite */
@@ -94,7 +94,8 @@ typedef struct {
   void* U[5];        /* device pointers to rho, m_x, m_y, m_z, E (see the element type above);
                         host pointers for hydro_step_host only */
   int nx, ny, nz;    /* interior cells, each >= 1 */
-  int ng;            /* ghost layers: 2 (caller-filled) or 0 (periodic box, wrapped by the library) */
+  int ng;            /* ghost layers: 2 (caller-filled; 3 in a HYDRO_PPM context) or 0 (periodic box,
+                        wrapped by the library) */
   long long sy, sz;  /* element strides of y and z in the stored (ghosted) array; x stride is 1.
                         Require sy >= nx + 2 ng and sz >= sy * (ny + 2 ng). */
   double dx;         /* cell size, > 0 */
@@ -124,11 +125,12 @@ int hydro_cfl_dt(hydro_ctx* ctx, const hydro_patch* p, int npatch, double* dt_de
  * fluxes on every face, conservative update; Sec. 2 and Sec. 4):
  *   out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] and cell size in[p].dx.
  * in, out: host arrays of npatch descriptors with equal nx, ny, nz and dx per patch; out[p] may
- * have ng 0 or 2 (only its interior is written) and must not overlap in[p] (use two buffers).
+ * have ng 0, 2 or (PPM) 3 (only its interior is written) and must not overlap in[p] (use two buffers).
  * dt_dev: device array of npatch doubles.  dt_next_dev: NULL, or a device array of npatch
  * doubles that receives the CFL dt of U^{n+1} (same formula as hydro_cfl_dt), fused into the
  * step.  A single periodic box (npatch == 1, ng == 0) runs the uniform-grid kernel; any other
- * set runs one persistent launch over a device-built tile work-list.  The descriptors are
+ * set (in[p] with ng == 2, or 3 in a HYDRO_PPM context) runs one persistent launch over a
+ * device-built tile work-list.  The descriptors are
  * uploaded and the work-list rebuilt only when the patch set differs from the previous call's. */
 int hydro_step(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
                double* dt_next_dev);

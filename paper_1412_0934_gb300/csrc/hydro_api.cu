@@ -116,9 +116,14 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_
 
 int elem_size(const hydro_ctx* c) { return c->cfg.precision == HYDRO_FP32 ? 4 : 8; }
 
+// PPM (stencil radius 3) steps periodic boxes and patches with three ghost layers; the calls built
+// on the radius-2 PLM stencil alone (the host-buffer step, octs, boundary fluxes, the adjoint)
+// reject a PPM context.
+bool ppm(const hydro_ctx* c) { return c->cfg.limiter == HYDRO_PPM; }
+
 bool valid_patch(const hydro_ctx* c, const hydro_patch& p) {
   if (p.nx < 1 || p.ny < 1 || p.nz < 1) return false;
-  if (p.ng != 0 && p.ng != 2) return false;
+  if (p.ng != 0 && p.ng != 2 && !(p.ng == 3 && ppm(c))) return false;
   if (!finite_pos(p.dx)) return false;
   const long long gx = p.nx + 2LL * p.ng, gy = p.ny + 2LL * p.ng;
   if (p.sy < gx || p.sz < p.sy * gy) return false;
@@ -163,10 +168,6 @@ HostPatchIO make_io(const hydro_patch& in, const hydro_patch& out) {
   return h;
 }
 
-// PPM (stencil radius 3) steps only single periodic boxes; every call built on the radius-2 PLM
-// stencil (ghosted patches, octs, boundary fluxes, the adjoint) rejects a PPM context.
-bool ppm(const hydro_ctx* c) { return c->cfg.limiter == HYDRO_PPM; }
-
 bool same_patch(const hydro_patch& a, const hydro_patch& b) { return std::memcmp(&a, &b, sizeof(hydro_patch)) == 0; }
 
 bool same_set(const std::vector<hydro_patch>& key, const hydro_patch* p, int n) {
@@ -191,8 +192,9 @@ int ensure_device(T** d, size_t* cap, size_t n) {
 // unless the cached set and tuning are unchanged.
 int prepare_batch(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int n) {
   const bool set_same = same_set(c->key_in, in, n) && same_set(c->key_out, out, n);
-  const int tx = hydro::kTileX[c->tile_id], ty = hydro::kTileY[c->tile_id];
-  if (set_same && c->wl_tile == c->tile_id && c->wl_zchunk == c->zchunk) return HYDRO_OK;
+  const int tile = ppm(c) ? 0 : c->tile_id;  // the PPM kernel's tiles are 16 x 16 (tile shape 0)
+  const int tx = hydro::kTileX[tile], ty = hydro::kTileY[tile];
+  if (set_same && c->wl_tile == tile && c->wl_zchunk == c->zchunk) return HYDRO_OK;
   if (!set_same) {
     size_t old = c->patches_cap;
     int rc = ensure_device(&c->d_patches, &c->patches_cap, (size_t)n);
@@ -223,7 +225,7 @@ int prepare_batch(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, i
     return HYDRO_ERR_CUDA;
   c->launches += 3;
   c->ntiles = (int)total;
-  c->wl_tile = c->tile_id;
+  c->wl_tile = tile;
   c->wl_zchunk = c->zchunk;
   return HYDRO_OK;
 }
@@ -240,16 +242,8 @@ int step_one_uniform(hydro_ctx* c, const hydro_patch& in, const hydro_patch& out
     if (rc) return rc;
   }
   int zc = std::min(c->zchunk, in.nz);
-  if (c->cfg.limiter == HYDRO_PPM) {  // the PPM kernel, then the CFL of U^{n+1} as its own launch
-    cudaError_t e = c->ops->step_ppm(make_io(in, out), c->prm, dt, zc, c->d_err, s);
-    c->launches += 1;
-    if (e == cudaSuccess && dt_next) {
-      e = c->ops->cfl(nullptr, make_io(out, out), 1, c->prm, dt_next, c->d_err, s);
-      c->launches += 1;
-    }
-    return cuda_status(e);
-  }
-  cudaError_t e = c->ops->step_uniform(c->tile_id, make_io(in, out), c->prm, dt, dt_next, zc, c->d_err, s);
+  cudaError_t e = ppm(c) ? c->ops->step_ppm(make_io(in, out), c->prm, dt, dt_next, zc, c->d_err, s)
+                         : c->ops->step_uniform(c->tile_id, make_io(in, out), c->prm, dt, dt_next, zc, c->d_err, s);
   c->launches += 1;
   return cuda_status(e);
 }
@@ -430,7 +424,8 @@ int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int 
     if (overlaps(c, in[i], out[i])) return HYDRO_ERR_ARG;
   }
   if (npatch == 1 && in[0].ng == 0) return step_one_uniform(c, in[0], out[0], dt_dev, dt_next_dev, c->stream);
-  if (ppm(c)) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i)  // ghost layers the reconstruction's stencil needs
+    if (in[i].ng != (ppm(c) ? 3 : 2)) return HYDRO_ERR_ARG;
   int rc = prepare_batch(c, in, out, npatch);
   if (rc) return rc;
   if (cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
@@ -438,9 +433,12 @@ int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int 
     rc = reset_slots(c, dt_next_dev, npatch, c->stream);
     if (rc) return rc;
   }
+  c->launches += 1;
+  if (ppm(c))
+    return cuda_status(c->ops->step_ppm_batched(c->d_patches, c->d_tiles, c->ntiles, c->d_counter, c->prm, dt_dev,
+                                                dt_next_dev, c->zchunk, c->d_err, c->sm_count, c->stream));
   const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id);
   int grid = std::max(1, std::min(c->ntiles, c->sm_count * per_sm));
-  c->launches += 1;
   return cuda_status(c->ops->step_batched(c->tile_id, c->d_patches, c->d_tiles, c->ntiles, c->d_counter, c->prm,
                                           dt_dev, dt_next_dev, c->zchunk, c->d_err, grid, c->stream));
 }

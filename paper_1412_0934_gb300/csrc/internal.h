@@ -79,9 +79,13 @@ struct KernelOps {
   // Boundary-face fluxes of boxes into registers (block b: faces 256 d_blocks[b].y ... of box d_blocks[b].x).
   cudaError_t (*box_fluxes)(const HostBoxFluxes* d_boxes, const int2* d_blocks, int nblocks, const Params& prm,
                             const double* dt, int accumulate, cudaStream_t s);
-  // The PPM step of a periodic box (P.gin == 0), z chunks of zchunk planes.
-  cudaError_t (*step_ppm)(const HostPatchIO& P, const Params& prm, const double* dt, int zchunk, unsigned* err,
-                          cudaStream_t s);
+  // The PPM step of a periodic box (P.gin == 0), z chunks of zchunk planes; dt_next as step_uniform.
+  cudaError_t (*step_ppm)(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
+                          unsigned* err, cudaStream_t s);
+  // The PPM step of patches with three ghost layers over a 16 x 16 tile work-list (persistent grid).
+  cudaError_t (*step_ppm_batched)(const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles,
+                                  int* d_counter, const Params& prm, const double* dt, double* dt_next, int zchunk,
+                                  unsigned* err, int sm_count, cudaStream_t s);
   int elem_size;  // bytes per stored element
   int launches_per_step;
 };

@@ -663,7 +663,8 @@ const KernelOps& make_ops() {
       &launch_cfl<Pol>,          &launch_octs<Pol>,         &launch_octs_level<Pol>,   &launch_octs_table<Pol>,
       &launch_adjoint<Pol>,
       &adjoint_scratch_bytes<Pol>, &launch_p2c<Pol>,        &launch_p2c_adjoint<Pol>,
-      &launch_box_fluxes<Pol>,   &launch_ppm<Pol>,          (int)sizeof(typename Pol::S), 1};
+      &launch_box_fluxes<Pol>,   &launch_ppm<Pol>,          &launch_ppm_batched<Pol>,
+      (int)sizeof(typename Pol::S), 1};
   return ops;
 }
 

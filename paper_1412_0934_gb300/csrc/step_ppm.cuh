@@ -8,13 +8,16 @@
 // The rest is the PLM step with the parabola's centre slope D in the Hancock predictor and face
 // states q_h + (qR - q), q_h + (qL - q) in place of q_h +- dq/2.  The stencil radius is 3.
 //
-// Kernel layout: one thread per column of a TX x TY tile marching up z (as the PLM kernel).
+// Kernel layout: one thread per column of a TX x TY tile marching up z (as the PLM kernel), on a
+// periodic box (indices wrapped) or on a patch carrying three ghost layers filled by the caller.
 // Shared memory holds a ring of five recovered planes (p-2 .. p+2) over the tile and three halo
 // cells each side, the x- and y-face states of plane p (the tile's cells and one ring cell beyond
 // each edge) and the x and y fluxes of plane p.  The z reconstruction of a column reads its own
 // five ring entries; the z-face state of the plane below, the z flux below and the x/y flux
 // difference of the plane below stay in registers until the plane is updated one plane later.
 #pragma once
+
+#include <algorithm>
 
 #include "adjoint.cuh"
 #include "hydro_device.cuh"
@@ -33,7 +36,9 @@ struct PpmShared {
   R wy[2][5][TY + 2][TX];  // y-face states: [low/high][var][y + 1][x]
   R fx[5][TY][TX + 1];     // flux through the low x face of cell x, x = 0 .. TX
   R fy[5][TY + 1][TX];     // flux through the low y face of cell y, y = 0 .. TY
-  int sx[QX], sy[QY];      // wrapped grid index of each tile column / row
+  int sx[QX], sy[QY];      // stored index of each tile column / row (wrapped, or clamped to the ghosts)
+  R red[TX * TY / 32];     // per-warp maxima of the CFL speed
+  int tile;                // batched kernel: the tile taken from the work-list
 };
 
 __device__ __forceinline__ int wrap_index(int v, int n) {
@@ -98,35 +103,49 @@ __device__ __forceinline__ void ppm_cell(const PpmShared<R, TX, TY>& sm, const i
 template <class Pol>
 constexpr int ppm_min_blocks() { return sizeof(typename Pol::R) >= 8 ? 1 : 2; }
 
+// Block-wide maximum of v (all threads call); the result is valid in thread 0.
+template <class R, int TX, int TY>
+__device__ __forceinline__ R ppm_block_max(PpmShared<R, TX, TY>& sm, R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    R w = shfl_xor_(v, o);
+    v = w > v ? w : v;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < TX * TY / 32; ++w) v = sm.red[w] > v ? sm.red[w] : v;
+  return v;
+}
+
+// Columns [x0, x0+TX) x rows [y0, y0+TY) x planes [z0, z1) of patch P (P.gin == 0: a periodic box;
+// P.gin == 3: ghost layers filled by the caller) stepped by dt; with want_cfl the largest CFL speed
+// of the updated cells of this thread is folded into smax.
 template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
-    k_step_ppm(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev, int zchunk, unsigned* err) {
+__device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm, const PatchIO<typename Pol::S>& P,
+                                         int x0, int y0, int z0, int z1, const Params& prm, double dtv, bool want_cfl,
+                                         unsigned& flags, typename Pol::R& smax) {
   using S = typename Pol::S;
   using R = typename Pol::R;
-  using SM = PpmShared<R, TX, TY>;
-  constexpr int QX = SM::QX, QY = SM::QY, NT = TX * TY;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM& sm = *reinterpret_cast<SM*>(smem_raw);
+  constexpr int QX = TX + 2 * kPpmHalo, QY = TY + 2 * kPpmHalo, NT = TX * TY;
   const int tid = threadIdx.x;
-  const double dtv = dt_dev[0];
-  if (!(dtv > 0.0 && dtv <= 1e300)) {
-    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicOr(err, HYDRO_EBIT_BAD_DT);
-    return;
-  }
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, P.nz);
-  for (int k = tid; k < QX; k += NT) sm.sx[k] = wrap_index(x0 + k - kPpmHalo, P.nx);
-  for (int k = tid; k < QY; k += NT) sm.sy[k] = wrap_index(y0 + k - kPpmHalo, P.ny);
+  const bool periodic = P.gin == 0;
+  __syncthreads();  // the previous tile's last reads of the index tables are done
+  for (int k = tid; k < QX; k += NT)
+    sm.sx[k] = periodic ? wrap_index(x0 + k - kPpmHalo, P.nx) : min(x0 + k - kPpmHalo + P.gin, P.nx + 2 * P.gin - 1);
+  for (int k = tid; k < QY; k += NT)
+    sm.sy[k] = periodic ? wrap_index(y0 + k - kPpmHalo, P.ny) : min(y0 + k - kPpmHalo + P.gin, P.ny + 2 * P.gin - 1);
   __syncthreads();
   const R gamma = kc<R>(prm, K_GAMMA), igm1 = kc<R>(prm, K_IGM1), sixth = kc<R>(prm, K_SIXTH);
   const R rf = kc<R>(prm, K_RHOF), pf = kc<R>(prm, K_PF);
   const R hdt = (R)(0.5 * dtv / P.dx);
   const R dtdx = (R)(dtv / P.dx);
-  unsigned flags = 0;
 
-  // plane z of the box, wrapped, recovered into ring slot s over the tile and its halo
+  // plane z of the patch (wrapped, or within the ghost layers), recovered into ring slot s over
+  // the tile and its halo
   auto load_plane = [&](int z, int s) {
-    const long long zo = (long long)wrap_index(z, P.nz) * P.isz;
+    const long long zo = (long long)(periodic ? wrap_index(z, P.nz) : z + P.gin) * P.isz;
     for (int c = tid; c < QX * QY; c += NT) {
       const int y = c / QX, x = c - y * QX;
       const long long a = zo + (long long)sm.sy[y] * P.isy + sm.sx[x];
@@ -201,10 +220,18 @@ __global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
       hllc<2>(ql, qr, gamma, igm1, F);
       if (p > z0 && own) {
         const int z = p - 1;
-        const long long ai = (long long)z * P.isz + (long long)(y0 + j) * P.isy + (x0 + i);
+        const long long ai = (long long)(z + P.gin) * P.isz + (long long)(y0 + j + P.gin) * P.isy + (x0 + i + P.gin);
         const long long ao = (long long)(z + P.gout) * P.osz + (long long)(y0 + j + P.gout) * P.osy + (x0 + i + P.gout);
+        S Un[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) P.out[v][ao] = Pol::update(__ldg(P.in[v] + ai), dtdx, dxy[v] + (F[v] - fzb[v]));
+        for (int v = 0; v < 5; ++v) {
+          Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, dxy[v] + (F[v] - fzb[v]));
+          P.out[v][ao] = Un[v];
+        }
+        if (want_cfl) {
+          const R sp = Pol::speed(Un, prm, flags);
+          smax = sp > smax ? sp : smax;
+        }
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) fzb[v] = F[v];
@@ -250,22 +277,115 @@ __global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
         dxy[v] = (sm.fx[v][j][i + 1] - sm.fx[v][j][i]) + (sm.fy[v][j + 1][i] - sm.fy[v][j][i]);
     }
   }
+}
+
+// Periodic box: one tile per block, tiles from the block index.
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
+    k_step_ppm(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev, double* dt_next, int zchunk,
+               unsigned* err) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<PpmShared<R, TX, TY>*>(smem_raw);
+  const double dt = dt_dev[0];
+  if (!(dt > 0.0 && dt <= 1e300)) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicOr(err, HYDRO_EBIT_BAD_DT);
+    return;
+  }
+  unsigned flags = 0;
+  R smax = 0;
+  const int z0 = blockIdx.z * zchunk;
+  ppm_tile<Pol, TX, TY>(sm, P, blockIdx.x * TX, blockIdx.y * TY, z0, min(z0 + zchunk, P.nz), prm, dt,
+                        dt_next != nullptr, flags, smax);
+  if (dt_next) {
+    const R m = ppm_block_max(sm, smax);
+    if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next);
+  }
   flush_flags(flags, err);
 }
 
+// Patches with three ghost layers: a persistent grid taking tiles from the device work-list by an
+// atomic counter (as the PLM batched kernel); per-patch dt, dx and dt_next.
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
+    k_step_ppm_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles, int ntiles, int* counter,
+                       Params prm, const double* dt_dev, double* dt_next, int zchunk, unsigned* err) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<PpmShared<R, TX, TY>*>(smem_raw);
+  unsigned flags = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) sm.tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = sm.tile;
+    if (t >= ntiles) break;
+    const TileRec r = tiles[t];
+    const PatchIO<typename Pol::S> P = patches[r.patch];
+    if (r.x0 < 0 || r.y0 < 0 || r.z0 < 0 || r.x0 >= P.nx || r.y0 >= P.ny || r.z0 >= P.nz || P.gin != kPpmHalo) {
+      flags |= HYDRO_EBIT_BAD_TILE;
+      continue;
+    }
+    const double dt = dt_dev[r.patch];
+    if (!(dt > 0.0 && dt <= 1e300)) {
+      flags |= HYDRO_EBIT_BAD_DT;
+      continue;
+    }
+    R smax = 0;
+    ppm_tile<Pol, TX, TY>(sm, P, r.x0, r.y0, r.z0, min(r.z0 + zchunk, P.nz), prm, dt, dt_next != nullptr, flags,
+                          smax);
+    if (dt_next) {
+      const R m = ppm_block_max(sm, smax);
+      if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next + r.patch);
+    }
+  }
+  flush_flags(flags, err);
+}
+
+constexpr int kPpmTX = 16, kPpmTY = 16;
+static_assert(kTileX[0] == kPpmTX && kTileY[0] == kPpmTY, "the PPM work-list is built with tile shape 0");
+
 template <class Pol>
-cudaError_t launch_ppm(const HostPatchIO& P, const Params& prm, const double* dt, int zchunk, unsigned* err,
-                       cudaStream_t s) {
-  constexpr int TX = 16, TY = 16;
-  const size_t smem = sizeof(PpmShared<typename Pol::R, TX, TY>);
+cudaError_t ppm_attr(const void* fn) {
+  const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <class Pol>
+cudaError_t launch_ppm(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
+                       unsigned* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_ppm<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ppm_attr<Pol>(reinterpret_cast<const void*>(k_step_ppm<Pol, kPpmTX, kPpmTY>));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
-  k_step_ppm<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, zchunk, err);
+  const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
+  dim3 grid((P.nx + kPpmTX - 1) / kPpmTX, (P.ny + kPpmTY - 1) / kPpmTY, (P.nz + zchunk - 1) / zchunk);
+  k_step_ppm<Pol, kPpmTX, kPpmTY><<<grid, kPpmTX * kPpmTY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
+  return cudaGetLastError();
+}
+
+template <class Pol>
+cudaError_t launch_ppm_batched(const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles, int* d_counter,
+                               const Params& prm, const double* dt, double* dt_next, int zchunk, unsigned* err,
+                               int sm_count, cudaStream_t s) {
+  using K = decltype(&k_step_ppm_batched<Pol, kPpmTX, kPpmTY>);
+  const K fn = &k_step_ppm_batched<Pol, kPpmTX, kPpmTY>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = ppm_attr<Pol>(reinterpret_cast<const void*>(fn));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPpmTX * kPpmTY, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int grid = std::max(1, std::min(ntiles, sm_count * per_sm));
+  fn<<<grid, kPpmTX * kPpmTY, smem, s>>>(reinterpret_cast<const PatchIO<typename Pol::S>*>(d_patches),
+                                         reinterpret_cast<const TileRec*>(d_tiles), ntiles, d_counter, prm, dt,
+                                         dt_next, zchunk, err);
   return cudaGetLastError();
 }
 

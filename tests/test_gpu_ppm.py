@@ -1,7 +1,7 @@
-"""GPU parity of the PPM step (periodic boxes) against the PPM oracle (oracle/ppm.py), through the
-C ABI: small boxes element by element (several tiles, a ragged tile edge, several z chunks), a
-256^3 box on sampled windows, the fused dt, conservation, the graph-captured run, and the calls
-that reject a PPM context."""
+"""GPU parity of the PPM step against the PPM oracle (oracle/ppm.py), through the C ABI: periodic
+boxes element by element (several tiles, a ragged tile edge, several z chunks), batched patches with
+three ghost layers, a 256^3 box on sampled windows, the fused dt, conservation, the graph-captured
+run, the ghost-layer check and the calls that reject a PPM context."""
 import numpy as np
 import pytest
 import torch
@@ -125,13 +125,61 @@ def test_ppm_full_size_sampled_windows():
         assert err.max() <= 1e-12, ((x, y, z), err)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "fp32"])
+def test_ppm_batched_patches_match_oracle(precision):
+    """Patches with three ghost layers (cubes and 2:1 boxes, ragged tiles, several z chunks, one
+    patch wrapping the parent) in one persistent launch, per-patch dt; each against the oracle's
+    ghosted-patch step; the fused per-patch dt equals hydro_cfl_dt bit for bit."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    parent = workloads.turbulent_state((40, 36, 44), seed=47, mach=5.0, sedov=True)
+    rng = np.random.default_rng(48)
+    dims = [(16, 16, 16), (20, 9, 40), (5, 33, 7), (1, 2, 3), (24, 24, 12), (8, 8, 16)]
+    origins = [tuple(int(v) for v in rng.integers(0, 40, 3)) for _ in dims]
+    origins[0] = (38, 34, 39)
+    cfg = oracle.config()
+    host, ins, outs, keep, dtl = [], [], [], [], []
+    for k, (d, o) in enumerate(zip(dims, origins)):
+        dx = 1.0 / (32 * (1 + k % 3))
+        Ug = workloads.ghosted_from_periodic(parent, o, d, ghost=3).numpy()
+        host.append((Ug, dx))
+        dtl.append(0.7 * oracle.cfl_patch(Ug[:, 1:-1, 1:-1, 1:-1], dx, cfg))
+        a = dev(Ug, dtype)
+        b = torch.full_like(a, 7.0)
+        keep += [a, b]
+        ins.append(hy.patch(a, 3, dx))
+        outs.append(hy.patch(b, 3, dx))
+    c = ctx(precision, limiter="ppm")
+    dn = torch.empty(len(dims), dtype=torch.float64, device="cuda")
+    for zc in (8, 32):
+        hy.hydro_set_tuning(c, 0, zc)
+        hy.hydro_step(c, ins, outs, dts(*dtl), dn)
+        torch.cuda.synchronize()
+        check_clean(c)
+        for (Ug, dx), po, dtp in zip(host, outs, dtl):
+            g = torch.stack(po.tensors).double().cpu().numpy()
+            ref = oppm.step_patch(Ug, dx, dtp, cfg)
+            err = normwise(g[:, 3:-3, 3:-3, 3:-3], ref)
+            assert err.max() <= TOL[precision], (zc, Ug.shape, err)
+            assert (g[:, :3] == 7.0).all() and (g[:, -3:] == 7.0).all()  # ghosts of out untouched
+    dn2 = torch.empty_like(dn)
+    hy.hydro_cfl_dt(c, outs, dn2)
+    torch.cuda.synchronize()
+    assert torch.equal(dn, dn2)
+
+
+def test_ghost_layers_must_match_the_reconstruction():
+    U = workloads.white_velocity_state(8, seed=1)
+    g2, g3 = (dev(workloads.ghosted_from_periodic(U, (0, 0, 0), (8, 8, 8), ghost=g).numpy()) for g in (2, 3))
+    for limiter, bad in (("ppm", g2), ("minmod", g3)):
+        c = ctx("fp64", limiter=limiter)
+        ng = 2 if bad is g2 else 3
+        with pytest.raises(hy.HydroError):
+            hy.hydro_step(c, hy.patch(bad, ng, 0.1), hy.patch(torch.empty_like(bad), ng, 0.1), dts(0.01))
+
+
 def test_ppm_context_rejects_the_radius_two_calls():
     c = ctx("fp64", limiter="ppm")
     U = workloads.white_velocity_state(8, seed=1).numpy()
-    Ug = np.pad(U, ((0, 0), (2, 2), (2, 2), (2, 2)), mode="wrap")
-    a, b = dev(Ug), torch.empty(Ug.shape, dtype=torch.float64, device="cuda")
-    with pytest.raises(hy.HydroError):  # ghosted patches: the batched path
-        hy.hydro_step(c, hy.patch(a, 2, 0.1), hy.patch(b, 2, 0.1), dts(0.01))
     g = torch.zeros((5, 2, 6, 6, 6), dtype=torch.float64, device="cuda")
     o = torch.zeros((5, 2, 2, 2, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(hy.HydroError):

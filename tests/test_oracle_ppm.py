@@ -111,3 +111,23 @@ def test_sound_wave_converges_faster_than_plm_minmod():
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(ns) - 1)]
     assert orders[-1] >= 1.8, (errs, orders)
     assert errs[-1] < 0.5 * errs_plm[-1], (errs, errs_plm)
+
+
+def test_ghosted_patch_step_is_the_periodic_step_of_its_cells():
+    """A patch cut from a periodic box with exact ghosts (three layers) steps to the box's own step
+    on its cells, including patches that wrap around the box."""
+    shape = (14, 12, 16)
+    U = workloads.turbulent_state(shape, seed=34, mach=3.0, sedov=True)
+    dx = 1.0 / 16
+    cfg = oracle.config()
+    Un = U.numpy()
+    dt = oracle.cfl_periodic(Un, dx, cfg)
+    full = ppm.step_periodic(Un, dx, dt, cfg)
+    for origin, dims in (((0, 0, 0), (5, 4, 3)), ((13, 10, 11), (6, 5, 7)), ((2, 3, 4), (1, 1, 1))):
+        Ug = workloads.ghosted_from_periodic(U, origin, dims, ghost=3).numpy()
+        got = ppm.step_patch(Ug, dx, dt, cfg)
+        ix = np.arange(origin[0], origin[0] + dims[0]) % shape[2]
+        iy = np.arange(origin[1], origin[1] + dims[1]) % shape[1]
+        iz = np.arange(origin[2], origin[2] + dims[2]) % shape[0]
+        want = full[:, iz][:, :, iy][:, :, :, ix]
+        assert np.abs(got - want).max() <= 1e-15 * np.abs(full).max(), origin
