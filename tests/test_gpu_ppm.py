@@ -131,7 +131,9 @@ def test_ppm_batched_patches_match_oracle(precision):
     patch wrapping the parent) in one persistent launch, per-patch dt; each against the oracle's
     ghosted-patch step; the fused per-patch dt equals hydro_cfl_dt bit for bit."""
     dtype = torch.float32 if precision == "fp32" else torch.float64
-    parent = workloads.turbulent_state((40, 36, 44), seed=47, mach=5.0, sedov=True)
+    # Mach 3: at Mach 5 one PPM step leaves a few cells of these patches with negative internal
+    # energy (in the oracle as well), which the fused CFL's recovery flags
+    parent = workloads.turbulent_state((40, 36, 44), seed=47, mach=3.0, sedov=True)
     rng = np.random.default_rng(48)
     dims = [(16, 16, 16), (20, 9, 40), (5, 33, 7), (1, 2, 3), (24, 24, 12), (8, 8, 16)]
     origins = [tuple(int(v) for v in rng.integers(0, 40, 3)) for _ in dims]
