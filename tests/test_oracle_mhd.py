@@ -1,0 +1,178 @@
+"""Pins of the MHD oracle (oracle/mhd.py): the flux against the pinned hydro flux at B = 0 and its
+tensor symmetries, the fast speed's closed forms, HLL consistency, the GLM face solution's
+characteristic invariants, uniform flow, conservation, the decay of a divergence error, and the
+convergence of an exact circularly polarised Alfven wave."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mhd
+
+
+def rand_prim(rng, shape=(), b=1.0):
+    q = np.empty((9,) + shape)
+    q[0] = rng.uniform(0.5, 2.0, shape)
+    q[1:4] = rng.normal(0, 0.7, (3,) + shape)
+    q[4] = rng.uniform(0.1, 1.5, shape)
+    q[5:8] = rng.normal(0, b, (3,) + shape)
+    q[8] = rng.normal(0, 0.2, shape)
+    return q
+
+
+def test_flux_at_zero_field_is_the_hydro_flux():
+    cfg = oracle.config()
+    rng = np.random.default_rng(51)
+    for _ in range(10):
+        q = rand_prim(rng, b=0.0)
+        q[8] = 0.0
+        for d in range(3):
+            F = mhd.flux(q, d, 1.3, cfg)
+            h = oracle.hllc(q[:5], q[:5], d, cfg)  # HLLC of equal states: the physical Euler flux
+            np.testing.assert_allclose(F[:5], h, rtol=1e-14, atol=1e-14)
+            assert np.all(F[5:8] == 0.0) and F[8] == 0.0
+
+
+def test_flux_tensor_symmetries():
+    """The momentum flux (Reynolds + Maxwell stress) is symmetric in (axis, component); the
+    induction flux u_d B_k - u_k B_d is antisymmetric; the energy flux matches its definition
+    through the conserved state."""
+    cfg = oracle.config()
+    rng = np.random.default_rng(52)
+    q = rand_prim(rng, (50,))
+    F = [mhd.flux(q, d, 0.7, cfg) for d in range(3)]
+    for d in range(3):
+        for k in range(3):
+            np.testing.assert_allclose(F[d][1 + k], F[k][1 + d], rtol=1e-13, atol=1e-13)
+            if k != d:
+                np.testing.assert_allclose(F[d][5 + k], -F[k][5 + d], rtol=1e-13, atol=1e-13)
+    U = mhd.conserved(q, cfg)
+    pt = q[4] + 0.5 * (q[5] ** 2 + q[6] ** 2 + q[7] ** 2)
+    uB = q[1] * q[5] + q[2] * q[6] + q[3] * q[7]
+    for d in range(3):
+        np.testing.assert_allclose(F[d][4], (U[4] + pt) * q[1 + d] - q[5 + d] * uB, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(F[d][0], U[1 + d], rtol=1e-15)
+
+
+def test_fast_speed_closed_forms():
+    cfg = oracle.config()
+    rng = np.random.default_rng(53)
+    q = rand_prim(rng, (20,))
+    a2 = cfg.gamma * q[4] / q[0]
+    for d in range(3):
+        par = q.copy()
+        par[5:8] = 0.0
+        par[5 + d] = q[5 + d]  # field along the axis: c_f = max(a, |B|/sqrt(rho))
+        # (where a ~ b the root of (a^2 + b^2)^2 - 4 a^2 b^2 = (a^2 - b^2)^2 cancels: a few 1e-14)
+        np.testing.assert_allclose(mhd.fast_speed(par, d, cfg), np.sqrt(np.maximum(a2, par[5 + d] ** 2 / q[0])),
+                                   rtol=1e-12)
+        perp = q.copy()
+        perp[5 + d] = 0.0  # field across the axis: c_f^2 = a^2 + b^2
+        b2 = (perp[5] ** 2 + perp[6] ** 2 + perp[7] ** 2) / q[0]
+        np.testing.assert_allclose(mhd.fast_speed(perp, d, cfg), np.sqrt(a2 + b2), rtol=1e-14)
+
+
+def test_hll_consistency_and_upwinding():
+    cfg = oracle.config()
+    rng = np.random.default_rng(54)
+    for _ in range(10):
+        q = rand_prim(rng)
+        for d in range(3):
+            np.testing.assert_allclose(mhd.hll(q, q, d, 0.9, cfg), mhd.flux(q, d, 0.9, cfg), rtol=1e-14, atol=1e-14)
+    # supersonic, super-Alfvenic flow along +x with the same normal field and psi on both sides:
+    # the flux is the left state's
+    qL, qR = rand_prim(rng), rand_prim(rng)
+    qL[1] = qR[1] = 50.0
+    qR[5], qR[8] = qL[5], qL[8]
+    np.testing.assert_allclose(mhd.hll(qL, qR, 0, 0.5, cfg), mhd.flux(qL, 0, 0.5, cfg), rtol=1e-14, atol=1e-12)
+
+
+def test_glm_face_characteristic_invariants():
+    """psi + c_h B_n is carried right from the left state, psi - c_h B_n left from the right one."""
+    rng = np.random.default_rng(55)
+    BL, BR, pL, pR = rng.normal(size=(4, 100))
+    ch = 1.7
+    Bm, pm = mhd.glm_face(BL, BR, pL, pR, ch)
+    np.testing.assert_allclose(pm + ch * Bm, pL + ch * BL, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(pm - ch * Bm, pR - ch * BR, rtol=1e-13, atol=1e-13)
+
+
+def test_uniform_state_unchanged_and_conservation():
+    cfg = oracle.config()
+    shape = (6, 8, 10)
+    q = np.stack([np.full(shape, v) for v in (1.2, 0.3, -0.2, 0.1, 0.6, 0.8, -0.4, 0.5, 0.0)])
+    U = mhd.conserved(q, cfg)
+    dt = mhd.cfl_periodic(U, 0.1, cfg)
+    np.testing.assert_allclose(mhd.step_periodic(U, 0.1, dt, cfg), U, rtol=1e-14, atol=1e-15)
+    rng = np.random.default_rng(56)
+    q = rand_prim(rng, (8, 6, 10), b=0.5)
+    U = mhd.conserved(q, cfg)
+    dt = mhd.cfl_periodic(U, 0.1, cfg)
+    V = U.copy()
+    for _ in range(4):
+        V = mhd.step_periodic(V, 0.1, dt, cfg)
+    tot0, tot = U.sum(axis=(1, 2, 3)), V.sum(axis=(1, 2, 3))
+    scale = np.abs(U).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(tot - tot0)[:8] / scale[:8] <= 1e-13)
+    # psi: the fluxes conserve it, the damping scales it by a constant factor each step
+    f = math.exp(-mhd.ALPHA * cfg.cfl / 3.0)
+    W = U.copy()
+    s = W[8].sum()
+    for _ in range(4):
+        W = mhd.step_periodic(W, 0.1, dt, cfg)
+        s *= f
+    assert abs(W[8].sum() - s) <= 1e-12 * np.abs(U[8]).sum()
+
+
+def test_divergence_error_decays():
+    """A divergence error in B (a Gaussian bump of B_x along x) is carried off by the cleaning waves
+    and damped; with the wrong sign in the cleaning system it would grow."""
+    cfg = oracle.config()
+    n = 32
+    x = (np.arange(n) + 0.5) / n
+    shape = (4, 4, n)
+    q = np.zeros((9,) + shape)
+    q[0], q[4] = 1.0, 1.0
+    q[5] = 0.5 + 0.3 * np.exp(-((x - 0.5) / 0.08) ** 2)[None, None, :]
+    q[6] = 0.2
+    U = mhd.conserved(q, cfg)
+    dx = 1.0 / n
+    e0 = np.sqrt((mhd.div_b(U, dx) ** 2).mean())
+    E0 = U[4].sum()
+    for _ in range(60):
+        U = mhd.step_periodic(U, dx, mhd.cfl_periodic(U, dx, cfg), cfg)
+    e1 = np.sqrt((mhd.div_b(U, dx) ** 2).mean())
+    assert e1 < 0.2 * e0, (e0, e1)
+    assert abs(U[4].sum() - E0) <= 1e-12 * E0
+
+
+def cp_alfven(n, A=0.1):
+    """Circularly polarised Alfven wave along x (an exact solution of ideal MHD): rho = 1, p = 0.1,
+    B_x = 1, B_perp = A (sin, cos)(2 pi x), v_perp = -B_perp; it moves at v_A = 1 (period 1)."""
+    x = (np.arange(n) + 0.5) / n
+    ph = 2 * np.pi * x
+    shape = (4, 4, n)
+    q = np.zeros((9,) + shape)
+    q[0], q[4], q[5] = 1.0, 0.1, 1.0
+    q[6] = A * np.sin(ph)
+    q[7] = A * np.cos(ph)
+    q[2], q[3] = -q[6], -q[7]
+    return q
+
+
+@pytest.mark.parametrize("limiter,min_order", [("none", 1.9), ("mc", 1.8)])
+def test_circularly_polarised_alfven_wave_converges(limiter, min_order):
+    cfg = oracle.config()
+    errs = []
+    for n in (16, 32, 64):
+        U0 = mhd.conserved(cp_alfven(n), cfg)
+        U, t, dx = U0.copy(), 0.0, 1.0 / n
+        while t < 1.0 - 1e-14:
+            dt = min(mhd.cfl_periodic(U, dx, cfg), 1.0 - t)
+            U = mhd.step_periodic(U, dx, dt, cfg, limiter=limiter)
+            t += dt
+        errs.append(np.abs(U[6] - U0[6]).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] >= min_order, (errs, orders)
+    assert errs[-1] < 2e-3, errs
