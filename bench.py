@@ -564,6 +564,43 @@ def form_ppm_batched(hy, steps, warmup, npatch=4096, precision="mixed"):
     return out
 
 
+def form_mhd(hy, precision, steps, warmup, n=256):
+    """Ideal MHD with GLM cleaning on an n^3 periodic box (smooth magnetised gas, plasma beta 0.5,
+    rms Mach 2): steps chained through the fused dt."""
+    import workloads
+    stream = torch.cuda.current_stream()
+    ctx = hy.hydro_init(precision=precision, limiter="minmod")
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    a = workloads.mhd_state(n, seed=7, beta=0.5, mach=2.0, device="cuda").to(dtype).contiguous()
+    b = torch.empty_like(a)
+    dx = 1.0 / n
+    dts = torch.empty(warmup + steps + 1, dtype=torch.float64, device="cuda")
+    hy.hydro_mhd_cfl_dt(ctx, a, dx, dts[0:1])
+    for i in range(warmup):
+        hy.hydro_mhd_step(ctx, a, b, dx, dts[i:i + 1], dts[i + 1:i + 2])
+        a, b = b, a
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        k = warmup + i
+        hy.hydro_mhd_step(ctx, a, b, dx, dts[k:k + 1], dts[k + 1:k + 2])
+        a, b = b, a
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    rc, bits = hy.hydro_get_error(ctx)
+    hbm, src = peaks()
+    es = 4 if precision == "fp32" else 8
+    out = {"cells": n ** 3, "steps": steps, "ms_per_step": ms, "mcell_updates_per_s": n ** 3 / (ms / 1e3) / 1e6,
+           "hbm_frac": n ** 3 * 2 * 9 * es / (ms / 1e3) / 1e9 / hbm, "launches_per_step": 4, "error_bits": bits,
+           "note": "three kernels (predict, face fluxes, update + fused dt) with 81 scratch elements per cell"}
+    del a, b
+    hy.hydro_finalize(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
 def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
     """One two-level AMR cycle, mixed precision: a 256^3 fine level tiled by 16^3 patches of random
     even edges (cuts at random even positions per axis) over a 128^3 coarse level.  Per cycle: the
@@ -794,7 +831,7 @@ def reference_arm(args):
 def run_forms(hy, args, n, precision):
     """The extra forms beside the headline (each failure reported, not fatal)."""
     forms = [] if args.forms == "none" else (
-        ["fp64", "fp32", "ppm", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all"
+        ["fp64", "fp32", "ppm", "mhd", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all"
         else args.forms.split(","))
     forms = [f for f in forms if f != precision]
     extra = {}
@@ -819,6 +856,9 @@ def run_forms(hy, args, n, precision):
                 for prec in ("df64", "fp32"):
                     extra["ppm_%d_%s" % (n, prec)] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None)
                 extra["ppm_batched_mixed"] = form_ppm_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch)
+            elif f == "mhd":
+                for prec in ("fp64", "fp32"):
+                    extra["mhd_256_" + prec] = form_mhd(hy, prec, args.steps, args.warmup)
             elif f == "graph1024":
                 extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                            sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,

@@ -260,6 +260,26 @@ int hydro_octs_build(hydro_ctx* ctx, const int* pos_dev, int noct, const int dim
 int hydro_step_octs_table(hydro_ctx* ctx, void* const in[5], void* const out[5], int noct, const int* nbr_dev,
                           const int* list_dev, long long ngroups, double dx, const double* dt_dev);
 
+/* Ideal magnetohydrodynamics on a periodic box, the second workload (the paper's Enzo runs MHD on
+ * the GPU, Sec. 4; it prints no equations).  Nine fields, each a device array of nx*ny*nz elements,
+ * x fastest: rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi, with E = p/(gamma-1) + |m|^2/(2 rho) +
+ * |B|^2/2 (magnetic pressure |B|^2/2) and psi the scalar of hyperbolic divergence cleaning
+ * (Dedner et al. 2002).  One step: primitive variables (rho, u, v, w, p, B, psi) reconstructed
+ * with the context's PLM limiter; conservative unsplit Hancock predictor (each extrapolated state
+ * minus dt/(2 dx) times the sum over axes of the flux differences of the cell's own extrapolated
+ * states), recovered and floored; HLL fluxes with Davis bounds from the fast magnetosonic speed,
+ * the normal field and psi at each face from the 2x2 cleaning system with c_h = (cfl/3) dx/dt;
+ * conservative update; psi scaled by exp(-0.4 c_h dt/dx).
+ *   hydro_mhd_step: out <- U^{n+1} of in with time step dt_dev[0]; in and out must not overlap;
+ *       dt_next_dev: NULL or one double receiving cfl dx / max_cells sum_d (|u_d| + c_f,d) of U^{n+1}.
+ *       Device scratch of 81 elements per cell (face states and fluxes) is owned by the context.
+ *   hydro_mhd_cfl_dt: dt_dev[0] <- the same CFL dt of U (bit-identical to the fused one).
+ * Element type: double in a HYDRO_FP64 context, float in HYDRO_FP32; other precisions and HYDRO_PPM
+ * return HYDRO_ERR_ARG, as do sizes with nx*ny*nz >= 2^31.  Floors and error bits as the hydro step. */
+int hydro_mhd_step(hydro_ctx* ctx, void* const in[9], void* const out[9], int nx, int ny, int nz, double dx,
+                   const double* dt_dev, double* dt_next_dev);
+int hydro_mhd_cfl_dt(hydro_ctx* ctx, void* const U[9], int nx, int ny, int nz, double dx, double* dt_dev);
+
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
  * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64,
  * HYDRO_FP64_DF (which runs the FP64 reverse sweep: faster on GB300 than a double-float one) or

@@ -38,7 +38,7 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_fill_ghosts", "hydro_fill_ghosts_time", "hydro_exchange_ghosts", "hydro_patch_fluxes",
+           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_mhd_step", "hydro_mhd_cfl_dt", "hydro_fill_ghosts", "hydro_fill_ghosts_time", "hydro_exchange_ghosts", "hydro_patch_fluxes",
            "hydro_level_fluxes", "hydro_reflux", "hydro_average_down",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
@@ -85,6 +85,8 @@ def lib():
         L.hydro_step_octs.argtypes = [vp, vp * 5, vp * 5, ll, d, vp]
         L.hydro_step_octs_level.argtypes = [vp, PP, vp, ll, vp * 5, vp]
         L.hydro_octs_build.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_int), vp, vp]
+        L.hydro_mhd_step.argtypes = [vp, vp * 9, vp * 9, i, i, i, d, vp, vp]
+        L.hydro_mhd_cfl_dt.argtypes = [vp, vp * 9, i, i, i, d, vp]
         L.hydro_step_octs_table.argtypes = [vp, vp * 5, vp * 5, i, vp, vp, ll, d, vp]
         L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
         L.hydro_fill_ghosts_time.argtypes = [vp, PP, PP, d, PP, ctypes.POINTER(ctypes.c_int), i]
@@ -364,6 +366,29 @@ def hydro_step_octs_table(ctx, U, out, nbr, octs, dx, dt):
             raise ValueError("oct arrays must be contiguous per field")
     _check(lib().hydro_step_octs_table(ctx.handle, i, o, nbr.shape[0], _ptr(nbr), _ptr(octs), octs.shape[0],
                                        float(dx), _ptr(dt)), "hydro_step_octs_table")
+
+
+def _mhd_fields(U):
+    if len(U) != 9:
+        raise ValueError("MHD state: nine fields (rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi)")
+    for v in range(9):
+        if not U[v].is_contiguous() or U[v].shape != U[0].shape or U[v].dim() != 3:
+            raise ValueError("MHD fields must be contiguous (nz, ny, nx) tensors of one shape")
+    nz, ny, nx = U[0].shape
+    return (ctypes.c_void_p * 9)(*[_ptr(U[v]) for v in range(9)]), nx, ny, nz
+
+
+def hydro_mhd_step(ctx, U, out, dx, dt, dt_next=None):
+    """U, out: (9, nz, ny, nx) tensors (or 9 tensors) of a periodic box; dt: device double."""
+    a, nx, ny, nz = _mhd_fields(U)
+    b, *_ = _mhd_fields(out)
+    _check(lib().hydro_mhd_step(ctx.handle, a, b, nx, ny, nz, float(dx), _ptr(dt),
+                                _ptr(dt_next) if dt_next is not None else None), "hydro_mhd_step")
+
+
+def hydro_mhd_cfl_dt(ctx, U, dx, dt):
+    a, nx, ny, nz = _mhd_fields(U)
+    _check(lib().hydro_mhd_cfl_dt(ctx.handle, a, nx, ny, nz, float(dx), _ptr(dt)), "hydro_mhd_cfl_dt")
 
 
 def hydro_step_octs(ctx, gathered, out, dx, dt):

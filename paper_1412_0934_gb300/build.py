@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC,
          "--expt-relaxed-constexpr"]
 SOURCES = ["hydro_api.cu", "worklist.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_mixed.cu", "kernels_df.cu", "noalloc.cu",
-           "ghosts.cu", "octs_build.cu"]
+           "ghosts.cu", "octs_build.cu", "mhd.cu"]
 
 
 def _headers():

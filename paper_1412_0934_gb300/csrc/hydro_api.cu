@@ -93,6 +93,9 @@ struct hydro_ctx {
   // oct builder scratch: key bitmap, word prefix sums, block prefix sums
   unsigned* d_octs_scratch = nullptr;
   size_t octs_scratch_cap = 0;
+  // MHD step scratch: constants, face states, fluxes
+  char* d_mhd = nullptr;
+  size_t mhd_cap = 0;
   long long launches = 0;
 };
 
@@ -373,6 +376,7 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_tasks);
   for (int k = 0; k < hydro_ctx::kAux; ++k) cudaFree(c->d_aux[k]);
   cudaFree(c->d_octs_scratch);
+  cudaFree(c->d_mhd);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
@@ -949,6 +953,59 @@ int hydro_step_octs_table(hydro_ctx* c, void* const in[5], void* const out[5], i
   c->launches += 1;
   return cuda_status(
       c->ops->octs_table(in, nbr_dev, noct, list_dev, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
+}
+
+// Arguments of the MHD calls: a periodic box of nine contiguous fields in a FP64 or FP32 context
+// with a PLM limiter.
+static bool mhd_args(const hydro_ctx* c, void* const* U, int nx, int ny, int nz, double dx) {
+  if (!c || !U || nx < 1 || ny < 1 || nz < 1 || !finite_pos(dx)) return false;
+  if ((long long)nx * ny * nz > 0x7fffffffLL) return false;
+  if (c->cfg.precision != HYDRO_FP64 && c->cfg.precision != HYDRO_FP32) return false;
+  if (ppm(c)) return false;
+  const int es = elem_size(c);
+  for (int v = 0; v < 9; ++v)
+    if (!U[v] || reinterpret_cast<uintptr_t>(U[v]) % es) return false;
+  return true;
+}
+
+static hydro::HostMhdBox mhd_box(void* const* in, void* const* out, int nx, int ny, int nz, double dx) {
+  hydro::HostMhdBox h;
+  for (int v = 0; v < 9; ++v) {
+    h.in[v] = in[v];
+    h.out[v] = out ? out[v] : nullptr;
+  }
+  h.nx = nx; h.ny = ny; h.nz = nz;
+  h.dx = dx;
+  return h;
+}
+
+int hydro_mhd_step(hydro_ctx* c, void* const in[9], void* const out[9], int nx, int ny, int nz, double dx,
+                   const double* dt_dev, double* dt_next_dev) {
+  if (!mhd_args(c, in, nx, ny, nz, dx) || !mhd_args(c, out, nx, ny, nz, dx) || !dt_dev) return HYDRO_ERR_ARG;
+  const uintptr_t bytes = (uintptr_t)nx * ny * nz * elem_size(c);
+  for (int v = 0; v < 9; ++v)  // out is written while in is read by other cells: no overlap
+    for (int u = 0; u < 9; ++u) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(out[v]), b = reinterpret_cast<uintptr_t>(in[u]);
+      if (a < b + bytes && b < a + bytes) return HYDRO_ERR_ARG;
+    }
+  int rc = ensure_device(&c->d_mhd, &c->mhd_cap, hydro::mhd_scratch_bytes(nx, ny, nz, elem_size(c)));
+  if (rc) return rc;
+  if (dt_next_dev) {
+    rc = reset_slots(c, dt_next_dev, 1, c->stream);
+    if (rc) return rc;
+  }
+  c->launches += 4;
+  return cuda_status(hydro::launch_mhd_step(elem_size(c), mhd_box(in, out, nx, ny, nz, dx), c->prm, dt_dev,
+                                            dt_next_dev, c->d_mhd, c->d_err, c->stream));
+}
+
+int hydro_mhd_cfl_dt(hydro_ctx* c, void* const U[9], int nx, int ny, int nz, double dx, double* dt_dev) {
+  if (!mhd_args(c, U, nx, ny, nz, dx) || !dt_dev) return HYDRO_ERR_ARG;
+  int rc = reset_slots(c, dt_dev, 1, c->stream);
+  if (rc) return rc;
+  c->launches += 1;
+  return cuda_status(
+      hydro::launch_mhd_cfl(elem_size(c), mhd_box(U, nullptr, nx, ny, nz, dx), c->prm, dt_dev, c->d_err, c->stream));
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

@@ -208,3 +208,42 @@ def gather_octs(U, origins, ghost=2):
     iz = (o[:, 2, None] + r[None, :]) % NZ
     flat = (iz[:, :, None, None] * NY + iy[:, None, :, None]) * NX + ix[:, None, None, :]  # (G,6,6,6)
     return U.reshape(5, -1)[:, flat]
+
+
+def mhd_state(shape, seed=1, beta=1.0, mach=1.0, psi_amp=0.01, modes=6, gamma=GAMMA, device="cpu"):
+    """Smooth periodic magnetised gas for the MHD step: each primitive field a sum of `modes` random
+    Fourier modes (wavenumbers 0..3 per axis, not all zero) on the unit box.  rho = 1 + 0.1 f (mean 1),
+    p = 1 + 0.1 g, velocities of rms Mach `mach` (sound speed of the mean state), B of rms
+    sqrt(2 <p> / beta) (plasma beta), psi of amplitude psi_amp; B is not divergence-free.  The mode
+    parameters come from a seeded numpy generator; the fields are formed with torch on `device`.
+    Returns the conserved state (9, nz, ny, nx) in float64: rho, m, E = p/(gamma-1) + rho |v|^2/2 +
+    |B|^2/2, B, psi."""
+    if isinstance(shape, int):
+        shape = (shape, shape, shape)
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed + 5000)
+    f64 = dict(device=device, dtype=torch.float64)
+    z = ((torch.arange(nz, **f64) + 0.5) / nz)[:, None, None]
+    y = ((torch.arange(ny, **f64) + 0.5) / ny)[None, :, None]
+    x = ((torch.arange(nx, **f64) + 0.5) / nx)[None, None, :]
+
+    def field():
+        f = torch.zeros(shape, **f64)
+        for _ in range(modes):
+            k = rng.integers(0, 4, 3)
+            if not k.any():
+                k[rng.integers(0, 3)] = 1
+            ph = float(rng.uniform(0, 2 * math.pi))
+            a = float(rng.normal())
+            f += a * torch.sin(2 * math.pi * (float(k[0]) * x + float(k[1]) * y + float(k[2]) * z) + ph)
+        return f / torch.sqrt((f * f).mean()).clamp_min(1e-300)
+
+    rho = 1.0 + 0.1 * field()
+    p = 1.0 + 0.1 * field()
+    cs = math.sqrt(gamma)
+    v = [mach * cs / math.sqrt(3.0) * field() for _ in range(3)]
+    b0 = math.sqrt(2.0 / beta) / math.sqrt(3.0)
+    B = [b0 * field() for _ in range(3)]
+    psi = psi_amp * field()
+    E = p / (gamma - 1.0) + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2) + 0.5 * (B[0] ** 2 + B[1] ** 2 + B[2] ** 2)
+    return torch.stack([rho, rho * v[0], rho * v[1], rho * v[2], E, B[0], B[1], B[2], psi])
