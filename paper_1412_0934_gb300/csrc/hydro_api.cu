@@ -67,7 +67,9 @@ struct hydro_ctx {
   long long stage_key[7] = {-1, -1, -1, -1, -1, -1, -1};  // nx ny nz sy sz tile zc of the uploaded list
   double stage_dx = 0.0;
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-  std::vector<cudaEvent_t> ev_copied, ev_stepped;
+  cudaStream_t s_cmp2 = nullptr;  // second compute stream: consecutive slabs' kernels overlap
+  cudaEvent_t ev_ready = nullptr;
+  std::vector<cudaEvent_t> ev_copied, ev_stepped, ev_halo;
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   // coarse-to-fine ghost fill: uploaded patch descriptors and ghost-cell offsets of the last set
   std::vector<hydro::HostGhostPatch> ghost_key;
@@ -366,6 +368,7 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_adj);
   if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
   if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
+  if (c->s_cmp2) cudaStreamSynchronize(c->s_cmp2);
   cudaFree(c->d_stage);
   cudaFree(c->d_stage_io);
   cudaFree(c->d_stage_tiles);
@@ -379,10 +382,13 @@ int hydro_finalize(hydro_ctx* c) {
   cudaFree(c->d_mhd);
   for (cudaEvent_t e : c->ev_copied) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stepped) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_halo) cudaEventDestroy(e);
   if (c->ev_begin) cudaEventDestroy(c->ev_begin);
   if (c->ev_end) cudaEventDestroy(c->ev_end);
   if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
   if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+  if (c->s_cmp2) cudaStreamDestroy(c->s_cmp2);
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
   if (c->h_patches) cudaFreeHost(c->h_patches);
   if (c->h_cfl) cudaFreeHost(c->h_cfl);
   delete c;
@@ -473,7 +479,8 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   // slabs: the z chunk shortened until the box has >= 16 slabs (or 2-plane chunks)
   int zc = c->zchunk;
   while (zc > 2 && I.nz / zc < 16) zc /= 2;
-  zc = std::max(1, std::min(zc, I.nz));
+  // at least two planes per slab: a slab's upper halo (two planes) then lies in the next slab
+  zc = std::max(std::min(2, I.nz), std::min(zc, I.nz));
   const int S = (I.nz + zc - 1) / zc;
   const int tx = hydro::kTileX[c->tile_id], ty = hydro::kTileY[c->tile_id];
   const int ntx = (I.nx + tx - 1) / tx, nty = (I.ny + ty - 1) / ty, tps = ntx * nty;
@@ -482,6 +489,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   if (c->stage_cap < 10 * fb) {
     if (c->s_h2d) cudaStreamSynchronize(c->s_h2d);
     if (c->s_d2h) cudaStreamSynchronize(c->s_d2h);
+    if (c->s_cmp2) cudaStreamSynchronize(c->s_cmp2);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
     cudaFree(c->d_stage);
     c->d_stage = nullptr;
@@ -497,18 +505,22 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   if (rc) return rc;
   if (!c->s_h2d && cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking) != cudaSuccess) return HYDRO_ERR_CUDA;
   if (!c->s_d2h && cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (!c->s_cmp2 && cudaStreamCreateWithFlags(&c->s_cmp2, cudaStreamNonBlocking) != cudaSuccess) return HYDRO_ERR_CUDA;
+  if (!c->ev_ready && cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess)
+    return HYDRO_ERR_CUDA;
   if (!c->ev_begin && (cudaEventCreateWithFlags(&c->ev_begin, cudaEventDisableTiming) != cudaSuccess ||
                        cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) != cudaSuccess))
     return HYDRO_ERR_CUDA;
   while ((int)c->ev_copied.size() < S) {
-    cudaEvent_t a, b;
-    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return HYDRO_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
-      cudaEventDestroy(a);
-      return HYDRO_ERR_CUDA;
-    }
-    c->ev_copied.push_back(a);
-    c->ev_stepped.push_back(b);
+    cudaEvent_t e[3];
+    for (int k = 0; k < 3; ++k)
+      if (cudaEventCreateWithFlags(&e[k], cudaEventDisableTiming) != cudaSuccess) {
+        for (int m = 0; m < k; ++m) cudaEventDestroy(e[m]);
+        return HYDRO_ERR_CUDA;
+      }
+    c->ev_copied.push_back(e[0]);
+    c->ev_stepped.push_back(e[1]);
+    c->ev_halo.push_back(e[2]);
   }
   char* din[5];
   char* dout[5];
@@ -558,9 +570,12 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   const int tail = S > 1 ? std::max(0, I.nz - 2) : I.nz;
   if (!upload(tail, I.nz)) return HYDRO_ERR_CUDA;
   for (int k = 0; k < S; ++k) {
-    const int za = k * zc, zb = std::min(I.nz, za + zc);
-    if (!upload(za, std::min(zb, tail))) return HYDRO_ERR_CUDA;
-    if (cudaEventRecord(c->ev_copied[k], c->s_h2d) != cudaSuccess) return HYDRO_ERR_CUDA;
+    const int za = k * zc, zb = std::min(std::min(I.nz, za + zc), tail);
+    // a slab's first two planes go first: with them the previous slab's step can start
+    const int zh = std::min(za + 2, zb);
+    if (!upload(za, zh) || cudaEventRecord(c->ev_halo[k], c->s_h2d) != cudaSuccess || !upload(zh, zb) ||
+        cudaEventRecord(c->ev_copied[k], c->s_h2d) != cudaSuccess)
+      return HYDRO_ERR_CUDA;
   }
   if (cudaMemsetAsync(c->d_stage_counters, 0, (size_t)S * sizeof(int), c->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
   if (dt_next_dev) {
@@ -569,15 +584,23 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   }
   const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id);
   const int grid = std::max(1, std::min(tps, c->sm_count * per_sm));
+  // slabs alternate between two compute streams, so that a slab's last partial wave of tiles runs
+  // beside the next slab's first (the slabs write disjoint planes; dt_next is an order-free min)
+  if (cudaEventRecord(c->ev_ready, c->stream) != cudaSuccess || cudaStreamWaitEvent(c->s_cmp2, c->ev_ready) != cudaSuccess)
+    return HYDRO_ERR_CUDA;
   for (int k = 0; k < S; ++k) {
     const int za = k * zc, zb = std::min(I.nz, za + zc);
-    if (cudaStreamWaitEvent(c->stream, c->ev_copied[std::min(k + 1, S - 1)]) != cudaSuccess) return HYDRO_ERR_CUDA;
+    cudaStream_t sk = (k & 1) ? c->s_cmp2 : c->stream;
+    // slab k and its upper halo: the first two planes of slab k+1 (the last slab's halo wraps onto
+    // slab 0, uploaded before it)
+    if (cudaStreamWaitEvent(sk, k + 1 < S ? c->ev_halo[k + 1] : c->ev_copied[S - 1]) != cudaSuccess)
+      return HYDRO_ERR_CUDA;
     c->launches += 1;
     if (c->ops->step_batched(c->tile_id, c->d_stage_io, c->d_stage_tiles + (size_t)k * tps, tps,
                              c->d_stage_counters + k, c->prm, dt_dev, dt_next_dev, zc, c->d_err, grid,
-                             c->stream) != cudaSuccess)
+                             sk) != cudaSuccess)
       return HYDRO_ERR_CUDA;
-    if (cudaEventRecord(c->ev_stepped[k], c->stream) != cudaSuccess ||
+    if (cudaEventRecord(c->ev_stepped[k], sk) != cudaSuccess ||
         cudaStreamWaitEvent(c->s_d2h, c->ev_stepped[k]) != cudaSuccess)
       return HYDRO_ERR_CUDA;
     if (!download(za, zb)) return HYDRO_ERR_CUDA;

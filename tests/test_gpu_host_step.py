@@ -58,6 +58,24 @@ def test_host_step_equals_device_step(precision, shape):
     assert torch.equal(gd, wd)
 
 
+@pytest.mark.parametrize("zchunk", [1, 2, 3, 8])
+def test_host_step_small_slabs(zchunk):
+    """Slabs of one to eight planes (one-plane chunks are widened to two, so that a slab's upper
+    halo lies in the next slab), each slab's step started by the arrival of the next slab's first
+    two planes, consecutive slabs on alternating compute streams: the same bits as hydro_step."""
+    c = ctx("fp64")
+    shape = (29, 12, 14)
+    U = workloads.turbulent_state(shape, seed=3, mach=5.0, sedov=True).contiguous()
+    dx = 1.0 / 14
+    want, wd = _device_steps(c, U, dx, 2)
+    hy.hydro_set_tuning(c, 0, zchunk)
+    got, gd = _host_steps(c, U, dx, 2, wd[0].item())
+    for g, w in zip(got, want):
+        assert torch.equal(g, w)
+    assert torch.equal(gd, wd)
+    check_clean(c)
+
+
 def test_host_step_pageable_memory():
     c = ctx("fp64")
     U = workloads.turbulent_state((24, 16, 16), seed=3, mach=2.0, sedov=False).contiguous()
