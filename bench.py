@@ -857,7 +857,7 @@ def run_forms(hy, args, n, precision):
                     extra["ppm_%d_%s" % (n, prec)] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None)
                 extra["ppm_batched_mixed"] = form_ppm_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch)
             elif f == "mhd":
-                for prec in ("fp64", "fp32"):
+                for prec in ("fp64", "df64", "fp32"):
                     extra["mhd_256_" + prec] = form_mhd(hy, prec, args.steps, args.warmup)
             elif f == "graph1024":
                 extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,

@@ -978,12 +978,12 @@ int hydro_step_octs_table(hydro_ctx* c, void* const in[5], void* const out[5], i
       c->ops->octs_table(in, nbr_dev, noct, list_dev, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
 }
 
-// Arguments of the MHD calls: a periodic box of nine contiguous fields in a FP64 or FP32 context
-// with a PLM limiter.
+// Arguments of the MHD calls: a periodic box of nine contiguous fields in a FP64, FP64_DF or FP32
+// context with a PLM limiter.
 static bool mhd_args(const hydro_ctx* c, void* const* U, int nx, int ny, int nz, double dx) {
   if (!c || !U || nx < 1 || ny < 1 || nz < 1 || !finite_pos(dx)) return false;
   if ((long long)nx * ny * nz > 0x7fffffffLL) return false;
-  if (c->cfg.precision != HYDRO_FP64 && c->cfg.precision != HYDRO_FP32) return false;
+  if (c->cfg.precision == HYDRO_MIXED) return false;
   if (ppm(c)) return false;
   const int es = elem_size(c);
   for (int v = 0; v < 9; ++v)
@@ -1018,7 +1018,7 @@ int hydro_mhd_step(hydro_ctx* c, void* const in[9], void* const out[9], int nx, 
     if (rc) return rc;
   }
   c->launches += 4;
-  return cuda_status(hydro::launch_mhd_step(elem_size(c), mhd_box(in, out, nx, ny, nz, dx), c->prm, dt_dev,
+  return cuda_status(hydro::launch_mhd_step(c->cfg.precision, mhd_box(in, out, nx, ny, nz, dx), c->prm, dt_dev,
                                             dt_next_dev, c->d_mhd, c->d_err, c->stream));
 }
 
@@ -1028,7 +1028,7 @@ int hydro_mhd_cfl_dt(hydro_ctx* c, void* const U[9], int nx, int ny, int nz, dou
   if (rc) return rc;
   c->launches += 1;
   return cuda_status(
-      hydro::launch_mhd_cfl(elem_size(c), mhd_box(U, nullptr, nx, ny, nz, dx), c->prm, dt_dev, c->d_err, c->stream));
+      hydro::launch_mhd_cfl(c->cfg.precision, mhd_box(U, nullptr, nx, ny, nz, dx), c->prm, dt_dev, c->d_err, c->stream));
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

@@ -144,8 +144,9 @@ cudaError_t launch_octs_build(const int* pos, int noct, const int dims[3], unsig
                               cudaStream_t s);
 
 // Ideal MHD with GLM cleaning on a periodic box (mhd.cu): nine fields (rho, m, E, B, psi), each
-// nx*ny*nz contiguous, x fastest; elem_size 8 (double) or 4 (float).  The step needs
-// mhd_scratch_bytes of device scratch (face states, fluxes, the step's constants).
+// nx*ny*nz contiguous, x fastest; precision HYDRO_FP64, HYDRO_FP32 or HYDRO_FP64_DF.  The step needs
+// mhd_scratch_bytes (elem_size: bytes of the arithmetic type) of device scratch (face states,
+// fluxes, the step's constants).
 struct HostMhdBox {
   const void* in[9];
   void* out[9];
@@ -153,9 +154,9 @@ struct HostMhdBox {
   double dx;
 };
 size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size);
-cudaError_t launch_mhd_step(int elem_size, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
+cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
                             void* scratch, unsigned* err, cudaStream_t s);
-cudaError_t launch_mhd_cfl(int elem_size, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,
+cudaError_t launch_mhd_cfl(int precision, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,
                            cudaStream_t s);
 
 // Work-list construction (precision-independent; descriptors read through HostPatchIO).

@@ -14,7 +14,10 @@
 // Three launches per step, one thread per cell each: predict (the cell's six face states into
 // scratch), flux (the HLL flux through the cell's three low faces into scratch), update (flux
 // divergence, damping, and the CFL speed of the new state folded into dt_next).  The scratch holds
-// 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays.
+// 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays, in the arithmetic type.
+// Precision policies as the hydro step: FP64 (double), FP32 (float, SFU reciprocal and square
+// root), FP64_DF (double state, double-float arithmetic on the FP32 pipes, the update summed in
+// double).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,68 +32,71 @@ namespace {
 constexpr int NV = 9;
 constexpr double kMhdAlpha = 0.4;  // psi damping: exp(-alpha c_h dt / dx) per step
 
-template <class T>
+template <class Pol>
 struct MhdBox {
-  const T* in[NV];
-  T* out[NV];
-  T* face;  // [6][NV][cells]: face 2d + h, h = 0 the low, 1 the high face along axis d
-  T* flux;  // [3][NV][cells]: the flux through the cell's low face along each axis
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  const S* in[NV];
+  S* out[NV];
+  R* face;  // [6][NV][cells]: face 2d + h, h = 0 the low, 1 the high face along axis d
+  R* flux;  // [3][NV][cells]: the flux through the cell's low face along each axis
   int nx, ny, nz;
   long long cells;
 };
 
-template <class T>
+template <class R>
 struct MhdConst {
-  T gamma, gm1, igm1, rf, pf, ch, hdt, dtdx, damp;
+  R gamma, gm1, igm1, rf, pf, ch, ch2, hdt, dtdx, damp;
   int limiter;
   int valid;  // 0: the step's dt was not positive and finite (nothing is updated)
 };
 
-// Limited slope of left and right differences (the hydro step's limiter, in T).
-template <class T>
-__device__ __forceinline__ T mhd_slope(T a, T b, int lim) {
-  if (lim == HYDRO_NOLIMIT) return T(0.5) * (a + b);
-  if (a * b <= T(0)) return T(0);
-  if (lim == HYDRO_MINMOD) return fabs(a) <= fabs(b) ? a : b;
-  T ta = T(2) * a, tb = T(2) * b, m = T(0.5) * (a + b);
-  T best = ta;
-  if (fabs(tb) < fabs(best)) best = tb;
-  if (fabs(m) < fabs(best)) best = m;
-  return best;
+// A stored value in the arithmetic type (double -> double-float exactly, by the IEEE bit fields).
+__device__ __forceinline__ double to_r(double x, double*) { return x; }
+__device__ __forceinline__ float to_r(float x, float*) { return x; }
+__device__ __forceinline__ df to_r(double x, df*) {
+  df r;
+  split_double(x, r.h, r.l);
+  return r;
 }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ double to_double(const df& x) { return (double)x; }
 
 // Primitive state of a conserved one, rho and p floored; flags as the hydro recovery.
-template <class T>
-__device__ __forceinline__ void mhd_recover(const T U[NV], const MhdConst<T>& c, T q[NV], unsigned& flags) {
-  if (!(U[0] >= c.rf)) flags |= isfinite(U[0]) ? HYDRO_EBIT_RHO_FLOOR : HYDRO_EBIT_NONFINITE;
-  const T rho = U[0] < c.rf ? c.rf : U[0];
-  const T ir = T(1) / rho;
-  const T kin = T(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir;
-  const T mag = T(0.5) * (U[5] * U[5] + U[6] * U[6] + U[7] * U[7]);
-  const T eint = (U[4] - kin) - mag;
-  if (eint < T(0)) flags |= HYDRO_EBIT_P_FLOOR;
-  if (!isfinite(eint)) flags |= HYDRO_EBIT_NONFINITE;
-  const T p = c.gm1 * eint;
+template <class R>
+__device__ __forceinline__ void mhd_recover(const R U[NV], const MhdConst<R>& c, R q[NV], unsigned& flags) {
+  if (!isfinite_(U[0])) flags |= HYDRO_EBIT_NONFINITE;
+  const bool low = cmp_lt_floor(U[0], c.rf);
+  if (low) flags |= HYDRO_EBIT_RHO_FLOOR;
+  const R rho = low ? c.rf : U[0];
+  const R ir = rcp_(rho);
+  const R kin = half_((U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir);
+  const R mag = half_(U[5] * U[5] + U[6] * U[6] + U[7] * U[7]);
+  const R eint = (U[4] - kin) - mag;
+  if (cmp_neg(eint)) flags |= HYDRO_EBIT_P_FLOOR;
+  if (!isfinite_(eint)) flags |= HYDRO_EBIT_NONFINITE;
+  const R p = c.gm1 * eint;
   q[0] = rho;
   q[1] = U[1] * ir;
   q[2] = U[2] * ir;
   q[3] = U[3] * ir;
-  q[4] = p < c.pf ? c.pf : p;
+  q[4] = cmp_lt_floor(p, c.pf) ? c.pf : p;
   q[5] = U[5];
   q[6] = U[6];
   q[7] = U[7];
   q[8] = U[8];
 }
 
-template <class T>
-__device__ __forceinline__ void mhd_conserved(const T q[NV], const MhdConst<T>& c, T U[NV]) {
-  const T rho = q[0];
+template <class R>
+__device__ __forceinline__ void mhd_conserved(const R q[NV], const MhdConst<R>& c, R U[NV]) {
+  const R rho = q[0];
   U[0] = rho;
   U[1] = rho * q[1];
   U[2] = rho * q[2];
   U[3] = rho * q[3];
-  U[4] = q[4] * c.igm1 + T(0.5) * rho * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) +
-         T(0.5) * (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]);
+  U[4] = (q[4] * c.igm1 + half_(rho * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]))) +
+         half_(q[5] * q[5] + q[6] * q[6] + q[7] * q[7]);
   U[5] = q[5];
   U[6] = q[6];
   U[7] = q[7];
@@ -98,71 +104,72 @@ __device__ __forceinline__ void mhd_conserved(const T q[NV], const MhdConst<T>& 
 }
 
 // Physical flux along axis D with the GLM terms (B_n's flux psi, psi's flux c_h^2 B_n).
-template <int D, class T>
-__device__ __forceinline__ void mhd_flux(const T q[NV], const MhdConst<T>& c, T F[NV]) {
+template <int D, class R>
+__device__ __forceinline__ void mhd_flux(const R q[NV], const MhdConst<R>& c, R F[NV]) {
   constexpr int N = 1 + D;
-  const T rho = q[0], p = q[4], un = q[N], Bn = q[5 + D];
-  const T B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
-  const T pt = p + T(0.5) * B2;
-  const T uB = q[1] * q[5] + q[2] * q[6] + q[3] * q[7];
-  const T E = p * c.igm1 + T(0.5) * rho * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) + T(0.5) * B2;
-  const T mn = rho * un;
+  const R rho = q[0], p = q[4], un = q[N], Bn = q[5 + D];
+  const R B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+  const R pt = p + half_(B2);
+  const R uB = q[1] * q[5] + q[2] * q[6] + q[3] * q[7];
+  const R E = (p * c.igm1 + half_(rho * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]))) + half_(B2);
+  const R mn = rho * un;
   F[0] = mn;
 #pragma unroll
   for (int k = 0; k < 3; ++k) F[1 + k] = mn * q[1 + k] - Bn * q[5 + k];
-  F[N] += pt;
+  F[N] = F[N] + pt;
   F[4] = (E + pt) * un - Bn * uB;
 #pragma unroll
   for (int k = 0; k < 3; ++k) F[5 + k] = un * q[5 + k] - q[1 + k] * Bn;
   F[5 + D] = q[8];
-  F[8] = c.ch * c.ch * Bn;
+  F[8] = c.ch2 * Bn;
 }
 
-template <class T>
-__device__ __forceinline__ T mhd_fast(const T q[NV], int d, const MhdConst<T>& c) {
-  const T ir = T(1) / q[0];
-  const T a2 = c.gamma * q[4] * ir;
-  const T b2 = (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]) * ir;
-  const T bn = q[5 + d];
-  const T bn2 = bn * bn * ir;
-  const T s = a2 + b2;
-  T r = s * s - T(4) * a2 * bn2;
-  r = r > T(0) ? r : T(0);
-  return sqrt(T(0.5) * (s + sqrt(r)));
+template <class R>
+__device__ __forceinline__ R mhd_fast(const R q[NV], int d, const MhdConst<R>& c) {
+  const R ir = rcp_(q[0]);
+  const R a2 = c.gamma * q[4] * ir;
+  const R b2 = (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]) * ir;
+  const R bn = d == 0 ? q[5] : (d == 1 ? q[6] : q[7]);
+  const R bn2 = bn * bn * ir;
+  const R s = a2 + b2;
+  R r = s * s - mulf_(a2 * bn2, 4.f);
+  r = cmp_pos(r) ? r : R(0);
+  return rsqrt_(half_(s + rsqrt_(r)));
 }
 
 // CFL speed sum over axes of |u_d| + c_f,d (the same function for the fused and standalone dt).
-template <class T>
-__device__ __forceinline__ T mhd_speed(const T q[NV], const MhdConst<T>& c) {
-  return ((fabs(q[1]) + mhd_fast(q, 0, c)) + (fabs(q[2]) + mhd_fast(q, 1, c))) + (fabs(q[3]) + mhd_fast(q, 2, c));
+template <class R>
+__device__ __forceinline__ R mhd_speed(const R q[NV], const MhdConst<R>& c) {
+  return ((rabs(q[1]) + mhd_fast(q, 0, c)) + (rabs(q[2]) + mhd_fast(q, 1, c))) + (rabs(q[3]) + mhd_fast(q, 2, c));
 }
 
-template <int D, class T>
-__device__ __forceinline__ void mhd_hll(T qL[NV], T qR[NV], const MhdConst<T>& c, T F[NV]) {
-  const T Bm = T(0.5) * (qL[5 + D] + qR[5 + D]) - (qR[8] - qL[8]) / (T(2) * c.ch);
-  const T pm = T(0.5) * (qL[8] + qR[8]) - T(0.5) * c.ch * (qR[5 + D] - qL[5 + D]);
+template <int D, class R>
+__device__ __forceinline__ void mhd_hll(R qL[NV], R qR[NV], const MhdConst<R>& c, R F[NV]) {
+  const R Bm = half_(qL[5 + D] + qR[5 + D]) - half_((qR[8] - qL[8]) * rcp_(c.ch));
+  const R pm = half_(qL[8] + qR[8]) - half_(c.ch * (qR[5 + D] - qL[5 + D]));
   qL[5 + D] = qR[5 + D] = Bm;
   qL[8] = qR[8] = pm;
   constexpr int N = 1 + D;
-  const T cL = mhd_fast(qL, D, c), cR = mhd_fast(qR, D, c);
-  const T a = qL[N] - cL, b = qR[N] - cR, e = qL[N] + cL, f = qR[N] + cR;
-  const T SL = a < b ? a : b, SR = e > f ? e : f;
-  if (SL >= T(0)) {
+  const R cL = mhd_fast(qL, D, c), cR = mhd_fast(qR, D, c);
+  const R a = qL[N] - cL, b = qR[N] - cR, e = qL[N] + cL, f = qR[N] + cR;
+  const R SL = a < b ? a : b, SR = e > f ? e : f;
+  if (!cmp_neg(SL)) {
     mhd_flux<D>(qL, c, F);
-  } else if (SR <= T(0)) {
+  } else if (!cmp_pos(SR)) {
     mhd_flux<D>(qR, c, F);
   } else {
-    T FL[NV], FR[NV], UL[NV], UR[NV];
+    R FL[NV], FR[NV], UL[NV], UR[NV];
     mhd_flux<D>(qL, c, FL);
     mhd_flux<D>(qR, c, FR);
     mhd_conserved(qL, c, UL);
     mhd_conserved(qR, c, UR);
-    const T is = T(1) / (SR - SL);
+    const R is = rcp_(SR - SL);
+    const R ss = SL * SR;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = ((SR * FL[v] - SL * FR[v]) + SL * SR * (UR[v] - UL[v])) * is;
+    for (int v = 0; v < NV; ++v) F[v] = ((SR * FL[v] - SL * FR[v]) + ss * (UR[v] - UL[v])) * is;
   }
   F[5 + D] = pm;
-  F[8] = c.ch * c.ch * Bm;
+  F[8] = c.ch2 * Bm;
 }
 
 __device__ __forceinline__ void cell_of(long long a, int nx, int ny, int& i, int& j, int& k) {
@@ -173,27 +180,30 @@ __device__ __forceinline__ void cell_of(long long a, int nx, int ny, int& i, int
   j = row - k * ny;
 }
 
-template <class T>
-__device__ __forceinline__ void load_q(const MhdBox<T>& B, long long a, const MhdConst<T>& c, T q[NV],
-                                       unsigned& flags) {
-  T U[NV];
+template <class Pol>
+__device__ __forceinline__ void load_q(const MhdBox<Pol>& B, long long a, const MhdConst<typename Pol::R>& c,
+                                       typename Pol::R q[NV], unsigned& flags) {
+  using R = typename Pol::R;
+  R U[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) U[v] = __ldg(B.in[v] + a);
+  for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(B.in[v] + a), (R*)nullptr);
   mhd_recover(U, c, q, flags);
 }
 
-template <int D, class T>
-__device__ __forceinline__ void axis_states(const MhdBox<T>& B, long long a, long long am, long long ap,
-                                            const T q[NV], const MhdConst<T>& c, T dF[NV]) {
+template <int D, class Pol>
+__device__ __forceinline__ void axis_states(const MhdBox<Pol>& B, long long a, long long am, long long ap,
+                                            const typename Pol::R q[NV], const MhdConst<typename Pol::R>& c,
+                                            typename Pol::R dF[NV]) {
+  using R = typename Pol::R;
   unsigned nf = 0;  // neighbours are flagged by their own threads
-  T qm[NV], qp[NV], lo[NV], hi[NV], Fl[NV], Fh[NV];
+  R qm[NV], qp[NV], lo[NV], hi[NV], Fl[NV], Fh[NV];
   load_q(B, am, c, qm, nf);
   load_q(B, ap, c, qp, nf);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const T s = mhd_slope(q[v] - qm[v], qp[v] - q[v], c.limiter);
-    lo[v] = q[v] - T(0.5) * s;
-    hi[v] = q[v] + T(0.5) * s;
+    const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
+    lo[v] = q[v] - half_(s);
+    hi[v] = q[v] + half_(s);
   }
   mhd_flux<D>(hi, c, Fh);
   mhd_flux<D>(lo, c, Fl);
@@ -205,20 +215,21 @@ __device__ __forceinline__ void axis_states(const MhdBox<T>& B, long long a, lon
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_mhd_predict(MhdBox<T> B, const MhdConst<T>* cp, unsigned* err) {
-  const MhdConst<T> c = *cp;
+template <class Pol>
+__global__ void __launch_bounds__(256) k_mhd_predict(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, unsigned* err) {
+  using R = typename Pol::R;
+  const MhdConst<R> c = *cp;
   if (!c.valid) return;
   unsigned flags = 0;
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
        a += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     cell_of(a, B.nx, B.ny, i, j, k);
-    const long long sx = 1, sy = B.nx, sz = (long long)B.nx * B.ny;
-    const long long axm = a + (i == 0 ? (B.nx - 1) * sx : -sx), axp = a + (i == B.nx - 1 ? -(B.nx - 1) * sx : sx);
+    const long long sy = B.nx, sz = (long long)B.nx * B.ny;
+    const long long axm = a + (i == 0 ? B.nx - 1 : -1), axp = a + (i == B.nx - 1 ? -(B.nx - 1) : 1);
     const long long aym = a + (j == 0 ? (B.ny - 1) * sy : -sy), ayp = a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy);
     const long long azm = a + (k == 0 ? (B.nz - 1) * sz : -sz), azp = a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz);
-    T q[NV], dF[NV];
+    R q[NV], dF[NV];
     load_q(B, a, c, q, flags);
     axis_states<0>(B, a, axm, axp, q, c, dF);
     axis_states<1>(B, a, aym, ayp, q, c, dF);
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(256) k_mhd_predict(MhdBox<T> B, const MhdConst
     unsigned nf = 0;
 #pragma unroll 1
     for (int f = 0; f < 6; ++f) {
-      T w[NV], U[NV], r[NV];
+      R w[NV], U[NV], r[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v] = B.face[((long long)f * NV + v) * B.cells + a];
       mhd_conserved(w, c, U);
@@ -242,9 +253,11 @@ __global__ void __launch_bounds__(256) k_mhd_predict(MhdBox<T> B, const MhdConst
   flush_flags(flags, err);
 }
 
-template <int D, class T>
-__device__ __forceinline__ void low_face_flux(const MhdBox<T>& B, long long a, long long am, const MhdConst<T>& c) {
-  T qL[NV], qR[NV], F[NV];
+template <int D, class Pol>
+__device__ __forceinline__ void low_face_flux(const MhdBox<Pol>& B, long long a, long long am,
+                                              const MhdConst<typename Pol::R>& c) {
+  using R = typename Pol::R;
+  R qL[NV], qR[NV], F[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     qL[v] = B.face[((long long)(2 * D + 1) * NV + v) * B.cells + am];  // high face of the cell below
@@ -255,9 +268,9 @@ __device__ __forceinline__ void low_face_flux(const MhdBox<T>& B, long long a, l
   for (int v = 0; v < NV; ++v) B.flux[((long long)D * NV + v) * B.cells + a] = F[v];
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_mhd_flux(MhdBox<T> B, const MhdConst<T>* cp) {
-  const MhdConst<T> c = *cp;
+template <class Pol>
+__global__ void __launch_bounds__(256) k_mhd_flux(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp) {
+  const MhdConst<typename Pol::R> c = *cp;
   if (!c.valid) return;
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
        a += (long long)gridDim.x * blockDim.x) {
@@ -270,12 +283,12 @@ __global__ void __launch_bounds__(256) k_mhd_flux(MhdBox<T> B, const MhdConst<T>
   }
 }
 
-template <class T>
-__device__ __forceinline__ T block_max_t(T v) {
-  __shared__ T red[8];
+template <class R>
+__device__ __forceinline__ R block_max_r(R v) {
+  __shared__ R red[8];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const T w = __shfl_xor_sync(0xffffffffu, v, o);
+    const R w = shfl_xor_(v, o);
     v = w > v ? w : v;
   }
   __syncthreads();
@@ -286,13 +299,15 @@ __device__ __forceinline__ T block_max_t(T v) {
   return v;
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_mhd_update(MhdBox<T> B, const MhdConst<T>* cp, double cfl, double dx,
-                                                    double* dt_next, unsigned* err) {
-  const MhdConst<T> c = *cp;
+template <class Pol>
+__global__ void __launch_bounds__(256) k_mhd_update(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl,
+                                                    double dx, double* dt_next, unsigned* err) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  const MhdConst<R> c = *cp;
   if (!c.valid) return;
   unsigned flags = 0;
-  T smax = T(0);
+  R smax = R(0);
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
        a += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -301,94 +316,100 @@ __global__ void __launch_bounds__(256) k_mhd_update(MhdBox<T> B, const MhdConst<
     const long long bx = a + (i == B.nx - 1 ? -(B.nx - 1) : 1);
     const long long by = a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy);
     const long long bz = a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz);
-    T Un[NV];
+    S Un[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const T* fx = B.flux + (long long)(0 * NV + v) * B.cells;
-      const T* fy = B.flux + (long long)(1 * NV + v) * B.cells;
-      const T* fz = B.flux + (long long)(2 * NV + v) * B.cells;
-      const T div = ((fx[bx] - fx[a]) + (fy[by] - fy[a])) + (fz[bz] - fz[a]);
-      Un[v] = __ldg(B.in[v] + a) - c.dtdx * div;
+      const R* fx = B.flux + (long long)(0 * NV + v) * B.cells;
+      const R* fy = B.flux + (long long)(1 * NV + v) * B.cells;
+      const R* fz = B.flux + (long long)(2 * NV + v) * B.cells;
+      const R div = ((fx[bx] - fx[a]) + (fy[by] - fy[a])) + (fz[bz] - fz[a]);
+      Un[v] = Pol::update(__ldg(B.in[v] + a), c.dtdx, div);
     }
-    Un[8] = Un[8] * c.damp;
+    Un[8] = Un[8] * (S)to_double(c.damp);
 #pragma unroll
     for (int v = 0; v < NV; ++v) B.out[v][a] = Un[v];
     if (dt_next) {
-      T q[NV];
-      mhd_recover(Un, c, q, flags);
-      const T s = mhd_speed(q, c);
+      R U[NV], q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
+      mhd_recover(U, c, q, flags);
+      const R s = mhd_speed(q, c);
       smax = s > smax ? s : smax;
     }
   }
   if (dt_next) {
-    const T m = block_max_t(smax);
-    if (threadIdx.x == 0) publish_dt(cfl, dx, (double)m, dt_next);
+    const R m = block_max_r(smax);
+    if (threadIdx.x == 0) publish_dt(cfl, dx, to_double(m), dt_next);
   }
   flush_flags(flags, err);
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_mhd_cfl(MhdBox<T> B, MhdConst<T> c, double cfl, double dx, double* dt,
-                                                 unsigned* err) {
+template <class Pol>
+__global__ void __launch_bounds__(256) k_mhd_cfl(MhdBox<Pol> B, MhdConst<typename Pol::R> c, double cfl, double dx,
+                                                 double* dt, unsigned* err) {
+  using R = typename Pol::R;
   unsigned flags = 0;
-  T smax = T(0);
+  R smax = R(0);
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
        a += (long long)gridDim.x * blockDim.x) {
-    T q[NV];
+    R q[NV];
     load_q(B, a, c, q, flags);
-    const T s = mhd_speed(q, c);
+    const R s = mhd_speed(q, c);
     smax = s > smax ? s : smax;
   }
-  const T m = block_max_t(smax);
-  if (threadIdx.x == 0) publish_dt(cfl, dx, (double)m, dt);
+  const R m = block_max_r(smax);
+  if (threadIdx.x == 0) publish_dt(cfl, dx, to_double(m), dt);
   flush_flags(flags, err);
 }
 
 // c_h and the half-step factors need dt, which lives on the device: a one-thread kernel turns it
 // into the constants the three step kernels read.
-template <class T>
-__global__ void k_mhd_consts(MhdConst<T> base, double cfl, double dx, double alpha, const double* dt_dev,
-                             MhdConst<T>* out, unsigned* err) {
+template <class R>
+__global__ void k_mhd_consts(MhdConst<R> base, double cfl, double dx, double alpha, const double* dt_dev,
+                             MhdConst<R>* out, unsigned* err) {
   const double dt = dt_dev[0];
-  MhdConst<T> c = base;
+  MhdConst<R> c = base;
   c.valid = dt > 0.0 && dt <= 1e300;
   if (!c.valid) {
     atomicOr(err, HYDRO_EBIT_BAD_DT);
   } else {
     const double ch = (cfl / 3.0) * dx / dt;
-    c.ch = (T)ch;
-    c.hdt = (T)(0.5 * dt / dx);
-    c.dtdx = (T)(dt / dx);
-    c.damp = (T)exp(-alpha * ch * dt / dx);
+    c.ch = R(ch);
+    c.ch2 = R(ch * ch);
+    c.hdt = R(0.5 * dt / dx);
+    c.dtdx = R(dt / dx);
+    c.damp = R(exp(-alpha * ch * dt / dx));
   }
   *out = c;
 }
 
-template <class T>
-MhdBox<T> box_of(const HostMhdBox& h, void* scratch) {
-  MhdBox<T> b;
+template <class Pol>
+MhdBox<Pol> box_of(const HostMhdBox& h, void* scratch) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  MhdBox<Pol> b;
   for (int v = 0; v < NV; ++v) {
-    b.in[v] = static_cast<const T*>(h.in[v]);
-    b.out[v] = static_cast<T*>(h.out[v]);
+    b.in[v] = static_cast<const S*>(h.in[v]);
+    b.out[v] = static_cast<S*>(h.out[v]);
   }
   b.nx = h.nx;
   b.ny = h.ny;
   b.nz = h.nz;
   b.cells = (long long)h.nx * h.ny * h.nz;
   // scratch: the step's constants in the first 256 bytes, then the face states and the fluxes
-  b.face = scratch ? reinterpret_cast<T*>(static_cast<char*>(scratch) + 256) : nullptr;
+  b.face = scratch ? reinterpret_cast<R*>(static_cast<char*>(scratch) + 256) : nullptr;
   b.flux = b.face ? b.face + 6LL * NV * b.cells : nullptr;
   return b;
 }
 
-template <class T>
-MhdConst<T> consts_of(const Params& prm) {
-  MhdConst<T> c{};
-  c.gamma = (T)prm.gamma;
-  c.gm1 = (T)(prm.gamma - 1.0);
-  c.igm1 = (T)(1.0 / (prm.gamma - 1.0));
-  c.rf = (T)prm.rho_floor;
-  c.pf = (T)prm.p_floor;
+template <class R>
+MhdConst<R> consts_of(const Params& prm) {
+  MhdConst<R> c{};
+  c.gamma = R(prm.gamma);
+  c.gm1 = R(prm.gamma - 1.0);
+  c.igm1 = R(1.0 / (prm.gamma - 1.0));
+  c.rf = R(prm.rho_floor);
+  c.pf = R(prm.p_floor);
   c.limiter = prm.limiter;
   c.valid = 1;
   return c;
@@ -399,24 +420,25 @@ int grid_for(long long cells) {
   return (int)(b < 1 ? 1 : (b > 152LL * 64 ? 152LL * 64 : b));
 }
 
-template <class T>
+template <class Pol>
 cudaError_t mhd_step_t(const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next, void* scratch,
                        unsigned* err, cudaStream_t s) {
-  MhdBox<T> B = box_of<T>(h, scratch);
-  static_assert(sizeof(MhdConst<T>) <= 256, "the constants fit before the face states");
-  auto* cp = static_cast<MhdConst<T>*>(scratch);
-  k_mhd_consts<T><<<1, 1, 0, s>>>(consts_of<T>(prm), prm.cfl, h.dx, kMhdAlpha, dt, cp, err);
+  using R = typename Pol::R;
+  MhdBox<Pol> B = box_of<Pol>(h, scratch);
+  static_assert(sizeof(MhdConst<R>) <= 256, "the constants fit before the face states");
+  auto* cp = static_cast<MhdConst<R>*>(scratch);
+  k_mhd_consts<R><<<1, 1, 0, s>>>(consts_of<R>(prm), prm.cfl, h.dx, kMhdAlpha, dt, cp, err);
   const int g = grid_for(B.cells);
-  k_mhd_predict<T><<<g, 256, 0, s>>>(B, cp, err);
-  k_mhd_flux<T><<<g, 256, 0, s>>>(B, cp);
-  k_mhd_update<T><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
+  k_mhd_predict<Pol><<<g, 256, 0, s>>>(B, cp, err);
+  k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
+  k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
   return cudaGetLastError();
 }
 
-template <class T>
+template <class Pol>
 cudaError_t mhd_cfl_t(const HostMhdBox& h, const Params& prm, double* dt, unsigned* err, cudaStream_t s) {
-  MhdBox<T> B = box_of<T>(h, nullptr);
-  k_mhd_cfl<T><<<grid_for(B.cells), 256, 0, s>>>(B, consts_of<T>(prm), prm.cfl, h.dx, dt, err);
+  MhdBox<Pol> B = box_of<Pol>(h, nullptr);
+  k_mhd_cfl<Pol><<<grid_for(B.cells), 256, 0, s>>>(B, consts_of<typename Pol::R>(prm), prm.cfl, h.dx, dt, err);
   return cudaGetLastError();
 }
 
@@ -426,15 +448,24 @@ size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size) {
   return (size_t)9 * NV * (size_t)nx * ny * nz * elem_size + 256;
 }
 
-cudaError_t launch_mhd_step(int elem_size, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
+cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
                             void* scratch, unsigned* err, cudaStream_t s) {
-  return elem_size == 4 ? mhd_step_t<float>(h, prm, dt, dt_next, scratch, err, s)
-                        : mhd_step_t<double>(h, prm, dt, dt_next, scratch, err, s);
+  switch (precision) {
+    case HYDRO_FP64: return mhd_step_t<PolF64>(h, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_FP32: return mhd_step_t<PolF32>(h, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_FP64_DF: return mhd_step_t<PolDF>(h, prm, dt, dt_next, scratch, err, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_mhd_cfl(int elem_size, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,
+cudaError_t launch_mhd_cfl(int precision, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,
                            cudaStream_t s) {
-  return elem_size == 4 ? mhd_cfl_t<float>(h, prm, dt, err, s) : mhd_cfl_t<double>(h, prm, dt, err, s);
+  switch (precision) {
+    case HYDRO_FP64: return mhd_cfl_t<PolF64>(h, prm, dt, err, s);
+    case HYDRO_FP32: return mhd_cfl_t<PolF32>(h, prm, dt, err, s);
+    case HYDRO_FP64_DF: return mhd_cfl_t<PolDF>(h, prm, dt, err, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace hydro
