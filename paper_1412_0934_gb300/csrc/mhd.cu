@@ -158,15 +158,24 @@ __device__ __forceinline__ void mhd_hll(R qL[NV], R qR[NV], const MhdConst<R>& c
   } else if (!cmp_pos(SR)) {
     mhd_flux<D>(qR, c, F);
   } else {
-    R FL[NV], FR[NV], UL[NV], UR[NV];
-    mhd_flux<D>(qL, c, FL);
-    mhd_flux<D>(qR, c, FR);
-    mhd_conserved(qL, c, UL);
-    mhd_conserved(qR, c, UR);
+    // (SR F_L - SL F_R + SL SR (U_R - U_L)) / (SR - SL), accumulated one side at a time so that
+    // only one side's flux and state are live
     const R is = rcp_(SR - SL);
     const R ss = SL * SR;
+    {
+      R Fs[NV], Us[NV];
+      mhd_flux<D>(qL, c, Fs);
+      mhd_conserved(qL, c, Us);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = ((SR * FL[v] - SL * FR[v]) + ss * (UR[v] - UL[v])) * is;
+      for (int v = 0; v < NV; ++v) F[v] = SR * Fs[v] - ss * Us[v];
+    }
+    {
+      R Fs[NV], Us[NV];
+      mhd_flux<D>(qR, c, Fs);
+      mhd_conserved(qR, c, Us);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] = ((F[v] - SL * Fs[v]) + ss * Us[v]) * is;
+    }
   }
   F[5 + D] = pm;
   F[8] = c.ch2 * Bm;
@@ -196,27 +205,35 @@ __device__ __forceinline__ void axis_states(const MhdBox<Pol>& B, long long a, l
                                             typename Pol::R dF[NV]) {
   using R = typename Pol::R;
   unsigned nf = 0;  // neighbours are flagged by their own threads
-  R qm[NV], qp[NV], lo[NV], hi[NV], Fl[NV], Fh[NV];
-  load_q(B, am, c, qm, nf);
-  load_q(B, ap, c, qp, nf);
+  R lo[NV], hi[NV];
+  {
+    R qm[NV], qp[NV];
+    load_q(B, am, c, qm, nf);
+    load_q(B, ap, c, qp, nf);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
-    lo[v] = q[v] - half_(s);
-    hi[v] = q[v] + half_(s);
+    for (int v = 0; v < NV; ++v) {
+      const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
+      lo[v] = q[v] - half_(s);
+      hi[v] = q[v] + half_(s);
+      B.face[((long long)(2 * D) * NV + v) * B.cells + a] = lo[v];
+      B.face[((long long)(2 * D + 1) * NV + v) * B.cells + a] = hi[v];
+    }
   }
+  R Fh[NV];
   mhd_flux<D>(hi, c, Fh);
-  mhd_flux<D>(lo, c, Fl);
+  {
+    R Fl[NV];
+    mhd_flux<D>(lo, c, Fl);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    dF[v] = D == 0 ? Fh[v] - Fl[v] : dF[v] + (Fh[v] - Fl[v]);
-    B.face[((long long)(2 * D) * NV + v) * B.cells + a] = lo[v];
-    B.face[((long long)(2 * D + 1) * NV + v) * B.cells + a] = hi[v];
+    for (int v = 0; v < NV; ++v) dF[v] = D == 0 ? Fh[v] - Fl[v] : dF[v] + (Fh[v] - Fl[v]);
   }
 }
 
+// Two resident blocks of 256 threads per SM at least (the register budget of 128 per thread): the
+// double-float kernels otherwise take ~170 registers and leave 8 warps per SM for long dependent
+// chains.
 template <class Pol>
-__global__ void __launch_bounds__(256) k_mhd_predict(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, unsigned* err) {
+__global__ void __launch_bounds__(256, 2) k_mhd_predict(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, unsigned* err) {
   using R = typename Pol::R;
   const MhdConst<R> c = *cp;
   if (!c.valid) return;
@@ -269,7 +286,7 @@ __device__ __forceinline__ void low_face_flux(const MhdBox<Pol>& B, long long a,
 }
 
 template <class Pol>
-__global__ void __launch_bounds__(256) k_mhd_flux(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp) {
+__global__ void __launch_bounds__(256, 2) k_mhd_flux(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp) {
   const MhdConst<typename Pol::R> c = *cp;
   if (!c.valid) return;
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
@@ -300,7 +317,7 @@ __device__ __forceinline__ R block_max_r(R v) {
 }
 
 template <class Pol>
-__global__ void __launch_bounds__(256) k_mhd_update(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl,
+__global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl,
                                                     double dx, double* dt_next, unsigned* err) {
   using S = typename Pol::S;
   using R = typename Pol::R;
