@@ -6,7 +6,11 @@ outputs the oracle computes one by one: each sampled cell from its own 5^3 perio
     (16x16, z chunk 128), and the fused dt of the result (oracle over every cell again);
   - 1024^3 Mach-10 MC FP32 (the first step of the graph-captured run): the step on samples, the dt
     at the cell the GPU's dt comes from and a lower bound at every sampled cell;
-  - the 4096-patch mixed-precision set in one persistent launch, per-patch dt, and 262144 oct groups."""
+  - the 4096-patch mixed-precision set in one persistent launch, per-patch dt, and 262144 oct groups;
+  - the 256^3 level stored oct-major (2,097,152 octs), its device-built Morton order and neighbour
+    table, every oct stepped through the table (mixed), sampled octs against the oracle's step
+    through its own table;
+  - the 4096-patch set with three ghost layers under PPM (mixed), sampled patches whole."""
 import numpy as np
 import pytest
 import torch
@@ -173,3 +177,83 @@ def test_4096_patches_and_262144_octs_mixed_sampled():
     assert err.max() <= TOL["mixed"], err
     rc, bits = hy.hydro_get_error(c)
     assert rc == hy.HYDRO_OK, bits
+
+
+def test_256_level_octs_through_the_table_mixed_sampled():
+    from oracle import octs as ooct
+    cfg = oracle.config()
+    c = ctx("mixed")
+    parent = workloads.turbulent_state(256, seed=3, sedov=False, device="cuda")
+    no = 128 ** 3
+    V = parent.reshape(5, 128, 2, 128, 2, 128, 2).permute(0, 1, 3, 5, 2, 4, 6).reshape(5, no, 8).contiguous()
+    idx = torch.arange(no, device="cuda", dtype=torch.int32)
+    pos = torch.stack([idx % 128, (idx // 128) % 128, idx // (128 * 128)], dim=1).contiguous()
+    order = torch.empty(no, dtype=torch.int32, device="cuda")
+    nbr = torch.empty((no, 27), dtype=torch.int32, device="cuda")
+    hy.hydro_octs_build(c, pos, (128, 128, 128), order, nbr)
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(c, hy.patch(parent, 0, 1.0 / 256), dt)
+    out = torch.empty_like(V)
+    hy.hydro_step_octs_table(c, V, out, nbr, order, 1.0 / 256, dt)
+    torch.cuda.synchronize()
+    rc, bits = hy.hydro_get_error(c)
+    assert rc == hy.HYDRO_OK, bits
+    # order: oct numbering x fastest, so the Morton order is the key order of the positions
+    rng = np.random.default_rng(21)
+    sel = np.concatenate([[0, no - 1, 127, 128 * 128 - 1], rng.choice(no, 300, replace=False)])
+    posh = pos.cpu().numpy()
+    assert np.array_equal(order.cpu().numpy(), ooct.sfc_order(posh))
+    # sampled octs: the oracle gathers each 6^3 stencil through its own neighbour table entries
+    nb = nbr.cpu().numpy()
+    for o in sel[:8]:
+        X, Y, Z = posh[o]
+        want = [((X + dx) % 128) + 128 * (((Y + dy) % 128) + 128 * ((Z + dz) % 128))
+                for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        assert np.array_equal(nb[o], want)
+    Vh = V[:, torch.as_tensor(np.unique(nb[sel]), device="cuda").long()]
+    lookup = {int(k): i for i, k in enumerate(np.unique(nb[sel]))}
+    Vsub = Vh.cpu().numpy()
+    d = dt.item()
+    got = out[:, torch.as_tensor(sel, device="cuda").long()].cpu().numpy()  # (5, S, 8)
+    want = np.empty_like(got)
+    for k, o in enumerate(sel):
+        table = np.array([[lookup[int(n)] for n in nb[o]]])
+        G = ooct.gather_stencil(Vsub, table, 0)
+        want[:, k] = oracle.step_patch(G, 1.0 / 256, d, cfg).reshape(5, 8)
+    err = fieldwise(got.transpose(1, 2, 0).reshape(-1, 5), want.transpose(1, 2, 0).reshape(-1, 5))
+    assert err.max() <= TOL["mixed"], err
+
+
+def test_4096_patches_ppm_mixed_sampled():
+    from oracle import ppm as oppm
+    cfg = oracle.config()
+    c = ctx("mixed", limiter="ppm")
+    # the bench's patch set and state (Mach 5: the scheme floors a few cells' pressure, both sides)
+    parent = workloads.turbulent_state(256, seed=3, sedov=False, device="cuda")
+    descs = workloads.patch_set(4096, seed=3)
+    origins = workloads.patch_origins(descs, parent.shape[1:], seed=3)
+    ins, outs, keep = [], [], []
+    for dsc, o in zip(descs, origins):
+        Ug = workloads.ghosted_from_periodic(parent, o, (dsc["nx"], dsc["ny"], dsc["nz"]), ghost=3).contiguous()
+        Vg = torch.empty_like(Ug)
+        keep.append((Ug, Vg))
+        ins.append(hy.patch(Ug, 3, dsc["dx"], dsc["level"]))
+        outs.append(hy.patch(Vg, 3, dsc["dx"], dsc["level"]))
+    dt = torch.empty(len(ins), dtype=torch.float64, device="cuda")
+    dn = torch.empty_like(dt)
+    hy.hydro_cfl_dt(c, ins, dt)
+    hy.hydro_step(c, ins, outs, dt, dn)
+    dn2 = torch.empty_like(dn)
+    hy.hydro_cfl_dt(c, outs, dn2)
+    torch.cuda.synchronize()
+    assert torch.equal(dn, dn2)
+    rng = np.random.default_rng(23)
+    big = sorted(range(len(descs)), key=lambda i: -descs[i]["nx"] * descs[i]["ny"] * descs[i]["nz"])[:2]
+    picks = sorted(set(big) | set(int(i) for i in rng.choice(len(descs), 10, replace=False)))
+    dth = dt.cpu().numpy()
+    for i in picks:
+        Ug, Vg = keep[i]
+        want = oppm.step_patch(Ug.cpu().numpy(), descs[i]["dx"], dth[i], cfg)
+        got = Vg[:, 3:-3, 3:-3, 3:-3].cpu().numpy()
+        err = fieldwise(got.reshape(5, -1).T, want.reshape(5, -1).T)
+        assert err.max() <= TOL["mixed"], (i, err)
