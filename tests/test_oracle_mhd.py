@@ -176,3 +176,27 @@ def test_circularly_polarised_alfven_wave_converges(limiter, min_order):
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert orders[-1] >= min_order, (errs, orders)
     assert errs[-1] < 2e-3, errs
+
+
+def test_ghosted_patch_step_is_the_periodic_step_of_its_cells():
+    """A patch cut from a periodic box with exact ghosts (two layers) steps to the box's own step on
+    its cells, including patches that wrap around the box."""
+    import workloads
+    shape = (12, 10, 14)
+    U = workloads.mhd_state(shape, seed=57, beta=0.5, mach=1.5, psi_amp=0.05)
+    cfg = oracle.config()
+    dx = 1.0 / 14
+    Un = U.numpy()
+    dt = mhd.cfl_periodic(Un, dx, cfg)
+    full = mhd.step_periodic(Un, dx, dt, cfg)
+    for origin, dims in (((0, 0, 0), (5, 4, 3)), ((12, 8, 10), (6, 5, 7)), ((2, 3, 4), (1, 1, 1))):
+        o, n = np.array(origin), np.array(dims)
+        ix = np.arange(o[0] - 2, o[0] + n[0] + 2) % shape[2]
+        iy = np.arange(o[1] - 2, o[1] + n[1] + 2) % shape[1]
+        iz = np.arange(o[2] - 2, o[2] + n[2] + 2) % shape[0]
+        Ug = Un[:, iz][:, :, iy][:, :, :, ix]
+        got = mhd.step_patch(Ug, dx, dt, cfg)
+        want = full[:, iz[2:-2]][:, :, iy[2:-2]][:, :, :, ix[2:-2]]
+        assert np.abs(got - want).max() <= 1e-15 * np.abs(full).max(), origin
+        sub = Un[:, iz[2:-2]][:, :, iy[2:-2]][:, :, :, ix[2:-2]]
+        assert mhd.cfl_patch(Ug, dx, cfg) == mhd.cfl_periodic(sub, dx, cfg)
