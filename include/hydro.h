@@ -282,6 +282,29 @@ int hydro_mhd_step(hydro_ctx* ctx, void* const in[9], void* const out[9], int nx
                    const double* dt_dev, double* dt_next_dev);
 int hydro_mhd_cfl_dt(hydro_ctx* ctx, void* const U[9], int nx, int ny, int nz, double dx, double* dt_dev);
 
+/* The same MHD step on AMR patches that carry two ghost layers filled by the caller (the paper's
+ * chunks carry their boundary cells, Sec. 3), many patches per call (one launch per stage over a
+ * block table of all patches).  A patch: */
+typedef struct {
+  void* U[9];        /* device pointers: rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi */
+  int nx, ny, nz;    /* interior cells */
+  int ng;            /* ghost layers: 2 (inputs and the CFL), 0 or 2 (outputs: only the interior is written) */
+  long long sy, sz;  /* element strides of y and z in the stored array; x stride 1 */
+  double dx;         /* cell size, > 0 */
+  int level;         /* refinement level (informational) */
+} hydro_mhd_patch;
+/*   hydro_mhd_step_patches: out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] (device
+ *       array of npatch doubles) and cell size in[p].dx; in[p] and out[p] of equal sizes and dx, not
+ *       overlapping; dt_next_dev: NULL or npatch doubles receiving each patch's CFL dt of U^{n+1}.
+ *       Device scratch of 81 elements per cell of each patch's interior grown by one cell per side.
+ *   hydro_mhd_cfl_patches: dt_dev[p] <- the CFL dt of each patch's interior (bit-identical to the
+ *       fused one).
+ * Precisions and errors as hydro_mhd_step.  The descriptors are uploaded when the patch set differs
+ * from the previous call's (the stream is synchronised first). */
+int hydro_mhd_step_patches(hydro_ctx* ctx, const hydro_mhd_patch* in, const hydro_mhd_patch* out, int npatch,
+                           const double* dt_dev, double* dt_next_dev);
+int hydro_mhd_cfl_patches(hydro_ctx* ctx, const hydro_mhd_patch* p, int npatch, double* dt_dev);
+
 /* Adjoint of one step with dt held fixed (the paper has no adjoint; this is the reverse mode of
  * hydro_step):  lam_n = (dU^{n+1}/dU^n)^T lam_np1, for periodic boxes (ng == 0) in HYDRO_FP64,
  * HYDRO_FP64_DF (which runs the FP64 reverse sweep: faster on GB300 than a double-float one) or

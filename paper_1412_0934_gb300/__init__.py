@@ -38,7 +38,8 @@ EBIT_TIMEOUT = 0x20
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",
-           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_mhd_step", "hydro_mhd_cfl_dt", "hydro_fill_ghosts", "hydro_fill_ghosts_time", "hydro_exchange_ghosts", "hydro_patch_fluxes",
+           "hydro_step_octs_level", "hydro_octs_build", "hydro_step_octs_table", "hydro_mhd_step", "hydro_mhd_cfl_dt",
+           "hydro_mhd_step_patches", "hydro_mhd_cfl_patches", "hydro_fill_ghosts", "hydro_fill_ghosts_time", "hydro_exchange_ghosts", "hydro_patch_fluxes",
            "hydro_level_fluxes", "hydro_reflux", "hydro_average_down",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
@@ -87,6 +88,9 @@ def lib():
         L.hydro_octs_build.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_int), vp, vp]
         L.hydro_mhd_step.argtypes = [vp, vp * 9, vp * 9, i, i, i, d, vp, vp]
         L.hydro_mhd_cfl_dt.argtypes = [vp, vp * 9, i, i, i, d, vp]
+        MP = ctypes.POINTER(hydro_mhd_patch)
+        L.hydro_mhd_step_patches.argtypes = [vp, MP, MP, i, vp, vp]
+        L.hydro_mhd_cfl_patches.argtypes = [vp, MP, i, vp]
         L.hydro_step_octs_table.argtypes = [vp, vp * 5, vp * 5, i, vp, vp, ll, d, vp]
         L.hydro_fill_ghosts.argtypes = [vp, PP, PP, ctypes.POINTER(ctypes.c_int), i]
         L.hydro_fill_ghosts_time.argtypes = [vp, PP, PP, d, PP, ctypes.POINTER(ctypes.c_int), i]
@@ -124,6 +128,42 @@ def hydro_status_string(status):
 def _check(rc, what):
     if rc != HYDRO_OK:
         raise HydroError(rc, what)
+
+
+class hydro_mhd_patch(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p * 9), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("ng", ctypes.c_int), ("sy", ctypes.c_longlong), ("sz", ctypes.c_longlong), ("dx", ctypes.c_double),
+                ("level", ctypes.c_int)]
+
+
+class MhdPatch:
+    """A hydro_mhd_patch plus the tensors it points into: fields (9, nz+2ng, ny+2ng, nx+2ng)."""
+
+    def __init__(self, fields, ng, dx, level=0):
+        fs = [fields[v] for v in range(9)] if isinstance(fields, torch.Tensor) else list(fields)
+        if len(fs) != 9:
+            raise ValueError("expected nine MHD fields")
+        for f in fs:
+            if not f.is_cuda or f.dim() != 3 or f.stride(2) != 1:
+                raise ValueError("MHD patch fields must be 3D CUDA tensors with unit x stride")
+            if f.shape != fs[0].shape or f.stride() != fs[0].stride() or f.dtype != fs[0].dtype:
+                raise ValueError("fields must share shape, strides and dtype")
+        Z, Y, X = fs[0].shape
+        self.tensors = fs
+        self.c = hydro_mhd_patch()
+        for v in range(9):
+            self.c.U[v] = fs[v].data_ptr()
+        self.c.nx, self.c.ny, self.c.nz = X - 2 * ng, Y - 2 * ng, Z - 2 * ng
+        self.c.ng = ng
+        self.c.sy = fs[0].stride(1)
+        self.c.sz = fs[0].stride(0)
+        self.c.dx = float(dx)
+        self.c.level = int(level)
+
+
+def _mhd_parray(patches):
+    patches = list(patches)
+    return (hydro_mhd_patch * len(patches))(*[p.c for p in patches]), len(patches)
 
 
 class Patch:
@@ -384,6 +424,21 @@ def hydro_mhd_step(ctx, U, out, dx, dt, dt_next=None):
     b, *_ = _mhd_fields(out)
     _check(lib().hydro_mhd_step(ctx.handle, a, b, nx, ny, nz, float(dx), _ptr(dt),
                                 _ptr(dt_next) if dt_next is not None else None), "hydro_mhd_step")
+
+
+def hydro_mhd_step_patches(ctx, inp, out, dt, dt_next=None):
+    """inp, out: lists of MhdPatch (ng 2 in; 0 or 2 out); dt: (npatch,) device doubles."""
+    a, n = _mhd_parray(inp)
+    b, m = _mhd_parray(out)
+    if m != n:
+        raise ValueError("one output patch per input patch")
+    _check(lib().hydro_mhd_step_patches(ctx.handle, a, b, n, _ptr(dt), _ptr(dt_next) if dt_next is not None else None),
+           "hydro_mhd_step_patches")
+
+
+def hydro_mhd_cfl_patches(ctx, patches, dt):
+    a, n = _mhd_parray(patches)
+    _check(lib().hydro_mhd_cfl_patches(ctx.handle, a, n, _ptr(dt)), "hydro_mhd_cfl_patches")
 
 
 def hydro_mhd_cfl_dt(ctx, U, dx, dt):

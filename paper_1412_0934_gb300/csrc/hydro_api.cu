@@ -88,9 +88,9 @@ struct hydro_ctx {
   int ntasks = 0;
   // flux registers (patch boxes, level boxes), refluxing, average-down: descriptors and block
   // tables of the last call of each kind (reused without an upload when unchanged)
-  static constexpr int kAux = 4;
-  char* d_aux[kAux] = {nullptr, nullptr, nullptr, nullptr};
-  size_t aux_cap[kAux] = {0, 0, 0, 0};
+  static constexpr int kAux = 6;  // 0, 1 box fluxes; 2 reflux; 3 average-down; 4 MHD step; 5 MHD CFL
+  char* d_aux[kAux] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t aux_cap[kAux] = {0, 0, 0, 0, 0, 0};
   std::vector<char> aux_last[kAux];
   // oct builder scratch: key bitmap, word prefix sums, block prefix sums
   unsigned* d_octs_scratch = nullptr;
@@ -1029,6 +1029,110 @@ int hydro_mhd_cfl_dt(hydro_ctx* c, void* const U[9], int nx, int ny, int nz, dou
   c->launches += 1;
   return cuda_status(
       hydro::launch_mhd_cfl(c->cfg.precision, mhd_box(U, nullptr, nx, ny, nz, dx), c->prm, dt_dev, c->d_err, c->stream));
+}
+
+// A patch of the batched MHD calls: sizes, ghost layers (2; 0 also allowed for an output unless
+// ghosts_only), strides and pointers.
+static bool mhd_patch_ok(const hydro_ctx* c, const hydro_mhd_patch& p, bool ghosts_only) {
+  if (p.nx < 1 || p.ny < 1 || p.nz < 1 || !finite_pos(p.dx)) return false;
+  if (p.ng != 2 && !(p.ng == 0 && !ghosts_only)) return false;
+  const long long gx = p.nx + 2LL * p.ng, gy = p.ny + 2LL * p.ng;
+  if (p.sy < gx || p.sz < p.sy * gy) return false;
+  if ((long long)(p.nx + 2) * (p.ny + 2) * (p.nz + 2) > 0x7fffff00LL) return false;
+  const int es = elem_size(c);
+  for (int v = 0; v < 9; ++v)
+    if (!p.U[v] || reinterpret_cast<uintptr_t>(p.U[v]) % es) return false;
+  return true;
+}
+
+static size_t mhd_patch_bytes(const hydro_ctx* c, const hydro_mhd_patch& p) {
+  return (size_t)(p.nz + 2 * p.ng) * (size_t)p.sz * elem_size(c);
+}
+
+// Descriptors and the block table (256 extended cells of one patch per block) of a patch set,
+// uploaded (or reused) as aux kind `kind`; returns the device descriptors, blocks and count.
+static int mhd_patch_tables(hydro_ctx* c, int kind, const hydro_mhd_patch* in, const hydro_mhd_patch* out, int npatch,
+                            const hydro::HostMhdPatch** d_patches, const int2** d_blocks, int* nblocks,
+                            size_t* scratch_elems) {
+  std::vector<hydro::HostMhdPatch> set((size_t)npatch);
+  std::vector<int2> blocks;
+  long long off = 0;
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_mhd_patch& I = in[i];
+    const hydro_mhd_patch& O = out ? out[i] : in[i];
+    hydro::HostMhdPatch& h = set[i];
+    for (int v = 0; v < 9; ++v) {
+      h.in[v] = I.U[v];
+      h.out[v] = O.U[v];
+    }
+    h.nx = I.nx; h.ny = I.ny; h.nz = I.nz; h.gout = O.ng;
+    h.isy = I.sy; h.isz = I.sz; h.osy = O.sy; h.osz = O.sz;
+    h.dx = I.dx;
+    h.scratch = off;
+    const long long ec = (long long)(I.nx + 2) * (I.ny + 2) * (I.nz + 2);
+    off += 81 * ec;
+    for (long long f = 0; f < ec; f += 256) blocks.push_back(make_int2(i, (int)f));
+  }
+  if (blocks.size() > 0x7fffffff) return HYDRO_ERR_ARG;
+  std::vector<char> bytes;
+  const size_t op = append(bytes, set.data(), set.size());
+  const size_t ob = append(bytes, blocks.data(), blocks.size());
+  char* d = upload_aux(c, kind, bytes);
+  if (!d) return HYDRO_ERR_CUDA;
+  *d_patches = reinterpret_cast<const hydro::HostMhdPatch*>(d + op);
+  *d_blocks = reinterpret_cast<const int2*>(d + ob);
+  *nblocks = (int)blocks.size();
+  *scratch_elems = (size_t)off;
+  return HYDRO_OK;
+}
+
+int hydro_mhd_step_patches(hydro_ctx* c, const hydro_mhd_patch* in, const hydro_mhd_patch* out, int npatch,
+                           const double* dt_dev, double* dt_next_dev) {
+  if (!c || !in || !out || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  if (c->cfg.precision == HYDRO_MIXED || ppm(c)) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i) {
+    const hydro_mhd_patch &I = in[i], &O = out[i];
+    if (!mhd_patch_ok(c, I, true) || !mhd_patch_ok(c, O, false)) return HYDRO_ERR_ARG;
+    if (I.nx != O.nx || I.ny != O.ny || I.nz != O.nz || I.dx != O.dx) return HYDRO_ERR_ARG;
+    const size_t bi = mhd_patch_bytes(c, I), bo = mhd_patch_bytes(c, O);
+    for (int v = 0; v < 9; ++v)  // the output is written while the input is read: no overlap
+      for (int u = 0; u < 9; ++u) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(O.U[v]), b = reinterpret_cast<uintptr_t>(I.U[u]);
+        if (a < b + bi && b < a + bo) return HYDRO_ERR_ARG;
+      }
+  }
+  const hydro::HostMhdPatch* dp = nullptr;
+  const int2* db = nullptr;
+  int nb = 0;
+  size_t elems = 0;
+  int rc = mhd_patch_tables(c, 4, in, out, npatch, &dp, &db, &nb, &elems);
+  if (rc) return rc;
+  rc = ensure_device(&c->d_mhd, &c->mhd_cap, hydro::mhd_patch_consts_bytes(npatch) + elems * elem_size(c));
+  if (rc) return rc;
+  if (dt_next_dev) {
+    rc = reset_slots(c, dt_next_dev, npatch, c->stream);
+    if (rc) return rc;
+  }
+  c->launches += 4;
+  return cuda_status(hydro::launch_mhd_patches(c->cfg.precision, dp, db, nb, npatch, c->prm, dt_dev, dt_next_dev,
+                                               c->d_mhd, c->d_err, c->stream));
+}
+
+int hydro_mhd_cfl_patches(hydro_ctx* c, const hydro_mhd_patch* p, int npatch, double* dt_dev) {
+  if (!c || !p || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
+  if (c->cfg.precision == HYDRO_MIXED || ppm(c)) return HYDRO_ERR_ARG;
+  for (int i = 0; i < npatch; ++i)
+    if (!mhd_patch_ok(c, p[i], true)) return HYDRO_ERR_ARG;
+  const hydro::HostMhdPatch* dp = nullptr;
+  const int2* db = nullptr;
+  int nb = 0;
+  size_t elems = 0;
+  int rc = mhd_patch_tables(c, 5, p, nullptr, npatch, &dp, &db, &nb, &elems);
+  if (rc) return rc;
+  rc = reset_slots(c, dt_dev, npatch, c->stream);
+  if (rc) return rc;
+  c->launches += 1;
+  return cuda_status(hydro::launch_mhd_patches_cfl(c->cfg.precision, dp, db, nb, c->prm, dt_dev, c->d_err, c->stream));
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

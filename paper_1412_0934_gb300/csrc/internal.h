@@ -154,6 +154,23 @@ struct HostMhdBox {
   double dx;
 };
 size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size);
+// A patch of the batched MHD step (two ghost layers in, 0 or 2 out): its scratch, 81 elements per
+// cell of its extended box (nx+2)(ny+2)(nz+2), starts at element offset `scratch` of the scratch
+// body, which follows mhd_patch_consts_bytes(npatch) bytes of per-patch constants.
+struct HostMhdPatch {
+  const void* in[9];
+  void* out[9];
+  int nx, ny, nz, gout;
+  long long isy, isz, osy, osz;
+  double dx;
+  long long scratch;
+};
+size_t mhd_patch_consts_bytes(int npatch);
+cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
+                               int npatch, const Params& prm, const double* dt, double* dt_next, void* scratch,
+                               unsigned* err, cudaStream_t s);
+cudaError_t launch_mhd_patches_cfl(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
+                                   const Params& prm, double* dt, unsigned* err, cudaStream_t s);
 cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
                             void* scratch, unsigned* err, cudaStream_t s);
 cudaError_t launch_mhd_cfl(int precision, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,

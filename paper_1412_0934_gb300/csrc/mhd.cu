@@ -459,7 +459,274 @@ cudaError_t mhd_cfl_t(const HostMhdBox& h, const Params& prm, double* dt, unsign
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ patches with two ghost layers
+// The same step on many patches in one set of launches.  Each patch's extended box is its interior
+// and one ring cell beyond each face, (nx+2)(ny+2)(nz+2) cells: the face states are formed there
+// (the ring cells' from the ghost layers), the low-face fluxes on the cells [0, n] of each axis,
+// the update on the interior.  Block b of every launch takes extended cells blocks[b].y ..
+// blocks[b].y + 255 of patch blocks[b].x; a patch's scratch starts at its own element offset.
+struct ExtCell {
+  int i, j, k;  // -1 .. n per axis
+  bool ring;    // outside the interior
+};
+
+__device__ __forceinline__ bool ext_cell(const HostMhdPatch& P, int t, ExtCell& e) {
+  const int ex = P.nx + 2, ey = P.ny + 2;
+  if (t >= ex * ey * (P.nz + 2)) return false;
+  const int row = t / ex, z = row / ey;
+  e.i = t - row * ex - 1;
+  e.j = row - z * ey - 1;
+  e.k = z - 1;
+  e.ring = e.i < 0 || e.j < 0 || e.k < 0 || e.i >= P.nx || e.j >= P.ny || e.k >= P.nz;
+  return true;
+}
+
+__device__ __forceinline__ long long in_addr(const HostMhdPatch& P, int i, int j, int k) {
+  return (long long)(k + 2) * P.isz + (long long)(j + 2) * P.isy + (i + 2);
+}
+
+template <class Pol>
+__device__ __forceinline__ void load_qp(const HostMhdPatch& P, long long a, const MhdConst<typename Pol::R>& c,
+                                        typename Pol::R q[NV], unsigned& flags) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  R U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(static_cast<const S*>(P.in[v]) + a), (R*)nullptr);
+  mhd_recover(U, c, q, flags);
+}
+
+template <class R>
+__global__ void k_mhdp_consts(const HostMhdPatch* patches, int npatch, MhdConst<R> base, double cfl, double alpha,
+                              const double* dt_dev, MhdConst<R>* out, unsigned* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npatch) return;
+  const double dt = dt_dev[p], dx = patches[p].dx;
+  MhdConst<R> c = base;
+  c.valid = dt > 0.0 && dt <= 1e300;
+  if (!c.valid) {
+    atomicOr(err, HYDRO_EBIT_BAD_DT);
+  } else {
+    const double ch = (cfl / 3.0) * dx / dt;
+    c.ch = R(ch);
+    c.ch2 = R(ch * ch);
+    c.hdt = R(0.5 * dt / dx);
+    c.dtdx = R(dt / dx);
+    c.damp = R(exp(-alpha * ch * dt / dx));
+  }
+  out[p] = c;
+}
+
+template <int D, class Pol>
+__device__ __forceinline__ void axis_states_p(const HostMhdPatch& P, typename Pol::R* face, long long ec, long long e,
+                                              const ExtCell& x, const typename Pol::R q[NV],
+                                              const MhdConst<typename Pol::R>& c, typename Pol::R dF[NV]) {
+  using R = typename Pol::R;
+  unsigned nf = 0;  // neighbours are flagged by their own threads
+  const int di = D == 0, dj = D == 1, dk = D == 2;
+  R lo[NV], hi[NV];
+  {
+    R qm[NV], qp[NV];
+    load_qp<Pol>(P, in_addr(P, x.i - di, x.j - dj, x.k - dk), c, qm, nf);
+    load_qp<Pol>(P, in_addr(P, x.i + di, x.j + dj, x.k + dk), c, qp, nf);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
+      lo[v] = q[v] - half_(s);
+      hi[v] = q[v] + half_(s);
+      face[((long long)(2 * D) * NV + v) * ec + e] = lo[v];
+      face[((long long)(2 * D + 1) * NV + v) * ec + e] = hi[v];
+    }
+  }
+  R Fh[NV];
+  mhd_flux<D>(hi, c, Fh);
+  {
+    R Fl[NV];
+    mhd_flux<D>(lo, c, Fl);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dF[v] = D == 0 ? Fh[v] - Fl[v] : dF[v] + (Fh[v] - Fl[v]);
+  }
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256, 2) k_mhdp_predict(const HostMhdPatch* patches, const int2* blocks,
+                                                         const MhdConst<typename Pol::R>* consts, void* scratch,
+                                                         unsigned* err) {
+  using R = typename Pol::R;
+  const int2 b = blocks[blockIdx.x];
+  const HostMhdPatch P = patches[b.x];
+  const MhdConst<R> c = consts[b.x];
+  ExtCell x;
+  if (!c.valid || !ext_cell(P, b.y + threadIdx.x, x)) return;
+  const long long ec = (long long)(P.nx + 2) * (P.ny + 2) * (P.nz + 2), e = b.y + threadIdx.x;
+  R* face = static_cast<R*>(scratch) + P.scratch;
+  unsigned flags = 0;
+  R q[NV], dF[NV];
+  load_qp<Pol>(P, in_addr(P, x.i, x.j, x.k), c, q, flags);
+  axis_states_p<0, Pol>(P, face, ec, e, x, q, c, dF);
+  axis_states_p<1, Pol>(P, face, ec, e, x, q, c, dF);
+  axis_states_p<2, Pol>(P, face, ec, e, x, q, c, dF);
+  unsigned nf = 0;
+#pragma unroll 1
+  for (int f = 0; f < 6; ++f) {
+    R w[NV], U[NV], r[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = face[((long long)f * NV + v) * ec + e];
+    mhd_conserved(w, c, U);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
+    mhd_recover(U, c, r, nf);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) face[((long long)f * NV + v) * ec + e] = r[v];
+  }
+  if (!x.ring && flags) atomicOr(err, flags);  // the interior's own recovery; ghosts are flagged by their owners
+}
+
+template <int D, class Pol>
+__device__ __forceinline__ void low_face_flux_p(const typename Pol::R* face, typename Pol::R* flux, long long ec,
+                                                long long e, long long em, const MhdConst<typename Pol::R>& c) {
+  using R = typename Pol::R;
+  R qL[NV], qR[NV], F[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    qL[v] = face[((long long)(2 * D + 1) * NV + v) * ec + em];  // high face of the cell below
+    qR[v] = face[((long long)(2 * D) * NV + v) * ec + e];       // low face of this cell
+  }
+  mhd_hll<D>(qL, qR, c, F);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) flux[((long long)D * NV + v) * ec + e] = F[v];
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256, 2) k_mhdp_flux(const HostMhdPatch* patches, const int2* blocks,
+                                                      const MhdConst<typename Pol::R>* consts, void* scratch) {
+  using R = typename Pol::R;
+  const int2 b = blocks[blockIdx.x];
+  const HostMhdPatch P = patches[b.x];
+  const MhdConst<R> c = consts[b.x];
+  ExtCell x;
+  if (!c.valid || !ext_cell(P, b.y + threadIdx.x, x)) return;
+  if (x.i < 0 || x.j < 0 || x.k < 0) return;  // low faces of the cells 0 .. n per axis
+  const long long ex = P.nx + 2, ey = P.ny + 2, ec = ex * ey * (P.nz + 2), e = b.y + threadIdx.x;
+  const R* face = static_cast<const R*>(scratch) + P.scratch;
+  R* flux = static_cast<R*>(scratch) + P.scratch + 6LL * NV * ec;
+  if (x.j < P.ny && x.k < P.nz) low_face_flux_p<0, Pol>(face, flux, ec, e, e - 1, c);
+  if (x.i < P.nx && x.k < P.nz) low_face_flux_p<1, Pol>(face, flux, ec, e, e - ex, c);
+  if (x.i < P.nx && x.j < P.ny) low_face_flux_p<2, Pol>(face, flux, ec, e, e - ex * ey, c);
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256, 2) k_mhdp_update(const HostMhdPatch* patches, const int2* blocks,
+                                                        const MhdConst<typename Pol::R>* consts, void* scratch,
+                                                        double cfl, double* dt_next, unsigned* err) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  const int2 b = blocks[blockIdx.x];
+  const HostMhdPatch P = patches[b.x];
+  const MhdConst<R> c = consts[b.x];
+  if (!c.valid) return;  // (block-uniform)
+  ExtCell x;
+  const bool live = ext_cell(P, b.y + threadIdx.x, x) && !x.ring;
+  unsigned flags = 0;
+  R smax = R(0);
+  if (live) {
+    const long long ex = P.nx + 2, ey = P.ny + 2, ec = ex * ey * (P.nz + 2), e = b.y + threadIdx.x;
+    const R* flux = static_cast<const R*>(scratch) + P.scratch + 6LL * NV * ec;
+    const long long ai = in_addr(P, x.i, x.j, x.k);
+    const long long ao = (long long)(x.k + P.gout) * P.osz + (long long)(x.j + P.gout) * P.osy + (x.i + P.gout);
+    S Un[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R* fx = flux + (long long)(0 * NV + v) * ec;
+      const R* fy = flux + (long long)(1 * NV + v) * ec;
+      const R* fz = flux + (long long)(2 * NV + v) * ec;
+      const R div = ((fx[e + 1] - fx[e]) + (fy[e + ex] - fy[e])) + (fz[e + ex * ey] - fz[e]);
+      Un[v] = Pol::update(__ldg(static_cast<const S*>(P.in[v]) + ai), c.dtdx, div);
+    }
+    Un[8] = Un[8] * (S)to_double(c.damp);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) static_cast<S*>(P.out[v])[ao] = Un[v];
+    if (dt_next) {
+      R U[NV], q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
+      mhd_recover(U, c, q, flags);
+      smax = mhd_speed(q, c);
+    }
+  }
+  if (dt_next) {
+    const R m = block_max_r(smax);
+    if (threadIdx.x == 0) publish_dt(cfl, P.dx, to_double(m), dt_next + b.x);
+  }
+  flush_flags(flags, err);
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256) k_mhdp_cfl(const HostMhdPatch* patches, const int2* blocks,
+                                                  MhdConst<typename Pol::R> c, double cfl, double* dt, unsigned* err) {
+  using R = typename Pol::R;
+  const int2 b = blocks[blockIdx.x];
+  const HostMhdPatch P = patches[b.x];
+  ExtCell x;
+  unsigned flags = 0;
+  R smax = R(0);
+  if (ext_cell(P, b.y + threadIdx.x, x) && !x.ring) {
+    R q[NV];
+    load_qp<Pol>(P, in_addr(P, x.i, x.j, x.k), c, q, flags);
+    smax = mhd_speed(q, c);
+  }
+  const R m = block_max_r(smax);
+  if (threadIdx.x == 0) publish_dt(cfl, P.dx, to_double(m), dt + b.x);
+  flush_flags(flags, err);
+}
+
+template <class Pol>
+cudaError_t mhd_patches_t(const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks, int npatch,
+                          const Params& prm, const double* dt, double* dt_next, void* scratch, unsigned* err,
+                          cudaStream_t s) {
+  using R = typename Pol::R;
+  auto* consts = static_cast<MhdConst<R>*>(scratch);
+  void* body = static_cast<char*>(scratch) + mhd_patch_consts_bytes(npatch);
+  k_mhdp_consts<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, consts_of<R>(prm), prm.cfl, kMhdAlpha, dt,
+                                                        consts, err);
+  k_mhdp_predict<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, err);
+  k_mhdp_flux<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body);
+  k_mhdp_update<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, prm.cfl, dt_next, err);
+  return cudaGetLastError();
+}
+
+template <class Pol>
+cudaError_t mhd_patches_cfl_t(const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks, const Params& prm,
+                              double* dt, unsigned* err, cudaStream_t s) {
+  k_mhdp_cfl<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts_of<typename Pol::R>(prm), prm.cfl, dt, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t mhd_patch_consts_bytes(int npatch) { return ((size_t)npatch * 128 + 255) / 256 * 256; }
+
+cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
+                               int npatch, const Params& prm, const double* dt, double* dt_next, void* scratch,
+                               unsigned* err, cudaStream_t s) {
+  static_assert(sizeof(MhdConst<double>) <= 128 && sizeof(MhdConst<df>) <= 128, "per-patch constants slot");
+  switch (precision) {
+    case HYDRO_FP64: return mhd_patches_t<PolF64>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_FP32: return mhd_patches_t<PolF32>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_FP64_DF: return mhd_patches_t<PolDF>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mhd_patches_cfl(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
+                                   const Params& prm, double* dt, unsigned* err, cudaStream_t s) {
+  switch (precision) {
+    case HYDRO_FP64: return mhd_patches_cfl_t<PolF64>(d_patches, d_blocks, nblocks, prm, dt, err, s);
+    case HYDRO_FP32: return mhd_patches_cfl_t<PolF32>(d_patches, d_blocks, nblocks, prm, dt, err, s);
+    case HYDRO_FP64_DF: return mhd_patches_cfl_t<PolDF>(d_patches, d_blocks, nblocks, prm, dt, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size) {
   return (size_t)9 * NV * (size_t)nx * ny * nz * elem_size + 256;

@@ -1,7 +1,7 @@
-"""GPU parity of the MHD step (ideal MHD with GLM cleaning, periodic box) against the MHD oracle
-(oracle/mhd.py), through the C ABI: small boxes element by element for each limiter and precision,
-a circularly polarised Alfven wave over a period, the fused dt, conservation, a 256^3 box on
-sampled windows, and the argument checks."""
+"""GPU parity of the MHD step (ideal MHD with GLM cleaning) against the MHD oracle (oracle/mhd.py),
+through the C ABI: periodic boxes element by element for each limiter and precision, a circularly
+polarised Alfven wave over a period, the fused dt, conservation, a 256^3 box on sampled windows,
+batched patches with two ghost layers, and the argument checks."""
 import numpy as np
 import pytest
 import torch
@@ -138,6 +138,70 @@ def test_mhd_full_size_sampled_windows():
         got = g[:, iz[2:10]][:, :, iy[2:10]][:, :, :, ix[2:10]]
         err = np.abs(got - ref).max(axis=(1, 2, 3)) / np.abs(U).max(axis=(1, 2, 3))
         assert err.max() <= 1e-12, ((x, y, z), err)
+
+
+def _ghosted(U, origin, dims, g):
+    o = np.asarray(origin)
+    _, NZ, NY, NX = U.shape
+    ix = np.arange(o[0] - g, o[0] + dims[0] + g) % NX
+    iy = np.arange(o[1] - g, o[1] + dims[1] + g) % NY
+    iz = np.arange(o[2] - g, o[2] + dims[2] + g) % NZ
+    return U[:, iz][:, :, iy][:, :, :, ix]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32"])
+def test_mhd_patches_match_oracle(precision):
+    """Patches with two ghost layers (sizes 1 to 40, a 2:1 box, one patch wrapping the parent, dx
+    and dt per patch) in one batched call: each against the oracle's ghosted-patch step; outputs with
+    and without ghost layers; the fused per-patch dt equals hydro_mhd_cfl_patches bit for bit."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    parent = workloads.mhd_state((30, 26, 34), seed=66, beta=0.5, mach=1.5, psi_amp=0.05).numpy()
+    rng = np.random.default_rng(67)
+    dims = [(16, 16, 16), (20, 9, 40), (5, 13, 7), (1, 2, 3), (12, 12, 24), (8, 8, 8)]
+    origins = [tuple(int(v) for v in rng.integers(0, 26, 3)) for _ in dims]
+    origins[0] = (30, 22, 27)
+    cfg = oracle.config()
+    c = ctx(precision)
+    host, ins, outs, dtl = [], [], [], []
+    for k, (d, o) in enumerate(zip(dims, origins)):
+        dx = 1.0 / (16 * (1 + k % 3))
+        Ug = _ghosted(parent, o, d, 2)
+        host.append((Ug, dx))
+        dtl.append(0.8 * omhd.cfl_patch(Ug, dx, cfg))
+        a = torch.as_tensor(Ug).to(device="cuda", dtype=dtype).contiguous()
+        ng_out = 2 if k % 2 else 0
+        b = torch.full((9, d[2] + 2 * ng_out, d[1] + 2 * ng_out, d[0] + 2 * ng_out), 7.0, dtype=dtype, device="cuda")
+        ins.append(hy.MhdPatch(a, 2, dx))
+        outs.append(hy.MhdPatch(b, ng_out, dx))
+    dn = torch.empty(len(dims), dtype=torch.float64, device="cuda")
+    hy.hydro_mhd_step_patches(c, ins, outs, dts(*dtl), dn)
+    torch.cuda.synchronize()
+    check_clean(c)
+    for (Ug, dx), po, dtp in zip(host, outs, dtl):
+        g = torch.stack(po.tensors).double().cpu().numpy()
+        ng = po.c.ng
+        gi = g[:, ng:g.shape[1] - ng, ng:g.shape[2] - ng, ng:g.shape[3] - ng]
+        ref = omhd.step_patch(Ug, dx, dtp, cfg)
+        err = normwise(gi, ref)
+        assert err.max() <= TOL[precision], (Ug.shape, err)
+        if ng:
+            assert (g[:, :2] == 7.0).all() and (g[:, -2:] == 7.0).all()
+    # the CFL of the results, through patches that carry two ghost layers
+    res = []
+    for po, (Ug, dx) in zip(outs, host):
+        t = torch.stack(po.tensors)
+        ng = po.c.ng
+        full = torch.zeros((9,) + tuple(s + 4 - 2 * ng for s in t.shape[1:]), dtype=dtype, device="cuda")
+        full[:, 2:-2, 2:-2, 2:-2] = t[:, ng:t.shape[1] - ng, ng:t.shape[2] - ng, ng:t.shape[3] - ng]
+        res.append(hy.MhdPatch(full.contiguous(), 2, dx))
+    d2 = torch.empty_like(dn)
+    hy.hydro_mhd_cfl_patches(c, res, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(dn, d2)
+    if precision != "fp32":
+        for k, (po, (Ug, dx)) in enumerate(zip(res, host)):
+            want = omhd.cfl_patch(torch.stack(po.tensors).cpu().numpy(), dx, cfg)
+            assert abs(dn[k].item() - want) <= 1e-12 * want
 
 
 def test_mhd_argument_checks_and_bad_dt():
