@@ -601,6 +601,52 @@ def form_mhd(hy, precision, steps, warmup, n=256):
     return out
 
 
+def form_mhd_patches(hy, precision, steps, warmup, npatch=512):
+    """MHD on AMR patches (two ghost layers, the patch-size mix of the batched hydro form, cut from
+    a 256^3 magnetised-gas parent), one batched call per step, per-patch dt and fused dt_next."""
+    import workloads
+    stream = torch.cuda.current_stream()
+    ctx = hy.hydro_init(precision=precision, limiter="minmod")
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    parent = workloads.mhd_state(256, seed=7, beta=0.5, mach=2.0, device="cuda").to(dtype)
+    descs = workloads.patch_set(npatch, seed=3)
+    origins = workloads.patch_origins(descs, parent.shape[1:], seed=3)
+    ins, outs, keep = [], [], []
+    interior = 0
+    _, NZ, NY, NX = parent.shape
+    for d, o in zip(descs, origins):
+        ix = (torch.arange(o[0] - 2, o[0] + d["nx"] + 2, device="cuda") % NX)
+        iy = (torch.arange(o[1] - 2, o[1] + d["ny"] + 2, device="cuda") % NY)
+        iz = (torch.arange(o[2] - 2, o[2] + d["nz"] + 2, device="cuda") % NZ)
+        Ug = parent[:, iz][:, :, iy][:, :, :, ix].contiguous()
+        Vg = torch.empty_like(Ug)
+        keep += [Ug, Vg]
+        ins.append(hy.MhdPatch(Ug, 2, d["dx"], d["level"]))
+        outs.append(hy.MhdPatch(Vg, 2, d["dx"], d["level"]))
+        interior += d["nx"] * d["ny"] * d["nz"]
+    dt = torch.empty(len(ins), dtype=torch.float64, device="cuda")
+    dn = torch.empty_like(dt)
+    hy.hydro_mhd_cfl_patches(ctx, ins, dt)
+    for _ in range(warmup):
+        hy.hydro_mhd_step_patches(ctx, ins, outs, dt, dn)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        hy.hydro_mhd_step_patches(ctx, ins, outs, dt, dn)  # same input each step: the per-patch dt stays valid
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    rc, bits = hy.hydro_get_error(ctx)
+    out = {"patches": len(ins), "interior_cells": interior, "ms_per_step": ms,
+           "mcell_updates_per_s": interior / (ms / 1e3) / 1e6, "launches_per_step": 4, "error_bits": bits,
+           "note": "MHD on the first 512 patches of the batched hydro form's patch set, two ghost layers"}
+    del keep, parent
+    hy.hydro_finalize(ctx)
+    torch.cuda.empty_cache()
+    return out
+
+
 def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
     """One two-level AMR cycle, mixed precision: a 256^3 fine level tiled by 16^3 patches of random
     even edges (cuts at random even positions per axis) over a 128^3 coarse level.  Per cycle: the
@@ -859,6 +905,7 @@ def run_forms(hy, args, n, precision):
             elif f == "mhd":
                 for prec in ("fp64", "df64", "fp32"):
                     extra["mhd_256_" + prec] = form_mhd(hy, prec, args.steps, args.warmup)
+                extra["mhd_patches_fp32"] = form_mhd_patches(hy, "fp32", max(3, args.steps // 2), 2)
             elif f == "graph1024":
                 extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                            sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,
