@@ -200,3 +200,27 @@ def test_ghosted_patch_step_is_the_periodic_step_of_its_cells():
         assert np.abs(got - want).max() <= 1e-15 * np.abs(full).max(), origin
         sub = Un[:, iz[2:-2]][:, :, iy[2:-2]][:, :, :, ix[2:-2]]
         assert mhd.cfl_patch(Ug, dx, cfg) == mhd.cfl_periodic(sub, dx, cfg)
+
+
+def test_sod_at_zero_field_converges_to_the_exact_euler_solution():
+    """With B = 0 and psi = 0 the MHD step is an Euler solver (HLL): on Sod's shock tube at gamma
+    1.4 its density converges at first order to the exact Riemann solution and the field stays 0."""
+    import workloads
+    from oracle import riemann_exact
+    cfg = oracle.config(gamma=1.4)
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = []
+    for n in (64, 128, 256):
+        U = np.zeros((9, 4, 4, n))
+        U[:5] = workloads.riemann_1d(n, left, right, axis=0, ntrans=4, gamma=1.4).numpy()
+        dx, t = 1.0 / n, 0.0
+        while t < 0.2 - 1e-15:
+            Ug = np.pad(U, ((0, 0), (2, 2), (2, 2), (2, 2)), mode="edge")
+            dt = min(mhd.cfl_periodic(U, dx, cfg), 0.2 - t)
+            U = mhd.step_patch(Ug, dx, dt, cfg)
+            t += dt
+        xc = (np.arange(n) + 0.5) / n
+        errs.append(np.abs(U[0, 1, 1, :] - riemann_exact.sample(left, right, 1.4, (xc - 0.5) / 0.2)[0]).mean())
+        assert np.all(U[5:] == 0.0)
+    assert errs[0] > errs[1] > errs[2] and errs[0] / errs[2] > 2.5, errs
+    assert errs[2] < 0.005, errs

@@ -131,3 +131,28 @@ def test_ghosted_patch_step_is_the_periodic_step_of_its_cells():
         iz = np.arange(origin[2], origin[2] + dims[2]) % shape[0]
         want = full[:, iz][:, :, iy][:, :, :, ix]
         assert np.abs(got - want).max() <= 1e-15 * np.abs(full).max(), origin
+
+
+def test_sod_converges_to_the_exact_solution_below_plm():
+    """Sod's shock tube at gamma 1.4 (zero-gradient ends): the L1 density error against the exact
+    Riemann solution falls at first order (discontinuities) and stays below PLM/MinMod's."""
+    from oracle import riemann_exact
+    cfg = oracle.config(gamma=1.4)
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+
+    def l1(n, stepper, g):
+        U = workloads.riemann_1d(n, left, right, axis=0, ntrans=4, gamma=1.4).numpy()
+        dx, t = 1.0 / n, 0.0
+        while t < 0.2 - 1e-15:
+            Ug = np.pad(U, ((0, 0), (g, g), (g, g), (g, g)), mode="edge")
+            dt = min(oracle.cfl_periodic(U, dx, cfg), 0.2 - t)
+            U = stepper(Ug, dx, dt, cfg)
+            t += dt
+        xc = (np.arange(n) + 0.5) / n
+        return np.abs(U[0, 1, 1, :] - riemann_exact.sample(left, right, 1.4, (xc - 0.5) / 0.2)[0]).mean()
+
+    e = [l1(n, ppm.step_patch, 3) for n in (64, 128, 256)]
+    plm = [l1(n, oracle.step_patch, 2) for n in (64, 128, 256)]
+    assert e[0] > e[1] > e[2] and e[0] / e[2] > 2.5, e
+    assert e[2] < 0.003, e
+    assert all(a < b for a, b in zip(e, plm)), (e, plm)
