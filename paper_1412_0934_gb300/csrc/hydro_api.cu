@@ -1011,13 +1011,15 @@ int hydro_mhd_step(hydro_ctx* c, void* const in[9], void* const out[9], int nx, 
       const uintptr_t a = reinterpret_cast<uintptr_t>(out[v]), b = reinterpret_cast<uintptr_t>(in[u]);
       if (a < b + bytes && b < a + bytes) return HYDRO_ERR_ARG;
     }
+  int rc = ensure_device(&c->d_mhd, &c->mhd_cap, hydro::mhd_scratch_bytes(nx, ny, nz, elem_size(c)));
+  if (rc) return rc;
   if (dt_next_dev) {
-    const int rc = reset_slots(c, dt_next_dev, 1, c->stream);
+    rc = reset_slots(c, dt_next_dev, 1, c->stream);
     if (rc) return rc;
   }
-  c->launches += 1;
+  c->launches += 4;
   return cuda_status(hydro::launch_mhd_step(c->cfg.precision, mhd_box(in, out, nx, ny, nz, dx), c->prm, dt_dev,
-                                            dt_next_dev, c->d_err, c->stream));
+                                            dt_next_dev, c->d_mhd, c->d_err, c->stream));
 }
 
 int hydro_mhd_cfl_dt(hydro_ctx* c, void* const U[9], int nx, int ny, int nz, double dx, double* dt_dev) {

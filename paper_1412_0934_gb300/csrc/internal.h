@@ -172,7 +172,7 @@ cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, con
 cudaError_t launch_mhd_patches_cfl(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
                                    const Params& prm, double* dt, unsigned* err, cudaStream_t s);
 cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
-                            unsigned* err, cudaStream_t s);
+                            void* scratch, unsigned* err, cudaStream_t s);
 cudaError_t launch_mhd_cfl(int precision, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,
                            cudaStream_t s);
 

@@ -20,7 +20,6 @@
 // double).
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <cmath>
 
 #include "hydro_device.cuh"
@@ -438,294 +437,19 @@ int grid_for(long long cells) {
   return (int)(b < 1 ? 1 : (b > 152LL * 64 ? 152LL * 64 : b));
 }
 
-// ------------------------------------------------------------------ single-pass tile kernel
-// The periodic box in one launch: a TX x TY column tile marching up z (as the hydro step).  Shared
-// memory holds a ring of three recovered planes (p-1, p, p+1) over the tile and two halo cells each
-// side, the x- and y-face states of plane p (the tile's cells and one ring cell beyond each edge),
-// the x and y fluxes of plane p, and each column's z-high face state of the plane below.  That plane
-// is updated one plane later, from the z flux below it (in registers) and its x and y fluxes (still
-// in shared memory until the next plane's flux phase).  No scratch in global memory.
-template <class R, int TX, int TY>
-struct MhdTileShared {
-  static constexpr int QX = TX + 4, QY = TY + 4;
-  R q[3][NV][QY][QX];       // ring of recovered planes: [slot][var][y + 2][x + 2]
-  R wx[2][NV][TY][TX + 2];  // x-face states of plane p: [low/high face][var][y][x + 1]
-  R wy[2][NV][TY + 2][TX];  // y-face states: [low/high][var][y + 1][x]
-  R fx[NV][TY][TX + 1];     // flux through the low x face of cell x, x = 0 .. TX
-  R fy[NV][TY + 1][TX];     // flux through the low y face of cell y, y = 0 .. TY
-  R zs[NV][TY][TX];         // each column's z-high face state of the plane below (its own slot)
-  int sx[QX], sy[QY];       // wrapped grid index of each tile column / row
-  R red[TX * TY / 32];
-};
-
-__device__ __forceinline__ int wrap_i(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
-// Limited slopes of the middle-plane cell at (X, Y) (ring coordinates) along axis D, all fields.
-template <int D, class R, int TX, int TY>
-__device__ __forceinline__ void tile_slopes(const MhdTileShared<R, TX, TY>& sm, const int sl[3], int X, int Y,
-                                            const R q[NV], int lim, R sl_out[NV]) {
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const R m = D == 0 ? sm.q[sl[1]][v][Y][X - 1] : (D == 1 ? sm.q[sl[1]][v][Y - 1][X] : sm.q[sl[0]][v][Y][X]);
-    const R p = D == 0 ? sm.q[sl[1]][v][Y][X + 1] : (D == 1 ? sm.q[sl[1]][v][Y + 1][X] : sm.q[sl[2]][v][Y][X]);
-    sl_out[v] = limited(q[v] - m, p - q[v], lim);
-  }
-}
-
-template <int D, class R, int TX, int TY>
-__device__ __forceinline__ void tile_dflux(const MhdTileShared<R, TX, TY>& sm, const int sl[3], int X, int Y,
-                                           const R q[NV], const MhdConst<R>& c, R dF[NV]) {
-  R s[NV], w[NV], Fh[NV];
-  tile_slopes<D>(sm, sl, X, Y, q, c.limiter, s);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) w[v] = q[v] + half_(s[v]);
-  mhd_flux<D>(w, c, Fh);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) w[v] = q[v] - half_(s[v]);
-  R Fl[NV];
-  mhd_flux<D>(w, c, Fl);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) dF[v] = D == 0 ? Fh[v] - Fl[v] : dF[v] + (Fh[v] - Fl[v]);
-}
-
-// Face state (axis D, high side if H) of the cell: the extrapolated state advanced by half a step
-// with the cell's flux differences dF, recovered and floored.
-template <int D, int H, class R, int TX, int TY>
-__device__ __forceinline__ void tile_face(const MhdTileShared<R, TX, TY>& sm, const int sl[3], int X, int Y,
-                                          const R q[NV], const R dF[NV], const MhdConst<R>& c, R out[NV]) {
-  R s[NV], w[NV], U[NV];
-  tile_slopes<D>(sm, sl, X, Y, q, c.limiter, s);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) w[v] = H ? q[v] + half_(s[v]) : q[v] - half_(s[v]);
-  mhd_conserved(w, c, U);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
-  unsigned nf = 0;  // face states are floored without a flag, as in the hydro step
-  mhd_recover(U, c, out, nf);
-}
-
 template <class Pol>
-constexpr int mhd_tile_min_blocks() { return sizeof(typename Pol::R) >= 8 ? 1 : 2; }
-
-template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, mhd_tile_min_blocks<Pol>())
-    k_mhd_tile(MhdBox<Pol> B, MhdConst<typename Pol::R> c, double cfl, double dx, double alpha, const double* dt_dev,
-               double* dt_next, int zchunk, unsigned* err) {
-  using S = typename Pol::S;
-  using R = typename Pol::R;
-  using SM = MhdTileShared<R, TX, TY>;
-  constexpr int QX = SM::QX, QY = SM::QY, NT = TX * TY;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM& sm = *reinterpret_cast<SM*>(smem_raw);
-  const int tid = threadIdx.x;
-  const double dt = dt_dev[0];
-  if (!(dt > 0.0 && dt <= 1e300)) {
-    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicOr(err, HYDRO_EBIT_BAD_DT);
-    return;
-  }
-  {
-    const double ch = (cfl / 3.0) * dx / dt;
-    c.ch = R(ch);
-    c.ch2 = R(ch * ch);
-    c.hdt = R(0.5 * dt / dx);
-    c.dtdx = R(dt / dx);
-    c.damp = R(exp(-alpha * ch * dt / dx));
-  }
-  const S damp = (S)to_double(c.damp);
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, B.nz);
-  for (int k = tid; k < QX; k += NT) sm.sx[k] = wrap_i(x0 + k - 2, B.nx);
-  for (int k = tid; k < QY; k += NT) sm.sy[k] = wrap_i(y0 + k - 2, B.ny);
-  __syncthreads();
-  unsigned flags = 0;
-  const long long sy = B.nx, sz = (long long)B.nx * B.ny;
-  auto load_plane = [&](int z, int slot) {
-    const long long zo = (long long)wrap_i(z, B.nz) * sz;
-    for (int t = tid; t < QX * QY; t += NT) {
-      const int y = t / QX, x = t - y * QX;
-      const long long a = zo + (long long)sm.sy[y] * sy + sm.sx[x];
-      R U[NV], q[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(B.in[v] + a), (R*)nullptr);
-      mhd_recover(U, c, q, flags);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sm.q[slot][v][y][x] = q[v];
-    }
-  };
-  // slot of plane z: (z - z0 + 2) mod 3
-  for (int k = 0; k < 3; ++k) load_plane(z0 - 2 + k, k);
-  __syncthreads();
-
-  const int i = tid % TX, j = tid / TX;
-  const bool own = x0 + i < B.nx && y0 + j < B.ny;
-  int rk = -1, ri = 0, rj = 0;  // ring cell: x-low (i = -1), x-high (i = TX), y-low (j = -1), y-high (j = TY)
-  if (tid < TY) { rk = 0; ri = -1; rj = tid; }
-  else if (tid < 2 * TY) { rk = 1; ri = TX; rj = tid - TY; }
-  else if (tid < 2 * TY + TX) { rk = 2; ri = tid - 2 * TY; rj = -1; }
-  else if (tid < 2 * TY + 2 * TX) { rk = 3; ri = tid - 2 * TY - TX; rj = TY; }
-
-  R fzb[NV];  // the z flux through the low face of the plane below
-#pragma unroll
-  for (int v = 0; v < NV; ++v) fzb[v] = R(0);
-  R smax = R(0);
-  for (int p = z0 - 1; p <= z1; ++p) {
-    const int base = p - z0 + 1;
-    const int sl[3] = {base % 3, (base + 1) % 3, (base + 2) % 3};  // planes p-1, p, p+1
-    const bool xy = p >= z0 && p < z1;
-    {
-      const int X = i + 2, Y = j + 2;
-      R q[NV], dF[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) q[v] = sm.q[sl[1]][v][Y][X];
-      tile_dflux<0>(sm, sl, X, Y, q, c, dF);
-      tile_dflux<1>(sm, sl, X, Y, q, c, dF);
-      tile_dflux<2>(sm, sl, X, Y, q, c, dF);
-      if (p > z0 - 1) {
-        // z face p - 1/2 between the plane below's z-high state and this plane's z-low state, then
-        // the update of plane p - 1 (its x and y fluxes are still in shared memory)
-        R zl[NV], zh[NV], F[NV];
-        tile_face<2, 0>(sm, sl, X, Y, q, dF, c, zl);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) zh[v] = sm.zs[v][j][i];
-        mhd_hll<2>(zh, zl, c, F);
-        if (p > z0 && own) {
-          const long long a = (long long)(p - 1) * sz + (long long)(y0 + j) * sy + (x0 + i);
-          S Un[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const R dxy = (sm.fx[v][j][i + 1] - sm.fx[v][j][i]) + (sm.fy[v][j + 1][i] - sm.fy[v][j][i]);
-            Un[v] = Pol::update(__ldg(B.in[v] + a), c.dtdx, dxy + (F[v] - fzb[v]));
-          }
-          Un[8] = Un[8] * damp;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) B.out[v][a] = Un[v];
-          if (dt_next) {
-            R U[NV], w[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
-            mhd_recover(U, c, w, flags);
-            const R sp = mhd_speed(w, c);
-            smax = sp > smax ? sp : smax;
-          }
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) fzb[v] = F[v];
-      }
-      {
-        R w[NV];
-        tile_face<2, 1>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.zs[v][j][i] = w[v];
-        if (xy) {
-          tile_face<0, 0>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) sm.wx[0][v][j][i + 1] = w[v];
-          tile_face<0, 1>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) sm.wx[1][v][j][i + 1] = w[v];
-          tile_face<1, 0>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) sm.wy[0][v][j + 1][i] = w[v];
-          tile_face<1, 1>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) sm.wy[1][v][j + 1][i] = w[v];
-        }
-      }
-    }
-    if (xy && rk >= 0) {
-      const int X = ri + 2, Y = rj + 2;
-      R q[NV], dF[NV], w[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) q[v] = sm.q[sl[1]][v][Y][X];
-      tile_dflux<0>(sm, sl, X, Y, q, c, dF);
-      tile_dflux<1>(sm, sl, X, Y, q, c, dF);
-      tile_dflux<2>(sm, sl, X, Y, q, c, dF);
-      if (rk == 0) {
-        tile_face<0, 1>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.wx[1][v][rj][0] = w[v];
-      } else if (rk == 1) {
-        tile_face<0, 0>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.wx[0][v][rj][TX + 1] = w[v];
-      } else if (rk == 2) {
-        tile_face<1, 1>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.wy[1][v][0][ri] = w[v];
-      } else {
-        tile_face<1, 0>(sm, sl, X, Y, q, dF, c, w);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.wy[0][v][TY + 1][ri] = w[v];
-      }
-    }
-    __syncthreads();  // face states written, plane p-1 updated: its fluxes and ring slot are free
-    if (xy) {
-      for (int f = tid; f < (TX + 1) * TY; f += NT) {
-        const int fy = f / (TX + 1), fx = f - fy * (TX + 1);
-        R ql[NV], qr[NV], F[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          ql[v] = sm.wx[1][v][fy][fx];
-          qr[v] = sm.wx[0][v][fy][fx + 1];
-        }
-        mhd_hll<0>(ql, qr, c, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.fx[v][fy][fx] = F[v];
-      }
-      for (int f = tid; f < TX * (TY + 1); f += NT) {
-        const int fy = f / TX, fx = f - fy * TX;
-        R ql[NV], qr[NV], F[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          ql[v] = sm.wy[1][v][fy][fx];
-          qr[v] = sm.wy[0][v][fy + 1][fx];
-        }
-        mhd_hll<1>(ql, qr, c, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sm.fy[v][fy][fx] = F[v];
-      }
-    }
-    if (p < z1) load_plane(p + 2, sl[0]);
-    __syncthreads();  // fluxes and plane p+2 in place
-  }
-  if (dt_next) {
-    const R m = block_max_r(smax);
-    if (threadIdx.x == 0) publish_dt(cfl, dx, to_double(m), dt_next);
-  }
-  flush_flags(flags, err);
-}
-
-template <class Pol>
-cudaError_t mhd_tile_t(const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next, int zchunk,
+cudaError_t mhd_step_t(const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next, void* scratch,
                        unsigned* err, cudaStream_t s) {
-  constexpr int TX = 16, TY = 16;
   using R = typename Pol::R;
-  const size_t smem = sizeof(MhdTileShared<R, TX, TY>);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mhd_tile<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  MhdBox<Pol> B = box_of<Pol>(h, nullptr);
-  zchunk = std::max(1, std::min(zchunk, h.nz));
-  dim3 grid((h.nx + TX - 1) / TX, (h.ny + TY - 1) / TY, (h.nz + zchunk - 1) / zchunk);
-  k_mhd_tile<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(B, consts_of<R>(prm), prm.cfl, h.dx, kMhdAlpha, dt, dt_next,
-                                                       zchunk, err);
+  MhdBox<Pol> B = box_of<Pol>(h, scratch);
+  static_assert(sizeof(MhdConst<R>) <= 256, "the constants fit before the face states");
+  auto* cp = static_cast<MhdConst<R>*>(scratch);
+  k_mhd_consts<R><<<1, 1, 0, s>>>(consts_of<R>(prm), prm.cfl, h.dx, kMhdAlpha, dt, cp, err);
+  const int g = grid_for(B.cells);
+  k_mhd_predict<Pol><<<g, 256, 0, s>>>(B, cp, err);
+  k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
+  k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
   return cudaGetLastError();
-}
-
-template <class Pol>
-cudaError_t mhd_step_t(const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next, unsigned* err,
-                       cudaStream_t s) {
-  // z chunks of up to 64 planes, shortened until the grid has four blocks per SM
-  const long long cols = (long long)((h.nx + 15) / 16) * ((h.ny + 15) / 16);
-  int zc = std::min(64, h.nz);
-  while (zc > 4 && cols * ((h.nz + zc - 1) / zc) < 4LL * 152) zc /= 2;
-  return mhd_tile_t<Pol>(h, prm, dt, dt_next, zc, err, s);
 }
 
 template <class Pol>
@@ -1009,11 +733,11 @@ size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size) {
 }
 
 cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
-                            unsigned* err, cudaStream_t s) {
+                            void* scratch, unsigned* err, cudaStream_t s) {
   switch (precision) {
-    case HYDRO_FP64: return mhd_step_t<PolF64>(h, prm, dt, dt_next, err, s);
-    case HYDRO_FP32: return mhd_step_t<PolF32>(h, prm, dt, dt_next, err, s);
-    case HYDRO_FP64_DF: return mhd_step_t<PolDF>(h, prm, dt, dt_next, err, s);
+    case HYDRO_FP64: return mhd_step_t<PolF64>(h, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_FP32: return mhd_step_t<PolF32>(h, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_FP64_DF: return mhd_step_t<PolDF>(h, prm, dt, dt_next, scratch, err, s);
   }
   return cudaErrorInvalidValue;
 }
