@@ -46,7 +46,7 @@ struct MhdBox {
 
 template <class R>
 struct MhdConst {
-  R gamma, gm1, igm1, rf, pf, ch, ch2, hdt, dtdx, damp;
+  R gamma, gm1, igm1, rf, pf, ch, ch2, ich, hdt, dtdx, damp;  // ich = 1/c_h
   int limiter;
   int valid;  // 0: the step's dt was not positive and finite (nothing is updated)
 };
@@ -124,28 +124,36 @@ __device__ __forceinline__ void mhd_flux(const R q[NV], const MhdConst<R>& c, R 
   F[8] = c.ch2 * Bn;
 }
 
+// Fast magnetosonic speed along an axis from a^2 = gamma p / rho, b^2 = |B|^2 / rho and b_n^2 / rho.
 template <class R>
-__device__ __forceinline__ R mhd_fast(const R q[NV], int d, const MhdConst<R>& c) {
-  const R ir = rcp_(q[0]);
-  const R a2 = c.gamma * q[4] * ir;
-  const R b2 = (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]) * ir;
-  const R bn = d == 0 ? q[5] : (d == 1 ? q[6] : q[7]);
-  const R bn2 = bn * bn * ir;
+__device__ __forceinline__ R mhd_fast_ab(R a2, R b2, R bn2) {
   const R s = a2 + b2;
   R r = s * s - mulf_(a2 * bn2, 4.f);
   r = cmp_pos(r) ? r : R(0);
   return rsqrt_(half_(s + rsqrt_(r)));
 }
 
-// CFL speed sum over axes of |u_d| + c_f,d (the same function for the fused and standalone dt).
+template <class R>
+__device__ __forceinline__ R mhd_fast(const R q[NV], int d, const MhdConst<R>& c) {
+  const R ir = rcp_(q[0]);
+  const R bn = d == 0 ? q[5] : (d == 1 ? q[6] : q[7]);
+  return mhd_fast_ab(c.gamma * q[4] * ir, (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]) * ir, bn * bn * ir);
+}
+
+// CFL speed sum over axes of |u_d| + c_f,d (the same function for the fused and standalone dt);
+// 1/rho, a^2 and b^2 formed once for the three axes.
 template <class R>
 __device__ __forceinline__ R mhd_speed(const R q[NV], const MhdConst<R>& c) {
-  return ((rabs(q[1]) + mhd_fast(q, 0, c)) + (rabs(q[2]) + mhd_fast(q, 1, c))) + (rabs(q[3]) + mhd_fast(q, 2, c));
+  const R ir = rcp_(q[0]);
+  const R a2 = c.gamma * q[4] * ir;
+  const R b2 = (q[5] * q[5] + q[6] * q[6] + q[7] * q[7]) * ir;
+  return ((rabs(q[1]) + mhd_fast_ab(a2, b2, q[5] * q[5] * ir)) + (rabs(q[2]) + mhd_fast_ab(a2, b2, q[6] * q[6] * ir))) +
+         (rabs(q[3]) + mhd_fast_ab(a2, b2, q[7] * q[7] * ir));
 }
 
 template <int D, class R>
 __device__ __forceinline__ void mhd_hll(R qL[NV], R qR[NV], const MhdConst<R>& c, R F[NV]) {
-  const R Bm = half_(qL[5 + D] + qR[5 + D]) - half_((qR[8] - qL[8]) * rcp_(c.ch));
+  const R Bm = half_(qL[5 + D] + qR[5 + D]) - half_((qR[8] - qL[8]) * c.ich);
   const R pm = half_(qL[8] + qR[8]) - half_(c.ch * (qR[5 + D] - qL[5 + D]));
   qL[5 + D] = qR[5 + D] = Bm;
   qL[8] = qR[8] = pm;
@@ -393,6 +401,7 @@ __global__ void k_mhd_consts(MhdConst<R> base, double cfl, double dx, double alp
     const double ch = (cfl / 3.0) * dx / dt;
     c.ch = R(ch);
     c.ch2 = R(ch * ch);
+    c.ich = R(1.0 / ch);
     c.hdt = R(0.5 * dt / dx);
     c.dtdx = R(dt / dx);
     c.damp = R(exp(-alpha * ch * dt / dx));
@@ -510,6 +519,7 @@ __global__ void k_mhdp_consts(const HostMhdPatch* patches, int npatch, MhdConst<
     const double ch = (cfl / 3.0) * dx / dt;
     c.ch = R(ch);
     c.ch2 = R(ch * ch);
+    c.ich = R(1.0 / ch);
     c.hdt = R(0.5 * dt / dx);
     c.dtdx = R(dt / dx);
     c.damp = R(exp(-alpha * ch * dt / dx));
