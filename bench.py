@@ -850,13 +850,22 @@ def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle  # noqa: F401  (the reference arm is the CPU oracle)
+    import oracle  # the reference arm is the CPU oracle
+    import workloads
     n = 96
+    # the sample is generated outside the timed region; each step is the oracle's CFL dt and step
+    U = workloads.turbulent_state(n, seed=2, mach=5.0, sedov=True).numpy()
+    dx = 1.0 / n
+    cfg = oracle.config()
+
+    def step(U):
+        return oracle.step_periodic(U, dx, oracle.cfl_periodic(U, dx, cfg), cfg)
+
     for _ in range(args.warmup):
-        cpu_baseline(n, 0.0, steps_cap=1)
+        U = step(U)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cpu_baseline(n, 0.0, steps_cap=1)
+        U = step(U)
     el = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     value = n ** 3 * args.steps / el / 1e6
@@ -868,7 +877,8 @@ def reference_arm(args):
                                    "turbulence box (lognormal rho sigma 1, P/rho 1e-4, Sedov cell), MinMod, CFL 0.8"
                                    % n},
             "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": threads, "kind": "oracle",
-                             "sample": "%d^3 per step (new state each step, CFL dt included)" % n},
+                             "sample": "%d^3 box of the headline workload, stepped on (CFL dt included); the "
+                                       "state generated before the timed steps" % n},
             "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
