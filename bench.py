@@ -913,7 +913,7 @@ def run_forms(hy, args, n, precision):
                     extra["ppm_%d_%s" % (n, prec)] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None)
                 extra["ppm_batched_mixed"] = form_ppm_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch)
             elif f == "mhd":
-                for prec in ("fp64", "df64", "fp32"):
+                for prec in ("fp64", "df64", "fp32", "mixed"):
                     extra["mhd_256_" + prec] = form_mhd(hy, prec, args.steps, args.warmup)
                 extra["mhd_patches_fp32"] = form_mhd_patches(hy, "fp32", max(3, args.steps // 2), 2)
             elif f == "graph1024":

@@ -274,10 +274,10 @@ int hydro_step_octs_table(hydro_ctx* ctx, void* const in[5], void* const out[5],
  *       dt_next_dev: NULL or one double receiving cfl dx / max_cells sum_d (|u_d| + c_f,d) of U^{n+1}.
  *       Device scratch of 81 elements per cell (face states and fluxes) is owned by the context.
  *   hydro_mhd_cfl_dt: dt_dev[0] <- the same CFL dt of U (bit-identical to the fused one).
- * Element type: double in HYDRO_FP64 and HYDRO_FP64_DF contexts (the latter computing in
- * double-float arithmetic, the update summed in double), float in HYDRO_FP32; HYDRO_MIXED and
- * HYDRO_PPM return HYDRO_ERR_ARG, as do sizes with nx*ny*nz >= 2^31.  Floors and error bits as the
- * hydro step. */
+ * Element type: double in HYDRO_FP64, HYDRO_FP64_DF (double-float arithmetic, the update summed in
+ * double) and HYDRO_MIXED (the state read as float, float arithmetic, the update summed in double)
+ * contexts, float in HYDRO_FP32; a HYDRO_PPM context returns HYDRO_ERR_ARG, as do sizes with
+ * nx*ny*nz >= 2^31.  Floors and error bits as the hydro step. */
 int hydro_mhd_step(hydro_ctx* ctx, void* const in[9], void* const out[9], int nx, int ny, int nz, double dx,
                    const double* dt_dev, double* dt_next_dev);
 int hydro_mhd_cfl_dt(hydro_ctx* ctx, void* const U[9], int nx, int ny, int nz, double dx, double* dt_dev);

@@ -978,12 +978,11 @@ int hydro_step_octs_table(hydro_ctx* c, void* const in[5], void* const out[5], i
       c->ops->octs_table(in, nbr_dev, noct, list_dev, out, ngroups, dx, c->prm, dt_dev, c->d_err, c->stream));
 }
 
-// Arguments of the MHD calls: a periodic box of nine contiguous fields in a FP64, FP64_DF or FP32
-// context with a PLM limiter.
+// Arguments of the MHD calls: a periodic box of nine contiguous fields in a context with a PLM
+// limiter.
 static bool mhd_args(const hydro_ctx* c, void* const* U, int nx, int ny, int nz, double dx) {
   if (!c || !U || nx < 1 || ny < 1 || nz < 1 || !finite_pos(dx)) return false;
   if ((long long)nx * ny * nz > 0x7fffffffLL) return false;
-  if (c->cfg.precision == HYDRO_MIXED) return false;
   if (ppm(c)) return false;
   const int es = elem_size(c);
   for (int v = 0; v < 9; ++v)
@@ -1089,7 +1088,7 @@ static int mhd_patch_tables(hydro_ctx* c, int kind, const hydro_mhd_patch* in, c
 int hydro_mhd_step_patches(hydro_ctx* c, const hydro_mhd_patch* in, const hydro_mhd_patch* out, int npatch,
                            const double* dt_dev, double* dt_next_dev) {
   if (!c || !in || !out || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
-  if (c->cfg.precision == HYDRO_MIXED || ppm(c)) return HYDRO_ERR_ARG;
+  if (ppm(c)) return HYDRO_ERR_ARG;
   for (int i = 0; i < npatch; ++i) {
     const hydro_mhd_patch &I = in[i], &O = out[i];
     if (!mhd_patch_ok(c, I, true) || !mhd_patch_ok(c, O, false)) return HYDRO_ERR_ARG;
@@ -1120,7 +1119,7 @@ int hydro_mhd_step_patches(hydro_ctx* c, const hydro_mhd_patch* in, const hydro_
 
 int hydro_mhd_cfl_patches(hydro_ctx* c, const hydro_mhd_patch* p, int npatch, double* dt_dev) {
   if (!c || !p || npatch < 1 || !dt_dev) return HYDRO_ERR_ARG;
-  if (c->cfg.precision == HYDRO_MIXED || ppm(c)) return HYDRO_ERR_ARG;
+  if (ppm(c)) return HYDRO_ERR_ARG;
   for (int i = 0; i < npatch; ++i)
     if (!mhd_patch_ok(c, p[i], true)) return HYDRO_ERR_ARG;
   const hydro::HostMhdPatch* dp = nullptr;

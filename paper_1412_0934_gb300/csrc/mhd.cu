@@ -17,7 +17,7 @@
 // 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays, in the arithmetic type.
 // Precision policies as the hydro step: FP64 (double), FP32 (float, SFU reciprocal and square
 // root), FP64_DF (double state, double-float arithmetic on the FP32 pipes, the update summed in
-// double).
+// double), MIXED (double state read as float, float arithmetic, the update summed in double).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -724,6 +724,7 @@ cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, con
     case HYDRO_FP64: return mhd_patches_t<PolF64>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
     case HYDRO_FP32: return mhd_patches_t<PolF32>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
     case HYDRO_FP64_DF: return mhd_patches_t<PolDF>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_MIXED: return mhd_patches_t<PolMixed>(d_patches, d_blocks, nblocks, npatch, prm, dt, dt_next, scratch, err, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -734,6 +735,7 @@ cudaError_t launch_mhd_patches_cfl(int precision, const HostMhdPatch* d_patches,
     case HYDRO_FP64: return mhd_patches_cfl_t<PolF64>(d_patches, d_blocks, nblocks, prm, dt, err, s);
     case HYDRO_FP32: return mhd_patches_cfl_t<PolF32>(d_patches, d_blocks, nblocks, prm, dt, err, s);
     case HYDRO_FP64_DF: return mhd_patches_cfl_t<PolDF>(d_patches, d_blocks, nblocks, prm, dt, err, s);
+    case HYDRO_MIXED: return mhd_patches_cfl_t<PolMixed>(d_patches, d_blocks, nblocks, prm, dt, err, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -748,6 +750,7 @@ cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& pr
     case HYDRO_FP64: return mhd_step_t<PolF64>(h, prm, dt, dt_next, scratch, err, s);
     case HYDRO_FP32: return mhd_step_t<PolF32>(h, prm, dt, dt_next, scratch, err, s);
     case HYDRO_FP64_DF: return mhd_step_t<PolDF>(h, prm, dt, dt_next, scratch, err, s);
+    case HYDRO_MIXED: return mhd_step_t<PolMixed>(h, prm, dt, dt_next, scratch, err, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -758,6 +761,7 @@ cudaError_t launch_mhd_cfl(int precision, const HostMhdBox& h, const Params& prm
     case HYDRO_FP64: return mhd_cfl_t<PolF64>(h, prm, dt, err, s);
     case HYDRO_FP32: return mhd_cfl_t<PolF32>(h, prm, dt, err, s);
     case HYDRO_FP64_DF: return mhd_cfl_t<PolDF>(h, prm, dt, err, s);
+    case HYDRO_MIXED: return mhd_cfl_t<PolMixed>(h, prm, dt, err, s);
   }
   return cudaErrorInvalidValue;
 }
