@@ -99,10 +99,9 @@ __device__ __forceinline__ void ppm_cell(const PpmShared<R, TX, TY>& sm, const i
   hancock(q, D[0], D[1], D[2], gamma, hdt, qh);
 }
 
-// Resident blocks per SM: a 16 x 16 tile's 8-byte ring and face arrays take ~165 KB of shared
-// memory (one block), a 16 x 8 tile's ~97 KB (two); float arrays take half.
-template <class Pol, int TX, int TY>
-constexpr int ppm_min_blocks() { return (sizeof(typename Pol::R) >= 8 && TX * TY > 128) ? 1 : 2; }
+// Resident blocks per SM: the 8-byte ring and face arrays take ~165 KB of shared memory.
+template <class Pol>
+constexpr int ppm_min_blocks() { return sizeof(typename Pol::R) >= 8 ? 1 : 2; }
 
 // Block-wide maximum of v (all threads call); the result is valid in thread 0.
 template <class R, int TX, int TY>
@@ -282,7 +281,7 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
 
 // Periodic box: one tile per block, tiles from the block index.
 template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (ppm_min_blocks<Pol, TX, TY>()))
+__global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
     k_step_ppm(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev, double* dt_next, int zchunk,
                unsigned* err) {
   using R = typename Pol::R;
@@ -308,7 +307,7 @@ __global__ void __launch_bounds__(TX * TY, (ppm_min_blocks<Pol, TX, TY>()))
 // Patches with three ghost layers: a persistent grid taking tiles from the device work-list by an
 // atomic counter (as the PLM batched kernel); per-patch dt, dx and dt_next.
 template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (ppm_min_blocks<Pol, TX, TY>()))
+__global__ void __launch_bounds__(TX * TY, ppm_min_blocks<Pol>())
     k_step_ppm_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles, int ntiles, int* counter,
                        Params prm, const double* dt_dev, double* dt_next, int zchunk, unsigned* err) {
   using R = typename Pol::R;
@@ -346,27 +345,24 @@ __global__ void __launch_bounds__(TX * TY, (ppm_min_blocks<Pol, TX, TY>()))
 constexpr int kPpmTX = 16, kPpmTY = 16;
 static_assert(kTileX[0] == kPpmTX && kTileY[0] == kPpmTY, "the PPM work-list is built with tile shape 0");
 
-template <class Pol, int TX = kPpmTX, int TY = kPpmTY>
+template <class Pol>
 cudaError_t ppm_attr(const void* fn) {
-  const size_t smem = sizeof(PpmShared<typename Pol::R, TX, TY>);
+  const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// The periodic box: 16 x 8 tiles for 8-byte arithmetic (two resident blocks, so that one block's
-// barriers overlap the other's work), 16 x 16 for float.
 template <class Pol>
 cudaError_t launch_ppm(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
                        unsigned* err, cudaStream_t s) {
-  constexpr int TX = 16, TY = sizeof(typename Pol::R) >= 8 ? 8 : 16;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = ppm_attr<Pol, TX, TY>(reinterpret_cast<const void*>(k_step_ppm<Pol, TX, TY>));
+    cudaError_t e = ppm_attr<Pol>(reinterpret_cast<const void*>(k_step_ppm<Pol, kPpmTX, kPpmTY>));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const size_t smem = sizeof(PpmShared<typename Pol::R, TX, TY>);
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
-  k_step_ppm<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
+  const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
+  dim3 grid((P.nx + kPpmTX - 1) / kPpmTX, (P.ny + kPpmTY - 1) / kPpmTY, (P.nz + zchunk - 1) / zchunk);
+  k_step_ppm<Pol, kPpmTX, kPpmTY><<<grid, kPpmTX * kPpmTY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
   return cudaGetLastError();
 }
 
