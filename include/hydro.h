@@ -2,7 +2,10 @@
  * hydro.h -- C ABI of the GB300 (sm_103a) hydro library: one second-order unsplit
  * MUSCL-Hancock step (PLM primitive reconstruction, Hancock half-step predictor, HLLC fluxes,
  * conservative update) of the 3D ideal-gas Euler equations on AMR grid patches, the per-patch
- * CFL time step, Ramses-style oct groups, and the adjoint of the step.
+ * CFL time step, Ramses-style oct groups (gathered, read in place, or through a device-built
+ * Morton order and neighbour table), the adjoint of the step, the coupling of AMR levels
+ * (coarse-fine ghosts, flux registers, refluxing, average-down), a PPM variant, and ideal MHD
+ * with hyperbolic divergence cleaning.
  *
  * What the calls compute follows the paper's description of the hydro path: the baryonic
  * component is an ideal fluid governed by the Euler equations, solved with PLM among other
@@ -121,8 +124,9 @@ int hydro_finalize(hydro_ctx* ctx);
  * same state. */
 int hydro_cfl_dt(hydro_ctx* ctx, const hydro_patch* p, int npatch, double* dt_dev);
 
-/* One MUSCL-Hancock/HLLC step of every patch (recovery, PLM slopes, Hancock predictor, HLLC
- * fluxes on every face, conservative update; Sec. 2 and Sec. 4):
+/* One MUSCL-Hancock/HLLC step of every patch (recovery, PLM slopes -- or the PPM parabola in a
+ * HYDRO_PPM context --, Hancock predictor, HLLC fluxes on every face, conservative update; Sec. 2
+ * and Sec. 4):
  *   out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] and cell size in[p].dx.
  * in, out: host arrays of npatch descriptors with equal nx, ny, nz and dx per patch; out[p] may
  * have ng 0, 2 or (PPM) 3 (only its interior is written) and must not overlap in[p] (use two buffers).
