@@ -39,3 +39,14 @@ def test_double_float_flop_constant():
     c = oracle.count_ops(U, 1 / 64, oracle.cfl_periodic(U, 1 / 64, cfg), cfg)
     df = sum(b.DF_COST[k] * v for k, v in c["by_kind"].items())
     assert df == pytest.approx(b.ALG_DF_FLOPS_PER_CELL["turb_minmod"], rel=0.01)
+
+
+def test_headline_profile_was_taken_on_the_current_step_kernel():
+    """The committed ncu summary of the headline step kernel carries the hash of the kernel's sources
+    it was taken on; the bench reports its DRAM traffic only while that hash matches, so a change to
+    the step kernel without a new capture shows here (and as a null roofline.traffic)."""
+    b = bench_module()
+    traffic, src = b.profile_traffic("step_uniform_512_df64.txt")
+    assert src.endswith("step_uniform_512_df64.txt"), src
+    # the DRAM bytes of one 512^3 launch stay within a few percent of the algorithmic 80 B per cell
+    assert traffic == pytest.approx(512 ** 3 * 80, rel=0.05)
