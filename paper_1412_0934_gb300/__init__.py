@@ -150,6 +150,7 @@ class MhdPatch:
                 raise ValueError("fields must share shape, strides and dtype")
         Z, Y, X = fs[0].shape
         self.tensors = fs
+        self.dtype = fs[0].dtype
         self.c = hydro_mhd_patch()
         for v in range(9):
             self.c.U[v] = fs[v].data_ptr()
@@ -222,6 +223,32 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _f64(t, n, what):
+    """Pointer to a CUDA float64 tensor of at least n elements (the time-step arrays), or None."""
+    if t is None:
+        return None
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() < n:
+        raise ValueError("%s must be a contiguous float64 CUDA tensor of at least %d elements" % (what, n))
+    return _ptr(t)
+
+
+def _dtypes(obj):
+    if isinstance(obj, (Patch, MhdPatch, torch.Tensor)):
+        yield obj.dtype
+    elif isinstance(obj, (list, tuple)):
+        for o in obj:
+            yield from _dtypes(o)
+
+
+def _same_dtype(ctx, *objs):
+    """The fields and registers a call reads or writes must hold the context's element type: the
+    library addresses them with it (double, or float for HYDRO_FP32)."""
+    for o in objs:
+        for dt in _dtypes(o):
+            if dt != ctx.dtype:
+                raise ValueError("the context works on %s data; got %s" % (ctx.dtype, dt))
+
+
 class Context:
     """An open hydro_ctx (create with hydro_init, release with hydro_finalize)."""
 
@@ -268,8 +295,9 @@ def hydro_finalize(ctx):
 
 
 def hydro_cfl_dt(ctx, patches, dt_out):
+    _same_dtype(ctx, patches)
     arr, n = _parray(patches)
-    _check(lib().hydro_cfl_dt(ctx.handle, arr, n, _ptr(dt_out)), "hydro_cfl_dt")
+    _check(lib().hydro_cfl_dt(ctx.handle, arr, n, _f64(dt_out, n, "dt_out")), "hydro_cfl_dt")
 
 
 def hydro_step(ctx, inp, out, dt, dt_next=None):
@@ -277,13 +305,15 @@ def hydro_step(ctx, inp, out, dt, dt_next=None):
     b, m = _parray(out)
     if n != m:
         raise ValueError("in and out patch counts differ")
-    _check(lib().hydro_step(ctx.handle, a, b, n, _ptr(dt), _ptr(dt_next)), "hydro_step")
+    _same_dtype(ctx, inp, out)
+    _check(lib().hydro_step(ctx.handle, a, b, n, _f64(dt, n, "dt"), _f64(dt_next, n, "dt_next")), "hydro_step")
 
 
 def hydro_step_host(ctx, inp, out, dt, dt_next=None):
     """One step of a host-resident periodic box (host_patch in / out; dt, dt_next CUDA tensors)."""
-    _check(lib().hydro_step_host(ctx.handle, ctypes.byref(inp.c), ctypes.byref(out.c), _ptr(dt), _ptr(dt_next)),
-           "hydro_step_host")
+    _same_dtype(ctx, inp, out)
+    _check(lib().hydro_step_host(ctx.handle, ctypes.byref(inp.c), ctypes.byref(out.c), _f64(dt, 1, "dt"),
+                                 _f64(dt_next, 1, "dt_next")), "hydro_step_host")
 
 
 def hydro_fill_ghosts(ctx, coarse, fine, origins):
@@ -293,6 +323,7 @@ def hydro_fill_ghosts(ctx, coarse, fine, origins):
     o = (ctypes.c_int * (3 * n))(*[int(v) for xyz in origins for v in xyz])
     if len(o) != 3 * n:
         raise ValueError("one (x, y, z) origin per patch")
+    _same_dtype(ctx, coarse, fine)
     _check(lib().hydro_fill_ghosts(ctx.handle, ctypes.byref(coarse.c), f, o, n), "hydro_fill_ghosts")
 
 
@@ -303,6 +334,7 @@ def hydro_fill_ghosts_time(ctx, coarse_old, coarse_new, theta, fine, origins):
     o = (ctypes.c_int * (3 * n))(*[int(v) for xyz in origins for v in xyz])
     if len(o) != 3 * n:
         raise ValueError("one (x, y, z) origin per patch")
+    _same_dtype(ctx, coarse_old, coarse_new, fine)
     _check(lib().hydro_fill_ghosts_time(ctx.handle, ctypes.byref(coarse_old.c), ctypes.byref(coarse_new.c),
                                         float(theta), f, o, n), "hydro_fill_ghosts_time")
 
@@ -315,6 +347,7 @@ def hydro_exchange_ghosts(ctx, fine, origins, period):
     if len(o) != 3 * n:
         raise ValueError("one (x, y, z) origin per patch")
     per = (ctypes.c_int * 3)(*[int(v) for v in period])
+    _same_dtype(ctx, fine)
     _check(lib().hydro_exchange_ghosts(ctx.handle, f, o, n, per), "hydro_exchange_ghosts")
 
 
@@ -337,7 +370,8 @@ def hydro_patch_fluxes(ctx, patches, dt, registers, accumulate=False):
     a, n = _parray(patches)
     if len(registers) != n:
         raise ValueError("one register per patch")
-    _check(lib().hydro_patch_fluxes(ctx.handle, a, n, _ptr(dt), _ptrs(registers), int(bool(accumulate))),
+    _same_dtype(ctx, patches, registers)
+    _check(lib().hydro_patch_fluxes(ctx.handle, a, n, _f64(dt, n, "dt"), _ptrs(registers), int(bool(accumulate))),
            "hydro_patch_fluxes")
 
 
@@ -345,14 +379,16 @@ def hydro_level_fluxes(ctx, level, box_origins, box_dims, dt, registers, accumul
     n = len(box_origins)
     if len(box_dims) != n or len(registers) != n:
         raise ValueError("one origin, size and register per box")
+    _same_dtype(ctx, level, registers)
     _check(lib().hydro_level_fluxes(ctx.handle, ctypes.byref(level.c), _ints(box_origins), _ints(box_dims), n,
-                                    _ptr(dt), _ptrs(registers), int(bool(accumulate))), "hydro_level_fluxes")
+                                    _f64(dt, 1, "dt"), _ptrs(registers), int(bool(accumulate))), "hydro_level_fluxes")
 
 
 def hydro_reflux(ctx, coarse, box_origins, box_dims, coarse_registers, fine_registers):
     n = len(box_origins)
     if len(box_dims) != n or len(coarse_registers) != n or len(fine_registers) != n:
         raise ValueError("one origin, size and pair of registers per box")
+    _same_dtype(ctx, coarse, coarse_registers, fine_registers)
     _check(lib().hydro_reflux(ctx.handle, ctypes.byref(coarse.c), _ints(box_origins), _ints(box_dims), n,
                               _ptrs(coarse_registers), _ptrs(fine_registers)), "hydro_reflux")
 
@@ -361,6 +397,7 @@ def hydro_average_down(ctx, coarse, fine, origins):
     f, n = _parray(fine)
     if len(origins) != n:
         raise ValueError("one origin per patch")
+    _same_dtype(ctx, coarse, fine)
     _check(lib().hydro_average_down(ctx.handle, ctypes.byref(coarse.c), f, _ints(origins), n), "hydro_average_down")
 
 
@@ -373,8 +410,9 @@ def hydro_step_octs_level(ctx, level, origins, out, dt):
     for v in range(5):
         if not out[v].is_contiguous():
             raise ValueError("oct arrays must be contiguous per field")
-    _check(lib().hydro_step_octs_level(ctx.handle, ctypes.byref(level.c), _ptr(origins), origins.shape[0], o, _ptr(dt)),
-           "hydro_step_octs_level")
+    _same_dtype(ctx, level, out)
+    _check(lib().hydro_step_octs_level(ctx.handle, ctypes.byref(level.c), _ptr(origins), origins.shape[0], o,
+                                       _f64(dt, 1, "dt")), "hydro_step_octs_level")
 
 
 def _int_tensor(t, what, cols=None):
@@ -404,8 +442,9 @@ def hydro_step_octs_table(ctx, U, out, nbr, octs, dx, dt):
     for v in range(5):
         if not U[v].is_contiguous() or not out[v].is_contiguous():
             raise ValueError("oct arrays must be contiguous per field")
+    _same_dtype(ctx, U, out)
     _check(lib().hydro_step_octs_table(ctx.handle, i, o, nbr.shape[0], _ptr(nbr), _ptr(octs), octs.shape[0],
-                                       float(dx), _ptr(dt)), "hydro_step_octs_table")
+                                       float(dx), _f64(dt, 1, "dt")), "hydro_step_octs_table")
 
 
 def _mhd_fields(U):
@@ -422,8 +461,9 @@ def hydro_mhd_step(ctx, U, out, dx, dt, dt_next=None):
     """U, out: (9, nz, ny, nx) tensors (or 9 tensors) of a periodic box; dt: device double."""
     a, nx, ny, nz = _mhd_fields(U)
     b, *_ = _mhd_fields(out)
-    _check(lib().hydro_mhd_step(ctx.handle, a, b, nx, ny, nz, float(dx), _ptr(dt),
-                                _ptr(dt_next) if dt_next is not None else None), "hydro_mhd_step")
+    _same_dtype(ctx, U, out)
+    _check(lib().hydro_mhd_step(ctx.handle, a, b, nx, ny, nz, float(dx), _f64(dt, 1, "dt"),
+                                _f64(dt_next, 1, "dt_next")), "hydro_mhd_step")
 
 
 def hydro_mhd_step_patches(ctx, inp, out, dt, dt_next=None):
@@ -432,18 +472,21 @@ def hydro_mhd_step_patches(ctx, inp, out, dt, dt_next=None):
     b, m = _mhd_parray(out)
     if m != n:
         raise ValueError("one output patch per input patch")
-    _check(lib().hydro_mhd_step_patches(ctx.handle, a, b, n, _ptr(dt), _ptr(dt_next) if dt_next is not None else None),
+    _same_dtype(ctx, inp, out)
+    _check(lib().hydro_mhd_step_patches(ctx.handle, a, b, n, _f64(dt, n, "dt"), _f64(dt_next, n, "dt_next")),
            "hydro_mhd_step_patches")
 
 
 def hydro_mhd_cfl_patches(ctx, patches, dt):
     a, n = _mhd_parray(patches)
-    _check(lib().hydro_mhd_cfl_patches(ctx.handle, a, n, _ptr(dt)), "hydro_mhd_cfl_patches")
+    _same_dtype(ctx, patches)
+    _check(lib().hydro_mhd_cfl_patches(ctx.handle, a, n, _f64(dt, n, "dt")), "hydro_mhd_cfl_patches")
 
 
 def hydro_mhd_cfl_dt(ctx, U, dx, dt):
     a, nx, ny, nz = _mhd_fields(U)
-    _check(lib().hydro_mhd_cfl_dt(ctx.handle, a, nx, ny, nz, float(dx), _ptr(dt)), "hydro_mhd_cfl_dt")
+    _same_dtype(ctx, U)
+    _check(lib().hydro_mhd_cfl_dt(ctx.handle, a, nx, ny, nz, float(dx), _f64(dt, 1, "dt")), "hydro_mhd_cfl_dt")
 
 
 def hydro_step_octs(ctx, gathered, out, dx, dt):
@@ -454,19 +497,22 @@ def hydro_step_octs(ctx, gathered, out, dx, dt):
         if not gathered[v].is_contiguous() or not out[v].is_contiguous():
             raise ValueError("oct arrays must be contiguous per field")
     G = gathered[0].shape[0]
-    _check(lib().hydro_step_octs(ctx.handle, g, o, G, float(dx), _ptr(dt)), "hydro_step_octs")
+    _same_dtype(ctx, gathered, out)
+    _check(lib().hydro_step_octs(ctx.handle, g, o, G, float(dx), _f64(dt, 1, "dt")), "hydro_step_octs")
 
 
 def hydro_adjoint_step(ctx, U_n, dt, lam_np1, lam_n):
     a, n = _parray(U_n)
     b, _ = _parray(lam_np1)
     c, _ = _parray(lam_n)
-    _check(lib().hydro_adjoint_step(ctx.handle, a, _ptr(dt), b, c, n), "hydro_adjoint_step")
+    _same_dtype(ctx, U_n, lam_np1, lam_n)
+    _check(lib().hydro_adjoint_step(ctx.handle, a, _f64(dt, n, "dt"), b, c, n), "hydro_adjoint_step")
 
 
 def hydro_prim_to_cons(ctx, W, U):
     a, n = _parray(W)
     b, _ = _parray(U)
+    _same_dtype(ctx, W, U)
     _check(lib().hydro_prim_to_cons(ctx.handle, a, b, n), "hydro_prim_to_cons")
 
 
@@ -474,20 +520,24 @@ def hydro_prim_to_cons_adjoint(ctx, W, lamU, lamW):
     a, n = _parray(W)
     b, _ = _parray(lamU)
     c, _ = _parray(lamW)
+    _same_dtype(ctx, W, lamU, lamW)
     _check(lib().hydro_prim_to_cons_adjoint(ctx.handle, a, b, c, n), "hydro_prim_to_cons_adjoint")
 
 
 def hydro_run(ctx, a, b, nsteps, dt_hist, use_graph=True):
     pa, _ = _parray(a)
     pb, _ = _parray(b)
-    _check(lib().hydro_run(ctx.handle, pa, pb, int(nsteps), _ptr(dt_hist), 1 if use_graph else 0), "hydro_run")
+    _same_dtype(ctx, a, b)
+    _check(lib().hydro_run(ctx.handle, pa, pb, int(nsteps), _f64(dt_hist, int(nsteps) + 1, "dt_hist"),
+                           1 if use_graph else 0), "hydro_run")
 
 
 def hydro_autotune(ctx, inp, out, dt, cache_path=None):
     a, n = _parray(inp)
     b, _ = _parray(out)
     cp = cache_path.encode() if cache_path else None
-    _check(lib().hydro_autotune(ctx.handle, a, b, n, _ptr(dt), cp), "hydro_autotune")
+    _same_dtype(ctx, inp, out)
+    _check(lib().hydro_autotune(ctx.handle, a, b, n, _f64(dt, n, "dt"), cp), "hydro_autotune")
 
 
 def hydro_get_tuning(ctx):
