@@ -1,7 +1,8 @@
 """Pins of the MHD oracle (oracle/mhd.py): the flux against the pinned hydro flux at B = 0 and its
 tensor symmetries, the fast speed's closed forms, HLL consistency, the GLM face solution's
 characteristic invariants, uniform flow, conservation, the decay of a divergence error, and the
-convergence of an exact circularly polarised Alfven wave."""
+convergence of an exact circularly polarised Alfven wave and of linear fast and slow magnetosonic
+waves."""
 import math
 
 import numpy as np
@@ -245,3 +246,51 @@ def test_axis_permutation():
     back = np.transpose(Vz, (0, 3, 2, 1))[pxz]
     err = max(np.abs(back[f] - V[f]).max() / np.abs(V[f]).max() for f in range(9))
     assert err <= 1e-13, err
+
+
+def magnetosonic_wave(n, mode, eps, cfg, rho=1.0, p=0.3, Bx=0.8, By=0.6):
+    """A linear fast or slow magnetosonic wave along x in a uniform state with the field oblique in
+    the x-y plane.  Linearising 1D ideal MHD about (rho, 0, p, Bx, By) for perturbations of
+    x - c t: drho = rho du / c, dp = rho a^2 du / c, dB_y = rho du (c^2 - a^2) / (c B_y),
+    dv = -B_x dB_y / (c rho), and c solves c^4 - (a^2 + b^2) c^2 + a^2 B_x^2 / rho = 0 (the larger
+    root fast, the smaller slow); B_x, w, B_z and psi stay unperturbed."""
+    a2 = cfg.gamma * p / rho
+    b2 = (Bx * Bx + By * By) / rho
+    roots = np.sort(np.roots([1.0, -(a2 + b2), a2 * Bx * Bx / rho]).real)
+    c = math.sqrt(roots[1] if mode == "fast" else roots[0])
+    x = (np.arange(n) + 0.5) / n
+    du = eps * np.sin(2 * np.pi * x)
+    dBy = rho * du * (c * c - a2) / (c * By)
+    q = np.zeros((9, 2, 2, n))
+    q[0] = rho + rho * du / c
+    q[1] = du
+    q[2] = -Bx * dBy / (c * rho)
+    q[4] = p + rho * a2 * du / c
+    q[5] = Bx
+    q[6] = By + dBy
+    return q, c
+
+
+@pytest.mark.parametrize("mode", ["fast", "slow"])
+@pytest.mark.parametrize("limiter,min_order", [("none", 1.9), ("mc", 1.7)])
+def test_linear_magnetosonic_waves_converge(mode, limiter, min_order):
+    """After one period the small-amplitude wave returns to its initial state; the error falls at
+    second order.  Its speed comes from the magnetic pressure, the Maxwell stress and the B (u.B)
+    energy flux, which the Alfven wave (|B| constant) leaves untested: a wrong factor on |B|^2/2,
+    a dropped stress or energy term, or a flipped induction sign gives an O(1) relative error."""
+    cfg = oracle.config()
+    eps = 1e-6
+    errs = []
+    for n in (16, 32, 64):
+        q, c = magnetosonic_wave(n, mode, eps, cfg)
+        U0 = mhd.conserved(q, cfg)
+        U, t, dx, T = U0.copy(), 0.0, 1.0 / n, 1.0 / c
+        while t < T - 1e-14:
+            dt = min(mhd.cfl_periodic(U, dx, cfg), T - t)
+            U = mhd.step_periodic(U, dx, dt, cfg, limiter=limiter)
+            t += dt
+        errs.append(max(np.abs(U[f] - U0[f]).mean() / eps for f in (0, 1, 2, 4, 6)))
+        assert np.all(U[[3, 7, 8]] == 0.0)
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] >= min_order, (errs, orders)
+    assert errs[-1] < 0.01, errs
