@@ -34,32 +34,36 @@ def config(gamma=5.0 / 3.0, cfl=0.8, rho_floor=1e-10, p_floor=1e-14, limiter="mi
     return OracleConfig(gamma, cfl, rho_floor, p_floor, lim)
 
 
+def load(so):
+    """A ctypes handle on an oracle library built from these sources, argument types set."""
+    L = ctypes.CDLL(so)
+    P = ctypes.POINTER(OracleConfig)
+    d = ctypes.c_double
+    i = ctypes.c_int
+    vp = ctypes.c_void_p
+    L.oracle_step_periodic.argtypes = [P, vp, vp, i, i, i, d, d]
+    L.oracle_step_patch.argtypes = [P, vp, vp, i, i, i, d, d]
+    L.oracle_cfl_periodic.argtypes = [P, vp, i, i, i, d]
+    L.oracle_cfl_periodic.restype = d
+    L.oracle_cfl_patch.argtypes = [P, vp, i, i, i, d]
+    L.oracle_cfl_patch.restype = d
+    L.oracle_step_periodic_tangent.argtypes = [P, vp, vp, vp, vp, i, i, i, d, d]
+    L.oracle_step_periodic_adjoint.argtypes = [P, vp, vp, vp, i, i, i, d, d, i]
+    L.oracle_step_patch_adjoint.argtypes = [P, vp, vp, vp, i, i, i, d, d]
+    L.oracle_hllc.argtypes = [P, vp, vp, i, vp]
+    L.oracle_hllc_n.argtypes = [P, vp, vp, i, vp, ctypes.c_long]
+    L.oracle_recover.argtypes = [P, vp, vp, ctypes.c_long]
+    L.oracle_prim_to_cons.argtypes = [P, vp, vp, ctypes.c_long]
+    L.oracle_prim_to_cons_adjoint.argtypes = [P, vp, vp, vp, ctypes.c_long]
+    L.oracle_count_ops.argtypes = [P, vp, i, i, i, d, d, vp]
+    L.oracle_patch_boundary_fluxes.argtypes = [P, vp, i, i, i, d, d, vp]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        so = _build.build()
-        L = ctypes.CDLL(so)
-        P = ctypes.POINTER(OracleConfig)
-        d = ctypes.c_double
-        i = ctypes.c_int
-        vp = ctypes.c_void_p
-        L.oracle_step_periodic.argtypes = [P, vp, vp, i, i, i, d, d]
-        L.oracle_step_patch.argtypes = [P, vp, vp, i, i, i, d, d]
-        L.oracle_cfl_periodic.argtypes = [P, vp, i, i, i, d]
-        L.oracle_cfl_periodic.restype = d
-        L.oracle_cfl_patch.argtypes = [P, vp, i, i, i, d]
-        L.oracle_cfl_patch.restype = d
-        L.oracle_step_periodic_tangent.argtypes = [P, vp, vp, vp, vp, i, i, i, d, d]
-        L.oracle_step_periodic_adjoint.argtypes = [P, vp, vp, vp, i, i, i, d, d, i]
-        L.oracle_step_patch_adjoint.argtypes = [P, vp, vp, vp, i, i, i, d, d]
-        L.oracle_hllc.argtypes = [P, vp, vp, i, vp]
-        L.oracle_hllc_n.argtypes = [P, vp, vp, i, vp, ctypes.c_long]
-        L.oracle_recover.argtypes = [P, vp, vp, ctypes.c_long]
-        L.oracle_prim_to_cons.argtypes = [P, vp, vp, ctypes.c_long]
-        L.oracle_prim_to_cons_adjoint.argtypes = [P, vp, vp, vp, ctypes.c_long]
-        L.oracle_count_ops.argtypes = [P, vp, i, i, i, d, d, vp]
-        L.oracle_patch_boundary_fluxes.argtypes = [P, vp, i, i, i, d, d, vp]
-        _lib = L
+        _lib = load(_build.build())
     return _lib
 
 

@@ -20,12 +20,17 @@ def _stale():
     return any(os.path.getmtime(p) > t for p in SOURCES + HEADERS)
 
 
+def command(sources, out):
+    """The g++ command line that builds the oracle library `out` from `sources`."""
+    return ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+            "-shared", "-fPIC", "-o", out] + list(sources)
+
+
 def build(force=False, verbose=False):
     if not force and not _stale():
         return SO
     tmp = SO + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-shared", "-fPIC", "-o", tmp] + SOURCES
+    cmd = command(SOURCES, tmp)
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)

@@ -294,3 +294,58 @@ def test_linear_magnetosonic_waves_converge(mode, limiter, min_order):
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert orders[-1] >= min_order, (errs, orders)
     assert errs[-1] < 0.01, errs
+
+
+@pytest.mark.parametrize("limiter", ["minmod", "mc", "none"])
+def test_mirror_symmetry(limiter):
+    """Reflecting x -> -x (cells in reverse order, u_x and B_x negated, psi unchanged) maps ideal MHD
+    with GLM cleaning onto itself, and the step commutes with it bit for bit: the limiters, the
+    Davis bounds (S_L and S_R exchange roles with their signs flipped) and the HLL average are all
+    mirror-symmetric, so a one-sided wave-speed bound or a lopsided average fails here."""
+    import workloads
+    cfg = oracle.config()
+    U = workloads.mhd_state((10, 12, 14), seed=59, beta=0.5, mach=1.5, psi_amp=0.05).numpy()
+
+    def mirror(V):
+        W = V[..., ::-1].copy()
+        W[1] = -W[1]
+        W[5] = -W[5]
+        return W
+
+    dx = 1.0 / 14
+    dt = 0.5 * mhd.cfl_periodic(U, dx, cfg)
+    np.testing.assert_array_equal(mhd.step_periodic(mirror(U), dx, dt, cfg, limiter=limiter),
+                                  mirror(mhd.step_periodic(U, dx, dt, cfg, limiter=limiter)))
+    assert mhd.cfl_periodic(mirror(U), dx, cfg) == mhd.cfl_periodic(U, dx, cfg)
+
+
+def test_cfl_bruteforce():
+    """The CFL dt against a cell-by-cell loop: the smallest cfl dx / sum_d (|u_d| + c_f,d) over the
+    box, the fast speed of each axis from its closed forms (field along the axis:
+    max(a, |B|/sqrt(rho)); field across it: sqrt(a^2 + b^2)); one cell made fast sets the dt."""
+    cfg = oracle.config()
+    rng = np.random.default_rng(60)
+    shape = (3, 4, 5)
+    q = np.zeros((9,) + shape)
+    q[0] = rng.uniform(0.5, 2.0, shape)
+    q[1:4] = rng.normal(0, 0.5, (3,) + shape)
+    q[4] = rng.uniform(0.2, 1.0, shape)
+    q[5] = rng.normal(0, 0.8, shape)   # field along x only: c_f,x = max(a, |B|/sqrt(rho)),
+    q[1, 1, 2, 3] = 6.0                # c_f,y = c_f,z = sqrt(a^2 + b^2)
+    U = mhd.conserved(q, cfg)
+    dx = 0.05
+    best = math.inf
+    for k in range(shape[0]):
+        for j in range(shape[1]):
+            for i in range(shape[2]):
+                rho, p, B = q[0, k, j, i], q[4, k, j, i], q[5, k, j, i]
+                a2, b2 = cfg.gamma * p / rho, B * B / rho
+                s = abs(q[1, k, j, i]) + math.sqrt(max(a2, b2))
+                s += abs(q[2, k, j, i]) + math.sqrt(a2 + b2)
+                s += abs(q[3, k, j, i]) + math.sqrt(a2 + b2)
+                best = min(best, cfg.cfl * dx / s)
+    got = mhd.cfl_periodic(U, dx, cfg)
+    assert abs(got - best) <= 1e-13 * best, (got, best)
+    fast = U.copy()
+    fast[:, 1, 2, 3] = U[:, 0, 0, 0]
+    assert mhd.cfl_periodic(fast, dx, cfg) > got   # the fast cell set the dt
