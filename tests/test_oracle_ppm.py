@@ -71,6 +71,11 @@ def test_edge_properties_on_rough_data():
     # local extrema are flattened
     ext = (np.roll(q, -1, 3) - q) * (q - np.roll(q, 1, 3)) <= 0
     assert np.all(flat[ext])
+    # each edge stays between its cell's value and the neighbour's across it: the constraints move
+    # the edge on the side of the parabola's extremum towards the cell value, never past it
+    qp, qm = np.roll(q, -1, 3), np.roll(q, 1, 3)
+    assert np.all((qR >= np.minimum(q, qp) - 1e-12) & (qR <= np.maximum(q, qp) + 1e-12))
+    assert np.all((qL >= np.minimum(q, qm) - 1e-12) & (qL <= np.maximum(q, qm) + 1e-12))
     # the parabola's mean is the cell value: qL + D/2 + Q6/6 == q
     np.testing.assert_allclose(qL + 0.5 * D + Q6 / 6.0, q, rtol=0, atol=1e-12)
 
