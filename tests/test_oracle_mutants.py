@@ -97,6 +97,28 @@ CPP = {
         (HPP, "U[4] = q[4] / T(c.gamma - 1.0) + T(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);",
          "U[4] = q[4] / T(c.gamma - 1.0) + T(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);",
          "test_first_step_of_a_zigzag_is_first_order_godunov", ("minmod",)),
+    # the derivative scalar types behind the oracle's tangent (J v) and tape adjoint (J^T w)
+    "tangent: quotient rule with a plus":
+        ("scalars.hpp", "return Dual(q, (a.d - q * b.d) / b.v);", "return Dual(q, (a.d + q * b.d) / b.v);",
+         "test_tangent_matches_central_differences", ("none",)),
+    "tangent: derivative of sqrt without the 1/2":
+        ("scalars.hpp", "return Dual(s, a.d / (2.0 * s));", "return Dual(s, a.d / s);",
+         "test_tangent_matches_central_differences", ("none",)),
+    "adjoint: product partials exchanged":
+        ("scalars.hpp", "return tv_make(a.v * b.v, a.i, b.v, b.i, a.v);", "return tv_make(a.v * b.v, a.i, a.v, b.i, b.v);",
+         "test_adjoint_dot_product", ("none",)),
+    "adjoint: quotient partial with the wrong sign":
+        ("scalars.hpp", "return tv_make(q, a.i, 1.0 / b.v, b.i, -q / b.v);", "return tv_make(q, a.i, 1.0 / b.v, b.i, q / b.v);",
+         "test_adjoint_dot_product", ("none",)),
+    "adjoint: difference partial +1 for the subtrahend":
+        ("scalars.hpp", "return tv_make(a.v - b.v, a.i, 1.0, b.i, -1.0);", "return tv_make(a.v - b.v, a.i, 1.0, b.i, 1.0);",
+         "test_adjoint_dot_product", ("none",)),
+    "adjoint: reverse sweep overwrites instead of accumulating":
+        ("scalars.hpp", "if (n.b >= 0) adj[(size_t)n.b] += n.db * g;", "if (n.b >= 0) adj[(size_t)n.b] = n.db * g;",
+         "test_adjoint_dot_product", ("none",)),
+    "op count: division not counted":
+        ("scalars.hpp", "{ ++op_counter(); ++op_kinds()[2]; return Counted(a.v / b.v); }",
+         "{ ++op_kinds()[2]; return Counted(a.v / b.v); }", "test_op_counts_match_stage_formulas", ()),
 }
 CPP_SOURCES = ("oracle_capi.cpp", "euler_oracle.hpp", "scalars.hpp")
 
