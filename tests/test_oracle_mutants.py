@@ -288,6 +288,29 @@ PY = {
     "AMR: sibling exchange reads one cell past an interior":
         ("amr", "inside = np.all(rel < dims[b][None, :], axis=1)", "inside = np.all(rel <= dims[b][None, :], axis=1)",
          pins_amr, "test_sibling_exchange_reassembles_a_partitioned_level", ()),
+    # exact Riemann solver and Sedov-Taylor constant
+    "Riemann: shock relation with gamma - 1 in place of gamma + 1":
+        ("riemann_exact", "A = 2.0 / ((g + 1.0) * rho)", "A = 2.0 / ((g - 1.0) * rho)", pins_hydro,
+         "test_exact_riemann_matches_toro_table", ()),
+    "Riemann: rarefaction relation with the exponent inverted":
+        ("riemann_exact", "    r = (p / pk) ** e\n", "    r = (p / pk) ** (1.0 / e)\n", pins_hydro,
+         "test_exact_riemann_matches_toro_table", ()),
+    "Riemann: star density behind a left shock without the ratio's gm":
+        ("riemann_exact", "st = (rl * (ps / pl + gm) / (gm * ps / pl + 1.0), us, ps)",
+         "st = (rl * (ps / pl) / (gm * ps / pl + 1.0), us, ps)", pins_hydro,
+         "test_exact_riemann_matches_toro_table", ()),
+    "Riemann: left fan velocity with the wrong sign of s":
+        ("riemann_exact", "u = 2.0 / (g + 1.0) * (cl + 0.5 * (g - 1.0) * ul + s)",
+         "u = 2.0 / (g + 1.0) * (cl + 0.5 * (g - 1.0) * ul - s)", pins_hydro,
+         "test_sod_converges_to_exact_solution", (1.4,)),
+    "Sedov: momentum equation without the 3 phi / 2 source":
+        ("sedov", "b = np.array([-2.0 * psi * phi / eta, 1.5 * phi, 3.0])",
+         "b = np.array([-2.0 * psi * phi / eta, 0.0 * phi, 3.0])", pins_hydro,
+         "test_sedov_constant_matches_tables", ()),
+    "Sedov: energy integral without the kinetic 1/2":
+        ("sedov", "dI = eta * eta * (0.5 * psi * phi * phi + f / (g - 1.0))",
+         "dI = eta * eta * (psi * phi * phi + f / (g - 1.0))", pins_hydro,
+         "test_sedov_constant_matches_tables", ()),
 }
 
 

@@ -177,6 +177,9 @@ def test_sod_converges_to_exact_solution(gamma):
             np.testing.assert_allclose(prim[4][plateau], ps, rtol=1e-2)
             np.testing.assert_allclose(prim[1][plateau], us, rtol=1e-2)
             np.testing.assert_allclose(prim[0][plateau], ex[0][plateau], rtol=1e-2)
+            # velocity and pressure over the whole tube, rarefaction fan included (L1 ~0.005, 0.0025)
+            assert np.abs(prim[1] - ex[1]).mean() < 0.01
+            assert np.abs(prim[4] - ex[2]).mean() < 0.005
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.006
     assert errs[0] / errs[2] > 2.5  # at least ~first order at discontinuities
