@@ -383,6 +383,31 @@ def test_adjoint_dot_product(limiter):
     assert abs(a - b) <= 1e-12 * max(abs(a), np.abs(w * Jv).sum())
 
 
+@pytest.mark.parametrize("limiter", ["minmod", "none"])
+def test_patch_adjoint_folds_onto_the_periodic_adjoint(limiter):
+    """The periodic step is the ghosted-patch step of the box padded by periodic wrap (a linear copy
+    P), so J_per^T w = P^T J_patch^T w: the patch adjoint's ghost-cell entries, added onto the cells
+    they copy, give the periodic adjoint (up to summation order)."""
+    cfg = oracle.config(limiter=limiter)
+    U = workloads.white_velocity_state((6, 7, 8), seed=13).numpy()
+    dx = 0.1
+    dt = 0.7 * oracle.cfl_periodic(U, dx, cfg)
+    w = np.random.default_rng(14).standard_normal(U.shape)
+    lam_g = oracle.step_patch_adjoint(oracle.fill_ghosts_periodic(U), w, dx, dt, cfg)
+    _, nz, ny, nx = U.shape
+    iz = (np.arange(nz + 4) - 2) % nz
+    iy = (np.arange(ny + 4) - 2) % ny
+    ix = (np.arange(nx + 4) - 2) % nx
+    folded = np.zeros_like(U)
+    np.add.at(folded, (slice(None), iz[:, None, None], iy[None, :, None], ix[None, None, :]), lam_g)
+    lam = oracle.step_periodic_adjoint(U, w, dx, dt, cfg)
+    for f in range(5):
+        assert np.abs(folded[f] - lam[f]).max() <= 1e-12 * np.abs(lam[f]).max(), f
+    # and the patch step itself is the periodic step on the padded box
+    np.testing.assert_array_equal(oracle.step_patch(oracle.fill_ghosts_periodic(U), dx, dt, cfg),
+                                  oracle.step_periodic(U, dx, dt, cfg))
+
+
 def test_adjoint_block_split_is_exact():
     cfg = oracle.config()
     U = workloads.white_velocity_state((6, 6, 8), seed=13).numpy()
