@@ -1,0 +1,56 @@
+"""Host-side pieces of bench.py on the CPU: the clock sampler's summary of nvidia-smi lines (median
+SM clock under load, the throttle reasons seen), the roofline object's arithmetic and choice of
+roof, and the whole-job throughput over ranks."""
+import math
+
+import pytest
+
+import bench
+
+
+def sampler(lines):
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.lines = list(lines)
+    return s
+
+
+def test_clock_summary_median_max_and_reasons():
+    lines = [
+        "2070, 2070, 900.5, Not Active, Not Active, Not Active, Not Active",
+        "1995, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
+        "2040, 2070, 1200.0, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], 2070, 10.0, Not Active, Not Active, Not Active, Not Active",   # unreadable: skipped
+        "2070, 2070",                                                           # short: skipped
+    ]
+    s = sampler(lines).summary()
+    assert s["sm_mhz"] == 2040 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    s = sampler(lines + ["1500, 2070, 800.0, Active, Not Active, Active, Not Active"]).summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert sampler([]).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
+
+def test_roofline_takes_the_roof_with_the_larger_fraction():
+    # native FP64: 1e6 cells in 1 ms at 375 flops and 80 B per cell -> 0.375 TFLOP/s, 80 GB/s
+    r = bench.roofline("fp64", 1e6, [1.0, 1.0], 375.0, 6681.8, "measured", None)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(0.375) and r["peak"] == pytest.approx(bench.FP64_PEAK_TFLOPS, abs=0.01)
+    assert r["frac"] == pytest.approx(0.375 / bench.FP64_PEAK_TFLOPS, abs=1e-4)
+    assert r["hbm_frac"] == pytest.approx(80.0 / 6681.8, abs=1e-4)
+    assert r["algorithmic_bytes_per_launch"] == 80e6 and r["traffic"] is None
+    # FP32 with few flops per cell: the HBM roof binds
+    r = bench.roofline("fp32", 1e6, [0.5], 10.0, 6681.8, "measured", 1.23e8)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(80.0) and r["frac"] == pytest.approx(80.0 / 6681.8, abs=1e-4)
+    assert r["traffic"] == 1.23e8
+    # double-float: the FP32 operations of the double-word algorithms against the FP32 peak
+    r = bench.roofline("df64", 1e6, [2.0], 375.0, 6681.8, "measured", None)
+    tfl = 1e6 * bench.ALG_DF_FLOPS_PER_CELL["turb_minmod"] / 2e-3 / 1e12
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(tfl, abs=1e-3)
+    assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS, abs=0.01)
+
+
+def test_job_value_counts_every_rank_over_the_slowest():
+    assert bench.job_value(1e6, 10, 1, 100.0) == pytest.approx(100.0)      # 1e7 updates in 0.1 s
+    assert bench.job_value(1e6, 10, 4, 200.0) == pytest.approx(200.0)      # 4e7 updates in 0.2 s
+    assert math.isclose(bench.job_time_ms(12.5, 1, "cpu"), 12.5)
