@@ -839,7 +839,7 @@ def cpu_baseline(n, seconds, steps_cap=1000):
         U = oracle.step_periodic(U, dx, dt, cfg)
         steps += 1
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle.threads()
     return {"value": n ** 3 * steps / el / 1e6, "unit": "Mcell-updates/s", "cores": threads, "kind": "oracle",
             "sample": "%d^3 box of the same workload (lognormal rho, k^-4 Mach-5 velocities, P/rho=1e-4, Sedov "
                       "cell), %d FP64 steps incl. CFL dt, %.1f s" % (n, steps, el)}
@@ -867,7 +867,7 @@ def reference_arm(args):
     for _ in range(args.steps):
         U = step(U)
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle.threads()
     value = n ** 3 * args.steps / el / 1e6
     line = {"impl": "reference", "metric": "Mcell-updates/s per hydro step (1 GB300)", "value": value,
             "unit": "Mcell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

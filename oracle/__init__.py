@@ -57,6 +57,8 @@ def load(so):
     L.oracle_prim_to_cons_adjoint.argtypes = [P, vp, vp, vp, ctypes.c_long]
     L.oracle_count_ops.argtypes = [P, vp, i, i, i, d, d, vp]
     L.oracle_patch_boundary_fluxes.argtypes = [P, vp, i, i, i, d, d, vp]
+    L.oracle_threads.argtypes = []
+    L.oracle_threads.restype = i
     return L
 
 
@@ -65,6 +67,11 @@ def lib():
     if _lib is None:
         _lib = load(_build.build())
     return _lib
+
+
+def threads():
+    """OpenMP threads of the oracle's parallel stages on this host."""
+    return int(lib().oracle_threads())
 
 
 def _c(a):

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <vector>
 
+#include <omp.h>
+
 #include "euler_oracle.hpp"
 
 using namespace oracle;
@@ -308,5 +310,8 @@ int oracle_count_ops(const oracle_config* cfg, const double* U, int nx, int ny, 
   record(4, stage_update(Ug, flux, B, dx, dt));
   return 0;
 }
+
+// The number of OpenMP threads the oracle's parallel stages run with on this host.
+int oracle_threads() { return omp_get_max_threads(); }
 
 }  // extern "C"

@@ -54,3 +54,38 @@ def test_job_value_counts_every_rank_over_the_slowest():
     assert bench.job_value(1e6, 10, 1, 100.0) == pytest.approx(100.0)      # 1e7 updates in 0.1 s
     assert bench.job_value(1e6, 10, 4, 200.0) == pytest.approx(200.0)      # 4e7 updates in 0.2 s
     assert math.isclose(bench.job_time_ms(12.5, 1, "cpu"), 12.5)
+
+
+def _run_bench(args, env_extra):
+    import json
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, OMP_NUM_THREADS="2", **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py")] + args,
+                       capture_output=True, text=True, env=env, timeout=600)
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    return r.returncode, lines
+
+
+def test_reference_arm_line():
+    """The reference arm (the CPU oracle on a bounded sample) prints one line with the contract's
+    keys; its cores are the oracle's OpenMP threads."""
+    rc, lines = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {})
+    assert rc == 0 and len(lines) == 1
+    line = lines[0]
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1 and line["n_gpus"] == 1
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None and "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    rc, lines = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                           {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert rc == 0 and lines == []
