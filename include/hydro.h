@@ -107,12 +107,15 @@ typedef struct {
 
 typedef struct hydro_ctx hydro_ctx;
 
-/* Create a context on the current CUDA device.  Validates cfg (gamma > 1, 0 < cfl <= 1,
+/* Create a context on the current CUDA device (library bookkeeping, no counterpart in the paper;
+ * cfg holds the ideal-gas gamma of Sec. 2 and the CFL number of the adaptive step, Sec. 4).
+ * Validates cfg (gamma > 1, 0 < cfl <= 1,
  * floors >= 0, enums in range) and allocates the device error word.  *ctx is set to NULL on
  * failure.  Returns HYDRO_OK, HYDRO_ERR_ARG, HYDRO_ERR_NOMEM or HYDRO_ERR_CUDA. */
 int hydro_init(hydro_ctx** ctx, const hydro_config* cfg);
 
-/* Synchronise the context's stream and free everything the context owns. NULL is a no-op. */
+/* Synchronise the context's stream and free everything the context owns (no counterpart in the
+ * paper).  NULL is a no-op. */
 int hydro_finalize(hydro_ctx* ctx);
 
 /* Per-patch CFL time step (adaptive time step, Sec. 2 and Sec. 4):
@@ -173,7 +176,8 @@ int hydro_fill_ghosts(hydro_ctx* ctx, const hydro_patch* coarse, const hydro_pat
 int hydro_fill_ghosts_time(hydro_ctx* ctx, const hydro_patch* coarse_old, const hydro_patch* coarse_new, double theta,
                            const hydro_patch* fine, const int* fine_origins, int npatch);
 
-/* Same-level ghost exchange: every ghost cell of a patch that lies in the interior of a patch of the
+/* Same-level ghost exchange (the boundary cells a chunk carries, Sec. 3, where a neighbouring patch
+ * of the same level covers them): every ghost cell of a patch that lies in the interior of a patch of the
  * same level (another one, or the patch itself across the period) takes that interior cell's
  * values; other ghost cells are left as they are (fill them from the coarser level first with
  * hydro_fill_ghosts).  The level is periodic with period[3] = (x, y, z) fine cells.
@@ -321,7 +325,8 @@ int hydro_mhd_cfl_patches(hydro_ctx* ctx, const hydro_mhd_patch* p, int npatch, 
 int hydro_adjoint_step(hydro_ctx* ctx, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,
                        const hydro_patch* lam_n, int npatch);
 
-/* Primitive -> conservative map of the initial state and its adjoint (used to turn gradients with
+/* Primitive -> conservative map of the initial state and its adjoint (part of the adjoint interface,
+ * no counterpart in the paper; the ideal-gas closure of Sec. 2; used to turn gradients with
  * respect to U^0 into gradients with respect to the initial density and velocity):
  *   U = (rho, rho u, rho v, rho w, p/(gamma-1) + rho |u|^2 / 2).
  * W holds (rho, u, v, w, p) in the layout of a patch; lamW receives (dU/dW)^T lamU. */
@@ -329,7 +334,8 @@ int hydro_prim_to_cons(hydro_ctx* ctx, const hydro_patch* W, const hydro_patch* 
 int hydro_prim_to_cons_adjoint(hydro_ctx* ctx, const hydro_patch* W, const hydro_patch* lamU,
                                const hydro_patch* lamW, int npatch);
 
-/* Multi-step run of one periodic box with the time step kept on the device (no host
+/* Multi-step run of one periodic box, each step at the adaptive time step of Sec. 2 and Sec. 4 (the
+ * graph capture has no counterpart in the paper), with the time step kept on the device (no host
  * synchronisation per step): dt_hist_dev[0] = CFL dt of the state in a; step n advances by
  * dt_hist_dev[n] and writes dt_hist_dev[n+1] = CFL dt of its result; states ping-pong between
  * a (even n) and b (odd n), so the result is in a if nsteps is even, else in b.
@@ -354,7 +360,8 @@ int hydro_run(hydro_ctx* ctx, const hydro_patch* a, const hydro_patch* b, int ns
 int hydro_step_host(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, const double* dt_dev,
                     double* dt_next_dev);
 
-/* Autotuner: times the candidate tile shapes and z-chunk depths of hydro_step on this patch set
+/* Autotuner (no counterpart in the paper, whose Sec. 3 finds that small chunks starve the GPU): times
+ * the candidate tile shapes and z-chunk depths of hydro_step on this patch set
  * (in, out, dt_dev as for hydro_step; contents of out are overwritten) and keeps the fastest in
  * the context for later hydro_step calls.  If cache_path is not NULL the choice is read from /
  * appended to that text file, keyed by GPU name, SM count, precision and patch-set signature.
@@ -362,17 +369,20 @@ int hydro_step_host(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* ou
 int hydro_autotune(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
                    const char* cache_path);
 
-/* Current tile configuration: *tile_id (index into the compiled tile shapes) and *zchunk. */
+/* Current tile configuration: *tile_id (index into the compiled tile shapes) and *zchunk (no
+ * counterpart in the paper). */
 int hydro_get_tuning(hydro_ctx* ctx, int* tile_id, int* zchunk);
 int hydro_set_tuning(hydro_ctx* ctx, int tile_id, int zchunk);
 
-/* Synchronise the context's stream and return the device error word in *error_bits (may be
+/* Failure reporting (no counterpart in the paper): synchronise the context's stream and return the
+ * device error word in *error_bits (may be
  * NULL).  Returns HYDRO_ERR_UNPHYSICAL if any bit is set, HYDRO_OK otherwise, HYDRO_ERR_CUDA on
  * a CUDA error.  hydro_clear_error zeroes the word (asynchronously). */
 int hydro_get_error(hydro_ctx* ctx, unsigned* error_bits);
 int hydro_clear_error(hydro_ctx* ctx);
 
-/* Number of kernels this context has launched so far (graph replays count their kernels). */
+/* Number of kernels this context has launched so far (graph replays count their kernels; no
+ * counterpart in the paper). */
 int hydro_launch_count(hydro_ctx* ctx, long long* count);
 
 /* The batched step of hydro_step for callers that cannot allocate device memory (no counterpart
