@@ -301,7 +301,8 @@ typedef struct {
   double dx;         /* cell size, > 0 */
   int level;         /* refinement level (informational) */
 } hydro_mhd_patch;
-/*   hydro_mhd_step_patches: out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] (device
+/* MHD on patches (Sec. 4, Enzo's MHD on the GPU; patches carrying their boundary cells, Sec. 3):
+ *   hydro_mhd_step_patches: out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] (device
  *       array of npatch doubles) and cell size in[p].dx; in[p] and out[p] of equal sizes and dx, not
  *       overlapping; dt_next_dev: NULL or npatch doubles receiving each patch's CFL dt of U^{n+1}.
  *       Device scratch of 81 elements per cell of each patch's interior grown by one cell per side.
@@ -405,7 +406,7 @@ int hydro_launch_count(hydro_ctx* ctx, long long* count);
 int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_patch* in, const hydro_patch* out, int npatch,
                                const double* dt_dev, double* dt_next_dev, unsigned* error_bits_dev);
 
-/* Static description of a status code. */
+/* Static description of a status code (no counterpart in the paper). */
 const char* hydro_status_string(int status);
 
 #ifdef __cplusplus
