@@ -69,8 +69,27 @@ def test_init_rejects_bad_config_without_gpu(libpath):
 
 
 def test_null_context_calls_are_argument_errors(libpath):
+    """Every entry point called with a NULL context (or config), NULL pointers and zero counts
+    returns HYDRO_ERR_ARG from its host-side checks, before any CUDA call (finalize of NULL is a
+    no-op; the status string is static)."""
     import paper_1412_0934_gb300 as hy
     L = hy.lib()
-    assert L.hydro_step(None, None, None, 1, None, None) == hy.HYDRO_ERR_ARG
-    assert L.hydro_cfl_dt(None, None, 1, None) == hy.HYDRO_ERR_ARG
-    assert L.hydro_finalize(None) == hy.HYDRO_OK
+    scalars = (ctypes.c_int, ctypes.c_uint, ctypes.c_long, ctypes.c_longlong, ctypes.c_size_t, ctypes.c_double,
+               ctypes.c_float)
+    results = {}
+    for name in sorted(hy.EXPORTS):
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        args = []
+        for t in f.argtypes:
+            if t in scalars:
+                args.append(0)
+            elif isinstance(t, type) and issubclass(t, ctypes.Array):
+                args.append(t())
+            else:
+                args.append(None)
+        results[name] = f(*args)
+    assert results.pop("hydro_finalize") == hy.HYDRO_OK
+    assert results.pop("hydro_status_string") == b"ok"
+    bad = {k: v for k, v in results.items() if v != hy.HYDRO_ERR_ARG}
+    assert not bad, bad
