@@ -10,6 +10,7 @@ the same pins in their own files.  Nothing here touches the CUDA library.
 import os
 import shutil
 import subprocess
+import time
 import types
 
 import pytest
@@ -129,9 +130,11 @@ def _slug(name):
 
 @pytest.fixture(scope="module")
 def cpp_mutants():
-    """Every C++ mutant built in parallel under tests/_mutants (removed afterwards)."""
+    """Every C++ mutant built under tests/_mutants, one compiler per core at a time (removed
+    afterwards)."""
     shutil.rmtree(WORK, ignore_errors=True)
     procs, libs = {}, {}
+    width = max(1, os.cpu_count() or 1)
     for name, (fname, old, new, _, _) in CPP.items():
         d = os.path.join(WORK, _slug(name))
         os.makedirs(d)
@@ -144,6 +147,8 @@ def cpp_mutants():
             with open(os.path.join(d, src), "w") as f:
                 f.write(text)
         libs[name] = os.path.join(d, "mutant.so")
+        while sum(p.poll() is None for p in procs.values()) >= width:
+            time.sleep(0.05)
         procs[name] = subprocess.Popen(obuild.command([os.path.join(d, "oracle_capi.cpp")], libs[name]))
     for name, p in procs.items():
         assert p.wait() == 0, name
