@@ -63,7 +63,11 @@ typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2, HYDRO_FP64_DF = 
  * HYDRO_FP64_DF: double state; every step of the scheme in double-float arithmetic (pairs of
  *              floats, about 48 significant bits, on the FP32 pipes), the update U + dU accumulated
  *              in double.  Same results as HYDRO_FP64 to about 1e-13 relative, several times faster
- *              on parts whose FP64 rate is a small fraction of their FP32 rate. */
+ *              on parts whose FP64 rate is a small fraction of their FP32 rate.  Its exponent range
+ *              is that of float: the intermediates of the scheme (state, speeds, fluxes, products
+ *              such as rho u^2) keep the FP64 accuracy only between about 1e-30 and 3e38 in
+ *              magnitude -- below, the low float of a pair leaves the normal range and relative
+ *              accuracy drops towards float's; above, they overflow. */
 
 typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2, HYDRO_PPM = 3 } hydro_limiter;
 /* HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT: piecewise-linear (PLM) reconstruction with that slope.
@@ -371,7 +375,11 @@ int hydro_autotune(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out
                    const char* cache_path);
 
 /* Current tile configuration: *tile_id (index into the compiled tile shapes) and *zchunk (no
- * counterpart in the paper). */
+ * counterpart in the paper).  Compiled shapes (columns x rows of one block's tile): 0 16 x 16,
+ * 1 32 x 8, 2 8 x 8, 3 32 x 16, 4 16 x 16 with a whole SM's registers for one block; the PPM
+ * kernel has one shape (16 x 16) and ignores tile_id.  hydro_set_tuning refuses tile_id outside
+ * [0, HYDRO_NUM_TILES) and zchunk outside [1, 4096]. */
+#define HYDRO_NUM_TILES 5
 int hydro_get_tuning(hydro_ctx* ctx, int* tile_id, int* zchunk);
 int hydro_set_tuning(hydro_ctx* ctx, int tile_id, int zchunk);
 
@@ -391,13 +399,15 @@ int hydro_launch_count(hydro_ctx* ctx, long long* count);
  * memory pool or a fixed memory budget, code that must not allocate after start-up, or a host
  * program that only receives device pointers.  hydro_step needs a context and hydro_init
  * allocates; this call needs none.  Its scratch -- uploaded patch descriptors, prefix-sum counts,
- * the tile work-list, the tile counter and a fallback error word -- is a set of file-scope device
- * arrays of fixed size (about 4.7 MB) that every GPU loading the library holds until the process
- * exits.  Limits: npatch <= 4096 and at most 262144 tiles of 16 x 16 columns x 32 planes
- * (HYDRO_ERR_ARG beyond either).  cfg, in, out, npatch, dt_dev, dt_next_dev have the meaning of
- * hydro_init's config and hydro_step's arguments; error_bits_dev, if not NULL, is a device word
- * that receives HYDRO_EBIT_* bits by atomic OR (the caller zeroes it); NULL uses the internal
- * word, which nothing reads back.  The first call on a device looks up the arrays' device
+ * the tile work-list and the tile counter -- is a set of file-scope device arrays of fixed size
+ * (about 4.7 MB) that every GPU loading the library holds until the process exits.  Limits:
+ * npatch <= 4096 and at most 262144 tiles of 16 x 16 columns x 32 planes (HYDRO_ERR_ARG beyond
+ * either).  cfg, in, out, npatch, dt_dev, dt_next_dev have the meaning of hydro_init's config and
+ * hydro_step's arguments, with hydro_step's ghost rule (every input patch carries two ghost
+ * layers; a single periodic box, ng == 0, none); the step runs the compiled tile 0 with 32-plane
+ * z chunks, so its results are those of hydro_step at that tuning, bit for bit.  error_bits_dev
+ * (required: NULL gives HYDRO_ERR_ARG) is a device word that receives HYDRO_EBIT_* bits by atomic
+ * OR; the caller zeroes it and reads it back.  The first call on a device looks up the arrays' device
  * addresses (cudaGetSymbolAddress, with that device current): make that first call before any
  * stream capture.  Every call reuses the same arrays (their previous contents are overwritten;
  * the tile counter is cleared on each call), so calls whose work overlaps on the GPU -- on

@@ -29,6 +29,10 @@ HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT, HYDRO_PPM = 0, 1, 2, 3
 PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED, "df64": HYDRO_FP64_DF}
 LIMITERS = {"minmod": HYDRO_MINMOD, "mc": HYDRO_MC, "none": HYDRO_NOLIMIT, "ppm": HYDRO_PPM}
 
+# Compiled tile shapes of the step kernels, by tile id (HYDRO_NUM_TILES in include/hydro.h).
+TILE_SHAPES = ((16, 16), (32, 8), (8, 8), (32, 16), (16, 16))
+NUM_TILES = len(TILE_SHAPES)
+
 EBIT_NONFINITE = 0x01
 EBIT_RHO_FLOOR = 0x02
 EBIT_P_FLOOR = 0x04

@@ -359,13 +359,11 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
   scr.ld = scr.lq + 5 * N;
   scr.code = reinterpret_cast<unsigned*>(scr.ld + 15 * N);
   const size_t smem = sizeof(AdjShared<R, TX, TY>);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_faces<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  cudaError_t ea = attr.call([&] {
+    return cudaFuncSetAttribute(k_adj_faces<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (ea != cudaSuccess) return ea;
   // z chunk: FP32 takes the longest of 16, 8, 4, 2 planes whose grid still fills half of the SMs'
   // resident blocks (a small grid leaves SMs idle, a short march repeats halo planes; half is the
   // measured balance).  FP64 keeps 16: it is bound by the FP64 pipe, which a few warps per SM

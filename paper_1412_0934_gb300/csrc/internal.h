@@ -2,9 +2,29 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "hydro.h"
 
 namespace hydro {
+
+// A setting made once per device (a kernel's shared-memory opt-in is a property of the kernel on
+// the device that is current when it is set): call() runs f the first time it is used with each
+// device (ordinals 0-63) current, and again on later calls only if f failed.
+struct PerDeviceOnce {
+  std::atomic<unsigned long long> done{0};
+  template <class F>
+  cudaError_t call(F&& f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+  }
+};
 
 struct Params;
 
@@ -25,7 +45,7 @@ struct HostTileRec {
 // Compiled tile shapes of the step kernels (TX x TY columns per block) and the resident blocks
 // per SM their register allocation targets (0: the policy default, 2 x 256 threads for 8-byte
 // arithmetic, 3 x 256 for float; 1: a whole SM's registers for one block, no spills).
-constexpr int kNumTiles = 5;
+constexpr int kNumTiles = HYDRO_NUM_TILES;
 constexpr int kTileX[kNumTiles] = {16, 32, 8, 32, 16};
 constexpr int kTileY[kNumTiles] = {16, 8, 8, 16, 16};
 constexpr int kTileMinBlocks[kNumTiles] = {0, 0, 0, 0, 1};

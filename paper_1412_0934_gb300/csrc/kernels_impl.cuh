@@ -16,13 +16,12 @@ template <class Pol, int TX, int TY, int MINB>
 cudaError_t launch_uniform_t(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
                              unsigned* err, cudaStream_t s) {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  cudaError_t e = attr.call([&] {
+    return cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
   k_step_uniform<Pol, TX, TY, MINB><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
   return cudaGetLastError();
@@ -33,13 +32,12 @@ cudaError_t launch_batched_t(const HostPatchIO* d_patches, const HostTileRec* d_
                              const Params& prm, const double* dt, double* dt_next, int zchunk, unsigned* err, int grid,
                              cudaStream_t s) {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  cudaError_t e = attr.call([&] {
+    return cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   k_step_batched<Pol, TX, TY, MINB><<<grid, TX * TY, smem, s>>>(
       reinterpret_cast<const PatchIO<typename Pol::S>*>(d_patches), reinterpret_cast<const TileRec*>(d_tiles), ntiles,
       d_counter, prm, dt, dt_next, zchunk, err);
@@ -416,12 +414,10 @@ cudaError_t launch_octs_src(const Src& src, void* const out[5], long long ngroup
                             const double* dt, unsigned* err, cudaStream_t s) {
   using S = typename Pol::S;
   const size_t smem = sizeof(OctSmem<Pol>);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_octs<Pol, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  cudaError_t e = attr.call(
+      [&] { return cudaFuncSetAttribute(k_octs<Pol, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
+  if (e != cudaSuccess) return e;
   long long blocks = (ngroups + kOctWarps - 1) / kOctWarps;
   const long long cap = 152LL * 64;
   if (blocks > cap) blocks = cap;

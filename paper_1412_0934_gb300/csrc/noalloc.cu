@@ -3,9 +3,10 @@
 // pool or under a strict memory budget, code that must not allocate after start-up, or a host
 // program that only receives device pointers from elsewhere.  hydro_step needs a context, and
 // hydro_init allocates; this entry point needs no context: the scratch that the batched step
-// uses (uploaded patch descriptors, the prefix-sum counts, the tile work-list, the tile counter
-// and a fallback error word) lives in the file-scope __device__ arrays below, which every GPU that
-// loads the library holds until the process exits (about 4.7 MB).
+// uses (uploaded patch descriptors, the prefix-sum counts, the tile work-list and the tile
+// counter) lives in the file-scope __device__ arrays below, which every GPU that loads the library
+// holds until the process exits (about 4.7 MB).  The caller passes the device word that receives
+// the error bits, so that no fault the kernels detect goes unread.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,7 +27,6 @@ static __device__ __align__(256) hydro::HostPatchIO g_patches[kMaxPatches];
 static __device__ __align__(256) int g_counts[kMaxPatches + 1];
 static __device__ __align__(256) hydro::HostTileRec g_tiles[kMaxTiles];
 static __device__ __align__(256) int g_counter[1];
-static __device__ __align__(256) unsigned g_error[1];
 
 // Device addresses of the arrays above, looked up once per device (host code must not use the
 // array names themselves: on the host they are stand-ins, not device addresses).
@@ -36,7 +36,6 @@ struct DeviceScratch {
   int* counts = nullptr;
   hydro::HostTileRec* tiles = nullptr;
   int* counter = nullptr;
-  unsigned* error = nullptr;
 };
 DeviceScratch g_scratch[kMaxDevices];
 std::mutex g_setup_mutex;
@@ -52,8 +51,7 @@ int setup_device(int dev, DeviceScratch** out) {
     if (cudaGetSymbolAddress(reinterpret_cast<void**>(&s.patches), g_patches) != cudaSuccess ||
         cudaGetSymbolAddress(reinterpret_cast<void**>(&s.counts), g_counts) != cudaSuccess ||
         cudaGetSymbolAddress(reinterpret_cast<void**>(&s.tiles), g_tiles) != cudaSuccess ||
-        cudaGetSymbolAddress(reinterpret_cast<void**>(&s.counter), g_counter) != cudaSuccess ||
-        cudaGetSymbolAddress(reinterpret_cast<void**>(&s.error), g_error) != cudaSuccess)
+        cudaGetSymbolAddress(reinterpret_cast<void**>(&s.counter), g_counter) != cudaSuccess)
       return HYDRO_ERR_CUDA;
     s.ready = true;
   }
@@ -87,7 +85,7 @@ bool disjoint(const hydro_patch& a, const hydro_patch& b, int es) {
 extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_patch* in, const hydro_patch* out,
                                           int npatch, const double* dt_dev, double* dt_next_dev,
                                           unsigned* error_bits_dev) {
-  if (!cfg || !in || !out || !dt_dev || npatch < 1) return HYDRO_ERR_ARG;
+  if (!cfg || !in || !out || !dt_dev || !error_bits_dev || npatch < 1) return HYDRO_ERR_ARG;
   if (npatch > kMaxPatches) return HYDRO_ERR_ARG;
   if (!(cfg->gamma > 1.0 && std::isfinite(cfg->gamma)) || !(cfg->cfl > 0.0 && cfg->cfl <= 1.0) ||
       !(cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0) || cfg->limiter < HYDRO_MINMOD || cfg->limiter > HYDRO_NOLIMIT ||
@@ -102,6 +100,8 @@ extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_p
     const hydro_patch &a = in[i], &b = out[i];
     if (!patch_ok(a, es) || !patch_ok(b, es)) return HYDRO_ERR_ARG;
     if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.dx != b.dx || !disjoint(a, b, es)) return HYDRO_ERR_ARG;
+    // the ghost layers hydro_step asks for: two per input patch, or none for a single periodic box
+    if (a.ng != 2 && !(npatch == 1 && a.ng == 0)) return HYDRO_ERR_ARG;
     total += (long long)((a.nx + tx - 1) / tx) * ((a.ny + ty - 1) / ty) * ((a.nz + zchunk - 1) / zchunk);
   }
   if (total > kMaxTiles) return HYDRO_ERR_ARG;
@@ -115,7 +115,7 @@ extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_p
   const hydro::KernelOps& ops = *hydro::ops_for(cfg->precision);
   const hydro::Params prm = hydro::make_params(cfg->gamma, cfg->cfl, cfg->rho_floor, cfg->p_floor, cfg->limiter);
   cudaStream_t st = static_cast<cudaStream_t>(cfg->cuda_stream);
-  unsigned* err = error_bits_dev ? error_bits_dev : s->error;
+  unsigned* err = error_bits_dev;
   {
     std::lock_guard<std::mutex> lock(g_stage_mutex);
     for (int i = 0; i < npatch; ++i) {

@@ -354,12 +354,9 @@ cudaError_t ppm_attr(const void* fn) {
 template <class Pol>
 cudaError_t launch_ppm(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
                        unsigned* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = ppm_attr<Pol>(reinterpret_cast<const void*>(k_step_ppm<Pol, kPpmTX, kPpmTY>));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  cudaError_t ea = attr.call([&] { return ppm_attr<Pol>(reinterpret_cast<const void*>(k_step_ppm<Pol, kPpmTX, kPpmTY>)); });
+  if (ea != cudaSuccess) return ea;
   const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
   dim3 grid((P.nx + kPpmTX - 1) / kPpmTX, (P.ny + kPpmTY - 1) / kPpmTY, (P.nz + zchunk - 1) / zchunk);
   k_step_ppm<Pol, kPpmTX, kPpmTY><<<grid, kPpmTX * kPpmTY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
@@ -372,12 +369,9 @@ cudaError_t launch_ppm_batched(const HostPatchIO* d_patches, const HostTileRec* 
                                int sm_count, cudaStream_t s) {
   using K = decltype(&k_step_ppm_batched<Pol, kPpmTX, kPpmTY>);
   const K fn = &k_step_ppm_batched<Pol, kPpmTX, kPpmTY>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = ppm_attr<Pol>(reinterpret_cast<const void*>(fn));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  cudaError_t ea = attr.call([&] { return ppm_attr<Pol>(reinterpret_cast<const void*>(fn)); });
+  if (ea != cudaSuccess) return ea;
   const size_t smem = sizeof(PpmShared<typename Pol::R, kPpmTX, kPpmTY>);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPpmTX * kPpmTY, smem) != cudaSuccess || per_sm < 1)

@@ -43,11 +43,15 @@ def test_roofline_takes_the_roof_with_the_larger_fraction():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(80.0) and r["frac"] == pytest.approx(80.0 / 6681.8, abs=1e-4)
     assert r["traffic"] == 1.23e8
-    # double-float: the FP32 operations of the double-word algorithms against the FP32 peak
+    # double-float: the method's 375 flops per cell against the FP32 peak (0.1875 TFLOP/s, 0.0023)
+    # lose to HBM (40 GB/s, 0.006); the emulating FP32 operations are reported beside it
     r = bench.roofline("df64", 1e6, [2.0], 375.0, 6681.8, "measured", None)
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(40.0) and r["unit"] == "GB/s"
+    assert r["alu_frac"] == pytest.approx(0.1875 / bench.FP32_PEAK_TFLOPS, abs=1e-4)
+    assert r["algorithmic_flops_per_launch"] == 375e6
     tfl = 1e6 * bench.ALG_DF_FLOPS_PER_CELL["turb_minmod"] / 2e-3 / 1e12
-    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(tfl, abs=1e-3)
-    assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS, abs=0.01)
+    assert r["emulated_fp32_tflops"] == pytest.approx(tfl, abs=1e-3)
+    assert r["emulated_fp32_frac"] == pytest.approx(tfl / bench.FP32_PEAK_TFLOPS, abs=1e-4)
 
 
 def test_job_value_counts_every_rank_over_the_slowest():

@@ -44,10 +44,81 @@ def test_fp64_one_step_matches_oracle(precision, limiter, shape):
     for U in _inputs(limiter, shape):
         dt = oracle.cfl_periodic(U, dx, ocfg(limiter))
         o = oracle.step_periodic(U, dx, dt, ocfg(limiter))
-        for tile in range(3):
+        for tile in range(hy.NUM_TILES):
             hy.hydro_set_tuning(c, tile, 8)
             g, _ = step_periodic(c, U, dx, dt)
             assert normwise(g, o).max() <= TOL64, (tile, normwise(g, o))
+    check_clean(c)
+
+
+ALL = ["fp64", "df64", "mixed", "fp32"]
+
+
+@pytest.mark.parametrize("precision", ALL)
+@pytest.mark.parametrize("shape", [(12, 40, 70), (37, 21, 19)])
+def test_every_tile_shape_matches_oracle(precision, shape):
+    """Every compiled tile shape (16x16, 32x8, 8x8, 32x16, and 16x16 with one block per SM) in every
+    policy, on boxes that span several tiles with ragged tails in x and y and z chunks with a ragged
+    last chunk, against the oracle (FP32 from the state rounded to float); the fused dt of the result
+    is the same bits for every tile shape (a maximum, whatever the order of its atomic folds)."""
+    dx = 1.0 / shape[2]
+    U = workloads.turbulent_state(shape, seed=2, mach=5.0, sedov=True).numpy()
+    dt = oracle.cfl_periodic(U, dx, ocfg())
+    Uin = U.astype(np.float32).astype(np.float64) if precision == "fp32" else U
+    o = oracle.step_periodic(U, dx, dt, ocfg())
+    tol = TOL64 if precision in F64 else TOL32
+    c = ctx(precision)
+    dnext = set()
+    for tile in range(hy.NUM_TILES):
+        for zc in (8, 5):
+            hy.hydro_set_tuning(c, tile, zc)
+            g, dn = step_periodic(c, Uin, dx, dt, dt_next=True)
+            assert normwise(g, o).max() <= tol, (tile, zc, normwise(g, o))
+            dnext.add(dn)
+    assert len(dnext) == 1, dnext
+    with pytest.raises(hy.HydroError):
+        hy.hydro_set_tuning(c, hy.NUM_TILES, 8)
+    check_clean(c)
+
+
+@pytest.mark.parametrize("precision", ALL)
+def test_autotuned_step_matches_oracle(precision, tmp_path):
+    """hydro_autotune on a box and on a patch set, then the step at the tuning it chose, against the
+    oracle; a cache file written by the first call gives the same tuning to a second context."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    tol = TOL64 if precision in F64 else TOL32
+    shape = (24, 48, 72)
+    dx = 1.0 / shape[2]
+    U = workloads.turbulent_state(shape, seed=2, mach=5.0, sedov=True).numpy()
+    Uin = U.astype(np.float32).astype(np.float64) if precision == "fp32" else U
+    dt = oracle.cfl_periodic(U, dx, ocfg())
+    o = oracle.step_periodic(U, dx, dt, ocfg())
+    c = ctx(precision)
+    a = dev(Uin, dtype)
+    b = torch.empty_like(a)
+    cache = str(tmp_path / "tuning.txt")
+    hy.hydro_autotune(c, hy.patch(a, 0, dx), hy.patch(b, 0, dx), dts(dt), cache_path=cache)
+    tuned = hy.hydro_get_tuning(c)
+    assert 0 <= tuned[0] < hy.NUM_TILES and tuned[1] >= 1
+    g, _ = step_periodic(c, Uin, dx, dt)
+    assert normwise(g, o).max() <= tol, (tuned, normwise(g, o))
+    c2 = ctx(precision)
+    hy.hydro_set_tuning(c2, (tuned[0] + 1) % hy.NUM_TILES, 3)
+    hy.hydro_autotune(c2, hy.patch(a, 0, dx), hy.patch(b, 0, dx), dts(dt), cache_path=cache)
+    assert hy.hydro_get_tuning(c2) == tuned
+    # a patch set
+    host, ins, outs = _patch_batch(16, 9, precision, dtype, edges=(8, 16, 24, 40))
+    dt_list = [0.7 * oracle.cfl_patch(Ug, d["dx"], ocfg()) for Ug, d in host]
+    hy.hydro_autotune(c, ins, outs, dts(*dt_list))
+    for po in outs:
+        for t in po.tensors:
+            t.zero_()
+    hy.hydro_step(c, ins, outs, dts(*dt_list))
+    torch.cuda.synchronize()
+    for (Ug, d), po, dtp in zip(host, outs, dt_list):
+        out = torch.stack(po.tensors).double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
+        Ur = Ug.astype(np.float32).astype(np.float64) if precision == "fp32" else Ug
+        assert normwise(out, oracle.step_patch(Ur, d["dx"], dtp, ocfg())).max() <= tol, hy.hydro_get_tuning(c)
     check_clean(c)
 
 
@@ -136,13 +207,13 @@ def _patch_batch(npatch, seed, precision, dtype, edges=(4, 8, 12, 16, 24), max_l
 @pytest.mark.parametrize("precision", ["fp64", "df64", "mixed", "fp32"])
 def test_batched_patches_match_oracle(precision):
     dtype = torch.float32 if precision == "fp32" else torch.float64
-    host, ins, outs = _patch_batch(24, 5, precision, dtype)
+    host, ins, outs = _patch_batch(24, 5, precision, dtype, edges=(4, 8, 12, 16, 24, 40))
     c = ctx(precision)
     dt_list = [0.7 * oracle.cfl_patch(Ug, d["dx"], ocfg()) for Ug, d in host]
     dt = dts(*dt_list)
     dn = torch.empty(len(host), dtype=torch.float64, device="cuda")
-    for tile in (0, 2):
-        hy.hydro_set_tuning(c, tile, 8)
+    for tile in range(hy.NUM_TILES):
+        hy.hydro_set_tuning(c, tile, 8 if tile % 2 else 5)
         hy.hydro_step(c, ins, outs, dt, dn)
         torch.cuda.synchronize()
         tol = TOL64 if precision in F64 else TOL32

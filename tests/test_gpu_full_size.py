@@ -2,8 +2,9 @@
 outputs the oracle computes one by one: each sampled cell from its own 5^3 periodic neighbourhood
 (the step's stencil radius is 2), each sampled patch or oct group whole.
   - 512^3 Mach-5 turbulence + Sedov cell, MinMod (the headline workload): the CFL dt of the whole
-    box (oracle over every cell), one step in double-float, FP64 and FP32 with the bench's tile
-    (16x16, z chunk 128), and the fused dt of the result (oracle over every cell again);
+    box (oracle over every cell), one step in double-float, FP64, FP32 and mixed at the tuning the
+    autotuner picks for this box (as bench.py runs it), and in double-float at fixed tile shapes, and
+    the fused dt of the result (oracle over every cell again);
   - 1024^3 Mach-10 MC FP32 (the first step of the graph-captured run): the step on samples, the dt
     at the cell the GPU's dt comes from and a lower bound at every sampled cell;
   - the 4096-patch mixed-precision set in one persistent launch, per-patch dt, and 262144 oct groups;
@@ -32,9 +33,9 @@ def sample_cells(shape, count, seed):
     nz, ny, nx = shape
     rng = np.random.default_rng(seed)
     cells = [tuple(int(rng.integers(0, m)) for m in shape) for _ in range(count)]
-    for z in (0, 1, 127, 128, nz - 1):
+    for z in (0, 1, 31, 32, 63, 64, 127, 128, nz - 1):
         for y in (0, 15, 16, ny - 1):
-            for x in (0, 15, 16, nx - 1):
+            for x in (0, 15, 16, 31, 32, nx - 1):
                 cells.append((z % nz, y % ny, x % nx))
     return np.array(cells)
 
@@ -60,21 +61,28 @@ def fieldwise(got, want):
     return (np.abs(got - want) / scale).max(axis=0)
 
 
-@pytest.mark.parametrize("precision", ["df64", "fp64", "fp32"])
-def test_512_headline_step_sampled(precision):
+@pytest.mark.parametrize("precision,tuning", [("df64", "auto"), ("df64", (0, 128)), ("df64", (3, 128)),
+                                              ("df64", (4, 64)), ("fp64", "auto"), ("fp32", "auto"),
+                                              ("mixed", "auto")])
+def test_512_headline_step_sampled(precision, tuning):
+    """The headline step at the tuning bench.py runs it with (the autotuner's choice on this machine), and
+    at fixed tile shapes: 16x16, 32x16, and 16x16 with one block per SM."""
     n = 512
     dx = 1.0 / n
     cfg = oracle.config()
     c = ctx(precision)
-    hy.hydro_set_tuning(c, 0, 128)
     dtype = torch.float32 if precision == "fp32" else torch.float64
     U = workloads.turbulent_state(n, seed=2, mach=5.0, sedov=True, device="cuda").to(dtype).contiguous()
     d = torch.empty(2, dtype=torch.float64, device="cuda")
     hy.hydro_cfl_dt(c, hy.patch(U, 0, dx), d[0:1])
+    out = torch.empty_like(U)
+    if tuning == "auto":
+        hy.hydro_autotune(c, hy.patch(U, 0, dx), hy.patch(out, 0, dx), d[0:1])
+    else:
+        hy.hydro_set_tuning(c, *tuning)
     Uh = U.double().cpu().numpy()
     assert d[0].item() == pytest.approx(oracle.cfl_periodic(Uh, dx, cfg), rel=DT_TOL[precision])
     del Uh
-    out = torch.empty_like(U)
     hy.hydro_step(c, hy.patch(U, 0, dx), hy.patch(out, 0, dx), d[0:1], d[1:2])
     torch.cuda.synchronize()
     cells = sample_cells((n, n, n), 3000, seed=11)
