@@ -43,11 +43,12 @@ import torch  # noqa: E402
 # recomputes them): recovery 12 + slopes + predictor 56 + 3 x face (states + HLLC) + update 35.
 ALG_FLOPS_PER_CELL = {"turb_minmod": 375.0, "turb_mc": 402.0, "mach10_mc": 387.0}
 # The same step in double-float arithmetic (the df64 precision): each operation of the scheme
-# becomes FP32 operations of the double-word algorithms -- add/sub 20 (two TwoSums, two
-# Fast2Sums), mul 9 (TwoProd by FMA, two cross FMAs, Fast2Sum), div 35, sqrt 12 -- applied to the
-# oracle's count by kind on the same sample (+- 178.3, * 167.5, / 22.9, sqrt 6.0 per cell).
-DF_COST = {"addsub": 20, "mul": 9, "div": 35, "sqrt": 12}
-ALG_DF_FLOPS_PER_CELL = {"turb_minmod": 5940.0}
+# becomes FP32 operations of the double-word algorithms -- add/sub 11 (TwoSum of the high words,
+# the low words' sum, Fast2Sum), mul 8 (TwoProd by FMA, a cross product and FMA, Fast2Sum), div 23,
+# sqrt 12 -- applied to the oracle's count by kind on the same sample (+- 178.3, * 167.5, / 22.9,
+# sqrt 6.0 per cell).  Reported beside the roofline as the emulation's work, not the method's.
+DF_COST = {"addsub": 11, "mul": 8, "div": 23, "sqrt": 12}
+ALG_DF_FLOPS_PER_CELL = {"turb_minmod": 3900.0}
 BYTES_PER_CELL = {"fp64": 80.0, "fp32": 40.0, "mixed": 80.0, "df64": 80.0}  # 5 fields read + 5 written
 
 PRECISION_TEXT = {
@@ -308,9 +309,108 @@ def roofline(precision, cells, per_ms, flops_per_cell, hbm_gbs, peak_src, traffi
     return r
 
 
+# ----------------------------------------------------------------------------- parity samples
+# Every form, after its timed region, takes one more step (or adjoint step) and copies to the host
+# the inputs and GPU outputs of sampled cells, whole patches or oct groups.  No oracle code runs
+# here: the CPU oracle leg (cpu_oracle_leg, rank 0 only, after every timed region) computes the same
+# outputs in FP64 and attaches the normwise error per field to the form (err_vs_oracle).
+CHECKS = []
+
+
+def sample_cells(shape, count, seed):
+    """Random cells plus the box corners and both sides of 16- and 32-cell tile seams and of 32-,
+    64- and 128-plane z-chunk seams (z, y, x)."""
+    import numpy as np
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    cells = [tuple(int(rng.integers(0, m)) for m in shape) for _ in range(count)]
+    for z in (0, 31, 32, 63, 64, 127, 128, nz - 1):
+        for y in (0, 15, 16, ny - 1):
+            for x in (0, 31, 32, nx - 1):
+                cells.append((z % nz, y % ny, x % nx))
+    return np.array(sorted(set(cells)))
+
+
+def neighbourhoods(U, cells, r):
+    """(S, F, 2r+1, 2r+1, 2r+1) periodic neighbourhoods of the cells (z, y, x), gathered on U's device."""
+    F, NZ, NY, NX = U.shape
+    c = torch.as_tensor(cells, device=U.device, dtype=torch.long)
+    o = torch.arange(-r, r + 1, device=U.device)
+    iz = (c[:, 0, None] + o) % NZ
+    iy = (c[:, 1, None] + o) % NY
+    ix = (c[:, 2, None] + o) % NX
+    flat = (iz[:, :, None, None] * NY + iy[:, None, :, None]) * NX + ix[:, None, None, :]
+    return U.reshape(F, -1)[:, flat].permute(1, 0, 2, 3, 4).double().cpu().numpy()
+
+
+def record_cells(path, scheme, U_in, U_out, dx, dt, limiter, count=600, seed=0, note=None):
+    """Sampled cells of one periodic step U_in -> U_out (scheme plm, ppm or mhd)."""
+    r = 3 if scheme == "ppm" else 2
+    cells = sample_cells(tuple(U_in.shape[1:]), count, seed)
+    ci = torch.as_tensor(cells, device=U_out.device)
+    got = U_out[:, ci[:, 0], ci[:, 1], ci[:, 2]].double().cpu().numpy().T
+    CHECKS.append({"path": path, "scheme": scheme, "inputs": neighbourhoods(U_in, cells, r), "got": got, "dx": dx,
+                   "dt": [dt] * len(cells), "limiter": limiter, "what": "%d sampled cells" % len(cells), "note": note})
+
+
+def record_boxes(path, scheme, boxes, limiter, what):
+    """Whole ghosted boxes (patches, oct stencils): [(ghosted input, GPU interior output, dx, dt)]."""
+    CHECKS.append({"path": path, "scheme": scheme, "boxes": boxes, "limiter": limiter, "what": what})
+
+
+def oracle_errors(checks):
+    """The CPU oracle's outputs for every recorded sample and the normwise error per field of the
+    GPU's (max over samples of |gpu - oracle| / max over samples of |oracle|), by form."""
+    import numpy as np
+    import oracle
+    from oracle import mhd as omhd
+    from oracle import ppm as oppm
+    acc = {}
+    for c in checks:
+        cfg = oracle.config(limiter=c["limiter"] if c["limiter"] != "ppm" else "minmod")
+        step = {"plm": lambda g, dx, dt: oracle.step_patch(g, dx, dt, cfg),
+                "ppm": lambda g, dx, dt: oppm.step_patch(g, dx, dt, cfg),
+                "mhd": lambda g, dx, dt: omhd.step_patch(g, dx, dt, cfg, limiter=c["limiter"])}.get(c["scheme"])
+        if c["scheme"] == "adjoint":
+            w = oracle.step_periodic_adjoint(c["U"], c["lam_out"], c["dx"], c["dt"], cfg)
+            F = w.shape[0]
+            want, got = w.reshape(F, -1).T, c["got"].reshape(F, -1).T
+        elif "inputs" in c:
+            want = np.stack([step(g, c["dx"], dt).reshape(g.shape[0]) for g, dt in zip(c["inputs"], c["dt"])])
+            got = np.asarray(c["got"], dtype=np.float64)
+        else:
+            ws, gs = [], []
+            for Ug, out, dx, dt in c["boxes"]:
+                w = step(Ug, dx, dt)
+                ws.append(w.reshape(w.shape[0], -1).T)
+                gs.append(np.asarray(out, dtype=np.float64).reshape(w.shape[0], -1).T)
+            want, got = np.concatenate(ws), np.concatenate(gs)
+        a = acc.setdefault(tuple(c["path"]), {"want": [], "got": [], "what": c["what"], "note": c.get("note")})
+        a["want"].append(want)
+        a["got"].append(got)
+    res = {}
+    for path, a in acc.items():
+        want, got = np.concatenate(a["want"]), np.concatenate(a["got"])
+        scale = np.maximum(np.abs(want).max(axis=0), 1e-300)
+        per_field = (np.abs(got - want).max(axis=0) / scale).tolist()
+        e = {"max": float("%.3g" % max(per_field)), "per_field": [float("%.3g" % v) for v in per_field],
+             "samples": a["what"], "metric": "per field max|gpu - oracle| / max|oracle| over the samples (FP64 oracle)"}
+        if a["note"]:
+            e["note"] = a["note"]
+        res[path] = e
+    return res
+
+
 # ----------------------------------------------------------------------------- forms
+def record_step(hy, ctx, src, dst, dx, d, path, scheme, limiter, count=600):
+    """One more step src -> dst at the form's tuning (dt d: the fused CFL dt of src), sampled."""
+    hy.hydro_step(ctx, hy.patch(src, 0, dx), hy.patch(dst, 0, dx), d)
+    torch.cuda.synchronize()
+    record_cells(path, scheme, src, dst, dx, d.item(), limiter, count=count, seed=len(CHECKS) + 17)
+
+
 def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, sigma=1.0, p_over_rho=1e-4,
-                 sedov=True, seed=2, graph=False):
+                 sedov=True, seed=2, graph=False, path=None):
     stream = torch.cuda.current_stream()
     ctx = hy.hydro_init(precision=precision, limiter=limiter)
     a = turbulent(n, precision, "cuda", seed=seed, mach=mach, sigma=sigma, p_over_rho=p_over_rho, sedov=sedov)
@@ -336,13 +436,33 @@ def form_uniform(hy, n, precision, limiter, steps, warmup, flops_key, mach=5.0, 
         out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
                "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "graph": True, "error_bits": bits,
                "tuning": tuning}
+        if path:
+            # one more step from the GPU's own state after the timed steps, and the cells of that
+            # state whose internal energy is negative (their pressure is floored, HYDRO_EBIT_P_FLOOR)
+            neg = 0
+            for z in range(0, n, 64):
+                W = a[:, z:z + 64].double()
+                neg += int(((W[4] - 0.5 * (W[1] ** 2 + W[2] ** 2 + W[3] ** 2) / W[0]) < 0).sum().item())
+            del W
+            d = torch.empty(1, dtype=torch.float64, device="cuda")
+            hy.hydro_cfl_dt(ctx, pa, d)
+            hy.hydro_step(ctx, pa, pb, d)
+            torch.cuda.synchronize()
+            out["negative_internal_energy_cells_after_last_step"] = neg
+            record_cells(path, "plm", a, b, dx, d.item(), limiter, count=400, seed=31,
+                         note="one further step from the GPU's state after the %d timed steps; that state has "
+                              "%d cells (%.2g of all) with negative internal energy, floored by the scheme"
+                              % (steps, neg, neg / cells))
     else:
         dts = torch.empty(warmup + steps + 1, dtype=torch.float64, device="cuda")
         tuning = tune(hy, ctx, a, b, dx, dts)
         if limiter == "ppm":
             tuning["tile"] = "16x16"  # the PPM kernel's one tile shape; only the z chunk is tuned
-        ms, per, _, launches = time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream)
+        ms, per, final, launches = time_steps(hy, ctx, a, b, dx, dts, steps, warmup, stream)
         rc, bits = hy.hydro_get_error(ctx)
+        if path:
+            record_step(hy, ctx, final, b if final is a else a, dx, dts[warmup + steps:warmup + steps + 1], path,
+                        "ppm" if limiter == "ppm" else "plm", limiter)
         hbm, src = peaks()
         out = {"cells": cells, "steps": steps, "ms_per_step": ms / steps,
                "mcell_updates_per_s": cells * steps / (ms / 1e3) / 1e6, "error_bits": bits, "tuning": tuning}
@@ -396,6 +516,13 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     launches = (hy.hydro_launch_count(ctx) - l0) / steps
+    rng_s = np.random.default_rng(41)
+    big = sorted(range(n), key=lambda i: -descs[i]["nx"] * descs[i]["ny"] * descs[i]["nz"])[:2]
+    picks = sorted(set(big) | set(int(i) for i in rng_s.choice(n, 22, replace=False)))
+    dth = dt.cpu().numpy()
+    record_boxes(("mixed_batched",), "plm",
+                 [(keep[2 * i].cpu().numpy(), keep[2 * i + 1][:, 2:-2, 2:-2, 2:-2].cpu().numpy(), descs[i]["dx"],
+                   float(dth[i])) for i in picks], "minmod", "%d whole patches (the 2 largest among them)" % len(picks))
     # oct groups
     og = workloads.oct_origins(ngroups, parent.shape[1:], seed=3)
     g = workloads.gather_octs(parent, og).contiguous()
@@ -410,6 +537,14 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     t1.record(stream)
     torch.cuda.synchronize()
     ms_o = t0.elapsed_time(t1) / steps
+    sel = torch.as_tensor(np.sort(rng_s.choice(ngroups, 400, replace=False)), device="cuda")
+
+    def record_octs(key, stencils, outs, what):
+        record_boxes(("mixed_batched", key), "plm",
+                     [(st, o, 1.0 / 256, dto.item()) for st, o in zip(stencils, outs)], "minmod", what)
+
+    record_octs("octs", g[:, sel].permute(1, 0, 2, 3, 4).cpu().numpy(),
+                go[:, sel].permute(1, 0, 2, 3, 4).cpu().numpy(), "400 whole oct groups")
     # the same groups read in place from the level grid (no gathered copy), in Morton order of
     # their origins (the space-filling-curve order a tree code keeps its octs in)
     oa = np.asarray(og)
@@ -428,6 +563,8 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     t1.record(stream)
     torch.cuda.synchronize()
     ms_l = t0.elapsed_time(t1) / steps
+    st_l = workloads.gather_octs(parent, od[sel].cpu().numpy()).permute(1, 0, 2, 3, 4).cpu().numpy()
+    record_octs("octs_level", st_l, go[:, sel].permute(1, 0, 2, 3, 4).cpu().numpy(), "400 whole oct groups")
     # the level stored oct-major (128^3 octs) with its device-built Morton order and neighbour
     # table (the device chunk builder); the same groups, then every oct of the level in Morton
     # order, stepped through the table
@@ -459,6 +596,14 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
         t1.record(stream)
         torch.cuda.synchronize()
         timed[name] = t0.elapsed_time(t1) / steps
+        # the octs stepped (oct-major: cell (i, j, k) of oct o at o * 8 + (k * 2 + j) * 2 + i)
+        pick = sel if name == "groups" else torch.as_tensor(np.sort(rng_s.choice(no, 400, replace=False)),
+                                                             device="cuda")
+        octs_sel = lst[pick].long()
+        pos_s = pos[octs_sel]
+        st_t = workloads.gather_octs(parent, (2 * pos_s).cpu().numpy()).permute(1, 0, 2, 3, 4).cpu().numpy()
+        got_t = Vo[:, octs_sel].reshape(5, -1, 2, 2, 2).permute(1, 0, 2, 3, 4).cpu().numpy()
+        record_octs("octs_table" if name == "groups" else "octs_table_level", st_t, got_t, "400 whole octs")
     ms_t, ms_tl = timed["groups"], timed["level"]
     # coarse-to-fine ghost fill of the same patch set from a 128^3 coarse level (fine dx = 1/256)
     coarse = turbulent(128, "mixed", "cuda", seed=3, sedov=False)
@@ -559,6 +704,13 @@ def form_ppm_batched(hy, steps, warmup, npatch=4096, precision="mixed"):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     rc, bits = hy.hydro_get_error(ctx)
+    import numpy as np
+    rng_s = np.random.default_rng(43)
+    dth = dt.cpu().numpy()
+    picks = sorted(int(i) for i in rng_s.choice(len(ins), 8, replace=False))
+    record_boxes(("ppm_batched_mixed",), "ppm",
+                 [(keep[2 * i].double().cpu().numpy(), keep[2 * i + 1][:, 3:-3, 3:-3, 3:-3].double().cpu().numpy(),
+                   descs[i]["dx"], float(dth[i])) for i in picks], "ppm", "%d whole patches" % len(picks))
     hbm, src = peaks()
     es = 4 if precision == "fp32" else 8
     out = {"patches": len(ins), "interior_cells": interior, "ghosted_cells": ghosted, "ms_per_step": ms,
@@ -597,6 +749,10 @@ def form_mhd(hy, precision, steps, warmup, n=256):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     rc, bits = hy.hydro_get_error(ctx)
+    k = warmup + steps
+    hy.hydro_mhd_step(ctx, a, b, dx, dts[k:k + 1])
+    torch.cuda.synchronize()
+    record_cells(("mhd_256_" + precision,), "mhd", a, b, dx, dts[k].item(), "minmod", count=300, seed=51)
     hbm, src = peaks()
     es = 4 if precision == "fp32" else 8
     out = {"cells": n ** 3, "steps": steps, "ms_per_step": ms, "mcell_updates_per_s": n ** 3 / (ms / 1e3) / 1e6,
@@ -645,6 +801,25 @@ def form_mhd_patches(hy, precision, steps, warmup, npatch=512):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     rc, bits = hy.hydro_get_error(ctx)
+    # sampled cells of sampled patches: each cell's 5^3 neighbourhood inside its ghosted input
+    import numpy as np
+    rng_s = np.random.default_rng(53)
+    dth = dt.cpu().numpy()
+    nbs, got, dxs, dtl = [], [], [], []
+    for i in sorted(int(i) for i in rng_s.choice(len(ins), 12, replace=False)):
+        Ug, Vg = keep[2 * i], keep[2 * i + 1]
+        d = descs[i]
+        for _ in range(25):
+            x, y, z = (int(rng_s.integers(0, m)) for m in (d["nx"], d["ny"], d["nz"]))
+            nbs.append(Ug[:, z:z + 5, y:y + 5, x:x + 5].double().cpu().numpy())
+            got.append(Vg[:, z + 2, y + 2, x + 2].double().cpu().numpy())
+            dxs.append(d["dx"])
+            dtl.append(float(dth[i]))
+    for dxv in sorted(set(dxs)):  # one record per cell size (the oracle takes one dx per record)
+        idx = [j for j, v in enumerate(dxs) if v == dxv]
+        CHECKS.append({"path": ("mhd_patches_fp32",), "scheme": "mhd", "inputs": np.stack([nbs[j] for j in idx]),
+                       "got": np.stack([got[j] for j in idx]), "dx": dxv, "dt": [dtl[j] for j in idx],
+                       "limiter": "minmod", "what": "%d sampled cells of 12 patches" % len(nbs)})
     out = {"patches": len(ins), "interior_cells": interior, "ms_per_step": ms,
            "mcell_updates_per_s": interior / (ms / 1e3) / 1e6, "launches_per_step": 4, "error_bits": bits,
            "note": "MHD on the first 512 patches of the batched hydro form's patch set, two ghost layers"}
@@ -748,6 +923,13 @@ def form_amr_level(hy, steps, warmup, n=256, pieces=16, seed=15):
         torch.cuda.synchronize()
         parts += [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
     parts /= steps
+    rng_s = np.random.default_rng(47)
+    dth = dt.cpu().numpy()
+    picks = sorted(int(i) for i in rng_s.choice(len(ins), 10, replace=False))
+    record_boxes(("amr_level_mixed",), "plm",
+                 [(keep[2 * i].cpu().numpy(), keep[2 * i + 1][:, 2:-2, 2:-2, 2:-2].cpu().numpy(), 1.0 / n,
+                   float(dth[i])) for i in picks], "minmod",
+                 "the fine step of %d whole patches (ghosts prolonged and exchanged on the GPU)" % len(picks))
     ghosts = sum(t[0].numel() for t in keep[0::2]) - interior
     rc, bits = hy.hydro_get_error(ctx)
     t, z = hy.hydro_get_tuning(ctx)
@@ -794,6 +976,11 @@ def form_adjoint(hy, precision, n=64, nsteps=40):
     t2.record(stream)
     torch.cuda.synchronize()
     f_ms, a_ms = t0.elapsed_time(t1) / reps, t1.elapsed_time(t2) / reps
+    CHECKS.append({"path": ("adjoint_" + precision,), "scheme": "adjoint", "U": U.double().cpu().numpy(),
+                   "lam_out": L.double().cpu().numpy(), "got": M.double().cpu().numpy(), "dx": dx, "dt": dt.item(),
+                   "limiter": "minmod",
+                   "what": "one adjoint step of the whole %d^3 grid (the 40-step checkpointed gradient is "
+                           "compared with the oracle's chained adjoint in tests/test_gpu_adjoint.py)" % n})
     # 40-step run: forward only vs forward + checkpointed gradient
     W = workloads.turbulent_state(n, seed=4, mach=2.0, sedov=False, device="cuda")
     rho0 = (W[0]).to(dtype).requires_grad_(True)
@@ -852,6 +1039,28 @@ def cpu_baseline(n, seconds, steps_cap=1000):
                       "cell), %d FP64 steps incl. CFL dt, %.1f s" % (n, steps, el)}
 
 
+def cpu_oracle_leg(line, seconds):
+    """The leg of the run that executes the CPU oracle, after every timed region: its timed baseline
+    (cpu_baseline) and its outputs for the samples each form recorded, whose errors it attaches
+    (err_vs_oracle of the headline and of each form)."""
+    line["cpu_baseline"] = cpu_baseline(128, seconds)
+    try:
+        errs = oracle_errors(CHECKS)
+    except Exception as e:  # reported, not fatal
+        line["err_vs_oracle"] = {"error": repr(e)[:300]}
+        return
+    forms = line.get("forms", {})
+    for path, e in errs.items():
+        if path == ("headline",):
+            line["err_vs_oracle"] = e
+            continue
+        node = forms.get(path[0])
+        for k in path[1:]:
+            node = node.get(k) if isinstance(node, dict) else None
+        if isinstance(node, dict):
+            node["err_vs_oracle"] = e
+
+
 # ----------------------------------------------------------------------------- arms
 def reference_arm(args):
     rank, world, _ = dist_env()
@@ -894,19 +1103,21 @@ def reference_arm(args):
 def run_forms(hy, args, n, precision):
     """The extra forms beside the headline (each failure reported, not fatal)."""
     forms = [] if args.forms == "none" else (
-        ["fp64", "fp32", "ppm", "mhd", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all"
+        ["fp64", "fp32", "mixed", "ppm", "mhd", "batched", "amr", "adjoint", "graph1024"] if args.forms == "all"
         else args.forms.split(","))
     forms = [f for f in forms if f != precision]
     extra = {}
     for f in forms:
         try:
-            if f == "fp32":
-                extra["fp32_512"] = form_uniform(hy, n, "fp32", "minmod", args.steps, args.warmup, "turb_minmod")
+            if f in ("fp32", "mixed"):
+                extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod",
+                                                 path=(f + "_512",))
             elif f == "fp64_256":
                 extra["fp64_256"] = form_uniform(hy, 256, "fp64", "minmod", args.steps, args.warmup,
-                                                 "turb_minmod")
+                                                 "turb_minmod", path=("fp64_256",))
             elif f in ("fp64", "df64"):
-                extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod")
+                extra[f + "_512"] = form_uniform(hy, n, f, "minmod", args.steps, args.warmup, "turb_minmod",
+                                                 path=(f + "_512",))
             elif f == "batched":
                 extra["mixed_batched"] = form_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch,
                                                       ngroups=args.ngroups)
@@ -917,7 +1128,8 @@ def run_forms(hy, args, n, precision):
                 extra["amr_level_mixed"] = form_amr_level(hy, max(3, args.steps // 2), 2)
             elif f == "ppm":
                 for prec in ("df64", "fp32"):
-                    extra["ppm_%d_%s" % (n, prec)] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None)
+                    key = "ppm_%d_%s" % (n, prec)
+                    extra[key] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None, path=(key,))
                 extra["ppm_batched_mixed"] = form_ppm_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch)
             elif f == "mhd":
                 for prec in ("fp64", "df64", "fp32", "mixed"):
@@ -926,7 +1138,7 @@ def run_forms(hy, args, n, precision):
             elif f == "graph1024":
                 extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                            sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,
-                                                           graph=True)
+                                                           graph=True, path=("graph_1024_fp32_mc",))
         except Exception as e:  # a failing extra form is reported, not fatal
             extra[f] = {"error": repr(e)[:300]}
     return extra
@@ -972,6 +1184,9 @@ def main():
     rc, bits = hy.hydro_get_error(ctx)
     if rc != hy.HYDRO_OK:
         print("device error bits %#x" % bits, file=sys.stderr)
+    if rank == 0:  # one more step at the timed tuning, sampled for the CPU oracle leg
+        record_step(hy, ctx, final, b if final is a else a, dx, dts[args.warmup + args.steps:], ("headline",), "plm",
+                    "minmod", count=1000)
     t_max = job_time_ms(ms, world, "cuda")
     value = job_value(cells, args.steps, world, t_max)
     hbm, src = peaks()
@@ -1027,7 +1242,7 @@ def main():
         extra = run_forms(hy, args, n, precision)
         line["forms"] = extra
         if args.cpu_seconds > 0:
-            line["cpu_baseline"] = cpu_baseline(128, args.cpu_seconds)
+            cpu_oracle_leg(line, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -1,9 +1,16 @@
 // Double-float numbers: a value hi + lo held in two floats with |lo| <= ulp(hi)/2, about 48
 // significant bits, computed on the FP32 pipes (GB300 runs FP64 at 1/73 of its FP32 rate).
 // Built from the error-free transformations of Dekker (1971) and Knuth (TwoSum) and the
-// double-word algorithms analysed by Joldes, Muller & Popescu (ACM TOMS 2017):
-//   add  "accurate double-word + double-word"   relative error < 3u^2 + 13u^3   (u = 2^-24)
-//   mul  "double-word x double-word" with FMA   relative error < 5u^2
+// double-word algorithms analysed by Joldes, Muller & Popescu (ACM TOMS 2017), u = 2^-24:
+//   add  the "sloppy" double-word sum (TwoSum of the high words, the low words added in float,
+//        Fast2Sum): 11 operations, absolute error below about 3u^2 (|x| + |y|) -- as accurate as
+//        the "accurate" 20-operation sum except under cancellation, where its error is relative to
+//        the operands rather than to the result: the same backward-stable behaviour as a double
+//        add at 2^-48 in place of 2^-53.  add_acc is the accurate sum (relative error < 3u^2 +
+//        13u^3), kept for the pressure recovery E - |m|^2/(2 rho), where cancellation in cold,
+//        fast gas is the reason for extra precision;
+//   mul  double-word x double-word with FMA, the low-by-low product dropped: 8 operations,
+//        relative error below about 6u^2; mulf_ (double-word x float) 6 operations;
 //   rcp, div, sqrt: one Newton correction of an SFU approximation, relative error ~2^-45.
 // Comparisons are exact (lexicographic on (hi, lo) of normalised values).  The exponent range is
 // that of float: the hydro state here stays far inside it.
@@ -40,15 +47,19 @@ __device__ __forceinline__ df operator-(const df& x) { return df(-x.h, -x.l); }
 
 __device__ __forceinline__ df operator+(const df& x, const df& y) {
   const df s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, s.l + (x.l + y.l));
+}
+__device__ __forceinline__ df operator-(const df& x, const df& y) { return x + (-y); }
+__device__ __forceinline__ df add_acc(const df& x, const df& y) {
+  const df s = two_sum(x.h, y.h);
   const df t = two_sum(x.l, y.l);
   const df v = fast_two_sum(s.h, s.l + t.h);
   return fast_two_sum(v.h, v.l + t.l);
 }
-__device__ __forceinline__ df operator-(const df& x, const df& y) { return x + (-y); }
 
 __device__ __forceinline__ df operator*(const df& x, const df& y) {
   const df c = two_prod(x.h, y.h);
-  const float t = fmaf(x.l, y.h, fmaf(x.h, y.l, x.l * y.l));
+  const float t = fmaf(x.l, y.h, x.h * y.l);
   return fast_two_sum(c.h, c.l + t);
 }
 
@@ -74,7 +85,7 @@ __device__ __forceinline__ df div_(const df& x, const df& y) {
   float r0;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(y.h));
   const float q1 = x.h * r0;
-  const df r = x - y * df(q1, 0.f);  // remainder x - y q1
+  const df r = x - mulf_(y, q1);  // remainder x - y q1
   const float q2 = r.h * r0;
   return fast_two_sum(q1, q2);
 }

@@ -85,6 +85,12 @@ __device__ __forceinline__ R kc(const Params& P, int i) {
   return KC<R>::get(P, i);
 }
 
+// a - b where cancellation is the point (internal energy from total minus kinetic energy): the
+// plain difference in float and double, the accurate double-word sum in double-float.
+__device__ __forceinline__ float sub_acc(float a, float b) { return a - b; }
+__device__ __forceinline__ double sub_acc(double a, double b) { return a - b; }
+__device__ __forceinline__ df sub_acc(const df& a, const df& b) { return add_acc(a, -b); }
+
 // 0.5 x, 2 x and x f for a float constant f (exact scalings; df overloads in df.cuh).
 __device__ __forceinline__ float half_(float x) { return 0.5f * x; }
 __device__ __forceinline__ double half_(double x) { return 0.5 * x; }
@@ -500,7 +506,7 @@ struct PolDF {
     if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
     const df ir = rcp_(rho);
     const df kin = half_(((mx * mx + my * my) + mz * mz) * ir);
-    const df eint = E - kin;
+    const df eint = sub_acc(E, kin);
     if (cmp_neg(eint)) flags |= HYDRO_EBIT_P_FLOOR;
     df p = kc<df>(P, K_GM1) * eint;
     if (!(isfinite(p.h) && isfinite(rho.h))) flags |= HYDRO_EBIT_NONFINITE;

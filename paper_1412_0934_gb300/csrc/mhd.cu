@@ -73,7 +73,7 @@ __device__ __forceinline__ void mhd_recover(const R U[NV], const MhdConst<R>& c,
   const R ir = rcp_(rho);
   const R kin = half_((U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir);
   const R mag = half_(U[5] * U[5] + U[6] * U[6] + U[7] * U[7]);
-  const R eint = (U[4] - kin) - mag;
+  const R eint = sub_acc(sub_acc(U[4], kin), mag);
   if (cmp_neg(eint)) flags |= HYDRO_EBIT_P_FLOOR;
   if (!isfinite_(eint)) flags |= HYDRO_EBIT_NONFINITE;
   const R p = c.gm1 * eint;

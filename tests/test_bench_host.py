@@ -6,6 +6,7 @@ import math
 import pytest
 
 import bench
+import torch
 
 
 def sampler(lines):
@@ -93,3 +94,34 @@ def test_reference_arm_other_ranks_exit_quietly():
     rc, lines = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--gpus", "2"],
                            {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert rc == 0 and lines == []
+
+
+def test_oracle_leg_errors_and_attachment():
+    """The CPU oracle leg computes the oracle's outputs for recorded samples (sampled cells' 5^3
+    neighbourhoods, whole ghosted boxes) and attaches the normwise error per field to the headline and
+    to nested forms; a GPU output off by a relative 1e-9 reads as ~1e-9."""
+    import numpy as np
+    import oracle
+    import workloads
+    U = workloads.turbulent_state(12, seed=2, mach=5.0, sedov=True).numpy()
+    dx = 1.0 / 12
+    cfg = oracle.config()
+    dt = oracle.cfl_periodic(U, dx, cfg)
+    full = oracle.step_periodic(U, dx, dt, cfg)
+    cells = bench.sample_cells((12, 12, 12), 30, seed=1)
+    t = torch.as_tensor(U)
+    nbs = bench.neighbourhoods(t, cells, 2)
+    got = full[:, cells[:, 0], cells[:, 1], cells[:, 2]].T * (1 + 1e-9)
+    bench.CHECKS.clear()
+    bench.CHECKS.append({"path": ("headline",), "scheme": "plm", "inputs": nbs, "got": got, "dx": dx,
+                         "dt": [dt] * len(cells), "limiter": "minmod", "what": "cells"})
+    Ug = oracle.fill_ghosts_periodic(U)
+    bench.record_boxes(("batched", "octs"), "plm", [(Ug, full + 1e-7 * np.abs(full).max(axis=(1, 2, 3), keepdims=True), dx, dt)], "minmod", "box")
+    line = {"forms": {"batched": {"octs": {}}, "other": {}}}
+    bench.cpu_oracle_leg(line, 0.2)
+    e = line["err_vs_oracle"]
+    assert 0.5e-9 <= e["max"] <= 2e-9 and len(e["per_field"]) == 5
+    assert line["forms"]["batched"]["octs"]["err_vs_oracle"]["max"] == pytest.approx(1e-7, rel=1e-3)
+    assert "err_vs_oracle" not in line["forms"]["other"]
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    bench.CHECKS.clear()
