@@ -318,12 +318,17 @@ CHECKS = []
 
 
 def sample_cells(shape, count, seed):
-    """Random cells plus the box corners and both sides of 16- and 32-cell tile seams and of 32-,
-    64- and 128-plane z-chunk seams (z, y, x)."""
+    """Random cells plus the box corners, both sides of 16- and 32-cell tile seams and of 32-, 64- and
+    128-plane z-chunk seams, and the 7^3 block around the box centre (the Sedov cell of the
+    turbulence boxes: where the step changes the state most, its time step set by the blast) (z, y, x)."""
     import numpy as np
     nz, ny, nx = shape
     rng = np.random.default_rng(seed)
     cells = [tuple(int(rng.integers(0, m)) for m in shape) for _ in range(count)]
+    for dz in range(-3, 4):
+        for dy in range(-3, 4):
+            for dx in range(-3, 4):
+                cells.append(((nz // 2 + dz) % nz, (ny // 2 + dy) % ny, (nx // 2 + dx) % nx))
     for z in (0, 31, 32, 63, 64, 127, 128, nz - 1):
         for y in (0, 15, 16, ny - 1):
             for x in (0, 31, 32, nx - 1):

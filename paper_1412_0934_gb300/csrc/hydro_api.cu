@@ -447,7 +447,7 @@ int hydro_step(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out, int 
   if (ppm(c))
     return cuda_status(c->ops->step_ppm_batched(c->d_patches, c->d_tiles, c->ntiles, c->d_counter, c->prm, dt_dev,
                                                 dt_next_dev, c->zchunk, c->d_err, c->sm_count, c->stream));
-  const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id);
+  const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id, c->cfg.limiter);
   int grid = std::max(1, std::min(c->ntiles, c->sm_count * per_sm));
   return cuda_status(c->ops->step_batched(c->tile_id, c->d_patches, c->d_tiles, c->ntiles, c->d_counter, c->prm,
                                           dt_dev, dt_next_dev, c->zchunk, c->d_err, grid, c->stream));
@@ -582,7 +582,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
     rc = reset_slots(c, dt_next_dev, 1, c->stream);
     if (rc) return rc;
   }
-  const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id);
+  const int per_sm = c->ops->batched_blocks_per_sm(c->tile_id, c->cfg.limiter);
   const int grid = std::max(1, std::min(tps, c->sm_count * per_sm));
   // slabs alternate between two compute streams, so that a slab's last partial wave of tiles runs
   // beside the next slab's first (the slabs write disjoint planes; dt_next is an order-free min)

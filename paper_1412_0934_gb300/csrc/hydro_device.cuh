@@ -155,6 +155,20 @@ __device__ __forceinline__ R limited(R a, R b, int lim) {
   return best;
 }
 
+// MinMod alone (the same values as limited(a, b, HYDRO_MINMOD)), for kernels that fix the limiter at
+// compile time.  Double-float: once the signs agree, |a| <= |b| is a <= b for positive values and
+// b <= a for negative ones (one lexicographic comparison instead of two absolute values).
+template <class R>
+__device__ __forceinline__ R minmod(R a, R b) {
+  if (prod_nonpos(a, b)) return R(0);
+  return abs_le(a, b) ? a : b;
+}
+__device__ __forceinline__ df minmod(const df& a, const df& b) {
+  if (prod_nonpos(a, b)) return df(0.f, 0.f);
+  const bool le = a.h > 0.f ? !(b < a) : !(a < b);
+  return le ? a : b;
+}
+
 // ------------------------------------------------------------------ Hancock predictor
 // qh = q - hdt * (A_x dqx + A_y dqy + A_z dqz), A_d the primitive Jacobian of direction d.
 template <class R>
@@ -321,9 +335,9 @@ __device__ __forceinline__ float small_uint_to_float(unsigned n) {
 // outside [2^-74, 2^99) take the conversion instructions instead.
 // The rare cases out of line, so that the common path carries no conversion instruction (an
 // inlined branch this short would be predicated, and its conversions issued for every value).
-static __device__ __noinline__ void split_double_cvt(double x, float& hi, float& lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
+static __device__ __noinline__ float2 split_double_cvt(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
 }
 static __device__ __noinline__ double float_to_double_cvt(float f) { return (double)f; }
 
@@ -331,7 +345,9 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
   const unsigned ex = (xh >> 20) & 0x7FFu;  // biased exponent, E = ex - 1023
   if (__builtin_expect(ex - 949u >= 173u, 0)) {
-    split_double_cvt(x, hi, lo);
+    const float2 c = split_double_cvt(x);  // returned in registers: no stack frame on the common path
+    hi = c.x;
+    lo = c.y;
     return;
   }
   const unsigned sign = xh & 0x80000000u;

@@ -72,8 +72,8 @@ struct KernelOps {
   cudaError_t (*step_batched)(int tile, const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles,
                               int* d_counter, const Params& prm, const double* dt, double* dt_next, int zchunk,
                               unsigned* err, int grid, cudaStream_t s);
-  // Occupancy (blocks per SM) of the batched kernel for a tile shape.
-  int (*batched_blocks_per_sm)(int tile);
+  // Occupancy (blocks per SM) of the batched kernel for a tile shape and limiter.
+  int (*batched_blocks_per_sm)(int tile, int limiter);
   // CFL dt per patch: d_patches (device) or a single patch by value when d_patches == nullptr.
   cudaError_t (*cfl)(const HostPatchIO* d_patches, const HostPatchIO& single, int npatch, const Params& prm,
                      double* dt_out, unsigned* err, cudaStream_t s);

@@ -12,58 +12,69 @@
 namespace hydro {
 
 // ------------------------------------------------------------------ step launchers
-template <class Pol, int TX, int TY, int MINB>
+// The step kernels are compiled for MinMod (LIM = HYDRO_MINMOD, the limiter fixed at compile time)
+// and for the limiter read from the parameters at run time (LIM = -1: MC, none).
+constexpr int kLimRuntime = -1;
+
+template <class Pol, int TX, int TY, int MINB, int LIM>
 cudaError_t launch_uniform_t(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
                              unsigned* err, cudaStream_t s) {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
   static PerDeviceOnce attr;
   cudaError_t e = attr.call([&] {
-    return cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step_uniform<Pol, TX, TY, MINB, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
   });
   if (e != cudaSuccess) return e;
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + zchunk - 1) / zchunk);
-  k_step_uniform<Pol, TX, TY, MINB><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
+  k_step_uniform<Pol, TX, TY, MINB, LIM><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(P), prm, dt, dt_next, zchunk, err);
   return cudaGetLastError();
 }
 
-template <class Pol, int TX, int TY, int MINB>
+template <class Pol, int TX, int TY, int MINB, int LIM>
 cudaError_t launch_batched_t(const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles, int* d_counter,
                              const Params& prm, const double* dt, double* dt_next, int zchunk, unsigned* err, int grid,
                              cudaStream_t s) {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
   static PerDeviceOnce attr;
   cudaError_t e = attr.call([&] {
-    return cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
   });
   if (e != cudaSuccess) return e;
-  k_step_batched<Pol, TX, TY, MINB><<<grid, TX * TY, smem, s>>>(
+  k_step_batched<Pol, TX, TY, MINB, LIM><<<grid, TX * TY, smem, s>>>(
       reinterpret_cast<const PatchIO<typename Pol::S>*>(d_patches), reinterpret_cast<const TileRec*>(d_tiles), ntiles,
       d_counter, prm, dt, dt_next, zchunk, err);
   return cudaGetLastError();
 }
 
-template <class Pol, int TX, int TY, int MINB>
+template <class Pol, int TX, int TY, int MINB, int LIM>
 int blocks_per_sm_t() {
   const size_t smem = sizeof(TileShared<Pol, TX, TY>);
-  cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_step_batched<Pol, TX, TY, MINB, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<Pol, TX, TY, MINB>, TX * TY, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_batched<Pol, TX, TY, MINB, LIM>, TX * TY, smem) !=
+      cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
+// Tile id -> compiled shape, and the limiter -> compiled variant.
+#define HYDRO_TILE_SWITCH(tile, lim, CALL)                                      \
+  switch (tile) {                                                               \
+    case 0: return lim == HYDRO_MINMOD ? CALL(0, HYDRO_MINMOD) : CALL(0, kLimRuntime); \
+    case 1: return lim == HYDRO_MINMOD ? CALL(1, HYDRO_MINMOD) : CALL(1, kLimRuntime); \
+    case 2: return lim == HYDRO_MINMOD ? CALL(2, HYDRO_MINMOD) : CALL(2, kLimRuntime); \
+    case 3: return lim == HYDRO_MINMOD ? CALL(3, HYDRO_MINMOD) : CALL(3, kLimRuntime); \
+    case 4: return lim == HYDRO_MINMOD ? CALL(4, HYDRO_MINMOD) : CALL(4, kLimRuntime); \
+  }
+
 template <class Pol>
 cudaError_t launch_uniform(int tile, const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next,
                            int zchunk, unsigned* err, cudaStream_t s) {
-  switch (tile) {
-    case 0: return launch_uniform_t<Pol, kTileX[0], kTileY[0], kTileMinBlocks[0]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 1: return launch_uniform_t<Pol, kTileX[1], kTileY[1], kTileMinBlocks[1]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 2: return launch_uniform_t<Pol, kTileX[2], kTileY[2], kTileMinBlocks[2]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 3: return launch_uniform_t<Pol, kTileX[3], kTileY[3], kTileMinBlocks[3]>(P, prm, dt, dt_next, zchunk, err, s);
-    case 4: return launch_uniform_t<Pol, kTileX[4], kTileY[4], kTileMinBlocks[4]>(P, prm, dt, dt_next, zchunk, err, s);
-  }
+#define HYDRO_CALL(T, L) launch_uniform_t<Pol, kTileX[T], kTileY[T], kTileMinBlocks[T], L>(P, prm, dt, dt_next, zchunk, err, s)
+  HYDRO_TILE_SWITCH(tile, prm.limiter, HYDRO_CALL)
+#undef HYDRO_CALL
   return cudaErrorInvalidValue;
 }
 
@@ -71,27 +82,22 @@ template <class Pol>
 cudaError_t launch_batched(int tile, const HostPatchIO* d_patches, const HostTileRec* d_tiles, int ntiles,
                            int* d_counter, const Params& prm, const double* dt, double* dt_next, int zchunk,
                            unsigned* err, int grid, cudaStream_t s) {
-  switch (tile) {
-    case 0: return launch_batched_t<Pol, kTileX[0], kTileY[0], kTileMinBlocks[0]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 1: return launch_batched_t<Pol, kTileX[1], kTileY[1], kTileMinBlocks[1]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 2: return launch_batched_t<Pol, kTileX[2], kTileY[2], kTileMinBlocks[2]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 3: return launch_batched_t<Pol, kTileX[3], kTileY[3], kTileMinBlocks[3]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-    case 4: return launch_batched_t<Pol, kTileX[4], kTileY[4], kTileMinBlocks[4]>(d_patches, d_tiles, ntiles, d_counter, prm, dt, dt_next, zchunk, err, grid, s);
-  }
+#define HYDRO_CALL(T, L)                                                                                          \
+  launch_batched_t<Pol, kTileX[T], kTileY[T], kTileMinBlocks[T], L>(d_patches, d_tiles, ntiles, d_counter, prm, dt, \
+                                                                    dt_next, zchunk, err, grid, s)
+  HYDRO_TILE_SWITCH(tile, prm.limiter, HYDRO_CALL)
+#undef HYDRO_CALL
   return cudaErrorInvalidValue;
 }
 
 template <class Pol>
-int batched_blocks_per_sm(int tile) {
-  switch (tile) {
-    case 0: return blocks_per_sm_t<Pol, kTileX[0], kTileY[0], kTileMinBlocks[0]>();
-    case 1: return blocks_per_sm_t<Pol, kTileX[1], kTileY[1], kTileMinBlocks[1]>();
-    case 2: return blocks_per_sm_t<Pol, kTileX[2], kTileY[2], kTileMinBlocks[2]>();
-    case 3: return blocks_per_sm_t<Pol, kTileX[3], kTileY[3], kTileMinBlocks[3]>();
-    case 4: return blocks_per_sm_t<Pol, kTileX[4], kTileY[4], kTileMinBlocks[4]>();
-  }
+int batched_blocks_per_sm(int tile, int limiter) {
+#define HYDRO_CALL(T, L) blocks_per_sm_t<Pol, kTileX[T], kTileY[T], kTileMinBlocks[T], L>()
+  HYDRO_TILE_SWITCH(tile, limiter, HYDRO_CALL)
+#undef HYDRO_CALL
   return 1;
 }
+#undef HYDRO_TILE_SWITCH
 
 // ------------------------------------------------------------------ CFL dt (standalone)
 // blockIdx.y walks the patches, blockIdx.x the interior cells of one patch.  The per-block

@@ -138,7 +138,7 @@ extern "C" int hydro_step_batched_noalloc(const hydro_config* cfg, const hydro_p
   if (cudaMemsetAsync(s->counter, 0, sizeof(int), st) != cudaSuccess) return HYDRO_ERR_CUDA;
   if (dt_next_dev && cudaMemsetAsync(dt_next_dev, 0xFF, (size_t)npatch * sizeof(double), st) != cudaSuccess)
     return HYDRO_ERR_CUDA;
-  const int per_sm = ops.batched_blocks_per_sm(tile);
+  const int per_sm = ops.batched_blocks_per_sm(tile, cfg->limiter);
   long long grid = (long long)sms * per_sm;
   if (grid > total) grid = total;
   if (grid < 1) grid = 1;

@@ -109,7 +109,16 @@ __device__ __forceinline__ int wrapi(int x, int n) {
 }
 __device__ __forceinline__ int ring_slot(int p) { return (p + 3) % 3; }
 
-template <class Pol, int TX, int TY>
+// Limited slope of a cell from its backward and forward differences.  LIM == HYDRO_MINMOD fixes the
+// limiter at compile time (the step kernels are compiled for MinMod and for a limiter read at run
+// time, prm.limiter: MC or none); minmod() is the same function as limited(., ., HYDRO_MINMOD).
+template <int LIM, class R>
+__device__ __forceinline__ R limited_t(R a, R b, int lim) {
+  if constexpr (LIM == HYDRO_MINMOD) return minmod(a, b);
+  else return limited(a, b, lim);
+}
+
+template <int LIM, class Pol, int TX, int TY>
 __device__ __forceinline__ void predict_cell(TileShared<Pol, TX, TY>& sm, int i, int j, int sm1, int s0, int sp1,
                                              const Params& prm, typename Pol::R hdt, typename Pol::R qh[5],
                                              typename Pol::R dqz[5]) {
@@ -125,9 +134,9 @@ __device__ __forceinline__ void predict_cell(TileShared<Pol, TX, TY>& sm, int i,
   sm.q[sp1].ld(cj, ci, zp);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    dqx[v] = limited(c[v] - xm[v], xp[v] - c[v], prm.limiter);
-    dqy[v] = limited(c[v] - ym[v], yp[v] - c[v], prm.limiter);
-    dqz[v] = limited(c[v] - zm[v], zp[v] - c[v], prm.limiter);
+    dqx[v] = limited_t<LIM>(c[v] - xm[v], xp[v] - c[v], prm.limiter);
+    dqy[v] = limited_t<LIM>(c[v] - ym[v], yp[v] - c[v], prm.limiter);
+    dqz[v] = limited_t<LIM>(c[v] - zm[v], zp[v] - c[v], prm.limiter);
   }
   hancock(c, dqx, dqy, dqz, kc<R>(prm, K_GAMMA), hdt, qh);
   sm.qh.st(j + 1, i + 1, qh);
@@ -187,7 +196,7 @@ __device__ __forceinline__ void face_flux_dyn(TileShared<Pol, TX, TY>& sm, int d
 }
 
 // Advances the tile; returns (through smax) the largest CFL speed of the updated cells.
-template <class Pol, int TX, int TY>
+template <int LIM, class Pol, int TX, int TY>
 __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Pol::S>& P, int x0, int y0, int z0,
                           int z1, const Params& prm, double dt, bool want_cfl, unsigned& flags,
                           typename Pol::R& smax) {
@@ -350,7 +359,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
           ring_cell(tid - (NT - NR), ci, cj);
         }
         R qh[5], dqz[5];
-        predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
+        predict_cell<LIM>(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
         if (it == 0) {
           z_faces(p, qh, dqz);
           if (upd) update(p - 1);
@@ -359,7 +368,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     } else {
       {
         R qh[5], dqz[5];
-        predict_cell(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
+        predict_cell<LIM>(sm, ti, tj, sm1, s0, sp1, prm, hdt, qh, dqz);
         z_faces(p, qh, dqz);
       }
       if (upd) update(p - 1);
@@ -367,7 +376,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
         int ci, cj;
         ring_cell(tid - (NT - NR), ci, cj);
         R qh[5], dqz[5];
-        predict_cell(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
+        predict_cell<LIM>(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
       }
     }
 #pragma unroll
@@ -455,7 +464,7 @@ constexpr int min_blocks() {
 }
 
 // Uniform grid: one tile per block, tiles from the block index.
-template <class Pol, int TX, int TY, int MINB>
+template <class Pol, int TX, int TY, int MINB, int LIM>
 __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
                                                          double* dt_next, int zchunk, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -469,7 +478,7 @@ __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_
   const int z1 = min(z0 + zchunk, P.nz);
   unsigned flags = 0;
   typename Pol::R smax = 0;
-  step_tile(sm, P, x0, y0, z0, z1, prm, dt, dt_next != nullptr, flags, smax);
+  step_tile<LIM>(sm, P, x0, y0, z0, z1, prm, dt, dt_next != nullptr, flags, smax);
   if (dt_next) {
     const auto m = block_max(sm, smax);
     if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next);
@@ -478,7 +487,7 @@ __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_
 }
 
 // Batched patches: a persistent grid pulls tiles from the work-list through an atomic counter.
-template <class Pol, int TX, int TY, int MINB>
+template <class Pol, int TX, int TY, int MINB, int LIM>
 __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_step_batched(const PatchIO<typename Pol::S>* patches, const TileRec* tiles,
                                                          int ntiles, int* counter, Params prm, const double* dt_dev,
                                                          double* dt_next, int zchunk, unsigned* err) {
@@ -504,7 +513,7 @@ __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_
     }
     const int z1 = min(r.z0 + zchunk, P.nz);
     typename Pol::R smax = 0;
-    step_tile(sm, P, r.x0, r.y0, r.z0, z1, prm, dt, dt_next != nullptr, flags, smax);
+    step_tile<LIM>(sm, P, r.x0, r.y0, r.z0, z1, prm, dt, dt_next != nullptr, flags, smax);
     if (dt_next) {
       const auto m = block_max(sm, smax);
       if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next + r.patch);

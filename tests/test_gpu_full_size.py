@@ -29,10 +29,16 @@ DT_TOL = {"fp64": 1e-13, "df64": 1e-12, "fp32": 1e-6, "mixed": 1e-6}
 
 
 def sample_cells(shape, count, seed):
-    """Random cells plus the box's corners and cells on both sides of tile and z-chunk seams."""
+    """Random cells plus the box's corners, cells on both sides of tile and z-chunk seams, and the 7^3
+    block around the box centre: the Sedov cell of the turbulence boxes, whose blast sets the time
+    step, so that elsewhere one step changes the state by little and the error there says little."""
     nz, ny, nx = shape
     rng = np.random.default_rng(seed)
     cells = [tuple(int(rng.integers(0, m)) for m in shape) for _ in range(count)]
+    for dz in range(-3, 4):
+        for dy in range(-3, 4):
+            for dx in range(-3, 4):
+                cells.append(((nz // 2 + dz) % nz, (ny // 2 + dy) % ny, (nx // 2 + dx) % nx))
     for z in (0, 1, 31, 32, 63, 64, 127, 128, nz - 1):
         for y in (0, 15, 16, ny - 1):
             for x in (0, 15, 16, 31, 32, nx - 1):
