@@ -51,7 +51,7 @@ struct AdjScratch {
   unsigned* code;  // [N] limiter branch codes, 2 bits per (d, v)
 };
 
-template <class Pol, int TX, int TY>
+template <class Pol, int TX, int TY, int LIM>
 __device__ __forceinline__ void adj_predict(AdjShared<typename Pol::R, TX, TY>& sm, int i, int j, int sq0, int sq1,
                                             int sq2, int sp, bool interior, const Params& prm, typename Pol::R hdt,
                                             unsigned& code) {
@@ -64,9 +64,9 @@ __device__ __forceinline__ void adj_predict(AdjShared<typename Pol::R, TX, TY>& 
     const R c = sm.q[sq1][v][cj][ci];
     unsigned cx, cy, cz;
     q0[v] = c;
-    dqx[v] = limited_code(c - sm.q[sq1][v][cj][ci - 1], sm.q[sq1][v][cj][ci + 1] - c, prm.limiter, cx);
-    dqy[v] = limited_code(c - sm.q[sq1][v][cj - 1][ci], sm.q[sq1][v][cj + 1][ci] - c, prm.limiter, cy);
-    dqz[v] = limited_code(c - sm.q[sq0][v][cj][ci], sm.q[sq2][v][cj][ci] - c, prm.limiter, cz);
+    dqx[v] = limited_code(c - sm.q[sq1][v][cj][ci - 1], sm.q[sq1][v][cj][ci + 1] - c, LIM, cx);
+    dqy[v] = limited_code(c - sm.q[sq1][v][cj - 1][ci], sm.q[sq1][v][cj + 1][ci] - c, LIM, cy);
+    dqz[v] = limited_code(c - sm.q[sq0][v][cj][ci], sm.q[sq2][v][cj][ci] - c, LIM, cz);
     code |= (cx << (2 * v)) | (cy << (2 * (5 + v))) | (cz << (2 * (10 + v)));
   }
   hancock(q0, dqx, dqy, dqz, kc<R>(prm, K_GAMMA), hdt, qh);
@@ -108,7 +108,8 @@ __device__ __forceinline__ void adj_face_xy(AdjShared<typename Pol::R, TX, TY>& 
   floor_mask(pR, lR, rf, pf);
 }
 
-template <class Pol, int TX, int TY>
+// LIM: the PLM limiter, fixed at compile time (one kernel per limiter; prm.limiter is the same value).
+template <class Pol, int TX, int TY, int LIM>
 __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P, PatchIO<typename Pol::S> L,
                                                       Params prm, const double* dt_dev, int zchunk,
                                                       AdjScratch<typename Pol::R> scr, unsigned* err) {
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
   auto predict = [&](int z, unsigned& code_interior) {
     const int sp = (z + 2) & 1;
     const int s0 = ring_slot(z - 1), s1 = ring_slot(z), s2 = ring_slot(z + 1);
-    adj_predict<Pol, TX, TY>(sm, ti, tj, s0, s1, s2, sp, true, prm, hdt, code_interior);
+    adj_predict<Pol, TX, TY, LIM>(sm, ti, tj, s0, s1, s2, sp, true, prm, hdt, code_interior);
     if (tid < 2 * (TX + TY)) {
       int ri, rj;
       const int r = tid;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
       else if (r < 2 * TX + TY) { ri = -1; rj = r - 2 * TX; }
       else { ri = TX; rj = r - 2 * TX - TY; }
       unsigned dummy;
-      adj_predict<Pol, TX, TY>(sm, ri, rj, s0, s1, s2, sp, false, prm, hdt, dummy);
+      adj_predict<Pol, TX, TY, LIM>(sm, ri, rj, s0, s1, s2, sp, false, prm, hdt, dummy);
     }
   };
 
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(TX* TY) k_adj_faces(PatchIO<typename Pol::S> P
 
 // Per cell: lam_n = lam_np1 + recover^T(lq_pred + slope gathers).  One thread per cell of a
 // 32 x 8 x 1 block over (x, y, z): indices from the grid, periodic neighbours by one compare each.
-template <class Pol>
+template <class Pol, int LIM>
 __global__ void __launch_bounds__(256) k_adj_cells(PatchIO<typename Pol::S> P, PatchIO<typename Pol::S> L,
                                                    Params prm, AdjScratch<typename Pol::R> scr,
                                                    typename Pol::S* o0, typename Pol::S* o1, typename Pol::S* o2,
@@ -304,9 +305,9 @@ __global__ void __launch_bounds__(256) k_adj_cells(PatchIO<typename Pol::S> P, P
     for (int v = 0; v < 5; ++v) {
       const int sh = 2 * (5 * d + v);
       float a0, b0, am, bm, ap, bp;
-      code_weights((cc >> sh) & 3u, prm.limiter, a0, b0);
-      code_weights((cm >> sh) & 3u, prm.limiter, am, bm);
-      code_weights((cp >> sh) & 3u, prm.limiter, ap, bp);
+      code_weights((cc >> sh) & 3u, LIM, a0, b0);
+      code_weights((cm >> sh) & 3u, LIM, am, bm);
+      code_weights((cp >> sh) & 3u, LIM, ap, bp);
       const R* ld = scr.ld + (long long)(5 * d + v) * N;
       lq[v] += (mulf_(ld[c], a0 - b0) + mulf_(ld[nb[d][0]], bm)) - mulf_(ld[nb[d][1]], ap);
     }
@@ -343,14 +344,11 @@ size_t adjoint_scratch_bytes(int nx, int ny, int nz) {
   return N * 20 * sizeof(typename Pol::R) + N * sizeof(unsigned) + 256;
 }
 
-template <class Pol>
-cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* const lam_out[5], const Params& prm,
-                           const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s) {
+template <class Pol, int LIM>
+cudaError_t launch_adjoint_t(const HostPatchIO& U, const HostPatchIO& lam, void* const lam_out[5], const Params& prm,
+                             const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s) {
   using R = typename Pol::R;
   using S = typename Pol::S;
-  if constexpr (std::is_same<Pol, PolMixed>::value || std::is_same<Pol, PolDF>::value) {
-    return cudaErrorNotSupported;  // the adjoint kernels are FP64 and FP32 (double-float uses FP64's)
-  } else {
   constexpr int TX = AdjTile<Pol>::TX, TY = AdjTile<Pol>::TY;
   if (scratch_bytes < adjoint_scratch_bytes<Pol>(U.nx, U.ny, U.nz)) return cudaErrorInvalidValue;
   const size_t N = (size_t)U.nx * U.ny * U.nz;
@@ -361,16 +359,17 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
   const size_t smem = sizeof(AdjShared<R, TX, TY>);
   static PerDeviceOnce attr;
   cudaError_t ea = attr.call([&] {
-    return cudaFuncSetAttribute(k_adj_faces<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_adj_faces<Pol, TX, TY, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (ea != cudaSuccess) return ea;
   // z chunk: FP32 takes the longest of 16, 8, 4, 2 planes whose grid still fills half of the SMs'
   // resident blocks (a small grid leaves SMs idle, a short march repeats halo planes; half is the
-  // measured balance).  FP64 keeps 16: it is bound by the FP64 pipe, which a few warps per SM
-  // already keep busy.
+  // measured balance).  FP64 takes the longest of 16, 8, 4 whose grid fills every resident slot:
+  // its FP64 pipe needs the warps to cover the latency of its dependent double operations.
   static int resident = 0;
   if (!resident) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adj_faces<Pol, TX, TY>, TX * TY, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adj_faces<Pol, TX, TY, LIM>, TX * TY,
+                                                                  smem);
     if (e != cudaSuccess) return e;
     if (resident < 1) resident = 1;
   }
@@ -379,19 +378,35 @@ cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* c
     return cudaErrorUnknown;
   const long long cols = (long long)((U.nx + TX - 1) / TX) * ((U.ny + TY - 1) / TY);
   int zc = 16;
-  while (!std::is_same<R, double>::value && zc > 2 && 2 * cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms)
-    zc /= 2;
+  if (std::is_same<R, double>::value) {
+    while (zc > 4 && cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms) zc /= 2;
+  } else {
+    while (zc > 2 && 2 * cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms) zc /= 2;
+  }
   if (zc > U.nz) zc = U.nz;
   dim3 grid((U.nx + TX - 1) / TX, (U.ny + TY - 1) / TY, (U.nz + zc - 1) / zc);
-  k_adj_faces<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, dt, zc, scr,
-                                                        err);
+  k_adj_faces<Pol, TX, TY, LIM><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, dt, zc, scr, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 cgrid((U.nx + 31) / 32, (U.ny + 7) / 8, U.nz);
-  k_adj_cells<Pol><<<cgrid, dim3(32, 8), 0, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, scr,
-                                                    (S*)lam_out[0], (S*)lam_out[1], (S*)lam_out[2], (S*)lam_out[3],
-                                                    (S*)lam_out[4], lam.gout, lam.osy, lam.osz);
+  k_adj_cells<Pol, LIM><<<cgrid, dim3(32, 8), 0, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, scr,
+                                                         (S*)lam_out[0], (S*)lam_out[1], (S*)lam_out[2],
+                                                         (S*)lam_out[3], (S*)lam_out[4], lam.gout, lam.osy, lam.osz);
   return cudaGetLastError();
+}
+
+template <class Pol>
+cudaError_t launch_adjoint(const HostPatchIO& U, const HostPatchIO& lam, void* const lam_out[5], const Params& prm,
+                           const double* dt, void* scratch, size_t scratch_bytes, unsigned* err, cudaStream_t s) {
+  if constexpr (std::is_same<Pol, PolMixed>::value || std::is_same<Pol, PolDF>::value) {
+    return cudaErrorNotSupported;  // the adjoint kernels are FP64 and FP32 (double-float uses FP64's)
+  } else {
+    switch (prm.limiter) {
+      case HYDRO_MINMOD: return launch_adjoint_t<Pol, HYDRO_MINMOD>(U, lam, lam_out, prm, dt, scratch, scratch_bytes, err, s);
+      case HYDRO_MC: return launch_adjoint_t<Pol, HYDRO_MC>(U, lam, lam_out, prm, dt, scratch, scratch_bytes, err, s);
+      case HYDRO_NOLIMIT: return launch_adjoint_t<Pol, HYDRO_NOLIMIT>(U, lam, lam_out, prm, dt, scratch, scratch_bytes, err, s);
+    }
+    return cudaErrorInvalidValue;
   }
 }
 

@@ -231,8 +231,12 @@ __device__ __forceinline__ void rcp2(const df& a, const df& b, df& ra, df& rb) {
   rb = rcp_(b);
 }
 
+// zn: the face normal is z.  The upwind side's kinetic sum |u|^2 is formed after the side is chosen,
+// from its face-normal components (u_n, u_t1, u_t2), in the x, y, z order of the velocity: (u_n^2 +
+// u_t1^2) + u_t2^2 for x and y normals (for y, u_n^2 + u_t1^2 = v^2 + u^2 = u^2 + v^2 exactly),
+// (u_t1^2 + u_t2^2) + u_n^2 for a z normal.
 template <class R>
-__device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R keR, R gamma, R inv_gm1, R F[5]) {
+__device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], bool zn, R gamma, R inv_gm1, R F[5]) {
   R irL, irR;
   rcp2(qL[0], qR[0], irL, irR);
   const R cL = rsqrt_(gamma * qL[4] * irL);
@@ -253,10 +257,11 @@ __device__ __forceinline__ void hllc_core(const R qL[5], const R qR[5], R keL, R
   const R t1 = left ? qL[2] : qR[2];
   const R t2 = left ? qL[3] : qR[3];
   const R pK = left ? qL[4] : qR[4];
-  const R keK = left ? keL : keR;
   const R irK = left ? irL : irR;
   const R SK = left ? SL : SR;
   const R mK = left ? mL : mR;
+  const R un2 = uK * uK, a2 = t1 * t1, b2 = t2 * t2;
+  const R keK = zn ? (a2 + b2) + un2 : (un2 + a2) + b2;
   const R EK = pK * inv_gm1 + half_(rK * keK);
   // Star state of side K: density r* = m_K/(S_K - S*), velocity S*, pressure p* = p_K + m_K (S* - u_K),
   // energy E* = r* (E_K/rho_K + (S* - u_K)(S* + p_K/m_K)).  F*_K = F_K + S_K (U*_K - U_K) equals the
@@ -292,7 +297,7 @@ __device__ __forceinline__ void hllc(const R qL[5], const R qR[5], R gamma, R in
   const R a[5] = {qL[0], qL[N], qL[T1], qL[T2], qL[4]};
   const R b[5] = {qR[0], qR[N], qR[T1], qR[T2], qR[4]};
   R Fr[5];
-  hllc_core(a, b, kinetic_sum(qL), kinetic_sum(qR), gamma, inv_gm1, Fr);
+  hllc_core(a, b, D == 2, gamma, inv_gm1, Fr);
   F[0] = Fr[0];
   F[N] = Fr[1];
   F[T1] = Fr[2];
@@ -308,7 +313,7 @@ __device__ __forceinline__ void hllc_dyn(int d, const R qL[5], const R qR[5], R 
   const R b[5] = {qR[0], d == 0 ? qR[1] : (d == 1 ? qR[2] : qR[3]), d == 0 ? qR[2] : qR[1],
                   d == 2 ? qR[2] : qR[3], qR[4]};
   R Fr[5];
-  hllc_core(a, b, kinetic_sum(qL), kinetic_sum(qR), gamma, inv_gm1, Fr);
+  hllc_core(a, b, d == 2, gamma, inv_gm1, Fr);
   F[0] = Fr[0];
   F[1] = d == 0 ? Fr[1] : Fr[2];
   F[2] = d == 1 ? Fr[1] : (d == 0 ? Fr[2] : Fr[3]);

@@ -12,9 +12,7 @@
 namespace hydro {
 
 // ------------------------------------------------------------------ step launchers
-// The step kernels are compiled for MinMod (LIM = HYDRO_MINMOD, the limiter fixed at compile time)
-// and for the limiter read from the parameters at run time (LIM = -1: MC, none).
-constexpr int kLimRuntime = -1;
+// The step kernels are compiled once per PLM limiter (LIM: HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT).
 
 template <class Pol, int TX, int TY, int MINB, int LIM>
 cudaError_t launch_uniform_t(const HostPatchIO& P, const Params& prm, const double* dt, double* dt_next, int zchunk,
@@ -60,13 +58,16 @@ int blocks_per_sm_t() {
 }
 
 // Tile id -> compiled shape, and the limiter -> compiled variant.
-#define HYDRO_TILE_SWITCH(tile, lim, CALL)                                      \
-  switch (tile) {                                                               \
-    case 0: return lim == HYDRO_MINMOD ? CALL(0, HYDRO_MINMOD) : CALL(0, kLimRuntime); \
-    case 1: return lim == HYDRO_MINMOD ? CALL(1, HYDRO_MINMOD) : CALL(1, kLimRuntime); \
-    case 2: return lim == HYDRO_MINMOD ? CALL(2, HYDRO_MINMOD) : CALL(2, kLimRuntime); \
-    case 3: return lim == HYDRO_MINMOD ? CALL(3, HYDRO_MINMOD) : CALL(3, kLimRuntime); \
-    case 4: return lim == HYDRO_MINMOD ? CALL(4, HYDRO_MINMOD) : CALL(4, kLimRuntime); \
+#define HYDRO_LIM_SWITCH(T, lim, CALL)                     \
+  (lim == HYDRO_MINMOD ? CALL(T, HYDRO_MINMOD)             \
+                       : lim == HYDRO_MC ? CALL(T, HYDRO_MC) : CALL(T, HYDRO_NOLIMIT))
+#define HYDRO_TILE_SWITCH(tile, lim, CALL)                    \
+  switch (tile) {                                             \
+    case 0: return HYDRO_LIM_SWITCH(0, lim, CALL);           \
+    case 1: return HYDRO_LIM_SWITCH(1, lim, CALL);           \
+    case 2: return HYDRO_LIM_SWITCH(2, lim, CALL);           \
+    case 3: return HYDRO_LIM_SWITCH(3, lim, CALL);           \
+    case 4: return HYDRO_LIM_SWITCH(4, lim, CALL);           \
   }
 
 template <class Pol>
@@ -98,6 +99,7 @@ int batched_blocks_per_sm(int tile, int limiter) {
   return 1;
 }
 #undef HYDRO_TILE_SWITCH
+#undef HYDRO_LIM_SWITCH
 
 // ------------------------------------------------------------------ CFL dt (standalone)
 // blockIdx.y walks the patches, blockIdx.x the interior cells of one patch.  The per-block

@@ -207,10 +207,16 @@ __device__ __forceinline__ void load_q(const MhdBox<Pol>& B, long long a, const 
   mhd_recover(U, c, q, flags);
 }
 
+// Float arithmetic keeps a cell's 27 slopes in registers between the face states' fluxes and their
+// advance (its six extrapolated states are q -+ s/2); 8-byte arithmetic has no registers to spare
+// and round-trips the states through the scratch instead.
+template <class R>
+constexpr bool kSlopesInRegs = sizeof(R) == 4;
+
 template <int D, class Pol>
 __device__ __forceinline__ void axis_states(const MhdBox<Pol>& B, long long a, long long am, long long ap,
                                             const typename Pol::R q[NV], const MhdConst<typename Pol::R>& c,
-                                            typename Pol::R dF[NV]) {
+                                            typename Pol::R dF[NV], typename Pol::R sl[NV]) {
   using R = typename Pol::R;
   unsigned nf = 0;  // neighbours are flagged by their own threads
   R lo[NV], hi[NV];
@@ -221,10 +227,13 @@ __device__ __forceinline__ void axis_states(const MhdBox<Pol>& B, long long a, l
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
+      sl[v] = s;
       lo[v] = q[v] - half_(s);
       hi[v] = q[v] + half_(s);
-      B.face[((long long)(2 * D) * NV + v) * B.cells + a] = lo[v];
-      B.face[((long long)(2 * D + 1) * NV + v) * B.cells + a] = hi[v];
+      if (!kSlopesInRegs<R>) {
+        B.face[((long long)(2 * D) * NV + v) * B.cells + a] = lo[v];
+        B.face[((long long)(2 * D + 1) * NV + v) * B.cells + a] = hi[v];
+      }
     }
   }
   R Fh[NV];
@@ -254,25 +263,31 @@ __global__ void __launch_bounds__(256, 2) k_mhd_predict(MhdBox<Pol> B, const Mhd
     const long long axm = a + (i == 0 ? B.nx - 1 : -1), axp = a + (i == B.nx - 1 ? -(B.nx - 1) : 1);
     const long long aym = a + (j == 0 ? (B.ny - 1) * sy : -sy), ayp = a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy);
     const long long azm = a + (k == 0 ? (B.nz - 1) * sz : -sz), azp = a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz);
-    R q[NV], dF[NV];
+    R q[NV], dF[NV], sl[3][NV];
     load_q(B, a, c, q, flags);
-    axis_states<0>(B, a, axm, axp, q, c, dF);
-    axis_states<1>(B, a, aym, ayp, q, c, dF);
-    axis_states<2>(B, a, azm, azp, q, c, dF);
-    // the six extrapolated states advanced by half a step, recovered and floored (this thread's
-    // own scratch entries, written just above)
+    axis_states<0>(B, a, axm, axp, q, c, dF, sl[0]);
+    axis_states<1>(B, a, aym, ayp, q, c, dF, sl[1]);
+    axis_states<2>(B, a, azm, azp, q, c, dF, sl[2]);
+    // the six extrapolated states advanced by half a step, recovered and floored (from the slopes
+    // in registers, or this thread's own scratch entries written just above)
     unsigned nf = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
 #pragma unroll 1
-    for (int f = 0; f < 6; ++f) {
-      R w[NV], U[NV], r[NV];
+      for (int h = 0; h < 2; ++h) {
+        const int f = 2 * d + h;
+        R w[NV], U[NV], r[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = B.face[((long long)f * NV + v) * B.cells + a];
-      mhd_conserved(w, c, U);
+        for (int v = 0; v < NV; ++v)
+          w[v] = kSlopesInRegs<R> ? (h ? q[v] + half_(sl[d][v]) : q[v] - half_(sl[d][v]))
+                                  : B.face[((long long)f * NV + v) * B.cells + a];
+        mhd_conserved(w, c, U);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
-      mhd_recover(U, c, r, nf);
+        for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
+        mhd_recover(U, c, r, nf);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) B.face[((long long)f * NV + v) * B.cells + a] = r[v];
+        for (int v = 0; v < NV; ++v) B.face[((long long)f * NV + v) * B.cells + a] = r[v];
+      }
     }
   }
   flush_flags(flags, err);
@@ -530,7 +545,8 @@ __global__ void k_mhdp_consts(const HostMhdPatch* patches, int npatch, MhdConst<
 template <int D, class Pol>
 __device__ __forceinline__ void axis_states_p(const HostMhdPatch& P, typename Pol::R* face, long long ec, long long e,
                                               const ExtCell& x, const typename Pol::R q[NV],
-                                              const MhdConst<typename Pol::R>& c, typename Pol::R dF[NV]) {
+                                              const MhdConst<typename Pol::R>& c, typename Pol::R dF[NV],
+                                              typename Pol::R sl[NV]) {
   using R = typename Pol::R;
   unsigned nf = 0;  // neighbours are flagged by their own threads
   const int di = D == 0, dj = D == 1, dk = D == 2;
@@ -542,10 +558,13 @@ __device__ __forceinline__ void axis_states_p(const HostMhdPatch& P, typename Po
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
+      sl[v] = s;
       lo[v] = q[v] - half_(s);
       hi[v] = q[v] + half_(s);
-      face[((long long)(2 * D) * NV + v) * ec + e] = lo[v];
-      face[((long long)(2 * D + 1) * NV + v) * ec + e] = hi[v];
+      if (!kSlopesInRegs<R>) {
+        face[((long long)(2 * D) * NV + v) * ec + e] = lo[v];
+        face[((long long)(2 * D + 1) * NV + v) * ec + e] = hi[v];
+      }
     }
   }
   R Fh[NV];
@@ -571,23 +590,29 @@ __global__ void __launch_bounds__(256, 2) k_mhdp_predict(const HostMhdPatch* pat
   const long long ec = (long long)(P.nx + 2) * (P.ny + 2) * (P.nz + 2), e = b.y + threadIdx.x;
   R* face = static_cast<R*>(scratch) + P.scratch;
   unsigned flags = 0;
-  R q[NV], dF[NV];
+  R q[NV], dF[NV], sl[3][NV];
   load_qp<Pol>(P, in_addr(P, x.i, x.j, x.k), c, q, flags);
-  axis_states_p<0, Pol>(P, face, ec, e, x, q, c, dF);
-  axis_states_p<1, Pol>(P, face, ec, e, x, q, c, dF);
-  axis_states_p<2, Pol>(P, face, ec, e, x, q, c, dF);
+  axis_states_p<0, Pol>(P, face, ec, e, x, q, c, dF, sl[0]);
+  axis_states_p<1, Pol>(P, face, ec, e, x, q, c, dF, sl[1]);
+  axis_states_p<2, Pol>(P, face, ec, e, x, q, c, dF, sl[2]);
   unsigned nf = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
 #pragma unroll 1
-  for (int f = 0; f < 6; ++f) {
-    R w[NV], U[NV], r[NV];
+    for (int h = 0; h < 2; ++h) {
+      const int f = 2 * d + h;
+      R w[NV], U[NV], r[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = face[((long long)f * NV + v) * ec + e];
-    mhd_conserved(w, c, U);
+      for (int v = 0; v < NV; ++v)
+        w[v] = kSlopesInRegs<R> ? (h ? q[v] + half_(sl[d][v]) : q[v] - half_(sl[d][v]))
+                                : face[((long long)f * NV + v) * ec + e];
+      mhd_conserved(w, c, U);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
-    mhd_recover(U, c, r, nf);
+      for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
+      mhd_recover(U, c, r, nf);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) face[((long long)f * NV + v) * ec + e] = r[v];
+      for (int v = 0; v < NV; ++v) face[((long long)f * NV + v) * ec + e] = r[v];
+    }
   }
   if (!x.ring && flags) atomicOr(err, flags);  // the interior's own recovery; ghosts are flagged by their owners
 }

@@ -99,6 +99,7 @@ struct TileShared {
   Plane5<R, TY + 1, TX> fy;        // y-face fluxes of plane p, index j+1 for face j+1/2
   long long yoff[TY + 4];          // y offset (y index * stride) of the halo rows
   int xoff[TX + 4];                // x index of the halo columns
+  int pairok[(TX + 4) / 2];        // halo columns 2k, 2k+1 adjacent in memory, the first even
   R red[TX * TY / 32];
   int tile;
 };
@@ -109,13 +110,13 @@ __device__ __forceinline__ int wrapi(int x, int n) {
 }
 __device__ __forceinline__ int ring_slot(int p) { return (p + 3) % 3; }
 
-// Limited slope of a cell from its backward and forward differences.  LIM == HYDRO_MINMOD fixes the
-// limiter at compile time (the step kernels are compiled for MinMod and for a limiter read at run
-// time, prm.limiter: MC or none); minmod() is the same function as limited(., ., HYDRO_MINMOD).
+// Limited slope of a cell from its backward and forward differences, the limiter fixed at compile
+// time (the step kernels are compiled once per limiter: its tests and selections then cost no
+// branches on a run-time value); the same values as limited(a, b, LIM).
 template <int LIM, class R>
-__device__ __forceinline__ R limited_t(R a, R b, int lim) {
+__device__ __forceinline__ R limited_t(R a, R b, int) {
   if constexpr (LIM == HYDRO_MINMOD) return minmod(a, b);
-  else return limited(a, b, lim);
+  else return limited(a, b, LIM);
 }
 
 template <int LIM, class Pol, int TX, int TY>
@@ -195,6 +196,19 @@ __device__ __forceinline__ void face_flux_dyn(TileShared<Pol, TX, TY>& sm, int d
   hllc_dyn(d, qL, qR, kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), F);
 }
 
+// Two x-adjacent stored values at an even, vector-aligned address (one 16-byte load for double,
+// 8-byte for float), read through the read-only path.
+__device__ __forceinline__ void ldg_pair(const double* p, double& a, double& b) {
+  const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void ldg_pair(const float* p, float& a, float& b) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  a = t.x;
+  b = t.y;
+}
+
 // Advances the tile; returns (through smax) the largest CFL speed of the updated cells.
 template <int LIM, class Pol, int TX, int TY>
 __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Pol::S>& P, int x0, int y0, int z0,
@@ -217,46 +231,71 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     y = periodic ? wrapi(y, P.ny) : min(max(y, -2), P.ny + 1) + 2;
     sm.yoff[c] = (long long)y * P.isy;
   }
+  // Vector loads of cell pairs need even strides and field pointers aligned to the pair's size.
+  bool vec = (P.isy % 2 == 0) && (P.isz % 2 == 0);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) vec = vec && (reinterpret_cast<uintptr_t>(P.in[v]) % (2 * sizeof(S)) == 0);
+  __syncthreads();
+  for (int k = tid; k < QW / 2; k += NT) {
+    const int a = sm.xoff[2 * k], b = sm.xoff[2 * k + 1];
+    sm.pairok[k] = vec && b == a + 1 && (a & 1) == 0;
+  }
   __syncthreads();
 
   auto plane_offset = [&](int z) {
     const int zi = periodic ? wrapi(z, P.nz) : z + 2;
     return (long long)zi * P.isz;
   };
-  // Plane loads: cell c of the (TX+4) x (TY+4) halo plane goes to thread NT-1-c (mod NT), so the
-  // threads that load a second cell are the last ones, not the warps that also take the tile's edge
-  // faces.
+  // Plane loads, two x-adjacent cells per thread: pair c of the (TX+4) x (TY+4) halo plane (cells
+  // 2 (c mod QP), +1 of row c / QP) goes to thread NT-1-c (mod NT), so the threads left without a
+  // pair (or with one pair where others take two) are the first ones, the warps that also take the
+  // tile's edge faces.  A pair adjacent in memory (pairok: no wrap or clamp between its columns, the
+  // first column even) is read with one vector load per field, else with two.
+  constexpr int QP = QW / 2, QNP = QH * QP;
+  auto fetch_pair = [&](long long zo, int c, S U0[5], S U1[5]) {
+    const int cy = c / QP, px = c - cy * QP;
+    const long long a = zo + sm.yoff[cy] + sm.xoff[2 * px];
+    if (sm.pairok[px]) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ldg_pair(P.in[v] + a, U0[v], U1[v]);
+    } else {
+      const long long a1 = zo + sm.yoff[cy] + sm.xoff[2 * px + 1];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        U0[v] = __ldg(P.in[v] + a);
+        U1[v] = __ldg(P.in[v] + a1);
+      }
+    }
+  };
+  auto store_pair = [&](int slot, int c, const S U0[5], const S U1[5]) {
+    const int cy = c / QP, cx = 2 * (c - cy * QP);
+    R q[5];
+    Pol::recover(U0, prm, q, flags);
+    sm.q[slot].st(cy, cx, q);
+    Pol::recover(U1, prm, q, flags);
+    sm.q[slot].st(cy, cx + 1, q);
+  };
   auto load_plane = [&](int z) {
     const int slot = ring_slot(z);
     const long long zo = plane_offset(z);
-    for (int c = NT - 1 - tid; c < QN; c += NT) {
-      const int cy = c / QW, cx = c - cy * QW;
-      const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
-      S U[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) U[v] = __ldg(P.in[v] + a);
-      R q[5];
-      Pol::recover(U, prm, q, flags);
-      sm.q[slot].st(cy, cx, q);
+    for (int c = NT - 1 - tid; c < QNP; c += NT) {
+      S U0[5], U1[5];
+      fetch_pair(zo, c, U0, U1);
+      store_pair(slot, c, U0, U1);
     }
   };
   // Float arithmetic: phase 2 issues the next plane's loads into registers before its face fluxes
   // and recovers them after, so the load latency overlaps the fluxes (8-byte arithmetic has no
   // registers to spare for it).
   constexpr bool kPrefetch = std::is_same<R, float>::value;
-  constexpr int NPF = kPrefetch ? (QN + NT - 1) / NT : 1;
-  S pre[NPF][5];
+  constexpr int NPF = kPrefetch ? (QNP + NT - 1) / NT : 1;
+  S pre0[NPF][5], pre1[NPF][5];
   auto fetch_plane = [&](int z) {
     const long long zo = plane_offset(z);
 #pragma unroll
     for (int k = 0; k < NPF; ++k) {
       const int c = NT - 1 - tid + k * NT;
-      if (c < QN) {
-        const int cy = c / QW, cx = c - cy * QW;
-        const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) pre[k][v] = __ldg(P.in[v] + a);
-      }
+      if (c < QNP) fetch_pair(zo, c, pre0[k], pre1[k]);
     }
   };
   auto commit_plane = [&](int z) {
@@ -264,12 +303,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
 #pragma unroll
     for (int k = 0; k < NPF; ++k) {
       const int c = NT - 1 - tid + k * NT;
-      if (c < QN) {
-        const int cy = c / QW, cx = c - cy * QW;
-        R q[5];
-        Pol::recover(pre[k], prm, q, flags);
-        sm.q[slot].st(cy, cx, q);
-      }
+      if (c < QNP) store_pair(slot, c, pre0[k], pre1[k]);
     }
   };
   constexpr bool kCompact = std::is_same<R, df>::value;  // double-float arithmetic
