@@ -364,8 +364,8 @@ cudaError_t launch_adjoint_t(const HostPatchIO& U, const HostPatchIO& lam, void*
   if (ea != cudaSuccess) return ea;
   // z chunk: FP32 takes the longest of 16, 8, 4, 2 planes whose grid still fills half of the SMs'
   // resident blocks (a small grid leaves SMs idle, a short march repeats halo planes; half is the
-  // measured balance).  FP64 takes the longest of 16, 8, 4 whose grid fills every resident slot:
-  // its FP64 pipe needs the warps to cover the latency of its dependent double operations.
+  // measured balance).  FP64 keeps 16: it is bound by the FP64 pipe, which a few warps per SM
+  // already keep busy (8-plane chunks that fill every resident slot measured 3% slower at 64^3).
   static int resident = 0;
   if (!resident) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adj_faces<Pol, TX, TY, LIM>, TX * TY,
@@ -378,11 +378,8 @@ cudaError_t launch_adjoint_t(const HostPatchIO& U, const HostPatchIO& lam, void*
     return cudaErrorUnknown;
   const long long cols = (long long)((U.nx + TX - 1) / TX) * ((U.ny + TY - 1) / TY);
   int zc = 16;
-  if (std::is_same<R, double>::value) {
-    while (zc > 4 && cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms) zc /= 2;
-  } else {
-    while (zc > 2 && 2 * cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms) zc /= 2;
-  }
+  while (!std::is_same<R, double>::value && zc > 2 && 2 * cols * ((U.nz + zc - 1) / zc) < (long long)resident * sms)
+    zc /= 2;
   if (zc > U.nz) zc = U.nz;
   dim3 grid((U.nx + TX - 1) / TX, (U.ny + TY - 1) / TY, (U.nz + zc - 1) / zc);
   k_adj_faces<Pol, TX, TY, LIM><<<grid, TX * TY, smem, s>>>(to_dev<Pol>(U), to_dev<Pol>(lam), prm, dt, zc, scr, err);

@@ -356,3 +356,94 @@ def test_error_word_flags_and_argument_errors():
     with pytest.raises(hy.HydroError):  # FP32 context given FP64 data of odd alignment is fine; a bad dx is not
         hy.hydro_cfl_dt(c, hy.patch(a, 0, 0.0), dts(0.0))
     check_clean(c)
+
+
+@pytest.mark.parametrize("precision", ALL)
+def test_odd_sizes_odd_strides_and_unaligned_views(precision):
+    """Ghosted patches of odd sizes stored as views with odd row strides that start one element into
+    their buffer, and a periodic box of odd size stored the same way: the paired (vector) halo loads
+    fall back to single-cell loads wherever a pair is not adjacent or not aligned in memory, and every
+    tile shape still gives the oracle's step."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    tol = TOL64 if precision in F64 else TOL32
+    rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if precision == "fp32" else (lambda a: a)
+    parent = workloads.turbulent_state(16, seed=8, mach=3.0, sedov=False)
+    dims = [(5, 7, 9), (13, 3, 11), (1, 1, 1), (17, 19, 6)]
+    origins = [(3, 5, 7), (15, 0, 2), (8, 8, 8), (0, 11, 13)]
+
+    def view_of(arr, pad):
+        F, Z, Y, X = arr.shape
+        buf = torch.zeros((F, Z, Y, X + pad), dtype=dtype, device="cuda")
+        v = buf[:, :, :, 1:1 + X]
+        v.copy_(torch.as_tensor(arr))
+        return buf, v
+
+    c = ctx(precision)
+    keep, ins, outs, host = [], [], [], []
+    for (nx, ny, nz), o in zip(dims, origins):
+        Ug = rnd(workloads.ghosted_from_periodic(parent, o, (nx, ny, nz)).numpy())
+        dx = 1.0 / 64
+        b1, vin = view_of(Ug, 2)   # row stride nx + 6: odd for odd nx
+        b2, vout = view_of(np.zeros_like(Ug), 4)
+        keep += [b1, b2]
+        ins.append(hy.patch(vin, 2, dx))
+        outs.append(hy.patch(vout, 2, dx))
+        host.append((Ug, dx, vout))
+    dt_list = [0.7 * oracle.cfl_patch(Ug, dx, ocfg()) for Ug, dx, _ in host]
+    U = rnd(workloads.turbulent_state((7, 9, 11), seed=9, mach=3.0, sedov=True).numpy())
+    bp, vp = view_of(U, 2)
+    bq, vq = view_of(np.zeros_like(U), 2)
+    dtp = oracle.cfl_periodic(U, 1.0 / 11, ocfg())
+    want_p = oracle.step_periodic(U, 1.0 / 11, dtp, ocfg())
+    for tile in range(hy.NUM_TILES):
+        hy.hydro_set_tuning(c, tile, 4)
+        hy.hydro_step(c, ins, outs, dts(*dt_list))
+        hy.hydro_step(c, hy.patch(vp, 0, 1.0 / 11), hy.patch(vq, 0, 1.0 / 11), dts(dtp))
+        torch.cuda.synchronize()
+        for (Ug, dx, vout), dt in zip(host, dt_list):
+            got = vout.double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
+            assert normwise(got, oracle.step_patch(Ug, dx, dt, ocfg())).max() <= tol, (tile, Ug.shape)
+        assert normwise(vq.double().cpu().numpy(), want_p).max() <= tol, tile
+    check_clean(c)
+
+
+@pytest.mark.parametrize("precision", ["df64", "fp32"])
+def test_writes_stay_inside_the_output_interior(precision):
+    """Canary-padded buffers: each output field lives inside a larger buffer whose every other element
+    (the padding around the box in x, y and z, and the output patch's own ghost layers) holds a
+    sentinel; after steps with every tile shape and several z chunks, batched and uniform, every
+    sentinel is intact: no write lands outside the interior it belongs to."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    sentinel = -12345.0
+    c = ctx(precision)
+    parent = workloads.turbulent_state(16, seed=10, mach=3.0, sedov=False)
+    dims = [(9, 5, 7), (16, 16, 16), (3, 20, 5)]
+    ins, outs, bufs = [], [], []
+    for k, (nx, ny, nz) in enumerate(dims):
+        Ug = workloads.ghosted_from_periodic(parent, (k, 2 * k, 3 * k), (nx, ny, nz)).to(dtype)
+        ins.append(hy.patch(Ug.to("cuda").contiguous(), 2, 1.0 / 64))
+        buf = torch.full((5, nz + 4 + 6, ny + 4 + 6, nx + 4 + 6), sentinel, dtype=dtype, device="cuda")
+        outs.append(hy.patch(buf[:, 3:-3, 3:-3, 3:-3], 2, 1.0 / 64))
+        bufs.append(buf)
+    dt = torch.empty(len(ins), dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(c, ins, dt)
+    U = workloads.turbulent_state((11, 13, 15), seed=11, mach=3.0, sedov=True).to("cuda", dtype)
+    pbuf = torch.full((5, 11 + 4, 13 + 4, 15 + 4), sentinel, dtype=dtype, device="cuda")
+    pout = pbuf[:, 2:-2, 2:-2, 2:-2]
+    dtp = torch.empty(1, dtype=torch.float64, device="cuda")
+    hy.hydro_cfl_dt(c, hy.patch(U.contiguous(), 0, 1.0 / 15), dtp)
+    for tile in range(hy.NUM_TILES):
+        for zc in (3, 32):
+            hy.hydro_set_tuning(c, tile, zc)
+            hy.hydro_step(c, ins, outs, dt)
+            hy.hydro_step(c, hy.patch(U.contiguous(), 0, 1.0 / 15), hy.patch(pout, 0, 1.0 / 15), dtp)
+    torch.cuda.synchronize()
+    for (nx, ny, nz), buf in zip(dims, bufs):
+        inner = torch.zeros_like(buf, dtype=torch.bool)
+        inner[:, 5:5 + nz, 5:5 + ny, 5:5 + nx] = True  # the interior: 3 padding + 2 ghost layers in
+        assert bool((buf[~inner] == sentinel).all())
+        assert not bool((buf[inner] == sentinel).any())
+    inner = torch.zeros_like(pbuf, dtype=torch.bool)
+    inner[:, 2:-2, 2:-2, 2:-2] = True
+    assert bool((pbuf[~inner] == sentinel).all()) and not bool((pbuf[inner] == sentinel).any())
+    check_clean(c)
