@@ -41,12 +41,20 @@ def test_double_float_flop_constant():
     assert df == pytest.approx(b.ALG_DF_FLOPS_PER_CELL["turb_minmod"], rel=0.01)
 
 
-def test_headline_profile_was_taken_on_the_current_step_kernel():
-    """The committed ncu summary of the headline step kernel carries the hash of the kernel's sources
-    it was taken on; the bench reports its DRAM traffic only while that hash matches, so a change to
-    the step kernel without a new capture shows here (and as a null roofline.traffic)."""
+@pytest.mark.parametrize("precision,bytes_per_cell", [("df64", 80), ("fp64", 80), ("fp32", 40), ("mixed", 80)])
+def test_step_profiles_were_taken_on_the_current_step_kernel(precision, bytes_per_cell):
+    """The committed ncu summaries of the step kernel carry the hash of the kernel's sources they were
+    taken on; the bench reports their DRAM traffic only while that hash matches, so a change to the
+    step kernel without a new capture shows here (and as a null roofline.traffic)."""
     b = bench_module()
-    traffic, src = b.profile_traffic("step_uniform_512_df64.txt")
-    assert src.endswith("step_uniform_512_df64.txt"), src
-    # the DRAM bytes of one 512^3 launch stay within a few percent of the algorithmic 80 B per cell
-    assert traffic == pytest.approx(512 ** 3 * 80, rel=0.05)
+    traffic, src = b.profile_traffic("step_uniform_512_%s.txt" % precision)
+    assert src.endswith("step_uniform_512_%s.txt" % precision), src
+    # the DRAM bytes of one 512^3 launch stay within a few percent of the algorithmic bytes per cell
+    assert traffic == pytest.approx(512 ** 3 * bytes_per_cell, rel=0.05)
+
+
+def test_launch_list_and_other_step_profiles_carry_the_current_hash():
+    b = bench_module()
+    for name in ("launches_bench_512_df64.txt", "step_batched_mixed_512patches.txt", "step_ppm_256_df64.txt"):
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        assert "kernel_source_hash = %s" % b.kernel_source_hash() in text, name

@@ -447,3 +447,27 @@ def test_writes_stay_inside_the_output_interior(precision):
     inner[:, 2:-2, 2:-2, 2:-2] = True
     assert bool((pbuf[~inner] == sentinel).all()) and not bool((pbuf[inner] == sentinel).any())
     check_clean(c)
+
+
+def test_double_float_exponent_range():
+    """The double-float policy keeps the exponent range of float (include/hydro.h at HYDRO_FP64_DF).
+    The step is scale-covariant (U -> a U scales every flux and update by a, floors scaled alike), so
+    the oracle's step of U, times a, is the step of a U: at a = 1e-20 (densities ~1e-20, pressures
+    ~1e-24, well inside the range) double-float still matches it within 1e-12, as FP64 does; at
+    a = 1e25 the momentum squares (~1e47) overflow float, and the step flags HYDRO_EBIT_NONFINITE
+    instead of returning silent garbage, while native FP64 steps it to the scaled oracle result."""
+    U = workloads.turbulent_state((12, 16, 20), seed=2, mach=5.0, sedov=False).numpy()
+    dx = 1.0 / 20
+    dt = 0.5 * oracle.cfl_periodic(U, dx, ocfg())  # the same for a U: velocities and sound speeds keep
+    o = oracle.step_periodic(U, dx, dt, ocfg())
+    for a, precision, ok in ((1e-20, "df64", True), (1e-20, "fp64", True), (1e25, "fp64", True),
+                             (1e25, "df64", False)):
+        c = ctx(precision, rho_floor=1e-10 * a, p_floor=1e-14 * a)
+        g, _ = step_periodic(c, a * U, dx, dt)
+        rc, bits = hy.hydro_get_error(c)
+        if ok:
+            assert rc == hy.HYDRO_OK and bits == 0, (a, precision, bits)
+            assert normwise(g / a, o).max() <= TOL64, (a, precision, normwise(g / a, o))
+        else:
+            assert bits & hy.EBIT_NONFINITE, (a, precision, bits)
+        hy.hydro_finalize(c)
