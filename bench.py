@@ -86,6 +86,7 @@ def parse():
     p.add_argument("--ngroups", type=int, default=262144, help="oct groups of the batched form")
     p.add_argument("--adj-n", type=int, default=64, help="grid edge of the adjoint form")
     p.add_argument("--adj-precisions", default="df64,fp64,fp32", help="precisions of the adjoint form")
+    p.add_argument("--mhd-precisions", default="fp64,df64,fp32,mixed", help="precisions of the MHD form")
     p.add_argument("--forms-only", action="store_true",
                    help="run only the extra forms and print their JSON (for profiling them alone)")
     return p.parse_args()
@@ -1137,9 +1138,10 @@ def run_forms(hy, args, n, precision):
                     extra[key] = form_uniform(hy, n, prec, "ppm", args.steps, args.warmup, None, path=(key,))
                 extra["ppm_batched_mixed"] = form_ppm_batched(hy, max(3, args.steps // 2), 2, npatch=args.npatch)
             elif f == "mhd":
-                for prec in ("fp64", "df64", "fp32", "mixed"):
+                for prec in args.mhd_precisions.split(","):
                     extra["mhd_256_" + prec] = form_mhd(hy, prec, args.steps, args.warmup)
-                extra["mhd_patches_fp32"] = form_mhd_patches(hy, "fp32", max(3, args.steps // 2), 2)
+                if "fp32" in args.mhd_precisions.split(","):
+                    extra["mhd_patches_fp32"] = form_mhd_patches(hy, "fp32", max(3, args.steps // 2), 2)
             elif f == "graph1024":
                 extra["graph_1024_fp32_mc"] = form_uniform(hy, 1024, "fp32", "mc", 20, 0, "mach10_mc", mach=10.0,
                                                            sigma=1.5, p_over_rho=1e-5, sedov=False, seed=5,
