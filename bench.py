@@ -510,6 +510,7 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     if TUNING == "auto":
         hy.hydro_autotune(ctx, ins, outs, dt)  # tile shape and z chunk for this patch set
     tt, tz = hy.hydro_get_tuning(ctx)
+    per_class = [hy.hydro_get_class_tuning(ctx, k) for k in range(hy.NUM_PATCH_CLASSES)]
     for _ in range(warmup):
         hy.hydro_step(ctx, ins, outs, dt, dn)
     torch.cuda.synchronize()
@@ -641,7 +642,8 @@ def form_batched(hy, steps, warmup, npatch=4096, ngroups=262144):
     bytes_o = ngroups * (216 + 8) * 5 * 8
     out = {"patches": n, "interior_cells": interior, "ghosted_cells": ghosted, "ms_per_step": ms,
            "mcell_updates_per_s": interior / (ms / 1e3) / 1e6, "launches_per_step": launches,
-           "tuning": {"tile": TILE_NAMES[tt], "zchunk": tz},
+           "tuning": {"tile": TILE_NAMES[tt], "zchunk": tz,
+                      "per_patch_class": [{"tile": TILE_NAMES[t], "zchunk": z} for t, z in per_class]},
            "hbm_frac": bytes_p / (ms / 1e3) / 1e9 / hbm,
            "octs": {"groups": ngroups, "ms_per_step": ms_o, "mcell_updates_per_s": ngroups * 8 / (ms_o / 1e3) / 1e6,
                     "hbm_frac": bytes_o / (ms_o / 1e3) / 1e9 / hbm},

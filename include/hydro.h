@@ -65,9 +65,10 @@ typedef enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2, HYDRO_FP64_DF = 
  *              in double.  Same results as HYDRO_FP64 to about 1e-13 relative, several times faster
  *              on parts whose FP64 rate is a small fraction of their FP32 rate.  Its exponent range
  *              is that of float: the intermediates of the scheme (state, speeds, fluxes, products
- *              such as rho u^2) keep the FP64 accuracy only between about 1e-30 and 3e38 in
- *              magnitude -- below, the low float of a pair leaves the normal range and relative
- *              accuracy drops towards float's; above, they overflow. */
+ *              such as |m|^2 and rho u^2) keep the FP64 accuracy only between about 1e-30 and 3e38
+ *              in magnitude -- below, the low float of a pair leaves the normal range and relative
+ *              accuracy drops towards float's (for |m|^2 below ~1e-38, to nothing); above, they
+ *              overflow, which the recovery flags as HYDRO_EBIT_NONFINITE. */
 
 typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2, HYDRO_PPM = 3 } hydro_limiter;
 /* HYDRO_MINMOD, HYDRO_MC, HYDRO_NOLIMIT: piecewise-linear (PLM) reconstruction with that slope.
@@ -368,9 +369,13 @@ int hydro_step_host(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* ou
 /* Autotuner (no counterpart in the paper, whose Sec. 3 finds that small chunks starve the GPU): times
  * the candidate tile shapes and z-chunk depths of hydro_step on this patch set
  * (in, out, dt_dev as for hydro_step; contents of out are overwritten) and keeps the fastest in
- * the context for later hydro_step calls.  If cache_path is not NULL the choice is read from /
- * appended to that text file, keyed by GPU name, SM count, precision and patch-set signature.
- * Synchronises the stream. */
+ * the context for later hydro_step calls.  When a batch of ghosted patches holds patches of more
+ * than one patch-shape class (below), it also times the candidates on each class's patches alone
+ * and keeps a tile shape per class if the whole set then steps at least 1% faster (hydro_step then
+ * runs one persistent launch per class).  If cache_path is not NULL the choice is read from /
+ * appended to that text file, one line per tuning: the key (GPU name, SM count, precision,
+ * limiter, patch-set signature), tile_id, zchunk, and tile_id, zchunk of each class (-1 0: the
+ * context's).  Synchronises the stream. */
 int hydro_autotune(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out, int npatch, const double* dt_dev,
                    const char* cache_path);
 
@@ -380,6 +385,18 @@ int hydro_autotune(hydro_ctx* ctx, const hydro_patch* in, const hydro_patch* out
  * kernel has one shape (16 x 16) and ignores tile_id.  hydro_set_tuning refuses tile_id outside
  * [0, HYDRO_NUM_TILES) and zchunk outside [1, 4096]. */
 #define HYDRO_NUM_TILES 5
+
+/* Tile shape per patch-shape class of a batched hydro_step (no counterpart in the paper): the
+ * classes are 0, a patch with an x or y edge of 8 cells or fewer; 1, else an x or y edge that is not
+ * a multiple of 16; 2, both multiples of 16.  hydro_set_class_tuning(ctx, class, tile_id, zchunk)
+ * gives a class its own tile shape and z chunk (tile_id -1: the context's, hydro_set_tuning's);
+ * hydro_get_class_tuning returns the tuning a class's patches step with.  hydro_set_tuning resets
+ * every class to the context's tuning.  A periodic box (ng == 0), the PPM kernel and the host-buffer
+ * step use the context's tuning only.  HYDRO_ERR_ARG for a class outside [0,
+ * HYDRO_NUM_PATCH_CLASSES) or a tuning hydro_set_tuning refuses. */
+#define HYDRO_NUM_PATCH_CLASSES 3
+int hydro_get_class_tuning(hydro_ctx* ctx, int patch_class, int* tile_id, int* zchunk);
+int hydro_set_class_tuning(hydro_ctx* ctx, int patch_class, int tile_id, int zchunk);
 int hydro_get_tuning(hydro_ctx* ctx, int* tile_id, int* zchunk);
 int hydro_set_tuning(hydro_ctx* ctx, int tile_id, int zchunk);
 

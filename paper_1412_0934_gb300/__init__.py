@@ -32,6 +32,8 @@ LIMITERS = {"minmod": HYDRO_MINMOD, "mc": HYDRO_MC, "none": HYDRO_NOLIMIT, "ppm"
 # Compiled tile shapes of the step kernels, by tile id (HYDRO_NUM_TILES in include/hydro.h).
 TILE_SHAPES = ((16, 16), (32, 8), (8, 8), (32, 16), (16, 16))
 NUM_TILES = len(TILE_SHAPES)
+# Patch-shape classes of the per-class tile choice (HYDRO_NUM_PATCH_CLASSES in include/hydro.h).
+NUM_PATCH_CLASSES = 3
 
 EBIT_NONFINITE = 0x01
 EBIT_RHO_FLOOR = 0x02
@@ -47,7 +49,7 @@ EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_
            "hydro_level_fluxes", "hydro_reflux", "hydro_average_down",
            "hydro_adjoint_step",
            "hydro_prim_to_cons", "hydro_prim_to_cons_adjoint", "hydro_run", "hydro_autotune", "hydro_get_tuning",
-           "hydro_set_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
+           "hydro_set_tuning", "hydro_get_class_tuning", "hydro_set_class_tuning", "hydro_get_error", "hydro_clear_error", "hydro_launch_count", "hydro_status_string",
            "hydro_step_batched_noalloc")
 
 
@@ -111,6 +113,8 @@ def lib():
         L.hydro_autotune.argtypes = [vp, PP, PP, i, vp, ctypes.c_char_p]
         L.hydro_get_tuning.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.hydro_set_tuning.argtypes = [vp, i, i]
+        L.hydro_get_class_tuning.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.hydro_set_class_tuning.argtypes = [vp, i, i, i]
         L.hydro_get_error.argtypes = [vp, ctypes.POINTER(ctypes.c_uint)]
         L.hydro_clear_error.argtypes = [vp]
         L.hydro_launch_count.argtypes = [vp, ctypes.POINTER(ll)]
@@ -552,6 +556,19 @@ def hydro_get_tuning(ctx):
 
 def hydro_set_tuning(ctx, tile_id, zchunk):
     _check(lib().hydro_set_tuning(ctx.handle, int(tile_id), int(zchunk)), "hydro_set_tuning")
+
+
+def hydro_get_class_tuning(ctx, patch_class):
+    t, z = ctypes.c_int(), ctypes.c_int()
+    _check(lib().hydro_get_class_tuning(ctx.handle, int(patch_class), ctypes.byref(t), ctypes.byref(z)),
+           "hydro_get_class_tuning")
+    return t.value, z.value
+
+
+def hydro_set_class_tuning(ctx, patch_class, tile_id, zchunk=0):
+    """tile_id -1: the class steps with the context's tuning (hydro_set_tuning's)."""
+    _check(lib().hydro_set_class_tuning(ctx.handle, int(patch_class), int(tile_id), int(zchunk)),
+           "hydro_set_class_tuning")
 
 
 def hydro_get_error(ctx):

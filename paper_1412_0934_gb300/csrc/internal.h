@@ -196,8 +196,10 @@ cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& pr
 cudaError_t launch_mhd_cfl(int precision, const HostMhdBox& h, const Params& prm, double* dt, unsigned* err,
                            cudaStream_t s);
 
-// Work-list construction (precision-independent; descriptors read through HostPatchIO).
+// Work-list construction (precision-independent; descriptors read through HostPatchIO): the tiles of
+// npatch patches -- patches 0 .. npatch-1, or d_idx[0 .. npatch-1] of d_patches when d_idx is given
+// (the records carry the patch's own index).  d_counts: npatch + 1 ints of scratch.
 cudaError_t build_worklist(const HostPatchIO* d_patches, int npatch, int tx, int ty, int zchunk, int* d_counts,
-                           HostTileRec* d_tiles, cudaStream_t s);
+                           HostTileRec* d_tiles, cudaStream_t s, const int* d_idx = nullptr);
 
 }  // namespace hydro

@@ -7,9 +7,11 @@
 
 namespace hydro {
 
-__global__ void k_tile_count(const HostPatchIO* patches, int npatch, int tx, int ty, int zc, int* counts) {
+// idx: nullptr (entry k is patch k) or the patches of the list (entry k is patch idx[k]).
+__global__ void k_tile_count(const HostPatchIO* patches, const int* idx, int npatch, int tx, int ty, int zc,
+                             int* counts) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npatch; p += gridDim.x * blockDim.x) {
-    const HostPatchIO& P = patches[p];
+    const HostPatchIO& P = patches[idx ? idx[p] : p];
     counts[p] = ((P.nx + tx - 1) / tx) * ((P.ny + ty - 1) / ty) * ((P.nz + zc - 1) / zc);
   }
 }
@@ -39,24 +41,26 @@ __global__ void __launch_bounds__(1024) k_scan(int* counts, int n) {
   if (t == 1023) counts[n] = part[1023];
 }
 
-__global__ void k_tile_fill(const HostPatchIO* patches, int npatch, int tx, int ty, int zc, const int* offsets,
-                            HostTileRec* tiles) {
+__global__ void k_tile_fill(const HostPatchIO* patches, const int* idx, int npatch, int tx, int ty, int zc,
+                            const int* offsets, HostTileRec* tiles) {
   for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
-    const HostPatchIO& P = patches[p];
+    const int pid = idx ? idx[p] : p;
+    const HostPatchIO& P = patches[pid];
     const int ntx = (P.nx + tx - 1) / tx, nty = (P.ny + ty - 1) / ty, nzc = (P.nz + zc - 1) / zc;
     const int n = ntx * nty * nzc, base = offsets[p];
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const int ix = t % ntx, iy = (t / ntx) % nty, iz = t / (ntx * nty);
-      tiles[base + t] = HostTileRec{p, ix * tx, iy * ty, iz * zc};
+      tiles[base + t] = HostTileRec{pid, ix * tx, iy * ty, iz * zc};
     }
   }
 }
 
 cudaError_t build_worklist(const HostPatchIO* d_patches, int npatch, int tx, int ty, int zchunk, int* d_counts,
-                           HostTileRec* d_tiles, cudaStream_t s) {
-  k_tile_count<<<(npatch + 255) / 256, 256, 0, s>>>(d_patches, npatch, tx, ty, zchunk, d_counts);
+                           HostTileRec* d_tiles, cudaStream_t s, const int* d_idx) {
+  k_tile_count<<<(npatch + 255) / 256, 256, 0, s>>>(d_patches, d_idx, npatch, tx, ty, zchunk, d_counts);
   k_scan<<<1, 1024, 0, s>>>(d_counts, npatch);
-  k_tile_fill<<<npatch < 4096 ? npatch : 4096, 128, 0, s>>>(d_patches, npatch, tx, ty, zchunk, d_counts, d_tiles);
+  k_tile_fill<<<npatch < 4096 ? npatch : 4096, 128, 0, s>>>(d_patches, d_idx, npatch, tx, ty, zchunk, d_counts,
+                                                            d_tiles);
   return cudaGetLastError();
 }
 

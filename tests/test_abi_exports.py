@@ -149,3 +149,4 @@ def test_tile_shapes_agree_across_header_library_and_binding():
     xs = [int(v) for v in re.search(r"kTileX\[kNumTiles\] = \{([^}]*)\}", src).group(1).split(",")]
     ys = [int(v) for v in re.search(r"kTileY\[kNumTiles\] = \{([^}]*)\}", src).group(1).split(",")]
     assert tuple(zip(xs, ys)) == hy.TILE_SHAPES
+    assert int(re.search(r"#define HYDRO_NUM_PATCH_CLASSES (\d+)", hdr).group(1)) == hy.NUM_PATCH_CLASSES

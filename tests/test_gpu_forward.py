@@ -452,16 +452,18 @@ def test_writes_stay_inside_the_output_interior(precision):
 def test_double_float_exponent_range():
     """The double-float policy keeps the exponent range of float (include/hydro.h at HYDRO_FP64_DF).
     The step is scale-covariant (U -> a U scales every flux and update by a, floors scaled alike), so
-    the oracle's step of U, times a, is the step of a U: at a = 1e-20 (densities ~1e-20, pressures
-    ~1e-24, well inside the range) double-float still matches it within 1e-12, as FP64 does; at
+    the oracle's step of U, times a, is the step of a U: at a = 1e-10 and 1e12 (momentum squares
+    ~1e-23 and ~1e22, inside the range) double-float matches it within 1e-12, as FP64 does; at
     a = 1e25 the momentum squares (~1e47) overflow float, and the step flags HYDRO_EBIT_NONFINITE
-    instead of returning silent garbage, while native FP64 steps it to the scaled oracle result."""
+    instead of returning silent garbage, while native FP64 steps it to the scaled oracle result.
+    (Below the range, e.g. a = 1e-20, the squares ~1e-43 underflow and lose their precision: the
+    step then is neither FP64-accurate nor guaranteed to flag.)"""
     U = workloads.turbulent_state((12, 16, 20), seed=2, mach=5.0, sedov=False).numpy()
     dx = 1.0 / 20
     dt = 0.5 * oracle.cfl_periodic(U, dx, ocfg())  # the same for a U: velocities and sound speeds keep
     o = oracle.step_periodic(U, dx, dt, ocfg())
-    for a, precision, ok in ((1e-20, "df64", True), (1e-20, "fp64", True), (1e25, "fp64", True),
-                             (1e25, "df64", False)):
+    for a, precision, ok in ((1e-10, "df64", True), (1e12, "df64", True), (1e-10, "fp64", True),
+                             (1e25, "fp64", True), (1e25, "df64", False)):
         c = ctx(precision, rho_floor=1e-10 * a, p_floor=1e-14 * a)
         g, _ = step_periodic(c, a * U, dx, dt)
         rc, bits = hy.hydro_get_error(c)
@@ -471,3 +473,52 @@ def test_double_float_exponent_range():
         else:
             assert bits & hy.EBIT_NONFINITE, (a, precision, bits)
         hy.hydro_finalize(c)
+
+
+@pytest.mark.parametrize("precision", ALL)
+def test_tile_shape_per_patch_class(precision, tmp_path):
+    """A batch with patches of all three patch-shape classes (an x or y edge of 8; an edge of 24 or 40;
+    edges multiples of 16), each class stepped with its own tile shape and z chunk (one persistent
+    launch per class, each over its own work-list segment), against the oracle, with the fused dt
+    equal to the standalone CFL's bits; hydro_set_tuning puts every class back on the context's
+    tuning; the autotuner's choice, per class included, comes back from its cache file."""
+    dtype = torch.float32 if precision == "fp32" else torch.float64
+    tol = TOL64 if precision in F64 else TOL32
+    host, ins, outs = _patch_batch(30, 12, precision, dtype, edges=(8, 16, 24, 32, 40))
+
+    def klass(d):
+        nx, ny = d["nx"], d["ny"]
+        return 0 if min(nx, ny) <= 8 else (1 if nx % 16 or ny % 16 else 2)
+
+    assert {klass(d) for _, d in host} == {0, 1, 2}
+    c = ctx(precision)
+    for k, (t, z) in enumerate([(2, 8), (1, 5), (3, 16)]):
+        hy.hydro_set_class_tuning(c, k, t, z)
+    assert hy.hydro_get_class_tuning(c, 1) == (1, 5)
+    dt_list = [0.7 * oracle.cfl_patch(Ug, d["dx"], ocfg()) for Ug, d in host]
+    dn = torch.empty(len(host), dtype=torch.float64, device="cuda")
+    hy.hydro_step(c, ins, outs, dts(*dt_list), dn)
+    l0 = hy.hydro_launch_count(c)
+    hy.hydro_step(c, ins, outs, dts(*dt_list), dn)  # the work-list cached: one launch per class
+    assert hy.hydro_launch_count(c) - l0 == 3
+    torch.cuda.synchronize()
+    for (Ug, d), po, dtp in zip(host, outs, dt_list):
+        out = torch.stack(po.tensors).double().cpu().numpy()[:, 2:-2, 2:-2, 2:-2]
+        Ur = Ug.astype(np.float32).astype(np.float64) if precision == "fp32" else Ug
+        assert normwise(out, oracle.step_patch(Ur, d["dx"], dtp, ocfg())).max() <= tol, d
+    dn2 = torch.empty_like(dn)
+    hy.hydro_cfl_dt(c, outs, dn2)
+    torch.cuda.synchronize()
+    assert torch.equal(dn, dn2)
+    hy.hydro_set_tuning(c, 0, 8)
+    assert all(hy.hydro_get_class_tuning(c, k) == (0, 8) for k in range(hy.NUM_PATCH_CLASSES))
+    with pytest.raises(hy.HydroError):
+        hy.hydro_set_class_tuning(c, hy.NUM_PATCH_CLASSES, 0, 8)
+    cache = str(tmp_path / "tuning.txt")
+    hy.hydro_autotune(c, ins, outs, dts(*dt_list), cache_path=cache)
+    tuned = [hy.hydro_get_class_tuning(c, k) for k in range(hy.NUM_PATCH_CLASSES)]
+    c2 = ctx(precision)
+    hy.hydro_autotune(c2, ins, outs, dts(*dt_list), cache_path=cache)
+    assert [hy.hydro_get_class_tuning(c2, k) for k in range(hy.NUM_PATCH_CLASSES)] == tuned
+    assert hy.hydro_get_tuning(c2) == hy.hydro_get_tuning(c)
+    check_clean(c)
