@@ -339,10 +339,33 @@ __device__ __forceinline__ R block_max_r(R v) {
   return v;
 }
 
+// The update of cell a from its flux divergence div (x, y, z summed in that order), psi damping, and
+// the CFL speed of the new state folded into smax when dt_next is wanted.
+template <class Pol>
+__device__ __forceinline__ void mhd_update_cell(const MhdBox<Pol>& B, long long a, const MhdConst<typename Pol::R>& c,
+                                                const typename Pol::R div[NV], bool want_cfl, unsigned& flags,
+                                                typename Pol::R& smax) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  S Un[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Un[v] = Pol::update(__ldg(B.in[v] + a), c.dtdx, div[v]);
+  Un[8] = Un[8] * (S)to_double(c.damp);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) B.out[v][a] = Un[v];
+  if (want_cfl) {
+    R U[NV], q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
+    mhd_recover(U, c, q, flags);
+    const R s = mhd_speed(q, c);
+    smax = s > smax ? s : smax;
+  }
+}
+
 template <class Pol>
 __global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl,
                                                     double dx, double* dt_next, unsigned* err) {
-  using S = typename Pol::S;
   using R = typename Pol::R;
   const MhdConst<R> c = *cp;
   if (!c.valid) return;
@@ -356,26 +379,81 @@ __global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdC
     const long long bx = a + (i == B.nx - 1 ? -(B.nx - 1) : 1);
     const long long by = a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy);
     const long long bz = a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz);
-    S Un[NV];
+    R div[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R* fx = B.flux + (long long)(0 * NV + v) * B.cells;
       const R* fy = B.flux + (long long)(1 * NV + v) * B.cells;
       const R* fz = B.flux + (long long)(2 * NV + v) * B.cells;
-      const R div = ((fx[bx] - fx[a]) + (fy[by] - fy[a])) + (fz[bz] - fz[a]);
-      Un[v] = Pol::update(__ldg(B.in[v] + a), c.dtdx, div);
+      div[v] = ((fx[bx] - fx[a]) + (fy[by] - fy[a])) + (fz[bz] - fz[a]);
     }
-    Un[8] = Un[8] * (S)to_double(c.damp);
+    mhd_update_cell(B, a, c, div, dt_next != nullptr, flags, smax);
+  }
+  if (dt_next) {
+    const R m = block_max_r(smax);
+    if (threadIdx.x == 0) publish_dt(cfl, dx, to_double(m), dt_next);
+  }
+  flush_flags(flags, err);
+}
+
+// Flux through the face between cell lo (its high face state along D) and cell hi (its low one).
+template <int D, class Pol>
+__device__ __forceinline__ void face_flux_between(const MhdBox<Pol>& B, long long lo, long long hi,
+                                                  const MhdConst<typename Pol::R>& c, typename Pol::R F[NV]) {
+  using R = typename Pol::R;
+  R qL[NV], qR[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) B.out[v][a] = Un[v];
-    if (dt_next) {
-      R U[NV], q[NV];
+  for (int v = 0; v < NV; ++v) {
+    qL[v] = B.face[((long long)(2 * D + 1) * NV + v) * B.cells + lo];
+    qR[v] = B.face[((long long)(2 * D) * NV + v) * B.cells + hi];
+  }
+  mhd_hll<D>(qL, qR, c, F);
+}
+
+// Fluxes and update in one pass, for float arithmetic: each cell forms the HLL fluxes through all
+// six of its faces from the face states (every face twice, once by each of its cells) instead of
+// writing the fluxes of its three low faces to scratch and reading them back with its neighbours'
+// -- the same flux bits, the same sums, less scratch traffic (the float step streams its scratch
+// at most of the HBM bandwidth; the 8-byte policies are bound by arithmetic and keep the two passes).
+template <class Pol>
+__global__ void __launch_bounds__(256, 2) k_mhd_flux_update(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp,
+                                                         double cfl, double dx, double* dt_next, unsigned* err) {
+  using R = typename Pol::R;
+  const MhdConst<R> c = *cp;
+  if (!c.valid) return;
+  unsigned flags = 0;
+  R smax = R(0);
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
+       a += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(a, B.nx, B.ny, i, j, k);
+    const long long sy = B.nx, sz = (long long)B.nx * B.ny;
+    R d[3][NV];
+    {
+      R Fl[NV], Fh[NV];
+      face_flux_between<0>(B, a + (i == 0 ? B.nx - 1 : -1), a, c, Fl);
+      face_flux_between<0>(B, a, a + (i == B.nx - 1 ? -(B.nx - 1) : 1), c, Fh);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
-      mhd_recover(U, c, q, flags);
-      const R s = mhd_speed(q, c);
-      smax = s > smax ? s : smax;
+      for (int v = 0; v < NV; ++v) d[0][v] = Fh[v] - Fl[v];
     }
+    {
+      R Fl[NV], Fh[NV];
+      face_flux_between<1>(B, a + (j == 0 ? (B.ny - 1) * sy : -sy), a, c, Fl);
+      face_flux_between<1>(B, a, a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy), c, Fh);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) d[1][v] = Fh[v] - Fl[v];
+    }
+    {
+      R Fl[NV], Fh[NV];
+      face_flux_between<2>(B, a + (k == 0 ? (B.nz - 1) * sz : -sz), a, c, Fl);
+      face_flux_between<2>(B, a, a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz), c, Fh);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) d[2][v] = Fh[v] - Fl[v];
+    }
+    R div[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) div[v] = (d[0][v] + d[1][v]) + d[2][v];
+    mhd_update_cell(B, a, c, div, dt_next != nullptr, flags, smax);
   }
   if (dt_next) {
     const R m = block_max_r(smax);
@@ -471,8 +549,12 @@ cudaError_t mhd_step_t(const HostMhdBox& h, const Params& prm, const double* dt,
   k_mhd_consts<R><<<1, 1, 0, s>>>(consts_of<R>(prm), prm.cfl, h.dx, kMhdAlpha, dt, cp, err);
   const int g = grid_for(B.cells);
   k_mhd_predict<Pol><<<g, 256, 0, s>>>(B, cp, err);
-  k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
-  k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
+  if constexpr (kSlopesInRegs<R>) {
+    k_mhd_flux_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
+  } else {
+    k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
+    k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
+  }
   return cudaGetLastError();
 }
 
