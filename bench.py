@@ -8,10 +8,14 @@ input, fused into the previous step's epilogue (device-resident, no host sync pe
 state (5.4 GB in FP64) is far larger than L2, so no flush is needed between steps.
 
 Prints one JSON line: value = interior cells x steps / time (Mcell-updates/s, whole job), the
-roofline of the step kernel (algorithmic bytes or flops per launch / CUDA-event duration), the
+roofline of the step kernel (the method's algorithmic bytes and flops per launch / CUDA-event
+duration, against the measured HBM and the arithmetic peak of the pipe that runs them), the
 clocks seen during the timed region, an end-to-end number through the C ABI with host buffers,
-the CPU oracle as a reported baseline, and the other forms (FP32, mixed-precision batched AMR
-patches and oct groups, adjoint/forward ratio, 1024^3 graph-captured run) beside it.
+the CPU oracle as a reported baseline, the other forms (native FP64, FP32, mixed, mixed-precision
+batched AMR patches and oct groups, PPM, MHD, the two-level AMR cycle, adjoint/forward ratios,
+1024^3 graph-captured run) beside it, and for the headline and every form the error of one more
+step against the FP64 oracle on sampled cells, patches or oct groups (err_vs_oracle; the oracle
+runs in the CPU oracle leg, rank 0, after every timed region).
 
 The headline step runs in double-float arithmetic (--precision df64): the double state with every
 operation of the scheme on pairs of floats, which meets the FP64 parity bar and runs on the FP32
