@@ -111,7 +111,7 @@ def _loss_setup(n, amp=1e-3):
 
 
 @pytest.mark.parametrize("precision,limiter,eps,tol", [("fp64", "none", 1e-6, 1e-6), ("fp64", "minmod", 1e-8, 1e-5),
-                                                       ("df64", "minmod", 1e-8, 1e-5)])
+                                                       ("fp64", "minmod", 1e-6, 1e-4), ("df64", "minmod", 1e-8, 1e-5)])
 def test_checkpointed_gradient_64cube_40steps_vs_central_differences(precision, limiter, eps, tol):
     """Loss sum (rho_40 - rho_target)^2 on the 64^3 periodic grid, 40 steps, checkpoint every 8;
     gradient w.r.t. rho0 and v0 against central differences over 64 random directions,
@@ -119,7 +119,8 @@ def test_checkpointed_gradient_64cube_40steps_vs_central_differences(precision, 
     kinks (a*b = 0 near every extremum of the wave): central differences measure a derivative only
     along directions where the loss is smooth at the scale eps, which a second difference at eps/2
     detects; directions that cross a kink are counted (they must be a minority) and the rest must
-    agree."""
+    agree: within 1e-5 at eps = 1e-8, and within 1e-4 at the configuration's eps = 1e-6 (kinks
+    crossed inside a direction's smooth-looking stretch add O(eps) to the difference)."""
     n, nsteps = 64, 40
     c = ctx(precision, limiter)
     q, target = _loss_setup(n)
