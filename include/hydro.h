@@ -87,6 +87,9 @@ typedef enum { HYDRO_MINMOD = 0, HYDRO_MC = 1, HYDRO_NOLIMIT = 2, HYDRO_PPM = 3 
 #define HYDRO_EBIT_BAD_DT 0x08u    /* a step was given dt <= 0 or non-finite (no update done) */
 #define HYDRO_EBIT_BAD_TILE 0x10u  /* a work-list record pointed outside its patch */
 #define HYDRO_EBIT_TIMEOUT 0x20u   /* a bounded device wait gave up */
+#define HYDRO_EBIT_OOB 0x40u       /* bounds-checked build only (HYDRO_CHECK_BOUNDS): a step kernel
+                                      computed a global index outside its patch's array; that
+                                      access was skipped.  Never set by the default build. */
 
 typedef struct {
   double gamma;      /* ratio of specific heats, > 1 */

@@ -14,7 +14,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhydro.so")
+# The library: the in-tree build, or the build the environment variable HYDRO_LIBRARY names (the
+# bounds-checked variant libhydro_checked.so, for instance).
+LIB_PATH = os.environ.get("HYDRO_LIBRARY") or os.path.join(_HERE, "libhydro.so")
 
 HYDRO_OK = 0
 HYDRO_ERR_ARG = -1
@@ -41,6 +43,7 @@ EBIT_P_FLOOR = 0x04
 EBIT_BAD_DT = 0x08
 EBIT_BAD_TILE = 0x10
 EBIT_TIMEOUT = 0x20
+EBIT_OOB = 0x40
 
 # C symbols that include/hydro.h declares (checked by the tests).
 EXPORTS = ("hydro_init", "hydro_finalize", "hydro_cfl_dt", "hydro_step", "hydro_step_host", "hydro_step_octs",

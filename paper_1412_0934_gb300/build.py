@@ -42,14 +42,19 @@ def _compile(src, obj, verbose, extra):
     return r.stderr
 
 
-def build(force=False, verbose=False, ptxas_info=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, ptxas_info=False, checked=False):
+    """Build libhydro.so, or with checked=True the bounds-checked variant libhydro_checked.so (every
+    global index of the step kernels tested against its array's extent: HYDRO_EBIT_OOB), loaded
+    instead of the default library when the environment variable HYDRO_LIBRARY names it."""
+    bdir = BUILD + ("_checked" if checked else "")
+    lib = LIB.replace("libhydro.so", "libhydro_checked.so") if checked else LIB
+    os.makedirs(bdir, exist_ok=True)
     hdr_time = _newest(_headers())
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DHYDRO_CHECK_BOUNDS"] if checked else [])
     jobs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(obj)
         if force or ptxas_info or not os.path.exists(obj) or os.path.getmtime(obj) < max(
                 hdr_time, os.path.getmtime(os.path.join(CSRC, src))):
@@ -60,14 +65,14 @@ def build(force=False, verbose=False, ptxas_info=False):
             futs = {ex.submit(_compile, s, o, verbose, extra): s for s, o in jobs}
             for f in concurrent.futures.as_completed(futs):
                 logs[futs[f]] = f.result()
-    if jobs or force or not os.path.exists(LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if jobs or force or not os.path.exists(lib):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB, logs
+        os.replace(tmp, lib)
+    return lib, logs
 
 
 if __name__ == "__main__":

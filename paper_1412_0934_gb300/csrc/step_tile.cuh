@@ -196,6 +196,22 @@ __device__ __forceinline__ void face_flux_dyn(TileShared<Pol, TX, TY>& sm, int d
   hllc_dyn(d, qL, qR, kc<R>(prm, K_GAMMA), kc<R>(prm, K_IGM1), F);
 }
 
+// Bounds-checked build (compiled with -DHYDRO_CHECK_BOUNDS; the library's default build has no
+// checks): every global index of the step is tested against the extent of its patch's array,
+// (nz + 2 ghost layers) z strides, before the access; an index outside sets HYDRO_EBIT_OOB and the
+// access is skipped (a load then reads zero).
+#ifdef HYDRO_CHECK_BOUNDS
+constexpr bool kCheckBounds = true;
+#else
+constexpr bool kCheckBounds = false;
+#endif
+__device__ __forceinline__ bool index_ok(long long a, long long extent, unsigned& flags) {
+  if (!kCheckBounds) return true;
+  const bool ok = a >= 0 && a < extent;
+  if (!ok) flags |= HYDRO_EBIT_OOB;
+  return ok;
+}
+
 // Two x-adjacent stored values at an even, vector-aligned address (one 16-byte load for double,
 // 8-byte for float), read through the read-only path.
 __device__ __forceinline__ void ldg_pair(const double* p, double& a, double& b) {
@@ -252,14 +268,25 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
   // tile's edge faces.  A pair adjacent in memory (pairok: no wrap or clamp between its columns, the
   // first column even) is read with one vector load per field, else with two.
   constexpr int QP = QW / 2, QNP = QH * QP;
+  const long long in_extent = (long long)(P.nz + 2 * P.gin) * P.isz;
   auto fetch_pair = [&](long long zo, int c, S U0[5], S U1[5]) {
     const int cy = c / QP, px = c - cy * QP;
     const long long a = zo + sm.yoff[cy] + sm.xoff[2 * px];
     if (sm.pairok[px]) {
+      if (!index_ok(a, in_extent, flags) || !index_ok(a + 1, in_extent, flags)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) U0[v] = U1[v] = S(0);
+        return;
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) ldg_pair(P.in[v] + a, U0[v], U1[v]);
     } else {
       const long long a1 = zo + sm.yoff[cy] + sm.xoff[2 * px + 1];
+      if (!index_ok(a, in_extent, flags) || !index_ok(a1, in_extent, flags)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) U0[v] = U1[v] = S(0);
+        return;
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         U0[v] = __ldg(P.in[v] + a);
@@ -346,6 +373,7 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     if (own) {
       const long long ai = (long long)(k + P.gin) * P.isz + (long long)(gy + P.gin) * P.isy + (gx + P.gin);
       const long long ao = (long long)(k + P.gout) * P.osz + (long long)(gy + P.gout) * P.osy + (gx + P.gout);
+      if (!index_ok(ai, in_extent, flags) || !index_ok(ao, (long long)(P.nz + 2 * P.gout) * P.osz, flags)) return;
       S Un[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
