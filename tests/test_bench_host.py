@@ -61,6 +61,15 @@ def test_job_value_counts_every_rank_over_the_slowest():
     assert math.isclose(bench.job_time_ms(12.5, 1, "cpu"), 12.5)
 
 
+def test_e2e_summary_median_and_mean_of_the_step_times():
+    # 1e6 cells; steps of 10 ms with one 100 ms stall: the median step gives 100 Mcell/s, the mean 50
+    e = bench.e2e_summary([10.0, 10.0, 100.0] + [10.0] * 9, 1e6)
+    assert e["steps"] == 12 and e["ms_per_step_median"] == 10.0 and e["ms_per_step_max"] == 100.0
+    assert e["value"] == pytest.approx(100.0) and e["mean_value"] == pytest.approx(1e6 / 17.5 / 1e3)
+    e = bench.e2e_summary([4.0, 2.0, 6.0, 8.0], 1e6)      # even count: the mean of the two middle steps
+    assert e["ms_per_step_median"] == 5.0 and e["value"] == pytest.approx(200.0)
+
+
 def _run_bench(args, env_extra):
     import json
     import os
