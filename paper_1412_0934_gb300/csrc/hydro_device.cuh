@@ -561,15 +561,74 @@ __device__ __forceinline__ double PolF64::speed(const double U[5], const Params&
   recover(U, P, q, flags);
   return cfl_speed(q, P.kd[K_GAMMA]);
 }
+// The mixed policy's arithmetic is float, and so is the accuracy its dt needs: each field is rounded
+// to float by its IEEE bit fields (fields outside [2^-40, 2^40), other than zero, take the pair
+// recovery instead) and recovered plainly in float.
+__device__ __forceinline__ float round_float(double x, bool& ok) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned ex = (h >> 20) & 0x7FFu;
+  const bool zero = (h & 0x7FFFFFFFu) == 0u && l == 0u;
+  ok = ok && (zero || ex - 983u < 80u);
+  const unsigned b = (h & 0x80000000u) | ((ex - 896u) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29);
+  return zero ? 0.f : __uint_as_float(b + ((l >> 28) & 1u));  // round half away from zero
+}
 __device__ __forceinline__ float PolMixed::speed(const double U[5], const Params& P, unsigned& flags) {
-  float q[5];
-  recover(U, P, q, flags);
-  return cfl_speed(q, P.kf[K_GAMMA]);
+  bool ok = true;
+  float f[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] = round_float(U[v], ok);
+  if (!ok) {
+    float q[5];
+    recover(U, P, q, flags);
+    return cfl_speed(q, P.kf[K_GAMMA]);
+  }
+  float rho = f[0];
+  const float rf = P.kf[K_RHOF];
+  if (rho < rf) { flags |= HYDRO_EBIT_RHO_FLOOR; rho = rf; }
+  const float ir = rcp_(rho);
+  const float u = f[1] * ir, v = f[2] * ir, w = f[3] * ir;
+  const float eint = f[4] - 0.5f * rho * ((u * u + v * v) + w * w);
+  if (eint < 0.f) flags |= HYDRO_EBIT_P_FLOOR;
+  float p = P.kf[K_GM1] * eint;
+  const float pf = P.kf[K_PF];
+  p = p < pf ? pf : p;
+  const float c = rsqrt_(P.kf[K_GAMMA] * p * ir);
+  return ((fabsf(u) + fabsf(v)) + fabsf(w)) + 3.0f * c;
 }
 __device__ __forceinline__ df PolDF::speed(const double U[5], const Params& P, unsigned& flags) {
   df q[5];
   recover(U, P, q, flags);
   return cfl_speed(q, kc<df>(P, K_GAMMA));
+}
+
+// ------------------------------------------------------------------ CFL candidates
+// A float estimate of the CFL speed of a double state, with which the step's fused CFL maximum
+// skips the exact speed of cells that cannot hold it.  Each field is cut to the float of its
+// leading 24 significant bits (relative error below 2^-23), recovered in float with the SFU
+// reciprocal and square root.  Returns false -- the cell then takes the exact speed -- unless every
+// field is zero or of magnitude in [2^-40, 2^40), the density exceeds twice its floor and the
+// internal energy exceeds 1e-3 of E + |m|^2/(2 rho).  When it returns true the exact recovery floors
+// nothing and flags nothing, the float internal energy is within ~1.1e-6 (E + |m|^2/(2 rho)), i.e.
+// 1.1e-3 of itself, so the sound speed is within ~6e-4 and s within 1e-3 of the exact speed.
+__device__ __forceinline__ float cut_float(double x, bool& ok) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned ex = (h >> 20) & 0x7FFu;
+  const bool zero = (h & 0x7FFFFFFFu) == 0u && l == 0u;
+  ok = ok && (zero || ex - 983u < 80u);
+  return zero ? 0.f : __uint_as_float((h & 0x80000000u) | ((ex - 896u) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+}
+__device__ __forceinline__ bool speed_estimate(const double U[5], const Params& P, float& s) {
+  bool ok = true;
+  const float r = cut_float(U[0], ok), mx = cut_float(U[1], ok), my = cut_float(U[2], ok);
+  const float mz = cut_float(U[3], ok), e = cut_float(U[4], ok);
+  const float ir = rcp_(r);
+  const float kin = 0.5f * (((mx * mx + my * my) + mz * mz) * ir);
+  const float eint = e - kin;
+  ok = ok && r > 2.f * P.kf[K_RHOF] && eint > 1e-3f * (e + kin);
+  float p = P.kf[K_GM1] * eint;
+  p = p < P.kf[K_PF] ? P.kf[K_PF] : p;
+  s = ((fabsf(mx) + fabsf(my)) + fabsf(mz)) * ir + 3.f * rsqrt_(P.kf[K_GAMMA] * p * ir);
+  return ok;
 }
 
 }  // namespace hydro

@@ -12,6 +12,10 @@
 //   2  HLLC fluxes of the x and y faces of plane p (each face once), and the load of U of plane
 //      p+2 over the tile plus 2 halo cells per side, recovered to q into the ring
 // Global memory is read once per cell per plane (halo re-reads come from L2) and written once.
+// In double-float arithmetic with one block per SM (32x16 tiles, or the one-block build), the
+// ring cells' predictions of phase 1 overlap the interior faces of phase 2 through named barriers:
+// the ring warps signal that their tile cells are predicted, predict the ring, and take the faces
+// between ring and tile, while the other warps take the faces between tile cells and the load.
 #pragma once
 #include <type_traits>
 
@@ -225,8 +229,27 @@ __device__ __forceinline__ void ldg_pair(const float* p, float& a, float& b) {
   b = t.y;
 }
 
+// Named block barriers 1-3 (0 is __syncthreads), in their non-aligned form: a thread that arrives does
+// not wait; a thread that syncs waits until `count` threads have arrived (arrive or sync).  Memory
+// accesses before an arrive or a sync are visible to the threads that return from the sync.
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("barrier.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Resident blocks per SM the register allocation must allow: 2 x 256 threads for 8-byte
+// arithmetic (its shared memory allows 2), 3 x 256 for float arithmetic (4 x 256, a 64-register
+// budget, spills more than the extra warps gain: measured -8% for FP32, 0..-2% for mixed).
+template <class Pol, int NT, int MINB>
+constexpr int min_blocks() {
+  constexpr int b = (sizeof(typename Pol::R) >= 8 ? 2 : 3) * 256 / NT;
+  return MINB > 0 ? MINB : (b < 1 ? 1 : b);
+}
+
 // Advances the tile; returns (through smax) the largest CFL speed of the updated cells.
-template <int LIM, class Pol, int TX, int TY>
+template <int LIM, int MINB, class Pol, int TX, int TY>
 __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Pol::S>& P, int x0, int y0, int z0,
                           int z1, const Params& prm, double dt, bool want_cfl, unsigned& flags,
                           typename Pol::R& smax) {
@@ -341,8 +364,10 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
   const bool own = (gx < P.nx) && (gy < P.ny);
   const R gamma = kc<R>(prm, K_GAMMA);
 
-  // Carried across planes: the lower z state of the next face, and the flux through the lower z
-  // face of the plane awaiting its update.
+  // Carried across planes: the lower z state of the next face, the flux through the lower z face of
+  // the plane awaiting its update, and the warp's running maximum of the sure CFL speed estimates.
+  constexpr bool kEstimate = std::is_same<R, double>::value;
+  float thr = 0.f;
   R LzPrev[5], FzPrev[5], Fz[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) { LzPrev[v] = FzPrev[v] = Fz[v] = R(0); }
@@ -370,18 +395,46 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     sm.fy.ld(tj, ti, ym);
 #pragma unroll
     for (int v = 0; v < 5; ++v) dF[v] = (xp[v] - xm[v]) + (yp[v] - ym[v]);
-    if (own) {
+    // the updated cell of this column, written to the output; false where the column lies outside
+    // the patch (or, in the bounds-checked build, an index lies outside its array)
+    auto write_cell = [&](S Un[5]) -> bool {
+      if (!own) return false;
       const long long ai = (long long)(k + P.gin) * P.isz + (long long)(gy + P.gin) * P.isy + (gx + P.gin);
       const long long ao = (long long)(k + P.gout) * P.osz + (long long)(gy + P.gout) * P.osy + (gx + P.gout);
-      if (!index_ok(ai, in_extent, flags) || !index_ok(ao, (long long)(P.nz + 2 * P.gout) * P.osz, flags)) return;
-      S Un[5];
+      if (!index_ok(ai, in_extent, flags) || !index_ok(ao, (long long)(P.nz + 2 * P.gout) * P.osz, flags)) return false;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const R div = (dF[v] - FzPrev[v]) + Fz[v];
         Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, div);
         P.out[v][ao] = Un[v];
       }
-      if (want_cfl) {
+      return true;
+    };
+    S Un[5];
+    if constexpr (!kEstimate) {
+      if (write_cell(Un) && want_cfl) {
+        const R sp = Pol::speed(Un, prm, flags);
+        smax = sp > smax ? sp : smax;
+      }
+    } else {
+      bool have = write_cell(Un);
+      if (!want_cfl) return;
+      // CFL maximum of the updated cells.  In double arithmetic the exact speed occupies the narrow
+      // FP64 pipe: every cell first takes the float estimate speed_estimate (FP32 and integer
+      // pipes), the warp keeps the running maximum T of the estimates it is sure of, and only cells
+      // whose estimate is unsure or at least 0.99 T take the exact speed.  The cell with the tile's
+      // largest exact speed always does (its estimate is at least 0.999 of that speed, T at most
+      // 1.001 of it), so the maximum, the dt and the flags are those of taking every cell's exact
+      // speed.  (+6.5% for the FP64 step at 512^3; the double-float step, whose exact speed runs on
+      // the FP32 pipes like the estimate, lost 4.7% with it.)
+      float se = 0.f;
+      bool sure = true;
+      if (have) sure = speed_estimate(Un, prm, se);
+      float w = sure ? se : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
+      thr = fmaxf(thr, w);
+      if (have && (!sure || se >= 0.99f * thr)) {
         const R sp = Pol::speed(Un, prm, flags);
         smax = sp > smax ? sp : smax;
       }
@@ -395,6 +448,15 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
   };
   constexpr int NR = 2 * (TX + TY);  // ring cells
   constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+  // Double-float: the ring cells go to the last RW warps (whole warps, for the split barriers);
+  // NIX + NIY faces lie between two tile cells.  The split barriers pay where a block is alone on
+  // its SM (512 threads, or the one-block-per-SM build): with two resident blocks the other block
+  // already fills the barrier waits, and interleaving the predictor with the faces costs more
+  // (measured at 16x16: 37.0 vs 31.7 ms per 512^3 step; at 32x16: 31.5 vs 32.7 ms).
+  constexpr bool kSplit = kCompact && min_blocks<Pol, NT, MINB>() == 1;
+  constexpr int RW = (NR + 31) / 32, NTI = kSplit ? NT - 32 * RW : NT - NR;
+  constexpr int NIX = (TX - 1) * TY, NIF = NIX + TX * (TY - 1);
+  const bool ringw = tid >= NTI;
 
   load_plane(z0 - 2);
   load_plane(z0 - 1);
@@ -412,19 +474,21 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     // ---- phase 1
     if constexpr (kCompact) {
       // One call site each for the predictor and the x/y face flux: double-float code is large
-      // enough that several inlined copies overflow the instruction cache.  The ring cells go
-      // to the last threads.
+      // enough that several inlined copies overflow the instruction cache.  The ring cells go to
+      // the last RW warps, which signal barrier 1 as soon as their tile cells are predicted and
+      // predict their ring cells while the other warps go on to the interior faces.
       for (int it = 0; it < 2; ++it) {
         int ci = ti, cj = tj;
         if (it == 1) {
-          if (!xy || tid < NT - NR) break;
-          ring_cell(tid - (NT - NR), ci, cj);
+          if (!xy || !ringw || (kSplit && tid - NTI >= NR)) break;
+          ring_cell(tid - NTI, ci, cj);
         }
         R qh[5], dqz[5];
         predict_cell<LIM>(sm, ci, cj, sm1, s0, sp1, prm, hdt, qh, dqz);
         if (it == 0) {
           z_faces(p, qh, dqz);
           if (upd) update(p - 1);
+          if (kSplit && xy && ringw) bar_arrive(1, NT);
         }
       }
     } else {
@@ -443,9 +507,58 @@ __device__ void step_tile(TileShared<Pol, TX, TY>& sm, const PatchIO<typename Po
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) FzPrev[v] = Fz[v];
+    const bool ld2 = p + 2 <= z1 + 1;
+    if (kSplit && xy) {
+      // Split barriers.  Barrier 1: every tile cell predicted (the ring warps arrive before their
+      // ring cells); barrier 2: the ring warps wait for it through the other warps' arrivals;
+      // barrier 3: the ring cells predicted, so that plane p-1's slot may be overwritten.
+      if (ringw) {
+        bar_arrive(3, NT);
+        bar_sync(2, NT);
+      } else {
+        bar_sync(1, NT);
+        bar_arrive(2, NT);
+      }
+      // ---- phase 2, double-float: the other warps take the faces between two tile cells, each
+      // ring thread the face between its ring cell and the tile (one call site for all of them)
+      const int r = tid - NTI;
+      int f = ringw ? NIF + r : tid;
+      const int fend = ringw ? NIF + NR : NIF;
+      const int fstep = ringw ? NR : NTI;
+      for (; f < fend; f += fstep) {
+        int d, i, j;
+        if (f < NIX) { d = 0; i = f % (TX - 1); j = f / (TX - 1); }
+        else if (f < NIF) { d = 1; i = (f - NIX) % TX; j = (f - NIX) / TX; }
+        else {
+          int ci, cj;
+          ring_cell(f - NIF, ci, cj);
+          d = (cj == -1 || cj == TY) ? 1 : 0;
+          i = d == 0 ? (ci < 0 ? -1 : TX - 1) : ci;
+          j = d == 1 ? (cj < 0 ? -1 : TY - 1) : cj;
+        }
+        R F[5];
+        face_flux_dyn(sm, d, i, j, prm, F);
+        if (d == 0) sm.fx.st(j, i + 1, F);
+        else sm.fy.st(j + 1, i, F);
+      }
+      // plane p+2 (an x/y plane is never the last one: p + 2 <= z1 + 1) into plane p-1's slot by
+      // the other warps, after barrier 3 (every thread of those warps syncs on it once per x/y
+      // plane, completing the ring warps' arrival)
+      if (!ringw) {
+        bar_sync(3, NT);
+        const int slot = ring_slot(p + 2);
+        const long long zo = plane_offset(p + 2);
+        for (int c = NTI - 1 - tid; ld2 && c < QNP; c += NTI) {
+          S U0[5], U1[5];
+          fetch_pair(zo, c, U0, U1);
+          store_pair(slot, c, U0, U1);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     __syncthreads();
     // ---- phase 2
-    const bool ld2 = p + 2 <= z1 + 1;
     if (kPrefetch && ld2) fetch_plane(p + 2);
     if (xy) {
       if constexpr (kCompact) {
@@ -516,15 +629,6 @@ __device__ __forceinline__ void publish_dt(double cfl, double dx, double smax, d
 }
 
 // ------------------------------------------------------------------ kernels
-// Resident blocks per SM the register allocation must allow: 2 x 256 threads for 8-byte
-// arithmetic (its shared memory allows 2), 3 x 256 for float arithmetic (4 x 256, a 64-register
-// budget, spills more than the extra warps gain: measured -8% for FP32, 0..-2% for mixed).
-template <class Pol, int NT, int MINB>
-constexpr int min_blocks() {
-  constexpr int b = (sizeof(typename Pol::R) >= 8 ? 2 : 3) * 256 / NT;
-  return MINB > 0 ? MINB : (b < 1 ? 1 : b);
-}
-
 // Uniform grid: one tile per block, tiles from the block index.
 template <class Pol, int TX, int TY, int MINB, int LIM>
 __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_step_uniform(PatchIO<typename Pol::S> P, Params prm, const double* dt_dev,
@@ -540,7 +644,7 @@ __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_
   const int z1 = min(z0 + zchunk, P.nz);
   unsigned flags = 0;
   typename Pol::R smax = 0;
-  step_tile<LIM>(sm, P, x0, y0, z0, z1, prm, dt, dt_next != nullptr, flags, smax);
+  step_tile<LIM, MINB>(sm, P, x0, y0, z0, z1, prm, dt, dt_next != nullptr, flags, smax);
   if (dt_next) {
     const auto m = block_max(sm, smax);
     if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next);
@@ -575,7 +679,7 @@ __global__ void __launch_bounds__(TX* TY, (min_blocks<Pol, TX * TY, MINB>())) k_
     }
     const int z1 = min(r.z0 + zchunk, P.nz);
     typename Pol::R smax = 0;
-    step_tile<LIM>(sm, P, r.x0, r.y0, r.z0, z1, prm, dt, dt_next != nullptr, flags, smax);
+    step_tile<LIM, MINB>(sm, P, r.x0, r.y0, r.z0, z1, prm, dt, dt_next != nullptr, flags, smax);
     if (dt_next) {
       const auto m = block_max(sm, smax);
       if (threadIdx.x == 0) publish_dt(prm.cfl, P.dx, (double)m, dt_next + r.patch);

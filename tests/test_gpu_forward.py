@@ -135,6 +135,59 @@ def test_fp64_cfl_matches_oracle_and_fused_is_bitwise(precision):
     check_clean(c)
 
 
+def _cfl_cases(shape, seed=4):
+    """States for the fused CFL maximum: near ties (a uniform flow whose speeds differ by ~1e-9),
+    cold fast gas (internal energy ~1e-9 of the kinetic: no float speed estimate is sure), a fast
+    jet (Mach ~80, internal energy ~3e-4 of the kinetic: unsure) holding the maximum inside warm gas
+    at the same pressure, and flow along x alone (zero y and z momenta in and out)."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    one = np.ones(shape)
+    cases = {}
+    cases["near_ties"] = (one, 0.5 + 1e-9 * rng.standard_normal(shape), 0.1 * one, -0.2 * one, one)
+    rho = np.exp(0.3 * rng.standard_normal(shape))
+    cases["cold_fast"] = (rho, 1.0 + 1e-7 * rng.standard_normal(shape), 0.3 + 1e-7 * rng.standard_normal(shape),
+                          -0.2 * one, 1e-9 * one)
+    u = 0.1 * rng.standard_normal(shape)
+    jet = (slice(nz // 3, nz // 3 + 2), slice(ny // 2, ny // 2 + 3), slice(None))
+    u[jet] = 100.0 + 1e-3 * rng.standard_normal(u[jet].shape)
+    cases["fast_jet"] = (one, u, 0.05 * rng.standard_normal(shape), 0.05 * rng.standard_normal(shape), one)
+    rx = np.exp(0.5 * rng.standard_normal(nx)) * one
+    ux = 0.5 * rng.standard_normal(nx) * one
+    cases["x_only"] = (rx, ux, 0 * one, 0 * one, one)
+    out = {}
+    for k, (r, vx, vy, vz, pr) in cases.items():
+        E = pr / (GAMMA_ - 1.0) + 0.5 * r * (vx * vx + vy * vy + vz * vz)
+        out[k] = np.stack([r, r * vx, r * vy, r * vz, E])
+    return out
+
+
+GAMMA_ = 5.0 / 3.0
+
+
+@pytest.mark.parametrize("precision", F64)
+def test_fused_cfl_max_on_near_ties_and_unsure_estimates(precision):
+    """The fused CFL of the FP64 step takes the exact speed only of cells whose float estimate is
+    unsure or near the warp's running maximum (double-float takes every cell's); on states built to
+    stress that choice (thousands of near ties, estimates unsure everywhere, an unsure cell holding
+    the maximum, zero momenta) the fused dt is, for every tile shape, the same bits as the
+    standalone CFL of the result and within 1e-13 of the oracle's CFL of it."""
+    shape = (10, 36, 40)
+    dx = 1.0 / shape[2]
+    c = ctx(precision)
+    for name, U in _cfl_cases(shape).items():
+        dt = 0.5 * oracle.cfl_periodic(U, dx, ocfg())
+        seen = set()
+        for tile in range(hy.NUM_TILES):
+            hy.hydro_set_tuning(c, tile, 4)
+            U1, dn = step_periodic(c, U, dx, dt, dt_next=True)
+            assert dn == cfl(c, U1, dx), (name, tile)
+            assert dn == pytest.approx(oracle.cfl_periodic(U1, dx, ocfg()), rel=1e-13), (name, tile)
+            seen.add(dn)
+        assert len(seen) == 1, (name, seen)
+        check_clean(c)
+
+
 @pytest.mark.parametrize("precision", F64)
 def test_fp64_ten_steps_config1(precision):
     """32^3, lognormal density (sigma 0.5), white velocities (0.3 c_s), P = 1, MinMod, CFL 0.8:
