@@ -584,7 +584,28 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   while (zc > 2 && I.nz / zc < 16) zc /= 2;
   // at least two planes per slab: a slab's upper halo (two planes) then lies in the next slab
   zc = std::max(std::min(2, I.nz), std::min(zc, I.nz));
-  const int S = (I.nz + zc - 1) / zc;
+  // Slab boundaries: zc planes each, but ramped at both ends (zc/4, zc/2, ..., zc/2, zc/4, each at
+  // least two planes) where the box is tall enough: the first step waits for the first slab and its
+  // halo to arrive, and the last copy-out waits for the last slab's step, so short end slabs cut
+  // the pipeline's fill and drain.
+  std::vector<int> zs;  // slab k covers planes [zs[k], zs[k+1])
+  {
+    const int a = std::max(2, zc / 4), b = std::max(2, zc / 2);
+    const int ends = 2 * (a + b);
+    zs.push_back(0);
+    if (zc >= 8 && I.nz >= ends + 2 * zc) {
+      for (int h : {a, b}) zs.push_back(zs.back() + h);
+      const int mid = I.nz - ends, nm = mid / zc, rem = mid - nm * zc;
+      for (int k = 0; k < nm; ++k) zs.push_back(zs.back() + zc);
+      if (rem >= 2) zs.push_back(zs.back() + rem);
+      else if (rem > 0) zs.back() += rem;  // one plane left over: the last middle slab takes it
+      for (int h : {b, a}) zs.push_back(zs.back() + h);
+    } else {
+      for (int z = zc; z < I.nz; z += zc) zs.push_back(z);
+      zs.push_back(I.nz);
+    }
+  }
+  const int S = (int)zs.size() - 1;
   const int tx = hydro::kTileX[c->tile_id], ty = hydro::kTileY[c->tile_id];
   const int ntx = (I.nx + tx - 1) / tx, nty = (I.ny + ty - 1) / ty, tps = ntx * nty;
   // staging, descriptors, tile list, counters, streams, events
@@ -644,7 +665,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
     std::vector<HostTileRec> t((size_t)S * tps);
     for (int k = 0; k < S; ++k)
       for (int j = 0; j < nty; ++j)
-        for (int i = 0; i < ntx; ++i) t[(size_t)k * tps + j * ntx + i] = HostTileRec{0, i * tx, j * ty, k * zc};
+        for (int i = 0; i < ntx; ++i) t[(size_t)k * tps + j * ntx + i] = HostTileRec{0, i * tx, j * ty, zs[k]};
     if (cudaMemcpy(c->d_stage_io, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_stage_tiles, t.data(), t.size() * sizeof(HostTileRec), cudaMemcpyHostToDevice) != cudaSuccess)
       return HYDRO_ERR_CUDA;
@@ -673,7 +694,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   const int tail = S > 1 ? std::max(0, I.nz - 2) : I.nz;
   if (!upload(tail, I.nz)) return HYDRO_ERR_CUDA;
   for (int k = 0; k < S; ++k) {
-    const int za = k * zc, zb = std::min(std::min(I.nz, za + zc), tail);
+    const int za = zs[k], zb = std::min(zs[k + 1], tail);
     // a slab's first two planes go first: with them the previous slab's step can start
     const int zh = std::min(za + 2, zb);
     if (!upload(za, zh) || cudaEventRecord(c->ev_halo[k], c->s_h2d) != cudaSuccess || !upload(zh, zb) ||
@@ -692,7 +713,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
   if (cudaEventRecord(c->ev_ready, c->stream) != cudaSuccess || cudaStreamWaitEvent(c->s_cmp2, c->ev_ready) != cudaSuccess)
     return HYDRO_ERR_CUDA;
   for (int k = 0; k < S; ++k) {
-    const int za = k * zc, zb = std::min(I.nz, za + zc);
+    const int za = zs[k], zb = zs[k + 1];
     cudaStream_t sk = (k & 1) ? c->s_cmp2 : c->stream;
     // slab k and its upper halo: the first two planes of slab k+1 (the last slab's halo wraps onto
     // slab 0, uploaded before it)
@@ -700,7 +721,7 @@ int hydro_step_host(hydro_ctx* c, const hydro_patch* in, const hydro_patch* out,
       return HYDRO_ERR_CUDA;
     c->launches += 1;
     if (c->ops->step_batched(c->tile_id, c->d_stage_io, c->d_stage_tiles + (size_t)k * tps, tps,
-                             c->d_stage_counters + k, c->prm, dt_dev, dt_next_dev, zc, c->d_err, grid,
+                             c->d_stage_counters + k, c->prm, dt_dev, dt_next_dev, zb - za, c->d_err, grid,
                              sk) != cudaSuccess)
       return HYDRO_ERR_CUDA;
     if (cudaEventRecord(c->ev_stepped[k], sk) != cudaSuccess ||

@@ -76,6 +76,25 @@ def test_host_step_small_slabs(zchunk):
     check_clean(c)
 
 
+@pytest.mark.parametrize("zchunk,nz", [(8, 128), (8, 130), (8, 133), (16, 262)])
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_host_step_ramped_slabs(precision, zchunk, nz):
+    """Boxes tall enough for slabs of the tuned z chunk ramped at both ends (zc/4, zc/2, ..., zc/2,
+    zc/4 planes; a left-over of one plane merged into the last full slab, of more into a slab of its
+    own): the same bits as hydro_step."""
+    c = ctx(precision)
+    shape = (nz, 12, 14)
+    U = workloads.turbulent_state(shape, seed=4, mach=5.0, sedov=True).contiguous()
+    dx = 1.0 / 14
+    want, wd = _device_steps(c, U, dx, 2)
+    hy.hydro_set_tuning(c, 0, zchunk)
+    got, gd = _host_steps(c, U, dx, 2, wd[0].item())
+    for g, w in zip(got, want):
+        assert torch.equal(g, w)
+    assert torch.equal(gd, wd)
+    check_clean(c)
+
+
 def test_host_step_pageable_memory():
     c = ctx("fp64")
     U = workloads.turbulent_state((24, 16, 16), seed=3, mach=2.0, sedov=False).contiguous()
