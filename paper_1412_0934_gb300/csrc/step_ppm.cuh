@@ -99,6 +99,62 @@ __device__ __forceinline__ void ppm_cell(const PpmShared<R, TX, TY>& sm, const i
   hancock(q, D[0], D[1], D[2], gamma, hdt, qh);
 }
 
+// The same reconstruction and prediction with the three axes in a loop, for double-float arithmetic,
+// whose fifteen inlined edge reconstructions per cell overflow the instruction cache: one copy of
+// the five per-variable reconstructions serves all axes (the stencil addresses per axis as offsets
+// in the ring), the Hancock terms are summed axis by axis in the x, y, z order of ppm_cell, and the
+// edge offsets (edge - q) go where the caller wants them: out(d, v, lo, hi) for axis d.
+template <class R, int TX, int TY, class Out>
+__device__ __forceinline__ void ppm_cell_axes(const PpmShared<R, TX, TY>& sm, const int sl[5], int i, int j, R gamma,
+                                              R hdt, R sixth, R qh[5], Out out) {
+  constexpr int QX = TX + 2 * kPpmHalo;
+  constexpr int SLOT = 5 * (TY + 2 * kPpmHalo) * QX;  // elements per ring slot
+  const R* c0 = &sm.q[sl[2]][0][j + kPpmHalo][i + kPpmHalo];
+  constexpr int VAR = (TY + 2 * kPpmHalo) * QX;  // elements per variable within a slot
+  R q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v] = c0[v * VAR];
+  const R ir = rcp_(q[0]);
+  const R gp = gamma * q[4];
+  R acc[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) acc[v] = R(0);
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    int off[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) off[k] = d == 2 ? (sl[k] - sl[2]) * SLOT : (k - 2) * (d == 0 ? 1 : QX);
+    R D[5], lo[5], hi[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const R* b = c0 + v * VAR;
+      R l, r;
+      ppm_edges(b[off[0]], b[off[1]], q[v], b[off[3]], b[off[4]], sixth, l, r);
+      D[v] = r - l;
+      lo[v] = l - q[v];
+      hi[v] = r - q[v];
+    }
+    out(d, lo, hi);
+    // Hancock terms of axis d (normal velocity q[1 + d]), as in hancock()
+    const R un = d == 0 ? q[1] : (d == 1 ? q[2] : q[3]);
+    const R Dn = d == 0 ? D[1] : (d == 1 ? D[2] : D[3]);
+    R t[5];
+    t[0] = un * D[0] + q[0] * Dn;
+    t[1] = un * D[1];
+    t[2] = un * D[2];
+    t[3] = un * D[3];
+    const R tn = (d == 0 ? t[1] : (d == 1 ? t[2] : t[3])) + D[4] * ir;
+    if (d == 0) t[1] = tn;
+    else if (d == 1) t[2] = tn;
+    else t[3] = tn;
+    t[4] = gp * Dn + un * D[4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = d == 0 ? t[v] : acc[v] + t[v];
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qh[v] = q[v] - hdt * acc[v];
+}
+
 // Resident blocks per SM: the 8-byte ring and face arrays take ~165 KB of shared memory.
 template <class Pol>
 constexpr int ppm_min_blocks() { return sizeof(typename Pol::R) >= 8 ? 1 : 2; }
@@ -129,6 +185,7 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
   using S = typename Pol::S;
   using R = typename Pol::R;
   constexpr int QX = TX + 2 * kPpmHalo, QY = TY + 2 * kPpmHalo, NT = TX * TY;
+  constexpr bool kCompactPpm = std::is_same<R, df>::value;  // double-float arithmetic
   const int tid = threadIdx.x;
   const bool periodic = P.gin == 0;
   __syncthreads();  // the previous tile's last reads of the index tables are done
@@ -181,7 +238,53 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
     for (int k = 0; k < 5; ++k) sl[k] = (base + k) % 5;
     const bool xy = p >= z0 && p < z1;  // plane p is updated: its x and y faces are needed
     R zlo[5], znew[5];
-    {
+    if constexpr (kCompactPpm) {
+      // double-float: the tile cell (it 0) and this thread's ring cell (it 1) through one inlined
+      // copy of the reconstruction; the x/y edge offsets are stored and completed with qh after it
+      for (int it = 0; it < 2; ++it) {
+        if (it == 1 && !(xy && rk >= 0)) break;
+        const int ci = it == 0 ? i : ri, cj = it == 0 ? j : rj;
+        R qh[5];
+        ppm_cell_axes(sm, sl, ci, cj, gamma, hdt, sixth, qh, [&](int d, const R lo[5], const R hi[5]) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            if (it == 0) {
+              if (d == 2) {
+                zlo[v] = lo[v];
+                znew[v] = hi[v];
+              } else if (xy && d == 0) {
+                sm.wx[0][v][j][i + 1] = lo[v];
+                sm.wx[1][v][j][i + 1] = hi[v];
+              } else if (xy) {
+                sm.wy[0][v][j + 1][i] = lo[v];
+                sm.wy[1][v][j + 1][i] = hi[v];
+              }
+            } else if (d == (rk >> 1)) {
+              if (rk == 0) sm.wx[1][v][rj][0] = hi[v];
+              else if (rk == 1) sm.wx[0][v][rj][TX + 1] = lo[v];
+              else if (rk == 2) sm.wy[1][v][0][ri] = hi[v];
+              else sm.wy[0][v][TY + 1][ri] = lo[v];
+            }
+          }
+        });
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if (it == 0) {
+            zlo[v] = qh[v] + zlo[v];
+            znew[v] = qh[v] + znew[v];
+            if (xy) {
+              sm.wx[0][v][j][i + 1] = qh[v] + sm.wx[0][v][j][i + 1];
+              sm.wx[1][v][j][i + 1] = qh[v] + sm.wx[1][v][j][i + 1];
+              sm.wy[0][v][j + 1][i] = qh[v] + sm.wy[0][v][j + 1][i];
+              sm.wy[1][v][j + 1][i] = qh[v] + sm.wy[1][v][j + 1][i];
+            }
+          } else if (rk == 0) sm.wx[1][v][rj][0] = qh[v] + sm.wx[1][v][rj][0];
+          else if (rk == 1) sm.wx[0][v][rj][TX + 1] = qh[v] + sm.wx[0][v][rj][TX + 1];
+          else if (rk == 2) sm.wy[1][v][0][ri] = qh[v] + sm.wy[1][v][0][ri];
+          else sm.wy[0][v][TY + 1][ri] = qh[v] + sm.wy[0][v][TY + 1][ri];
+        }
+      }
+    } else {
       R lo[3][5], hi[3][5], qh[5];
       ppm_cell(sm, sl, i, j, gamma, hdt, sixth, lo, hi, qh);
 #pragma unroll
@@ -196,7 +299,7 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
         }
       }
     }
-    if (xy && rk >= 0) {
+    if (!kCompactPpm && xy && rk >= 0) {
       R lo[3][5], hi[3][5], qh[5];
       ppm_cell(sm, sl, ri, rj, gamma, hdt, sixth, lo, hi, qh);
 #pragma unroll
@@ -239,7 +342,30 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
 #pragma unroll
     for (int v = 0; v < 5; ++v) zhi[v] = znew[v];
     __syncthreads();  // face states written; ring slot of plane p-2 free
-    if (xy) {
+    if (kCompactPpm && xy) {
+      // double-float: x and y faces through one inlined copy of HLLC (runtime normal)
+      constexpr int NXF = (TX + 1) * TY;
+      for (int f = tid; f < NXF + TX * (TY + 1); f += NT) {
+        const int d = f < NXF ? 0 : 1;
+        const int g = d == 0 ? f : f - NXF;
+        const int w = d == 0 ? TX + 1 : TX;
+        const int fy = g / w, fx = g - fy * w;
+        R ql[5], qr[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ql[v] = d == 0 ? sm.wx[1][v][fy][fx] : sm.wy[1][v][fy][fx];
+          qr[v] = d == 0 ? sm.wx[0][v][fy][fx + 1] : sm.wy[0][v][fy + 1][fx];
+        }
+        floor_state(ql, rf, pf);
+        floor_state(qr, rf, pf);
+        hllc_dyn(d, ql, qr, gamma, igm1, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if (d == 0) sm.fx[v][fy][fx] = F[v];
+          else sm.fy[v][fy][fx] = F[v];
+        }
+      }
+    } else if (xy) {
       for (int f = tid; f < (TX + 1) * TY; f += NT) {
         const int fy = f / (TX + 1), fx = f - fy * (TX + 1);
         R ql[5], qr[5], F[5];
