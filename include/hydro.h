@@ -288,7 +288,9 @@ int hydro_step_octs_table(hydro_ctx* ctx, void* const in[5], void* const out[5],
  * conservative update; psi scaled by exp(-0.4 c_h dt/dx).
  *   hydro_mhd_step: out <- U^{n+1} of in with time step dt_dev[0]; in and out must not overlap;
  *       dt_next_dev: NULL or one double receiving cfl dx / max_cells sum_d (|u_d| + c_f,d) of U^{n+1}.
- *       Device scratch of 81 elements per cell (face states and fluxes) is owned by the context.
+ *       HYDRO_FP32 and HYDRO_MIXED run one fused launch with no per-cell scratch; HYDRO_FP64 and
+ *       HYDRO_FP64_DF use 81 elements per cell of device scratch (face states and fluxes), owned
+ *       by the context.
  *   hydro_mhd_cfl_dt: dt_dev[0] <- the same CFL dt of U (bit-identical to the fused one).
  * Element type: double in HYDRO_FP64, HYDRO_FP64_DF (double-float arithmetic, the update summed in
  * double) and HYDRO_MIXED (the state read as float, float arithmetic, the update summed in double)

@@ -1134,13 +1134,14 @@ int hydro_mhd_step(hydro_ctx* c, void* const in[9], void* const out[9], int nx, 
       const uintptr_t a = reinterpret_cast<uintptr_t>(out[v]), b = reinterpret_cast<uintptr_t>(in[u]);
       if (a < b + bytes && b < a + bytes) return HYDRO_ERR_ARG;
     }
-  int rc = ensure_device(&c->d_mhd, &c->mhd_cap, hydro::mhd_scratch_bytes(nx, ny, nz, elem_size(c)));
+  int rc = ensure_device(&c->d_mhd, &c->mhd_cap,
+                         hydro::mhd_scratch_bytes(c->cfg.precision, nx, ny, nz, elem_size(c)));
   if (rc) return rc;
   if (dt_next_dev) {
     rc = reset_slots(c, dt_next_dev, 1, c->stream);
     if (rc) return rc;
   }
-  c->launches += 4;
+  c->launches += hydro::mhd_step_launches(c->cfg.precision);
   return cuda_status(hydro::launch_mhd_step(c->cfg.precision, mhd_box(in, out, nx, ny, nz, dx), c->prm, dt_dev,
                                             dt_next_dev, c->d_mhd, c->d_err, c->stream));
 }

@@ -164,16 +164,17 @@ cudaError_t launch_octs_build(const int* pos, int noct, const int dims[3], unsig
                               cudaStream_t s);
 
 // Ideal MHD with GLM cleaning on a periodic box (mhd.cu): nine fields (rho, m, E, B, psi), each
-// nx*ny*nz contiguous, x fastest; precision HYDRO_FP64, HYDRO_FP32 or HYDRO_FP64_DF.  The step needs
-// mhd_scratch_bytes (elem_size: bytes of the arithmetic type) of device scratch (face states,
-// fluxes, the step's constants).
+// nx*ny*nz contiguous, x fastest; any precision.  The step needs mhd_scratch_bytes (elem_size: bytes
+// of the arithmetic type) of device scratch: the step's constants, and for the 8-byte arithmetic the
+// face states and fluxes of its three-launch form; mhd_step_launches kernels per step.
 struct HostMhdBox {
   const void* in[9];
   void* out[9];
   int nx, ny, nz;
   double dx;
 };
-size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size);
+size_t mhd_scratch_bytes(int precision, int nx, int ny, int nz, int elem_size);
+int mhd_step_launches(int precision);
 // A patch of the batched MHD step (two ghost layers in, 0 or 2 out): its scratch, 81 elements per
 // cell of its extended box (nx+2)(ny+2)(nz+2), starts at element offset `scratch` of the scratch
 // body, which follows mhd_patch_consts_bytes(npatch) bytes of per-patch constants.

@@ -11,10 +11,12 @@
 //   (psi_R - psi_L)/(2 c_h), psi* = (psi_L + psi_R)/2 - c_h (B_nR - B_nL)/2; fluxes psi* and
 //   c_h^2 B_n*.  c_h = (cfl/3) dx/dt; after the update psi decays by exp(-alpha c_h dt/dx), alpha 0.4.
 //
-// Three launches per step, one thread per cell each: predict (the cell's six face states into
-// scratch), flux (the HLL flux through the cell's three low faces into scratch), update (flux
-// divergence, damping, and the CFL speed of the new state folded into dt_next).  The scratch holds
-// 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays, in the arithmetic type.
+// Float arithmetic (FP32, mixed) steps a periodic box in one fused launch, a column tile marching
+// in z through shared memory (k_mhd_tile, below), with no per-cell scratch.  The 8-byte arithmetic
+// and the patches take three launches, one thread per cell each: predict (the cell's six face
+// states into scratch), flux (the HLL flux through the cell's three low faces into scratch), update
+// (flux divergence, damping, and the CFL speed of the new state folded into dt_next); the scratch
+// holds 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays, in the arithmetic type.
 // Precision policies as the hydro step: FP64 (double), FP32 (float, SFU reciprocal and square
 // root), FP64_DF (double state, double-float arithmetic on the FP32 pipes, the update summed in
 // double), MIXED (double state read as float, float arithmetic, the update summed in double).
@@ -396,70 +398,306 @@ __global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdC
   flush_flags(flags, err);
 }
 
-// Flux through the face between cell lo (its high face state along D) and cell hi (its low one).
-template <int D, class Pol>
-__device__ __forceinline__ void face_flux_between(const MhdBox<Pol>& B, long long lo, long long hi,
-                                                  const MhdConst<typename Pol::R>& c, typename Pol::R F[NV]) {
-  using R = typename Pol::R;
-  R qL[NV], qR[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    qL[v] = B.face[((long long)(2 * D + 1) * NV + v) * B.cells + lo];
-    qR[v] = B.face[((long long)(2 * D) * NV + v) * B.cells + hi];
-  }
-  mhd_hll<D>(qL, qR, c, F);
+// ------------------------------------------------------------------ fused tile step (periodic box)
+// One launch per step: a TX x TY column tile marching in z, the structure of the hydro step.  The
+// primitive planes p-1, p, p+1 of the tile plus two halo cells per side sit in a shared-memory ring.
+// Per plane p, two phases between block barriers:
+//   1  each column predicts its cell of plane p (slopes, the six extrapolated states advanced by the
+//      conservative Hancock half step and recovered): the four in-plane face states go to shared
+//      memory, the low z state meets the high z state of plane p-1 (kept in registers) in the HLL
+//      flux of face p-1/2, and the column's cell of plane p-1 is updated from its x/y fluxes (shared
+//      memory) and its two z fluxes; the last 2 (TX + TY) threads then predict one ring cell each,
+//      for its face state toward the tile
+//   2  the HLL fluxes of plane p's x and y faces, each once, into shared memory, and the load of
+//      plane p+2 (recovered) into the slot of plane p-1
+// No global scratch: each cell is read once per plane (halo re-reads from L2) and written once; the
+// same operations in the same order as the three-launch form, so the same values.
+template <class R, int TX, int TY>
+struct MhdTileShared {
+  R q[3][NV][TY + 4][TX + 4];  // primitive planes, slot (p + 3) % 3
+  R lx[NV][TY][TX + 1];        // low x face state of cell i, i = 0 .. TX (TX: the right ring cell)
+  R hx[NV][TY][TX + 1];        // high x face state of cell i - 1 (i = 0: the left ring cell)
+  R ly[NV][TY + 1][TX];        // low y face state of cell j, j = 0 .. TY
+  R hy[NV][TY + 1][TX];        // high y face state of cell j - 1
+  R fx[NV][TY][TX + 1];        // HLL flux through the x face between cells i - 1 and i
+  R fy[NV][TY + 1][TX];        // HLL flux through the y face between cells j - 1 and j
+  int xoff[TX + 4];            // x index of the halo columns (periodic)
+  int yoff[TY + 4];            // y index x nx of the halo rows
+};
+
+constexpr int kMhdTX = 16, kMhdTY = 16;
+
+// The policies whose periodic step runs the fused tile kernel: float arithmetic (FP32, mixed; at
+// 256^3 +15% and +35% over the three-launch form).  The 8-byte arithmetic's tile state fills an SM
+// with one 8-warp block (FP64 -21%, double-float -39%): those keep the three launches.
+template <class Pol>
+constexpr bool kMhdFused = sizeof(typename Pol::R) == 4;
+
+// Resident blocks per SM: float arithmetic fits two tiles' shared memory per SM, 8-byte one.
+template <class Pol>
+constexpr int mhd_tile_blocks() {
+  return sizeof(typename Pol::R) == 4 ? 2 : 1;
 }
 
-// Fluxes and update in one pass, for float arithmetic: each cell forms the HLL fluxes through all
-// six of its faces from the face states (every face twice, once by each of its cells) instead of
-// writing the fluxes of its three low faces to scratch and reading them back with its neighbours'
-// -- the same flux bits, the same sums, less scratch traffic (the float step streams its scratch
-// at most of the HBM bandwidth; the 8-byte policies are bound by arithmetic and keep the two passes).
-template <class Pol>
-__global__ void __launch_bounds__(256, 2) k_mhd_flux_update(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp,
-                                                         double cfl, double dx, double* dt_next, unsigned* err) {
+// Slopes of the cell (ci, cj) of plane p (tile coordinates; the ring at -1 and TX / TY) and the
+// sum over axes of the flux differences of its extrapolated states, as axis_states.
+template <class Pol, int TX, int TY>
+__device__ __forceinline__ void mhd_tile_predict(const MhdTileShared<typename Pol::R, TX, TY>& sm, int ci, int cj,
+                                                 int sm1, int s0, int sp1, const MhdConst<typename Pol::R>& c,
+                                                 typename Pol::R q[NV], typename Pol::R sl[3][NV],
+                                                 typename Pol::R dF[NV]) {
   using R = typename Pol::R;
+  const int x = ci + 2, y = cj + 2;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) q[v] = sm.q[s0][v][y][x];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R lo[NV], hi[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R qm = d == 0 ? sm.q[s0][v][y][x - 1] : (d == 1 ? sm.q[s0][v][y - 1][x] : sm.q[sm1][v][y][x]);
+      const R qp = d == 0 ? sm.q[s0][v][y][x + 1] : (d == 1 ? sm.q[s0][v][y + 1][x] : sm.q[sp1][v][y][x]);
+      const R s = limited(q[v] - qm, qp - q[v], c.limiter);
+      sl[d][v] = s;
+      lo[v] = q[v] - half_(s);
+      hi[v] = q[v] + half_(s);
+    }
+    R Fh[NV], Fl[NV];
+    if (d == 0) {
+      mhd_flux<0>(hi, c, Fh);
+      mhd_flux<0>(lo, c, Fl);
+    } else if (d == 1) {
+      mhd_flux<1>(hi, c, Fh);
+      mhd_flux<1>(lo, c, Fl);
+    } else {
+      mhd_flux<2>(hi, c, Fh);
+      mhd_flux<2>(lo, c, Fl);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dF[v] = d == 0 ? Fh[v] - Fl[v] : dF[v] + (Fh[v] - Fl[v]);
+  }
+}
+
+// One extrapolated state (low, h = 0, or high, h = 1, along the axis of the slopes sl) advanced by
+// half a step and recovered (floored; its flags belong to no cell and are dropped).
+template <class R>
+__device__ __forceinline__ void mhd_face_state(const R q[NV], const R sl[NV], const R dF[NV], int h,
+                                               const MhdConst<R>& c, R r[NV]) {
+  R w[NV], U[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) w[v] = h ? q[v] + half_(sl[v]) : q[v] - half_(sl[v]);
+  mhd_conserved(w, c, U);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
+  unsigned nf = 0;
+  mhd_recover(U, c, r, nf);
+}
+
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
+    k_mhd_tile(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl, double dx, double* dt_next, int zchunk,
+               unsigned* err) {
+  using S = typename Pol::S;
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<MhdTileShared<R, TX, TY>*>(smem_raw);
   const MhdConst<R> c = *cp;
   if (!c.valid) return;
+  constexpr int NT = TX * TY, QW = TX + 4, QH = TY + 4, QN = QW * QH;
+  constexpr int NR = 2 * (TX + TY), NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+  const int tid = threadIdx.x, ti = tid % TX, tj = tid / TX;
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, nz);
+  const long long sz = (long long)nx * ny;
+  for (int k = tid; k < QW; k += NT) sm.xoff[k] = wrapi(x0 - 2 + k, nx);
+  for (int k = tid; k < QH; k += NT) sm.yoff[k] = wrapi(y0 - 2 + k, ny) * nx;
+  __syncthreads();
+
   unsigned flags = 0;
+  // plane z of the tile and its halo, recovered into its ring slot; the flags of a cell count once,
+  // in the tile that updates it
+  auto load_plane = [&](int z) {
+    R(&qs)[NV][TY + 4][TX + 4] = sm.q[ring_slot(z)];
+    const long long zo = (long long)wrapi(z, nz) * sz;
+    const bool zmine = z >= z0 && z < z1;
+    for (int k = tid; k < QN; k += NT) {
+      const int cy = k / QW, cx = k - cy * QW;
+      const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
+      R U[NV], w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(B.in[v] + a), (R*)nullptr);
+      unsigned f = 0;
+      mhd_recover(U, c, w, f);
+      if (zmine && cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2 && x0 + cx - 2 < nx && y0 + cy - 2 < ny) flags |= f;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qs[v][cy][cx] = w[v];
+    }
+  };
+
+  const bool own = (x0 + ti < nx) && (y0 + tj < ny);
+  const bool ringw = tid >= NT - NR;
+  R LzPrev[NV], FzPrev[NV], Fz[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) LzPrev[v] = FzPrev[v] = Fz[v] = R(0);
   R smax = R(0);
-  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < B.cells;
-       a += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    cell_of(a, B.nx, B.ny, i, j, k);
-    const long long sy = B.nx, sz = (long long)B.nx * B.ny;
-    R d[3][NV];
-    {
-      R Fl[NV], Fh[NV];
-      face_flux_between<0>(B, a + (i == 0 ? B.nx - 1 : -1), a, c, Fl);
-      face_flux_between<0>(B, a, a + (i == B.nx - 1 ? -(B.nx - 1) : 1), c, Fh);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) d[0][v] = Fh[v] - Fl[v];
-    }
-    {
-      R Fl[NV], Fh[NV];
-      face_flux_between<1>(B, a + (j == 0 ? (B.ny - 1) * sy : -sy), a, c, Fl);
-      face_flux_between<1>(B, a, a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy), c, Fh);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) d[1][v] = Fh[v] - Fl[v];
-    }
-    {
-      R Fl[NV], Fh[NV];
-      face_flux_between<2>(B, a + (k == 0 ? (B.nz - 1) * sz : -sz), a, c, Fl);
-      face_flux_between<2>(B, a, a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz), c, Fh);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) d[2][v] = Fh[v] - Fl[v];
-    }
+
+  // the column's cell of plane k: the x/y flux differences of plane k and its two z fluxes
+  auto update = [&](int k) {
     R div[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) div[v] = (d[0][v] + d[1][v]) + d[2][v];
-    mhd_update_cell(B, a, c, div, dt_next != nullptr, flags, smax);
+    for (int v = 0; v < NV; ++v)
+      div[v] = ((sm.fx[v][tj][ti + 1] - sm.fx[v][tj][ti]) + (sm.fy[v][tj + 1][ti] - sm.fy[v][tj][ti])) +
+               (Fz[v] - FzPrev[v]);
+    const long long a = (long long)k * sz + (long long)(y0 + tj) * nx + (x0 + ti);
+    S Un[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Un[v] = Pol::update(__ldg(B.in[v] + a), c.dtdx, div[v]);
+    Un[8] = Un[8] * (S)to_double(c.damp);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) B.out[v][a] = Un[v];
+    if (dt_next) {
+      R U[NV], w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
+      mhd_recover(U, c, w, flags);
+      const R s = mhd_speed(w, c);
+      smax = s > smax ? s : smax;
+    }
+  };
+
+  load_plane(z0 - 2);
+  load_plane(z0 - 1);
+  load_plane(z0);
+  __syncthreads();
+  for (int p = z0 - 1; p <= z1; ++p) {
+    const int sm1 = ring_slot(p - 1), s0 = ring_slot(p), sp1 = ring_slot(p + 1);
+    const bool xy = p >= z0 && p < z1;
+    // ---- phase 1: the column's cell (it = 0), then a ring cell (it = 1), through one call site
+    for (int it = 0; it < 2; ++it) {
+      int ci = ti, cj = tj;
+      unsigned mask;  // face states wanted: bit 2d + h, h = 0 low, 1 high along axis d
+      if (it == 0) {
+        mask = (xy ? 0xFu : 0u) | (p >= z0 && own ? 0x10u : 0u) | (p < z1 ? 0x20u : 0u);
+      } else {
+        if (!xy || !ringw) break;
+        const int r = tid - (NT - NR);
+        if (r < TX) { ci = r; cj = -1; mask = 8u; }                       // below the tile: high y
+        else if (r < 2 * TX) { ci = r - TX; cj = TY; mask = 4u; }         // above: low y
+        else if (r < 2 * TX + TY) { ci = -1; cj = r - 2 * TX; mask = 2u; }  // left: high x
+        else { ci = TX; cj = r - 2 * TX - TY; mask = 1u; }                // right: low x
+      }
+      R q[NV], sl[3][NV], dF[NV];
+      mhd_tile_predict<Pol>(sm, ci, cj, sm1, s0, sp1, c, q, sl, dF);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          if (!((mask >> (2 * d + h)) & 1u)) continue;
+          R r[NV];
+          mhd_face_state(q, sl[d], dF, h, c, r);
+          if (d == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              if (h) sm.hx[v][cj][ci + 1] = r[v];
+              else sm.lx[v][cj][ci] = r[v];
+            }
+          } else if (d == 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              if (h) sm.hy[v][cj + 1][ci] = r[v];
+              else sm.ly[v][cj][ci] = r[v];
+            }
+          } else if (h == 0) {
+            mhd_hll<2>(LzPrev, r, c, Fz);  // face p-1/2
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) LzPrev[v] = r[v];
+          }
+        }
+      }
+      if (it == 0) {
+        if (p >= z0 + 1 && own) update(p - 1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) FzPrev[v] = Fz[v];
+      }
+    }
+    __syncthreads();
+    // ---- phase 2
+    if (xy) {
+      for (int f = tid; f < NXF + NYF; f += NT) {
+        R qL[NV], qR[NV], F[NV];
+        if (f < NXF) {
+          const int j = f / (TX + 1), i = f - j * (TX + 1);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            qL[v] = sm.hx[v][j][i];
+            qR[v] = sm.lx[v][j][i];
+          }
+          mhd_hll<0>(qL, qR, c, F);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) sm.fx[v][j][i] = F[v];
+        } else {
+          const int g = f - NXF, j = g / TX, i = g - j * TX;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            qL[v] = sm.hy[v][j][i];
+            qR[v] = sm.ly[v][j][i];
+          }
+          mhd_hll<1>(qL, qR, c, F);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) sm.fy[v][j][i] = F[v];
+        }
+      }
+    }
+    if (p + 2 <= z1 + 1) load_plane(p + 2);
+    __syncthreads();
   }
   if (dt_next) {
     const R m = block_max_r(smax);
     if (threadIdx.x == 0) publish_dt(cfl, dx, to_double(m), dt_next);
   }
   flush_flags(flags, err);
+}
+
+// Planes per z chunk: the fewest waves of resident blocks times the planes a block marches (its
+// chunk plus the plane below it, predicted for its z face, and the two halo loads of each end).
+inline int mhd_zchunk(int nx, int ny, int nz, int resident) {
+  const long long cols = (long long)((nx + kMhdTX - 1) / kMhdTX) * ((ny + kMhdTY - 1) / kMhdTY);
+  int best = nz;
+  double best_cost = 1e300;
+  for (int zc = 8; zc <= 128; zc *= 2) {
+    const int z = zc < nz ? zc : nz;
+    const long long blocks = cols * ((nz + z - 1) / z);
+    const long long waves = (blocks + resident - 1) / resident;
+    const double cost = (double)waves * (z + 1.5);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = z;
+    }
+    if (z == nz) break;
+  }
+  return best;
+}
+
+template <class Pol>
+cudaError_t mhd_tile_launch(const MhdBox<Pol>& B, const MhdConst<typename Pol::R>* cp, double cfl, double dx,
+                            double* dt_next, unsigned* err, cudaStream_t s) {
+  using R = typename Pol::R;
+  constexpr int TX = kMhdTX, TY = kMhdTY;
+  const size_t smem = sizeof(MhdTileShared<R, TX, TY>);
+  static PerDeviceOnce attr;
+  cudaError_t e = attr.call([&] {
+    return cudaFuncSetAttribute(k_mhd_tile<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int zc = mhd_zchunk(B.nx, B.ny, B.nz, sms * mhd_tile_blocks<Pol>());
+  dim3 grid((B.nx + TX - 1) / TX, (B.ny + TY - 1) / TY, (B.nz + zc - 1) / zc);
+  k_mhd_tile<Pol, TX, TY><<<grid, TX * TY, smem, s>>>(B, cp, cfl, dx, dt_next, zc, err);
+  return cudaGetLastError();
 }
 
 template <class Pol>
@@ -547,14 +785,14 @@ cudaError_t mhd_step_t(const HostMhdBox& h, const Params& prm, const double* dt,
   static_assert(sizeof(MhdConst<R>) <= 256, "the constants fit before the face states");
   auto* cp = static_cast<MhdConst<R>*>(scratch);
   k_mhd_consts<R><<<1, 1, 0, s>>>(consts_of<R>(prm), prm.cfl, h.dx, kMhdAlpha, dt, cp, err);
+  if constexpr (kMhdFused<Pol>) {
+    B.face = B.flux = nullptr;  // no per-cell scratch
+    return mhd_tile_launch<Pol>(B, cp, prm.cfl, h.dx, dt_next, err, s);
+  }
   const int g = grid_for(B.cells);
   k_mhd_predict<Pol><<<g, 256, 0, s>>>(B, cp, err);
-  if constexpr (kSlopesInRegs<R>) {
-    k_mhd_flux_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
-  } else {
-    k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
-    k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
-  }
+  k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
+  k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
   return cudaGetLastError();
 }
 
@@ -847,9 +1085,22 @@ cudaError_t launch_mhd_patches_cfl(int precision, const HostMhdPatch* d_patches,
   return cudaErrorInvalidValue;
 }
 
-size_t mhd_scratch_bytes(int nx, int ny, int nz, int elem_size) {
+static bool mhd_fused(int precision) {
+  switch (precision) {
+    case HYDRO_FP64: return kMhdFused<PolF64>;
+    case HYDRO_FP32: return kMhdFused<PolF32>;
+    case HYDRO_FP64_DF: return kMhdFused<PolDF>;
+    case HYDRO_MIXED: return kMhdFused<PolMixed>;
+  }
+  return false;
+}
+
+size_t mhd_scratch_bytes(int precision, int nx, int ny, int nz, int elem_size) {
+  if (mhd_fused(precision)) return 256;  // the step's constants alone
   return (size_t)9 * NV * (size_t)nx * ny * nz * elem_size + 256;
 }
+
+int mhd_step_launches(int precision) { return mhd_fused(precision) ? 2 : 4; }
 
 cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
                             void* scratch, unsigned* err, cudaStream_t s) {

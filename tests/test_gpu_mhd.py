@@ -115,20 +115,52 @@ def test_mhd_conservation(precision):
     assert rel <= (1e-6 if precision in ("fp32", "mixed") else 1e-12), rel
 
 
-def test_mhd_full_size_sampled_windows():
-    """256^3 FP64 MHD step; each sampled 8^3 block equals the oracle's step of the 12^3 window
-    around it (stencil radius 2)."""
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32", "mixed"])
+def test_mhd_step_several_tiles_and_chunks(precision):
+    """A box of several 16 x 16 column tiles and z chunks, ragged in every axis (35 x 21 x 37 cells),
+    on a rough state (white noise of 5% on rho and on the internal energy): every cell against the oracle, and the fused dt
+    against the standalone one."""
+    shape = (37, 21, 35)
+    U = workloads.mhd_state(shape, seed=68, beta=0.5, mach=2.0, psi_amp=0.05).numpy()
+    rng = np.random.default_rng(69)
+    kin = 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
+    eint = U[4] - kin - 0.5 * (U[5] ** 2 + U[6] ** 2 + U[7] ** 2)
+    f = 1 + 0.05 * rng.standard_normal(U[0].shape)  # rho and m scaled alike: velocities kept
+    U[0:4] *= f
+    U[4] += (f - 1) * kin + 0.05 * rng.standard_normal(U[0].shape) * eint
+    dx = 1.0 / 35
+    cfg = oracle.config()
+    dt = omhd.cfl_periodic(U, dx, cfg)
+    c = ctx(precision)
+    b, dn = gpu_step(c, U, dx, dt, dt_next=True)
+    check_clean(c)
+    ref = omhd.step_periodic(U, dx, dt, cfg)
+    err = normwise(b.double().cpu().numpy(), ref)
+    assert err.max() <= TOL[precision], err
+    d2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    hy.hydro_mhd_cfl_dt(c, b, dx, d2)
+    torch.cuda.synchronize()
+    assert dn == d2.item()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mhd_full_size_sampled_windows(precision):
+    """256^3 MHD step (the bench's magnetised-gas box); each sampled 8^3 block equals the oracle's
+    step of the 12^3 window around it (stencil radius 2): per field, the largest difference over the
+    blocks within 1e-12 (FP64) or 1e-5 (FP32) of the oracle's largest value there (the normwise
+    metric; psi grows tenfold in this first step, the field B not being divergence-free)."""
     n = 256
     U = workloads.mhd_state(n, seed=63, beta=0.5, mach=2.0).numpy()
     dx = 1.0 / n
     cfg = oracle.config()
     dt = omhd.cfl_periodic(U, dx, cfg)
-    c = ctx("fp64")
+    c = ctx(precision)
     b, dn = gpu_step(c, U, dx, dt, dt_next=True)
     check_clean(c)
-    g = b.cpu().numpy()
+    g = b.double().cpu().numpy()
     rng = np.random.default_rng(64)
     corners = [(0, 0, 0), (n - 8, n - 8, n - 8)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(6)]
+    diff, scale = np.zeros(9), np.zeros(9)
     for (x, y, z) in corners:
         ix = np.arange(x - 2, x + 10) % n
         iy = np.arange(y - 2, y + 10) % n
@@ -136,8 +168,10 @@ def test_mhd_full_size_sampled_windows():
         win = U[:, iz][:, :, iy][:, :, :, ix]
         ref = omhd.step_periodic(win, dx, dt, cfg)[:, 2:10, 2:10, 2:10]
         got = g[:, iz[2:10]][:, :, iy[2:10]][:, :, :, ix[2:10]]
-        err = np.abs(got - ref).max(axis=(1, 2, 3)) / np.abs(U).max(axis=(1, 2, 3))
-        assert err.max() <= 1e-12, ((x, y, z), err)
+        diff = np.maximum(diff, np.abs(got - ref).max(axis=(1, 2, 3)))
+        scale = np.maximum(scale, np.abs(ref).max(axis=(1, 2, 3)))
+    err = diff / scale
+    assert err.max() <= TOL[precision], err
 
 
 def _ghosted(U, origin, dims, g):
