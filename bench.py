@@ -782,7 +782,7 @@ def form_mhd(hy, precision, steps, warmup, n=256):
     out = {"cells": n ** 3, "steps": steps, "ms_per_step": ms, "mcell_updates_per_s": n ** 3 / (ms / 1e3) / 1e6,
            "hbm_frac": n ** 3 * 2 * 9 * es / (ms / 1e3) / 1e9 / hbm, "launches_per_step": 2 if fused else 4,
            "error_bits": bits,
-           "note": ("the step's constants, then one fused tile kernel (16x16 columns marching in z through "
+           "note": ("the step's constants, then one fused tile kernel (32x8 columns marching in z through "
                     "shared memory, fused dt), no per-cell scratch" if fused else
                     "the step's constants, then three kernels (predict, face fluxes, update + fused dt) with "
                     "81 scratch elements per cell")}

@@ -425,7 +425,7 @@ struct MhdTileShared {
   int yoff[TY + 4];            // y index x nx of the halo rows
 };
 
-constexpr int kMhdTX = 16, kMhdTY = 16;
+constexpr int kMhdTX = 32, kMhdTY = 8;  // one row per warp: conflict-free shared rows
 
 // The policies whose periodic step runs the fused tile kernel: float arithmetic (FP32, mixed; at
 // 256^3 +15% and +35% over the three-launch form).  The 8-byte arithmetic's tile state fills an SM
@@ -504,7 +504,11 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
   const MhdConst<R> c = *cp;
   if (!c.valid) return;
   constexpr int NT = TX * TY, QW = TX + 4, QH = TY + 4, QN = QW * QH;
-  constexpr int NR = 2 * (TX + TY), NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+  // ring cells, taken by the last RW whole warps (NTI threads before them); faces between two
+  // tile cells: NIX in x, NIF in all
+  constexpr int NR = 2 * (TX + TY), RW = (NR + 31) / 32, NTI = NT - 32 * RW;
+  constexpr int NIX = (TX - 1) * TY, NIF = NIX + TX * (TY - 1);
+  static_assert(NTI > 0 && NT % 32 == 0, "whole warps on both sides of the split");
   const int tid = threadIdx.x, ti = tid % TX, tj = tid / TX;
   const int nx = B.nx, ny = B.ny, nz = B.nz;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
@@ -515,13 +519,13 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
   __syncthreads();
 
   unsigned flags = 0;
-  // plane z of the tile and its halo, recovered into its ring slot; the flags of a cell count once,
-  // in the tile that updates it
-  auto load_plane = [&](int z) {
+  // plane z of the tile and its halo, recovered into its ring slot, cells first, first + stride,
+  // ...; the flags of a cell count once, in the tile that updates it
+  auto load_plane = [&](int z, int first, int stride) {
     R(&qs)[NV][TY + 4][TX + 4] = sm.q[ring_slot(z)];
     const long long zo = (long long)wrapi(z, nz) * sz;
     const bool zmine = z >= z0 && z < z1;
-    for (int k = tid; k < QN; k += NT) {
+    for (int k = first; k < QN; k += stride) {
       const int cy = k / QW, cx = k - cy * QW;
       const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
       R U[NV], w[NV];
@@ -536,7 +540,8 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
   };
 
   const bool own = (x0 + ti < nx) && (y0 + tj < ny);
-  const bool ringw = tid >= NT - NR;
+  const bool ringw = tid >= NTI;
+  const int r = tid - NTI;  // ring cell of a ring-warp thread (r < NR)
   R LzPrev[NV], FzPrev[NV], Fz[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) LzPrev[v] = FzPrev[v] = Fz[v] = R(0);
@@ -565,11 +570,48 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
       smax = s > smax ? s : smax;
     }
   };
+  // the HLL flux through the x face between cells i - 1 and i of row j (D = 0), or the y face
+  // between rows j - 1 and j of column i (D = 1)
+  auto face = [&](int d, int i, int j) {
+    R qL[NV], qR[NV], F[NV];
+    if (d == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        qL[v] = sm.hx[v][j][i];
+        qR[v] = sm.lx[v][j][i];
+      }
+      mhd_hll<0>(qL, qR, c, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sm.fx[v][j][i] = F[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        qL[v] = sm.hy[v][j][i];
+        qR[v] = sm.ly[v][j][i];
+      }
+      mhd_hll<1>(qL, qR, c, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sm.fy[v][j][i] = F[v];
+    }
+  };
+  auto ring_cell = [&](int& ci, int& cj, unsigned& mask) {
+    if (r < TX) { ci = r; cj = -1; mask = 8u; }                       // below the tile: high y state
+    else if (r < 2 * TX) { ci = r - TX; cj = TY; mask = 4u; }         // above: low y
+    else if (r < 2 * TX + TY) { ci = -1; cj = r - 2 * TX; mask = 2u; }  // left: high x
+    else { ci = TX; cj = r - 2 * TX - TY; mask = 1u; }                // right: low x
+  };
 
-  load_plane(z0 - 2);
-  load_plane(z0 - 1);
-  load_plane(z0);
+  load_plane(z0 - 2, NT - 1 - tid, NT);
+  load_plane(z0 - 1, NT - 1 - tid, NT);
+  load_plane(z0, NT - 1 - tid, NT);
   __syncthreads();
+  // Per plane p:
+  //   1  every thread predicts its column's cell (its z face p-1/2 and the update of plane p-1
+  //      follow); on x/y planes the ring warps then signal barrier 1 and predict their ring cells
+  //   2  (x/y planes) the other warps, once every tile cell is predicted (barrier 1), signal
+  //      barrier 2 and take the faces between two tile cells, then, once the ring cells are
+  //      predicted (barrier 3: plane p-1 no longer read), load plane p+2 into its slot; the ring
+  //      warps, after barrier 2, take the faces between their ring cell and the tile
   for (int p = z0 - 1; p <= z1; ++p) {
     const int sm1 = ring_slot(p - 1), s0 = ring_slot(p), sp1 = ring_slot(p + 1);
     const bool xy = p >= z0 && p < z1;
@@ -580,12 +622,8 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
       if (it == 0) {
         mask = (xy ? 0xFu : 0u) | (p >= z0 && own ? 0x10u : 0u) | (p < z1 ? 0x20u : 0u);
       } else {
-        if (!xy || !ringw) break;
-        const int r = tid - (NT - NR);
-        if (r < TX) { ci = r; cj = -1; mask = 8u; }                       // below the tile: high y
-        else if (r < 2 * TX) { ci = r - TX; cj = TY; mask = 4u; }         // above: low y
-        else if (r < 2 * TX + TY) { ci = -1; cj = r - 2 * TX; mask = 2u; }  // left: high x
-        else { ci = TX; cj = r - 2 * TX - TY; mask = 1u; }                // right: low x
+        if (!xy || !ringw || r >= NR) break;
+        ring_cell(ci, cj, mask);
       }
       R q[NV], sl[3][NV], dF[NV];
       mhd_tile_predict<Pol>(sm, ci, cj, sm1, s0, sp1, c, q, sl, dF);
@@ -594,25 +632,25 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           if (!((mask >> (2 * d + h)) & 1u)) continue;
-          R r[NV];
-          mhd_face_state(q, sl[d], dF, h, c, r);
+          R rs[NV];
+          mhd_face_state(q, sl[d], dF, h, c, rs);
           if (d == 0) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              if (h) sm.hx[v][cj][ci + 1] = r[v];
-              else sm.lx[v][cj][ci] = r[v];
+              if (h) sm.hx[v][cj][ci + 1] = rs[v];
+              else sm.lx[v][cj][ci] = rs[v];
             }
           } else if (d == 1) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-              if (h) sm.hy[v][cj + 1][ci] = r[v];
-              else sm.ly[v][cj][ci] = r[v];
+              if (h) sm.hy[v][cj + 1][ci] = rs[v];
+              else sm.ly[v][cj][ci] = rs[v];
             }
           } else if (h == 0) {
-            mhd_hll<2>(LzPrev, r, c, Fz);  // face p-1/2
+            mhd_hll<2>(LzPrev, rs, c, Fz);  // face p-1/2
           } else {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) LzPrev[v] = r[v];
+            for (int v = 0; v < NV; ++v) LzPrev[v] = rs[v];
           }
         }
       }
@@ -620,37 +658,40 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
         if (p >= z0 + 1 && own) update(p - 1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) FzPrev[v] = Fz[v];
+        if (xy && ringw) bar_arrive(1, NT);
       }
     }
-    __syncthreads();
-    // ---- phase 2
-    if (xy) {
-      for (int f = tid; f < NXF + NYF; f += NT) {
-        R qL[NV], qR[NV], F[NV];
-        if (f < NXF) {
-          const int j = f / (TX + 1), i = f - j * (TX + 1);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            qL[v] = sm.hx[v][j][i];
-            qR[v] = sm.lx[v][j][i];
-          }
-          mhd_hll<0>(qL, qR, c, F);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) sm.fx[v][j][i] = F[v];
+    if (!xy) {
+      __syncthreads();
+      if (p + 2 <= z1 + 1) load_plane(p + 2, NT - 1 - tid, NT);
+      __syncthreads();
+      continue;
+    }
+    // ---- phase 2 (x/y plane; p + 2 <= z1 + 1)
+    if (ringw) {
+      bar_arrive(3, NT);
+      bar_sync(2, NT);
+      if (r < NR) {
+        if (r < TX) face(1, r, 0);
+        else if (r < 2 * TX) face(1, r - TX, TY);
+        else if (r < 2 * TX + TY) face(0, 0, r - 2 * TX);
+        else face(0, TX, r - 2 * TX - TY);
+      }
+    } else {
+      bar_sync(1, NT);
+      bar_arrive(2, NT);
+      for (int f = tid; f < NIF; f += NTI) {
+        if (f < NIX) {
+          const int j = f / (TX - 1);
+          face(0, f - j * (TX - 1) + 1, j);
         } else {
-          const int g = f - NXF, j = g / TX, i = g - j * TX;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            qL[v] = sm.hy[v][j][i];
-            qR[v] = sm.ly[v][j][i];
-          }
-          mhd_hll<1>(qL, qR, c, F);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) sm.fy[v][j][i] = F[v];
+          const int g = f - NIX, j = g / TX;
+          face(1, g - j * TX, j + 1);
         }
       }
+      bar_sync(3, NT);
+      load_plane(p + 2, NTI - 1 - tid, NTI);
     }
-    if (p + 2 <= z1 + 1) load_plane(p + 2);
     __syncthreads();
   }
   if (dt_next) {
