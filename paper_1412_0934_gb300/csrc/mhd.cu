@@ -191,6 +191,76 @@ __device__ __forceinline__ void mhd_hll(R qL[NV], R qR[NV], const MhdConst<R>& c
   F[8] = c.ch2 * Bm;
 }
 
+// The same flux and HLL flux for a run-time normal d (one inlined copy serves the x and y faces):
+// the components of the normal axis picked by selects, the same operations in the same order.
+template <class R>
+__device__ __forceinline__ R pick3(int d, R a, R b, R c) {
+  return d == 0 ? a : (d == 1 ? b : c);
+}
+
+template <class R>
+__device__ __forceinline__ void mhd_flux_dyn(int d, const R q[NV], const MhdConst<R>& c, R F[NV]) {
+  const R rho = q[0], p = q[4], un = pick3(d, q[1], q[2], q[3]), Bn = pick3(d, q[5], q[6], q[7]);
+  const R B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+  const R pt = p + half_(B2);
+  const R uB = q[1] * q[5] + q[2] * q[6] + q[3] * q[7];
+  const R E = (p * c.igm1 + half_(rho * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]))) + half_(B2);
+  const R mn = rho * un;
+  F[0] = mn;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R m = mn * q[1 + k] - Bn * q[5 + k];
+    F[1 + k] = k == d ? m + pt : m;
+  }
+  F[4] = (E + pt) * un - Bn * uB;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) F[5 + k] = k == d ? q[8] : un * q[5 + k] - q[1 + k] * Bn;
+  F[8] = c.ch2 * Bn;
+}
+
+template <class R>
+__device__ __forceinline__ void mhd_hll_dyn(int d, R qL[NV], R qR[NV], const MhdConst<R>& c, R F[NV]) {
+  const R bL = pick3(d, qL[5], qL[6], qL[7]), bR = pick3(d, qR[5], qR[6], qR[7]);
+  const R Bm = half_(bL + bR) - half_((qR[8] - qL[8]) * c.ich);
+  const R pm = half_(qL[8] + qR[8]) - half_(c.ch * (bR - bL));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k == d) qL[5 + k] = qR[5 + k] = Bm;
+  }
+  qL[8] = qR[8] = pm;
+  const R cL = mhd_fast(qL, d, c), cR = mhd_fast(qR, d, c);
+  const R uL = pick3(d, qL[1], qL[2], qL[3]), uR = pick3(d, qR[1], qR[2], qR[3]);
+  const R a = uL - cL, b = uR - cR, e = uL + cL, f = uR + cR;
+  const R SL = a < b ? a : b, SR = e > f ? e : f;
+  if (!cmp_neg(SL)) {
+    mhd_flux_dyn(d, qL, c, F);
+  } else if (!cmp_pos(SR)) {
+    mhd_flux_dyn(d, qR, c, F);
+  } else {
+    const R is = rcp_(SR - SL);
+    const R ss = SL * SR;
+    {
+      R Fs[NV], Us[NV];
+      mhd_flux_dyn(d, qL, c, Fs);
+      mhd_conserved(qL, c, Us);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] = SR * Fs[v] - ss * Us[v];
+    }
+    {
+      R Fs[NV], Us[NV];
+      mhd_flux_dyn(d, qR, c, Fs);
+      mhd_conserved(qR, c, Us);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] = ((F[v] - SL * Fs[v]) + ss * Us[v]) * is;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k == d) F[5 + k] = pm;
+  }
+  F[8] = c.ch2 * Bm;
+}
+
 __device__ __forceinline__ void cell_of(long long a, int nx, int ny, int& i, int& j, int& k) {
   const int t = (int)a;  // cells < 2^31
   const int row = t / nx;
@@ -570,29 +640,23 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
       smax = s > smax ? s : smax;
     }
   };
-  // the HLL flux through the x face between cells i - 1 and i of row j (D = 0), or the y face
-  // between rows j - 1 and j of column i (D = 1)
+  // the HLL flux through the x face between cells i - 1 and i of row j (d = 0), or the y face
+  // between rows j - 1 and j of column i (d = 1)
   auto face = [&](int d, int i, int j) {
+    constexpr int XS = TY * (TX + 1), YS = (TY + 1) * TX;  // field strides of the x / y arrays
+    const int o = d == 0 ? j * (TX + 1) + i : j * TX + i, st = d == 0 ? XS : YS;
+    const R* hs = d == 0 ? &sm.hx[0][0][0] : &sm.hy[0][0][0];
+    const R* ls = d == 0 ? &sm.lx[0][0][0] : &sm.ly[0][0][0];
+    R* fs = d == 0 ? &sm.fx[0][0][0] : &sm.fy[0][0][0];
     R qL[NV], qR[NV], F[NV];
-    if (d == 0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        qL[v] = sm.hx[v][j][i];
-        qR[v] = sm.lx[v][j][i];
-      }
-      mhd_hll<0>(qL, qR, c, F);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sm.fx[v][j][i] = F[v];
-    } else {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        qL[v] = sm.hy[v][j][i];
-        qR[v] = sm.ly[v][j][i];
-      }
-      mhd_hll<1>(qL, qR, c, F);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sm.fy[v][j][i] = F[v];
+    for (int v = 0; v < NV; ++v) {
+      qL[v] = hs[v * st + o];
+      qR[v] = ls[v * st + o];
     }
+    mhd_hll_dyn(d, qL, qR, c, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) fs[v * st + o] = F[v];
   };
   auto ring_cell = [&](int& ci, int& cj, unsigned& mask) {
     if (r < TX) { ci = r; cj = -1; mask = 8u; }                       // below the tile: high y state
@@ -667,28 +731,33 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
       __syncthreads();
       continue;
     }
-    // ---- phase 2 (x/y plane; p + 2 <= z1 + 1)
+    // ---- phase 2 (x/y plane; p + 2 <= z1 + 1): faces f < NIF between two tile cells (x, then
+    // y), f = NIF + r between ring cell r and the tile, through one call site
     if (ringw) {
       bar_arrive(3, NT);
       bar_sync(2, NT);
-      if (r < NR) {
-        if (r < TX) face(1, r, 0);
-        else if (r < 2 * TX) face(1, r - TX, TY);
-        else if (r < 2 * TX + TY) face(0, 0, r - 2 * TX);
-        else face(0, TX, r - 2 * TX - TY);
-      }
     } else {
       bar_sync(1, NT);
       bar_arrive(2, NT);
-      for (int f = tid; f < NIF; f += NTI) {
-        if (f < NIX) {
-          const int j = f / (TX - 1);
-          face(0, f - j * (TX - 1) + 1, j);
-        } else {
-          const int g = f - NIX, j = g / TX;
-          face(1, g - j * TX, j + 1);
-        }
+    }
+    const int fend = ringw ? (r < NR ? NIF + r + 1 : 0) : NIF;
+    for (int f = ringw ? NIF + r : tid; f < fend; f += NTI) {
+      int d, i, j;
+      if (f < NIX) {
+        d = 0; j = f / (TX - 1); i = f - j * (TX - 1) + 1;
+      } else if (f < NIF) {
+        const int g = f - NIX;
+        d = 1; j = g / TX; i = g - j * TX; j += 1;
+      } else {
+        const int e = f - NIF;
+        if (e < TX) { d = 1; i = e; j = 0; }
+        else if (e < 2 * TX) { d = 1; i = e - TX; j = TY; }
+        else if (e < 2 * TX + TY) { d = 0; i = 0; j = e - 2 * TX; }
+        else { d = 0; i = TX; j = e - 2 * TX - TY; }
       }
+      face(d, i, j);
+    }
+    if (!ringw) {
       bar_sync(3, NT);
       load_plane(p + 2, NTI - 1 - tid, NTI);
     }
