@@ -849,8 +849,11 @@ def form_mhd_patches(hy, precision, steps, warmup, npatch=512):
                        "got": np.stack([got[j] for j in idx]), "dx": dxv, "dt": [dtl[j] for j in idx],
                        "limiter": "minmod", "what": "%d sampled cells of 12 patches" % len(nbs)})
     out = {"patches": len(ins), "interior_cells": interior, "ms_per_step": ms,
-           "mcell_updates_per_s": interior / (ms / 1e3) / 1e6, "launches_per_step": 4, "error_bits": bits,
-           "note": "MHD on the first 512 patches of the batched hydro form's patch set, two ghost layers"}
+           "mcell_updates_per_s": interior / (ms / 1e3) / 1e6,
+           "launches_per_step": 2 if precision in ("fp32", "mixed") else 4, "error_bits": bits,
+           "note": "MHD on the first 512 patches of the batched hydro form's patch set, two ghost layers"
+                   + ("; the step's constants, then one fused tile kernel over 32x8x32 tiles of every patch"
+                      if precision in ("fp32", "mixed") else "")}
     del keep, parent
     hy.hydro_finalize(ctx)
     torch.cuda.empty_cache()

@@ -315,7 +315,9 @@ typedef struct {
  *   hydro_mhd_step_patches: out[p] interior <- U^{n+1} of in[p] with time step dt_dev[p] (device
  *       array of npatch doubles) and cell size in[p].dx; in[p] and out[p] of equal sizes and dx, not
  *       overlapping; dt_next_dev: NULL or npatch doubles receiving each patch's CFL dt of U^{n+1}.
- *       Device scratch of 81 elements per cell of each patch's interior grown by one cell per side.
+ *       HYDRO_FP32 and HYDRO_MIXED run one fused launch over tiles of 32 x 8 columns and 32 planes
+ *       of every patch, with no per-cell scratch; HYDRO_FP64 and HYDRO_FP64_DF use device scratch of
+ *       81 elements per cell of each patch's interior grown by one cell per side.
  *   hydro_mhd_cfl_patches: dt_dev[p] <- the CFL dt of each patch's interior (bit-identical to the
  *       fused one).
  * Precisions and errors as hydro_mhd_step.  The descriptors are uploaded when the patch set differs

@@ -1173,13 +1173,18 @@ static size_t mhd_patch_bytes(const hydro_ctx* c, const hydro_mhd_patch& p) {
   return (size_t)(p.nz + 2 * p.ng) * (size_t)p.sz * elem_size(c);
 }
 
-// Descriptors and the block table (256 extended cells of one patch per block) of a patch set,
-// uploaded (or reused) as aux kind `kind`; returns the device descriptors, blocks and count.
+// Descriptors and the block table of a patch set, uploaded (or reused) as aux kind `kind`: with
+// tiles, the fused step's tile records (patch, x0, y0, z0) when the precision has them, else 256
+// extended cells of one patch per block; returns the device descriptors, table, count and the
+// per-cell scratch elements.
 static int mhd_patch_tables(hydro_ctx* c, int kind, const hydro_mhd_patch* in, const hydro_mhd_patch* out, int npatch,
-                            const hydro::HostMhdPatch** d_patches, const int2** d_blocks, int* nblocks,
+                            bool tiles, const hydro::HostMhdPatch** d_patches, const void** d_blocks, int* nblocks,
                             size_t* scratch_elems) {
   std::vector<hydro::HostMhdPatch> set((size_t)npatch);
   std::vector<int2> blocks;
+  std::vector<int4> recs;
+  int tx = 0, ty = 0, zc = 0;
+  tiles = tiles && hydro::mhd_patch_tiles(c->cfg.precision, &tx, &ty, &zc);
   long long off = 0;
   for (int i = 0; i < npatch; ++i) {
     const hydro_mhd_patch& I = in[i];
@@ -1193,19 +1198,26 @@ static int mhd_patch_tables(hydro_ctx* c, int kind, const hydro_mhd_patch* in, c
     h.isy = I.sy; h.isz = I.sz; h.osy = O.sy; h.osz = O.sz;
     h.dx = I.dx;
     h.scratch = off;
+    if (tiles) {
+      h.scratch = 0;
+      for (int z = 0; z < I.nz; z += zc)
+        for (int y = 0; y < I.ny; y += ty)
+          for (int x = 0; x < I.nx; x += tx) recs.push_back(make_int4(i, x, y, z));
+      continue;
+    }
     const long long ec = (long long)(I.nx + 2) * (I.ny + 2) * (I.nz + 2);
     off += 81 * ec;
     for (long long f = 0; f < ec; f += 256) blocks.push_back(make_int2(i, (int)f));
   }
-  if (blocks.size() > 0x7fffffff) return HYDRO_ERR_ARG;
+  if (blocks.size() > 0x7fffffff || recs.size() > 0x7fffffff) return HYDRO_ERR_ARG;
   std::vector<char> bytes;
   const size_t op = append(bytes, set.data(), set.size());
-  const size_t ob = append(bytes, blocks.data(), blocks.size());
+  const size_t ob = tiles ? append(bytes, recs.data(), recs.size()) : append(bytes, blocks.data(), blocks.size());
   char* d = upload_aux(c, kind, bytes);
   if (!d) return HYDRO_ERR_CUDA;
   *d_patches = reinterpret_cast<const hydro::HostMhdPatch*>(d + op);
-  *d_blocks = reinterpret_cast<const int2*>(d + ob);
-  *nblocks = (int)blocks.size();
+  *d_blocks = d + ob;
+  *nblocks = (int)(tiles ? recs.size() : blocks.size());
   *scratch_elems = (size_t)off;
   return HYDRO_OK;
 }
@@ -1226,10 +1238,10 @@ int hydro_mhd_step_patches(hydro_ctx* c, const hydro_mhd_patch* in, const hydro_
       }
   }
   const hydro::HostMhdPatch* dp = nullptr;
-  const int2* db = nullptr;
+  const void* db = nullptr;
   int nb = 0;
   size_t elems = 0;
-  int rc = mhd_patch_tables(c, 4, in, out, npatch, &dp, &db, &nb, &elems);
+  int rc = mhd_patch_tables(c, 4, in, out, npatch, true, &dp, &db, &nb, &elems);
   if (rc) return rc;
   rc = ensure_device(&c->d_mhd, &c->mhd_cap, hydro::mhd_patch_consts_bytes(npatch) + elems * elem_size(c));
   if (rc) return rc;
@@ -1237,7 +1249,7 @@ int hydro_mhd_step_patches(hydro_ctx* c, const hydro_mhd_patch* in, const hydro_
     rc = reset_slots(c, dt_next_dev, npatch, c->stream);
     if (rc) return rc;
   }
-  c->launches += 4;
+  c->launches += hydro::mhd_step_launches(c->cfg.precision);
   return cuda_status(hydro::launch_mhd_patches(c->cfg.precision, dp, db, nb, npatch, c->prm, dt_dev, dt_next_dev,
                                                c->d_mhd, c->d_err, c->stream));
 }
@@ -1248,15 +1260,16 @@ int hydro_mhd_cfl_patches(hydro_ctx* c, const hydro_mhd_patch* p, int npatch, do
   for (int i = 0; i < npatch; ++i)
     if (!mhd_patch_ok(c, p[i], true)) return HYDRO_ERR_ARG;
   const hydro::HostMhdPatch* dp = nullptr;
-  const int2* db = nullptr;
+  const void* db = nullptr;
   int nb = 0;
   size_t elems = 0;
-  int rc = mhd_patch_tables(c, 5, p, nullptr, npatch, &dp, &db, &nb, &elems);
+  int rc = mhd_patch_tables(c, 5, p, nullptr, npatch, false, &dp, &db, &nb, &elems);
   if (rc) return rc;
   rc = reset_slots(c, dt_dev, npatch, c->stream);
   if (rc) return rc;
   c->launches += 1;
-  return cuda_status(hydro::launch_mhd_patches_cfl(c->cfg.precision, dp, db, nb, c->prm, dt_dev, c->d_err, c->stream));
+  return cuda_status(hydro::launch_mhd_patches_cfl(c->cfg.precision, dp, static_cast<const int2*>(db), nb, c->prm,
+                                                   dt_dev, c->d_err, c->stream));
 }
 
 int hydro_adjoint_step(hydro_ctx* c, const hydro_patch* U_n, const double* dt_dev, const hydro_patch* lam_np1,

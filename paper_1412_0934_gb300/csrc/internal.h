@@ -187,7 +187,11 @@ struct HostMhdPatch {
   long long scratch;
 };
 size_t mhd_patch_consts_bytes(int npatch);
-cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
+// The step on patches: d_blocks is the int4 tile table (patch, x0, y0, z0) of mhd_patch_tiles'
+// shape where that returns true (float arithmetic, one fused launch, no per-cell scratch), else the
+// int2 block table (patch, first extended cell) of the three launches.
+bool mhd_patch_tiles(int precision, int* tx, int* ty, int* zc);
+cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, const void* d_blocks, int nblocks,
                                int npatch, const Params& prm, const double* dt, double* dt_next, void* scratch,
                                unsigned* err, cudaStream_t s);
 cudaError_t launch_mhd_patches_cfl(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,

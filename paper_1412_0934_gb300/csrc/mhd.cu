@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "hydro_device.cuh"
 #include "internal.h"
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdC
 //      plane p+2 (recovered) into the slot of plane p-1
 // No global scratch: each cell is read once per plane (halo re-reads from L2) and written once; the
 // same operations in the same order as the three-launch form, so the same values.
-template <class R, int TX, int TY>
+template <class R, int TX, int TY, class Off>
 struct MhdTileShared {
   R q[3][NV][TY + 4][TX + 4];  // primitive planes, slot (p + 3) % 3
   R lx[NV][TY][TX + 1];        // low x face state of cell i, i = 0 .. TX (TX: the right ring cell)
@@ -491,11 +492,13 @@ struct MhdTileShared {
   R hy[NV][TY + 1][TX];        // high y face state of cell j - 1
   R fx[NV][TY][TX + 1];        // HLL flux through the x face between cells i - 1 and i
   R fy[NV][TY + 1][TX];        // HLL flux through the y face between cells j - 1 and j
-  int xoff[TX + 4];            // x index of the halo columns (periodic)
-  int yoff[TY + 4];            // y index x nx of the halo rows
+  Off yoff[TY + 4];            // y offset (stored y index x its stride) of the halo rows
+  int xoff[TX + 4];            // stored x index of the halo columns
 };
 
+
 constexpr int kMhdTX = 32, kMhdTY = 8;  // one row per warp: conflict-free shared rows
+constexpr int kMhdPatchZChunk = 32;     // planes per tile record of a patch
 
 // The policies whose periodic step runs the fused tile kernel: float arithmetic (FP32, mixed; at
 // 256^3 +15% and +35% over the three-launch form).  The 8-byte arithmetic's tile state fills an SM
@@ -511,8 +514,8 @@ constexpr int mhd_tile_blocks() {
 
 // Slopes of the cell (ci, cj) of plane p (tile coordinates; the ring at -1 and TX / TY) and the
 // sum over axes of the flux differences of its extrapolated states, as axis_states.
-template <class Pol, int TX, int TY>
-__device__ __forceinline__ void mhd_tile_predict(const MhdTileShared<typename Pol::R, TX, TY>& sm, int ci, int cj,
+template <class Pol, class Sh>
+__device__ __forceinline__ void mhd_tile_predict(const Sh& sm, int ci, int cj,
                                                  int sm1, int s0, int sp1, const MhdConst<typename Pol::R>& c,
                                                  typename Pol::R q[NV], typename Pol::R sl[3][NV],
                                                  typename Pol::R dF[NV]) {
@@ -563,16 +566,24 @@ __device__ __forceinline__ void mhd_face_state(const R q[NV], const R sl[NV], co
   mhd_recover(U, c, r, nf);
 }
 
-template <class Pol, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
-    k_mhd_tile(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl, double dx, double* dt_next, int zchunk,
-               unsigned* err) {
+// The tile [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of box B advanced by one step (want_cfl: the
+// largest CFL speed of its new cells into smax); every thread of the block calls it.  GH: B is an
+// AMR patch (HostMhdPatch) whose input carries two ghost layers filled by the caller and whose
+// output carries B.gout (left as they are); else B is a periodic box (MhdBox: indices wrap, the
+// fields contiguous).  Fixed at compile time, so that the periodic kernel carries no strides.
+// Offsets of the halo rows: int on a periodic box (fewer than 2^31 cells), 64-bit on a patch.
+template <bool GH>
+using MhdOff = typename std::conditional<GH, long long, int>::type;
+template <class Pol, int TX, int TY, bool GH>
+using MhdTileSh = MhdTileShared<typename Pol::R, TX, TY, MhdOff<GH>>;
+
+template <class Pol, int TX, int TY, bool GH, class Box>
+__device__ __forceinline__ void mhd_tile_body(MhdTileSh<Pol, TX, TY, GH>& sm, const Box& B,
+                                              const MhdConst<typename Pol::R>& c,
+                                              int x0, int y0, int z0, int z1, bool want_cfl, unsigned& flags,
+                                              typename Pol::R& smax) {
   using S = typename Pol::S;
   using R = typename Pol::R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& sm = *reinterpret_cast<MhdTileShared<R, TX, TY>*>(smem_raw);
-  const MhdConst<R> c = *cp;
-  if (!c.valid) return;
   constexpr int NT = TX * TY, QW = TX + 4, QH = TY + 4, QN = QW * QH;
   // ring cells, taken by the last RW whole warps (NTI threads before them); faces between two
   // tile cells: NIX in x, NIF in all
@@ -581,26 +592,40 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
   static_assert(NTI > 0 && NT % 32 == 0, "whole warps on both sides of the split");
   const int tid = threadIdx.x, ti = tid % TX, tj = tid / TX;
   const int nx = B.nx, ny = B.ny, nz = B.nz;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, nz);
-  const long long sz = (long long)nx * ny;
-  for (int k = tid; k < QW; k += NT) sm.xoff[k] = wrapi(x0 - 2 + k, nx);
-  for (int k = tid; k < QH; k += NT) sm.yoff[k] = wrapi(y0 - 2 + k, ny) * nx;
+  // field pointers, read where used (a periodic box's from the kernel parameters)
+  auto fin = [&](int v) -> const S* { return static_cast<const S*>(B.in[v]); };
+  auto fout = [&](int v) -> S* { return static_cast<S*>(B.out[v]); };
+  constexpr bool periodic = !GH;
+  constexpr int gin = GH ? 2 : 0;
+  long long isy = nx, isz = (long long)nx * ny, osy = isy, osz = isz;
+  int gout = 0;
+  if constexpr (GH) {
+    isy = B.isy; isz = B.isz; osy = B.osy; osz = B.osz;
+    gout = B.gout;
+  }
+  __syncthreads();  // the previous tile of this block is done with the offsets
+  for (int k = tid; k < QW; k += NT) {
+    const int x = x0 - 2 + k;
+    sm.xoff[k] = periodic ? wrapi(x, nx) : min(max(x, -2), nx + 1) + 2;
+  }
+  for (int k = tid; k < QH; k += NT) {
+    const int y = y0 - 2 + k;
+    sm.yoff[k] = (MhdOff<GH>)(periodic ? wrapi(y, ny) : min(max(y, -2), ny + 1) + 2) * (MhdOff<GH>)isy;
+  }
   __syncthreads();
 
-  unsigned flags = 0;
   // plane z of the tile and its halo, recovered into its ring slot, cells first, first + stride,
   // ...; the flags of a cell count once, in the tile that updates it
   auto load_plane = [&](int z, int first, int stride) {
     R(&qs)[NV][TY + 4][TX + 4] = sm.q[ring_slot(z)];
-    const long long zo = (long long)wrapi(z, nz) * sz;
+    const long long zo = (long long)(periodic ? wrapi(z, nz) : z + 2) * isz;
     const bool zmine = z >= z0 && z < z1;
     for (int k = first; k < QN; k += stride) {
       const int cy = k / QW, cx = k - cy * QW;
       const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
       R U[NV], w[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(B.in[v] + a), (R*)nullptr);
+      for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(fin(v) + a), (R*)nullptr);
       unsigned f = 0;
       mhd_recover(U, c, w, f);
       if (zmine && cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2 && x0 + cx - 2 < nx && y0 + cy - 2 < ny) flags |= f;
@@ -615,7 +640,6 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
   R LzPrev[NV], FzPrev[NV], Fz[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) LzPrev[v] = FzPrev[v] = Fz[v] = R(0);
-  R smax = R(0);
 
   // the column's cell of plane k: the x/y flux differences of plane k and its two z fluxes
   auto update = [&](int k) {
@@ -624,14 +648,16 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
     for (int v = 0; v < NV; ++v)
       div[v] = ((sm.fx[v][tj][ti + 1] - sm.fx[v][tj][ti]) + (sm.fy[v][tj + 1][ti] - sm.fy[v][tj][ti])) +
                (Fz[v] - FzPrev[v]);
-    const long long a = (long long)k * sz + (long long)(y0 + tj) * nx + (x0 + ti);
+    const int gx = x0 + ti, gy = y0 + tj;
+    const long long ai = (long long)(k + gin) * isz + (long long)(gy + gin) * isy + (gx + gin);
+    const long long ao = GH ? (long long)(k + gout) * osz + (long long)(gy + gout) * osy + (gx + gout) : ai;
     S Un[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Un[v] = Pol::update(__ldg(B.in[v] + a), c.dtdx, div[v]);
+    for (int v = 0; v < NV; ++v) Un[v] = Pol::update(__ldg(fin(v) + ai), c.dtdx, div[v]);
     Un[8] = Un[8] * (S)to_double(c.damp);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) B.out[v][a] = Un[v];
-    if (dt_next) {
+    for (int v = 0; v < NV; ++v) fout(v)[ao] = Un[v];
+    if (want_cfl) {
       R U[NV], w[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) U[v] = to_r(Un[v], (R*)nullptr);
@@ -763,9 +789,49 @@ __global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
     }
     __syncthreads();
   }
+}
+
+// Periodic box: one tile per block, tiles from the block index.
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
+    k_mhd_tile(MhdBox<Pol> B, const MhdConst<typename Pol::R>* cp, double cfl, double dx, double* dt_next, int zchunk,
+               unsigned* err) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<MhdTileSh<Pol, TX, TY, false>*>(smem_raw);
+  const MhdConst<R> c = *cp;
+  if (!c.valid) return;
+  const int z0 = blockIdx.z * zchunk;
+  unsigned flags = 0;
+  R smax = R(0);
+  mhd_tile_body<Pol, TX, TY, false>(sm, B, c, blockIdx.x * TX, blockIdx.y * TY, z0, min(z0 + zchunk, B.nz),
+                                    dt_next != nullptr, flags, smax);
   if (dt_next) {
     const R m = block_max_r(smax);
     if (threadIdx.x == 0) publish_dt(cfl, dx, to_double(m), dt_next);
+  }
+  flush_flags(flags, err);
+}
+
+// AMR patches with two ghost layers: one tile record (patch, x0, y0, z0) per block, each patch's
+// constants and dt slot its own.
+template <class Pol, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, (mhd_tile_blocks<Pol>()))
+    k_mhdp_tile(const HostMhdPatch* patches, const int4* tiles, const MhdConst<typename Pol::R>* consts, double cfl,
+                double* dt_next, int zchunk, unsigned* err) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<MhdTileSh<Pol, TX, TY, true>*>(smem_raw);
+  const int4 t = tiles[blockIdx.x];
+  const HostMhdPatch H = patches[t.x];  // in registers: its pointers are read at every load
+  const MhdConst<R> c = consts[t.x];
+  if (!c.valid) return;  // (block-uniform)
+  unsigned flags = 0;
+  R smax = R(0);
+  mhd_tile_body<Pol, TX, TY, true>(sm, H, c, t.y, t.z, t.w, min(t.w + zchunk, H.nz), dt_next != nullptr, flags, smax);
+  if (dt_next) {
+    const R m = block_max_r(smax);
+    if (threadIdx.x == 0) publish_dt(cfl, H.dx, to_double(m), dt_next + t.x);
   }
   flush_flags(flags, err);
 }
@@ -795,7 +861,7 @@ cudaError_t mhd_tile_launch(const MhdBox<Pol>& B, const MhdConst<typename Pol::R
                             double* dt_next, unsigned* err, cudaStream_t s) {
   using R = typename Pol::R;
   constexpr int TX = kMhdTX, TY = kMhdTY;
-  const size_t smem = sizeof(MhdTileShared<R, TX, TY>);
+  const size_t smem = sizeof(MhdTileSh<Pol, TX, TY, false>);
   static PerDeviceOnce attr;
   cudaError_t e = attr.call([&] {
     return cudaFuncSetAttribute(k_mhd_tile<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1146,7 +1212,7 @@ __global__ void __launch_bounds__(256) k_mhdp_cfl(const HostMhdPatch* patches, c
 }
 
 template <class Pol>
-cudaError_t mhd_patches_t(const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks, int npatch,
+cudaError_t mhd_patches_t(const HostMhdPatch* d_patches, const void* d_table, int ntable, int npatch,
                           const Params& prm, const double* dt, double* dt_next, void* scratch, unsigned* err,
                           cudaStream_t s) {
   using R = typename Pol::R;
@@ -1154,6 +1220,20 @@ cudaError_t mhd_patches_t(const HostMhdPatch* d_patches, const int2* d_blocks, i
   void* body = static_cast<char*>(scratch) + mhd_patch_consts_bytes(npatch);
   k_mhdp_consts<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, consts_of<R>(prm), prm.cfl, kMhdAlpha, dt,
                                                         consts, err);
+  if constexpr (kMhdFused<Pol>) {
+    constexpr int TX = kMhdTX, TY = kMhdTY;
+    const size_t smem = sizeof(MhdTileSh<Pol, TX, TY, true>);
+    static PerDeviceOnce attr;
+    cudaError_t e = attr.call([&] {
+      return cudaFuncSetAttribute(k_mhdp_tile<Pol, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
+    k_mhdp_tile<Pol, TX, TY><<<ntable, TX * TY, smem, s>>>(d_patches, static_cast<const int4*>(d_table), consts,
+                                                           prm.cfl, dt_next, kMhdPatchZChunk, err);
+    return cudaGetLastError();
+  }
+  const int nblocks = ntable;
+  const int2* d_blocks = static_cast<const int2*>(d_table);
   k_mhdp_predict<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, err);
   k_mhdp_flux<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body);
   k_mhdp_update<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, prm.cfl, dt_next, err);
@@ -1171,7 +1251,7 @@ cudaError_t mhd_patches_cfl_t(const HostMhdPatch* d_patches, const int2* d_block
 
 size_t mhd_patch_consts_bytes(int npatch) { return ((size_t)npatch * 128 + 255) / 256 * 256; }
 
-cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, const int2* d_blocks, int nblocks,
+cudaError_t launch_mhd_patches(int precision, const HostMhdPatch* d_patches, const void* d_blocks, int nblocks,
                                int npatch, const Params& prm, const double* dt, double* dt_next, void* scratch,
                                unsigned* err, cudaStream_t s) {
   static_assert(sizeof(MhdConst<double>) <= 128 && sizeof(MhdConst<df>) <= 128, "per-patch constants slot");
@@ -1211,6 +1291,14 @@ size_t mhd_scratch_bytes(int precision, int nx, int ny, int nz, int elem_size) {
 }
 
 int mhd_step_launches(int precision) { return mhd_fused(precision) ? 2 : 4; }
+
+bool mhd_patch_tiles(int precision, int* tx, int* ty, int* zc) {
+  if (!mhd_fused(precision)) return false;
+  *tx = kMhdTX;
+  *ty = kMhdTY;
+  *zc = kMhdPatchZChunk;
+  return true;
+}
 
 cudaError_t launch_mhd_step(int precision, const HostMhdBox& h, const Params& prm, const double* dt, double* dt_next,
                             void* scratch, unsigned* err, cudaStream_t s) {
