@@ -201,9 +201,9 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
 
   // plane z of the patch (wrapped, or within the ghost layers), recovered into ring slot s over
   // the tile and its halo
-  auto load_plane = [&](int z, int s) {
+  auto load_plane = [&](int z, int s, int first, int stride) {
     const long long zo = (long long)(periodic ? wrap_index(z, P.nz) : z + P.gin) * P.isz;
-    for (int c = tid; c < QX * QY; c += NT) {
+    for (int c = first; c < QX * QY; c += stride) {
       const int y = c / QX, x = c - y * QX;
       const long long a = zo + (long long)sm.sy[y] * P.isy + sm.sx[x];
       S U[5];
@@ -216,7 +216,7 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
     }
   };
   // slot of plane z: (z - z0 + 3) mod 5
-  for (int k = 0; k < 5; ++k) load_plane(z0 - kPpmHalo + k, k);
+  for (int k = 0; k < 5; ++k) load_plane(z0 - kPpmHalo + k, k, tid, NT);
   __syncthreads();
 
   const int i = tid % TX, j = tid / TX;
@@ -228,6 +228,20 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
   else if (tid < 2 * TY + TX) { rk = 2; ri = tid - 2 * TY; rj = -1; }
   else if (tid < 2 * TY + 2 * TX) { rk = 3; ri = tid - 2 * TY - TX; rj = TY; }
 
+  // Split barriers (ids 1-3), in double-float arithmetic, whose block is alone on its SM: the
+  // ring cells belong to the first NR threads, whole warps, which signal barrier 1 once their tile
+  // cells are predicted, predict the ring, signal barrier 3 and take the faces between ring and
+  // tile after barrier 2; the other warps wait for every tile cell (barrier 1), signal barrier 2,
+  // take the faces between two tile cells and, once the ring cells no longer read plane p-2
+  // (barrier 3), load plane p+3 into its slot.  The ring cells' full reconstructions then overlap
+  // the interior faces instead of holding the other warps at one block barrier (+4.5% at 512^3).
+  // Float arithmetic keeps one block barrier per phase: with two resident blocks the other block
+  // fills the waits, and the split (FP32 -6.5%, the batched mixed step -5%) or one call site for
+  // the tile and ring reconstructions (FP32 -10%) cost more.
+  constexpr int NR = 2 * (TX + TY), NIX = (TX - 1) * TY, NIF = NIX + TX * (TY - 1);
+  constexpr bool kSplit = kCompactPpm && NR % 32 == 0 && NR < NT;
+  const bool ringw = tid < NR;
+
   R zhi[5], fzb[5], dxy[5];  // z-high face state, z flux below, x/y flux difference: plane p-1
 #pragma unroll
   for (int v = 0; v < 5; ++v) zhi[v] = fzb[v] = dxy[v] = R(0);
@@ -238,6 +252,39 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
     for (int k = 0; k < 5; ++k) sl[k] = (base + k) % 5;
     const bool xy = p >= z0 && p < z1;  // plane p is updated: its x and y faces are needed
     R zlo[5], znew[5];
+    // z face p - 1/2, then the update of plane p - 1 (its faces p - 3/2 and p - 1/2 are known)
+    auto zface_update = [&]() {
+      if (p > z0 - 1) {
+        R ql[5], qr[5], F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ql[v] = zhi[v];
+          qr[v] = zlo[v];
+        }
+        floor_state(ql, rf, pf);
+        floor_state(qr, rf, pf);
+        hllc<2>(ql, qr, gamma, igm1, F);
+        if (p > z0 && own) {
+          const int z = p - 1;
+          const long long ai = (long long)(z + P.gin) * P.isz + (long long)(y0 + j + P.gin) * P.isy + (x0 + i + P.gin);
+          const long long ao = (long long)(z + P.gout) * P.osz + (long long)(y0 + j + P.gout) * P.osy + (x0 + i + P.gout);
+          S Un[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, dxy[v] + (F[v] - fzb[v]));
+            P.out[v][ao] = Un[v];
+          }
+          if (want_cfl) {
+            const R sp = Pol::speed(Un, prm, flags);
+            smax = sp > smax ? sp : smax;
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) fzb[v] = F[v];
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) zhi[v] = znew[v];
+    };
     if constexpr (kCompactPpm) {
       // double-float: the tile cell (it 0) and this thread's ring cell (it 1) through one inlined
       // copy of the reconstruction; the x/y edge offsets are stored and completed with qh after it
@@ -283,6 +330,10 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
           else if (rk == 2) sm.wy[1][v][0][ri] = qh[v] + sm.wy[1][v][0][ri];
           else sm.wy[0][v][TY + 1][ri] = qh[v] + sm.wy[0][v][TY + 1][ri];
         }
+        if (it == 0) {
+          zface_update();
+          if (kSplit && xy && ringw) bar_arrive(1, NT);
+        }
       }
     } else {
       R lo[3][5], hi[3][5], qh[5];
@@ -310,37 +361,56 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
         else sm.wy[0][v][TY + 1][ri] = qh[v] + lo[1][v];
       }
     }
-    // z face p - 1/2, then the update of plane p - 1 (its faces p - 3/2 and p - 1/2 are known)
-    if (p > z0 - 1) {
-      R ql[5], qr[5], F[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        ql[v] = zhi[v];
-        qr[v] = zlo[v];
+    if constexpr (!kCompactPpm) zface_update();
+    if (kSplit && xy) {
+      if (ringw) {
+        bar_arrive(3, NT);
+        bar_sync(2, NT);
+      } else {
+        bar_sync(1, NT);
+        bar_arrive(2, NT);
       }
-      floor_state(ql, rf, pf);
-      floor_state(qr, rf, pf);
-      hllc<2>(ql, qr, gamma, igm1, F);
-      if (p > z0 && own) {
-        const int z = p - 1;
-        const long long ai = (long long)(z + P.gin) * P.isz + (long long)(y0 + j + P.gin) * P.isy + (x0 + i + P.gin);
-        const long long ao = (long long)(z + P.gout) * P.osz + (long long)(y0 + j + P.gout) * P.osy + (x0 + i + P.gout);
-        S Un[5];
+      // faces f < NIF between two tile cells (x, then y) by the other warps; face NIF + tid
+      // between this thread's ring cell and the tile by a ring thread; one HLLC call site
+      const int fend = ringw ? NIF + tid + 1 : NIF;
+      for (int f = ringw ? NIF + tid : tid - NR; f < fend; f += NT - NR) {
+        int d, fx, fy;
+        if (f < NIX) {
+          d = 0; fy = f / (TX - 1); fx = f - fy * (TX - 1) + 1;
+        } else if (f < NIF) {
+          const int g = f - NIX;
+          d = 1; fy = g / TX; fx = g - fy * TX; fy += 1;
+        } else if (rk == 0) { d = 0; fx = 0; fy = rj; }
+        else if (rk == 1) { d = 0; fx = TX; fy = rj; }
+        else if (rk == 2) { d = 1; fx = ri; fy = 0; }
+        else { d = 1; fx = ri; fy = TY; }
+        R ql[5], qr[5], F[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          Un[v] = Pol::update(__ldg(P.in[v] + ai), dtdx, dxy[v] + (F[v] - fzb[v]));
-          P.out[v][ao] = Un[v];
+          ql[v] = d == 0 ? sm.wx[1][v][fy][fx] : sm.wy[1][v][fy][fx];
+          qr[v] = d == 0 ? sm.wx[0][v][fy][fx + 1] : sm.wy[0][v][fy + 1][fx];
         }
-        if (want_cfl) {
-          const R sp = Pol::speed(Un, prm, flags);
-          smax = sp > smax ? sp : smax;
+        floor_state(ql, rf, pf);
+        floor_state(qr, rf, pf);
+        hllc_dyn(d, ql, qr, gamma, igm1, F);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if (d == 0) sm.fx[v][fy][fx] = F[v];
+          else sm.fy[v][fy][fx] = F[v];
         }
       }
+      if (!ringw) {
+        bar_sync(3, NT);
+        load_plane(p + kPpmHalo, sl[0], tid - NR, NT - NR);  // (p < z1 on an x/y plane)
+      }
+      __syncthreads();  // fluxes and plane p+3 in place
+      if (xy) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) fzb[v] = F[v];
+        for (int v = 0; v < 5; ++v)
+          dxy[v] = (sm.fx[v][j][i + 1] - sm.fx[v][j][i]) + (sm.fy[v][j + 1][i] - sm.fy[v][j][i]);
+      }
+      continue;
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) zhi[v] = znew[v];
     __syncthreads();  // face states written; ring slot of plane p-2 free
     if (kCompactPpm && xy) {
       // double-float: x and y faces through one inlined copy of HLLC (runtime normal)
@@ -395,7 +465,7 @@ __device__ __forceinline__ void ppm_tile(PpmShared<typename Pol::R, TX, TY>& sm,
         for (int v = 0; v < 5; ++v) sm.fy[v][fy][fx] = F[v];
       }
     }
-    if (p < z1) load_plane(p + kPpmHalo, sl[0]);
+    if (p < z1) load_plane(p + kPpmHalo, sl[0], tid, NT);
     __syncthreads();  // fluxes and plane p+3 in place
     if (xy) {
 #pragma unroll
