@@ -185,13 +185,14 @@ def _ghosted(U, origin, dims, g):
 
 @pytest.mark.parametrize("precision", ["fp64", "df64", "fp32", "mixed"])
 def test_mhd_patches_match_oracle(precision):
-    """Patches with two ghost layers (sizes 1 to 40, a 2:1 box, one patch wrapping the parent, dx
-    and dt per patch) in one batched call: each against the oracle's ghosted-patch step; outputs with
-    and without ghost layers; the fused per-patch dt equals hydro_mhd_cfl_patches bit for bit."""
+    """Patches with two ghost layers (sizes 1 to 40, a 2:1 box, one patch wrapping the parent, one
+    wider than a 32-column tile, dx and dt per patch) in one batched call: each against the
+    oracle's ghosted-patch step; outputs with and without ghost layers; the fused per-patch dt
+    equals hydro_mhd_cfl_patches bit for bit."""
     dtype = torch.float32 if precision == "fp32" else torch.float64
     parent = workloads.mhd_state((30, 26, 34), seed=66, beta=0.5, mach=1.5, psi_amp=0.05).numpy()
     rng = np.random.default_rng(67)
-    dims = [(16, 16, 16), (20, 9, 40), (5, 13, 7), (1, 2, 3), (12, 12, 24), (8, 8, 8)]
+    dims = [(16, 16, 16), (20, 9, 40), (5, 13, 7), (1, 2, 3), (12, 12, 24), (8, 8, 8), (40, 11, 6)]
     origins = [tuple(int(v) for v in rng.integers(0, 26, 3)) for _ in dims]
     origins[0] = (30, 22, 27)
     cfg = oracle.config()
