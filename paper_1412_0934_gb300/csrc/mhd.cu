@@ -1,4 +1,5 @@
-// Ideal MHD with hyperbolic (GLM) divergence cleaning on a periodic box: the paper's second code
+// Ideal MHD with hyperbolic (GLM) divergence cleaning on a periodic box or on AMR patches with two
+// ghost layers: the paper's second code
 // runs magnetohydrodynamics on the GPU (Enzo MHD, Sec. 4); it prints no equations, so the scheme
 // is the textbook one below.
 //   U = (rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi), E = p/(gamma-1) + |m|^2/(2 rho) + |B|^2/2.
@@ -11,12 +12,13 @@
 //   (psi_R - psi_L)/(2 c_h), psi* = (psi_L + psi_R)/2 - c_h (B_nR - B_nL)/2; fluxes psi* and
 //   c_h^2 B_n*.  c_h = (cfl/3) dx/dt; after the update psi decays by exp(-alpha c_h dt/dx), alpha 0.4.
 //
-// Float arithmetic (FP32, mixed) steps a periodic box in one fused launch, a column tile marching
-// in z through shared memory (k_mhd_tile, below), with no per-cell scratch.  The 8-byte arithmetic
-// and the patches take three launches, one thread per cell each: predict (the cell's six face
-// states into scratch), flux (the HLL flux through the cell's three low faces into scratch), update
-// (flux divergence, damping, and the CFL speed of the new state folded into dt_next); the scratch
-// holds 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays, in the arithmetic type.
+// Float arithmetic (FP32, mixed) steps a periodic box or a batch of patches in one fused launch, a
+// column tile marching in z through shared memory (k_mhd_tile / k_mhdp_tile, below), with no
+// per-cell scratch.  The 8-byte arithmetic takes three launches, one thread per cell each: predict
+// (the cell's six face states into scratch), flux (the HLL flux through the cell's three low faces
+// into scratch), update (flux divergence, damping, and the CFL speed of the new state folded into
+// dt_next); the scratch holds 6 x 9 face states and 3 x 9 fluxes per cell, structure of arrays, in
+// the arithmetic type (its shared-memory tile state would leave one 8-warp block per SM).
 // Precision policies as the hydro step: FP64 (double), FP32 (float, SFU reciprocal and square
 // root), FP64_DF (double state, double-float arithmetic on the FP32 pipes, the update summed in
 // double), MIXED (double state read as float, float arithmetic, the update summed in double).
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdC
   flush_flags(flags, err);
 }
 
-// ------------------------------------------------------------------ fused tile step (periodic box)
+// ------------------------------------------------------------------ fused tile step
 // One launch per step: a TX x TY column tile marching in z, the structure of the hydro step.  The
 // primitive planes p-1, p, p+1 of the tile plus two halo cells per side sit in a shared-memory ring.
 // Per plane p, two phases between block barriers:
@@ -477,12 +479,13 @@ __global__ void __launch_bounds__(256, 2) k_mhd_update(MhdBox<Pol> B, const MhdC
 //      conservative Hancock half step and recovered): the four in-plane face states go to shared
 //      memory, the low z state meets the high z state of plane p-1 (kept in registers) in the HLL
 //      flux of face p-1/2, and the column's cell of plane p-1 is updated from its x/y fluxes (shared
-//      memory) and its two z fluxes; the last 2 (TX + TY) threads then predict one ring cell each,
-//      for its face state toward the tile
+//      memory) and its two z fluxes; the last warps then predict one ring cell per thread, for its
+//      face state toward the tile
 //   2  the HLL fluxes of plane p's x and y faces, each once, into shared memory, and the load of
-//      plane p+2 (recovered) into the slot of plane p-1
+//      plane p+2 (recovered) into the slot of plane p-1; split named barriers let the ring warps
+//      take the tile-edge faces while the other warps take the interior faces and the load
 // No global scratch: each cell is read once per plane (halo re-reads from L2) and written once; the
-// same operations in the same order as the three-launch form, so the same values.
+// operations and their order per cell are those of the three-launch form.
 template <class R, int TX, int TY, class Off>
 struct MhdTileShared {
   R q[3][NV][TY + 4][TX + 4];  // primitive planes, slot (p + 3) % 3
