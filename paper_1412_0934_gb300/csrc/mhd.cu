@@ -282,16 +282,13 @@ __device__ __forceinline__ void load_q(const MhdBox<Pol>& B, long long a, const 
   mhd_recover(U, c, q, flags);
 }
 
-// Float arithmetic keeps a cell's 27 slopes in registers between the face states' fluxes and their
-// advance (its six extrapolated states are q -+ s/2); 8-byte arithmetic has no registers to spare
-// and round-trips the states through the scratch instead.
-template <class R>
-constexpr bool kSlopesInRegs = sizeof(R) == 4;
-
+// The three-launch form (8-byte arithmetic): a cell's two extrapolated states along axis D into the
+// scratch (read back for their advance: no registers to spare for the 27 slopes) and the flux
+// difference of those states added into dF.
 template <int D, class Pol>
 __device__ __forceinline__ void axis_states(const MhdBox<Pol>& B, long long a, long long am, long long ap,
                                             const typename Pol::R q[NV], const MhdConst<typename Pol::R>& c,
-                                            typename Pol::R dF[NV], typename Pol::R sl[NV]) {
+                                            typename Pol::R dF[NV]) {
   using R = typename Pol::R;
   unsigned nf = 0;  // neighbours are flagged by their own threads
   R lo[NV], hi[NV];
@@ -302,13 +299,10 @@ __device__ __forceinline__ void axis_states(const MhdBox<Pol>& B, long long a, l
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
-      sl[v] = s;
       lo[v] = q[v] - half_(s);
       hi[v] = q[v] + half_(s);
-      if (!kSlopesInRegs<R>) {
-        B.face[((long long)(2 * D) * NV + v) * B.cells + a] = lo[v];
-        B.face[((long long)(2 * D + 1) * NV + v) * B.cells + a] = hi[v];
-      }
+      B.face[((long long)(2 * D) * NV + v) * B.cells + a] = lo[v];
+      B.face[((long long)(2 * D + 1) * NV + v) * B.cells + a] = hi[v];
     }
   }
   R Fh[NV];
@@ -338,13 +332,13 @@ __global__ void __launch_bounds__(256, 2) k_mhd_predict(MhdBox<Pol> B, const Mhd
     const long long axm = a + (i == 0 ? B.nx - 1 : -1), axp = a + (i == B.nx - 1 ? -(B.nx - 1) : 1);
     const long long aym = a + (j == 0 ? (B.ny - 1) * sy : -sy), ayp = a + (j == B.ny - 1 ? -(B.ny - 1) * sy : sy);
     const long long azm = a + (k == 0 ? (B.nz - 1) * sz : -sz), azp = a + (k == B.nz - 1 ? -(B.nz - 1) * sz : sz);
-    R q[NV], dF[NV], sl[3][NV];
+    R q[NV], dF[NV];
     load_q(B, a, c, q, flags);
-    axis_states<0>(B, a, axm, axp, q, c, dF, sl[0]);
-    axis_states<1>(B, a, aym, ayp, q, c, dF, sl[1]);
-    axis_states<2>(B, a, azm, azp, q, c, dF, sl[2]);
-    // the six extrapolated states advanced by half a step, recovered and floored (from the slopes
-    // in registers, or this thread's own scratch entries written just above)
+    axis_states<0>(B, a, axm, axp, q, c, dF);
+    axis_states<1>(B, a, aym, ayp, q, c, dF);
+    axis_states<2>(B, a, azm, azp, q, c, dF);
+    // the six extrapolated states advanced by half a step, recovered and floored (this thread's
+    // own scratch entries written just above)
     unsigned nf = 0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -353,9 +347,7 @@ __global__ void __launch_bounds__(256, 2) k_mhd_predict(MhdBox<Pol> B, const Mhd
         const int f = 2 * d + h;
         R w[NV], U[NV], r[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          w[v] = kSlopesInRegs<R> ? (h ? q[v] + half_(sl[d][v]) : q[v] - half_(sl[d][v]))
-                                  : B.face[((long long)f * NV + v) * B.cells + a];
+        for (int v = 0; v < NV; ++v) w[v] = B.face[((long long)f * NV + v) * B.cells + a];
         mhd_conserved(w, c, U);
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
@@ -967,12 +959,13 @@ cudaError_t mhd_step_t(const HostMhdBox& h, const Params& prm, const double* dt,
   if constexpr (kMhdFused<Pol>) {
     B.face = B.flux = nullptr;  // no per-cell scratch
     return mhd_tile_launch<Pol>(B, cp, prm.cfl, h.dx, dt_next, err, s);
+  } else {
+    const int g = grid_for(B.cells);
+    k_mhd_predict<Pol><<<g, 256, 0, s>>>(B, cp, err);
+    k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
+    k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
+    return cudaGetLastError();
   }
-  const int g = grid_for(B.cells);
-  k_mhd_predict<Pol><<<g, 256, 0, s>>>(B, cp, err);
-  k_mhd_flux<Pol><<<g, 256, 0, s>>>(B, cp);
-  k_mhd_update<Pol><<<g, 256, 0, s>>>(B, cp, prm.cfl, h.dx, dt_next, err);
-  return cudaGetLastError();
 }
 
 template <class Pol>
@@ -1044,8 +1037,7 @@ __global__ void k_mhdp_consts(const HostMhdPatch* patches, int npatch, MhdConst<
 template <int D, class Pol>
 __device__ __forceinline__ void axis_states_p(const HostMhdPatch& P, typename Pol::R* face, long long ec, long long e,
                                               const ExtCell& x, const typename Pol::R q[NV],
-                                              const MhdConst<typename Pol::R>& c, typename Pol::R dF[NV],
-                                              typename Pol::R sl[NV]) {
+                                              const MhdConst<typename Pol::R>& c, typename Pol::R dF[NV]) {
   using R = typename Pol::R;
   unsigned nf = 0;  // neighbours are flagged by their own threads
   const int di = D == 0, dj = D == 1, dk = D == 2;
@@ -1057,13 +1049,10 @@ __device__ __forceinline__ void axis_states_p(const HostMhdPatch& P, typename Po
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R s = limited(q[v] - qm[v], qp[v] - q[v], c.limiter);
-      sl[v] = s;
       lo[v] = q[v] - half_(s);
       hi[v] = q[v] + half_(s);
-      if (!kSlopesInRegs<R>) {
-        face[((long long)(2 * D) * NV + v) * ec + e] = lo[v];
-        face[((long long)(2 * D + 1) * NV + v) * ec + e] = hi[v];
-      }
+      face[((long long)(2 * D) * NV + v) * ec + e] = lo[v];
+      face[((long long)(2 * D + 1) * NV + v) * ec + e] = hi[v];
     }
   }
   R Fh[NV];
@@ -1089,11 +1078,11 @@ __global__ void __launch_bounds__(256, 2) k_mhdp_predict(const HostMhdPatch* pat
   const long long ec = (long long)(P.nx + 2) * (P.ny + 2) * (P.nz + 2), e = b.y + threadIdx.x;
   R* face = static_cast<R*>(scratch) + P.scratch;
   unsigned flags = 0;
-  R q[NV], dF[NV], sl[3][NV];
+  R q[NV], dF[NV];
   load_qp<Pol>(P, in_addr(P, x.i, x.j, x.k), c, q, flags);
-  axis_states_p<0, Pol>(P, face, ec, e, x, q, c, dF, sl[0]);
-  axis_states_p<1, Pol>(P, face, ec, e, x, q, c, dF, sl[1]);
-  axis_states_p<2, Pol>(P, face, ec, e, x, q, c, dF, sl[2]);
+  axis_states_p<0, Pol>(P, face, ec, e, x, q, c, dF);
+  axis_states_p<1, Pol>(P, face, ec, e, x, q, c, dF);
+  axis_states_p<2, Pol>(P, face, ec, e, x, q, c, dF);
   unsigned nf = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -1102,9 +1091,7 @@ __global__ void __launch_bounds__(256, 2) k_mhdp_predict(const HostMhdPatch* pat
       const int f = 2 * d + h;
       R w[NV], U[NV], r[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
-        w[v] = kSlopesInRegs<R> ? (h ? q[v] + half_(sl[d][v]) : q[v] - half_(sl[d][v]))
-                                : face[((long long)f * NV + v) * ec + e];
+      for (int v = 0; v < NV; ++v) w[v] = face[((long long)f * NV + v) * ec + e];
       mhd_conserved(w, c, U);
 #pragma unroll
       for (int v = 0; v < NV; ++v) U[v] = U[v] - c.hdt * dF[v];
@@ -1234,13 +1221,14 @@ cudaError_t mhd_patches_t(const HostMhdPatch* d_patches, const void* d_table, in
     k_mhdp_tile<Pol, TX, TY><<<ntable, TX * TY, smem, s>>>(d_patches, static_cast<const int4*>(d_table), consts,
                                                            prm.cfl, dt_next, kMhdPatchZChunk, err);
     return cudaGetLastError();
+  } else {
+    const int nblocks = ntable;
+    const int2* d_blocks = static_cast<const int2*>(d_table);
+    k_mhdp_predict<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, err);
+    k_mhdp_flux<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body);
+    k_mhdp_update<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, prm.cfl, dt_next, err);
+    return cudaGetLastError();
   }
-  const int nblocks = ntable;
-  const int2* d_blocks = static_cast<const int2*>(d_table);
-  k_mhdp_predict<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, err);
-  k_mhdp_flux<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body);
-  k_mhdp_update<Pol><<<nblocks, 256, 0, s>>>(d_patches, d_blocks, consts, body, prm.cfl, dt_next, err);
-  return cudaGetLastError();
 }
 
 template <class Pol>
