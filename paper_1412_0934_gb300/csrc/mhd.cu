@@ -609,6 +609,8 @@ __device__ __forceinline__ void mhd_tile_body(MhdTileSh<Pol, TX, TY, GH>& sm, co
   }
   __syncthreads();
 
+  // extents of the input and output arrays (elements per field), for the bounds-checked build
+  const long long in_extent = (long long)(nz + 2 * gin) * isz, out_extent = (long long)(nz + 2 * gout) * osz;
   // plane z of the tile and its halo, recovered into its ring slot, cells first, first + stride,
   // ...; the flags of a cell count once, in the tile that updates it
   auto load_plane = [&](int z, int first, int stride) {
@@ -618,9 +620,10 @@ __device__ __forceinline__ void mhd_tile_body(MhdTileSh<Pol, TX, TY, GH>& sm, co
     for (int k = first; k < QN; k += stride) {
       const int cy = k / QW, cx = k - cy * QW;
       const long long a = zo + sm.yoff[cy] + sm.xoff[cx];
+      const bool ok = index_ok(a, in_extent, flags);  // (always true outside the checked build)
       R U[NV], w[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) U[v] = to_r(__ldg(fin(v) + a), (R*)nullptr);
+      for (int v = 0; v < NV; ++v) U[v] = ok ? to_r(__ldg(fin(v) + a), (R*)nullptr) : R(0);
       unsigned f = 0;
       mhd_recover(U, c, w, f);
       if (zmine && cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2 && x0 + cx - 2 < nx && y0 + cy - 2 < ny) flags |= f;
@@ -646,6 +649,7 @@ __device__ __forceinline__ void mhd_tile_body(MhdTileSh<Pol, TX, TY, GH>& sm, co
     const int gx = x0 + ti, gy = y0 + tj;
     const long long ai = (long long)(k + gin) * isz + (long long)(gy + gin) * isy + (gx + gin);
     const long long ao = GH ? (long long)(k + gout) * osz + (long long)(gy + gout) * osy + (gx + gout) : ai;
+    if (!index_ok(ai, in_extent, flags) || !index_ok(ao, out_extent, flags)) return;
     S Un[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Un[v] = Pol::update(__ldg(fin(v) + ai), c.dtdx, div[v]);

@@ -1,10 +1,10 @@
 """The bounds-checked build (libhydro_checked.so, compiled with HYDRO_CHECK_BOUNDS): every global index of
-the step kernels is tested against its patch array's extent and an index outside sets HYDRO_EBIT_OOB
-(the access skipped).  A sanitizer stand-in that faults nothing: the same steps -- periodic boxes of
-odd sizes, ghosted patches of odd sizes stored as unaligned views with odd strides, every tile shape,
-several z chunks, a tile shape per patch class, four precisions -- run through the checked library (in
-a child process that loads it) and through the default one; the checked run raises no bit and gives
-the same bits."""
+the step kernels and of the fused MHD tile kernel is tested against its array's extent and an index
+outside sets HYDRO_EBIT_OOB (the access skipped).  A sanitizer stand-in that faults nothing: the same
+steps -- periodic boxes of odd sizes, ghosted patches of odd sizes stored as unaligned views with odd
+strides, every tile shape, several z chunks, a tile shape per patch class, MHD boxes and patches, four
+precisions -- run through the checked library (in a child process that loads it) and through the
+default one; the checked run raises no bit and gives the same bits."""
 import os
 import subprocess
 import sys
@@ -60,6 +60,36 @@ def run_cases(hy):
         hy.hydro_step(c, ins, outs, dtp)
         for k, po in enumerate(outs):
             out["%s_patch%d_classes" % (precision, k)] = torch.stack(po.tensors).double().cpu().numpy()
+        # MHD (one fused tile kernel in float arithmetic): periodic boxes of odd sizes, then ghosted
+        # patches of odd sizes stored as views with odd strides, one element into their buffers
+        for si, shape in enumerate([(13, 21, 35), (5, 9, 3)]):
+            Um = workloads.mhd_state(shape, seed=70 + si, beta=0.5, mach=1.5, psi_amp=0.05)
+            Um = Um.to("cuda", dtype).contiguous()
+            dx = 1.0 / shape[2]
+            dm = torch.empty(2, dtype=torch.float64, device="cuda")
+            hy.hydro_mhd_cfl_dt(c, Um, dx, dm[0:1])
+            Vm = torch.empty_like(Um)
+            hy.hydro_mhd_step(c, Um, Vm, dx, dm[0:1], dm[1:2])
+            out["%s_mhd_box%d" % (precision, si)] = Vm.double().cpu().numpy()
+            out["%s_mhd_box%d_dt" % (precision, si)] = dm.cpu().numpy()
+        mparent = workloads.mhd_state((18, 14, 22), seed=72, beta=0.5, mach=1.5, psi_amp=0.05)
+        mins, mouts = [], []
+        for k, ((nx, ny, nz), o) in enumerate(zip([(35, 9, 5), (3, 17, 11), (1, 1, 2)],
+                                                   [(2, 3, 4), (10, 0, 7), (5, 5, 5)])):
+            Ug = workloads.ghosted_from_periodic(mparent, o, (nx, ny, nz)).to("cuda", dtype)
+            F, Z, Y, X = Ug.shape
+            gout = 2 * (k % 2)
+            bi = torch.zeros((F, Z, Y, X + 2), dtype=dtype, device="cuda")
+            bo = torch.zeros((F, nz + 2 * gout, ny + 2 * gout, nx + 2 * gout + 3), dtype=dtype, device="cuda")
+            bi[:, :, :, 1:1 + X].copy_(Ug)
+            mins.append(hy.MhdPatch(bi[:, :, :, 1:1 + X], 2, 1.0 / 32))
+            mouts.append(hy.MhdPatch(bo[:, :, :, 1:1 + nx + 2 * gout], gout, 1.0 / 32))
+        dtm = torch.empty(2 * len(mins), dtype=torch.float64, device="cuda")
+        hy.hydro_mhd_cfl_patches(c, mins, dtm[:len(mins)])
+        hy.hydro_mhd_step_patches(c, mins, mouts, dtm[:len(mins)], dtm[len(mins):])
+        for k, po in enumerate(mouts):
+            out["%s_mhd_patch%d" % (precision, k)] = torch.stack(po.tensors).double().cpu().numpy()
+        out["%s_mhd_patch_dt" % precision] = dtm.cpu().numpy()
         rc, b = hy.hydro_get_error(c)
         bits |= b
         hy.hydro_finalize(c)
